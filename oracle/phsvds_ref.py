@@ -1,0 +1,588 @@
+"""Plain CPU FP64 restatement of the PHSVDS method -- oracle code.
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU-baseline
+leg of the benchmark may import this module.  It shares no code with the GPU
+path; sparse products (scipy CSR @ dense) and the symmetric eigensolver and SVD
+of the small projected matrices (numpy/LAPACK) serve as library primitives.
+
+Paper: L. Wu and A. Stathopoulos, "A preconditioned hybrid SVD method for
+computing accurately singular triplets of large matrices" (arXiv 1408.5535).
+
+Steps, in the paper's order:
+* stage 1 (Algorithm 1): block GD+k on C = A^T A, convergence test with the
+  dynamic tolerance delta_C = max(delta * s_i / s_n, eps) (Sec. 3.1, eq. for
+  delta_C, Algorithm 1 step 2), then an optional Rayleigh-Ritz on the returned
+  basis (Algorithm 1 step 3, Sec. 3.1);
+* switch test delta < eps ||A|| / s_i (Sec. 3.1);
+* stage 2 (Algorithm 2): GD on B = [0 A^T; A 0] with the refined projection
+  min ||(B - s I) V y|| through an incrementally updated QR of W - s V, one
+  target at a time, locking and re-introduction of the next initial guess;
+* final triplet test sqrt(||r_u||^2 + ||r_v||^2) < ||A|| delta (Sec. 5).
+
+GD+k itself is named but not defined in the paper (Sec. 2.2, Sec. 5: "GD+k",
+"GD_Olsen_PlusK"); the restart with k previous Ritz vectors and the Olsen form
+of the correction follow the method as its authors published it
+(Stathopoulos, SIAM J. Sci. Comput. 29(2), 2007).
+
+Readings where the paper is silent are marked READING and listed with the
+design notes of the repository.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import math
+
+import numpy as np
+import scipy.sparse as sp
+
+EPS64 = 2.0 ** -52
+EPS32 = 2.0 ** -23
+
+# SplitMix64 streams for the random vectors the method itself draws.
+RS_INIT = 0x1000    # columns 2..b of the initial block
+RS_BREAK = 0x2000   # replacement of a numerically dependent new basis vector
+RS_U = 0x3000       # random left vector for an (extremely) small sigma
+
+
+# ---------------------------------------------------------------------------
+# random vectors the method draws (counter-based SplitMix64, Vigna's constants)
+# ---------------------------------------------------------------------------
+
+def _splitmix(seed: int, stream: int, count: int) -> np.ndarray:
+    mask = (1 << 64) - 1
+    with np.errstate(over="ignore"):
+        key = np.uint64(seed & mask) ^ (np.uint64(stream & mask) * np.uint64(0xD1B54A32D192ED03))
+        z = np.arange(1, count + 1, dtype=np.uint64) * np.uint64(0x9E3779B97F4A7C15) + key
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def rand_vec(seed: int, stream: int, n: int) -> np.ndarray:
+    """Uniform entries in [-1, 1): 2 * (top 53 bits * 2^-53) - 1."""
+    z = _splitmix(seed, stream, n)
+    return (z >> np.uint64(11)).astype(np.float64) * (2.0 / 9007199254740992.0) - 1.0
+
+
+# ---------------------------------------------------------------------------
+# operators
+# ---------------------------------------------------------------------------
+
+def as_scipy(csr) -> sp.csr_matrix:
+    return sp.csr_matrix((np.asarray(csr.val, dtype=np.float64), np.asarray(csr.col),
+                          np.asarray(csr.row_ptr)), shape=(csr.m, csr.n))
+
+
+class Ops:
+    """Products with C = A^T A and B = [0 A^T; A 0] (Section 1), counting matvecs.
+
+    ``mv_A`` / ``mv_At`` count products of one vector with A and with A^T.
+    """
+
+    def __init__(self, A: sp.csr_matrix):
+        self.A = A
+        self.At = A.T.tocsr()
+        self.m, self.n = A.shape
+        self.mv_A = 0
+        self.mv_At = 0
+
+    def C(self, X: np.ndarray) -> np.ndarray:
+        X = X.reshape(self.n, -1)
+        self.mv_A += X.shape[1]
+        self.mv_At += X.shape[1]
+        return self.At @ (self.A @ X)
+
+    def B(self, X: np.ndarray) -> np.ndarray:
+        X = X.reshape(self.m + self.n, -1)
+        n = self.n
+        self.mv_A += X.shape[1]
+        self.mv_At += X.shape[1]
+        return np.vstack([self.At @ X[n:], self.A @ X[:n]])
+
+    def Av(self, v):
+        self.mv_A += 1 if v.ndim == 1 else v.shape[1]
+        return self.A @ v
+
+    def Atu(self, u):
+        self.mv_At += 1 if u.ndim == 1 else u.shape[1]
+        return self.At @ u
+
+
+# ---------------------------------------------------------------------------
+# orthogonalisation (classical Gram-Schmidt applied twice)
+# ---------------------------------------------------------------------------
+
+def orth_append(Q: np.ndarray, T: np.ndarray, seed: int, counter: list, drop_tol: float = 1e-10):
+    """Orthonormalise the columns of T, one at a time, against Q and each other.
+
+    Each column gets two passes of classical Gram-Schmidt against all previous
+    columns, then is normalised.  A column whose remaining norm is below
+    drop_tol times its input norm is numerically dependent; it is replaced by a
+    random vector (stream RS_BREAK + counter) and orthogonalised again.
+    """
+    basis = Q
+    out = []
+    for c in range(T.shape[1]):
+        t = T[:, c].copy()
+        for attempt in range(4):
+            nin = np.linalg.norm(t)
+            for _ in range(2):
+                if basis.shape[1]:
+                    t = t - basis @ (basis.T @ t)
+            nout = np.linalg.norm(t)
+            if nin > 0 and nout > drop_tol * nin:
+                break
+            t = rand_vec(seed, RS_BREAK + counter[0], T.shape[0])
+            counter[0] += 1
+        t = t / np.linalg.norm(t)
+        out.append(t)
+        basis = np.column_stack([basis, t]) if basis.shape[1] else t[:, None]
+    return np.column_stack(out) if out else np.zeros((T.shape[0], 0))
+
+
+def qr_cgs2(Z: np.ndarray, seed: int, counter: list):
+    """Z = Q R, column by column with classical Gram-Schmidt applied twice.
+
+    A column that is numerically in the span of the previous ones keeps its
+    (tiny) R diagonal and gets a random orthonormal completion for q.
+    """
+    N, j = Z.shape
+    Q = np.zeros((N, j))
+    R = np.zeros((j, j))
+    for c in range(j):
+        Q[:, c], R[:c + 1, c] = qr_add_column(Q[:, :c], Z[:, c], seed, counter)
+    return Q, R
+
+
+def qr_add_column(Q: np.ndarray, z: np.ndarray, seed: int, counter: list):
+    """One-column update of a QR factorisation (Algorithm 2, step 8)."""
+    c = Q.shape[1]
+    r = np.zeros(c + 1)
+    q = z.copy()
+    for _ in range(2):
+        if c:
+            h = Q.T @ q
+            q = q - Q @ h
+            r[:c] += h
+    rho = np.linalg.norm(q)
+    r[c] = rho
+    if rho > 1e-300 and rho > 1e-14 * np.linalg.norm(z):
+        q = q / rho
+    else:
+        # numerically dependent column: keep R, complete Q with a random direction
+        q = orth_append(Q, rand_vec(seed, RS_BREAK + counter[0], z.size)[:, None], seed, counter)[:, 0]
+        counter[0] += 1
+    return q, r
+
+
+# ---------------------------------------------------------------------------
+# options / results
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Opts:
+    block: int = 1              # block size of stage 1
+    max_basis: int = 35         # maxBasisSize (Sec. 5)
+    min_restart: int = 21       # minRestartSize (Sec. 5)
+    max_restarts: int = 10000   # per stage (Sec. 5)
+    eps_factor: float = 4.0     # READING: delta_C floor is eps_factor * eps (O(||C|| eps), Sec. 3.1)
+    stage1_eps: float = EPS64   # unit roundoff of stage 1 (EPS32 for the mixed form)
+    rr: bool = True             # Algorithm 1 step 3
+    stage2: bool = True         # False: stage 1 only
+    precond: str = "none"       # "none" or "jacobi" (diag(C) - theta)^-1 with Olsen
+    seed: int = 0
+    max_iters: int = 10 ** 7
+    trace: object = None        # optional callable(stage, iteration, info dict)
+
+
+@dataclass
+class Result:
+    sigma: np.ndarray
+    U: np.ndarray
+    V: np.ndarray
+    resid: np.ndarray                 # sqrt(||r_u||^2 + ||r_v||^2) per triplet
+    normA: float
+    stats: dict = field(default_factory=dict)
+
+
+# ---------------------------------------------------------------------------
+# stage 1: block GD+k on a symmetric operator
+# ---------------------------------------------------------------------------
+
+def gdk(apply_op, n: int, k: int, largest: bool, tol_fn, o: Opts, diagC=None, X0=None,
+        stats=None):
+    """Block GD+k for the k extreme eigenpairs of a symmetric operator.
+
+    Per iteration: Rayleigh-Ritz on the basis V (H = V^T W, W = op(V)); the
+    first b unconverged Ritz pairs in target order are the block; residuals
+    r = W s - theta V s; converged pairs are locked (moved out of the basis);
+    when the basis would exceed max_basis it is restarted with the
+    min_restart - b best Ritz vectors plus the b Ritz vectors of the previous
+    iteration (the "+k" of GD+k); the correction is t = r (no preconditioner)
+    or the Olsen form t = M r - e M x, e = x^T M r / x^T M x, with
+    M = (diag(C) - theta I)^-1.  New vectors are orthonormalised against the
+    locked vectors and the basis (classical Gram-Schmidt twice).
+
+    tol_fn(theta_i, theta_max) gives the residual threshold of Ritz value
+    theta_i, theta_max being the largest Ritz value seen (the ||C|| estimate).
+    Returns (lam (k,), X (n x k), state) with the final basis in ``state``.
+    """
+    stats = {} if stats is None else stats
+    b = max(1, min(o.block, k))
+    maxb, mins, kp = o.max_basis, o.min_restart, max(1, min(o.block, k))
+    counter = [0]
+    Xl = np.zeros((n, 0))
+    lam_l = []
+    V = np.zeros((n, 0))
+    W = np.zeros((n, 0))
+    H = np.zeros((0, 0))
+    if X0 is not None:
+        T = np.array(X0, dtype=np.float64).reshape(n, -1)
+    else:
+        T = np.empty((n, b))
+        T[:, 0] = 1.0 / math.sqrt(n)           # ones(n,1) start (Sec. 5), normalised
+        for c in range(1, b):
+            T[:, c] = rand_vec(o.seed, RS_INIT + c, n)
+    s_prev = np.zeros((0, 0))
+    theta_max = 0.0
+    it = restarts = 0
+    theta = np.zeros(0)
+    S = np.zeros((0, 0))
+    while True:
+        # ---- expand the basis with the new block
+        if T.shape[1]:
+            Tn = orth_append(np.hstack([Xl, V]), T, o.seed, counter)
+            Wn = apply_op(Tn)
+            Hvw = V.T @ Wn
+            Htt = Tn.T @ Wn
+            Htt = 0.5 * (Htt + Htt.T)
+            j0 = V.shape[1]
+            H = np.block([[H, Hvw], [Hvw.T, Htt]]) if j0 else Htt
+            V = np.hstack([V, Tn])
+            W = np.hstack([W, Wn])
+            if s_prev.shape[1]:
+                s_prev = np.vstack([s_prev, np.zeros((Tn.shape[1], s_prev.shape[1]))])
+        j = V.shape[1]
+        # ---- Rayleigh-Ritz
+        theta, S = np.linalg.eigh(H)
+        if largest:
+            theta, S = theta[::-1], S[:, ::-1]
+        theta_max = max(theta_max, float(np.max(theta)))
+        it += 1
+        nt = min(b, k - len(lam_l), j)
+        X = V @ S[:, :nt]
+        R = W @ S[:, :nt] - X * theta[:nt]
+        rn = np.linalg.norm(R, axis=0)
+        conv = [i for i in range(nt) if rn[i] < tol_fn(theta[i], theta_max)]
+        unconv = [i for i in range(nt) if i not in conv]
+        for i in conv:
+            Xl = np.column_stack([Xl, X[:, i]])
+            lam_l.append(float(theta[i]))
+        if len(lam_l) >= k:
+            stats.update(iters=it, restarts=restarts, theta_max=theta_max)
+            order = np.argsort(lam_l)
+            if largest:
+                order = order[::-1]
+            state = dict(V=V, W=W, theta=theta, S=S, conv=conv)
+            return np.array(lam_l)[order], Xl[:, order], state
+        if it >= o.max_iters:
+            raise RuntimeError("stage 1: iteration limit")
+        keep_all = [c for c in range(j) if c not in conv]
+        Y = None
+        if len(keep_all) + len(unconv) > maxb:
+            # ---- thick restart with +k previous Ritz vectors
+            restarts += 1
+            if restarts > o.max_restarts:
+                raise RuntimeError("stage 1: restart limit")
+            nkeep = min(mins - kp, len(keep_all))
+            Yk = S[:, keep_all[:nkeep]]
+            cols = [Yk]
+            if s_prev.shape[1]:
+                P = s_prev.copy()
+                Sc = S[:, conv]
+                basis = np.hstack([Sc, Yk])
+                for c in range(P.shape[1]):
+                    p = P[:, c]
+                    for _ in range(2):
+                        p = p - basis @ (basis.T @ p)
+                    nrm = np.linalg.norm(p)
+                    if nrm > 1e-8:
+                        p = p / nrm
+                        basis = np.column_stack([basis, p])
+                        cols.append(p[:, None])
+            Y = np.hstack(cols)
+        elif conv:
+            Y = S[:, keep_all]
+        if Y is not None:
+            V = V @ Y
+            W = W @ Y
+            H = Y.T @ H @ Y
+            H = 0.5 * (H + H.T)
+            s_prev = Y.T @ S[:, unconv]
+        else:
+            s_prev = S[:, unconv].copy()
+        # ---- corrections for the unconverged targets
+        if unconv:
+            Ru = R[:, unconv]
+            Xu = X[:, unconv]
+            if o.precond == "jacobi" and diagC is not None:
+                T = np.empty_like(Ru)
+                for c, i in enumerate(unconv):
+                    d = diagC - theta[i]
+                    guard = EPS64 * max(theta_max, 1e-300)
+                    d = np.where(np.abs(d) < guard, np.where(d < 0, -guard, guard), d)
+                    Mr = Ru[:, c] / d
+                    Mx = Xu[:, c] / d
+                    e = float(Xu[:, c] @ Mr) / float(Xu[:, c] @ Mx)
+                    T[:, c] = Mr - e * Mx
+            else:
+                T = Ru.copy()
+        else:
+            T = np.zeros((n, 0))
+
+
+def stage1_tol(delta: float, o: Opts):
+    """Algorithm 1 step 2: ||r_C|| < delta_C ||C||, delta_C = max(delta s_i/s_n, eps).
+
+    With ||C|| ~ s_n^2 = theta_max this is ||r_C|| < max(delta s_i s_n, eps theta_max).
+    READING: the floor is eps_factor * eps (the attainable O(||C|| eps) of Sec. 3.1).
+    """
+    floor = o.eps_factor * o.stage1_eps
+
+    def tol(theta_i, theta_max):
+        s_i = math.sqrt(max(theta_i, 0.0))
+        s_n = math.sqrt(max(theta_max, 0.0))
+        return max(delta * s_i * s_n, floor * theta_max)
+
+    return tol
+
+
+def rayleigh_ritz_post(ops: Ops, Xl: np.ndarray, state: dict, k: int, largest: bool, o: Opts):
+    """Algorithm 1 step 3: Rayleigh-Ritz of C on the returned basis.
+
+    READING: the basis is the k locked vectors plus the min_restart - k best
+    remaining Ritz vectors of the final basis (min_restart vectors in all, the
+    "21 extra matrix-vector operations" of Sec. 5.3), with fresh products.
+    """
+    V, S = state["V"], state["S"]
+    conv = set(state["conv"])
+    extra = max(0, min(o.min_restart - k, V.shape[1] - len(conv)))
+    cols = [c for c in range(S.shape[1]) if c not in conv][:extra]
+    Z = np.hstack([Xl, V @ S[:, cols]]) if cols else Xl
+    Q = orth_append(np.zeros((Z.shape[0], 0)), Z, o.seed, [10 ** 6])
+    WQ = ops.C(Q)
+    Hq = Q.T @ WQ
+    Hq = 0.5 * (Hq + Hq.T)
+    th, Sq = np.linalg.eigh(Hq)
+    if largest:
+        th, Sq = th[::-1], Sq[:, ::-1]
+    return th[:k], Q @ Sq[:, :k]
+
+
+# ---------------------------------------------------------------------------
+# stage 2: refined projection on B (Algorithm 2)
+# ---------------------------------------------------------------------------
+
+def stage2(ops: Ops, sig: np.ndarray, Vt: np.ndarray, normA: float, delta: float, o: Opts,
+           stats: dict):
+    """Algorithm 2 with a GD outer loop (the PHSVDS(GD+k) variant of Sec. 5).
+
+    Targets are the k stage-1 values in the given order, one at a time, with
+    shift s = the stage-1 value.  Per iteration: QR of W - s V (full at start,
+    restart and new target; one-column update otherwise); eig of H ordered by
+    closeness to s; smallest right singular vector s1 of R gives the refined
+    vector x = V s1 and its Rayleigh quotient theta1 = s1^T H s1; the residual
+    r = W s1 - theta1 V s1 decides locking (||r_B|| < delta ||A|| / sqrt(2),
+    Sec. 3.1).  On locking the next initial guess is re-introduced.  The new
+    direction is t = r.
+    READINGS: restart keeps [s1, Ritz vectors closest to s, previous s1];
+    the shift becomes theta1 at a restart once the residual is below that of
+    the initial guess; b = 1.
+    """
+    m, n = ops.m, ops.n
+    N = m + n
+    k = sig.size
+    mins, maxb = o.min_restart, o.max_basis
+    counter = [2 * 10 ** 6]
+    # ---- initial guesses [v; A v / s] / sqrt(2) (Algorithm 2 step 1, Sec. 3.3)
+    x0 = np.zeros((N, k))
+    for i in range(k):
+        v = Vt[:, i] / np.linalg.norm(Vt[:, i])
+        if sig[i] > math.sqrt(EPS64) * normA:
+            u = ops.Av(v) / sig[i]
+        else:
+            u = rand_vec(o.seed, RS_U + i, m)   # Sec. 3.3: tiny sigma, random left vector
+        u = u / np.linalg.norm(u)
+        x0[:n, i] = v / math.sqrt(2.0)
+        x0[n:, i] = u / math.sqrt(2.0)
+    # ---- initial basis: K_{s-k}(B, x0_1) and the guesses (Algorithm 2 step 2)
+    q = max(1, mins - k)
+    V = orth_append(np.zeros((N, 0)), x0[:, :1], o.seed, counter)
+    for _ in range(q - 1):
+        V = np.hstack([V, orth_append(V, ops.B(V[:, -1]), o.seed, counter)])
+    nguess = min(k - 1, maxb - 1 - V.shape[1])
+    if nguess > 0:
+        V = np.hstack([V, orth_append(V, x0[:, 1:1 + nguess], o.seed, counter)])
+    W = ops.B(V)
+    H = V.T @ W
+    H = 0.5 * (H + H.T)
+    Xl = np.zeros((N, 0))
+    th_l = []
+    target = 0
+    shift = float(sig[0])
+    qr_full = True
+    Q = R = None
+    s_prev = None
+    r0 = None
+    it = restarts = 0
+    normA_est = normA
+    while True:
+        it += 1
+        if it > o.max_iters:
+            raise RuntimeError("stage 2: iteration limit")
+        j = V.shape[1]
+        if qr_full:
+            Q, R = qr_cgs2(W - shift * V, o.seed, counter)
+            qr_full = False
+        theta, S = np.linalg.eigh(H)
+        normA_est = max(normA_est, float(np.max(np.abs(theta))))
+        order = np.argsort(np.abs(theta - shift), kind="stable")
+        theta, S = theta[order], S[:, order]
+        _, _, SRt = np.linalg.svd(R)
+        s1 = SRt[-1]
+        th1 = float(s1 @ H @ s1)
+        x = V @ s1
+        r = W @ s1 - th1 * x
+        rn = float(np.linalg.norm(r))
+        if r0 is None:
+            r0 = rn
+        if o.trace is not None:
+            o.trace(2, it, dict(target=target, shift=shift, theta1=th1, rnorm=rn, j=j, restarts=restarts))
+        if rn < delta * normA / math.sqrt(2.0):
+            Xl = np.column_stack([Xl, x])
+            th_l.append(th1)
+            target += 1
+            if target >= k:
+                break
+            Y = SRt[:-1].T                     # orthonormal complement of s1
+            V, W = V @ Y, W @ Y
+            H = Y.T @ H @ Y
+            H = 0.5 * (H + H.T)
+            # re-introduce the next initial guess (Algorithm 2 step 9)
+            t = orth_append(np.hstack([Xl, V]), x0[:, target:target + 1], o.seed, counter)
+            wt = ops.B(t)
+            H = np.block([[H, V.T @ wt], [wt.T @ V, t.T @ wt]])
+            H = 0.5 * (H + H.T)
+            V, W = np.hstack([V, t]), np.hstack([W, wt])
+            shift = float(sig[target])
+            qr_full = True
+            s_prev = None
+            r0 = None
+            continue
+        if j >= maxb:
+            restarts += 1
+            if restarts > o.max_restarts:
+                raise RuntimeError("stage 2: restart limit")
+            cand = [s1] + [S[:, c] for c in range(S.shape[1])]
+            if s_prev is not None:
+                cand_prev = s_prev
+            else:
+                cand_prev = None
+            cols = []
+            for c in cand:
+                if len(cols) >= mins - 1:
+                    break
+                p = c.copy()
+                for _ in range(2):
+                    for qv in cols:
+                        p = p - qv * (qv @ p)
+                nrm = np.linalg.norm(p)
+                if nrm > 1e-8:
+                    cols.append(p / nrm)
+            if cand_prev is not None:
+                p = cand_prev.copy()
+                for _ in range(2):
+                    for qv in cols:
+                        p = p - qv * (qv @ p)
+                nrm = np.linalg.norm(p)
+                if nrm > 1e-8:
+                    cols.append(p / nrm)
+            Y = np.column_stack(cols)
+            V, W = V @ Y, W @ Y
+            H = Y.T @ H @ Y
+            H = 0.5 * (H + H.T)
+            s1 = Y.T @ s1
+            if rn < r0:
+                shift = th1
+            qr_full = True
+        s_prev = s1.copy()
+        # ---- expand with t = r (Algorithm 2 step 4)
+        t = orth_append(np.hstack([Xl, V]), r[:, None], o.seed, counter)
+        wt = ops.B(t)
+        H = np.block([[H, V.T @ wt], [wt.T @ V, t.T @ wt]])
+        H = 0.5 * (H + H.T)
+        V, W = np.hstack([V, t]), np.hstack([W, wt])
+        s_prev = np.concatenate([s_prev, [0.0]])
+        if not qr_full:
+            qn, rcol = qr_add_column(Q, (wt - shift * t)[:, 0], o.seed, counter)
+            Q = np.column_stack([Q, qn])
+            R = np.block([[R, rcol[:-1, None]], [np.zeros((1, R.shape[1])), rcol[-1:, None]]])
+    stats.update(iters2=it, restarts2=restarts)
+    return np.array(th_l), Xl, normA_est
+
+
+# ---------------------------------------------------------------------------
+# driver
+# ---------------------------------------------------------------------------
+
+def triplet_residuals(A: sp.csr_matrix, sigma, U, V):
+    """||A v - s u||, ||A^T u - s v|| and their root-sum-square (Sec. 5 criterion)."""
+    rv = np.linalg.norm(A @ V - U * sigma, axis=0)
+    ru = np.linalg.norm(A.T @ U - V * sigma, axis=0)
+    return ru, rv, np.sqrt(ru * ru + rv * rv)
+
+
+def phsvds(csr, k: int, largest: bool = False, delta: float = 1e-14, o: Opts | None = None) -> Result:
+    """PHSVDS (Sections 3-5) for the k smallest or largest singular triplets of A."""
+    o = Opts() if o is None else o
+    A = as_scipy(csr)
+    m, n = A.shape
+    if m < n:
+        raise ValueError("PHSVDS needs m >= n")
+    ops = Ops(A)
+    stats: dict = {}
+    diagC = np.asarray(A.multiply(A).sum(axis=0)).ravel() if o.precond == "jacobi" else None
+    lam, Xv, state = gdk(ops.C, n, k, largest, stage1_tol(delta, o), o, diagC=diagC, stats=stats)
+    theta_max = stats["theta_max"]
+    normA = math.sqrt(theta_max)
+    # stage-1 triplets: s = ||A v||, u = A v / s (r_v = 0)
+    AV = ops.Av(Xv)
+    sig1 = np.linalg.norm(AV, axis=0)
+    U1 = AV / np.where(sig1 > 0, sig1, 1.0)
+    ru, rv, res = triplet_residuals(A, sig1, U1, Xv)
+    ops.mv_At += k
+    floor = o.eps_factor * o.stage1_eps
+    need2 = bool(np.any(delta < floor * normA / np.maximum(sig1, 1e-300)) or np.any(res >= delta * normA))
+    stats.update(stage1_mv_A=ops.mv_A, stage1_mv_At=ops.mv_At, switched=need2)
+    if not need2 or not o.stage2:
+        order = np.argsort(sig1)[::-1] if largest else np.argsort(sig1)
+        return Result(sig1[order], U1[:, order], Xv[:, order], res[order], normA,
+                      dict(stats, mv_A=ops.mv_A, mv_At=ops.mv_At))
+    if o.rr:
+        lam, Xv = rayleigh_ritz_post(ops, Xv, state, k, largest, o)
+    sig_s = np.sqrt(np.maximum(lam, 0.0))
+    # stage 2 in ascending (smallest) or descending (largest) order of the shifts
+    th, X2, normA2 = stage2(ops, sig_s, Xv, normA, delta, o, stats)
+    Vv = X2[:n]
+    Uu = X2[n:]
+    Vv = Vv / np.linalg.norm(Vv, axis=0)
+    Uu = Uu / np.linalg.norm(Uu, axis=0)
+    sig = np.einsum("ij,ij->j", Uu, A @ Vv)
+    neg = sig < 0
+    Uu[:, neg] *= -1.0
+    sig = np.abs(sig)
+    ru, rv, res = triplet_residuals(A, sig, Uu, Vv)
+    order = np.argsort(sig)[::-1] if largest else np.argsort(sig)
+    return Result(sig[order], Uu[:, order], Vv[:, order], res[order], normA,
+                  dict(stats, mv_A=ops.mv_A, mv_At=ops.mv_At))
