@@ -1,0 +1,191 @@
+/*
+ * phsvds.h -- C ABI of the GB300 (sm_103a) implementation of PHSVDS.
+ *
+ * PHSVDS (Wu & Stathopoulos, "A preconditioned hybrid SVD method for computing
+ * accurately singular triplets of large matrices", arXiv 1408.5535) computes the
+ * k smallest (or largest) singular triplets (sigma_i, u_i, v_i) of a sparse
+ * A in R^{m x n}, m >= n, full column rank (Section 1, eq. 1.1), in two stages:
+ *   stage 1 (Algorithm 1): block GD+k on C = A^T A to the accuracy the normal
+ *           equations allow (Section 3.1, the dynamic tolerance delta_C);
+ *   stage 2 (Algorithm 2): Jacobi-Davidson-type outer loop on the augmented
+ *           B = [0 A^T; A 0] with the refined projection (Section 3.2),
+ * until sqrt(||r_u||^2 + ||r_v||^2) <= tol * ||A|| (Section 5).
+ *
+ * Conventions for every entry point:
+ *  - All matrices are dense column-major unless stated otherwise; CSR arrays
+ *    are 0-based with row_ptr[0] = 0 and row_ptr[m] = nnz, column indices of a
+ *    row strictly increasing (validated; violation -> PHSVDS_ERR_INVALID).
+ *  - The caller owns every pointer it passes; the library never frees them.
+ *    Pointers are host pointers unless the argument says "device" or the
+ *    call's ptr_on_device flag is 1.
+ *  - The library owns its device copies and workspaces; they live until
+ *    phsvds_destroy (or until the next solve on the same handle).
+ *  - Errors: every call returns a phsvds_status.  On error nothing is written to
+ *    the output arrays except what the status documents; phsvds_last_error()
+ *    returns a one-line description of the last failure on this handle.
+ *  - A handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef PHSVDS_H
+#define PHSVDS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct phsvds_ctx* phsvds_handle;
+
+typedef enum {
+    PHSVDS_OK = 0,
+    PHSVDS_ERR_INVALID = 1,        /* bad argument, CSR structure, m < n, k out of range */
+    PHSVDS_ERR_NOT_CONVERGED = 2,  /* max_restarts reached (Section 5: 10000 restarts) */
+    PHSVDS_ERR_BREAKDOWN = 3,      /* orthogonalisation could not extend the basis */
+    PHSVDS_ERR_NAN = 4,            /* a NaN/Inf appeared in A or in the iteration */
+    PHSVDS_ERR_TIMEOUT = 5,        /* wall-clock limit (opts.time_limit_s) reached */
+    PHSVDS_ERR_CUDA = 6,           /* a CUDA runtime call failed */
+    PHSVDS_ERR_OOM = 7             /* device allocation failed */
+} phsvds_status;
+
+typedef enum { PHSVDS_SMALLEST = 0, PHSVDS_LARGEST = 1 } phsvds_target;
+
+/* Correction operator of stage 1 (Section 4): identity (plain GD+k), or the
+ * Jacobi preconditioner M = (diag(C) - theta I)^{-1}, diag(C)_j = ||A e_j||^2,
+ * applied in the Olsen form t = M r - e M x, e = x^T M r / x^T M x. */
+typedef enum { PHSVDS_PREC_NONE = 0, PHSVDS_PREC_JACOBI = 1 } phsvds_precond;
+
+/* PHSVDS_FP64: every step in FP64.  PHSVDS_MIXED: stage 1 first runs with FP32
+ * storage, FP32 SpMM and Gram products (FP64 reduction across thread blocks) to
+ * the FP32-attainable tolerance, then continues in FP64 from that basis; the
+ * projected eigenproblems, stage 2 and the final residuals are FP64. */
+typedef enum { PHSVDS_FP64 = 0, PHSVDS_MIXED = 1 } phsvds_precision;
+
+/* SpMM schedule for C X = A^T (A X): fused single pass with L2 atomics, or two
+ * phases (Z = A X kept in L2, then A^T Z from a CSC copy), or picked by timing. */
+typedef enum { PHSVDS_SPMM_AUTO = 0, PHSVDS_SPMM_FUSED_ATOMIC = 1, PHSVDS_SPMM_TWO_PHASE = 2 } phsvds_spmm_schedule;
+
+typedef struct {
+    int block_size;        /* stage-1 block size b (1..8), default 1 */
+    int max_basis;         /* maxBasisSize, default 35 (Section 5) */
+    int min_restart;       /* minRestartSize, default 21 (Section 5) */
+    int max_restarts;      /* per stage, default 10000 (Section 5) */
+    double eps_factor;     /* delta_C floor = eps_factor * eps (O(||C|| eps), Sec. 3.1), default 4 */
+    phsvds_precision precision;
+    phsvds_spmm_schedule spmm;
+    int stage2;            /* 1 = automatic switch (Sec. 3.1), 0 = stage 1 only */
+    int rayleigh_ritz;     /* 1 = Algorithm 1 step 3 before stage 2, default 1 */
+    uint64_t seed;         /* SplitMix64 seed of the random vectors the method draws */
+    double time_limit_s;   /* 0 = none */
+} phsvds_opts;
+
+typedef struct {
+    int64_t matvecs_A;     /* products of one vector with A */
+    int64_t matvecs_At;    /* products of one vector with A^T */
+    int64_t iters_stage1;  /* outer iterations (all stage-1 passes) */
+    int64_t iters_stage1_fp32; /* of which in FP32 (mixed precision) */
+    int64_t iters_stage2;
+    int64_t restarts;
+    int switched;          /* 1 if stage 2 ran */
+    double norm_A_est;     /* running ||A|| estimate (largest Ritz value) */
+    double t_stage1_ms, t_stage2_ms, t_total_ms;
+    int spmm_schedule;     /* schedule used: 1 fused atomic, 2 two-phase */
+} phsvds_stats;
+
+/* Create a context on CUDA device `device`.  cuda_stream: a cudaStream_t to run
+ * on, or NULL to let the library create its own. */
+phsvds_status phsvds_create(phsvds_handle* out, int device, void* cuda_stream);
+
+/* Fill *opts with the defaults listed above. */
+phsvds_status phsvds_default_opts(phsvds_opts* opts);
+
+/*
+ * k smallest (target = PHSVDS_SMALLEST) or largest singular triplets of A.
+ *  m, n, nnz     : A is m x n (m >= n >= 1) with nnz stored entries;
+ *  row_ptr       : m+1 int64 offsets; col_idx: nnz int32; val: nnz doubles (CSR);
+ *  ptr_on_device : 1 if row_ptr/col_idx/val are device pointers, else host;
+ *  k             : 1 <= k <= min(n, opts.min_restart - 1);
+ *  tol           : delta of the criterion sqrt(||r_u||^2+||r_v||^2) <= delta ||A||;
+ *  precond       : stage-1 correction operator;
+ *  opts          : NULL for defaults;
+ *  sigma[k], U (m x k), V (n x k), resid[k] : host outputs, sigma ascending for
+ *                  SMALLEST and descending for LARGEST; resid[i] is the final
+ *                  sqrt(||A v_i - s_i u_i||^2 + ||A^T u_i - s_i v_i||^2);
+ *                  any of U, V, resid may be NULL;
+ *  stats         : may be NULL; filled also on NOT_CONVERGED.
+ * The library copies A to the device (and builds its CSC copy) on each call.
+ */
+phsvds_status phsvds_solve(phsvds_handle h, int64_t m, int64_t n, int64_t nnz,
+                           const int64_t* row_ptr, const int32_t* col_idx, const double* val,
+                           int ptr_on_device, int k, phsvds_target target, double tol,
+                           phsvds_precond precond, const phsvds_opts* opts,
+                           double* sigma, double* U, double* V, double* resid,
+                           phsvds_stats* stats);
+
+/*
+ * Kernel-level entry point: Y = A^T (A X) for a block of b vectors (Section 1,
+ * C = A^T A), all pointers DEVICE pointers, FP64.  X and Y are n x b ROW-major
+ * (the b values of one row contiguous).  row_ptr int32 (nnz < 2^31).
+ * schedule 1 = fused single pass with atomics (Y is overwritten: the call zeroes
+ * it first), 2 = two phases through Z = A X (z: caller-provided m x b device
+ * scratch) using the CSC copy (csc_ptr n+1, csc_row nnz, csc_val nnz).
+ * b in {1, 2, 4, 8}.  Runs on the handle's stream; asynchronous.
+ */
+phsvds_status phsvds_ata_spmm_f64(phsvds_handle h, int schedule, int64_t m, int64_t n,
+                                  const int32_t* row_ptr, const int32_t* col_idx, const double* val,
+                                  const int32_t* csc_ptr, const int32_t* csc_row, const double* csc_val,
+                                  int b, const double* X, double* Y, double* z);
+
+/* Same in FP32 (values, X, Y and z float). */
+phsvds_status phsvds_ata_spmm_f32(phsvds_handle h, int schedule, int64_t m, int64_t n,
+                                  const int32_t* row_ptr, const int32_t* col_idx, const float* val,
+                                  const int32_t* csc_ptr, const int32_t* csc_row, const float* csc_val,
+                                  int b, const float* X, float* Y, float* z);
+
+/*
+ * Kernel-level entry point: CSR -> CSC transpose on the device (setup step of the
+ * two-phase SpMM).  Inputs/outputs are DEVICE pointers: row_ptr (m+1), col_idx,
+ * val (nnz); outputs csc_ptr (n+1), csc_row (nnz), csc_val (nnz).  Row indices
+ * within each column come out increasing (deterministic).
+ */
+phsvds_status phsvds_csr_to_csc_f64(phsvds_handle h, int64_t m, int64_t n, int64_t nnz,
+                                    const int32_t* row_ptr, const int32_t* col_idx, const double* val,
+                                    int32_t* csc_ptr, int32_t* csc_row, double* csc_val);
+
+/*
+ * Kernel-level entry point: one-CTA FP64 cyclic Jacobi eigensolver for a
+ * symmetric j x j matrix (the projected problem H = V^T C V of the Rayleigh-Ritz
+ * step; Algorithm 2 step 7).  DEVICE pointers.  H (j x j, column-major,
+ * overwritten by the rotated matrix, whose diagonal holds the eigenvalues),
+ * S (j x j, on entry the accumulated rotation -- identity for a cold start --
+ * on exit S * J, so that S^T H_in S = diag(theta) for a cold start), theta (j).
+ * 1 <= j <= 64.  Sweeps until every |h_pq| <= tol * sqrt(|h_pp h_qq|) or
+ * max_sweeps; *sweeps_out (device int) receives the sweep count.
+ */
+phsvds_status phsvds_jacobi_eig_f64(phsvds_handle h, int j, double* H, double* S, double* theta,
+                                    double tol, int max_sweeps, int* sweeps_out);
+
+/*
+ * Kernel-level entry point: one-CTA FP64 one-sided (Hestenes) Jacobi SVD of a
+ * j x j matrix G (refined projection, Algorithm 2 step 8: R = U Sigma S^T).
+ * DEVICE pointers.  G (column-major, overwritten by G * J = U Sigma), S (on
+ * entry an orthogonal start -- identity for a cold start -- on exit S * J),
+ * sig (j) the column norms of the result.  1 <= j <= 64.
+ */
+phsvds_status phsvds_jacobi_svd_f64(phsvds_handle h, int j, double* G, double* S, double* sig,
+                                    double tol, int max_sweeps, int* sweeps_out);
+
+/* Synchronise the handle's stream. */
+phsvds_status phsvds_sync(phsvds_handle h);
+
+/* One-line description of the last error on this handle ("" if none). */
+const char* phsvds_last_error(phsvds_handle h);
+
+const char* phsvds_status_string(phsvds_status s);
+
+void phsvds_destroy(phsvds_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PHSVDS_H */

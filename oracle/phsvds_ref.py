@@ -276,6 +276,9 @@ def gdk(apply_op, n: int, k: int, largest: bool, tol_fn, o: Opts, diagC=None, X0
         rn = np.linalg.norm(R, axis=0)
         conv = [i for i in range(nt) if rn[i] < tol_fn(theta[i], theta_max)]
         unconv = [i for i in range(nt) if i not in conv]
+        if o.trace is not None:
+            o.trace(1, it, dict(j=j, nlock=len(lam_l), theta0=float(theta[0]), rnorm0=float(rn[0]),
+                                theta_max=theta_max, nconv=len(conv)))
         for i in conv:
             Xl = np.column_stack([Xl, X[:, i]])
             lam_l.append(float(theta[i]))

@@ -1,0 +1,683 @@
+// One-CTA FP64 kernels for the projected (small) problems of PHSVDS:
+//  * cyclic two-sided Jacobi eigensolver for the Rayleigh-Ritz matrix
+//    H = V^T W (Algorithm 2 step 7; the projected problem of GD+k in stage 1),
+//    warm-startable: the working matrix A = S^T H S and the accumulated
+//    rotation S are kept between outer iterations, so only the entries coupled
+//    to the newly added basis vectors need rotating;
+//  * one-sided (Hestenes) Jacobi SVD of the refined-projection factor R
+//    (Algorithm 2 step 8), warm-startable the same way (G = R S);
+//  * Cholesky of a block Gram matrix (CholQR of the new block), the restart /
+//    locking transform builder and small gathers.
+// Small matrices are column-major with a leading dimension ld (<= 64).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ph {
+
+constexpr int SM_MAXJ = 64;
+constexpr int SM_THREADS = 256;
+
+// Round-robin (circle) pairing of jj (even) indices: round r, pair k.
+__device__ inline void rr_pair(int jj, int r, int k, int& p, int& q) {
+  const int m = jj - 1;
+  int a, b;
+  if (k == 0) {
+    a = r % m;
+    b = m;
+  } else {
+    a = (r + k) % m;
+    b = (r - k + m) % m;
+  }
+  p = a < b ? a : b;
+  q = a < b ? b : a;
+}
+
+// ---------------------------------------------------------------------------
+// Two-sided cyclic Jacobi.  A rotation is applied to pair (p, q) when
+// |a_pq| > thr, thr = tol * max_i |a_ii| (absolute accuracy tol * ||H||).
+// Each round rotates up to jj/2 disjoint pairs at once; the update of A is
+// done per 2 x 2 block (pair k rows, pair l columns), so one round needs a
+// single barrier after the rotation parameters and one after the update.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(SM_THREADS) k_jacobi_eig(int j, double* H, int ldh, double* S, int lds,
+                                                           double* theta, double tol, int max_sweeps,
+                                                           int* sweeps_out) {
+  extern __shared__ __align__(16) double dsm[];
+  double* A = dsm;                              // [SM_MAXJ * (SM_MAXJ + 1)]
+  double* Sm = A + SM_MAXJ * (SM_MAXJ + 1);     // [SM_MAXJ * (SM_MAXJ + 1)]
+  __shared__ double cs[SM_MAXJ / 2], sn[SM_MAXJ / 2], tt[SM_MAXJ / 2];
+  __shared__ int pp[SM_MAXJ / 2], qq[SM_MAXJ / 2], rot[SM_MAXJ / 2];
+  __shared__ double scale_s;
+  const int tid = threadIdx.x;
+  const int LA = SM_MAXJ + 1;
+  for (int e = tid; e < j * j; e += SM_THREADS) {
+    const int r = e % j, c = e / j;
+    A[r + c * LA] = H[r + (size_t)c * ldh];
+    Sm[r + c * LA] = S[r + (size_t)c * lds];
+  }
+  __syncthreads();
+  if (tid < 32) {
+    double mx = 0.0;
+    for (int i = tid; i < j; i += 32) mx = fmax(mx, fabs(A[i + i * LA]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (tid == 0) scale_s = mx;
+  }
+  __syncthreads();
+  double mxoff = 0.0;
+  for (int e = tid; e < j * j; e += SM_THREADS) {
+    const int r = e % j, c = e / j;
+    if (r != c) mxoff = fmax(mxoff, fabs(A[r + c * LA]));
+  }
+  // the scale must cover an all-zero diagonal (e.g. the augmented matrix)
+  for (int o = 16; o > 0; o >>= 1) mxoff = fmax(mxoff, __shfl_xor_sync(0xffffffffu, mxoff, o));
+  __shared__ double wmx[SM_THREADS / 32];
+  if ((tid & 31) == 0) wmx[tid >> 5] = mxoff;
+  __syncthreads();
+  if (tid == 0) {
+    double m2 = 0.0;
+    for (int w = 0; w < SM_THREADS / 32; ++w) m2 = fmax(m2, wmx[w]);
+    scale_s = fmax(scale_s, m2);
+  }
+  __syncthreads();
+  const double thr = tol * scale_s;
+  const int jj = j + (j & 1);
+  const int np = jj / 2;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    int any = 0;
+    for (int e = tid; e < j * j; e += SM_THREADS) {
+      const int r = e % j, c = e / j;
+      if (r < c && fabs(A[r + c * LA]) > thr) any = 1;
+    }
+    if (!__syncthreads_or(any)) break;
+    for (int round = 0; round < jj - 1; ++round) {
+      int mine = 0;
+      if (tid < np) {
+        int p, q;
+        rr_pair(jj, round, tid, p, q);
+        pp[tid] = p;
+        qq[tid] = q;
+        int r = 0;
+        if (q < j) {
+          const double apq = A[p + q * LA];
+          if (fabs(apq) > thr) {
+            const double tau = (A[q + q * LA] - A[p + p * LA]) / (2.0 * apq);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            const double c = 1.0 / sqrt(1.0 + t * t);
+            cs[tid] = c;
+            sn[tid] = t * c;
+            tt[tid] = t;
+            r = 1;
+          }
+        }
+        rot[tid] = r;
+        mine = r;
+      }
+      if (!__syncthreads_or(mine)) continue;
+      // 2 x 2 blocks (k, l): rows of pair k, columns of pair l
+      for (int it = tid; it < np * np; it += SM_THREADS) {
+        const int k = it / np, l = it % np;
+        const int rk = rot[k], rl = rot[l];
+        if (!rk && !rl) continue;
+        const int pk = pp[k], qk = qq[k], pl = pp[l], ql = qq[l];
+        if (k == l) {
+          if (qk < j) {
+            const double apq = A[pk + qk * LA];
+            A[pk + pk * LA] -= tt[k] * apq;
+            A[qk + qk * LA] += tt[k] * apq;
+            A[pk + qk * LA] = 0.0;
+            A[qk + pk * LA] = 0.0;
+          }
+          continue;
+        }
+        const double ck = rk ? cs[k] : 1.0, sk = rk ? sn[k] : 0.0;
+        const double cl = rl ? cs[l] : 1.0, sl = rl ? sn[l] : 0.0;
+        const bool vqk = qk < j, vql = ql < j;
+        const double b00 = A[pk + pl * LA];
+        const double b01 = vql ? A[pk + ql * LA] : 0.0;
+        const double b10 = vqk ? A[qk + pl * LA] : 0.0;
+        const double b11 = (vqk && vql) ? A[qk + ql * LA] : 0.0;
+        // rows: [p';q'] = [c -s; s c] [p; q]
+        const double r00 = ck * b00 - sk * b10, r01 = ck * b01 - sk * b11;
+        const double r10 = sk * b00 + ck * b10, r11 = sk * b01 + ck * b11;
+        // columns: [p' q'] = [p q] [c s; -s c]
+        A[pk + pl * LA] = cl * r00 - sl * r01;
+        if (vql) A[pk + ql * LA] = sl * r00 + cl * r01;
+        if (vqk) A[qk + pl * LA] = cl * r10 - sl * r11;
+        if (vqk && vql) A[qk + ql * LA] = sl * r10 + cl * r11;
+      }
+      // accumulate S <- S J
+      for (int it = tid; it < j * np; it += SM_THREADS) {
+        const int row = it / np, k = it % np;
+        if (!rot[k]) continue;
+        const int p = pp[k], q = qq[k];
+        const double sp = Sm[row + p * LA], sq = Sm[row + q * LA];
+        Sm[row + p * LA] = cs[k] * sp - sn[k] * sq;
+        Sm[row + q * LA] = sn[k] * sp + cs[k] * sq;
+      }
+      __syncthreads();
+    }
+  }
+  for (int e = tid; e < j * j; e += SM_THREADS) {
+    const int r = e % j, c = e / j;
+    H[r + (size_t)c * ldh] = A[r + c * LA];
+    S[r + (size_t)c * lds] = Sm[r + c * LA];
+  }
+  for (int i = tid; i < j; i += SM_THREADS) theta[i] = A[i + i * LA];
+  if (tid == 0 && sweeps_out) *sweeps_out = sweep;
+}
+
+void jacobi_eig_ld(cudaStream_t s, int j, double* H, int ldh, double* S, int lds, double* theta, double tol,
+                   int max_sweeps, int* sweeps_out) {
+  const size_t smem = sizeof(double) * 2 * SM_MAXJ * (SM_MAXJ + 1);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_jacobi_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  k_jacobi_eig<<<1, SM_THREADS, smem, s>>>(j, H, ldh, S, lds, theta, tol, max_sweeps, sweeps_out);
+}
+void jacobi_eig(cudaStream_t s, int j, double* H, double* S, double* theta, double tol, int max_sweeps,
+                int* sweeps_out) {
+  jacobi_eig_ld(s, j, H, j, S, j, theta, tol, max_sweeps, sweeps_out);
+}
+
+// ---------------------------------------------------------------------------
+// One-sided Jacobi SVD: rotate column pairs of G until
+// |g_p^T g_q| <= tol * ||g_p|| ||g_q|| for all pairs (relative accuracy).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(SM_THREADS) k_jacobi_svd(int j, double* G, int ldg, double* S, int lds,
+                                                           double* sig, double tol, int max_sweeps,
+                                                           int* sweeps_out) {
+  extern __shared__ __align__(16) double dsm[];
+  double* Gm = dsm;                             // [SM_MAXJ * (SM_MAXJ + 1)]
+  double* Sm = Gm + SM_MAXJ * (SM_MAXJ + 1);    // [SM_MAXJ * (SM_MAXJ + 1)]
+  __shared__ double cs[SM_MAXJ / 2], sn[SM_MAXJ / 2];
+  __shared__ int pp[SM_MAXJ / 2], qq[SM_MAXJ / 2], rot[SM_MAXJ / 2];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int LA = SM_MAXJ + 1;
+  for (int e = tid; e < j * j; e += SM_THREADS) {
+    const int r = e % j, c = e / j;
+    Gm[r + c * LA] = G[r + (size_t)c * ldg];
+    Sm[r + c * LA] = S[r + (size_t)c * lds];
+  }
+  __syncthreads();
+  const int jj = j + (j & 1);
+  const int np = jj / 2;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    int any_sweep = 0;
+    for (int round = 0; round < jj - 1; ++round) {
+      // one warp per pair: the three inner products
+      for (int k = warp; k < np; k += SM_THREADS / 32) {
+        int p, q;
+        rr_pair(jj, round, k, p, q);
+        double a = 0.0, b = 0.0, g = 0.0;
+        if (q < j) {
+          for (int r = lane; r < j; r += 32) {
+            const double gp = Gm[r + p * LA], gq = Gm[r + q * LA];
+            a = fma(gp, gp, a);
+            b = fma(gq, gq, b);
+            g = fma(gp, gq, g);
+          }
+        }
+        a = warp_sum(a);
+        b = warp_sum(b);
+        g = warp_sum(g);
+        if (lane == 0) {
+          pp[k] = p;
+          qq[k] = q;
+          int r = 0;
+          if (q < j && g != 0.0 && fabs(g) > tol * sqrt(a * b)) {
+            const double zeta = (b - a) / (2.0 * g);
+            const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+            const double c = 1.0 / sqrt(1.0 + t * t);
+            cs[k] = c;
+            sn[k] = c * t;
+            r = 1;
+          }
+          rot[k] = r;
+        }
+      }
+      __syncthreads();
+      int mine = 0;
+      if (tid < np) mine = rot[tid];
+      if (!__syncthreads_or(mine)) continue;
+      any_sweep = 1;
+      for (int it = tid; it < j * np; it += SM_THREADS) {
+        const int row = it / np, k = it % np;
+        if (!rot[k]) continue;
+        const int p = pp[k], q = qq[k];
+        const double c = cs[k], s_ = sn[k];
+        const double gp = Gm[row + p * LA], gq = Gm[row + q * LA];
+        Gm[row + p * LA] = c * gp - s_ * gq;
+        Gm[row + q * LA] = s_ * gp + c * gq;
+        const double sp = Sm[row + p * LA], sq = Sm[row + q * LA];
+        Sm[row + p * LA] = c * sp - s_ * sq;
+        Sm[row + q * LA] = s_ * sp + c * sq;
+      }
+      __syncthreads();
+    }
+    if (!any_sweep) break;
+  }
+  for (int e = tid; e < j * j; e += SM_THREADS) {
+    const int r = e % j, c = e / j;
+    G[r + (size_t)c * ldg] = Gm[r + c * LA];
+    S[r + (size_t)c * lds] = Sm[r + c * LA];
+  }
+  __syncthreads();
+  for (int c = warp; c < j; c += SM_THREADS / 32) {
+    double a = 0.0;
+    for (int r = lane; r < j; r += 32) a = fma(Gm[r + c * LA], Gm[r + c * LA], a);
+    a = warp_sum(a);
+    if (lane == 0) sig[c] = sqrt(a);
+  }
+  if (tid == 0 && sweeps_out) *sweeps_out = sweep;
+}
+
+void jacobi_svd_ld(cudaStream_t s, int j, double* G, int ldg, double* S, int lds, double* sig, double tol,
+                   int max_sweeps, int* sweeps_out) {
+  const size_t smem = sizeof(double) * 2 * SM_MAXJ * (SM_MAXJ + 1);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_jacobi_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  k_jacobi_svd<<<1, SM_THREADS, smem, s>>>(j, G, ldg, S, lds, sig, tol, max_sweeps, sweeps_out);
+}
+void jacobi_svd(cudaStream_t s, int j, double* G, double* S, double* sig, double tol, int max_sweeps,
+                int* sweeps_out) {
+  jacobi_svd_ld(s, j, G, j, S, j, sig, tol, max_sweeps, sweeps_out);
+}
+
+// ---------------------------------------------------------------------------
+// Cholesky of the q x q Gram P = L L^T (q <= 8), M = L^{-T} (upper triangular),
+// flags[c] = 1 when pivot^2 < drop^2 * in_norm2[c]: column c of the block is
+// numerically in the span of the basis and the previous block columns.
+// ---------------------------------------------------------------------------
+__global__ void k_chol(int q, const double* __restrict__ P, const double* __restrict__ in_norm2, double drop,
+                       double* __restrict__ M, int* __restrict__ flags) {
+  if (threadIdx.x != 0) return;
+  double L[8][8];
+  for (int a = 0; a < q; ++a)
+    for (int b = 0; b < q; ++b) L[a][b] = 0.0;
+  int bad = 0;
+  for (int c = 0; c < q; ++c) {
+    double d = P[c + c * q];
+    for (int k = 0; k < c; ++k) d -= L[c][k] * L[c][k];
+    const double ref = in_norm2 ? in_norm2[c] : P[c + c * q];
+    int f = 0;
+    if (!(d > drop * drop * ref) || !(d > 0.0)) {
+      f = 1;
+      d = 1.0;  // keep the factor finite; the caller replaces the column
+    }
+    flags[c] = f;
+    bad |= f;
+    const double lcc = sqrt(d);
+    L[c][c] = lcc;
+    for (int r = c + 1; r < q; ++r) {
+      double v = P[r + c * q];
+      for (int k = 0; k < c; ++k) v -= L[r][k] * L[c][k];
+      L[r][c] = f ? 0.0 : v / lcc;
+    }
+  }
+  // M = L^{-T}: solve L^T M = I (upper triangular M)
+  for (int c = 0; c < q; ++c) {
+    for (int r = q - 1; r >= 0; --r) {
+      double v = (r == c) ? 1.0 : 0.0;
+      for (int k = r + 1; k < q; ++k) v -= L[k][r] * M[k + c * q];
+      M[r + c * q] = v / L[r][r];
+    }
+  }
+  flags[q] = bad;
+}
+void chol_factor(cudaStream_t s, int q, const double* P, const double* in_norm2, double drop, double* M,
+                 int* flags) {
+  k_chol<<<1, 32, 0, s>>>(q, P, in_norm2, drop, M, flags);
+}
+
+// ---------------------------------------------------------------------------
+// Small dense products on several CTAs (one thread per output entry).
+// ---------------------------------------------------------------------------
+__global__ void k_gemm_tn(int a, int r, int c, const double* __restrict__ A, int lda, const double* __restrict__ B,
+                          int ldb, double* __restrict__ C, int ldc) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= r * c) return;
+  const int i = e % r, k = e / r;
+  double acc = 0.0;
+  for (int t = 0; t < a; ++t) acc = fma(A[t + (size_t)i * lda], B[t + (size_t)k * ldb], acc);
+  C[i + (size_t)k * ldc] = acc;
+}
+__global__ void k_gemm_nn(int r, int a, int c, const double* __restrict__ A, int lda, const double* __restrict__ B,
+                          int ldb, double* __restrict__ C, int ldc) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= r * c) return;
+  const int i = e % r, k = e / r;
+  double acc = 0.0;
+  for (int t = 0; t < a; ++t) acc = fma(A[i + (size_t)t * lda], B[t + (size_t)k * ldb], acc);
+  C[i + (size_t)k * ldc] = acc;
+}
+void small_gemm_tn(cudaStream_t s, int a, int r, int c, const double* A, int lda, const double* B, int ldb,
+                   double* C, int ldc) {
+  if (r * c > 0) k_gemm_tn<<<ceil_div(r * c, 64), 64, 0, s>>>(a, r, c, A, lda, B, ldb, C, ldc);
+}
+void small_gemm_nn(cudaStream_t s, int r, int a, int c, const double* A, int lda, const double* B, int ldb,
+                   double* C, int ldc) {
+  if (r * c > 0) k_gemm_nn<<<ceil_div(r * c, 64), 64, 0, s>>>(r, a, c, A, lda, B, ldb, C, ldc);
+}
+
+// ---------------------------------------------------------------------------
+// Append nb new basis vectors to the Jacobi frame.  Hnew ((j0+nb) x nb, ld
+// j0+nb) holds V^T W_new in basis coordinates.  A (frame matrix) gets
+// A[0:j0, j0+c] = S[:, 0:j0]^T Hnew[0:j0, c], A[j0+a, j0+c] = sym(Hnew[j0+a, c])
+// and the mirrored lower part; S becomes blockdiag(S, I).
+// ---------------------------------------------------------------------------
+__global__ void k_frame_append(int j0, int nb, double* A, int lda, double* S, int lds, const double* __restrict__ Hn) {
+  const int tid = threadIdx.x;
+  const int ldh = j0 + nb;
+  for (int e = tid; e < j0 * nb; e += blockDim.x) {
+    const int i = e % j0, c = e / j0;
+    double acc = 0.0;
+    for (int r = 0; r < j0; ++r) acc = fma(S[r + (size_t)i * lds], Hn[r + (size_t)c * ldh], acc);
+    A[i + (size_t)(j0 + c) * lda] = acc;
+    A[(j0 + c) + (size_t)i * lda] = acc;
+  }
+  for (int e = tid; e < nb * nb; e += blockDim.x) {
+    const int a = e % nb, c = e / nb;
+    const double v = 0.5 * (Hn[(j0 + a) + (size_t)c * ldh] + Hn[(j0 + c) + (size_t)a * ldh]);
+    A[(j0 + a) + (size_t)(j0 + c) * lda] = v;
+  }
+  const int jn = j0 + nb;
+  for (int e = tid; e < jn * nb; e += blockDim.x) {
+    const int r = e % jn, c = e / jn;
+    S[r + (size_t)(j0 + c) * lds] = (r == j0 + c) ? 1.0 : 0.0;  // new columns
+    if (r < j0) S[(j0 + c) + (size_t)r * lds] = 0.0;            // new rows of old columns
+  }
+}
+void frame_append(cudaStream_t s, int j0, int nb, double* A, int lda, double* S, int lds, const double* Hn) {
+  k_frame_append<<<1, SM_THREADS, 0, s>>>(j0, nb, A, lda, S, lds, Hn);
+}
+
+// Append nb new basis vectors to the projected matrix H (basis coordinates):
+// H[0:j0+nb, j0+c] = Hn[:, c] with the new diagonal block symmetrised and the
+// mirrored rows; the rotation S becomes blockdiag(S, I).
+__global__ void k_h_append(int j0, int nb, double* H, int ldh, double* S, int lds, const double* __restrict__ Hn) {
+  const int jn = j0 + nb;
+  for (int e = threadIdx.x; e < jn * nb; e += blockDim.x) {
+    const int r = e % jn, c = e / jn;
+    double v = Hn[r + (size_t)c * jn];
+    if (r >= j0) v = 0.5 * (v + Hn[(j0 + c) + (size_t)(r - j0) * jn]);
+    H[r + (size_t)(j0 + c) * ldh] = v;
+    H[(j0 + c) + (size_t)r * ldh] = v;
+    S[r + (size_t)(j0 + c) * lds] = (r == j0 + c) ? 1.0 : 0.0;
+    if (r < j0) S[(j0 + c) + (size_t)r * lds] = 0.0;
+  }
+}
+void h_append(cudaStream_t s, int j0, int nb, double* H, int ldh, double* S, int lds, const double* Hn) {
+  k_h_append<<<1, SM_THREADS, 0, s>>>(j0, nb, H, ldh, S, lds, Hn);
+}
+
+// F <- 1.5 I - 0.5 F (one Newton-Schulz step for the orthonormal polar factor:
+// S <- S (3I - S^T S) / 2).
+__global__ void k_ns_factor(int j, double* F, int ldf) {
+  for (int e = threadIdx.x + blockIdx.x * blockDim.x; e < j * j; e += blockDim.x * gridDim.x) {
+    const int r = e % j, c = e / j;
+    F[r + (size_t)c * ldf] = (r == c ? 1.5 : 0.0) - 0.5 * F[r + (size_t)c * ldf];
+  }
+}
+void ns_factor(cudaStream_t s, int j, double* F, int ldf) { k_ns_factor<<<ceil_div(j * j, 256), 256, 0, s>>>(j, F, ldf); }
+
+// A <- (A + A^T) / 2
+__global__ void k_symmetrise(int j, double* A, int lda) {
+  for (int e = threadIdx.x + blockIdx.x * blockDim.x; e < j * j; e += blockDim.x * gridDim.x) {
+    const int r = e % j, c = e / j;
+    if (r < c) {
+      const double v = 0.5 * (A[r + (size_t)c * lda] + A[c + (size_t)r * lda]);
+      A[r + (size_t)c * lda] = v;
+      A[c + (size_t)r * lda] = v;
+    }
+  }
+}
+void symmetrise(cudaStream_t s, int j, double* A, int lda) {
+  k_symmetrise<<<ceil_div(j * j, 256), 256, 0, s>>>(j, A, lda);
+}
+
+// Sort order of theta (j <= 64): mode 0 ascending, 1 descending, 2 ascending |theta - shift|.
+__global__ void k_order(int j, const double* __restrict__ th, int mode, double shift, int* __restrict__ order) {
+  const int i = threadIdx.x;
+  if (i >= j) return;
+  auto key = [&](int t) { return mode == 0 ? th[t] : (mode == 1 ? -th[t] : fabs(th[t] - shift)); };
+  const double ki = key(i);
+  int rank = 0;
+  for (int t = 0; t < j; ++t) {
+    const double kt = key(t);
+    if (kt < ki || (kt == ki && t < i)) ++rank;
+  }
+  order[rank] = i;
+}
+void order_theta(cudaStream_t s, int j, const double* th, int mode, double shift, int* order) {
+  k_order<<<1, SM_MAXJ, 0, s>>>(j, th, mode, shift, order);
+}
+
+// out[:, c] = S[:, idx[c]] (j rows), th_out[c] = th[idx[c]]
+__global__ void k_gather(int j, const double* __restrict__ S, int lds, const int* __restrict__ idx, int nc,
+                         double* __restrict__ out, int ldo, const double* __restrict__ th, double* __restrict__ th_out) {
+  for (int e = threadIdx.x; e < j * nc; e += blockDim.x) {
+    const int r = e % j, c = e / j;
+    out[r + (size_t)c * ldo] = S[r + (size_t)idx[c] * lds];
+  }
+  if (th && threadIdx.x < nc) th_out[threadIdx.x] = th[idx[threadIdx.x]];
+}
+void gather_cols(cudaStream_t s, int j, const double* S, int lds, const int* idx, int nc, double* out, int ldo,
+                 const double* th, double* th_out) {
+  k_gather<<<1, SM_THREADS, 0, s>>>(j, S, lds, idx, nc, out, ldo, th, th_out);
+}
+
+// ---------------------------------------------------------------------------
+// Transform builder (thick restart, locking).  Candidates (j x nc, basis
+// coordinates, priority order) are orthonormalised by classical Gram-Schmidt
+// twice in the j-dimensional coefficient space against the exclusion columns
+// (j x ne) and the accepted candidates; a candidate whose remaining norm is
+// below 1e-8 is dropped; at most nmax are kept.  Outputs Y (j x jn, basis
+// coordinates, ld ldy), *jn_out, and the new frame matrix
+// A' = Yh^T A Yh with Yh = S^T Y (jn x jn, ld lda2), i.e. Y^T H Y.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(SM_THREADS) k_transform(int j, const double* __restrict__ S, int lds,
+                                                          const double* __restrict__ A, int lda,
+                                                          const double* __restrict__ cand, int ldc, int nc,
+                                                          int nc_a, int lim_a,
+                                                          const double* __restrict__ excl, int lde, int ne, int nmax,
+                                                          double* __restrict__ Y, int ldy, int* jn_out,
+                                                          double* __restrict__ A2, int lda2) {
+  extern __shared__ __align__(16) double dsm[];
+  double* Ys = dsm;                          // accepted columns (coefficient space)
+  double* Yh = Ys + SM_MAXJ * SM_MAXJ;       // S^T Y
+  double* AY = Yh + SM_MAXJ * SM_MAXJ;       // A Yh
+  __shared__ double v[SM_MAXJ];
+  __shared__ double red[SM_THREADS / 32];
+  __shared__ int nacc_s;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) nacc_s = 0;
+  __syncthreads();
+  auto block_dot = [&](const double* x, const double* y) -> double {
+    double a = 0.0;
+    for (int r = tid; r < j; r += SM_THREADS) a = fma(x[r], y[r], a);
+    a = warp_sum(a);
+    if (lane == 0) red[warp] = a;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < SM_THREADS / 32; ++w) t += red[w];
+    __syncthreads();
+    return t;
+  };
+  for (int c = 0; c < nc; ++c) {
+    const int nacc = nacc_s;
+    if (nacc >= nmax) break;
+    if (c < nc_a && nacc >= lim_a) continue;  // group A is full: go on with group B
+    for (int r = tid; r < j; r += SM_THREADS) v[r] = cand[r + (size_t)c * ldc];
+    __syncthreads();
+    const double n0 = sqrt(block_dot(v, v));
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int e = 0; e < ne; ++e) {
+        const double h = block_dot(excl + (size_t)e * lde, v);
+        for (int r = tid; r < j; r += SM_THREADS) v[r] -= h * excl[r + (size_t)e * lde];
+        __syncthreads();
+      }
+      for (int e = 0; e < nacc; ++e) {
+        const double h = block_dot(Ys + e * SM_MAXJ, v);
+        for (int r = tid; r < j; r += SM_THREADS) v[r] -= h * Ys[r + e * SM_MAXJ];
+        __syncthreads();
+      }
+    }
+    const double nv = sqrt(block_dot(v, v));
+    if (nv > 1e-8 * (n0 > 1.0 ? 1.0 : n0) && nv > 0.0) {
+      for (int r = tid; r < j; r += SM_THREADS) Ys[r + nacc * SM_MAXJ] = v[r] / nv;
+      __syncthreads();
+      if (tid == 0) nacc_s = nacc + 1;
+    }
+    __syncthreads();
+  }
+  const int jn = nacc_s;
+  if (A2 == nullptr) {
+    for (int e = tid; e < j * jn; e += SM_THREADS) {
+      const int r = e % j, c = e / j;
+      Y[r + (size_t)c * ldy] = Ys[r + c * SM_MAXJ];
+    }
+    if (tid == 0) *jn_out = jn;
+    return;
+  }
+  // Yh = S^T Y
+  for (int e = tid; e < j * jn; e += SM_THREADS) {
+    const int i = e % j, c = e / j;
+    double acc = 0.0;
+    for (int r = 0; r < j; ++r) acc = fma(S[r + (size_t)i * lds], Ys[r + c * SM_MAXJ], acc);
+    Yh[i + c * SM_MAXJ] = acc;
+  }
+  __syncthreads();
+  for (int e = tid; e < j * jn; e += SM_THREADS) {
+    const int i = e % j, c = e / j;
+    double acc = 0.0;
+    for (int r = 0; r < j; ++r) acc = fma(A[i + (size_t)r * lda], Yh[r + c * SM_MAXJ], acc);
+    AY[i + c * SM_MAXJ] = acc;
+  }
+  __syncthreads();
+  for (int e = tid; e < jn * jn; e += SM_THREADS) {
+    const int a = e % jn, c = e / jn;
+    if (a > c) continue;
+    double acc = 0.0;
+    for (int r = 0; r < j; ++r) acc = fma(Yh[r + a * SM_MAXJ], AY[r + c * SM_MAXJ], acc);
+    double acc2 = 0.0;
+    for (int r = 0; r < j; ++r) acc2 = fma(Yh[r + c * SM_MAXJ], AY[r + a * SM_MAXJ], acc2);
+    const double v2 = 0.5 * (acc + acc2);
+    A2[a + (size_t)c * lda2] = v2;
+    A2[c + (size_t)a * lda2] = v2;
+  }
+  for (int e = tid; e < j * jn; e += SM_THREADS) {
+    const int r = e % j, c = e / j;
+    Y[r + (size_t)c * ldy] = Ys[r + c * SM_MAXJ];
+  }
+  if (tid == 0) *jn_out = jn;
+}
+void build_transform(cudaStream_t s, int j, const double* S, int lds, const double* A, int lda, const double* cand,
+                     int ldc, int nc, int nc_a, int lim_a, const double* excl, int lde, int ne, int nmax, double* Y,
+                     int ldy, int* jn_out, double* A2, int lda2) {
+  const size_t smem = sizeof(double) * 3 * SM_MAXJ * SM_MAXJ;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_transform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  k_transform<<<1, SM_THREADS, smem, s>>>(j, S, lds, A, lda, cand, ldc, nc, nc_a, lim_a, excl, lde, ne, nmax, Y,
+                                          ldy, jn_out, A2, lda2);
+}
+
+// QR column bookkeeping of the refined projection: R[0:c, c] = g1 + g2 (the
+// two classical Gram-Schmidt passes), R[c, c] = rho = sqrt(tnorm2), zero below;
+// the working SVD matrix G gets the same new column and the new row
+// [0 ... 0 rho] (G = R S_R with S_R <- blockdiag(S_R, 1)); minv = 1 / rho.
+__global__ void k_qr_column(int c, const double* __restrict__ g1, const double* __restrict__ g2,
+                            const double* __restrict__ tnorm2, double* R, int ldr, double* G, int ldg, double* SR,
+                            int ldsr, double* minv, int update_g) {
+  const double rho = sqrt(fmax(tnorm2[0], 0.0));
+  for (int r = threadIdx.x; r <= c; r += blockDim.x) {
+    const double v = r < c ? (g1 ? g1[r] : 0.0) + (g2 ? g2[r] : 0.0) : rho;
+    R[r + (size_t)c * ldr] = v;
+    if (update_g) {
+      G[r + (size_t)c * ldg] = v;
+      if (r < c) {
+        G[c + (size_t)r * ldg] = 0.0;
+        SR[c + (size_t)r * ldsr] = 0.0;
+        SR[r + (size_t)c * ldsr] = 0.0;
+      } else {
+        SR[c + (size_t)c * ldsr] = 1.0;
+      }
+    }
+  }
+  if (threadIdx.x == 0) minv[0] = rho > 0.0 ? 1.0 / rho : 0.0;
+}
+void qr_column(cudaStream_t s, int c, const double* g1, const double* g2, const double* tnorm2, double* R, int ldr,
+               double* G, int ldg, double* SR, int ldsr, double* minv, int update_g) {
+  k_qr_column<<<1, SM_MAXJ, 0, s>>>(c, g1, g2, tnorm2, R, ldr, G, ldg, SR, ldsr, minv, update_g);
+}
+
+// Final triplet of stage 2 from x = [v; u]: out[c] = (||v||^2, ||u||^2) is
+// computed elsewhere; here sigma = u^T (A v) / (||u|| ||v||) given the dot.
+
+
+// Set S (j x j, ld lds) to the identity.
+__global__ void k_identity(int j, double* S, int lds) {
+  for (int e = threadIdx.x + blockIdx.x * blockDim.x; e < j * j; e += blockDim.x * gridDim.x) {
+    const int r = e % j, c = e / j;
+    S[r + (size_t)c * lds] = r == c ? 1.0 : 0.0;
+  }
+}
+void set_identity(cudaStream_t s, int j, double* S, int lds) { k_identity<<<1, SM_THREADS, 0, s>>>(j, S, lds); }
+
+// Refined vector of stage 2: s1 = S_R[:, argmin sig] (basis coordinates), the
+// Rayleigh quotient theta1 = s1^T H s1 = (S^T s1)^T A (S^T s1), written to
+// out[0] = theta1, out[1] = sigma_min(R), s1 to s1_out (j).
+__global__ void k_refined(int j, const double* __restrict__ SR, int ldr, const double* __restrict__ sig,
+                          const double* __restrict__ S, int lds, const double* __restrict__ A, int lda,
+                          double* __restrict__ s1_out, double* __restrict__ out) {
+  __shared__ double s1[SM_MAXJ], y[SM_MAXJ], ay[SM_MAXJ];
+  __shared__ int imin;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    int b = 0;
+    for (int c = 1; c < j; ++c)
+      if (sig[c] < sig[b]) b = c;
+    imin = b;
+  }
+  __syncthreads();
+  for (int r = tid; r < j; r += blockDim.x) s1[r] = SR[r + (size_t)imin * ldr];
+  __syncthreads();
+  for (int i = tid; i < j; i += blockDim.x) {
+    double acc = 0.0;
+    if (S) {
+      for (int r = 0; r < j; ++r) acc = fma(S[r + (size_t)i * lds], s1[r], acc);
+    } else {
+      acc = s1[i];
+    }
+    y[i] = acc;
+  }
+  __syncthreads();
+  for (int i = tid; i < j; i += blockDim.x) {
+    double acc = 0.0;
+    for (int r = 0; r < j; ++r) acc = fma(A[i + (size_t)r * lda], y[r], acc);
+    ay[i] = acc;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double th = 0.0;
+    for (int r = 0; r < j; ++r) th = fma(y[r], ay[r], th);
+    out[0] = th;
+    out[1] = sig[imin];
+  }
+  for (int r = tid; r < j; r += blockDim.x) s1_out[r] = s1[r];
+}
+void refined_vector(cudaStream_t s, int j, const double* SR, int ldr, const double* sig, const double* S, int lds,
+                    const double* A, int lda, double* s1_out, double* out) {
+  k_refined<<<1, SM_MAXJ, 0, s>>>(j, SR, ldr, sig, S, lds, A, lda, s1_out, out);
+}
+
+}  // namespace ph

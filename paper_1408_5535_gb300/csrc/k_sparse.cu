@@ -1,0 +1,307 @@
+// Sparse kernels: products with C = A^T A and B = [0 A^T; A 0] (Section 1 of the
+// PHSVDS paper), the CSR -> CSC transpose they use, and diag(C).
+//
+// Layout: CSR of A (row_ptr int32, col int32, val T); the CSC copy is the CSR of
+// A^T.  Blocks of b vectors are ROW-major n x b (the b values of a row are
+// contiguous, so one gathered row is one 8..64-byte vector load).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ph {
+
+// One group of L lanes per sparse row: lanes stride over the row's entries,
+// then reduce their B partial sums inside the group.
+template <typename T, int B, int L>
+__global__ void __launch_bounds__(256) k_csr_rows(int nrows, const int* __restrict__ rp,
+                                                  const int* __restrict__ ci, const T* __restrict__ va,
+                                                  const T* __restrict__ X, T* __restrict__ Z) {
+  const int lane = threadIdx.x % L;
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) / L;
+  const bool active = row < nrows;  // inactive groups still take part in the shuffles
+  T acc[B];
+#pragma unroll
+  for (int q = 0; q < B; ++q) acc[q] = T(0);
+  const int e0 = active ? rp[row] : 0, e1 = active ? rp[row + 1] : 0;
+  for (int e = e0 + lane; e < e1; e += L) {
+    const T a = va[e];
+    T x[B];
+    load_row<T, B>(X + (size_t)ci[e] * B, x);
+#pragma unroll
+    for (int q = 0; q < B; ++q) acc[q] = fma(a, x[q], acc[q]);
+  }
+  if constexpr (L > 1) {
+    const unsigned mask = 0xffffffffu;
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1)
+#pragma unroll
+      for (int q = 0; q < B; ++q) acc[q] += __shfl_xor_sync(mask, acc[q], o, L);
+  }
+  if (active && lane == 0) store_row<T, B>(Z + (size_t)row * B, acc);
+}
+
+// Fused single pass Y += A^T (A X): a group computes z = a_i^T X for its row,
+// keeps it in registers and scatters a_ij * z into Y with L2 atomics.
+template <typename T, int B, int L>
+__global__ void __launch_bounds__(256) k_ata_fused(int nrows, const int* __restrict__ rp,
+                                                   const int* __restrict__ ci, const T* __restrict__ va,
+                                                   const T* __restrict__ X, T* __restrict__ Y) {
+  const int lane = threadIdx.x % L;
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) / L;
+  const bool active = row < nrows;  // inactive groups still take part in the shuffles
+  T z[B];
+#pragma unroll
+  for (int q = 0; q < B; ++q) z[q] = T(0);
+  const int e0 = active ? rp[row] : 0, e1 = active ? rp[row + 1] : 0;
+  for (int e = e0 + lane; e < e1; e += L) {
+    const T a = va[e];
+    T x[B];
+    load_row<T, B>(X + (size_t)ci[e] * B, x);
+#pragma unroll
+    for (int q = 0; q < B; ++q) z[q] = fma(a, x[q], z[q]);
+  }
+  if constexpr (L > 1) {
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1)
+#pragma unroll
+      for (int q = 0; q < B; ++q) z[q] += __shfl_xor_sync(0xffffffffu, z[q], o, L);
+  }
+  for (int e = e0 + lane; e < e1; e += L) {
+    const T a = va[e];
+    T y[B];
+#pragma unroll
+    for (int q = 0; q < B; ++q) y[q] = a * z[q];
+    atomic_add_row<T, B>(Y + (size_t)ci[e] * B, y);
+  }
+}
+
+template <typename T, int B>
+static void rows_dispatch_L(cudaStream_t s, int L, int nrows, const int* rp, const int* ci, const T* va,
+                            const T* X, T* Z) {
+  const int th = 256;
+  const int blocks = ceil_div((int64_t)nrows * L, th);
+  if (nrows <= 0) return;
+  switch (L) {
+    case 1: k_csr_rows<T, B, 1><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Z); break;
+    case 2: k_csr_rows<T, B, 2><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Z); break;
+    case 4: k_csr_rows<T, B, 4><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Z); break;
+    default: k_csr_rows<T, B, 8><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Z); break;
+  }
+}
+
+template <typename T, int B>
+static void fused_dispatch_L(cudaStream_t s, int L, int nrows, const int* rp, const int* ci, const T* va,
+                             const T* X, T* Y) {
+  const int th = 256;
+  const int blocks = ceil_div((int64_t)nrows * L, th);
+  if (nrows <= 0) return;
+  switch (L) {
+    case 1: k_ata_fused<T, B, 1><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Y); break;
+    case 2: k_ata_fused<T, B, 2><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Y); break;
+    case 4: k_ata_fused<T, B, 4><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Y); break;
+    default: k_ata_fused<T, B, 8><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Y); break;
+  }
+}
+
+int lanes_for(double avg_row) {
+  if (avg_row <= 2.5) return 1;
+  if (avg_row <= 6.0) return 2;
+  if (avg_row <= 16.0) return 4;
+  return 8;
+}
+
+template <typename T>
+void csr_spmm(cudaStream_t s, const SparseView<T>& A, int b, const T* X, T* Z) {
+  const int L = lanes_for(A.avg_row());
+  switch (b) {
+    case 1: rows_dispatch_L<T, 1>(s, L, A.nrows, A.ptr, A.idx, A.val, X, Z); break;
+    case 2: rows_dispatch_L<T, 2>(s, L, A.nrows, A.ptr, A.idx, A.val, X, Z); break;
+    case 4: rows_dispatch_L<T, 4>(s, L, A.nrows, A.ptr, A.idx, A.val, X, Z); break;
+    case 8: rows_dispatch_L<T, 8>(s, L, A.nrows, A.ptr, A.idx, A.val, X, Z); break;
+    default: break;
+  }
+}
+
+template <typename T>
+void ata_fused(cudaStream_t s, const SparseView<T>& A, int ncols, int b, const T* X, T* Y) {
+  cudaMemsetAsync(Y, 0, sizeof(T) * (size_t)ncols * b, s);
+  const int L = lanes_for(A.avg_row());
+  switch (b) {
+    case 1: fused_dispatch_L<T, 1>(s, L, A.nrows, A.ptr, A.idx, A.val, X, Y); break;
+    case 2: fused_dispatch_L<T, 2>(s, L, A.nrows, A.ptr, A.idx, A.val, X, Y); break;
+    case 4: fused_dispatch_L<T, 4>(s, L, A.nrows, A.ptr, A.idx, A.val, X, Y); break;
+    case 8: fused_dispatch_L<T, 8>(s, L, A.nrows, A.ptr, A.idx, A.val, X, Y); break;
+    default: break;
+  }
+}
+
+template <typename T>
+void ata_two_phase(cudaStream_t s, const SparseView<T>& A, const SparseView<T>& At, int b, const T* X, T* Y,
+                   T* Z) {
+  csr_spmm<T>(s, A, b, X, Z);
+  csr_spmm<T>(s, At, b, Z, Y);
+}
+
+template void csr_spmm<double>(cudaStream_t, const SparseView<double>&, int, const double*, double*);
+template void csr_spmm<float>(cudaStream_t, const SparseView<float>&, int, const float*, float*);
+template void ata_fused<double>(cudaStream_t, const SparseView<double>&, int, int, const double*, double*);
+template void ata_fused<float>(cudaStream_t, const SparseView<float>&, int, int, const float*, float*);
+template void ata_two_phase<double>(cudaStream_t, const SparseView<double>&, const SparseView<double>&, int,
+                                    const double*, double*, double*);
+template void ata_two_phase<float>(cudaStream_t, const SparseView<float>&, const SparseView<float>&, int,
+                                   const float*, float*, float*);
+
+// ---------------------------------------------------------------------------
+// CSR -> CSC on the device: count, scan, scatter, then sort each column by row.
+// ---------------------------------------------------------------------------
+__global__ void k_count_cols(int64_t nnz, const int* __restrict__ ci, int* __restrict__ cnt) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&cnt[ci[e]], 1);
+}
+
+// Exclusive scan of cnt[0..n) into out[0..n] by one CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) k_scan_one_cta(int n, const int* __restrict__ cnt, int* __restrict__ out) {
+  __shared__ int warp_tot[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int base = 0; base < n; base += 1024) {
+    const int i = base + threadIdx.x;
+    const int v = i < n ? cnt[i] : 0;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      int t = warp_tot[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      warp_tot[lane] = t;
+    }
+    __syncthreads();
+    const int incl = x + (w > 0 ? warp_tot[w - 1] : 0);
+    if (i < n) out[i] = carry + incl - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[n] = carry;
+}
+
+template <typename T>
+__global__ void k_scatter_csc(int m, const int* __restrict__ rp, const int* __restrict__ ci, const T* __restrict__ va,
+                              const int* __restrict__ cp, int* __restrict__ fill, int* __restrict__ ri,
+                              T* __restrict__ cv) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+    const int c = ci[e];
+    const int pos = cp[c] + atomicAdd(&fill[c], 1);
+    ri[pos] = i;
+    cv[pos] = va[e];
+  }
+}
+
+template <typename T>
+__global__ void k_sort_cols(int n, const int* __restrict__ cp, int* __restrict__ ri, T* __restrict__ cv) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  const int e0 = cp[c], e1 = cp[c + 1];
+  for (int e = e0 + 1; e < e1; ++e) {  // insertion sort by row index (columns are short)
+    const int r = ri[e];
+    const T v = cv[e];
+    int f = e - 1;
+    while (f >= e0 && ri[f] > r) {
+      ri[f + 1] = ri[f];
+      cv[f + 1] = cv[f];
+      --f;
+    }
+    ri[f + 1] = r;
+    cv[f + 1] = v;
+  }
+}
+
+template <typename T>
+void csr_to_csc(cudaStream_t s, int m, int n, int64_t nnz, const int* rp, const int* ci, const T* va, int* cp,
+                int* ri, T* cv, int* work_n) {
+  cudaMemsetAsync(work_n, 0, sizeof(int) * (size_t)n, s);
+  if (nnz > 0) k_count_cols<<<ceil_div(nnz, 256) < 4096 ? ceil_div(nnz, 256) : 4096, 256, 0, s>>>(nnz, ci, work_n);
+  k_scan_one_cta<<<1, 1024, 0, s>>>(n, work_n, cp);
+  cudaMemsetAsync(work_n, 0, sizeof(int) * (size_t)n, s);
+  if (m > 0) k_scatter_csc<T><<<ceil_div(m, 256), 256, 0, s>>>(m, rp, ci, va, cp, work_n, ri, cv);
+  k_sort_cols<T><<<ceil_div(n, 256), 256, 0, s>>>(n, cp, ri, cv);
+}
+template void csr_to_csc<double>(cudaStream_t, int, int, int64_t, const int*, const int*, const double*, int*, int*,
+                                 double*, int*);
+
+// FP64 CSR -> FP32 values (mixed precision copy of A).
+__global__ void k_to_float(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+void to_float(cudaStream_t s, int64_t n, const double* a, float* b) {
+  if (n > 0) k_to_float<<<ceil_div(n, 256) < 8192 ? ceil_div(n, 256) : 8192, 256, 0, s>>>(n, a, b);
+}
+
+// diag(C)_j = sum_i a_ij^2 from the CSC copy (one thread per column).
+__global__ void k_col_norms2(int n, const int* __restrict__ cp, const double* __restrict__ cv, double* __restrict__ d) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  double acc = 0.0;
+  for (int e = cp[c]; e < cp[c + 1]; ++e) acc = fma(cv[e], cv[e], acc);
+  d[c] = acc;
+}
+void col_norms2(cudaStream_t s, int n, const int* cp, const double* cv, double* d) {
+  if (n > 0) k_col_norms2<<<ceil_div(n, 256), 256, 0, s>>>(n, cp, cv, d);
+}
+
+// Validation of a CSR given with int64 row offsets, in two steps so that no
+// kernel reads col/val through an unchecked offset:
+//  1. k_rowptr_check: rp64[0] = 0, rp64[m] = nnz, non-decreasing, and converts
+//     to int32 offsets clamped into [0, nnz] (flags |= 1 on violation);
+//  2. k_validate_rows: indices in range and strictly increasing within a row
+//     (flags |= 1), finite values (flags |= 2).
+__global__ void k_rowptr_check(int m, int64_t nnz, const int64_t* __restrict__ rp64, int* __restrict__ rp32,
+                               int* flags) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > m) return;
+  const int64_t v = rp64[i];
+  int bad = 0;
+  if (v < 0 || v > nnz) bad = 1;
+  if (i == 0 && v != 0) bad = 1;
+  if (i == m && v != nnz) bad = 1;
+  if (i < m && rp64[i + 1] < v) bad = 1;
+  int64_t c = v < 0 ? 0 : (v > nnz ? nnz : v);
+  rp32[i] = (int)c;
+  if (bad) atomicOr(flags, 1);
+}
+__global__ void k_validate_rows(int m, int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                                const double* __restrict__ va, int* flags) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const int e0 = rp[i], e1 = rp[i + 1];
+  int bad = 0;
+  int prev = -1;
+  for (int e = e0; e < e1; ++e) {
+    const int c = ci[e];
+    if (c < 0 || c >= n || c <= prev) { bad |= 1; break; }
+    prev = c;
+    if (!isfinite(va[e])) bad |= 2;
+  }
+  if (bad) atomicOr(flags, bad);
+}
+void rowptr_check(cudaStream_t s, int m, int64_t nnz, const int64_t* rp64, int* rp32, int* flags) {
+  k_rowptr_check<<<ceil_div((int64_t)m + 1, 256), 256, 0, s>>>(m, nnz, rp64, rp32, flags);
+}
+void validate_rows(cudaStream_t s, int m, int n, const int* rp, const int* ci, const double* va, int* flags) {
+  if (m > 0) k_validate_rows<<<ceil_div(m, 256), 256, 0, s>>>(m, n, rp, ci, va, flags);
+}
+
+}  // namespace ph

@@ -1,0 +1,436 @@
+// Tall-skinny dense kernels of the eigensolver iteration: block classical
+// Gram-Schmidt passes with the V^T W projection products, basis transforms
+// V <- V Y (thick restart / locking), Ritz vectors and residuals
+// R = W S - X Theta, and the Jacobi (Olsen) correction.
+//
+// Storage is T (double, or float in the mixed-precision stage 1); every
+// product accumulates per thread in T and across thread blocks in FP64.
+// On GB300 the FP64 variants are bound by the FP64 pipe (~1.2 TFLOP/s), the
+// FP32 variants by HBM bandwidth.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace ph {
+
+static int g_num_sms = 0;
+static int num_sms() {
+  if (!g_num_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 152;
+  }
+  return g_num_sms;
+}
+
+constexpr int CG_ROWS = 256;   // rows per chunk (one per thread in phase A)
+constexpr int CG_THREADS = 256;
+constexpr int CG_MAXP = 64;    // max basis columns handled per pass
+constexpr int CG_PC = CG_MAXP / (CG_THREADS / 32);  // columns per warp
+
+__device__ inline double atomic_add_f64(double* p, double v) { return atomicAdd(p, v); }
+
+// Block CGS pass.  Phase A: one thread per row loads the row of P (into smem)
+// and of T, applies T -= P Gsub, stores T.  Phase B: warp w accumulates the
+// P^T T entries of columns w, w+8, ... and the T^T T pairs k = w, w+8, ...
+template <typename T, int Q>
+__global__ void __launch_bounds__(CG_THREADS) k_cgs_pass(int n, Basis<T> P, T* __restrict__ Tb, int ldt, int q,
+                                                         const double* __restrict__ Gsub, double* __restrict__ Gout,
+                                                         double* __restrict__ Tout) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = P.cols();
+  T* Ps = reinterpret_cast<T*>(smem_raw);                 // [p][CG_ROWS]
+  T* Ts = Ps + (size_t)p * CG_ROWS;                        // [Q][CG_ROWS]
+  T* Gs = Ts + (size_t)Q * CG_ROWS;                        // [p][Q] in T precision
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // Gs[c + r*p] = Gsub[c + r*p] (column-major p x q), zero for r >= q
+  if (Gsub)
+    for (int k = tid; k < p * Q; k += CG_THREADS) Gs[k] = k < p * q ? (T)Gsub[k] : T(0);
+  T accG[CG_PC][Q];
+  T accT[(Q * (Q + 1) / 2 + 7) / 8];
+#pragma unroll
+  for (int a = 0; a < CG_PC; ++a)
+#pragma unroll
+    for (int r = 0; r < Q; ++r) accG[a][r] = T(0);
+#pragma unroll
+  for (int a = 0; a < (Q * (Q + 1) / 2 + 7) / 8; ++a) accT[a] = T(0);
+  __syncthreads();
+  const int nchunks = (n + CG_ROWS - 1) / CG_ROWS;
+  for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const int row0 = ch * CG_ROWS;
+    const int i = row0 + tid;
+    const bool act = i < n;
+    // ---- phase A
+    T t[Q];
+#pragma unroll
+    for (int r = 0; r < Q; ++r) t[r] = (act && r < q) ? Tb[(size_t)r * ldt + i] : T(0);
+    for (int c = 0; c < p; ++c) {
+      T pc = T(0);
+      if (act) pc = c < P.c1 ? P.p1[(size_t)c * P.ld1 + i] : P.p2[(size_t)(c - P.c1) * P.ld2 + i];
+      Ps[(size_t)c * CG_ROWS + tid] = pc;
+      if (Gsub) {
+#pragma unroll
+        for (int r = 0; r < Q; ++r) t[r] = fma(-pc, Gs[c + r * p], t[r]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < Q; ++r) {
+      Ts[r * CG_ROWS + tid] = t[r];
+      if (Gsub && act && r < q) Tb[(size_t)r * ldt + i] = t[r];
+    }
+    __syncthreads();
+    // ---- phase B
+    if (Gout) {
+#pragma unroll
+      for (int a = 0; a < CG_PC; ++a) {
+        const int c = warp + a * (CG_THREADS / 32);
+        if (c < p) {
+          for (int rr = lane; rr < CG_ROWS; rr += 32) {
+            const T pv = Ps[(size_t)c * CG_ROWS + rr];
+#pragma unroll
+            for (int r = 0; r < Q; ++r) accG[a][r] = fma(pv, Ts[r * CG_ROWS + rr], accG[a][r]);
+          }
+        }
+      }
+    }
+    if (Tout) {
+      int k = 0;
+#pragma unroll
+      for (int r = 0; r < Q; ++r)
+#pragma unroll
+        for (int s2 = r; s2 < Q; ++s2, ++k) {
+          if (k % 8 == warp) {
+            T acc = T(0);
+            for (int rr = lane; rr < CG_ROWS; rr += 32) acc = fma(Ts[r * CG_ROWS + rr], Ts[s2 * CG_ROWS + rr], acc);
+            accT[k / 8] += acc;
+          }
+        }
+    }
+    __syncthreads();
+  }
+  // ---- reduce and accumulate into the FP64 outputs
+  if (Gout) {
+#pragma unroll
+    for (int a = 0; a < CG_PC; ++a) {
+      const int c = warp + a * (CG_THREADS / 32);
+#pragma unroll
+      for (int r = 0; r < Q; ++r) {
+        double v = (double)warp_sum(accG[a][r]);
+        if (lane == 0 && c < p && r < q) atomic_add_f64(&Gout[c + (size_t)r * p], v);
+      }
+    }
+  }
+  if (Tout) {
+    int k = 0;
+#pragma unroll
+    for (int r = 0; r < Q; ++r)
+#pragma unroll
+      for (int s2 = r; s2 < Q; ++s2, ++k) {
+        if (k % 8 == warp) {
+          double v = (double)warp_sum(accT[k / 8]);
+          if (lane == 0 && s2 < q) {
+            atomic_add_f64(&Tout[r + s2 * q], v);
+            if (s2 != r) atomic_add_f64(&Tout[s2 + r * q], v);
+          }
+        }
+      }
+  }
+}
+
+template <typename T, int Q>
+static void cgs_launch(cudaStream_t s, int n, const Basis<T>& P, T* Tb, int ldt, int q, const double* Gsub,
+                       double* Gout, double* Tout) {
+  const int p = P.cols();
+  const size_t smem = sizeof(T) * ((size_t)p * CG_ROWS + (size_t)Q * CG_ROWS + (size_t)p * Q);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_cgs_pass<T, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(T) * ((size_t)CG_MAXP * CG_ROWS + 8 * CG_ROWS + CG_MAXP * 8)));
+    attr = true;
+  }
+  int grid = ceil_div(n, CG_ROWS);
+  const int cap = num_sms() * (sizeof(T) == 8 ? 2 : 4);
+  if (grid > cap) grid = cap;
+  if (grid < 1) grid = 1;
+  k_cgs_pass<T, Q><<<grid, CG_THREADS, smem, s>>>(n, P, Tb, ldt, q, Gsub, Gout, Tout);
+}
+
+template <typename T>
+void cgs_pass(cudaStream_t s, int n, const Basis<T>& P, T* Tb, int ldt, int q, const double* Gsub, double* Gout,
+              double* Tout) {
+  if (n <= 0 || q <= 0) return;
+  Basis<T> PP = P;
+  if (PP.cols() == 0) { Gsub = nullptr; Gout = nullptr; }
+  switch (q) {
+    case 1: cgs_launch<T, 1>(s, n, PP, Tb, ldt, q, Gsub, Gout, Tout); break;
+    case 2: cgs_launch<T, 2>(s, n, PP, Tb, ldt, q, Gsub, Gout, Tout); break;
+    case 3: case 4: cgs_launch<T, 4>(s, n, PP, Tb, ldt, q, Gsub, Gout, Tout); break;
+    default: cgs_launch<T, 8>(s, n, PP, Tb, ldt, q, Gsub, Gout, Tout); break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Out = P * Y [- Xs diag(theta)], optional column norms.
+// ---------------------------------------------------------------------------
+constexpr int TS_ROWS = 128;
+template <typename T>
+__global__ void __launch_bounds__(TS_ROWS) k_tall_small(int n, const T* P, int ldp, int p,
+                                                        const double* __restrict__ Y, int ldy, int r, T* Out,
+                                                        int ldo, const T* __restrict__ Xs, int ldx,
+                                                        const double* __restrict__ theta, double* norms2) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* nrm = reinterpret_cast<double*>(smem_raw);            // [r]
+  T* Ys = reinterpret_cast<T*>(smem_raw + sizeof(double) * (size_t)r);  // [r][p]
+  T* Ps = Ys + (size_t)p * r;                                    // [p][TS_ROWS]
+  const int tid = threadIdx.x;
+  for (int k = tid; k < p * r; k += TS_ROWS) {
+    const int c = k / p, a = k % p;
+    Ys[(size_t)c * p + a] = (T)Y[a + (size_t)c * ldy];
+  }
+  if (norms2)
+    for (int c = tid; c < r; c += TS_ROWS) nrm[c] = 0.0;
+  __syncthreads();
+  const int nchunks = (n + TS_ROWS - 1) / TS_ROWS;
+  for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const int i = ch * TS_ROWS + tid;
+    const bool act = i < n;
+    for (int a = 0; a < p; ++a) Ps[(size_t)a * TS_ROWS + tid] = act ? P[(size_t)a * ldp + i] : T(0);
+    __syncthreads();  // every row of the chunk is read before any (in-place) write
+    for (int c = 0; c < r; ++c) {
+      T acc = T(0);
+      const T* yc = Ys + (size_t)c * p;
+      for (int a = 0; a < p; ++a) acc = fma(Ps[(size_t)a * TS_ROWS + tid], yc[a], acc);
+      if (theta && act) acc = fma((T)(-theta[c]), Xs[(size_t)c * ldx + i], acc);
+      if (act) Out[(size_t)c * ldo + i] = acc;
+      if (norms2) {
+        double v = warp_sum((double)acc * (double)acc);
+        if ((tid & 31) == 0) atomicAdd(&nrm[c], v);
+      }
+    }
+    __syncthreads();
+  }
+  if (norms2) {
+    __syncthreads();
+    for (int c = tid; c < r; c += TS_ROWS) atomicAdd(&norms2[c], nrm[c]);
+  }
+}
+
+template <typename T>
+void tall_times_small(cudaStream_t s, int n, const T* P, int ldp, int p, const double* Y, int ldy, int r, T* Out,
+                      int ldo, const T* Xs, int ldx, const double* theta, double* norms2) {
+  if (n <= 0 || r <= 0) return;
+  const size_t smem = sizeof(double) * (size_t)r + sizeof(T) * ((size_t)p * r + (size_t)p * TS_ROWS);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_tall_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  int grid = ceil_div(n, TS_ROWS);
+  const int cap = num_sms() * 8;
+  if (grid > cap) grid = cap;
+  k_tall_small<T><<<grid, TS_ROWS, smem, s>>>(n, P, ldp, p, Y, ldy, r, Out, ldo, Xs, ldx, theta, norms2);
+}
+
+// ---------------------------------------------------------------------------
+// T <- T * M (q x q, FP64), optional copy to Dst.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_scale_block(int n, T* Tb, int ldt, int q, const double* __restrict__ M, T* Dst, int ldd) {
+  __shared__ T Ms[64];
+  for (int k = threadIdx.x; k < q * q; k += blockDim.x) Ms[k] = (T)M[k];
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T t[8], o[8];
+  for (int r = 0; r < q; ++r) t[r] = Tb[(size_t)r * ldt + i];
+  for (int c = 0; c < q; ++c) {
+    T acc = T(0);
+    for (int r = 0; r < q; ++r) acc = fma(t[r], Ms[r + c * q], acc);
+    o[c] = acc;
+  }
+  for (int c = 0; c < q; ++c) {
+    Tb[(size_t)c * ldt + i] = o[c];
+    if (Dst) Dst[(size_t)c * ldd + i] = o[c];
+  }
+}
+template <typename T>
+void scale_block(cudaStream_t s, int n, T* Tb, int ldt, int q, const double* M, T* Dst, int ldd) {
+  if (n > 0 && q > 0) k_scale_block<T><<<ceil_div(n, 256), 256, 0, s>>>(n, Tb, ldt, q, M, Dst, ldd);
+}
+
+template <typename T>
+__global__ void k_cm_to_rm(int n, const T* __restrict__ src, int lds, int q, T* __restrict__ dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int r = 0; r < q; ++r) dst[(size_t)i * q + r] = src[(size_t)r * lds + i];
+}
+template <typename T>
+__global__ void k_rm_to_cm(int n, const T* __restrict__ src, int q, T* __restrict__ dst, int ldd) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int r = 0; r < q; ++r) dst[(size_t)r * ldd + i] = src[(size_t)i * q + r];
+}
+template <typename T> void cm_to_rm(cudaStream_t s, int n, const T* src, int lds, int q, T* dst) {
+  if (n > 0 && q > 0) k_cm_to_rm<T><<<ceil_div(n, 256), 256, 0, s>>>(n, src, lds, q, dst);
+}
+template <typename T> void rm_to_cm(cudaStream_t s, int n, const T* src, int q, T* dst, int ldd) {
+  if (n > 0 && q > 0) k_rm_to_cm<T><<<ceil_div(n, 256), 256, 0, s>>>(n, src, q, dst, ldd);
+}
+
+// ---------------------------------------------------------------------------
+// Jacobi (diag(C) - theta)^-1 with the Olsen correction.
+// ---------------------------------------------------------------------------
+__device__ inline double guarded(double d, double guard) {
+  if (fabs(d) < guard) return d < 0 ? -guard : guard;
+  return d;
+}
+template <typename T>
+__global__ void k_jacobi_dots(int n, const double* __restrict__ d, const T* __restrict__ X, int ldx,
+                              const T* __restrict__ R, int ldr, int q, const double* __restrict__ theta, double guard,
+                              double* dots) {
+  double a[8], b[8];
+  for (int c = 0; c < q; ++c) a[c] = b[c] = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int c = 0; c < q; ++c) {
+      const double m = 1.0 / guarded(d[i] - theta[c], guard);
+      const double x = (double)X[(size_t)c * ldx + i];
+      a[c] += x * m * (double)R[(size_t)c * ldr + i];
+      b[c] += x * m * x;
+    }
+  }
+  for (int c = 0; c < q; ++c) {
+    double va = warp_sum(a[c]), vb = warp_sum(b[c]);
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(&dots[2 * c], va);
+      atomicAdd(&dots[2 * c + 1], vb);
+    }
+  }
+}
+template <typename T>
+__global__ void k_jacobi_apply(int n, const double* __restrict__ d, const T* __restrict__ X, int ldx,
+                               const T* __restrict__ R, int ldr, int q, const double* __restrict__ theta, double guard,
+                               const double* __restrict__ dots, T* __restrict__ Tout, int ldt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int c = 0; c < q; ++c) {
+    const double m = 1.0 / guarded(d[i] - theta[c], guard);
+    const double e = dots[2 * c + 1] != 0.0 ? dots[2 * c] / dots[2 * c + 1] : 0.0;
+    Tout[(size_t)c * ldt + i] = (T)(m * ((double)R[(size_t)c * ldr + i] - e * (double)X[(size_t)c * ldx + i]));
+  }
+}
+template <typename T>
+void jacobi_dots(cudaStream_t s, int n, const double* d, const T* X, int ldx, const T* R, int ldr, int q,
+                 const double* theta, double guard, double* dots) {
+  int grid = ceil_div(n, 256);
+  if (grid > num_sms() * 4) grid = num_sms() * 4;
+  if (n > 0) k_jacobi_dots<T><<<grid, 256, 0, s>>>(n, d, X, ldx, R, ldr, q, theta, guard, dots);
+}
+template <typename T>
+void jacobi_apply(cudaStream_t s, int n, const double* d, const T* X, int ldx, const T* R, int ldr, int q,
+                  const double* theta, double guard, const double* dots, T* Tout, int ldt) {
+  if (n > 0) k_jacobi_apply<T><<<ceil_div(n, 256), 256, 0, s>>>(n, d, X, ldx, R, ldr, q, theta, guard, dots, Tout, ldt);
+}
+
+template <typename T>
+__global__ void k_fill_random(int n, T* dst, uint64_t seed, uint64_t stream) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (T)sm64_pm1(seed, stream, (uint64_t)i);
+}
+template <typename T> void fill_random(cudaStream_t s, int n, T* dst, uint64_t seed, uint64_t stream) {
+  if (n > 0) k_fill_random<T><<<ceil_div(n, 256), 256, 0, s>>>(n, dst, seed, stream);
+}
+
+__global__ void k_f32_f64(int64_t n, const float* a, double* b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+__global__ void k_f64_f32(int64_t n, const double* a, float* b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+void convert_f32_to_f64(cudaStream_t s, int64_t n, const float* a, double* b) {
+  if (n > 0) k_f32_f64<<<ceil_div(n, 256) < 8192 ? ceil_div(n, 256) : 8192, 256, 0, s>>>(n, a, b);
+}
+void convert_f64_to_f32(cudaStream_t s, int64_t n, const double* a, float* b) {
+  if (n > 0) k_f64_f32<<<ceil_div(n, 256) < 8192 ? ceil_div(n, 256) : 8192, 256, 0, s>>>(n, a, b);
+}
+__global__ void k_axpby(int64_t n, double a, const double* x, double b, double* y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i] + b * y[i];
+}
+void axpby(cudaStream_t s, int64_t n, double a, const double* x, double b, double* y) {
+  if (n > 0) k_axpby<<<ceil_div(n, 256) < 8192 ? ceil_div(n, 256) : 8192, 256, 0, s>>>(n, a, x, b, y);
+}
+
+template <typename T>
+__global__ void k_colnorms(int n, const T* __restrict__ X, int ldx, int q, double* norms2) {
+  double a[8];
+  for (int c = 0; c < q; ++c) a[c] = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    for (int c = 0; c < q; ++c) {
+      const double v = (double)X[(size_t)c * ldx + i];
+      a[c] += v * v;
+    }
+  for (int c = 0; c < q; ++c) {
+    double v = warp_sum(a[c]);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&norms2[c], v);
+  }
+}
+template <typename T> void col_norms2_dense(cudaStream_t s, int n, const T* X, int ldx, int q, double* norms2) {
+  int grid = ceil_div(n, 256);
+  if (grid > num_sms() * 4) grid = num_sms() * 4;
+  if (n > 0) k_colnorms<T><<<grid, 256, 0, s>>>(n, X, ldx, q, norms2);
+}
+
+// out[0] += x^T y (FP64)
+__global__ void k_dot(int64_t n, const double* __restrict__ x, const double* __restrict__ y, double* out) {
+  double a = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a = fma(x[i], y[i], a);
+  a = warp_sum(a);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, a);
+}
+void dot_accum(cudaStream_t s, int64_t n, const double* x, const double* y, double* out) {
+  int grid = ceil_div(n, 256);
+  if (grid > num_sms() * 4) grid = num_sms() * 4;
+  if (n > 0) k_dot<<<grid, 256, 0, s>>>(n, x, y, out);
+}
+// x *= a (a read from device memory when ap != nullptr)
+__global__ void k_scal(int64_t n, double a, const double* ap, double* x) {
+  const double f = ap ? ap[0] : a;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] *= f;
+}
+void scal(cudaStream_t s, int64_t n, double a, const double* ap, double* x) {
+  if (n > 0) k_scal<<<ceil_div(n, 256) < 8192 ? ceil_div(n, 256) : 8192, 256, 0, s>>>(n, a, ap, x);
+}
+// x[i] = v (constant fill)
+template <typename T>
+__global__ void k_fill(int64_t n, T v, T* x) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = v;
+}
+template <typename T> void fill_const(cudaStream_t s, int64_t n, T v, T* x) {
+  if (n > 0) k_fill<T><<<ceil_div(n, 256) < 8192 ? ceil_div(n, 256) : 8192, 256, 0, s>>>(n, v, x);
+}
+template void fill_const<double>(cudaStream_t, int64_t, double, double*);
+template void fill_const<float>(cudaStream_t, int64_t, float, float*);
+
+// explicit instantiations
+#define PH_INST(T)                                                                                              \
+  template void cgs_pass<T>(cudaStream_t, int, const Basis<T>&, T*, int, int, const double*, double*, double*); \
+  template void tall_times_small<T>(cudaStream_t, int, const T*, int, int, const double*, int, int, T*, int,    \
+                                    const T*, int, const double*, double*);                                    \
+  template void scale_block<T>(cudaStream_t, int, T*, int, int, const double*, T*, int);                       \
+  template void cm_to_rm<T>(cudaStream_t, int, const T*, int, int, T*);                                        \
+  template void rm_to_cm<T>(cudaStream_t, int, const T*, int, T*, int);                                        \
+  template void jacobi_dots<T>(cudaStream_t, int, const double*, const T*, int, const T*, int, int,            \
+                               const double*, double, double*);                                                \
+  template void jacobi_apply<T>(cudaStream_t, int, const double*, const T*, int, const T*, int, int,           \
+                                const double*, double, const double*, T*, int);                                \
+  template void fill_random<T>(cudaStream_t, int, T*, uint64_t, uint64_t);                                     \
+  template void col_norms2_dense<T>(cudaStream_t, int, const T*, int, int, double*);
+PH_INST(double)
+PH_INST(float)
+
+}  // namespace ph

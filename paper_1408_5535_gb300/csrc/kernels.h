@@ -1,0 +1,131 @@
+// Internal declarations of the PHSVDS device kernels and their launchers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ph {
+
+// A CSR view: nrows rows, ptr (nrows+1), idx, val (T).  The CSC copy of A is
+// the CSR view of A^T.
+template <typename T>
+struct SparseView {
+  int nrows = 0, ncols = 0;
+  int64_t nnz = 0;
+  const int* ptr = nullptr;
+  const int* idx = nullptr;
+  const T* val = nullptr;
+  double avg_row() const { return nrows ? (double)nnz / nrows : 0.0; }
+};
+
+int lanes_for(double avg_row);
+
+// ---- sparse (k_sparse.cu)
+template <typename T> void csr_spmm(cudaStream_t s, const SparseView<T>& A, int b, const T* X, T* Z);
+template <typename T> void ata_fused(cudaStream_t s, const SparseView<T>& A, int ncols, int b, const T* X, T* Y);
+template <typename T>
+void ata_two_phase(cudaStream_t s, const SparseView<T>& A, const SparseView<T>& At, int b, const T* X, T* Y, T* Z);
+template <typename T>
+void csr_to_csc(cudaStream_t s, int m, int n, int64_t nnz, const int* rp, const int* ci, const T* va, int* cp,
+                int* ri, T* cv, int* work_n);
+void to_float(cudaStream_t s, int64_t n, const double* a, float* b);
+void col_norms2(cudaStream_t s, int n, const int* cp, const double* cv, double* d);
+void rowptr_check(cudaStream_t s, int m, int64_t nnz, const int64_t* rp64, int* rp32, int* flags);
+void validate_rows(cudaStream_t s, int m, int n, const int* rp, const int* ci, const double* va, int* flags);
+
+// ---- tall-skinny dense (k_tall.cu)
+// All tall matrices are column-major with leading dimension ld (>= rows).
+// A "Basis" is up to two column-major pieces [P1 | P2] seen as one.
+template <typename T>
+struct Basis {
+  const T* p1 = nullptr; int ld1 = 0; int c1 = 0;
+  const T* p2 = nullptr; int ld2 = 0; int c2 = 0;
+  __host__ __device__ int cols() const { return c1 + c2; }
+};
+
+// One pass of block classical Gram-Schmidt over a block of q columns T
+// (column-major, ld ldt):
+//   if Gsub:  T <- T - P * Gsub      (Gsub: p x q, column-major ld p, FP64)
+//   if Gout:  Gout += P^T T          (p x q, FP64, must be zeroed by caller)
+//   if Tout:  Tout += T^T T          (q x q, FP64, must be zeroed by caller)
+template <typename T>
+void cgs_pass(cudaStream_t s, int n, const Basis<T>& P, T* Tb, int ldt, int q, const double* Gsub, double* Gout,
+              double* Tout);
+
+// Out (n x r, column-major ld ldo) = P (n x p) * Y (p x r, FP64 column-major ld ldy)
+// [- Xs (n x r) * diag(theta)] when theta != nullptr.  In-place allowed when
+// Out == P and r <= p (each thread reads its whole row before writing).
+// If norms2 != nullptr: norms2[c] += ||Out(:,c)||^2 (FP64, zeroed by caller).
+template <typename T>
+void tall_times_small(cudaStream_t s, int n, const T* P, int ldp, int p, const double* Y, int ldy, int r, T* Out,
+                      int ldo, const T* Xs, int ldx, const double* theta, double* norms2);
+
+// T <- T * Linv^T  (q x q upper-triangular inverse factor applied on the right,
+// FP64) and copy T into column-major destination Dst (ld ldd) when non-null.
+template <typename T>
+void scale_block(cudaStream_t s, int n, T* Tb, int ldt, int q, const double* M, T* Dst, int ldd);
+
+// Column-major <-> row-major block copies (n x q).
+template <typename T> void cm_to_rm(cudaStream_t s, int n, const T* src, int lds, int q, T* dst);
+template <typename T> void rm_to_cm(cudaStream_t s, int n, const T* src, int q, T* dst, int ldd);
+
+// Olsen/Jacobi correction: t_c = M r_c - e_c M x_c, M = diag(1/(d - theta_c)),
+// e_c = (x^T M r)/(x^T M x); dots (2*q, FP64) computed by jacobi_dots first.
+template <typename T>
+void jacobi_dots(cudaStream_t s, int n, const double* d, const T* X, int ldx, const T* R, int ldr, int q,
+                 const double* theta, double guard, double* dots);
+template <typename T>
+void jacobi_apply(cudaStream_t s, int n, const double* d, const T* X, int ldx, const T* R, int ldr, int q,
+                  const double* theta, double guard, const double* dots, T* Tout, int ldt);
+
+// Random uniform [-1,1) column (SplitMix64 stream) into column-major dst.
+template <typename T> void fill_random(cudaStream_t s, int n, T* dst, uint64_t seed, uint64_t stream);
+// dst = src (conversion between precisions).
+void convert_f32_to_f64(cudaStream_t s, int64_t n, const float* a, double* b);
+void convert_f64_to_f32(cudaStream_t s, int64_t n, const double* a, float* b);
+// y = a*x + b*y on n doubles
+void axpby(cudaStream_t s, int64_t n, double a, const double* x, double b, double* y);
+// norms2[c] += ||X(:,c)||^2 for q columns (FP64 output)
+template <typename T> void col_norms2_dense(cudaStream_t s, int n, const T* X, int ldx, int q, double* norms2);
+
+void dot_accum(cudaStream_t s, int64_t n, const double* x, const double* y, double* out);
+void scal(cudaStream_t s, int64_t n, double a, const double* ap, double* x);
+template <typename T> void fill_const(cudaStream_t s, int64_t n, T v, T* x);
+
+// ---- small one-CTA problems (k_small.cu), FP64, j <= 64
+// Cyclic Jacobi on the symmetric j x j H (column-major, ld j); S <- S * J.
+void jacobi_eig(cudaStream_t s, int j, double* H, double* S, double* theta, double tol, int max_sweeps,
+                int* sweeps_out);
+// One-sided Jacobi on G (j x j): G <- G J, S <- S J, sig = column norms of G.
+void jacobi_svd(cudaStream_t s, int j, double* G, double* S, double* sig, double tol, int max_sweeps,
+                int* sweeps_out);
+// Cholesky of the q x q Gram P; writes Linv^T-style right factor M (q x q) with
+// T * M orthonormal; flags[c] = 1 for columns whose pivot fell below
+// drop^2 * max(P_cc, in_norm2[c]) (numerically dependent).
+void chol_factor(cudaStream_t s, int q, const double* P, const double* in_norm2, double drop, double* M,
+                 int* flags);
+// C (r x c) = A^T (a x r)^T * B (a x c)   -- small dense product, FP64 column-major
+void small_gemm_tn(cudaStream_t s, int a, int r, int c, const double* A, int lda, const double* B, int ldb,
+                   double* C, int ldc);
+void small_gemm_nn(cudaStream_t s, int r, int a, int c, const double* A, int lda, const double* B, int ldb,
+                   double* C, int ldc);
+void jacobi_eig_ld(cudaStream_t s, int j, double* H, int ldh, double* S, int lds, double* theta, double tol,
+                   int max_sweeps, int* sweeps_out);
+void jacobi_svd_ld(cudaStream_t s, int j, double* G, int ldg, double* S, int lds, double* sig, double tol,
+                   int max_sweeps, int* sweeps_out);
+void frame_append(cudaStream_t s, int j0, int nb, double* A, int lda, double* S, int lds, const double* Hn);
+void order_theta(cudaStream_t s, int j, const double* th, int mode, double shift, int* order);
+void gather_cols(cudaStream_t s, int j, const double* S, int lds, const int* idx, int nc, double* out, int ldo,
+                 const double* th, double* th_out);
+void build_transform(cudaStream_t s, int j, const double* S, int lds, const double* A, int lda, const double* cand,
+                     int ldc, int nc, int nc_a, int lim_a, const double* excl, int lde, int ne, int nmax, double* Y,
+                     int ldy, int* jn_out, double* A2, int lda2);
+void set_identity(cudaStream_t s, int j, double* S, int lds);
+void h_append(cudaStream_t s, int j0, int nb, double* H, int ldh, double* S, int lds, const double* Hn);
+void ns_factor(cudaStream_t s, int j, double* F, int ldf);
+void symmetrise(cudaStream_t s, int j, double* A, int lda);
+void refined_vector(cudaStream_t s, int j, const double* SR, int ldr, const double* sig, const double* S, int lds,
+                    const double* A, int lda, double* s1_out, double* out);
+void qr_column(cudaStream_t s, int c, const double* g1, const double* g2, const double* tnorm2, double* R, int ldr,
+               double* G, int ldg, double* SR, int ldsr, double* minv, int update_g);
+
+}  // namespace ph

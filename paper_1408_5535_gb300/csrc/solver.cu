@@ -1,0 +1,1359 @@
+// Host driver of PHSVDS on one GB300 and the C ABI (include/phsvds.h).
+//
+// Stage 1 (Algorithm 1): block GD+k on C = A^T A.  Stage 2 (Algorithm 2): GD
+// outer loop on B = [0 A^T; A 0] with the refined projection through an
+// incrementally updated QR of W - s V.  Every arithmetic step runs in the
+// kernels of k_sparse.cu / k_tall.cu / k_small.cu; the host only sequences
+// launches and reads back the few scalars that decide locking and restarts.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "phsvds.h"
+
+namespace ph {
+
+constexpr int LD = 64;                    // leading dimension of the small matrices
+constexpr double EPS64 = 2.220446049250313e-16;
+constexpr double EPS32 = 1.1920928955078125e-07;
+constexpr uint64_t RS_INIT = 0x1000, RS_BREAK = 0x2000, RS_U = 0x3000;
+constexpr double JAC_TOL = 1e-17;         // absolute Jacobi threshold relative to ||H||
+
+struct PhError {
+  phsvds_status st;
+  std::string msg;
+};
+
+#define CUCHK(x)                                                                                  \
+  do {                                                                                            \
+    cudaError_t e_ = (x);                                                                         \
+    if (e_ != cudaSuccess) throw PhError{e_ == cudaErrorMemoryAllocation ? PHSVDS_ERR_OOM : PHSVDS_ERR_CUDA, \
+                                         std::string(#x) + ": " + cudaGetErrorString(e_)};      \
+  } while (0)
+
+// Device allocation owned by a solve (stream-ordered pool).
+struct Pool {
+  cudaStream_t s;
+  std::vector<void*> ptrs;
+  explicit Pool(cudaStream_t st) : s(st) {}
+  template <typename T>
+  T* get(size_t count) {
+    void* p = nullptr;
+    if (count == 0) count = 1;
+    CUCHK(cudaMallocAsync(&p, sizeof(T) * count, s));
+    ptrs.push_back(p);
+    return static_cast<T*>(p);
+  }
+  ~Pool() {
+    for (void* p : ptrs) cudaFreeAsync(p, s);
+  }
+};
+
+}  // namespace ph
+
+struct phsvds_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  unsigned char* host = nullptr;  // pinned readback / upload area
+  size_t host_bytes = 0;
+};
+
+namespace ph {
+
+// Pinned staging area of the context (readbacks of a few scalars per iteration).
+struct Host {
+  phsvds_ctx* c;
+  unsigned char* base;
+  size_t bytes;
+  explicit Host(phsvds_ctx* cc) : c(cc), base(cc->host), bytes(cc->host_bytes) {}
+  template <typename T> T* at(size_t off_bytes) { return reinterpret_cast<T*>(base + off_bytes); }
+};
+
+static bool trace_on() {
+  static int t = -1;
+  if (t < 0) t = getenv("PHSVDS_TRACE") ? 1 : 0;
+  return t == 1;
+}
+
+static void sync(cudaStream_t s) {
+  CUCHK(cudaGetLastError());
+  CUCHK(cudaStreamSynchronize(s));
+}
+
+template <typename T> static void zero(cudaStream_t s, T* p, size_t count) {
+  if (count) CUCHK(cudaMemsetAsync(p, 0, sizeof(T) * count, s));
+}
+
+// ---------------------------------------------------------------------------
+// The matrix on the device
+// ---------------------------------------------------------------------------
+struct DevA {
+  int m = 0, n = 0;
+  int64_t nnz = 0;
+  int *rp = nullptr, *ci = nullptr, *cp = nullptr, *ri = nullptr;
+  double *va = nullptr, *cv = nullptr, *diagC = nullptr;
+  float *va32 = nullptr, *cv32 = nullptr;
+  SparseView<double> A64, At64;
+  SparseView<float> A32, At32;
+  double *Z64 = nullptr;
+  float *Z32 = nullptr;
+};
+
+static void upload_matrix(phsvds_ctx* ctx, Pool& pool, DevA& d, int64_t m, int64_t n, int64_t nnz, const int64_t* rp,
+                          const int32_t* ci, const double* va, int on_dev, bool need32, bool need_diag, int bmax) {
+  cudaStream_t s = ctx->stream;
+  d.m = (int)m;
+  d.n = (int)n;
+  d.nnz = nnz;
+  int64_t* rp64 = pool.get<int64_t>(m + 1);
+  d.rp = pool.get<int>(m + 1);
+  d.ci = pool.get<int>(nnz);
+  d.va = pool.get<double>(nnz);
+  const cudaMemcpyKind kind = on_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  CUCHK(cudaMemcpyAsync(rp64, rp, sizeof(int64_t) * (m + 1), kind, s));
+  if (nnz) {
+    CUCHK(cudaMemcpyAsync(d.ci, ci, sizeof(int) * nnz, kind, s));
+    CUCHK(cudaMemcpyAsync(d.va, va, sizeof(double) * nnz, kind, s));
+  }
+  int* flags = pool.get<int>(2);
+  zero(s, flags, 2);
+  rowptr_check(s, d.m, nnz, rp64, d.rp, flags);
+  validate_rows(s, d.m, d.n, d.rp, d.ci, d.va, flags);
+  Host h(ctx);
+  CUCHK(cudaMemcpyAsync(h.at<int>(0), flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+  sync(s);
+  const int f = *h.at<int>(0);
+  if (f & 1) throw PhError{PHSVDS_ERR_INVALID, "invalid CSR structure (row_ptr or column indices)"};
+  if (f & 2) throw PhError{PHSVDS_ERR_NAN, "A holds a NaN or Inf value"};
+  d.cp = pool.get<int>(n + 1);
+  d.ri = pool.get<int>(nnz);
+  d.cv = pool.get<double>(nnz);
+  int* work = pool.get<int>(n);
+  csr_to_csc<double>(s, d.m, d.n, nnz, d.rp, d.ci, d.va, d.cp, d.ri, d.cv, work);
+  d.A64 = SparseView<double>{d.m, d.n, nnz, d.rp, d.ci, d.va};
+  d.At64 = SparseView<double>{d.n, d.m, nnz, d.cp, d.ri, d.cv};
+  d.Z64 = pool.get<double>((size_t)m * bmax);
+  if (need32) {
+    d.va32 = pool.get<float>(nnz);
+    d.cv32 = pool.get<float>(nnz);
+    to_float(s, nnz, d.va, d.va32);
+    to_float(s, nnz, d.cv, d.cv32);
+    d.A32 = SparseView<float>{d.m, d.n, nnz, d.rp, d.ci, d.va32};
+    d.At32 = SparseView<float>{d.n, d.m, nnz, d.cp, d.ri, d.cv32};
+    d.Z32 = pool.get<float>((size_t)m * bmax);
+  }
+  if (need_diag) {
+    d.diagC = pool.get<double>(n);
+    col_norms2(s, d.n, d.cp, d.cv, d.diagC);
+  }
+}
+
+// C X = A^T (A X) on a row-major block of b in {1,2,4,8} vectors.
+template <typename T> struct COp {
+  const SparseView<T>* A;
+  const SparseView<T>* At;
+  T* Z;
+  int n;
+  int schedule;  // 1 fused atomic, 2 two-phase
+  void apply(cudaStream_t s, int b, const T* X, T* Y) const {
+    if (schedule == 1)
+      ata_fused<T>(s, *A, n, b, X, Y);
+    else
+      ata_two_phase<T>(s, *A, *At, b, X, Y, Z);
+  }
+};
+
+// Pick the faster SpMM schedule for this matrix and block size by timing both.
+template <typename T>
+static int autotune_spmm(cudaStream_t s, Pool& pool, const SparseView<T>& A, const SparseView<T>& At, T* Z, int n,
+                         int b) {
+  T* X = pool.get<T>((size_t)n * b);
+  T* Y = pool.get<T>((size_t)n * b);
+  fill_random<T>(s, n * b, X, 7, 0x77);
+  cudaEvent_t e0, e1;
+  CUCHK(cudaEventCreate(&e0));
+  CUCHK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int pick = 2;
+  for (int sch = 1; sch <= 2; ++sch) {
+    COp<T> op{&A, &At, Z, n, sch};
+    op.apply(s, b, X, Y);  // warm
+    CUCHK(cudaEventRecord(e0, s));
+    for (int r = 0; r < 3; ++r) op.apply(s, b, X, Y);
+    CUCHK(cudaEventRecord(e1, s));
+    CUCHK(cudaEventSynchronize(e1));
+    float ms = 0;
+    CUCHK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      pick = sch;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return pick;
+}
+
+static inline int spmm_width(int nb) { return nb >= 8 ? 8 : nb >= 4 ? 4 : nb >= 2 ? 2 : 1; }
+
+// Jacobi frame of the projected problem, rebuilt each outer iteration from the
+// exact projected matrix Ht (basis coordinates): S <- S (3I - S^T S)/2 (one
+// Newton-Schulz step keeps the accumulated rotation orthonormal), then
+// Aw = S^T Ht S.  The warm-started Jacobi then only rotates what the new basis
+// vectors disturbed.  With S = I the frame is Ht itself.
+static void frame_from_true(cudaStream_t s, int j, const double* Ht, double* S, double* Aw, double* w1, double* w2,
+                            bool ident) {
+  if (ident) {
+    CUCHK(cudaMemcpy2DAsync(Aw, LD * sizeof(double), Ht, LD * sizeof(double), j * sizeof(double), j,
+                            cudaMemcpyDeviceToDevice, s));
+    return;
+  }
+  small_gemm_tn(s, j, j, j, S, LD, S, LD, w1, LD);
+  ns_factor(s, j, w1, LD);
+  small_gemm_nn(s, j, j, j, S, LD, w1, LD, w2, LD);
+  CUCHK(cudaMemcpy2DAsync(S, LD * sizeof(double), w2, LD * sizeof(double), j * sizeof(double), j,
+                          cudaMemcpyDeviceToDevice, s));
+  small_gemm_nn(s, j, j, j, Ht, LD, S, LD, w1, LD);
+  small_gemm_tn(s, j, j, j, S, LD, w1, LD, Aw, LD);
+  symmetrise(s, j, Aw, LD);
+}
+
+// Ht = V^T W recomputed from the tall basis after a transform (j x j, FP64
+// accumulation): no rounding drift of the projected matrix survives a restart.
+template <typename T>
+static void gram_full(cudaStream_t s, int n, const T* V, T* W, int j, double* Ht, double* tmp) {
+  Basis<T> P{V, n, j, nullptr, 0, 0};
+  for (int c = 0; c < j; c += 8) {
+    const int w = std::min(8, j - c);
+    zero(s, tmp, (size_t)j * w);
+    cgs_pass<T>(s, n, P, W + (size_t)c * n, n, w, nullptr, tmp, nullptr);
+    CUCHK(cudaMemcpy2DAsync(Ht + (size_t)c * LD, LD * sizeof(double), tmp, j * sizeof(double), j * sizeof(double), w,
+                            cudaMemcpyDeviceToDevice, s));
+  }
+  symmetrise(s, j, Ht, LD);
+}
+
+// Ht <- Y^T Ht Y for an orthonormal Y (j x jn, basis coordinates).
+static void transform_h(cudaStream_t s, int j, int jn, double* Ht, const double* Y, double* w1, double* w2) {
+  small_gemm_nn(s, j, j, jn, Ht, LD, Y, LD, w1, LD);
+  small_gemm_tn(s, j, jn, jn, Y, LD, w1, LD, w2, LD);
+  CUCHK(cudaMemcpy2DAsync(Ht, LD * sizeof(double), w2, LD * sizeof(double), jn * sizeof(double), jn,
+                          cudaMemcpyDeviceToDevice, s));
+  symmetrise(s, jn, Ht, LD);
+}
+
+// ---------------------------------------------------------------------------
+// Stage 1: block GD+k on C (storage precision T)
+// ---------------------------------------------------------------------------
+struct Stage1Out {
+  std::vector<double> lam;   // k eigenvalues of C (target order)
+  double theta_max = 0.0;
+  int64_t iters = 0, restarts = 0, mv = 0;
+};
+
+template <typename T>
+struct Stage1 {
+  phsvds_ctx* ctx;
+  cudaStream_t s;
+  Pool& pool;
+  int n, k, b, maxb, mins, kp;
+  bool largest;
+  double delta, floor_eps;
+  int precond;
+  const double* diagC;
+  COp<T> op;
+  uint64_t seed;
+  int max_restarts;
+  double time_limit_s;
+  std::chrono::steady_clock::time_point t0;
+  // device
+  T *V, *W, *Xl, *Tb, *Xrm, *Yrm, *Xr, *Rr, *XU;
+  double *Aw, *S, *Ht, *w1, *w2, *theta, *Hn, *G1, *G2, *P1, *P2, *M1, *M2, *innorm, *norms, *Scols, *thcols, *Yt,
+      *A2, *cand, *excl, *sprev, *dots, *thU;
+  int *order, *flags, *jn, *idx;
+  // host state
+  int j = 0, nlock = 0, nsp = 0, rand_ctr = 0;
+  bool s_ident = true;
+  Stage1Out out;
+
+  Stage1(phsvds_ctx* c, Pool& p, int n_, int k_, const phsvds_opts& o, bool largest_, double delta_, double eps,
+         int precond_, const double* diag, COp<T> op_)
+      : ctx(c), s(c->stream), pool(p), n(n_), k(k_), largest(largest_), delta(delta_), precond(precond_),
+        diagC(diag), op(op_) {
+    b = std::max(1, std::min(o.block_size, k));
+    maxb = o.max_basis;
+    mins = o.min_restart;
+    kp = b;
+    floor_eps = o.eps_factor * eps;
+    seed = o.seed;
+    max_restarts = o.max_restarts;
+    time_limit_s = o.time_limit_s;
+    const size_t nn = (size_t)n;
+    V = pool.get<T>(nn * maxb);
+    W = pool.get<T>(nn * maxb);
+    Xl = pool.get<T>(nn * k);
+    Tb = pool.get<T>(nn * 8);
+    Xrm = pool.get<T>(nn * 8);
+    Yrm = pool.get<T>(nn * 8);
+    Xr = pool.get<T>(nn * 8);
+    Rr = pool.get<T>(nn * 8);
+    XU = pool.get<T>(nn * 8);
+    Aw = pool.get<double>(LD * LD);
+    S = pool.get<double>(LD * LD);
+    Ht = pool.get<double>(LD * LD);
+    w1 = pool.get<double>(LD * LD);
+    w2 = pool.get<double>(LD * LD);
+    theta = pool.get<double>(LD);
+    Hn = pool.get<double>(LD * 8);
+    G1 = pool.get<double>(LD * 8 + LD);
+    G2 = pool.get<double>(LD * 8 + LD);
+    P1 = pool.get<double>(64);
+    P2 = pool.get<double>(64);
+    M1 = pool.get<double>(64);
+    M2 = pool.get<double>(64);
+    innorm = pool.get<double>(8);
+    norms = pool.get<double>(8);
+    Scols = pool.get<double>(LD * LD);
+    thcols = pool.get<double>(LD);
+    Yt = pool.get<double>(LD * LD);
+    A2 = pool.get<double>(LD * LD);
+    cand = pool.get<double>(LD * (LD + 8));
+    excl = pool.get<double>(LD * 8);
+    sprev = pool.get<double>(LD * 8);
+    dots = pool.get<double>(16);
+    thU = pool.get<double>(8);
+    order = pool.get<int>(LD);
+    flags = pool.get<int>(32);
+    jn = pool.get<int>(4);
+    idx = pool.get<int>(2 * LD);
+    zero(s, sprev, LD * 8);
+  }
+
+  void check_time() {
+    if (time_limit_s > 0) {
+      const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (el > time_limit_s) throw PhError{PHSVDS_ERR_TIMEOUT, "time limit reached in stage 1"};
+    }
+  }
+
+  // Orthonormalise nb (<= 8) columns of Tb against [Xl | V] (classical
+  // Gram-Schmidt twice, then CholQR twice) and append them to V.
+  void orth_append(int nb) {
+    Host h(ctx);
+    Basis<T> P{Xl, n, nlock, V, n, j};
+    const int p = P.cols();
+    for (int attempt = 0;; ++attempt) {
+      zero(s, innorm, nb);
+      col_norms2_dense<T>(s, n, Tb, n, nb, innorm);
+      zero(s, G1, (size_t)p * nb);
+      zero(s, G2, (size_t)p * nb);
+      zero(s, P1, (size_t)nb * nb);
+      cgs_pass<T>(s, n, P, Tb, n, nb, nullptr, G1, nullptr);
+      cgs_pass<T>(s, n, P, Tb, n, nb, G1, G2, nullptr);
+      cgs_pass<T>(s, n, P, Tb, n, nb, G2, nullptr, P1);
+      chol_factor(s, nb, P1, innorm, 1e-10, M1, flags);
+      CUCHK(cudaMemcpyAsync(h.at<int>(0), flags, sizeof(int) * (nb + 1), cudaMemcpyDeviceToHost, s));
+      sync(s);
+      int* f = h.at<int>(0);
+      if (!f[nb]) break;
+      if (attempt >= 3) throw PhError{PHSVDS_ERR_BREAKDOWN, "stage 1: cannot extend the basis"};
+      for (int c = 0; c < nb; ++c)
+        if (f[c]) fill_random<T>(s, n, Tb + (size_t)c * n, seed, RS_BREAK + (uint64_t)(rand_ctr++));
+    }
+    if (nb == 1) {
+      scale_block<T>(s, n, Tb, n, 1, M1, V + (size_t)j * n, n);
+    } else {
+      scale_block<T>(s, n, Tb, n, nb, M1, nullptr, 0);
+      zero(s, P2, (size_t)nb * nb);
+      Basis<T> none{};
+      cgs_pass<T>(s, n, none, Tb, n, nb, nullptr, nullptr, P2);
+      chol_factor(s, nb, P2, nullptr, 0.0, M2, flags + 8);
+      scale_block<T>(s, n, Tb, n, nb, M2, V + (size_t)j * n, n);
+    }
+  }
+
+  // W(:, j0:j0+nb) = C V(:, j0:j0+nb) in row-major chunks of 8/4/2/1.
+  void apply_C(int j0, int nb) {
+    int c = 0;
+    while (c < nb) {
+      const int w = spmm_width(nb - c);
+      cm_to_rm<T>(s, n, V + (size_t)(j0 + c) * n, n, w, Xrm);
+      op.apply(s, w, Xrm, Yrm);
+      rm_to_cm<T>(s, n, Yrm, w, W + (size_t)(j0 + c) * n, n);
+      c += w;
+    }
+    out.mv += nb;
+  }
+
+  // Append nb columns (already in Tb) to the basis and the Jacobi frame.
+  void expand(int nb) {
+    orth_append(nb);
+    apply_C(j, nb);
+    zero(s, Hn, (size_t)(j + nb) * nb);
+    Basis<T> Pv{V, n, j + nb, nullptr, 0, 0};
+    cgs_pass<T>(s, n, Pv, W + (size_t)j * n, n, nb, nullptr, Hn, nullptr);
+    h_append(s, j, nb, Ht, LD, S, LD, Hn);
+    if (nsp) CUCHK(cudaMemset2DAsync(sprev + j, LD * sizeof(double), 0, nb * sizeof(double), nsp, s));
+    j += nb;
+  }
+
+  // Append more than 8 columns (initial guesses) in chunks.
+  void expand_many(const T* X0, int ncol) {
+    int c = 0;
+    while (c < ncol) {
+      const int nb = std::min(8, ncol - c);
+      CUCHK(cudaMemcpyAsync(Tb, X0 + (size_t)c * n, sizeof(T) * (size_t)n * nb, cudaMemcpyDeviceToDevice, s));
+      expand(nb);
+      c += nb;
+    }
+  }
+
+  double tol_of(double th, double thmax) const {
+    const double si = std::sqrt(std::max(th, 0.0)), sn = std::sqrt(std::max(thmax, 0.0));
+    return std::max(delta * si * sn, floor_eps * thmax);
+  }
+
+  // Runs GD+k to convergence.  X0 (n x nx, may be null) replaces the default
+  // start (ones(n,1)/sqrt(n) plus random columns).  On return Xl holds the k
+  // locked eigenvectors in target order and V/S/order describe the final basis.
+  void run(const T* X0, int nx) {
+    t0 = std::chrono::steady_clock::now();
+    Host h(ctx);
+    if (X0 && nx > 0) {
+      expand_many(X0, nx);
+    } else {
+      fill_const<T>(s, n, (T)(1.0 / std::sqrt((double)n)), Tb);
+      for (int c = 1; c < b; ++c) fill_random<T>(s, n, Tb + (size_t)c * n, seed, RS_INIT + c);
+      expand(b);
+    }
+    std::vector<double> thv(LD);
+    std::vector<int> ord(LD);
+    int nb = 0;
+    while (true) {
+      check_time();
+      if (nb > 0) expand(nb);
+      frame_from_true(s, j, Ht, S, Aw, w1, w2, s_ident);
+      s_ident = false;
+      jacobi_eig_ld(s, j, Aw, LD, S, LD, theta, JAC_TOL, 60, flags + 12);
+      order_theta(s, j, theta, largest ? 1 : 0, 0.0, order);
+      const int nt = std::min(std::min(b, k - nlock), j);
+      gather_cols(s, j, S, LD, order, nt, Scols, LD, theta, thcols);
+      tall_times_small<T>(s, n, V, n, j, Scols, LD, nt, Xr, n, nullptr, 0, nullptr, nullptr);
+      zero(s, norms, nt);
+      tall_times_small<T>(s, n, W, n, j, Scols, LD, nt, Rr, n, Xr, n, thcols, norms);
+      double* hth = h.at<double>(0);        // bytes [0, 512)
+      int* hord = h.at<int>(512);            // bytes [512, 768)
+      double* hn = h.at<double>(768);        // bytes [768, 832)
+      CUCHK(cudaMemcpyAsync(hth, theta, sizeof(double) * j, cudaMemcpyDeviceToHost, s));
+      CUCHK(cudaMemcpyAsync(hord, order, sizeof(int) * j, cudaMemcpyDeviceToHost, s));
+      CUCHK(cudaMemcpyAsync(hn, norms, sizeof(double) * nt, cudaMemcpyDeviceToHost, s));
+      sync(s);
+      out.iters++;
+      for (int i = 0; i < j; ++i) {
+        ord[i] = hord[i];
+        thv[i] = hth[hord[i]];
+        if (!std::isfinite(thv[i])) throw PhError{PHSVDS_ERR_NAN, "stage 1: non-finite Ritz value"};
+        out.theta_max = std::max(out.theta_max, thv[i]);
+      }
+      std::vector<int> conv, unconv;
+      for (int t = 0; t < nt; ++t) {
+        const double rn = std::sqrt(std::max(hn[t], 0.0));
+        if (!std::isfinite(rn)) throw PhError{PHSVDS_ERR_NAN, "stage 1: non-finite residual"};
+        (rn < tol_of(thv[t], out.theta_max) ? conv : unconv).push_back(t);
+      }
+      if (trace_on())
+        fprintf(stderr, "s1[%d] it=%lld j=%d nlock=%d th0=%.17g rn0=%.6e thmax=%.6e nconv=%d\n", (int)sizeof(T),
+                (long long)out.iters, j, nlock, thv[0], std::sqrt(std::max(hn[0], 0.0)), out.theta_max,
+                (int)conv.size());
+      for (int t : conv) {
+        CUCHK(cudaMemcpyAsync(Xl + (size_t)nlock * n, Xr + (size_t)t * n, sizeof(T) * n, cudaMemcpyDeviceToDevice, s));
+        out.lam.push_back(thv[t]);
+        ++nlock;
+      }
+      if (nlock >= k) {
+        final_conv = conv;
+        final_ord = ord;
+        return;
+      }
+      // frame indices kept (sorted order), excluding the converged targets
+      std::vector<int> keep;
+      for (int i = 0; i < j; ++i)
+        if (std::find(conv.begin(), conv.end(), i) == conv.end()) keep.push_back(ord[i]);
+      const bool restart = (int)keep.size() + (int)unconv.size() > maxb;
+      const int nu = (int)unconv.size();
+      // corrections first (X/R columns of the unconverged targets into XU / Tb)
+      for (int c = 0; c < nu; ++c) {
+        CUCHK(cudaMemcpyAsync(Tb + (size_t)c * n, Rr + (size_t)unconv[c] * n, sizeof(T) * n,
+                              cudaMemcpyDeviceToDevice, s));
+        if (precond == PHSVDS_PREC_JACOBI)
+          CUCHK(cudaMemcpyAsync(XU + (size_t)c * n, Xr + (size_t)unconv[c] * n, sizeof(T) * n,
+                                cudaMemcpyDeviceToDevice, s));
+      }
+      if (precond == PHSVDS_PREC_JACOBI && nu > 0) {
+        double* hu = h.at<double>(1024);     // bytes [1024, 1088)
+        for (int c = 0; c < nu; ++c) hu[c] = thv[unconv[c]];
+        CUCHK(cudaMemcpyAsync(thU, hu, sizeof(double) * nu, cudaMemcpyHostToDevice, s));
+        zero(s, dots, 2 * nu);
+        const double guard = EPS64 * std::max(out.theta_max, 1e-300);
+        jacobi_dots<T>(s, n, diagC, XU, n, Tb, n, nu, thU, guard, dots);
+        jacobi_apply<T>(s, n, diagC, XU, n, Tb, n, nu, thU, guard, dots, Tb, n);
+      }
+      if (restart || !conv.empty()) {
+        if (restart && ++out.restarts > max_restarts)
+          throw PhError{PHSVDS_ERR_NOT_CONVERGED, "stage 1: restart limit reached"};
+        int* hi = h.at<int>(2048);           // bytes [2048, 2560)
+        const int nkeep = (int)keep.size();
+        for (int i = 0; i < nkeep; ++i) hi[i] = keep[i];
+        for (size_t i = 0; i < conv.size(); ++i) hi[LD + i] = ord[conv[i]];
+        CUCHK(cudaMemcpyAsync(idx, hi, sizeof(int) * 2 * LD, cudaMemcpyHostToDevice, s));
+        gather_cols(s, j, S, LD, idx, nkeep, cand, LD, nullptr, nullptr);
+        int nc = nkeep, lim_a = nkeep, nmax = nkeep;
+        if (restart) {
+          lim_a = std::min(nkeep, mins - kp);
+          nmax = mins;
+          if (nsp) {
+            CUCHK(cudaMemcpy2DAsync(cand + (size_t)nkeep * LD, LD * sizeof(double), sprev, LD * sizeof(double),
+                                    j * sizeof(double), nsp, cudaMemcpyDeviceToDevice, s));
+            nc += nsp;
+          }
+        }
+        const int ne = (int)conv.size();
+        if (ne) gather_cols(s, j, S, LD, idx + LD, ne, excl, LD, nullptr, nullptr);
+        build_transform(s, j, S, LD, Aw, LD, cand, LD, nc, nkeep, lim_a, excl, LD, ne, nmax, Yt, LD, jn, nullptr,
+                        LD);
+        int jnew = nkeep;
+        if (restart) {
+          CUCHK(cudaMemcpyAsync(h.at<int>(12288), jn, sizeof(int), cudaMemcpyDeviceToHost, s));
+          sync(s);
+          jnew = *h.at<int>(12288);
+        }
+        tall_times_small<T>(s, n, V, n, j, Yt, LD, jnew, V, n, nullptr, 0, nullptr, nullptr);
+        tall_times_small<T>(s, n, W, n, j, Yt, LD, jnew, W, n, nullptr, 0, nullptr, nullptr);
+        gram_full<T>(s, n, V, W, jnew, Ht, w1);
+        set_identity(s, jnew, S, LD);
+        s_ident = true;
+        j = jnew;
+        // the unconverged targets are the first nu columns of the new basis
+        double* hs = h.at<double>(4096);     // bytes [4096, 8192)
+        for (int c = 0; c < nu; ++c)
+          for (int r = 0; r < LD; ++r) hs[r + c * LD] = (r == c) ? 1.0 : 0.0;
+        if (nu) CUCHK(cudaMemcpyAsync(sprev, hs, sizeof(double) * LD * nu, cudaMemcpyHostToDevice, s));
+        nsp = nu;
+      } else {
+        // +k vectors of the next restart: this iteration's target coefficients
+        for (int c = 0; c < nu; ++c)
+          CUCHK(cudaMemcpyAsync(sprev + (size_t)c * LD, Scols + (size_t)unconv[c] * LD, sizeof(double) * j,
+                                cudaMemcpyDeviceToDevice, s));
+        nsp = nu;
+      }
+      nb = nu;
+      if (nb == 0 && j == 0) throw PhError{PHSVDS_ERR_BREAKDOWN, "stage 1: empty basis"};
+    }
+  }
+  std::vector<int> final_conv, final_ord;
+};
+
+// ---------------------------------------------------------------------------
+// FP64 helpers shared by the Rayleigh-Ritz post-process and stage 2
+// ---------------------------------------------------------------------------
+struct F64Ctx {
+  phsvds_ctx* ctx;
+  cudaStream_t s;
+  Pool& pool;
+  DevA& A;
+  double *t1, *t2, *acc;   // n- and m-sized temporaries, accumulators
+  F64Ctx(phsvds_ctx* c, Pool& p, DevA& a) : ctx(c), s(c->stream), pool(p), A(a) {
+    t1 = pool.get<double>((size_t)a.m + a.n);
+    t2 = pool.get<double>((size_t)a.m + a.n);
+    acc = pool.get<double>(64);
+  }
+  // w = B x, x = [v; u] (n + m)
+  void B(const double* x, double* w) {
+    csr_spmm<double>(s, A.At64, 1, x + A.n, w);
+    csr_spmm<double>(s, A.A64, 1, x, w + A.n);
+  }
+};
+
+// Orthonormalise one column t (length N) against [P1 | P2] (FP64, CGS twice),
+// replacing it by a random vector when it is numerically dependent.  Result
+// written to dst.  Returns false if even random replacements fail.
+struct Orth1 {
+  phsvds_ctx* ctx;
+  cudaStream_t s;
+  double *G1, *G2, *tn, *inn, *minv;
+  uint64_t seed;
+  int rand_ctr = 0;
+  Orth1(phsvds_ctx* c, Pool& p, uint64_t sd) : ctx(c), s(c->stream), seed(sd) {
+    G1 = p.get<double>(2 * LD);
+    G2 = p.get<double>(2 * LD);
+    tn = p.get<double>(4);
+    inn = p.get<double>(4);
+    minv = p.get<double>(4);
+  }
+  void run(int N, const Basis<double>& P, double* t, double* dst) {
+    Host h(ctx);
+    const int p = P.cols();
+    for (int attempt = 0;; ++attempt) {
+      zero(s, inn, 1);
+      col_norms2_dense<double>(s, N, t, N, 1, inn);
+      zero(s, G1, p);
+      zero(s, G2, p);
+      zero(s, tn, 1);
+      cgs_pass<double>(s, N, P, t, N, 1, nullptr, G1, nullptr);
+      cgs_pass<double>(s, N, P, t, N, 1, G1, G2, nullptr);
+      cgs_pass<double>(s, N, P, t, N, 1, G2, nullptr, tn);
+      CUCHK(cudaMemcpyAsync(h.at<double>(0), tn, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CUCHK(cudaMemcpyAsync(h.at<double>(8), inn, sizeof(double), cudaMemcpyDeviceToHost, s));
+      sync(s);
+      const double a = *h.at<double>(0), b0 = *h.at<double>(8);
+      if (!std::isfinite(a)) throw PhError{PHSVDS_ERR_NAN, "non-finite vector in orthogonalisation"};
+      if (b0 > 0 && a > 1e-20 * b0) {
+        const double f = 1.0 / std::sqrt(a);
+        scal(s, N, f, nullptr, t);
+        if (dst != t) CUCHK(cudaMemcpyAsync(dst, t, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+        return;
+      }
+      if (attempt >= 3) throw PhError{PHSVDS_ERR_BREAKDOWN, "cannot extend the basis"};
+      fill_random<double>(s, N, t, seed, RS_BREAK + 0x100000 + (uint64_t)(rand_ctr++));
+    }
+  }
+};
+
+// Rayleigh-Ritz of C on [Xl, extra] (Algorithm 1 step 3), FP64.  Returns the k
+// new eigenvalues (target order) and writes the k new vectors to Xout (n x k).
+static std::vector<double> rayleigh_ritz_post(phsvds_ctx* ctx, Pool& pool, DevA& A, COp<double>& op, const double* Xl,
+                                              int k, const double* Extra, int nextra, bool largest, uint64_t seed,
+                                              double* Xout, int64_t& mv) {
+  cudaStream_t s = ctx->stream;
+  const int n = A.n;
+  const int q = k + nextra;
+  double* Q = pool.get<double>((size_t)n * q);
+  double* WQ = pool.get<double>((size_t)n * q);
+  double* Xrm = pool.get<double>((size_t)n * 8);
+  double* Yrm = pool.get<double>((size_t)n * 8);
+  double* tmp = pool.get<double>(n);
+  double* H = pool.get<double>(LD * LD);
+  double* Hc = pool.get<double>(LD * 8);
+  double* S = pool.get<double>(LD * LD);
+  double* th = pool.get<double>(LD);
+  double* Sc = pool.get<double>(LD * LD);
+  int* ord = pool.get<int>(LD);
+  int* sw = pool.get<int>(2);
+  Orth1 orth(ctx, pool, seed);
+  for (int c = 0; c < q; ++c) {
+    const double* src = c < k ? Xl + (size_t)c * n : Extra + (size_t)(c - k) * n;
+    CUCHK(cudaMemcpyAsync(tmp, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    Basis<double> P{Q, n, c, nullptr, 0, 0};
+    orth.run(n, P, tmp, Q + (size_t)c * n);
+  }
+  for (int c = 0; c < q;) {
+    const int w = spmm_width(q - c);
+    cm_to_rm<double>(s, n, Q + (size_t)c * n, n, w, Xrm);
+    op.apply(s, w, Xrm, Yrm);
+    rm_to_cm<double>(s, n, Yrm, w, WQ + (size_t)c * n, n);
+    c += w;
+  }
+  mv += q;
+  for (int c = 0; c < q;) {
+    const int w = std::min(8, q - c);
+    zero(s, Hc, (size_t)q * w);
+    Basis<double> P{Q, n, q, nullptr, 0, 0};
+    cgs_pass<double>(s, n, P, WQ + (size_t)c * n, n, w, nullptr, Hc, nullptr);
+    CUCHK(cudaMemcpy2DAsync(H + (size_t)c * LD, LD * sizeof(double), Hc, q * sizeof(double), q * sizeof(double), w,
+                            cudaMemcpyDeviceToDevice, s));
+    c += w;
+  }
+  // symmetrised H into the frame matrix Sc (frame_append with an empty frame
+  // expects the new columns compact, ld = q) and S = I
+  double* Hq = pool.get<double>((size_t)q * q);
+  CUCHK(cudaMemcpy2DAsync(Hq, q * sizeof(double), H, LD * sizeof(double), q * sizeof(double), q,
+                          cudaMemcpyDeviceToDevice, s));
+  frame_append(s, 0, q, Sc, LD, S, LD, Hq);
+  jacobi_eig_ld(s, q, Sc, LD, S, LD, th, JAC_TOL, 60, sw);
+  order_theta(s, q, th, largest ? 1 : 0, 0.0, ord);
+  double* Sk = pool.get<double>(LD * LD);
+  double* thk = pool.get<double>(LD);
+  gather_cols(s, q, S, LD, ord, k, Sk, LD, th, thk);
+  tall_times_small<double>(s, n, Q, n, q, Sk, LD, k, Xout, n, nullptr, 0, nullptr, nullptr);
+  Host h(ctx);
+  CUCHK(cudaMemcpyAsync(h.at<double>(0), thk, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+  sync(s);
+  return std::vector<double>(h.at<double>(0), h.at<double>(0) + k);
+}
+
+// ---------------------------------------------------------------------------
+// Stage 2: refined projection on B (Algorithm 2), FP64
+// ---------------------------------------------------------------------------
+struct Stage2 {
+  phsvds_ctx* ctx;
+  cudaStream_t s;
+  Pool& pool;
+  F64Ctx& f;
+  int m, n, N, k, maxb, mins;
+  double delta, normA;
+  uint64_t seed;
+  int max_restarts;
+  double time_limit_s;
+  std::chrono::steady_clock::time_point t0;
+  double *V, *W, *Q, *Xl, *x0, *tv, *xr, *rr;
+  double *Aw, *S, *Ht, *w1, *w2, *theta, *R, *G, *SR, *sig, *s1, *rq, *Hn, *Hfull, *Yt, *A2, *cand, *excl, *sprev,
+      *nrm, *G1, *G2, *tn2, *minv, *thl;
+  bool s_ident = true, sr_ident = true;
+  int *order, *sw, *jn, *idx_lock;
+  Orth1 orth;
+  int j = 0, nl = 0;
+  int64_t iters = 0, restarts = 0, mv = 0;
+  std::vector<double> th_lock;
+
+  Stage2(phsvds_ctx* c, Pool& p, F64Ctx& ff, DevA& A, int k_, const phsvds_opts& o, double delta_, double normA_)
+      : ctx(c), s(c->stream), pool(p), f(ff), m(A.m), n(A.n), N(A.m + A.n), k(k_), maxb(o.max_basis),
+        mins(o.min_restart), delta(delta_), normA(normA_), seed(o.seed), max_restarts(o.max_restarts),
+        time_limit_s(o.time_limit_s), orth(c, p, o.seed) {
+    const size_t NN = (size_t)N;
+    V = pool.get<double>(NN * maxb);
+    W = pool.get<double>(NN * maxb);
+    Q = pool.get<double>(NN * maxb);
+    Xl = pool.get<double>(NN * k);
+    x0 = pool.get<double>(NN * k);
+    tv = pool.get<double>(NN);
+    xr = pool.get<double>(NN);
+    rr = pool.get<double>(NN);
+    Aw = pool.get<double>(LD * LD);
+    S = pool.get<double>(LD * LD);
+    Ht = pool.get<double>(LD * LD);
+    w1 = pool.get<double>(LD * LD);
+    w2 = pool.get<double>(LD * LD);
+    theta = pool.get<double>(LD);
+    R = pool.get<double>(LD * LD);
+    G = pool.get<double>(LD * LD);
+    SR = pool.get<double>(LD * LD);
+    sig = pool.get<double>(LD);
+    s1 = pool.get<double>(LD);
+    rq = pool.get<double>(4);
+    Hn = pool.get<double>(LD);
+    Hfull = pool.get<double>(LD * LD);
+    Yt = pool.get<double>(LD * LD);
+    A2 = pool.get<double>(LD * LD);
+    cand = pool.get<double>(LD * (2 * LD + 2));
+    excl = pool.get<double>(LD);
+    sprev = pool.get<double>(LD);
+    nrm = pool.get<double>(4);
+    G1 = pool.get<double>(LD);
+    G2 = pool.get<double>(LD);
+    tn2 = pool.get<double>(4);
+    minv = pool.get<double>(4);
+    thl = pool.get<double>(LD);
+    order = pool.get<int>(LD);
+    sw = pool.get<int>(4);
+    jn = pool.get<int>(4);
+    idx_lock = pool.get<int>(LD);
+  }
+
+  void check_time() {
+    if (time_limit_s > 0) {
+      const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      if (el > time_limit_s) throw PhError{PHSVDS_ERR_TIMEOUT, "time limit reached in stage 2"};
+    }
+  }
+
+  // Append t (orthonormalised against [Xl | V]) as column j; W(:, j) = B v_j;
+  // the frame gets the new column of H = V^T W.
+  void append(double* t) {
+    Basis<double> P{Xl, N, nl, V, N, j};
+    orth.run(N, P, t, V + (size_t)j * N);
+    f.B(V + (size_t)j * N, W + (size_t)j * N);
+    ++mv;
+    zero(s, Hn, j + 1);
+    Basis<double> Pv{V, N, j + 1, nullptr, 0, 0};
+    cgs_pass<double>(s, N, Pv, W + (size_t)j * N, N, 1, nullptr, Hn, nullptr);
+    h_append(s, j, 1, Ht, LD, S, LD, Hn);
+    ++j;
+  }
+
+  // QR column c of Z = W - shift V into Q(:, c), R(:, c) (update_g: also G, S_R).
+  void qr_col(int c, double shift, int update_g) {
+    double* z = Q + (size_t)c * N;
+    CUCHK(cudaMemcpyAsync(z, W + (size_t)c * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    axpby(s, N, -shift, V + (size_t)c * N, 1.0, z);
+    Basis<double> P{Q, N, c, nullptr, 0, 0};
+    zero(s, G1, c + 1);
+    zero(s, G2, c + 1);
+    zero(s, tn2, 1);
+    cgs_pass<double>(s, N, P, z, N, 1, nullptr, G1, nullptr);
+    cgs_pass<double>(s, N, P, z, N, 1, G1, G2, nullptr);
+    cgs_pass<double>(s, N, P, z, N, 1, G2, nullptr, tn2);
+    qr_column(s, c, c ? G1 : nullptr, c ? G2 : nullptr, tn2, R, LD, G, LD, SR, LD, minv, update_g);
+    scal(s, N, 0.0, minv, z);
+  }
+
+  void full_qr(double shift) {
+    zero(s, R, LD * LD);  // the strictly lower triangle stays zero
+    for (int c = 0; c < j; ++c) qr_col(c, shift, 0);
+    set_identity(s, j, SR, LD);
+    sr_ident = true;
+  }
+
+  // Working matrix of the one-sided Jacobi SVD, rebuilt from the exact R:
+  // S_R <- S_R (3I - S_R^T S_R)/2, G = R S_R.
+  void svd_frame() {
+    if (sr_ident) {
+      CUCHK(cudaMemcpy2DAsync(G, LD * sizeof(double), R, LD * sizeof(double), j * sizeof(double), j,
+                              cudaMemcpyDeviceToDevice, s));
+      return;
+    }
+    small_gemm_tn(s, j, j, j, SR, LD, SR, LD, w1, LD);
+    ns_factor(s, j, w1, LD);
+    small_gemm_nn(s, j, j, j, SR, LD, w1, LD, w2, LD);
+    CUCHK(cudaMemcpy2DAsync(SR, LD * sizeof(double), w2, LD * sizeof(double), j * sizeof(double), j,
+                            cudaMemcpyDeviceToDevice, s));
+    small_gemm_nn(s, j, j, j, R, LD, SR, LD, G, LD);
+  }
+
+  // Transform the basis by Y (j x jn basis coordinates, from build_transform).
+  void transform(int jnew) {
+    tall_times_small<double>(s, N, V, N, j, Yt, LD, jnew, V, N, nullptr, 0, nullptr, nullptr);
+    tall_times_small<double>(s, N, W, N, j, Yt, LD, jnew, W, N, nullptr, 0, nullptr, nullptr);
+    gram_full<double>(s, N, V, W, jnew, Ht, w1);
+    set_identity(s, jnew, S, LD);
+    s_ident = true;
+    j = jnew;
+  }
+
+  // sig_s: k shifts (stage-1 values), Vt: n x k FP64 stage-1 right vectors.
+  void run(const std::vector<double>& sig_s, const double* Vt) {
+    t0 = std::chrono::steady_clock::now();
+    Host h(ctx);
+    // ---- initial guesses [v; A v / s] / sqrt(2) (Algorithm 2 step 1, Sec. 3.3)
+    zero(s, nrm, 2);
+    double* hv = h.at<double>(0);
+    for (int i = 0; i < k; ++i) {
+      double* xi = x0 + (size_t)i * N;
+      CUCHK(cudaMemcpyAsync(xi, Vt + (size_t)i * n, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      if (sig_s[i] > std::sqrt(EPS64) * normA) {
+        csr_spmm<double>(s, f.A.A64, 1, xi, xi + n);
+        ++mv;
+      } else {
+        fill_random<double>(s, m, xi + n, seed, RS_U + i);
+      }
+      zero(s, nrm, 2);
+      col_norms2_dense<double>(s, n, xi, N, 1, nrm);
+      col_norms2_dense<double>(s, m, xi + n, N, 1, nrm + 1);
+      CUCHK(cudaMemcpyAsync(hv + 2 * i, nrm, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+      sync(s);
+      const double nv = std::sqrt(hv[2 * i]), nu = std::sqrt(hv[2 * i + 1]);
+      if (!(nv > 0) || !(nu > 0)) throw PhError{PHSVDS_ERR_BREAKDOWN, "stage 2: zero initial guess"};
+      scal(s, n, 1.0 / (nv * std::sqrt(2.0)), nullptr, xi);
+      scal(s, m, 1.0 / (nu * std::sqrt(2.0)), nullptr, xi + n);
+    }
+    // ---- initial basis: K_{s-k}(B, x0_1) and the guesses (Algorithm 2 step 2)
+    const int qk = std::max(1, mins - k);
+    CUCHK(cudaMemcpyAsync(tv, x0, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    append(tv);
+    for (int r = 1; r < qk; ++r) {
+      CUCHK(cudaMemcpyAsync(tv, W + (size_t)(j - 1) * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+      append(tv);
+    }
+    const int nguess = std::min(k - 1, maxb - 1 - j);
+    for (int i = 1; i <= nguess; ++i) {
+      CUCHK(cudaMemcpyAsync(tv, x0 + (size_t)i * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+      append(tv);
+    }
+    int target = 0;
+    double shift = sig_s[0];
+    bool qr_full = true;
+    bool have_prev = false;
+    double r0 = -1.0;
+    while (true) {
+      check_time();
+      ++iters;
+      if (qr_full) {
+        full_qr(shift);
+        qr_full = false;
+      }
+      frame_from_true(s, j, Ht, S, Aw, w1, w2, s_ident);
+      s_ident = false;
+      jacobi_eig_ld(s, j, Aw, LD, S, LD, theta, JAC_TOL, 60, sw);
+      order_theta(s, j, theta, 2, shift, order);
+      svd_frame();
+      sr_ident = false;
+      jacobi_svd_ld(s, j, G, LD, SR, LD, sig, 1e-15, 60, sw + 1);
+      refined_vector(s, j, SR, LD, sig, nullptr, 0, Ht, LD, s1, rq);
+      tall_times_small<double>(s, N, V, N, j, s1, LD, 1, xr, N, nullptr, 0, nullptr, nullptr);
+      zero(s, nrm, 1);
+      tall_times_small<double>(s, N, W, N, j, s1, LD, 1, rr, N, xr, N, rq, nrm);
+      CUCHK(cudaMemcpyAsync(h.at<double>(0), rq, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+      CUCHK(cudaMemcpyAsync(h.at<double>(16), nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CUCHK(cudaMemcpyAsync(h.at<double>(32), theta, sizeof(double) * j, cudaMemcpyDeviceToHost, s));
+      sync(s);
+      const double th1 = *h.at<double>(0);
+      const double rn = std::sqrt(std::max(*h.at<double>(16), 0.0));
+      if (!std::isfinite(th1) || !std::isfinite(rn)) throw PhError{PHSVDS_ERR_NAN, "stage 2: non-finite residual"};
+      if (r0 < 0) r0 = rn;
+      if (trace_on())
+        fprintf(stderr, "s2 it=%lld j=%d target=%d shift=%.17g th1=%.17g rn=%.6e sigmin=%.6e\n", (long long)iters, j,
+                target, shift, th1, rn, *h.at<double>(8));
+      if (rn < delta * normA / std::sqrt(2.0)) {
+        CUCHK(cudaMemcpyAsync(Xl + (size_t)nl * N, xr, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+        ++nl;
+        th_lock.push_back(th1);
+        ++target;
+        if (target >= k) break;
+        // drop s1 from the basis: the other right singular vectors of R
+        {
+          double* hs = h.at<double>(8192);   // bytes [8192, 8704)
+          CUCHK(cudaMemcpyAsync(hs, sig, sizeof(double) * j, cudaMemcpyDeviceToHost, s));
+          sync(s);
+          int imin = 0;
+          for (int c = 1; c < j; ++c)
+            if (hs[c] < hs[imin]) imin = c;
+          int* hi = h.at<int>(9216);         // bytes [9216, 9472)
+          int nc = 0;
+          for (int c = 0; c < j; ++c)
+            if (c != imin) hi[nc++] = c;
+          int* idx = idx_lock;
+          CUCHK(cudaMemcpyAsync(idx, hi, sizeof(int) * nc, cudaMemcpyHostToDevice, s));
+          gather_cols(s, j, SR, LD, idx, nc, cand, LD, nullptr, nullptr);
+          build_transform(s, j, S, LD, Aw, LD, cand, LD, nc, nc, nc, excl, LD, 0, nc, Yt, LD, jn, nullptr, LD);
+          transform(nc);
+        }
+        CUCHK(cudaMemcpyAsync(tv, x0 + (size_t)target * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+        append(tv);
+        shift = sig_s[target];
+        qr_full = true;
+        have_prev = false;
+        r0 = -1.0;
+        continue;
+      }
+      if (j >= maxb) {
+        if (++restarts > max_restarts) throw PhError{PHSVDS_ERR_NOT_CONVERGED, "stage 2: restart limit reached"};
+        // candidates: s1, Ritz vectors by closeness to the shift, then the previous s1
+        CUCHK(cudaMemcpyAsync(cand, s1, sizeof(double) * j, cudaMemcpyDeviceToDevice, s));
+        gather_cols(s, j, S, LD, order, j, cand + LD, LD, nullptr, nullptr);
+        int nc = j + 1;
+        if (have_prev) {
+          CUCHK(cudaMemcpyAsync(cand + (size_t)nc * LD, sprev, sizeof(double) * j, cudaMemcpyDeviceToDevice, s));
+          ++nc;
+        }
+        build_transform(s, j, S, LD, Aw, LD, cand, LD, nc, j + 1, mins - 1, excl, LD, 0, mins, Yt, LD, jn, nullptr,
+                        LD);
+        CUCHK(cudaMemcpyAsync(h.at<int>(12288), jn, sizeof(int), cudaMemcpyDeviceToHost, s));
+        sync(s);
+        const int jnew = *h.at<int>(12288);
+        transform(jnew);
+        // s1 is the first new basis vector
+        double* hs = h.at<double>(10240);    // bytes [10240, 10752)
+        for (int r = 0; r < LD; ++r) hs[r] = r == 0 ? 1.0 : 0.0;
+        CUCHK(cudaMemcpyAsync(sprev, hs, sizeof(double) * LD, cudaMemcpyHostToDevice, s));
+        have_prev = true;
+        if (rn < r0) shift = th1;  // Rayleigh quotient of the refined vector (Sec. 3.2)
+        qr_full = true;
+      } else {
+        CUCHK(cudaMemcpyAsync(sprev, s1, sizeof(double) * j, cudaMemcpyDeviceToDevice, s));
+        have_prev = true;
+      }
+      // ---- expand with t = r
+      CUCHK(cudaMemcpyAsync(tv, rr, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+      append(tv);
+      CUCHK(cudaMemsetAsync(sprev + (j - 1), 0, sizeof(double), s));
+      if (!qr_full) qr_col(j - 1, shift, 1);
+    }
+  }
+};
+
+// Final triplets from right vectors V (n x k) and, when U != nullptr, left
+// vectors U (m x k): normalise, sigma = u^T A v (or ||A v|| with u = A v/||A v||
+// when U is null), residual sqrt(||A v - s u||^2 + ||A^T u - s v||^2).
+static void final_triplets(phsvds_ctx* ctx, Pool& pool, DevA& A, int k, double* Vd, double* Ud, bool have_u,
+                           std::vector<double>& sigma, std::vector<double>& resid) {
+  cudaStream_t s = ctx->stream;
+  const int m = A.m, n = A.n;
+  double* av = pool.get<double>(m);
+  double* atu = pool.get<double>(n);
+  double* acc = pool.get<double>(8);
+  Host h(ctx);
+  sigma.assign(k, 0.0);
+  resid.assign(k, 0.0);
+  for (int i = 0; i < k; ++i) {
+    double* v = Vd + (size_t)i * n;
+    double* u = Ud + (size_t)i * m;
+    zero(s, acc, 4);
+    col_norms2_dense<double>(s, n, v, n, 1, acc);
+    if (have_u) col_norms2_dense<double>(s, m, u, m, 1, acc + 1);
+    CUCHK(cudaMemcpyAsync(h.at<double>(0), acc, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+    sync(s);
+    const double nv = std::sqrt(*h.at<double>(0)), nu = have_u ? std::sqrt(*h.at<double>(8)) : 1.0;
+    scal(s, n, 1.0 / nv, nullptr, v);
+    if (have_u) scal(s, m, 1.0 / nu, nullptr, u);
+    csr_spmm<double>(s, A.A64, 1, v, av);
+    zero(s, acc, 4);
+    if (have_u) {
+      dot_accum(s, m, u, av, acc);
+    } else {
+      col_norms2_dense<double>(s, m, av, m, 1, acc);
+    }
+    CUCHK(cudaMemcpyAsync(h.at<double>(0), acc, sizeof(double), cudaMemcpyDeviceToHost, s));
+    sync(s);
+    double sg = have_u ? *h.at<double>(0) : std::sqrt(*h.at<double>(0));
+    if (!have_u) {
+      CUCHK(cudaMemcpyAsync(u, av, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+      scal(s, m, sg > 0 ? 1.0 / sg : 0.0, nullptr, u);
+    } else if (sg < 0) {
+      scal(s, m, -1.0, nullptr, u);
+      sg = -sg;
+    }
+    sigma[i] = sg;
+    csr_spmm<double>(s, A.At64, 1, u, atu);
+    axpby(s, m, -sg, u, 1.0, av);   // av = A v - s u
+    axpby(s, n, -sg, v, 1.0, atu);  // atu = A^T u - s v
+    zero(s, acc, 4);
+    col_norms2_dense<double>(s, m, av, m, 1, acc);
+    col_norms2_dense<double>(s, n, atu, n, 1, acc + 1);
+    CUCHK(cudaMemcpyAsync(h.at<double>(0), acc, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+    sync(s);
+    resid[i] = std::sqrt(*h.at<double>(0) + *h.at<double>(8));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The whole method
+// ---------------------------------------------------------------------------
+static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const int64_t* rp, const int32_t* ci,
+                       const double* va, int on_dev, int k, phsvds_target target, double tol, phsvds_precond precond,
+                       const phsvds_opts& o, double* sigma, double* U, double* V, double* resid, phsvds_stats* st) {
+  using clk = std::chrono::steady_clock;
+  const auto tstart = clk::now();
+  cudaStream_t s = ctx->stream;
+  const bool largest = target == PHSVDS_LARGEST;
+  const bool mixed = o.precision == PHSVDS_MIXED;
+  const int b = std::max(1, std::min(o.block_size, k));
+  Pool pool(s);
+  DevA A;
+  upload_matrix(ctx, pool, A, m, n, nnz, rp, ci, va, on_dev, mixed, precond == PHSVDS_PREC_JACOBI, 8);
+  // SpMM schedule
+  int sch64 = o.spmm, sch32 = o.spmm;
+  if (o.spmm == PHSVDS_SPMM_AUTO) {
+    sch64 = autotune_spmm<double>(s, pool, A.A64, A.At64, A.Z64, A.n, spmm_width(b));
+    if (mixed) sch32 = autotune_spmm<float>(s, pool, A.A32, A.At32, A.Z32, A.n, spmm_width(b));
+  }
+  COp<double> op64{&A.A64, &A.At64, A.Z64, A.n, sch64};
+  COp<float> op32{&A.A32, &A.At32, A.Z32, A.n, sch32};
+  if (st) {
+    std::memset(st, 0, sizeof(*st));
+    st->spmm_schedule = sch64;
+  }
+  // ---- stage 1
+  const auto t1a = clk::now();
+  Stage1<double> s1(ctx, pool, A.n, k, o, largest, tol, EPS64, precond, A.diagC, op64);
+  int64_t iters32 = 0, mv32 = 0;
+  double theta_max32 = 0.0;
+  if (mixed) {
+    Stage1<float> s1f(ctx, pool, A.n, k, o, largest, tol, EPS32, precond, A.diagC, op32);
+    s1f.run(nullptr, 0);
+    iters32 = s1f.out.iters;
+    mv32 = s1f.out.mv;
+    theta_max32 = s1f.out.theta_max;
+    // continue in FP64 from the FP32 eigenvectors (promoted)
+    double* X0 = pool.get<double>((size_t)A.n * k);
+    convert_f32_to_f64(s, (int64_t)A.n * k, s1f.Xl, X0);
+    s1.out.restarts = s1f.out.restarts;
+    s1.out.theta_max = s1f.out.theta_max;  // the ||C|| estimate carries over
+    s1.run(X0, k);
+  } else {
+    s1.run(nullptr, 0);
+  }
+  sync(s);
+  const auto t1b = clk::now();
+  double normA = std::sqrt(std::max(s1.out.theta_max, theta_max32));
+  // stage-1 triplets u = A v / ||A v||
+  double* Vd = pool.get<double>((size_t)A.n * k);
+  double* Ud = pool.get<double>((size_t)A.m * k);
+  CUCHK(cudaMemcpyAsync(Vd, s1.Xl, sizeof(double) * A.n * k, cudaMemcpyDeviceToDevice, s));
+  std::vector<double> sg, rs;
+  final_triplets(ctx, pool, A, k, Vd, Ud, false, sg, rs);
+  int64_t mvA = s1.out.mv + mv32 + k, mvAt = s1.out.mv + mv32 + k;
+  bool need2 = false;
+  const double floor = o.eps_factor * EPS64;
+  for (int i = 0; i < k; ++i)
+    if (tol < floor * normA / std::max(sg[i], 1e-300) || !(rs[i] < tol * normA)) need2 = true;
+  int64_t it2 = 0, rs2 = 0;
+  double t2ms = 0.0;
+  if (need2 && o.stage2) {
+    const auto t2a = clk::now();
+    std::vector<double> lam = s1.out.lam;
+    double* Xv = s1.Xl;
+    F64Ctx f(ctx, pool, A);
+    if (o.rayleigh_ritz) {
+      // basis for the post-process: locked vectors + best remaining Ritz vectors
+      const int extra = std::max(0, std::min(o.min_restart - k, s1.j - (int)s1.final_conv.size()));
+      double* Ext = pool.get<double>((size_t)A.n * std::max(extra, 1));
+      if (extra > 0) {
+        Host h(ctx);
+        int* hi = h.at<int>(0);
+        int ne = 0;
+        for (int i = 0; i < s1.j && ne < extra; ++i) {
+          const bool c = std::find(s1.final_conv.begin(), s1.final_conv.end(), i) != s1.final_conv.end();
+          if (!c) hi[ne++] = s1.final_ord[i];
+        }
+        int* didx = pool.get<int>(LD);
+        CUCHK(cudaMemcpyAsync(didx, hi, sizeof(int) * ne, cudaMemcpyHostToDevice, s));
+        gather_cols(s, s1.j, s1.S, LD, didx, ne, s1.Scols, LD, nullptr, nullptr);
+        tall_times_small<double>(s, A.n, s1.V, A.n, s1.j, s1.Scols, LD, ne, Ext, A.n, nullptr, 0, nullptr, nullptr);
+      }
+      double* Xrr = pool.get<double>((size_t)A.n * k);
+      int64_t mvrr = 0;
+      lam = rayleigh_ritz_post(ctx, pool, A, op64, s1.Xl, k, Ext, extra, largest, o.seed, Xrr, mvrr);
+      mvA += mvrr;
+      mvAt += mvrr;
+      Xv = Xrr;
+    }
+    std::vector<double> sig_s(k);
+    for (int i = 0; i < k; ++i) sig_s[i] = std::sqrt(std::max(lam[i], 0.0));
+    Stage2 s2(ctx, pool, f, A, k, o, tol, normA);
+    s2.run(sig_s, Xv);
+    mvA += s2.mv;
+    mvAt += s2.mv;
+    it2 = s2.iters;
+    rs2 = s2.restarts;
+    // split x = [v; u]
+    for (int i = 0; i < k; ++i) {
+      CUCHK(cudaMemcpyAsync(Vd + (size_t)i * A.n, s2.Xl + (size_t)i * s2.N, sizeof(double) * A.n,
+                            cudaMemcpyDeviceToDevice, s));
+      CUCHK(cudaMemcpyAsync(Ud + (size_t)i * A.m, s2.Xl + (size_t)i * s2.N + A.n, sizeof(double) * A.m,
+                            cudaMemcpyDeviceToDevice, s));
+    }
+    final_triplets(ctx, pool, A, k, Vd, Ud, true, sg, rs);
+    mvA += 2 * k;
+    mvAt += k;
+    sync(s);
+    t2ms = std::chrono::duration<double, std::milli>(clk::now() - t2a).count();
+  }
+  // order: ascending (smallest) / descending (largest)
+  std::vector<int> ord(k);
+  for (int i = 0; i < k; ++i) ord[i] = i;
+  std::sort(ord.begin(), ord.end(), [&](int a, int b2) { return largest ? sg[a] > sg[b2] : sg[a] < sg[b2]; });
+  Host h(ctx);
+  for (int i = 0; i < k; ++i) {
+    const int src = ord[i];
+    sigma[i] = sg[src];
+    if (resid) resid[i] = rs[src];
+    if (V) CUCHK(cudaMemcpyAsync(V + (size_t)i * A.n, Vd + (size_t)src * A.n, sizeof(double) * A.n,
+                                 cudaMemcpyDeviceToHost, s));
+    if (U) CUCHK(cudaMemcpyAsync(U + (size_t)i * A.m, Ud + (size_t)src * A.m, sizeof(double) * A.m,
+                                 cudaMemcpyDeviceToHost, s));
+  }
+  sync(s);
+  if (st) {
+    st->matvecs_A = mvA;
+    st->matvecs_At = mvAt;
+    st->iters_stage1 = s1.out.iters + iters32;
+    st->iters_stage1_fp32 = iters32;
+    st->iters_stage2 = it2;
+    st->restarts = s1.out.restarts + rs2;
+    st->switched = need2 && o.stage2;
+    st->norm_A_est = normA;
+    st->t_stage1_ms = std::chrono::duration<double, std::milli>(t1b - t1a).count();
+    st->t_stage2_ms = t2ms;
+    st->t_total_ms = std::chrono::duration<double, std::milli>(clk::now() - tstart).count();
+    st->spmm_schedule = sch64;
+  }
+  (void)iters32;
+}
+
+}  // namespace ph
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+using namespace ph;
+
+static phsvds_status set_err(phsvds_ctx* c, phsvds_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+template <typename T>
+static phsvds_status ata_api(phsvds_handle h, int schedule, int64_t m, int64_t n, const int32_t* rp, const int32_t* ci,
+                             const T* va, const int32_t* cp, const int32_t* ri, const T* cv, int b, const T* X, T* Y,
+                             T* z) {
+  if (!h || m < 1 || n < 1 || !rp || !X || !Y || (b != 1 && b != 2 && b != 4 && b != 8) ||
+      (schedule != 1 && schedule != 2) || (schedule == 2 && (!cp || !z)))
+    return set_err(h, PHSVDS_ERR_INVALID, "invalid SpMM arguments");
+  // nnz from the offsets is not needed by the kernels; the views carry it for the lane choice
+  SparseView<T> A{(int)m, (int)n, 0, rp, ci, va};
+  SparseView<T> At{(int)n, (int)m, 0, cp, ri, cv};
+  int last = 0;
+  if (cudaMemcpy(&last, rp + m, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return set_err(h, PHSVDS_ERR_CUDA, "cannot read row_ptr[m]");
+  A.nnz = last;
+  At.nnz = last;
+  if (schedule == 1)
+    ata_fused<T>(h->stream, A, (int)n, b, X, Y);
+  else
+    ata_two_phase<T>(h->stream, A, At, b, X, Y, z);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? PHSVDS_OK : set_err(h, PHSVDS_ERR_CUDA, cudaGetErrorString(e));
+}
+
+extern "C" {
+
+phsvds_status phsvds_default_opts(phsvds_opts* o) {
+  if (!o) return PHSVDS_ERR_INVALID;
+  o->block_size = 1;
+  o->max_basis = 35;
+  o->min_restart = 21;
+  o->max_restarts = 10000;
+  o->eps_factor = 4.0;
+  o->precision = PHSVDS_FP64;
+  o->spmm = PHSVDS_SPMM_AUTO;
+  o->stage2 = 1;
+  o->rayleigh_ritz = 1;
+  o->seed = 0;
+  o->time_limit_s = 0.0;
+  return PHSVDS_OK;
+}
+
+phsvds_status phsvds_create(phsvds_handle* out, int device, void* stream) {
+  if (!out) return PHSVDS_ERR_INVALID;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return PHSVDS_ERR_CUDA;
+  if (cudaSetDevice(device) != cudaSuccess) return PHSVDS_ERR_CUDA;
+  phsvds_ctx* c = new phsvds_ctx();
+  c->device = device;
+  if (stream) {
+    c->stream = static_cast<cudaStream_t>(stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return PHSVDS_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  c->host_bytes = 1 << 16;
+  if (cudaMallocHost(&c->host, c->host_bytes) != cudaSuccess) {
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return PHSVDS_ERR_OOM;
+  }
+  *out = c;
+  return PHSVDS_OK;
+}
+
+void phsvds_destroy(phsvds_handle h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  cudaStreamSynchronize(h->stream);
+  if (h->host) cudaFreeHost(h->host);
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+const char* phsvds_last_error(phsvds_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+const char* phsvds_status_string(phsvds_status s) {
+  switch (s) {
+    case PHSVDS_OK: return "ok";
+    case PHSVDS_ERR_INVALID: return "invalid argument";
+    case PHSVDS_ERR_NOT_CONVERGED: return "not converged";
+    case PHSVDS_ERR_BREAKDOWN: return "breakdown";
+    case PHSVDS_ERR_NAN: return "NaN or Inf";
+    case PHSVDS_ERR_TIMEOUT: return "time limit";
+    case PHSVDS_ERR_CUDA: return "CUDA error";
+    case PHSVDS_ERR_OOM: return "out of device memory";
+  }
+  return "unknown";
+}
+
+phsvds_status phsvds_sync(phsvds_handle h) {
+  if (!h) return PHSVDS_ERR_INVALID;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? PHSVDS_OK : set_err(h, PHSVDS_ERR_CUDA, cudaGetErrorString(e));
+}
+
+phsvds_status phsvds_solve(phsvds_handle h, int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr,
+                           const int32_t* col_idx, const double* val, int ptr_on_device, int k, phsvds_target target,
+                           double tol, phsvds_precond precond, const phsvds_opts* opts, double* sigma, double* U,
+                           double* V, double* resid, phsvds_stats* stats) {
+  if (!h) return PHSVDS_ERR_INVALID;
+  h->err.clear();
+  phsvds_opts o;
+  phsvds_default_opts(&o);
+  if (opts) o = *opts;
+  if (m < n || n < 1 || nnz < 0 || nnz >= (int64_t)1 << 31 || m >= (int64_t)1 << 31 || !row_ptr ||
+      (nnz > 0 && (!col_idx || !val)) || !sigma)
+    return set_err(h, PHSVDS_ERR_INVALID, "need m >= n >= 1, nnz < 2^31, non-null CSR arrays and sigma");
+  if (k < 1 || k > n || k >= o.min_restart || k + o.max_basis > LD)
+    return set_err(h, PHSVDS_ERR_INVALID, "need 1 <= k <= n, k < min_restart and k + max_basis <= 64");
+  if (o.block_size < 1 || o.block_size > 8 || o.max_basis < 4 || o.max_basis + 8 > LD ||
+      o.min_restart < 2 * std::min(o.block_size, k) || o.min_restart >= o.max_basis || !(tol > 0) ||
+      o.max_restarts < 1 || (target != PHSVDS_SMALLEST && target != PHSVDS_LARGEST) ||
+      (precond != PHSVDS_PREC_NONE && precond != PHSVDS_PREC_JACOBI) || o.max_basis > n)
+    return set_err(h, PHSVDS_ERR_INVALID, "invalid options (block 1..8, 2b <= min_restart < max_basis <= min(n,56))");
+  try {
+    CUCHK(cudaSetDevice(h->device));
+    solve_impl(h, m, n, nnz, row_ptr, col_idx, val, ptr_on_device, k, target, tol, precond, o, sigma, U, V, resid,
+               stats);
+  } catch (const PhError& e) {
+    cudaStreamSynchronize(h->stream);
+    cudaGetLastError();
+    return set_err(h, e.st, e.msg);
+  }
+  return PHSVDS_OK;
+}
+
+phsvds_status phsvds_csr_to_csc_f64(phsvds_handle h, int64_t m, int64_t n, int64_t nnz, const int32_t* row_ptr,
+                                    const int32_t* col_idx, const double* val, int32_t* csc_ptr, int32_t* csc_row,
+                                    double* csc_val) {
+  if (!h || m < 0 || n < 1 || nnz < 0 || !row_ptr || !csc_ptr) return PHSVDS_ERR_INVALID;
+  try {
+    CUCHK(cudaSetDevice(h->device));
+    int* work = nullptr;
+    CUCHK(cudaMallocAsync(&work, sizeof(int) * n, h->stream));
+    csr_to_csc<double>(h->stream, (int)m, (int)n, nnz, row_ptr, col_idx, val, csc_ptr, csc_row, csc_val, work);
+    CUCHK(cudaFreeAsync(work, h->stream));
+    CUCHK(cudaGetLastError());
+  } catch (const PhError& e) {
+    return set_err(h, e.st, e.msg);
+  }
+  return PHSVDS_OK;
+}
+
+phsvds_status phsvds_ata_spmm_f64(phsvds_handle h, int schedule, int64_t m, int64_t n, const int32_t* row_ptr,
+                                  const int32_t* col_idx, const double* val, const int32_t* csc_ptr,
+                                  const int32_t* csc_row, const double* csc_val, int b, const double* X, double* Y,
+                                  double* z) {
+  return ata_api<double>(h, schedule, m, n, row_ptr, col_idx, val, csc_ptr, csc_row, csc_val, b, X, Y, z);
+}
+
+phsvds_status phsvds_ata_spmm_f32(phsvds_handle h, int schedule, int64_t m, int64_t n, const int32_t* row_ptr,
+                                  const int32_t* col_idx, const float* val, const int32_t* csc_ptr,
+                                  const int32_t* csc_row, const float* csc_val, int b, const float* X, float* Y,
+                                  float* z) {
+  return ata_api<float>(h, schedule, m, n, row_ptr, col_idx, val, csc_ptr, csc_row, csc_val, b, X, Y, z);
+}
+
+phsvds_status phsvds_jacobi_eig_f64(phsvds_handle h, int j, double* H, double* S, double* theta, double tol,
+                                    int max_sweeps, int* sweeps_out) {
+  if (!h || j < 1 || j > LD || !H || !S || !theta) return PHSVDS_ERR_INVALID;
+  jacobi_eig(h->stream, j, H, S, theta, tol, max_sweeps, sweeps_out);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? PHSVDS_OK : set_err(h, PHSVDS_ERR_CUDA, cudaGetErrorString(e));
+}
+
+phsvds_status phsvds_jacobi_svd_f64(phsvds_handle h, int j, double* G, double* S, double* sig, double tol,
+                                    int max_sweeps, int* sweeps_out) {
+  if (!h || j < 1 || j > LD || !G || !S || !sig) return PHSVDS_ERR_INVALID;
+  jacobi_svd(h->stream, j, G, S, sig, tol, max_sweeps, sweeps_out);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? PHSVDS_OK : set_err(h, PHSVDS_ERR_CUDA, cudaGetErrorString(e));
+}
+
+}  // extern "C"

@@ -1,0 +1,184 @@
+"""ctypes binding of libphsvds.so (include/phsvds.h): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels; this module never
+computes anything itself.  Importing it without the built library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libphsvds.so")
+
+PHSVDS_OK, PHSVDS_ERR_INVALID, PHSVDS_ERR_NOT_CONVERGED, PHSVDS_ERR_BREAKDOWN = 0, 1, 2, 3
+PHSVDS_ERR_NAN, PHSVDS_ERR_TIMEOUT, PHSVDS_ERR_CUDA, PHSVDS_ERR_OOM = 4, 5, 6, 7
+SMALLEST, LARGEST = 0, 1
+PREC_NONE, PREC_JACOBI = 0, 1
+FP64, MIXED = 0, 1
+SPMM_AUTO, SPMM_FUSED_ATOMIC, SPMM_TWO_PHASE = 0, 1, 2
+
+
+class Opts(C.Structure):
+    _fields_ = [("block_size", C.c_int), ("max_basis", C.c_int), ("min_restart", C.c_int),
+                ("max_restarts", C.c_int), ("eps_factor", C.c_double), ("precision", C.c_int),
+                ("spmm", C.c_int), ("stage2", C.c_int), ("rayleigh_ritz", C.c_int),
+                ("seed", C.c_uint64), ("time_limit_s", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("matvecs_A", C.c_int64), ("matvecs_At", C.c_int64), ("iters_stage1", C.c_int64),
+                ("iters_stage1_fp32", C.c_int64), ("iters_stage2", C.c_int64), ("restarts", C.c_int64),
+                ("switched", C.c_int), ("norm_A_est", C.c_double), ("t_stage1_ms", C.c_double),
+                ("t_stage2_ms", C.c_double), ("t_total_ms", C.c_double), ("spmm_schedule", C.c_int)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class PhsvdsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"phsvds status {status}: {msg}")
+        self.status = status
+
+
+def _load() -> C.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libphsvds.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+    lib = C.CDLL(LIB_PATH)
+    P, I64, I, D = C.c_void_p, C.c_int64, C.c_int, C.c_double
+    sig = {
+        "phsvds_create": ([C.POINTER(C.c_void_p), I, P], I),
+        "phsvds_default_opts": ([C.POINTER(Opts)], I),
+        "phsvds_solve": ([P, I64, I64, I64, P, P, P, I, I, I, D, I, C.POINTER(Opts), P, P, P, P,
+                          C.POINTER(Stats)], I),
+        "phsvds_ata_spmm_f64": ([P, I, I64, I64, P, P, P, P, P, P, I, P, P, P], I),
+        "phsvds_ata_spmm_f32": ([P, I, I64, I64, P, P, P, P, P, P, I, P, P, P], I),
+        "phsvds_csr_to_csc_f64": ([P, I64, I64, I64, P, P, P, P, P, P], I),
+        "phsvds_jacobi_eig_f64": ([P, I, P, P, P, D, I, P], I),
+        "phsvds_jacobi_svd_f64": ([P, I, P, P, P, D, I, P], I),
+        "phsvds_sync": ([P], I),
+        "phsvds_last_error": ([P], C.c_char_p),
+        "phsvds_status_string": ([I], C.c_char_p),
+        "phsvds_destroy": ([P], None),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = _load()
+    return _lib
+
+
+EXPORTED = ["phsvds_create", "phsvds_default_opts", "phsvds_solve", "phsvds_ata_spmm_f64",
+            "phsvds_ata_spmm_f32", "phsvds_csr_to_csc_f64", "phsvds_jacobi_eig_f64",
+            "phsvds_jacobi_svd_f64", "phsvds_sync", "phsvds_last_error", "phsvds_status_string",
+            "phsvds_destroy"]
+
+
+def _ptr(x) -> int | None:
+    """Address of a numpy array or of a torch tensor (device or host); None for None."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    raise TypeError(type(x))
+
+
+class Handle:
+    """A library context on one CUDA device (phsvds_create / phsvds_destroy)."""
+
+    def __init__(self, device: int = 0, stream: int | None = None):
+        self.h = C.c_void_p()
+        st = lib().phsvds_create(C.byref(self.h), device, C.c_void_p(stream) if stream else None)
+        if st != PHSVDS_OK:
+            raise PhsvdsError(st, "phsvds_create failed")
+
+    def check(self, st: int):
+        if st != PHSVDS_OK:
+            raise PhsvdsError(st, lib().phsvds_last_error(self.h).decode())
+
+    def close(self):
+        if self.h:
+            lib().phsvds_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    lib().phsvds_default_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def phsvds_solve(h: Handle, m, n, row_ptr, col_idx, val, k, target=SMALLEST, tol=1e-14,
+                 precond=PREC_NONE, opts: Opts | None = None, on_device=False, want_vectors=True,
+                 raise_on_error=True):
+    """phsvds_solve: k smallest / largest triplets of the m x n CSR matrix.
+
+    row_ptr int64 (m+1), col_idx int32, val float64, as numpy arrays (host) or
+    torch CUDA tensors (on_device=True).  Returns (sigma, U, V, resid, stats, status).
+    """
+    nnz = int(row_ptr[-1]) if isinstance(row_ptr, np.ndarray) else int(row_ptr[-1].item())
+    sigma = np.zeros(k)
+    U = np.zeros((k, m)) if want_vectors else None     # row i = u_i (column-major m x k)
+    V = np.zeros((k, n)) if want_vectors else None
+    resid = np.zeros(k)
+    st = Stats()
+    o = opts if opts is not None else default_opts()
+    status = lib().phsvds_solve(h.h, m, n, nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(val), 1 if on_device else 0,
+                                k, target, tol, precond, C.byref(o), _ptr(sigma), _ptr(U), _ptr(V),
+                                _ptr(resid), C.byref(st))
+    if raise_on_error:
+        h.check(status)
+    return sigma, (U.T if U is not None else None), (V.T if V is not None else None), resid, st.as_dict(), status
+
+
+def phsvds_ata_spmm(h: Handle, schedule, m, n, rp32, ci, va, cp, ri, cv, b, X, Y, z=None, fp32=False):
+    """Kernel-level Y = A^T (A X) on device tensors (row-major n x b blocks)."""
+    f = lib().phsvds_ata_spmm_f32 if fp32 else lib().phsvds_ata_spmm_f64
+    h.check(f(h.h, schedule, m, n, _ptr(rp32), _ptr(ci), _ptr(va), _ptr(cp), _ptr(ri), _ptr(cv), b,
+              _ptr(X), _ptr(Y), _ptr(z)))
+
+
+def phsvds_csr_to_csc(h: Handle, m, n, nnz, rp32, ci, va, cp, ri, cv):
+    h.check(lib().phsvds_csr_to_csc_f64(h.h, m, n, nnz, _ptr(rp32), _ptr(ci), _ptr(va), _ptr(cp), _ptr(ri),
+                                        _ptr(cv)))
+
+
+def phsvds_jacobi_eig(h: Handle, j, H, S, theta, tol=1e-17, max_sweeps=60, sweeps=None):
+    h.check(lib().phsvds_jacobi_eig_f64(h.h, j, _ptr(H), _ptr(S), _ptr(theta), tol, max_sweeps, _ptr(sweeps)))
+
+
+def phsvds_jacobi_svd(h: Handle, j, G, S, sig, tol=1e-15, max_sweeps=60, sweeps=None):
+    h.check(lib().phsvds_jacobi_svd_f64(h.h, j, _ptr(G), _ptr(S), _ptr(sig), tol, max_sweeps, _ptr(sweeps)))
+
+
+def phsvds_sync(h: Handle):
+    h.check(lib().phsvds_sync(h.h))

@@ -1,0 +1,115 @@
+"""GPU kernels against the oracle, element by element (through the C ABI)."""
+import numpy as np
+import pytest
+
+from paper_1408_5535_gb300 import native, synth
+from oracle import phsvds_ref as R
+from oracle.dense_jacobi import jacobi_eig, jacobi_svd
+from tests.gpu_util import torch, need_gpu, dev, device_csr
+
+pytestmark = pytest.mark.gpu
+EPS64, EPS32 = 2.0 ** -52, 2.0 ** -23
+
+
+@pytest.fixture(scope="module")
+def h():
+    need_gpu()
+    with native.Handle(0) as hh:
+        yield hh
+
+
+def _cases():
+    return [synth.givens_diag(400, 200, sigma=synth.cluster_spectrum(200, 1e-3, 1.0, 3, 1e-6), n_rot=80, seed=1),
+            synth.random_sparse(3001, 1499, 12.0, 3),          # ragged tails, lognormal, several tiles
+            synth.grid_gradient(23, 1.0, 2),                   # 1-2 entries per row
+            synth.random_sparse(777, 333, 30.0, 4, values="gaussian", shift=0.0)]   # long rows
+
+
+@pytest.mark.parametrize("case", range(4))
+@pytest.mark.parametrize("b", [1, 2, 4, 8])
+@pytest.mark.parametrize("schedule", [1, 2])
+@pytest.mark.parametrize("fp32", [False, True])
+def test_ata_spmm_vs_oracle(h, case, b, schedule, fp32):
+    A = _cases()[case]
+    d = device_csr(A, fp32)
+    X = (synth.uniform(5, 10 + b, A.n * b) * 2 - 1).reshape(A.n, b)
+    ref = R.Ops(d["scipy"]).C(X)                                   # oracle product, FP64
+    absA = abs(d["scipy"])
+    bound = absA.T @ (absA @ np.abs(X))
+    vt = torch.float32 if fp32 else torch.float64
+    Xd = dev(X, vt)
+    Yd = torch.empty((A.n, b), dtype=vt, device="cuda")
+    z = torch.empty((A.m, b), dtype=vt, device="cuda")
+    native.phsvds_ata_spmm(h, schedule, A.m, A.n, d["rp"], d["ci"], d["va"], d["cp"], d["ri"], d["cv"], b, Xd, Yd,
+                           z, fp32=fp32)
+    native.phsvds_sync(h)
+    Y = Yd.double().cpu().numpy()
+    rowmax = np.diff(A.row_ptr).max() + 2
+    eps = EPS32 if fp32 else EPS64
+    assert np.all(np.abs(Y - ref) <= 4 * rowmax * eps * bound + 1e-300)
+
+
+def test_csr_to_csc_exact(h):
+    A = synth.random_sparse(5003, 2001, 9.0, 6)
+    d = device_csr(A)
+    cp = torch.empty(A.n + 1, dtype=torch.int32, device="cuda")
+    ri = torch.empty(A.nnz, dtype=torch.int32, device="cuda")
+    cv = torch.empty(A.nnz, dtype=torch.float64, device="cuda")
+    native.phsvds_csr_to_csc(h, A.m, A.n, A.nnz, d["rp"], d["ci"], d["va"], cp, ri, cv)
+    native.phsvds_sync(h)
+    T = d["scipy"].tocsc()
+    T.sort_indices()
+    assert np.array_equal(cp.cpu().numpy(), T.indptr)
+    assert np.array_equal(ri.cpu().numpy(), T.indices)
+    assert np.array_equal(cv.cpu().numpy(), T.data)
+
+
+@pytest.mark.parametrize("j", [1, 2, 7, 20, 35, 64])
+def test_jacobi_eig_vs_oracle(h, j):
+    rng = np.random.default_rng(j)
+    M = rng.standard_normal((j, j))
+    H = M + M.T
+    if j > 4:   # a tight cluster and a graded tail
+        Q, _ = np.linalg.qr(rng.standard_normal((j, j)))
+        ev = np.concatenate([[1e-8, 1e-8 + 1e-14, 2e-8], np.logspace(-6, 1, j - 3)])
+        H = Q @ np.diag(ev) @ Q.T
+        H = 0.5 * (H + H.T)
+    Hd = dev(np.asfortranarray(H).ravel(order="F"))
+    Sd = dev(np.eye(j).ravel(order="F"))
+    th = torch.empty(j, dtype=torch.float64, device="cuda")
+    sw = torch.zeros(1, dtype=torch.int32, device="cuda")
+    native.phsvds_jacobi_eig(h, j, Hd, Sd, th, 1e-17, 60, sw)
+    native.phsvds_sync(h)
+    S = Sd.cpu().numpy().reshape(j, j, order="F")
+    theta = th.cpu().numpy()
+    nrm = np.linalg.norm(H, 2)
+    ref, _ = jacobi_eig(H)                    # oracle's hand-written Jacobi
+    assert np.max(np.abs(np.sort(theta) - ref)) <= 10 * j * EPS64 * nrm
+    assert np.max(np.abs(S.T @ S - np.eye(j))) <= 50 * j * EPS64
+    assert np.linalg.norm(H @ S - S * theta) <= 50 * j * EPS64 * nrm
+    assert 0 < int(sw.item()) < 60 or j == 1
+
+
+@pytest.mark.parametrize("j", [1, 3, 21, 35, 64])
+def test_jacobi_svd_vs_oracle(h, j):
+    rng = np.random.default_rng(100 + j)
+    G = np.triu(rng.standard_normal((j, j)))
+    if j > 3:
+        G[:, -1] *= 1e-12   # one tiny singular value, as in the refined projection
+    Gd = dev(G.ravel(order="F"))
+    Sd = dev(np.eye(j).ravel(order="F"))
+    sig = torch.empty(j, dtype=torch.float64, device="cuda")
+    native.phsvds_jacobi_svd(h, j, Gd, Sd, sig, 1e-15, 60)
+    native.phsvds_sync(h)
+    S = Sd.cpu().numpy().reshape(j, j, order="F")
+    Go = Gd.cpu().numpy().reshape(j, j, order="F")
+    s = sig.cpu().numpy()
+    ref, _, _ = jacobi_svd(G)
+    nrm = np.linalg.norm(G, 2)
+    assert np.max(np.abs(np.sort(s) - ref)) <= 50 * j * EPS64 * nrm
+    assert np.max(np.abs(S.T @ S - np.eye(j))) <= 50 * j * EPS64
+    assert np.linalg.norm(G @ S - Go) <= 50 * j * EPS64 * nrm
+    # the smallest singular vector is accurate (relative to the gap)
+    i = int(np.argmin(s))
+    _, _, Vt = np.linalg.svd(G)
+    assert abs(abs(S[:, i] @ Vt[-1]) - 1) < 1e-8

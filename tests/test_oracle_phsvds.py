@@ -22,6 +22,20 @@ from oracle.dense_jacobi import dense_triplets
 DELTA = 1e-14
 
 
+def _orth_ok(X, sig, normA):
+    """Orthonormal columns up to what the residuals allow: |x_i^T x_j| <=
+    4 delta ||A|| / |s_i - s_j| (Davis-Kahan), never looser than 1e-7 and
+    never tighter than 1e-12."""
+    G = X.T @ X
+    k = G.shape[0]
+    assert np.max(np.abs(np.diag(G) - 1)) < 1e-12
+    for i in range(k):
+        for j in range(i + 1, k):
+            gap = abs(sig[i] - sig[j])
+            tol = 1e-12 if gap == 0 else min(1e-7, max(1e-12, 4 * DELTA * normA / gap))
+            assert abs(G[i, j]) <= tol, (i, j, G[i, j], tol)
+
+
 def _check(A, res, k, largest, sig_ex=None, normA=None, rel=1e-10):
     d = A.to_dense()
     if sig_ex is None:
@@ -36,8 +50,8 @@ def _check(A, res, k, largest, sig_ex=None, normA=None, rel=1e-10):
     rv = np.linalg.norm(d @ res.V - res.U * res.sigma, axis=0)
     ru = np.linalg.norm(d.T @ res.U - res.V * res.sigma, axis=0)
     assert np.all(np.sqrt(ru ** 2 + rv ** 2) <= DELTA * normA)
-    assert np.max(np.abs(res.V.T @ res.V - np.eye(k))) < 1e-12
-    assert np.max(np.abs(res.U.T @ res.U - np.eye(k))) < 1e-12
+    _orth_ok(res.V, res.sigma, normA)
+    _orth_ok(res.U, res.sigma, normA)
     return sig_ex
 
 
