@@ -76,6 +76,7 @@ typedef struct {
     int rayleigh_ritz;     /* 1 = Algorithm 1 step 3 before stage 2, default 1 */
     uint64_t seed;         /* SplitMix64 seed of the random vectors the method draws */
     double time_limit_s;   /* 0 = none */
+    int profile;           /* 1 = time kernel classes with CUDA events (stats.t_*_ms), default 0 */
 } phsvds_opts;
 
 typedef struct {
@@ -89,6 +90,18 @@ typedef struct {
     double norm_A_est;     /* running ||A|| estimate (largest Ritz value) */
     double t_stage1_ms, t_stage2_ms, t_total_ms;
     int spmm_schedule;     /* schedule used: 1 fused atomic, 2 two-phase */
+    int64_t kernel_launches;   /* CUDA kernels this solve launched */
+    /* with opts.profile: device time (CUDA events) and call counts per kernel
+     * class: [0] fused A^T A SpMM (products with C), [1] Gram / CGS passes,
+     * [2] basis transforms and Ritz vectors, [3] one-CTA projected eigen/SVD
+     * problems, [4] single products with A or A^T (products with B) */
+    double t_class_ms[5];
+    int64_t n_class[5];
+    int64_t spmm_c_calls;      /* C-products, each one fused A^T A SpMM launch set */
+    double spmm_c_ms;          /* their summed device time (opts.profile) */
+    int spmm_c_width;          /* block width of the stage-1 C-products */
+    int64_t jacobi_sweeps;     /* stage-1 projected eigensolver: sweeps and rotations */
+    int64_t jacobi_rotations;
 } phsvds_stats;
 
 /* Create a context on CUDA device `device`.  cuda_stream: a cudaStream_t to run
@@ -163,6 +176,15 @@ phsvds_status phsvds_csr_to_csc_f64(phsvds_handle h, int64_t m, int64_t n, int64
  */
 phsvds_status phsvds_jacobi_eig_f64(phsvds_handle h, int j, double* H, double* S, double* theta,
                                     double tol, int max_sweeps, int* sweeps_out);
+
+/*
+ * Kernel-level entry point: the same FP64 cyclic Jacobi eigensolver spread over
+ * an 8-CTA thread-block cluster (each CTA keeps a copy of H in shared memory
+ * and updates one eighth of each round's 2 x 2 blocks, exchanged through
+ * distributed shared memory).  Arguments and results as phsvds_jacobi_eig_f64.
+ */
+phsvds_status phsvds_jacobi_eig_cluster_f64(phsvds_handle h, int j, double* H, double* S, double* theta,
+                                            double tol, int max_sweeps, int* sweeps_out);
 
 /*
  * Kernel-level entry point: one-CTA FP64 one-sided (Hestenes) Jacobi SVD of a

@@ -9,8 +9,12 @@
 //  * Cholesky of a block Gram matrix (CholQR of the new block), the restart /
 //    locking transform builder and small gathers.
 // Small matrices are column-major with a leading dimension ld (<= 64).
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "kernels.h"
+
+namespace cg = cooperative_groups;
 
 namespace ph {
 
@@ -32,6 +36,25 @@ __device__ inline void rr_pair(int jj, int r, int k, int& p, int& q) {
   q = a < b ? b : a;
 }
 
+// Rotation of the pair (p, q) that (nearly) annihilates a_pq.  The angle is
+// computed in FP32 from the entries scaled by 1/scale (FP64 division and square
+// root are long dependent chains on GB300's FP64 pipe); c and s are then made
+// orthonormal in FP64 (two Newton steps for c = (1 + t^2)^(-1/2), s = t c), so
+// every rotation is exact to FP64 rounding while a_pq shrinks by ~1e-7 per
+// rotation (the next sweep removes the rest).
+__device__ inline void rot_params(double app, double aqq, double apq, double inv_scale, double& c, double& s_) {
+  const float fpp = (float)(app * inv_scale), fqq = (float)(aqq * inv_scale), fpq = (float)(apq * inv_scale);
+  const float ftau = (fqq - fpp) / (2.0f * fpq);
+  const float ft = copysignf(1.0f, ftau) / (fabsf(ftau) + sqrtf(1.0f + ftau * ftau));
+  const double t = (double)ft;
+  const double x = 1.0 + t * t;
+  double cc = (double)rsqrtf((float)x);
+  cc = cc * (1.5 - 0.5 * x * cc * cc);
+  cc = cc * (1.5 - 0.5 * x * cc * cc);
+  c = cc;
+  s_ = t * cc;
+}
+
 // ---------------------------------------------------------------------------
 // Two-sided cyclic Jacobi.  A rotation is applied to pair (p, q) when
 // |a_pq| > thr, thr = tol * max_i |a_ii| (absolute accuracy tol * ||H||).
@@ -39,55 +62,93 @@ __device__ inline void rr_pair(int jj, int r, int k, int& p, int& q) {
 // done per 2 x 2 block (pair k rows, pair l columns), so one round needs a
 // single barrier after the rotation parameters and one after the update.
 // ---------------------------------------------------------------------------
+// R = double: the FP64 solver (in place on H, S <- S J).  R = float: the bulk
+// pass of the mixed-precision solver -- H is read and left unchanged, and S
+// receives the FP32 rotation J alone (S_in is ignored), converted to FP64.
+template <typename R>
 __global__ void __launch_bounds__(SM_THREADS) k_jacobi_eig(int j, double* H, int ldh, double* S, int lds,
                                                            double* theta, double tol, int max_sweeps,
-                                                           int* sweeps_out) {
+                                                           int* sweeps_out, double tol_loose, int ntarget,
+                                                           int tmode, double tshift, int* rot_out) {
   extern __shared__ __align__(16) double dsm[];
-  double* A = dsm;                              // [SM_MAXJ * (SM_MAXJ + 1)]
-  double* Sm = A + SM_MAXJ * (SM_MAXJ + 1);     // [SM_MAXJ * (SM_MAXJ + 1)]
-  __shared__ double cs[SM_MAXJ / 2], sn[SM_MAXJ / 2], tt[SM_MAXJ / 2];
+  R* A = reinterpret_cast<R*>(dsm);                              // [SM_MAXJ * (SM_MAXJ + 1)]
+  R* Sm = A + SM_MAXJ * (SM_MAXJ + 1);     // [SM_MAXJ * (SM_MAXJ + 1)]
+  __shared__ R cs[SM_MAXJ / 2], sn[SM_MAXJ / 2], tt[SM_MAXJ / 2];
   __shared__ int pp[SM_MAXJ / 2], qq[SM_MAXJ / 2], rot[SM_MAXJ / 2];
-  __shared__ double scale_s;
+  __shared__ R scale_s;
+  constexpr bool F64 = sizeof(R) == 8;
   const int tid = threadIdx.x;
   const int LA = SM_MAXJ + 1;
   for (int e = tid; e < j * j; e += SM_THREADS) {
     const int r = e % j, c = e / j;
-    A[r + c * LA] = H[r + (size_t)c * ldh];
-    Sm[r + c * LA] = S[r + (size_t)c * lds];
+    A[r + c * LA] = (R)H[r + (size_t)c * ldh];
+    Sm[r + c * LA] = F64 ? (R)S[r + (size_t)c * lds] : (R)(r == c ? 1 : 0);
   }
   __syncthreads();
   if (tid < 32) {
-    double mx = 0.0;
+    R mx = 0;
     for (int i = tid; i < j; i += 32) mx = fmax(mx, fabs(A[i + i * LA]));
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (tid == 0) scale_s = mx;
   }
   __syncthreads();
-  double mxoff = 0.0;
+  R mxoff = 0;
   for (int e = tid; e < j * j; e += SM_THREADS) {
     const int r = e % j, c = e / j;
     if (r != c) mxoff = fmax(mxoff, fabs(A[r + c * LA]));
   }
   // the scale must cover an all-zero diagonal (e.g. the augmented matrix)
   for (int o = 16; o > 0; o >>= 1) mxoff = fmax(mxoff, __shfl_xor_sync(0xffffffffu, mxoff, o));
-  __shared__ double wmx[SM_THREADS / 32];
+  __shared__ R wmx[SM_THREADS / 32];
   if ((tid & 31) == 0) wmx[tid >> 5] = mxoff;
   __syncthreads();
   if (tid == 0) {
-    double m2 = 0.0;
+    R m2 = 0;
     for (int w = 0; w < SM_THREADS / 32; ++w) m2 = fmax(m2, wmx[w]);
     scale_s = fmax(scale_s, m2);
   }
   __syncthreads();
-  const double thr = tol * scale_s;
+  const R thr_t = (R)(tol * (double)scale_s);
+  const double inv_scale = (double)scale_s > 0.0 ? 1.0 / (double)scale_s : 1.0;                                  // pairs touching a target
+  // pairs not touching a target rotate when |a_pq| > tol_loose sqrt|a_pp a_qq|
+  // (relative, never below the absolute threshold); ntarget = 0: absolute everywhere
+  const R rel = (R)(ntarget > 0 ? tol_loose : 0.0);
   const int jj = j + (j & 1);
   const int np = jj / 2;
+  // targets: the ntarget smallest (tmode 0), largest (1) or closest to tshift
+  // (2) diagonal entries, re-ranked at the start of every sweep
+  __shared__ unsigned char is_t[SM_MAXJ];
+  auto need = [&](int p, int q, R apq) -> bool {
+    if (is_t[p] | is_t[q]) return fabs(apq) > thr_t;
+    if (rel == (R)0) return fabs(apq) > thr_t;
+    const float r2 = (float)rel * sqrtf(fabsf((float)A[p + p * LA] * (float)A[q + q * LA]));
+    return fabs(apq) > ((R)r2 > thr_t ? (R)r2 : thr_t);
+  };
   int sweep = 0;
+  int nrot = 0;
   for (; sweep < max_sweeps; ++sweep) {
+    if (tid < j) {
+      int r = 1;
+      if (ntarget > 0) {
+        auto key = [&](int t2) {
+          const double d = (double)A[t2 + t2 * LA];
+          return tmode == 0 ? d : (tmode == 1 ? -d : fabs(d - tshift));
+        };
+        const double ki = key(tid);
+        int rank = 0;
+        for (int t2 = 0; t2 < j; ++t2) {
+          const double kt = key(t2);
+          if (kt < ki || (kt == ki && t2 < tid)) ++rank;
+        }
+        r = rank < ntarget;
+      }
+      is_t[tid] = (unsigned char)r;
+    }
+    __syncthreads();
     int any = 0;
     for (int e = tid; e < j * j; e += SM_THREADS) {
       const int r = e % j, c = e / j;
-      if (r < c && fabs(A[r + c * LA]) > thr) any = 1;
+      if (r < c && need(r, c, A[r + c * LA])) any = 1;
     }
     if (!__syncthreads_or(any)) break;
     for (int round = 0; round < jj - 1; ++round) {
@@ -99,14 +160,20 @@ __global__ void __launch_bounds__(SM_THREADS) k_jacobi_eig(int j, double* H, int
         qq[tid] = q;
         int r = 0;
         if (q < j) {
-          const double apq = A[p + q * LA];
-          if (fabs(apq) > thr) {
-            const double tau = (A[q + q * LA] - A[p + p * LA]) / (2.0 * apq);
-            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            const double c = 1.0 / sqrt(1.0 + t * t);
-            cs[tid] = c;
-            sn[tid] = t * c;
-            tt[tid] = t;
+          const R apq = A[p + q * LA];
+          if (need(p, q, apq)) {
+            if constexpr (F64) {
+              double c, sv;
+              rot_params(A[p + p * LA], A[q + q * LA], apq, inv_scale, c, sv);
+              cs[tid] = c;
+              sn[tid] = sv;
+            } else {
+              const R tau = (A[q + q * LA] - A[p + p * LA]) / ((R)2 * apq);
+              const R t = (tau >= (R)0 ? (R)1 : (R)-1) / (fabs(tau) + sqrt((R)1 + tau * tau));
+              const R c = (R)1 / sqrt((R)1 + t * t);
+              cs[tid] = c;
+              sn[tid] = t * c;
+            }
             r = 1;
           }
         }
@@ -114,6 +181,11 @@ __global__ void __launch_bounds__(SM_THREADS) k_jacobi_eig(int j, double* H, int
         mine = r;
       }
       if (!__syncthreads_or(mine)) continue;
+      if (tid == 0) {
+        int cnt = 0;
+        for (int k2 = 0; k2 < np; ++k2) cnt += rot[k2];
+        nrot += cnt;
+      }
       // 2 x 2 blocks (k, l): rows of pair k, columns of pair l
       for (int it = tid; it < np * np; it += SM_THREADS) {
         const int k = it / np, l = it % np;
@@ -121,25 +193,30 @@ __global__ void __launch_bounds__(SM_THREADS) k_jacobi_eig(int j, double* H, int
         if (!rk && !rl) continue;
         const int pk = pp[k], qk = qq[k], pl = pp[l], ql = qq[l];
         if (k == l) {
-          if (qk < j) {
-            const double apq = A[pk + qk * LA];
-            A[pk + pk * LA] -= tt[k] * apq;
-            A[qk + qk * LA] += tt[k] * apq;
-            A[pk + qk * LA] = 0.0;
-            A[qk + pk * LA] = 0.0;
+          if (qk < j) {  // full 2 x 2 update J^T B J (the angle is not exact)
+            const R c = cs[k], sv = sn[k];
+            const R app = A[pk + pk * LA], aqq = A[qk + qk * LA], apq = A[pk + qk * LA];
+            const R r00 = c * app - sv * apq, r01 = c * apq - sv * aqq;
+            const R r10 = sv * app + c * apq, r11 = sv * apq + c * aqq;
+            const R n00 = c * r00 - sv * r01, n11 = sv * r10 + c * r11;
+            const R n01 = (sv * r00 + c * r01 + c * r10 - sv * r11) * (R)0.5;
+            A[pk + pk * LA] = n00;
+            A[qk + qk * LA] = n11;
+            A[pk + qk * LA] = n01;
+            A[qk + pk * LA] = n01;
           }
           continue;
         }
-        const double ck = rk ? cs[k] : 1.0, sk = rk ? sn[k] : 0.0;
-        const double cl = rl ? cs[l] : 1.0, sl = rl ? sn[l] : 0.0;
+        const R ck = rk ? cs[k] : (R)1, sk = rk ? sn[k] : (R)0;
+        const R cl = rl ? cs[l] : (R)1, sl = rl ? sn[l] : (R)0;
         const bool vqk = qk < j, vql = ql < j;
-        const double b00 = A[pk + pl * LA];
-        const double b01 = vql ? A[pk + ql * LA] : 0.0;
-        const double b10 = vqk ? A[qk + pl * LA] : 0.0;
-        const double b11 = (vqk && vql) ? A[qk + ql * LA] : 0.0;
+        const R b00 = A[pk + pl * LA];
+        const R b01 = vql ? A[pk + ql * LA] : (R)0;
+        const R b10 = vqk ? A[qk + pl * LA] : (R)0;
+        const R b11 = (vqk && vql) ? A[qk + ql * LA] : (R)0;
         // rows: [p';q'] = [c -s; s c] [p; q]
-        const double r00 = ck * b00 - sk * b10, r01 = ck * b01 - sk * b11;
-        const double r10 = sk * b00 + ck * b10, r11 = sk * b01 + ck * b11;
+        const R r00 = ck * b00 - sk * b10, r01 = ck * b01 - sk * b11;
+        const R r10 = sk * b00 + ck * b10, r11 = sk * b01 + ck * b11;
         // columns: [p' q'] = [p q] [c s; -s c]
         A[pk + pl * LA] = cl * r00 - sl * r01;
         if (vql) A[pk + ql * LA] = sl * r00 + cl * r01;
@@ -151,7 +228,7 @@ __global__ void __launch_bounds__(SM_THREADS) k_jacobi_eig(int j, double* H, int
         const int row = it / np, k = it % np;
         if (!rot[k]) continue;
         const int p = pp[k], q = qq[k];
-        const double sp = Sm[row + p * LA], sq = Sm[row + q * LA];
+        const R sp = Sm[row + p * LA], sq = Sm[row + q * LA];
         Sm[row + p * LA] = cs[k] * sp - sn[k] * sq;
         Sm[row + q * LA] = sn[k] * sp + cs[k] * sq;
       }
@@ -160,26 +237,239 @@ __global__ void __launch_bounds__(SM_THREADS) k_jacobi_eig(int j, double* H, int
   }
   for (int e = tid; e < j * j; e += SM_THREADS) {
     const int r = e % j, c = e / j;
-    H[r + (size_t)c * ldh] = A[r + c * LA];
-    S[r + (size_t)c * lds] = Sm[r + c * LA];
+    if (F64) H[r + (size_t)c * ldh] = (double)A[r + c * LA];
+    S[r + (size_t)c * lds] = (double)Sm[r + c * LA];
   }
-  for (int i = tid; i < j; i += SM_THREADS) theta[i] = A[i + i * LA];
-  if (tid == 0 && sweeps_out) *sweeps_out = sweep;
+  for (int i = tid; i < j; i += SM_THREADS) theta[i] = (double)A[i + i * LA];
+  if (tid == 0 && sweeps_out) sweeps_out[0] = sweep;
+  if (tid == 0 && rot_out) rot_out[0] = nrot;
 }
 
 void jacobi_eig_ld(cudaStream_t s, int j, double* H, int ldh, double* S, int lds, double* theta, double tol,
-                   int max_sweeps, int* sweeps_out) {
+                   int max_sweeps, int* sweeps_out, double tol_loose, int ntarget, int tmode, double tshift,
+                   int* rot_out) {
+  ProfScope ps(s, PROF_SMALL);
   const size_t smem = sizeof(double) * 2 * SM_MAXJ * (SM_MAXJ + 1);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_jacobi_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_jacobi_eig<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  k_jacobi_eig<<<1, SM_THREADS, smem, s>>>(j, H, ldh, S, lds, theta, tol, max_sweeps, sweeps_out);
+  k_jacobi_eig<double><<<1, SM_THREADS, smem, s>>>(j, H, ldh, S, lds, theta, tol, max_sweeps, sweeps_out,
+                                                    tol_loose, ntarget, tmode, tshift, rot_out); count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// The same FP64 cyclic Jacobi spread over a thread-block cluster of JC_CTAS
+// CTAs (one SM's FP64 pipe is the limit of the single-CTA kernel on GB300).
+// Every CTA holds a full copy of the frame matrix in its shared memory and
+// computes all rotation parameters of a round itself (the copies are
+// identical, so every CTA takes the same decisions); CTA c updates the 2 x 2
+// blocks whose column pair l has l % JC_CTAS == c and stores the results into
+// all copies through distributed shared memory; the rows of the accumulated
+// rotation S are split among the CTAs.  One cluster barrier per round (a
+// hardware barrier: no spin loop).
+// ---------------------------------------------------------------------------
+constexpr int JC_CTAS = 8;
+
+__global__ void __cluster_dims__(JC_CTAS, 1, 1) __launch_bounds__(SM_THREADS)
+    k_jacobi_eig_cluster(int j, double* H, int ldh, double* S, int lds, double* theta, double tol, int max_sweeps,
+                         int* sweeps_out, double tol_rel, int ntarget, int tmode, double tshift, int* rot_out) {
+  extern __shared__ __align__(16) double dsm[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int crank = (int)cl.block_rank();
+  double* A = dsm;                              // [SM_MAXJ * (SM_MAXJ + 1)]
+  double* Sm = A + SM_MAXJ * (SM_MAXJ + 1);     // rows r0..r1 used
+  __shared__ double cs[SM_MAXJ / 2], sn[SM_MAXJ / 2];
+  __shared__ int pp[SM_MAXJ / 2], qq[SM_MAXJ / 2], rot[SM_MAXJ / 2];
+  __shared__ unsigned char is_t[SM_MAXJ];
+  __shared__ double scale_s;
+  __shared__ double wmx[SM_THREADS / 32];
+  double* Ar[JC_CTAS];
+#pragma unroll
+  for (int r = 0; r < JC_CTAS; ++r) Ar[r] = cl.map_shared_rank(A, r);
+  const int tid = threadIdx.x;
+  const int LA = SM_MAXJ + 1;
+  const int rows_per = (j + JC_CTAS - 1) / JC_CTAS;
+  const int r0 = crank * rows_per, r1 = min(j, r0 + rows_per);
+  for (int e = tid; e < j * j; e += SM_THREADS) {
+    const int r = e % j, c = e / j;
+    A[r + c * LA] = H[r + (size_t)c * ldh];
+    if (r >= r0 && r < r1) Sm[r + c * LA] = S[r + (size_t)c * lds];
+  }
+  __syncthreads();
+  double mx = 0.0;
+  for (int e = tid; e < j * j; e += SM_THREADS) mx = fmax(mx, fabs(A[(e % j) + (e / j) * LA]));
+  mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 16));
+  mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 8));
+  mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 4));
+  mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+  mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+  if ((tid & 31) == 0) wmx[tid >> 5] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    double m2 = 0.0;
+    for (int w = 0; w < SM_THREADS / 32; ++w) m2 = fmax(m2, wmx[w]);
+    scale_s = m2;
+  }
+  cl.sync();  // every copy is loaded before any remote store
+  const double thr_t = tol * scale_s;
+  const double inv_scale = scale_s > 0.0 ? 1.0 / scale_s : 1.0;
+  const double rel = ntarget > 0 ? tol_rel : 0.0;
+  auto need = [&](int p, int q, double apq) -> bool {
+    if (is_t[p] | is_t[q]) return fabs(apq) > thr_t;
+    if (rel == 0.0) return fabs(apq) > thr_t;
+    const float r2 = (float)rel * sqrtf(fabsf((float)(A[p + p * LA] * inv_scale) * (float)(A[q + q * LA] * inv_scale)));
+    return fabs(apq) > fmax((double)r2 * scale_s, thr_t);
+  };
+  const int jj = j + (j & 1);
+  const int np = jj / 2;
+  int sweep = 0, nrot = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tid < j) {
+      int rr = 1;
+      if (ntarget > 0) {
+        auto key = [&](int t2) {
+          const double d = A[t2 + t2 * LA];
+          return tmode == 0 ? d : (tmode == 1 ? -d : fabs(d - tshift));
+        };
+        const double ki = key(tid);
+        int rank = 0;
+        for (int t2 = 0; t2 < j; ++t2) {
+          const double kt = key(t2);
+          if (kt < ki || (kt == ki && t2 < tid)) ++rank;
+        }
+        rr = rank < ntarget;
+      }
+      is_t[tid] = (unsigned char)rr;
+    }
+    __syncthreads();
+    int any = 0;
+    for (int e = tid; e < j * j; e += SM_THREADS) {
+      const int r = e % j, c = e / j;
+      if (r < c && need(r, c, A[r + c * LA])) any = 1;
+    }
+    if (!__syncthreads_or(any)) break;  // identical in every CTA
+    for (int round = 0; round < jj - 1; ++round) {
+      int mine = 0;
+      if (tid < np) {
+        int p, q;
+        rr_pair(jj, round, tid, p, q);
+        pp[tid] = p;
+        qq[tid] = q;
+        int rr = 0;
+        if (q < j) {
+          const double apq = A[p + q * LA];
+          if (need(p, q, apq)) {
+            double c, sv;
+            rot_params(A[p + p * LA], A[q + q * LA], apq, inv_scale, c, sv);
+            cs[tid] = c;
+            sn[tid] = sv;
+            rr = 1;
+          }
+        }
+        rot[tid] = rr;
+        mine = rr;
+      }
+      if (!__syncthreads_or(mine)) continue;  // identical in every CTA
+      if (crank == 0 && tid == 0) {
+        int cnt = 0;
+        for (int k2 = 0; k2 < np; ++k2) cnt += rot[k2];
+        nrot += cnt;
+      }
+      // this CTA's column pairs: l = crank, crank + JC_CTAS, ...
+      const int nl = (np - crank + JC_CTAS - 1) / JC_CTAS;
+      for (int it = tid; it < np * nl; it += SM_THREADS) {
+        const int k = it % np, l = crank + (it / np) * JC_CTAS;
+        const int rk = rot[k], rl = rot[l];
+        if (!rk && !rl) continue;
+        const int pk = pp[k], qk = qq[k], pl = pp[l], ql = qq[l];
+        if (k == l) {
+          if (qk < j) {  // full 2 x 2 update J^T B J (the angle is not exact)
+            const double c = cs[k], sv = sn[k];
+            const double app = A[pk + pk * LA], aqq = A[qk + qk * LA], apq = A[pk + qk * LA];
+            const double r00 = c * app - sv * apq, r01 = c * apq - sv * aqq;
+            const double r10 = sv * app + c * apq, r11 = sv * apq + c * aqq;
+            const double n00 = c * r00 - sv * r01, n11 = sv * r10 + c * r11;
+            const double n01 = (sv * r00 + c * r01 + c * r10 - sv * r11) * 0.5;
+#pragma unroll
+            for (int r = 0; r < JC_CTAS; ++r) {
+              Ar[r][pk + pk * LA] = n00;
+              Ar[r][qk + qk * LA] = n11;
+              Ar[r][pk + qk * LA] = n01;
+              Ar[r][qk + pk * LA] = n01;
+            }
+          }
+          continue;
+        }
+        const double ck = rk ? cs[k] : 1.0, sk = rk ? sn[k] : 0.0;
+        const double cl2 = rl ? cs[l] : 1.0, sl = rl ? sn[l] : 0.0;
+        const bool vqk = qk < j, vql = ql < j;
+        const double b00 = A[pk + pl * LA];
+        const double b01 = vql ? A[pk + ql * LA] : 0.0;
+        const double b10 = vqk ? A[qk + pl * LA] : 0.0;
+        const double b11 = (vqk && vql) ? A[qk + ql * LA] : 0.0;
+        const double r00 = ck * b00 - sk * b10, r01 = ck * b01 - sk * b11;
+        const double r10 = sk * b00 + ck * b10, r11 = sk * b01 + ck * b11;
+        const double n00 = cl2 * r00 - sl * r01, n01 = sl * r00 + cl2 * r01;
+        const double n10 = cl2 * r10 - sl * r11, n11 = sl * r10 + cl2 * r11;
+#pragma unroll
+        for (int r = 0; r < JC_CTAS; ++r) {
+          Ar[r][pk + pl * LA] = n00;
+          if (vql) Ar[r][pk + ql * LA] = n01;
+          if (vqk) Ar[r][qk + pl * LA] = n10;
+          if (vqk && vql) Ar[r][qk + ql * LA] = n11;
+        }
+      }
+      // the rows of S this CTA owns
+      for (int it = tid; it < (r1 - r0) * np; it += SM_THREADS) {
+        const int row = r0 + it / np, k = it % np;
+        if (!rot[k]) continue;
+        const int p = pp[k], q = qq[k];
+        const double sp = Sm[row + p * LA], sq = Sm[row + q * LA];
+        Sm[row + p * LA] = cs[k] * sp - sn[k] * sq;
+        Sm[row + q * LA] = sn[k] * sp + cs[k] * sq;
+      }
+      cl.sync();
+    }
+  }
+  for (int e = tid; e < j * j; e += SM_THREADS) {
+    const int r = e % j, c = e / j;
+    if (crank == 0) H[r + (size_t)c * ldh] = A[r + c * LA];
+    if (r >= r0 && r < r1) S[r + (size_t)c * lds] = Sm[r + c * LA];
+  }
+  if (crank == 0) {
+    for (int i = tid; i < j; i += SM_THREADS) theta[i] = A[i + i * LA];
+    if (tid == 0 && sweeps_out) sweeps_out[0] = sweep;
+    if (tid == 0 && rot_out) rot_out[0] = nrot;
+  }
+  cl.sync();  // no CTA leaves while another may still read its shared memory
+}
+
+void jacobi_eig_cluster_ld(cudaStream_t s, int j, double* H, int ldh, double* S, int lds, double* theta, double tol,
+                           int max_sweeps, int* sweeps_out, double tol_rel, int ntarget, int tmode, double tshift,
+                           int* rot_out) {
+  ProfScope ps(s, PROF_SMALL);
+  const size_t smem = sizeof(double) * 2 * SM_MAXJ * (SM_MAXJ + 1);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_jacobi_eig_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  k_jacobi_eig_cluster<<<JC_CTAS, SM_THREADS, smem, s>>>(j, H, ldh, S, lds, theta, tol, max_sweeps, sweeps_out,
+                                                          tol_rel, ntarget, tmode, tshift, rot_out); count_launch();
+}
+
+void jacobi_eig32_ld(cudaStream_t s, int j, const double* H, int ldh, double* Sf, int lds, double* theta, double tol,
+                     int max_sweeps, int* sweeps_out, int* rot_out) {
+  ProfScope ps(s, PROF_SMALL);
+  const size_t smem = sizeof(float) * 2 * SM_MAXJ * (SM_MAXJ + 1);
+  k_jacobi_eig<float><<<1, SM_THREADS, smem, s>>>(j, const_cast<double*>(H), ldh, Sf, lds, theta, tol, max_sweeps,
+                                                   sweeps_out, tol, 0, 0, 0.0, rot_out); count_launch();
 }
 void jacobi_eig(cudaStream_t s, int j, double* H, double* S, double* theta, double tol, int max_sweeps,
                 int* sweeps_out) {
-  jacobi_eig_ld(s, j, H, j, S, j, theta, tol, max_sweeps, sweeps_out);
+  jacobi_eig_ld(s, j, H, j, S, j, theta, tol, max_sweeps, sweeps_out, tol, 0, 0, 0.0, nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -277,13 +567,14 @@ __global__ void __launch_bounds__(SM_THREADS) k_jacobi_svd(int j, double* G, int
 
 void jacobi_svd_ld(cudaStream_t s, int j, double* G, int ldg, double* S, int lds, double* sig, double tol,
                    int max_sweeps, int* sweeps_out) {
+  ProfScope ps(s, PROF_SMALL);
   const size_t smem = sizeof(double) * 2 * SM_MAXJ * (SM_MAXJ + 1);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_jacobi_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  k_jacobi_svd<<<1, SM_THREADS, smem, s>>>(j, G, ldg, S, lds, sig, tol, max_sweeps, sweeps_out);
+  k_jacobi_svd<<<1, SM_THREADS, smem, s>>>(j, G, ldg, S, lds, sig, tol, max_sweeps, sweeps_out); count_launch();
 }
 void jacobi_svd(cudaStream_t s, int j, double* G, double* S, double* sig, double tol, int max_sweeps,
                 int* sweeps_out) {
@@ -333,7 +624,7 @@ __global__ void k_chol(int q, const double* __restrict__ P, const double* __rest
 }
 void chol_factor(cudaStream_t s, int q, const double* P, const double* in_norm2, double drop, double* M,
                  int* flags) {
-  k_chol<<<1, 32, 0, s>>>(q, P, in_norm2, drop, M, flags);
+  k_chol<<<1, 32, 0, s>>>(q, P, in_norm2, drop, M, flags); count_launch();
 }
 
 // ---------------------------------------------------------------------------
@@ -359,11 +650,11 @@ __global__ void k_gemm_nn(int r, int a, int c, const double* __restrict__ A, int
 }
 void small_gemm_tn(cudaStream_t s, int a, int r, int c, const double* A, int lda, const double* B, int ldb,
                    double* C, int ldc) {
-  if (r * c > 0) k_gemm_tn<<<ceil_div(r * c, 64), 64, 0, s>>>(a, r, c, A, lda, B, ldb, C, ldc);
+  if (r * c > 0) k_gemm_tn<<<ceil_div(r * c, 64), 64, 0, s>>>(a, r, c, A, lda, B, ldb, C, ldc); count_launch();
 }
 void small_gemm_nn(cudaStream_t s, int r, int a, int c, const double* A, int lda, const double* B, int ldb,
                    double* C, int ldc) {
-  if (r * c > 0) k_gemm_nn<<<ceil_div(r * c, 64), 64, 0, s>>>(r, a, c, A, lda, B, ldb, C, ldc);
+  if (r * c > 0) k_gemm_nn<<<ceil_div(r * c, 64), 64, 0, s>>>(r, a, c, A, lda, B, ldb, C, ldc); count_launch();
 }
 
 // ---------------------------------------------------------------------------
@@ -395,7 +686,7 @@ __global__ void k_frame_append(int j0, int nb, double* A, int lda, double* S, in
   }
 }
 void frame_append(cudaStream_t s, int j0, int nb, double* A, int lda, double* S, int lds, const double* Hn) {
-  k_frame_append<<<1, SM_THREADS, 0, s>>>(j0, nb, A, lda, S, lds, Hn);
+  k_frame_append<<<1, SM_THREADS, 0, s>>>(j0, nb, A, lda, S, lds, Hn); count_launch();
 }
 
 // Append nb new basis vectors to the projected matrix H (basis coordinates):
@@ -414,7 +705,7 @@ __global__ void k_h_append(int j0, int nb, double* H, int ldh, double* S, int ld
   }
 }
 void h_append(cudaStream_t s, int j0, int nb, double* H, int ldh, double* S, int lds, const double* Hn) {
-  k_h_append<<<1, SM_THREADS, 0, s>>>(j0, nb, H, ldh, S, lds, Hn);
+  k_h_append<<<1, SM_THREADS, 0, s>>>(j0, nb, H, ldh, S, lds, Hn); count_launch();
 }
 
 // F <- 1.5 I - 0.5 F (one Newton-Schulz step for the orthonormal polar factor:
@@ -425,7 +716,7 @@ __global__ void k_ns_factor(int j, double* F, int ldf) {
     F[r + (size_t)c * ldf] = (r == c ? 1.5 : 0.0) - 0.5 * F[r + (size_t)c * ldf];
   }
 }
-void ns_factor(cudaStream_t s, int j, double* F, int ldf) { k_ns_factor<<<ceil_div(j * j, 256), 256, 0, s>>>(j, F, ldf); }
+void ns_factor(cudaStream_t s, int j, double* F, int ldf) { k_ns_factor<<<ceil_div(j * j, 256), 256, 0, s>>>(j, F, ldf); count_launch(); }
 
 // A <- (A + A^T) / 2
 __global__ void k_symmetrise(int j, double* A, int lda) {
@@ -439,7 +730,7 @@ __global__ void k_symmetrise(int j, double* A, int lda) {
   }
 }
 void symmetrise(cudaStream_t s, int j, double* A, int lda) {
-  k_symmetrise<<<ceil_div(j * j, 256), 256, 0, s>>>(j, A, lda);
+  k_symmetrise<<<ceil_div(j * j, 256), 256, 0, s>>>(j, A, lda); count_launch();
 }
 
 // Sort order of theta (j <= 64): mode 0 ascending, 1 descending, 2 ascending |theta - shift|.
@@ -456,7 +747,7 @@ __global__ void k_order(int j, const double* __restrict__ th, int mode, double s
   order[rank] = i;
 }
 void order_theta(cudaStream_t s, int j, const double* th, int mode, double shift, int* order) {
-  k_order<<<1, SM_MAXJ, 0, s>>>(j, th, mode, shift, order);
+  k_order<<<1, SM_MAXJ, 0, s>>>(j, th, mode, shift, order); count_launch();
 }
 
 // out[:, c] = S[:, idx[c]] (j rows), th_out[c] = th[idx[c]]
@@ -470,7 +761,7 @@ __global__ void k_gather(int j, const double* __restrict__ S, int lds, const int
 }
 void gather_cols(cudaStream_t s, int j, const double* S, int lds, const int* idx, int nc, double* out, int ldo,
                  const double* th, double* th_out) {
-  k_gather<<<1, SM_THREADS, 0, s>>>(j, S, lds, idx, nc, out, ldo, th, th_out);
+  k_gather<<<1, SM_THREADS, 0, s>>>(j, S, lds, idx, nc, out, ldo, th, th_out); count_launch();
 }
 
 // ---------------------------------------------------------------------------
@@ -485,7 +776,7 @@ void gather_cols(cudaStream_t s, int j, const double* S, int lds, const int* idx
 __global__ void __launch_bounds__(SM_THREADS) k_transform(int j, const double* __restrict__ S, int lds,
                                                           const double* __restrict__ A, int lda,
                                                           const double* __restrict__ cand, int ldc, int nc,
-                                                          int nc_a, int lim_a,
+                                                          int nc_a, int lim_a, int a_orth,
                                                           const double* __restrict__ excl, int lde, int ne, int nmax,
                                                           double* __restrict__ Y, int ldy, int* jn_out,
                                                           double* __restrict__ A2, int lda2) {
@@ -494,46 +785,89 @@ __global__ void __launch_bounds__(SM_THREADS) k_transform(int j, const double* _
   double* Yh = Ys + SM_MAXJ * SM_MAXJ;       // S^T Y
   double* AY = Yh + SM_MAXJ * SM_MAXJ;       // A Yh
   __shared__ double v[SM_MAXJ];
-  __shared__ double red[SM_THREADS / 32];
+  __shared__ double h[2 * SM_MAXJ];
   __shared__ int nacc_s;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) nacc_s = 0;
+  // group A holds Ritz / singular coefficient vectors: when a_orth is set they
+  // are orthonormal up to rounding and are copied (up to lim_a of them);
+  // otherwise they go through the same Gram-Schmidt as group B
+  int c0 = 0;
+  if (a_orth) {
+    const int na = nc_a < lim_a ? nc_a : lim_a;
+    const int na2 = na < nmax ? na : nmax;
+    for (int e = tid; e < j * na2; e += SM_THREADS) {
+      const int r = e % j, c = e / j;
+      Ys[r + c * SM_MAXJ] = cand[r + (size_t)c * ldc];
+    }
+    if (tid == 0) nacc_s = na2;
+    c0 = nc_a;
+  } else if (tid == 0) {
+    nacc_s = 0;
+  }
   __syncthreads();
-  auto block_dot = [&](const double* x, const double* y) -> double {
-    double a = 0.0;
-    for (int r = tid; r < j; r += SM_THREADS) a = fma(x[r], y[r], a);
-    a = warp_sum(a);
-    if (lane == 0) red[warp] = a;
-    __syncthreads();
-    double t = 0.0;
-    for (int w = 0; w < SM_THREADS / 32; ++w) t += red[w];
-    __syncthreads();
-    return t;
-  };
-  for (int c = 0; c < nc; ++c) {
+  // classical Gram-Schmidt twice against [excl | accepted], one warp per inner
+  // product, then normalise; a candidate below 1e-8 of its input norm is dropped
+  for (int c = c0; c < nc; ++c) {
     const int nacc = nacc_s;
     if (nacc >= nmax) break;
     if (c < nc_a && nacc >= lim_a) continue;  // group A is full: go on with group B
     for (int r = tid; r < j; r += SM_THREADS) v[r] = cand[r + (size_t)c * ldc];
     __syncthreads();
-    const double n0 = sqrt(block_dot(v, v));
+    double n0 = 0.0;
+    for (int r = lane; r < j; r += 32) n0 = fma(v[r], v[r], n0);
+    n0 = warp_sum(n0);
+    const int nb = ne + nacc;
     for (int pass = 0; pass < 2; ++pass) {
-      for (int e = 0; e < ne; ++e) {
-        const double h = block_dot(excl + (size_t)e * lde, v);
-        for (int r = tid; r < j; r += SM_THREADS) v[r] -= h * excl[r + (size_t)e * lde];
-        __syncthreads();
+      for (int q = warp; q < nb; q += SM_THREADS / 32) {
+        const double* col = q < ne ? excl + (size_t)q * lde : Ys + (q - ne) * SM_MAXJ;
+        double d = 0.0;
+        for (int r = lane; r < j; r += 32) d = fma(col[r], v[r], d);
+        d = warp_sum(d);
+        if (lane == 0) h[q] = d;
       }
-      for (int e = 0; e < nacc; ++e) {
-        const double h = block_dot(Ys + e * SM_MAXJ, v);
-        for (int r = tid; r < j; r += SM_THREADS) v[r] -= h * Ys[r + e * SM_MAXJ];
-        __syncthreads();
+      __syncthreads();
+      for (int r = tid; r < j; r += SM_THREADS) {
+        double acc = v[r];
+        for (int q = 0; q < nb; ++q) {
+          const double* col = q < ne ? excl + (size_t)q * lde : Ys + (q - ne) * SM_MAXJ;
+          acc = fma(-h[q], col[r], acc);
+        }
+        v[r] = acc;
       }
+      __syncthreads();
     }
-    const double nv = sqrt(block_dot(v, v));
+    double nv = 0.0;
+    for (int r = lane; r < j; r += 32) nv = fma(v[r], v[r], nv);
+    nv = sqrt(warp_sum(nv));
+    n0 = sqrt(n0);
     if (nv > 1e-8 * (n0 > 1.0 ? 1.0 : n0) && nv > 0.0) {
       for (int r = tid; r < j; r += SM_THREADS) Ys[r + nacc * SM_MAXJ] = v[r] / nv;
       __syncthreads();
       if (tid == 0) nacc_s = nacc + 1;
+    }
+    __syncthreads();
+  }
+  // one Newton-Schulz step, Ys <- Ys (3I - Ys^T Ys)/2, removes what rounding
+  // left of the loss of orthogonality (so V Y stays orthonormal across restarts)
+  {
+    const int na = nacc_s;
+    double* Gm = Yh;   // scratch: Ys^T Ys, then the copy of Ys
+    for (int e = tid; e < na * na; e += SM_THREADS) {
+      const int a2 = e % na, c = e / na;
+      double d = 0.0;
+      for (int r = 0; r < j; ++r) d = fma(Ys[r + a2 * SM_MAXJ], Ys[r + c * SM_MAXJ], d);
+      AY[a2 + c * SM_MAXJ] = (a2 == c ? 1.5 : 0.0) - 0.5 * d;
+    }
+    for (int e = tid; e < j * na; e += SM_THREADS) {
+      const int r = e % j, c = e / j;
+      Gm[r + c * SM_MAXJ] = Ys[r + c * SM_MAXJ];
+    }
+    __syncthreads();
+    for (int e = tid; e < j * na; e += SM_THREADS) {
+      const int r = e % j, c = e / j;
+      double acc = 0.0;
+      for (int q = 0; q < na; ++q) acc = fma(Gm[r + q * SM_MAXJ], AY[q + c * SM_MAXJ], acc);
+      Ys[r + c * SM_MAXJ] = acc;
     }
     __syncthreads();
   }
@@ -562,15 +896,15 @@ __global__ void __launch_bounds__(SM_THREADS) k_transform(int j, const double* _
   }
   __syncthreads();
   for (int e = tid; e < jn * jn; e += SM_THREADS) {
-    const int a = e % jn, c = e / jn;
-    if (a > c) continue;
+    const int a2 = e % jn, c = e / jn;
+    if (a2 > c) continue;
     double acc = 0.0;
-    for (int r = 0; r < j; ++r) acc = fma(Yh[r + a * SM_MAXJ], AY[r + c * SM_MAXJ], acc);
+    for (int r = 0; r < j; ++r) acc = fma(Yh[r + a2 * SM_MAXJ], AY[r + c * SM_MAXJ], acc);
     double acc2 = 0.0;
-    for (int r = 0; r < j; ++r) acc2 = fma(Yh[r + c * SM_MAXJ], AY[r + a * SM_MAXJ], acc2);
+    for (int r = 0; r < j; ++r) acc2 = fma(Yh[r + c * SM_MAXJ], AY[r + a2 * SM_MAXJ], acc2);
     const double v2 = 0.5 * (acc + acc2);
-    A2[a + (size_t)c * lda2] = v2;
-    A2[c + (size_t)a * lda2] = v2;
+    A2[a2 + (size_t)c * lda2] = v2;
+    A2[c + (size_t)a2 * lda2] = v2;
   }
   for (int e = tid; e < j * jn; e += SM_THREADS) {
     const int r = e % j, c = e / j;
@@ -578,17 +912,18 @@ __global__ void __launch_bounds__(SM_THREADS) k_transform(int j, const double* _
   }
   if (tid == 0) *jn_out = jn;
 }
+
 void build_transform(cudaStream_t s, int j, const double* S, int lds, const double* A, int lda, const double* cand,
-                     int ldc, int nc, int nc_a, int lim_a, const double* excl, int lde, int ne, int nmax, double* Y,
-                     int ldy, int* jn_out, double* A2, int lda2) {
+                     int ldc, int nc, int nc_a, int lim_a, int a_orth, const double* excl, int lde, int ne, int nmax,
+                     double* Y, int ldy, int* jn_out, double* A2, int lda2) {
   const size_t smem = sizeof(double) * 3 * SM_MAXJ * SM_MAXJ;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_transform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
-  k_transform<<<1, SM_THREADS, smem, s>>>(j, S, lds, A, lda, cand, ldc, nc, nc_a, lim_a, excl, lde, ne, nmax, Y,
-                                          ldy, jn_out, A2, lda2);
+  k_transform<<<1, SM_THREADS, smem, s>>>(j, S, lds, A, lda, cand, ldc, nc, nc_a, lim_a, a_orth, excl, lde, ne,
+                                          nmax, Y, ldy, jn_out, A2, lda2); count_launch();
 }
 
 // QR column bookkeeping of the refined projection: R[0:c, c] = g1 + g2 (the
@@ -617,7 +952,7 @@ __global__ void k_qr_column(int c, const double* __restrict__ g1, const double* 
 }
 void qr_column(cudaStream_t s, int c, const double* g1, const double* g2, const double* tnorm2, double* R, int ldr,
                double* G, int ldg, double* SR, int ldsr, double* minv, int update_g) {
-  k_qr_column<<<1, SM_MAXJ, 0, s>>>(c, g1, g2, tnorm2, R, ldr, G, ldg, SR, ldsr, minv, update_g);
+  k_qr_column<<<1, SM_MAXJ, 0, s>>>(c, g1, g2, tnorm2, R, ldr, G, ldg, SR, ldsr, minv, update_g); count_launch();
 }
 
 // Final triplet of stage 2 from x = [v; u]: out[c] = (||v||^2, ||u||^2) is
@@ -631,7 +966,7 @@ __global__ void k_identity(int j, double* S, int lds) {
     S[r + (size_t)c * lds] = r == c ? 1.0 : 0.0;
   }
 }
-void set_identity(cudaStream_t s, int j, double* S, int lds) { k_identity<<<1, SM_THREADS, 0, s>>>(j, S, lds); }
+void set_identity(cudaStream_t s, int j, double* S, int lds) { k_identity<<<1, SM_THREADS, 0, s>>>(j, S, lds); count_launch(); }
 
 // Refined vector of stage 2: s1 = S_R[:, argmin sig] (basis coordinates), the
 // Rayleigh quotient theta1 = s1^T H s1 = (S^T s1)^T A (S^T s1), written to
@@ -677,7 +1012,7 @@ __global__ void k_refined(int j, const double* __restrict__ SR, int ldr, const d
 }
 void refined_vector(cudaStream_t s, int j, const double* SR, int ldr, const double* sig, const double* S, int lds,
                     const double* A, int lda, double* s1_out, double* out) {
-  k_refined<<<1, SM_MAXJ, 0, s>>>(j, SR, ldr, sig, S, lds, A, lda, s1_out, out);
+  k_refined<<<1, SM_MAXJ, 0, s>>>(j, SR, ldr, sig, S, lds, A, lda, s1_out, out); count_launch();
 }
 
 }  // namespace ph

@@ -81,10 +81,10 @@ static void rows_dispatch_L(cudaStream_t s, int L, int nrows, const int* rp, con
   const int blocks = ceil_div((int64_t)nrows * L, th);
   if (nrows <= 0) return;
   switch (L) {
-    case 1: k_csr_rows<T, B, 1><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Z); break;
-    case 2: k_csr_rows<T, B, 2><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Z); break;
-    case 4: k_csr_rows<T, B, 4><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Z); break;
-    default: k_csr_rows<T, B, 8><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Z); break;
+    case 1: k_csr_rows<T, B, 1><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Z); count_launch(); break;
+    case 2: k_csr_rows<T, B, 2><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Z); count_launch(); break;
+    case 4: k_csr_rows<T, B, 4><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Z); count_launch(); break;
+    default: k_csr_rows<T, B, 8><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Z); count_launch(); break;
   }
 }
 
@@ -95,10 +95,10 @@ static void fused_dispatch_L(cudaStream_t s, int L, int nrows, const int* rp, co
   const int blocks = ceil_div((int64_t)nrows * L, th);
   if (nrows <= 0) return;
   switch (L) {
-    case 1: k_ata_fused<T, B, 1><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Y); break;
-    case 2: k_ata_fused<T, B, 2><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Y); break;
-    case 4: k_ata_fused<T, B, 4><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Y); break;
-    default: k_ata_fused<T, B, 8><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Y); break;
+    case 1: k_ata_fused<T, B, 1><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Y); count_launch(); break;
+    case 2: k_ata_fused<T, B, 2><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Y); count_launch(); break;
+    case 4: k_ata_fused<T, B, 4><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Y); count_launch(); break;
+    default: k_ata_fused<T, B, 8><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Y); count_launch(); break;
   }
 }
 
@@ -111,6 +111,7 @@ int lanes_for(double avg_row) {
 
 template <typename T>
 void csr_spmm(cudaStream_t s, const SparseView<T>& A, int b, const T* X, T* Z) {
+  ProfScope ps(s, PROF_SPMV);
   const int L = lanes_for(A.avg_row());
   switch (b) {
     case 1: rows_dispatch_L<T, 1>(s, L, A.nrows, A.ptr, A.idx, A.val, X, Z); break;
@@ -123,6 +124,7 @@ void csr_spmm(cudaStream_t s, const SparseView<T>& A, int b, const T* X, T* Z) {
 
 template <typename T>
 void ata_fused(cudaStream_t s, const SparseView<T>& A, int ncols, int b, const T* X, T* Y) {
+  ProfScope ps(s, PROF_CSPMM);
   cudaMemsetAsync(Y, 0, sizeof(T) * (size_t)ncols * b, s);
   const int L = lanes_for(A.avg_row());
   switch (b) {
@@ -137,6 +139,7 @@ void ata_fused(cudaStream_t s, const SparseView<T>& A, int ncols, int b, const T
 template <typename T>
 void ata_two_phase(cudaStream_t s, const SparseView<T>& A, const SparseView<T>& At, int b, const T* X, T* Y,
                    T* Z) {
+  ProfScope ps(s, PROF_CSPMM);
   csr_spmm<T>(s, A, b, X, Z);
   csr_spmm<T>(s, At, b, Z, Y);
 }
@@ -232,11 +235,11 @@ template <typename T>
 void csr_to_csc(cudaStream_t s, int m, int n, int64_t nnz, const int* rp, const int* ci, const T* va, int* cp,
                 int* ri, T* cv, int* work_n) {
   cudaMemsetAsync(work_n, 0, sizeof(int) * (size_t)n, s);
-  if (nnz > 0) k_count_cols<<<ceil_div(nnz, 256) < 4096 ? ceil_div(nnz, 256) : 4096, 256, 0, s>>>(nnz, ci, work_n);
-  k_scan_one_cta<<<1, 1024, 0, s>>>(n, work_n, cp);
+  if (nnz > 0) k_count_cols<<<ceil_div(nnz, 256) < 4096 ? ceil_div(nnz, 256) : 4096, 256, 0, s>>>(nnz, ci, work_n); count_launch();
+  k_scan_one_cta<<<1, 1024, 0, s>>>(n, work_n, cp); count_launch();
   cudaMemsetAsync(work_n, 0, sizeof(int) * (size_t)n, s);
-  if (m > 0) k_scatter_csc<T><<<ceil_div(m, 256), 256, 0, s>>>(m, rp, ci, va, cp, work_n, ri, cv);
-  k_sort_cols<T><<<ceil_div(n, 256), 256, 0, s>>>(n, cp, ri, cv);
+  if (m > 0) k_scatter_csc<T><<<ceil_div(m, 256), 256, 0, s>>>(m, rp, ci, va, cp, work_n, ri, cv); count_launch();
+  k_sort_cols<T><<<ceil_div(n, 256), 256, 0, s>>>(n, cp, ri, cv); count_launch();
 }
 template void csr_to_csc<double>(cudaStream_t, int, int, int64_t, const int*, const int*, const double*, int*, int*,
                                  double*, int*);
@@ -247,7 +250,7 @@ __global__ void k_to_float(int64_t n, const double* __restrict__ a, float* __res
     b[i] = (float)a[i];
 }
 void to_float(cudaStream_t s, int64_t n, const double* a, float* b) {
-  if (n > 0) k_to_float<<<ceil_div(n, 256) < 8192 ? ceil_div(n, 256) : 8192, 256, 0, s>>>(n, a, b);
+  if (n > 0) k_to_float<<<ceil_div(n, 256) < 8192 ? ceil_div(n, 256) : 8192, 256, 0, s>>>(n, a, b); count_launch();
 }
 
 // diag(C)_j = sum_i a_ij^2 from the CSC copy (one thread per column).
@@ -259,7 +262,7 @@ __global__ void k_col_norms2(int n, const int* __restrict__ cp, const double* __
   d[c] = acc;
 }
 void col_norms2(cudaStream_t s, int n, const int* cp, const double* cv, double* d) {
-  if (n > 0) k_col_norms2<<<ceil_div(n, 256), 256, 0, s>>>(n, cp, cv, d);
+  if (n > 0) k_col_norms2<<<ceil_div(n, 256), 256, 0, s>>>(n, cp, cv, d); count_launch();
 }
 
 // Validation of a CSR given with int64 row offsets, in two steps so that no
@@ -298,10 +301,10 @@ __global__ void k_validate_rows(int m, int n, const int* __restrict__ rp, const 
   if (bad) atomicOr(flags, bad);
 }
 void rowptr_check(cudaStream_t s, int m, int64_t nnz, const int64_t* rp64, int* rp32, int* flags) {
-  k_rowptr_check<<<ceil_div((int64_t)m + 1, 256), 256, 0, s>>>(m, nnz, rp64, rp32, flags);
+  k_rowptr_check<<<ceil_div((int64_t)m + 1, 256), 256, 0, s>>>(m, nnz, rp64, rp32, flags); count_launch();
 }
 void validate_rows(cudaStream_t s, int m, int n, const int* rp, const int* ci, const double* va, int* flags) {
-  if (m > 0) k_validate_rows<<<ceil_div(m, 256), 256, 0, s>>>(m, n, rp, ci, va, flags);
+  if (m > 0) k_validate_rows<<<ceil_div(m, 256), 256, 0, s>>>(m, n, rp, ci, va, flags); count_launch();
 }
 
 }  // namespace ph

@@ -36,12 +36,12 @@ __device__ inline double atomic_add_f64(double* p, double v) { return atomicAdd(
 template <typename T, int Q>
 __global__ void __launch_bounds__(CG_THREADS) k_cgs_pass(int n, Basis<T> P, T* __restrict__ Tb, int ldt, int q,
                                                          const double* __restrict__ Gsub, double* __restrict__ Gout,
-                                                         double* __restrict__ Tout) {
+                                                         double* __restrict__ Tout, int rows) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int p = P.cols();
-  T* Ps = reinterpret_cast<T*>(smem_raw);                 // [p][CG_ROWS]
-  T* Ts = Ps + (size_t)p * CG_ROWS;                        // [Q][CG_ROWS]
-  T* Gs = Ts + (size_t)Q * CG_ROWS;                        // [p][Q] in T precision
+  T* Ps = reinterpret_cast<T*>(smem_raw);                 // [p][rows]
+  T* Ts = Ps + (size_t)p * rows;                           // [Q][rows]
+  T* Gs = Ts + (size_t)Q * rows;                           // [p][Q] in T precision
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // Gs[c + r*p] = Gsub[c + r*p] (column-major p x q), zero for r >= q
   if (Gsub)
@@ -55,11 +55,11 @@ __global__ void __launch_bounds__(CG_THREADS) k_cgs_pass(int n, Basis<T> P, T* _
 #pragma unroll
   for (int a = 0; a < (Q * (Q + 1) / 2 + 7) / 8; ++a) accT[a] = T(0);
   __syncthreads();
-  const int nchunks = (n + CG_ROWS - 1) / CG_ROWS;
+  const int nchunks = (n + rows - 1) / rows;
   for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-    const int row0 = ch * CG_ROWS;
+    const int row0 = ch * rows;
     const int i = row0 + tid;
-    const bool act = i < n;
+    const bool act = tid < rows && i < n;
     // ---- phase A
     T t[Q];
 #pragma unroll
@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(CG_THREADS) k_cgs_pass(int n, Basis<T> P, T* _
     for (int c = 0; c < p; ++c) {
       T pc = T(0);
       if (act) pc = c < P.c1 ? P.p1[(size_t)c * P.ld1 + i] : P.p2[(size_t)(c - P.c1) * P.ld2 + i];
-      Ps[(size_t)c * CG_ROWS + tid] = pc;
+      if (tid < rows) Ps[(size_t)c * rows + tid] = pc;
       if (Gsub) {
 #pragma unroll
         for (int r = 0; r < Q; ++r) t[r] = fma(-pc, Gs[c + r * p], t[r]);
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(CG_THREADS) k_cgs_pass(int n, Basis<T> P, T* _
     }
 #pragma unroll
     for (int r = 0; r < Q; ++r) {
-      Ts[r * CG_ROWS + tid] = t[r];
+      if (tid < rows) Ts[r * rows + tid] = t[r];
       if (Gsub && act && r < q) Tb[(size_t)r * ldt + i] = t[r];
     }
     __syncthreads();
@@ -85,10 +85,10 @@ __global__ void __launch_bounds__(CG_THREADS) k_cgs_pass(int n, Basis<T> P, T* _
       for (int a = 0; a < CG_PC; ++a) {
         const int c = warp + a * (CG_THREADS / 32);
         if (c < p) {
-          for (int rr = lane; rr < CG_ROWS; rr += 32) {
-            const T pv = Ps[(size_t)c * CG_ROWS + rr];
+          for (int rr = lane; rr < rows; rr += 32) {
+            const T pv = Ps[(size_t)c * rows + rr];
 #pragma unroll
-            for (int r = 0; r < Q; ++r) accG[a][r] = fma(pv, Ts[r * CG_ROWS + rr], accG[a][r]);
+            for (int r = 0; r < Q; ++r) accG[a][r] = fma(pv, Ts[r * rows + rr], accG[a][r]);
           }
         }
       }
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(CG_THREADS) k_cgs_pass(int n, Basis<T> P, T* _
         for (int s2 = r; s2 < Q; ++s2, ++k) {
           if (k % 8 == warp) {
             T acc = T(0);
-            for (int rr = lane; rr < CG_ROWS; rr += 32) acc = fma(Ts[r * CG_ROWS + rr], Ts[s2 * CG_ROWS + rr], acc);
+            for (int rr = lane; rr < rows; rr += 32) acc = fma(Ts[r * rows + rr], Ts[s2 * rows + rr], acc);
             accT[k / 8] += acc;
           }
         }
@@ -141,24 +141,29 @@ template <typename T, int Q>
 static void cgs_launch(cudaStream_t s, int n, const Basis<T>& P, T* Tb, int ldt, int q, const double* Gsub,
                        double* Gout, double* Tout) {
   const int p = P.cols();
-  const size_t smem = sizeof(T) * ((size_t)p * CG_ROWS + (size_t)Q * CG_ROWS + (size_t)p * Q);
+  // rows per chunk: 256 when the grid fills the GPU, fewer for short vectors
+  // (the FP64 work of a pass then spreads over more SMs)
+  int rows = CG_ROWS;
+  while (rows > 32 && (int64_t)ceil_div(n, rows) < 2LL * num_sms()) rows >>= 1;
+  const size_t smem = sizeof(T) * ((size_t)p * rows + (size_t)Q * rows + (size_t)p * Q);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_cgs_pass<T, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(sizeof(T) * ((size_t)CG_MAXP * CG_ROWS + 8 * CG_ROWS + CG_MAXP * 8)));
     attr = true;
   }
-  int grid = ceil_div(n, CG_ROWS);
+  int grid = ceil_div(n, rows);
   const int cap = num_sms() * (sizeof(T) == 8 ? 2 : 4);
   if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;
-  k_cgs_pass<T, Q><<<grid, CG_THREADS, smem, s>>>(n, P, Tb, ldt, q, Gsub, Gout, Tout);
+  k_cgs_pass<T, Q><<<grid, CG_THREADS, smem, s>>>(n, P, Tb, ldt, q, Gsub, Gout, Tout, rows); count_launch();
 }
 
 template <typename T>
 void cgs_pass(cudaStream_t s, int n, const Basis<T>& P, T* Tb, int ldt, int q, const double* Gsub, double* Gout,
               double* Tout) {
   if (n <= 0 || q <= 0) return;
+  ProfScope ps(s, PROF_GRAM);
   Basis<T> PP = P;
   if (PP.cols() == 0) { Gsub = nullptr; Gout = nullptr; }
   switch (q) {
@@ -181,25 +186,26 @@ __global__ void __launch_bounds__(TS_ROWS) k_tall_small(int n, const T* P, int l
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* nrm = reinterpret_cast<double*>(smem_raw);            // [r]
   T* Ys = reinterpret_cast<T*>(smem_raw + sizeof(double) * (size_t)r);  // [r][p]
-  T* Ps = Ys + (size_t)p * r;                                    // [p][TS_ROWS]
+  T* Ps = Ys + (size_t)p * r;                                    // [p][blockDim.x]
   const int tid = threadIdx.x;
-  for (int k = tid; k < p * r; k += TS_ROWS) {
+  for (int k = tid; k < p * r; k += blockDim.x) {
     const int c = k / p, a = k % p;
     Ys[(size_t)c * p + a] = (T)Y[a + (size_t)c * ldy];
   }
   if (norms2)
-    for (int c = tid; c < r; c += TS_ROWS) nrm[c] = 0.0;
+    for (int c = tid; c < r; c += blockDim.x) nrm[c] = 0.0;
   __syncthreads();
-  const int nchunks = (n + TS_ROWS - 1) / TS_ROWS;
+  const int R = blockDim.x;
+  const int nchunks = (n + R - 1) / R;
   for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-    const int i = ch * TS_ROWS + tid;
+    const int i = ch * R + tid;
     const bool act = i < n;
-    for (int a = 0; a < p; ++a) Ps[(size_t)a * TS_ROWS + tid] = act ? P[(size_t)a * ldp + i] : T(0);
+    for (int a = 0; a < p; ++a) Ps[(size_t)a * R + tid] = act ? P[(size_t)a * ldp + i] : T(0);
     __syncthreads();  // every row of the chunk is read before any (in-place) write
     for (int c = 0; c < r; ++c) {
       T acc = T(0);
       const T* yc = Ys + (size_t)c * p;
-      for (int a = 0; a < p; ++a) acc = fma(Ps[(size_t)a * TS_ROWS + tid], yc[a], acc);
+      for (int a = 0; a < p; ++a) acc = fma(Ps[(size_t)a * R + tid], yc[a], acc);
       if (theta && act) acc = fma((T)(-theta[c]), Xs[(size_t)c * ldx + i], acc);
       if (act) Out[(size_t)c * ldo + i] = acc;
       if (norms2) {
@@ -211,7 +217,7 @@ __global__ void __launch_bounds__(TS_ROWS) k_tall_small(int n, const T* P, int l
   }
   if (norms2) {
     __syncthreads();
-    for (int c = tid; c < r; c += TS_ROWS) atomicAdd(&norms2[c], nrm[c]);
+    for (int c = tid; c < r; c += blockDim.x) atomicAdd(&norms2[c], nrm[c]);
   }
 }
 
@@ -219,16 +225,19 @@ template <typename T>
 void tall_times_small(cudaStream_t s, int n, const T* P, int ldp, int p, const double* Y, int ldy, int r, T* Out,
                       int ldo, const T* Xs, int ldx, const double* theta, double* norms2) {
   if (n <= 0 || r <= 0) return;
-  const size_t smem = sizeof(double) * (size_t)r + sizeof(T) * ((size_t)p * r + (size_t)p * TS_ROWS);
+  ProfScope ps(s, PROF_TALL);
+  int R = TS_ROWS;
+  while (R > 32 && (int64_t)ceil_div(n, R) < 2LL * num_sms()) R >>= 1;
+  const size_t smem = sizeof(double) * (size_t)r + sizeof(T) * ((size_t)p * r + (size_t)p * R);
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_tall_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr = true;
   }
-  int grid = ceil_div(n, TS_ROWS);
+  int grid = ceil_div(n, R);
   const int cap = num_sms() * 8;
   if (grid > cap) grid = cap;
-  k_tall_small<T><<<grid, TS_ROWS, smem, s>>>(n, P, ldp, p, Y, ldy, r, Out, ldo, Xs, ldx, theta, norms2);
+  k_tall_small<T><<<grid, R, smem, s>>>(n, P, ldp, p, Y, ldy, r, Out, ldo, Xs, ldx, theta, norms2); count_launch();
 }
 
 // ---------------------------------------------------------------------------
@@ -255,7 +264,7 @@ __global__ void k_scale_block(int n, T* Tb, int ldt, int q, const double* __rest
 }
 template <typename T>
 void scale_block(cudaStream_t s, int n, T* Tb, int ldt, int q, const double* M, T* Dst, int ldd) {
-  if (n > 0 && q > 0) k_scale_block<T><<<ceil_div(n, 256), 256, 0, s>>>(n, Tb, ldt, q, M, Dst, ldd);
+  if (n > 0 && q > 0) k_scale_block<T><<<ceil_div(n, 256), 256, 0, s>>>(n, Tb, ldt, q, M, Dst, ldd); count_launch();
 }
 
 template <typename T>
@@ -271,10 +280,10 @@ __global__ void k_rm_to_cm(int n, const T* __restrict__ src, int q, T* __restric
   for (int r = 0; r < q; ++r) dst[(size_t)r * ldd + i] = src[(size_t)i * q + r];
 }
 template <typename T> void cm_to_rm(cudaStream_t s, int n, const T* src, int lds, int q, T* dst) {
-  if (n > 0 && q > 0) k_cm_to_rm<T><<<ceil_div(n, 256), 256, 0, s>>>(n, src, lds, q, dst);
+  if (n > 0 && q > 0) k_cm_to_rm<T><<<ceil_div(n, 256), 256, 0, s>>>(n, src, lds, q, dst); count_launch();
 }
 template <typename T> void rm_to_cm(cudaStream_t s, int n, const T* src, int q, T* dst, int ldd) {
-  if (n > 0 && q > 0) k_rm_to_cm<T><<<ceil_div(n, 256), 256, 0, s>>>(n, src, q, dst, ldd);
+  if (n > 0 && q > 0) k_rm_to_cm<T><<<ceil_div(n, 256), 256, 0, s>>>(n, src, q, dst, ldd); count_launch();
 }
 
 // ---------------------------------------------------------------------------
@@ -323,12 +332,12 @@ void jacobi_dots(cudaStream_t s, int n, const double* d, const T* X, int ldx, co
                  const double* theta, double guard, double* dots) {
   int grid = ceil_div(n, 256);
   if (grid > num_sms() * 4) grid = num_sms() * 4;
-  if (n > 0) k_jacobi_dots<T><<<grid, 256, 0, s>>>(n, d, X, ldx, R, ldr, q, theta, guard, dots);
+  if (n > 0) k_jacobi_dots<T><<<grid, 256, 0, s>>>(n, d, X, ldx, R, ldr, q, theta, guard, dots); count_launch();
 }
 template <typename T>
 void jacobi_apply(cudaStream_t s, int n, const double* d, const T* X, int ldx, const T* R, int ldr, int q,
                   const double* theta, double guard, const double* dots, T* Tout, int ldt) {
-  if (n > 0) k_jacobi_apply<T><<<ceil_div(n, 256), 256, 0, s>>>(n, d, X, ldx, R, ldr, q, theta, guard, dots, Tout, ldt);
+  if (n > 0) k_jacobi_apply<T><<<ceil_div(n, 256), 256, 0, s>>>(n, d, X, ldx, R, ldr, q, theta, guard, dots, Tout, ldt); count_launch();
 }
 
 template <typename T>
@@ -337,7 +346,7 @@ __global__ void k_fill_random(int n, T* dst, uint64_t seed, uint64_t stream) {
   if (i < n) dst[i] = (T)sm64_pm1(seed, stream, (uint64_t)i);
 }
 template <typename T> void fill_random(cudaStream_t s, int n, T* dst, uint64_t seed, uint64_t stream) {
-  if (n > 0) k_fill_random<T><<<ceil_div(n, 256), 256, 0, s>>>(n, dst, seed, stream);
+  if (n > 0) k_fill_random<T><<<ceil_div(n, 256), 256, 0, s>>>(n, dst, seed, stream); count_launch();
 }
 
 __global__ void k_f32_f64(int64_t n, const float* a, double* b) {
@@ -349,17 +358,17 @@ __global__ void k_f64_f32(int64_t n, const double* a, float* b) {
     b[i] = (float)a[i];
 }
 void convert_f32_to_f64(cudaStream_t s, int64_t n, const float* a, double* b) {
-  if (n > 0) k_f32_f64<<<ceil_div(n, 256) < 8192 ? ceil_div(n, 256) : 8192, 256, 0, s>>>(n, a, b);
+  if (n > 0) k_f32_f64<<<ceil_div(n, 256) < 8192 ? ceil_div(n, 256) : 8192, 256, 0, s>>>(n, a, b); count_launch();
 }
 void convert_f64_to_f32(cudaStream_t s, int64_t n, const double* a, float* b) {
-  if (n > 0) k_f64_f32<<<ceil_div(n, 256) < 8192 ? ceil_div(n, 256) : 8192, 256, 0, s>>>(n, a, b);
+  if (n > 0) k_f64_f32<<<ceil_div(n, 256) < 8192 ? ceil_div(n, 256) : 8192, 256, 0, s>>>(n, a, b); count_launch();
 }
 __global__ void k_axpby(int64_t n, double a, const double* x, double b, double* y) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = a * x[i] + b * y[i];
 }
 void axpby(cudaStream_t s, int64_t n, double a, const double* x, double b, double* y) {
-  if (n > 0) k_axpby<<<ceil_div(n, 256) < 8192 ? ceil_div(n, 256) : 8192, 256, 0, s>>>(n, a, x, b, y);
+  if (n > 0) k_axpby<<<ceil_div(n, 256) < 8192 ? ceil_div(n, 256) : 8192, 256, 0, s>>>(n, a, x, b, y); count_launch();
 }
 
 template <typename T>
@@ -379,7 +388,7 @@ __global__ void k_colnorms(int n, const T* __restrict__ X, int ldx, int q, doubl
 template <typename T> void col_norms2_dense(cudaStream_t s, int n, const T* X, int ldx, int q, double* norms2) {
   int grid = ceil_div(n, 256);
   if (grid > num_sms() * 4) grid = num_sms() * 4;
-  if (n > 0) k_colnorms<T><<<grid, 256, 0, s>>>(n, X, ldx, q, norms2);
+  if (n > 0) k_colnorms<T><<<grid, 256, 0, s>>>(n, X, ldx, q, norms2); count_launch();
 }
 
 // out[0] += x^T y (FP64)
@@ -393,7 +402,7 @@ __global__ void k_dot(int64_t n, const double* __restrict__ x, const double* __r
 void dot_accum(cudaStream_t s, int64_t n, const double* x, const double* y, double* out) {
   int grid = ceil_div(n, 256);
   if (grid > num_sms() * 4) grid = num_sms() * 4;
-  if (n > 0) k_dot<<<grid, 256, 0, s>>>(n, x, y, out);
+  if (n > 0) k_dot<<<grid, 256, 0, s>>>(n, x, y, out); count_launch();
 }
 // x *= a (a read from device memory when ap != nullptr)
 __global__ void k_scal(int64_t n, double a, const double* ap, double* x) {
@@ -402,7 +411,7 @@ __global__ void k_scal(int64_t n, double a, const double* ap, double* x) {
     x[i] *= f;
 }
 void scal(cudaStream_t s, int64_t n, double a, const double* ap, double* x) {
-  if (n > 0) k_scal<<<ceil_div(n, 256) < 8192 ? ceil_div(n, 256) : 8192, 256, 0, s>>>(n, a, ap, x);
+  if (n > 0) k_scal<<<ceil_div(n, 256) < 8192 ? ceil_div(n, 256) : 8192, 256, 0, s>>>(n, a, ap, x); count_launch();
 }
 // x[i] = v (constant fill)
 template <typename T>
@@ -411,7 +420,7 @@ __global__ void k_fill(int64_t n, T v, T* x) {
     x[i] = v;
 }
 template <typename T> void fill_const(cudaStream_t s, int64_t n, T v, T* x) {
-  if (n > 0) k_fill<T><<<ceil_div(n, 256) < 8192 ? ceil_div(n, 256) : 8192, 256, 0, s>>>(n, v, x);
+  if (n > 0) k_fill<T><<<ceil_div(n, 256) < 8192 ? ceil_div(n, 256) : 8192, 256, 0, s>>>(n, v, x); count_launch();
 }
 template void fill_const<double>(cudaStream_t, int64_t, double, double*);
 template void fill_const<float>(cudaStream_t, int64_t, float, float*);

@@ -19,6 +19,19 @@ struct SparseView {
 
 int lanes_for(double avg_row);
 
+// Instrumentation (per host thread): kernel launch count, and optional CUDA
+// events around kernel classes when a solve runs with opts.profile = 1.
+enum ProfCat { PROF_CSPMM = 0, PROF_GRAM = 1, PROF_TALL = 2, PROF_SMALL = 3, PROF_SPMV = 4, PROF_NCAT = 5 };
+void count_launch();
+void prof_begin(cudaStream_t s, int cat);
+void prof_end(cudaStream_t s, int cat);
+struct ProfScope {
+  cudaStream_t s;
+  int cat;
+  ProfScope(cudaStream_t st, int c) : s(st), cat(c) { prof_begin(s, cat); }
+  ~ProfScope() { prof_end(s, cat); }
+};
+
 // ---- sparse (k_sparse.cu)
 template <typename T> void csr_spmm(cudaStream_t s, const SparseView<T>& A, int b, const T* X, T* Z);
 template <typename T> void ata_fused(cudaStream_t s, const SparseView<T>& A, int ncols, int b, const T* X, T* Y);
@@ -108,8 +121,23 @@ void small_gemm_tn(cudaStream_t s, int a, int r, int c, const double* A, int lda
                    double* C, int ldc);
 void small_gemm_nn(cudaStream_t s, int r, int a, int c, const double* A, int lda, const double* B, int ldb,
                    double* C, int ldc);
+// tol (times max |a_ij|) is the threshold of pairs touching one of the
+// ntarget targets (smallest diagonal entries for tmode 0, largest for 1,
+// closest to tshift for 2); the other pairs rotate when
+// |a_pq| > tol_loose sqrt|a_pp a_qq| (relative); ntarget = 0 applies tol
+// everywhere.  *sweeps_out = sweeps,
+// *rot_out = rotations (either may be null).
 void jacobi_eig_ld(cudaStream_t s, int j, double* H, int ldh, double* S, int lds, double* theta, double tol,
-                   int max_sweeps, int* sweeps_out);
+                   int max_sweeps, int* sweeps_out, double tol_loose, int ntarget, int tmode, double tshift,
+                   int* rot_out);
+// Same as jacobi_eig_ld (FP64), spread over an 8-CTA thread-block cluster.
+void jacobi_eig_cluster_ld(cudaStream_t s, int j, double* H, int ldh, double* S, int lds, double* theta, double tol,
+                           int max_sweeps, int* sweeps_out, double tol_rel, int ntarget, int tmode, double tshift,
+                           int* rot_out);
+// FP32 bulk pass: Sf (FP64 out) = the FP32 Jacobi rotation diagonalising H to
+// ~tol * ||H||; H is not modified.
+void jacobi_eig32_ld(cudaStream_t s, int j, const double* H, int ldh, double* Sf, int lds, double* theta, double tol,
+                     int max_sweeps, int* sweeps_out, int* rot_out);
 void jacobi_svd_ld(cudaStream_t s, int j, double* G, int ldg, double* S, int lds, double* sig, double tol,
                    int max_sweeps, int* sweeps_out);
 void frame_append(cudaStream_t s, int j0, int nb, double* A, int lda, double* S, int lds, const double* Hn);
@@ -117,8 +145,8 @@ void order_theta(cudaStream_t s, int j, const double* th, int mode, double shift
 void gather_cols(cudaStream_t s, int j, const double* S, int lds, const int* idx, int nc, double* out, int ldo,
                  const double* th, double* th_out);
 void build_transform(cudaStream_t s, int j, const double* S, int lds, const double* A, int lda, const double* cand,
-                     int ldc, int nc, int nc_a, int lim_a, const double* excl, int lde, int ne, int nmax, double* Y,
-                     int ldy, int* jn_out, double* A2, int lda2);
+                     int ldc, int nc, int nc_a, int lim_a, int a_orth, const double* excl, int lde, int ne, int nmax,
+                     double* Y, int ldy, int* jn_out, double* A2, int lda2);
 void set_identity(cudaStream_t s, int j, double* S, int lds);
 void h_append(cudaStream_t s, int j0, int nb, double* H, int ldh, double* S, int lds, const double* Hn);
 void ns_factor(cudaStream_t s, int j, double* F, int ldf);

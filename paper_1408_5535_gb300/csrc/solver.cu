@@ -23,7 +23,10 @@ constexpr int LD = 64;                    // leading dimension of the small matr
 constexpr double EPS64 = 2.220446049250313e-16;
 constexpr double EPS32 = 1.1920928955078125e-07;
 constexpr uint64_t RS_INIT = 0x1000, RS_BREAK = 0x2000, RS_U = 0x3000;
-constexpr double JAC_TOL = 1e-17;         // absolute Jacobi threshold relative to ||H||
+constexpr double JAC_TOL = 5e-17;         // Jacobi threshold for pairs touching a target, relative to ||H||
+constexpr double TOL_MARGIN = 0.9;        // stopping tests use 0.9 delta: the residual the test sees and an
+                                          // independent recomputation differ by rounding of order eps ||C||
+constexpr double JAC_REL = 1e-8;          // relative threshold of the other pairs (they span the restart space)
 
 struct PhError {
   phsvds_status st;
@@ -76,6 +79,54 @@ struct Host {
   explicit Host(phsvds_ctx* cc) : c(cc), base(cc->host), bytes(cc->host_bytes) {}
   template <typename T> T* at(size_t off_bytes) { return reinterpret_cast<T*>(base + off_bytes); }
 };
+
+// ---- instrumentation (per host thread)
+static thread_local int64_t g_launch_count = 0;
+void count_launch() { ++g_launch_count; }
+
+struct Profiler {
+  bool on = false;
+  int depth[PROF_NCAT] = {0, 0, 0, 0, 0};
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> evcat;
+  size_t used = 0;
+  void start(size_t cap) {
+    on = true;
+    for (int c = 0; c < PROF_NCAT; ++c) depth[c] = 0;
+    while (ev.size() < cap) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) break;
+      ev.push_back(e);
+    }
+    evcat.assign(ev.size(), 0);
+    used = 0;
+  }
+  void mark(cudaStream_t s, int cat, bool begin) {
+    if (!on) return;
+    if (begin && depth[cat]++ > 0) return;
+    if (!begin && --depth[cat] > 0) return;
+    if (used >= ev.size()) return;
+    if (!begin && (used & 1) == 0) return;  // unmatched end
+    if (begin && (used & 1) == 1) return;   // another class is open: skip nested
+    cudaEventRecord(ev[used], s);
+    evcat[used] = cat;
+    ++used;
+  }
+  void finish(double* ms, int64_t* cnt) {
+    on = false;
+    for (size_t i = 0; i + 1 < used; i += 2) {
+      float t = 0.f;
+      if (cudaEventSynchronize(ev[i + 1]) == cudaSuccess && cudaEventElapsedTime(&t, ev[i], ev[i + 1]) == cudaSuccess) {
+        ms[evcat[i]] += t;
+        cnt[evcat[i]] += 1;
+      }
+    }
+    used = 0;
+  }
+};
+static thread_local Profiler g_prof;
+void prof_begin(cudaStream_t s, int cat) { g_prof.mark(s, cat, true); }
+void prof_end(cudaStream_t s, int cat) { g_prof.mark(s, cat, false); }
 
 static bool trace_on() {
   static int t = -1;
@@ -163,7 +214,9 @@ template <typename T> struct COp {
   T* Z;
   int n;
   int schedule;  // 1 fused atomic, 2 two-phase
+  mutable int64_t calls = 0;
   void apply(cudaStream_t s, int b, const T* X, T* Y) const {
+    ++calls;
     if (schedule == 1)
       ata_fused<T>(s, *A, n, b, X, Y);
     else
@@ -204,26 +257,55 @@ static int autotune_spmm(cudaStream_t s, Pool& pool, const SparseView<T>& A, con
 
 static inline int spmm_width(int nb) { return nb >= 8 ? 8 : nb >= 4 ? 4 : nb >= 2 ? 2 : 1; }
 
-// Jacobi frame of the projected problem, rebuilt each outer iteration from the
-// exact projected matrix Ht (basis coordinates): S <- S (3I - S^T S)/2 (one
-// Newton-Schulz step keeps the accumulated rotation orthonormal), then
-// Aw = S^T Ht S.  The warm-started Jacobi then only rotates what the new basis
-// vectors disturbed.  With S = I the frame is Ht itself.
+// Jacobi frame of the projected problem, rebuilt from the exact projected
+// matrix Ht (basis coordinates): ns_steps Newton-Schulz steps
+// S <- S (3I - S^T S)/2 keep the accumulated rotation orthonormal (each step
+// squares its loss of orthogonality), then Aw = S^T Ht S.  With ns_steps < 0
+// the rotation is the identity and the frame is Ht itself.
 static void frame_from_true(cudaStream_t s, int j, const double* Ht, double* S, double* Aw, double* w1, double* w2,
-                            bool ident) {
-  if (ident) {
+                            int ns_steps) {
+  if (ns_steps < 0) {
     CUCHK(cudaMemcpy2DAsync(Aw, LD * sizeof(double), Ht, LD * sizeof(double), j * sizeof(double), j,
                             cudaMemcpyDeviceToDevice, s));
     return;
   }
-  small_gemm_tn(s, j, j, j, S, LD, S, LD, w1, LD);
-  ns_factor(s, j, w1, LD);
-  small_gemm_nn(s, j, j, j, S, LD, w1, LD, w2, LD);
-  CUCHK(cudaMemcpy2DAsync(S, LD * sizeof(double), w2, LD * sizeof(double), j * sizeof(double), j,
-                          cudaMemcpyDeviceToDevice, s));
+  for (int it = 0; it < ns_steps; ++it) {
+    small_gemm_tn(s, j, j, j, S, LD, S, LD, w1, LD);
+    ns_factor(s, j, w1, LD);
+    small_gemm_nn(s, j, j, j, S, LD, w1, LD, w2, LD);
+    CUCHK(cudaMemcpy2DAsync(S, LD * sizeof(double), w2, LD * sizeof(double), j * sizeof(double), j,
+                            cudaMemcpyDeviceToDevice, s));
+  }
   small_gemm_nn(s, j, j, j, Ht, LD, S, LD, w1, LD);
   small_gemm_tn(s, j, j, j, S, LD, w1, LD, Aw, LD);
   symmetrise(s, j, Aw, LD);
+}
+
+// Mixed-precision Rayleigh-Ritz eigensolve on GB300 (one SM's FP64 pipe is
+// ~60x slower than its FP32 pipe): an FP32 cyclic Jacobi pass does the large
+// rotations of the warm frame, S <- S Sf is re-orthonormalised and the exact
+// FP64 frame S^T Ht S rebuilt, and (when fp64_cleanup) an FP64 Jacobi pass,
+// tight only on pairs touching the targets, brings the targeted Ritz pairs to
+// FP64 accuracy.  theta = diagonal of the final frame, S = its rotation.
+static void eig_mixed(cudaStream_t s, int j, const double* Ht, double* S, double* Aw, double* Sf, double* theta,
+                      double* w1, double* w2, bool s_ident, bool fp64_cleanup, int ntarget, int tmode, double tshift,
+                      int* counters) {
+  frame_from_true(s, j, Ht, S, Aw, w1, w2, s_ident ? -1 : 0);
+  jacobi_eig32_ld(s, j, Aw, LD, Sf, LD, theta, 1e-6, 30, counters, counters + 1);
+  if (s_ident) {
+    CUCHK(cudaMemcpy2DAsync(S, LD * sizeof(double), Sf, LD * sizeof(double), j * sizeof(double), j,
+                            cudaMemcpyDeviceToDevice, s));
+  } else {
+    small_gemm_nn(s, j, j, j, S, LD, Sf, LD, w2, LD);
+    CUCHK(cudaMemcpy2DAsync(S, LD * sizeof(double), w2, LD * sizeof(double), j * sizeof(double), j,
+                            cudaMemcpyDeviceToDevice, s));
+  }
+  frame_from_true(s, j, Ht, S, Aw, w1, w2, fp64_cleanup ? 2 : 1);
+  if (fp64_cleanup)
+    jacobi_eig_ld(s, j, Aw, LD, S, LD, theta, JAC_TOL, 60, counters + 2, JAC_REL, ntarget, tmode, tshift,
+                  counters + 3);
+  else
+    jacobi_eig32_ld(s, j, Aw, LD, Sf, LD, theta, 1e-6, 0, nullptr, nullptr);  // theta = diag of the rebuilt frame
 }
 
 // Ht = V^T W recomputed from the tall basis after a transform (j x j, FP64
@@ -257,6 +339,7 @@ struct Stage1Out {
   std::vector<double> lam;   // k eigenvalues of C (target order)
   double theta_max = 0.0;
   int64_t iters = 0, restarts = 0, mv = 0;
+  int64_t jac_sweeps = 0, jac_rot = 0;
 };
 
 template <typename T>
@@ -276,8 +359,8 @@ struct Stage1 {
   std::chrono::steady_clock::time_point t0;
   // device
   T *V, *W, *Xl, *Tb, *Xrm, *Yrm, *Xr, *Rr, *XU;
-  double *Aw, *S, *Ht, *w1, *w2, *theta, *Hn, *G1, *G2, *P1, *P2, *M1, *M2, *innorm, *norms, *Scols, *thcols, *Yt,
-      *A2, *cand, *excl, *sprev, *dots, *thU;
+  double *Aw, *S, *Ht, *w1, *w2, *Sf, *theta, *Hn, *G1, *G2, *P1, *P2, *M1, *M2, *innorm, *norms, *Scols, *thcols,
+      *Yt, *A2, *cand, *excl, *sprev, *dots, *thU;
   int *order, *flags, *jn, *idx;
   // host state
   int j = 0, nlock = 0, nsp = 0, rand_ctr = 0;
@@ -311,6 +394,7 @@ struct Stage1 {
     Ht = pool.get<double>(LD * LD);
     w1 = pool.get<double>(LD * LD);
     w2 = pool.get<double>(LD * LD);
+    Sf = pool.get<double>(LD * LD);
     theta = pool.get<double>(LD);
     Hn = pool.get<double>(LD * 8);
     G1 = pool.get<double>(LD * 8 + LD);
@@ -331,7 +415,7 @@ struct Stage1 {
     dots = pool.get<double>(16);
     thU = pool.get<double>(8);
     order = pool.get<int>(LD);
-    flags = pool.get<int>(32);
+    flags = pool.get<int>(48);
     jn = pool.get<int>(4);
     idx = pool.get<int>(2 * LD);
     zero(s, sprev, LD * 8);
@@ -440,9 +524,10 @@ struct Stage1 {
     while (true) {
       check_time();
       if (nb > 0) expand(nb);
-      frame_from_true(s, j, Ht, S, Aw, w1, w2, s_ident);
+      frame_from_true(s, j, Ht, S, Aw, w1, w2, s_ident ? -1 : 1);
       s_ident = false;
-      jacobi_eig_ld(s, j, Aw, LD, S, LD, theta, JAC_TOL, 60, flags + 12);
+      jacobi_eig_cluster_ld(s, j, Aw, LD, S, LD, theta, JAC_TOL, 60, flags + 12, JAC_REL,
+                            std::min(b, k - nlock) + 1, largest ? 1 : 0, 0.0, flags + 13);
       order_theta(s, j, theta, largest ? 1 : 0, 0.0, order);
       const int nt = std::min(std::min(b, k - nlock), j);
       gather_cols(s, j, S, LD, order, nt, Scols, LD, theta, thcols);
@@ -455,8 +540,11 @@ struct Stage1 {
       CUCHK(cudaMemcpyAsync(hth, theta, sizeof(double) * j, cudaMemcpyDeviceToHost, s));
       CUCHK(cudaMemcpyAsync(hord, order, sizeof(int) * j, cudaMemcpyDeviceToHost, s));
       CUCHK(cudaMemcpyAsync(hn, norms, sizeof(double) * nt, cudaMemcpyDeviceToHost, s));
+      CUCHK(cudaMemcpyAsync(h.at<int>(960), flags + 12, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
       sync(s);
       out.iters++;
+      out.jac_sweeps += *h.at<int>(960);
+      out.jac_rot += *h.at<int>(964);
       for (int i = 0; i < j; ++i) {
         ord[i] = hord[i];
         thv[i] = hth[hord[i]];
@@ -527,7 +615,7 @@ struct Stage1 {
         }
         const int ne = (int)conv.size();
         if (ne) gather_cols(s, j, S, LD, idx + LD, ne, excl, LD, nullptr, nullptr);
-        build_transform(s, j, S, LD, Aw, LD, cand, LD, nc, nkeep, lim_a, excl, LD, ne, nmax, Yt, LD, jn, nullptr,
+        build_transform(s, j, S, LD, Aw, LD, cand, LD, nc, nkeep, lim_a, 1, excl, LD, ne, nmax, Yt, LD, jn, nullptr,
                         LD);
         int jnew = nkeep;
         if (restart) {
@@ -677,7 +765,7 @@ static std::vector<double> rayleigh_ritz_post(phsvds_ctx* ctx, Pool& pool, DevA&
   CUCHK(cudaMemcpy2DAsync(Hq, q * sizeof(double), H, LD * sizeof(double), q * sizeof(double), q,
                           cudaMemcpyDeviceToDevice, s));
   frame_append(s, 0, q, Sc, LD, S, LD, Hq);
-  jacobi_eig_ld(s, q, Sc, LD, S, LD, th, JAC_TOL, 60, sw);
+  jacobi_eig_cluster_ld(s, q, Sc, LD, S, LD, th, JAC_TOL, 60, sw, JAC_TOL, 0, 0, 0.0, nullptr);
   order_theta(s, q, th, largest ? 1 : 0, 0.0, ord);
   double* Sk = pool.get<double>(LD * LD);
   double* thk = pool.get<double>(LD);
@@ -704,8 +792,8 @@ struct Stage2 {
   double time_limit_s;
   std::chrono::steady_clock::time_point t0;
   double *V, *W, *Q, *Xl, *x0, *tv, *xr, *rr;
-  double *Aw, *S, *Ht, *w1, *w2, *theta, *R, *G, *SR, *sig, *s1, *rq, *Hn, *Hfull, *Yt, *A2, *cand, *excl, *sprev,
-      *nrm, *G1, *G2, *tn2, *minv, *thl;
+  double *Aw, *S, *Ht, *w1, *w2, *Sf, *theta, *R, *G, *SR, *sig, *s1, *rq, *Hn, *Hfull, *Yt, *A2, *cand, *excl,
+      *sprev, *nrm, *G1, *G2, *tn2, *minv, *thl;
   bool s_ident = true, sr_ident = true;
   int *order, *sw, *jn, *idx_lock;
   Orth1 orth;
@@ -731,6 +819,7 @@ struct Stage2 {
     Ht = pool.get<double>(LD * LD);
     w1 = pool.get<double>(LD * LD);
     w2 = pool.get<double>(LD * LD);
+    Sf = pool.get<double>(LD * LD);
     theta = pool.get<double>(LD);
     R = pool.get<double>(LD * LD);
     G = pool.get<double>(LD * LD);
@@ -752,7 +841,7 @@ struct Stage2 {
     minv = pool.get<double>(4);
     thl = pool.get<double>(LD);
     order = pool.get<int>(LD);
-    sw = pool.get<int>(4);
+    sw = pool.get<int>(16);
     jn = pool.get<int>(4);
     idx_lock = pool.get<int>(LD);
   }
@@ -878,9 +967,8 @@ struct Stage2 {
         full_qr(shift);
         qr_full = false;
       }
-      frame_from_true(s, j, Ht, S, Aw, w1, w2, s_ident);
+      eig_mixed(s, j, Ht, S, Aw, Sf, theta, w1, w2, s_ident, false, 1, 2, shift, sw + 2);
       s_ident = false;
-      jacobi_eig_ld(s, j, Aw, LD, S, LD, theta, JAC_TOL, 60, sw);
       order_theta(s, j, theta, 2, shift, order);
       svd_frame();
       sr_ident = false;
@@ -921,7 +1009,7 @@ struct Stage2 {
           int* idx = idx_lock;
           CUCHK(cudaMemcpyAsync(idx, hi, sizeof(int) * nc, cudaMemcpyHostToDevice, s));
           gather_cols(s, j, SR, LD, idx, nc, cand, LD, nullptr, nullptr);
-          build_transform(s, j, S, LD, Aw, LD, cand, LD, nc, nc, nc, excl, LD, 0, nc, Yt, LD, jn, nullptr, LD);
+          build_transform(s, j, S, LD, Aw, LD, cand, LD, nc, nc, nc, 1, excl, LD, 0, nc, Yt, LD, jn, nullptr, LD);
           transform(nc);
         }
         CUCHK(cudaMemcpyAsync(tv, x0 + (size_t)target * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
@@ -942,7 +1030,7 @@ struct Stage2 {
           CUCHK(cudaMemcpyAsync(cand + (size_t)nc * LD, sprev, sizeof(double) * j, cudaMemcpyDeviceToDevice, s));
           ++nc;
         }
-        build_transform(s, j, S, LD, Aw, LD, cand, LD, nc, j + 1, mins - 1, excl, LD, 0, mins, Yt, LD, jn, nullptr,
+        build_transform(s, j, S, LD, Aw, LD, cand, LD, nc, j + 1, mins - 1, 0, excl, LD, 0, mins, Yt, LD, jn, nullptr,
                         LD);
         CUCHK(cudaMemcpyAsync(h.at<int>(12288), jn, sizeof(int), cudaMemcpyDeviceToHost, s));
         sync(s);
@@ -1036,6 +1124,7 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
   const int b = std::max(1, std::min(o.block_size, k));
   Pool pool(s);
   DevA A;
+  const int64_t launches0 = g_launch_count;
   upload_matrix(ctx, pool, A, m, n, nnz, rp, ci, va, on_dev, mixed, precond == PHSVDS_PREC_JACOBI, 8);
   // SpMM schedule
   int sch64 = o.spmm, sch32 = o.spmm;
@@ -1049,16 +1138,20 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
     std::memset(st, 0, sizeof(*st));
     st->spmm_schedule = sch64;
   }
+  if (o.profile) g_prof.start(1 << 16);
   // ---- stage 1
   const auto t1a = clk::now();
-  Stage1<double> s1(ctx, pool, A.n, k, o, largest, tol, EPS64, precond, A.diagC, op64);
-  int64_t iters32 = 0, mv32 = 0;
+  const double tol_in = TOL_MARGIN * tol;
+  Stage1<double> s1(ctx, pool, A.n, k, o, largest, tol_in, EPS64, precond, A.diagC, op64);
+  int64_t iters32 = 0, mv32 = 0, jac32[2] = {0, 0};
   double theta_max32 = 0.0;
   if (mixed) {
-    Stage1<float> s1f(ctx, pool, A.n, k, o, largest, tol, EPS32, precond, A.diagC, op32);
+    Stage1<float> s1f(ctx, pool, A.n, k, o, largest, tol_in, EPS32, precond, A.diagC, op32);
     s1f.run(nullptr, 0);
     iters32 = s1f.out.iters;
     mv32 = s1f.out.mv;
+    jac32[0] = s1f.out.jac_sweeps;
+    jac32[1] = s1f.out.jac_rot;
     theta_max32 = s1f.out.theta_max;
     // continue in FP64 from the FP32 eigenvectors (promoted)
     double* X0 = pool.get<double>((size_t)A.n * k);
@@ -1082,7 +1175,7 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
   bool need2 = false;
   const double floor = o.eps_factor * EPS64;
   for (int i = 0; i < k; ++i)
-    if (tol < floor * normA / std::max(sg[i], 1e-300) || !(rs[i] < tol * normA)) need2 = true;
+    if (tol < floor * normA / std::max(sg[i], 1e-300) || !(rs[i] < tol_in * normA)) need2 = true;
   int64_t it2 = 0, rs2 = 0;
   double t2ms = 0.0;
   if (need2 && o.stage2) {
@@ -1116,7 +1209,7 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
     }
     std::vector<double> sig_s(k);
     for (int i = 0; i < k; ++i) sig_s[i] = std::sqrt(std::max(lam[i], 0.0));
-    Stage2 s2(ctx, pool, f, A, k, o, tol, normA);
+    Stage2 s2(ctx, pool, f, A, k, o, tol_in, normA);
     s2.run(sig_s, Xv);
     mvA += s2.mv;
     mvAt += s2.mv;
@@ -1150,7 +1243,20 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
                                  cudaMemcpyDeviceToHost, s));
   }
   sync(s);
+  double cls_ms[PROF_NCAT] = {0, 0, 0, 0, 0};
+  int64_t cls_n[PROF_NCAT] = {0, 0, 0, 0, 0};
+  if (o.profile) g_prof.finish(cls_ms, cls_n);
   if (st) {
+    for (int c = 0; c < PROF_NCAT; ++c) {
+      st->t_class_ms[c] = cls_ms[c];
+      st->n_class[c] = cls_n[c];
+    }
+    st->kernel_launches = g_launch_count - launches0;
+    st->spmm_c_calls = cls_n[PROF_CSPMM] ? cls_n[PROF_CSPMM] : s1.out.mv / std::max(1, spmm_width(b));
+    st->spmm_c_ms = cls_ms[PROF_CSPMM];
+    st->spmm_c_width = spmm_width(b);
+    st->jacobi_sweeps = s1.out.jac_sweeps + jac32[0];
+    st->jacobi_rotations = s1.out.jac_rot + jac32[1];
     st->matvecs_A = mvA;
     st->matvecs_At = mvAt;
     st->iters_stage1 = s1.out.iters + iters32;
@@ -1217,6 +1323,7 @@ phsvds_status phsvds_default_opts(phsvds_opts* o) {
   o->rayleigh_ritz = 1;
   o->seed = 0;
   o->time_limit_s = 0.0;
+  o->profile = 0;
   return PHSVDS_OK;
 }
 
@@ -1304,6 +1411,9 @@ phsvds_status phsvds_solve(phsvds_handle h, int64_t m, int64_t n, int64_t nnz, c
   } catch (const PhError& e) {
     cudaStreamSynchronize(h->stream);
     cudaGetLastError();
+    double ms[PROF_NCAT] = {0, 0, 0, 0, 0};
+    int64_t cnt[PROF_NCAT] = {0, 0, 0, 0, 0};
+    g_prof.finish(ms, cnt);
     return set_err(h, e.st, e.msg);
   }
   return PHSVDS_OK;
@@ -1344,6 +1454,14 @@ phsvds_status phsvds_jacobi_eig_f64(phsvds_handle h, int j, double* H, double* S
                                     int max_sweeps, int* sweeps_out) {
   if (!h || j < 1 || j > LD || !H || !S || !theta) return PHSVDS_ERR_INVALID;
   jacobi_eig(h->stream, j, H, S, theta, tol, max_sweeps, sweeps_out);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? PHSVDS_OK : set_err(h, PHSVDS_ERR_CUDA, cudaGetErrorString(e));
+}
+
+phsvds_status phsvds_jacobi_eig_cluster_f64(phsvds_handle h, int j, double* H, double* S, double* theta, double tol,
+                                            int max_sweeps, int* sweeps_out) {
+  if (!h || j < 1 || j > LD || !H || !S || !theta) return PHSVDS_ERR_INVALID;
+  jacobi_eig_cluster_ld(h->stream, j, H, j, S, j, theta, tol, max_sweeps, sweeps_out, tol, 0, 0, 0.0, nullptr);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? PHSVDS_OK : set_err(h, PHSVDS_ERR_CUDA, cudaGetErrorString(e));
 }

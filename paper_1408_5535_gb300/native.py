@@ -25,17 +25,24 @@ class Opts(C.Structure):
     _fields_ = [("block_size", C.c_int), ("max_basis", C.c_int), ("min_restart", C.c_int),
                 ("max_restarts", C.c_int), ("eps_factor", C.c_double), ("precision", C.c_int),
                 ("spmm", C.c_int), ("stage2", C.c_int), ("rayleigh_ritz", C.c_int),
-                ("seed", C.c_uint64), ("time_limit_s", C.c_double)]
+                ("seed", C.c_uint64), ("time_limit_s", C.c_double), ("profile", C.c_int)]
 
 
 class Stats(C.Structure):
     _fields_ = [("matvecs_A", C.c_int64), ("matvecs_At", C.c_int64), ("iters_stage1", C.c_int64),
                 ("iters_stage1_fp32", C.c_int64), ("iters_stage2", C.c_int64), ("restarts", C.c_int64),
                 ("switched", C.c_int), ("norm_A_est", C.c_double), ("t_stage1_ms", C.c_double),
-                ("t_stage2_ms", C.c_double), ("t_total_ms", C.c_double), ("spmm_schedule", C.c_int)]
+                ("t_stage2_ms", C.c_double), ("t_total_ms", C.c_double), ("spmm_schedule", C.c_int),
+                ("kernel_launches", C.c_int64), ("t_class_ms", C.c_double * 5), ("n_class", C.c_int64 * 5),
+                ("spmm_c_calls", C.c_int64), ("spmm_c_ms", C.c_double), ("spmm_c_width", C.c_int),
+                ("jacobi_sweeps", C.c_int64), ("jacobi_rotations", C.c_int64)]
 
     def as_dict(self) -> dict:
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        d = {}
+        for f, _ in self._fields_:
+            v = getattr(self, f)
+            d[f] = list(v) if hasattr(v, "__len__") else v
+        return d
 
 
 class PhsvdsError(RuntimeError):
@@ -58,6 +65,7 @@ def _load() -> C.CDLL:
         "phsvds_ata_spmm_f32": ([P, I, I64, I64, P, P, P, P, P, P, I, P, P, P], I),
         "phsvds_csr_to_csc_f64": ([P, I64, I64, I64, P, P, P, P, P, P], I),
         "phsvds_jacobi_eig_f64": ([P, I, P, P, P, D, I, P], I),
+        "phsvds_jacobi_eig_cluster_f64": ([P, I, P, P, P, D, I, P], I),
         "phsvds_jacobi_svd_f64": ([P, I, P, P, P, D, I, P], I),
         "phsvds_sync": ([P], I),
         "phsvds_last_error": ([P], C.c_char_p),
@@ -82,7 +90,7 @@ def lib() -> C.CDLL:
 
 
 EXPORTED = ["phsvds_create", "phsvds_default_opts", "phsvds_solve", "phsvds_ata_spmm_f64",
-            "phsvds_ata_spmm_f32", "phsvds_csr_to_csc_f64", "phsvds_jacobi_eig_f64",
+            "phsvds_ata_spmm_f32", "phsvds_csr_to_csc_f64", "phsvds_jacobi_eig_f64", "phsvds_jacobi_eig_cluster_f64",
             "phsvds_jacobi_svd_f64", "phsvds_sync", "phsvds_last_error", "phsvds_status_string",
             "phsvds_destroy"]
 
@@ -172,8 +180,9 @@ def phsvds_csr_to_csc(h: Handle, m, n, nnz, rp32, ci, va, cp, ri, cv):
                                         _ptr(cv)))
 
 
-def phsvds_jacobi_eig(h: Handle, j, H, S, theta, tol=1e-17, max_sweeps=60, sweeps=None):
-    h.check(lib().phsvds_jacobi_eig_f64(h.h, j, _ptr(H), _ptr(S), _ptr(theta), tol, max_sweeps, _ptr(sweeps)))
+def phsvds_jacobi_eig(h: Handle, j, H, S, theta, tol=1e-17, max_sweeps=60, sweeps=None, cluster=False):
+    f = lib().phsvds_jacobi_eig_cluster_f64 if cluster else lib().phsvds_jacobi_eig_f64
+    h.check(f(h.h, j, _ptr(H), _ptr(S), _ptr(theta), tol, max_sweeps, _ptr(sweeps)))
 
 
 def phsvds_jacobi_svd(h: Handle, j, G, S, sig, tol=1e-15, max_sweeps=60, sweeps=None):

@@ -64,8 +64,9 @@ def test_csr_to_csc_exact(h):
     assert np.array_equal(cv.cpu().numpy(), T.data)
 
 
+@pytest.mark.parametrize("cluster", [False, True])
 @pytest.mark.parametrize("j", [1, 2, 7, 20, 35, 64])
-def test_jacobi_eig_vs_oracle(h, j):
+def test_jacobi_eig_vs_oracle(h, j, cluster):
     rng = np.random.default_rng(j)
     M = rng.standard_normal((j, j))
     H = M + M.T
@@ -78,7 +79,7 @@ def test_jacobi_eig_vs_oracle(h, j):
     Sd = dev(np.eye(j).ravel(order="F"))
     th = torch.empty(j, dtype=torch.float64, device="cuda")
     sw = torch.zeros(1, dtype=torch.int32, device="cuda")
-    native.phsvds_jacobi_eig(h, j, Hd, Sd, th, 1e-17, 60, sw)
+    native.phsvds_jacobi_eig(h, j, Hd, Sd, th, 1e-17, 60, sw, cluster=cluster)
     native.phsvds_sync(h)
     S = Sd.cpu().numpy().reshape(j, j, order="F")
     theta = th.cpu().numpy()
