@@ -45,6 +45,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--spmm-only", action="store_true", help="only the full-size fused A^T A SpMM timings")
+    p.add_argument("--spmm-cases", default="c2,c3", help="full-size SpMM workloads: c2 (512^2 grid), c3 (1e6 x 5e5)")
+    p.add_argument("--spmm-reps", type=int, default=10)
     return p.parse_args()
 
 
@@ -148,6 +151,66 @@ def spmm_bytes(m, n, nnz, b, p):
     """Algorithmic bytes of one fused A^T A SpMM launch set: one read of the CSR
     (values p bytes, column indices 4), the row offsets, X read and Y written."""
     return nnz * (p + 4) + 4 * (m + 1) + 2 * p * n * b
+
+
+def spmm_full(a):
+    """Fused A^T A SpMM (products with C) on the full-size configurations,
+    both schedules, FP64 and FP32; CUDA events over spmm_reps launches with a
+    256 MiB L2 flush between launches."""
+    import numpy as np
+    import torch
+    from paper_1408_5535_gb300 import native, synth
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream(device=dev)
+    h = native.Handle(dev, stream.cuda_stream)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+    hbm, _ = peaks()
+    out = []
+    cases = {"c2": ("weighted grid gradient 512x512 (sigma_log=1, seed 2)", lambda: synth.grid_gradient(512, 1.0, 2), 4),
+             "c3": ("random 1e6 x 5e5, Poisson(12)/row, lognormal(2) +-, +1e-3[I;0], seed 3",
+                    lambda: synth.random_sparse(1000000, 500000, 12.0, 3), 8)}
+    for key in [c for c in a.spmm_cases.split(",") if c]:
+        name, gen, b = cases[key]
+        A = gen()
+        rp = torch.from_numpy(A.row_ptr.astype(np.int32)).cuda()
+        ci = torch.from_numpy(A.col).cuda()
+        va = torch.from_numpy(A.val).cuda()
+        cp = torch.empty(A.n + 1, dtype=torch.int32, device="cuda")
+        ri = torch.empty(A.nnz, dtype=torch.int32, device="cuda")
+        cv = torch.empty(A.nnz, dtype=torch.float64, device="cuda")
+        native.phsvds_csr_to_csc(h, A.m, A.n, A.nnz, rp, ci, va, cp, ri, cv)
+        native.phsvds_sync(h)
+        for fp32 in (True, False):
+            vt = torch.float32 if fp32 else torch.float64
+            v1, v2 = (va.float(), cv.float()) if fp32 else (va, cv)
+            X = torch.rand((A.n, b), dtype=vt, device="cuda")
+            Y = torch.empty((A.n, b), dtype=vt, device="cuda")
+            Z = torch.empty((A.m, b), dtype=vt, device="cuda")
+            p_bytes = 4 if fp32 else 8
+            alg = spmm_bytes(A.m, A.n, A.nnz, b, p_bytes)
+            for sch in (1, 2):
+                for _ in range(3):
+                    native.phsvds_ata_spmm(h, sch, A.m, A.n, rp, ci, v1, cp, ri, v2, b, X, Y, Z, fp32=fp32)
+                ts = []
+                for _ in range(a.spmm_reps):
+                    flush.fill_(1.0)
+                    torch.cuda.synchronize()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    native.phsvds_ata_spmm(h, sch, A.m, A.n, rp, ci, v1, cp, ri, v2, b, X, Y, Z, fp32=fp32)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                ms = float(np.mean(ts))
+                gbs = alg / (ms * 1e-3) / 1e9
+                out.append({"case": key, "workload": name, "m": A.m, "n": A.n, "nnz": A.nnz, "b": b,
+                            "dtype": "f32" if fp32 else "f64",
+                            "schedule": "fused-atomic" if sch == 1 else "two-phase (Z=AX, CSC)",
+                            "avg_launch_ms": ms, "alg_bytes": alg, "GBps": gbs, "frac_of_hbm": gbs / hbm})
+        del A
+    h.close()
+    return out
 
 
 def cpu_baseline(A, a, gpu_stats, k):
@@ -260,6 +323,11 @@ def main():
         return run_reference(a, rank, world)
     import torch
     from paper_1408_5535_gb300 import native
+    if a.spmm_only:
+        r = spmm_full(a)
+        if rank == 0:
+            print(json.dumps({"spmm": r}), flush=True)
+        return
     A, cfg, res = run_ours(a, rank, world)
     head = native.MIXED if native.MIXED in res else native.FP64
     r = res[head]
@@ -310,6 +378,17 @@ def main():
                         "speedup_mixed_over_fp64": f["ms"] / r["ms"],
                         "max_sigma_rel_diff_vs_mixed": max(abs(x - y) / y for x, y in zip(r["sigma"], f["sigma"])),
                         "class_ms": dict(zip(names, f["prof"]["t_class_ms"]))}
+    if a.spmm_cases:
+        sp = spmm_full(a)
+        line["spmm"] = sp
+        best = max((x for x in sp if x["case"] == "c3" and x["dtype"] == "f32"), key=lambda x: x["GBps"], default=None)
+        if best is None and sp:
+            best = max(sp, key=lambda x: x["GBps"])
+        if best:
+            line["spmm_roofline"] = {"bound": "hbm", "kernel": f"fused A^T A SpMM, {best['schedule']}, {best['dtype']}",
+                                     "workload": best["workload"], "achieved": best["GBps"], "peak": hbm,
+                                     "unit": "GB/s", "frac": best["GBps"] / hbm, "traffic": None,
+                                     "bytes_per_launch": best["alg_bytes"], "avg_launch_ms": best["avg_launch_ms"]}
     if rank == 0 and not a.no_cpu:
         line["cpu_baseline"] = cpu_baseline(A, a, st, cfg["k"])
     if rank == 0:

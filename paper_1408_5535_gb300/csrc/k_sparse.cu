@@ -9,10 +9,13 @@
 
 namespace ph {
 
-// One group of L lanes per sparse row: lanes stride over the row's entries,
-// then reduce their B partial sums inside the group.
-template <typename T, int B, int L>
-__global__ void __launch_bounds__(256) k_csr_rows(int nrows, const int* __restrict__ rp,
+// One group of L lanes per sparse row.  Each pass a lane first loads U
+// (column, value) pairs of its row (streaming: the matrix is read once and
+// should not evict the gathered vectors from L2), then issues the U gathers of
+// X rows back to back, so U independent loads are in flight per lane; the B
+// partial sums are reduced inside the group at the end.
+template <typename T, int B, int L, int U>
+__global__ void __launch_bounds__(256) k_csr_rows(int nrows, int xrows, const int* __restrict__ rp,
                                                   const int* __restrict__ ci, const T* __restrict__ va,
                                                   const T* __restrict__ X, T* __restrict__ Z) {
   const int lane = threadIdx.x % L;
@@ -22,12 +25,28 @@ __global__ void __launch_bounds__(256) k_csr_rows(int nrows, const int* __restri
 #pragma unroll
   for (int q = 0; q < B; ++q) acc[q] = T(0);
   const int e0 = active ? rp[row] : 0, e1 = active ? rp[row + 1] : 0;
-  for (int e = e0 + lane; e < e1; e += L) {
-    const T a = va[e];
-    T x[B];
-    load_row<T, B>(X + (size_t)ci[e] * B, x);
+  for (int base = e0; base < e1; base += L * U) {
+    int col[U];
+    T v[U];
 #pragma unroll
-    for (int q = 0; q < B; ++q) acc[q] = fma(a, x[q], acc[q]);
+    for (int u = 0; u < U; ++u) {
+      // every address stays inside the row (e0 < e1 here): dead slots re-read
+      // entry e0 and get the value zero
+      const int e = base + u * L + lane;
+      const bool ok = e < e1;
+      const int ec = ok ? e : e0;
+      const int c = __ldcs(ci + ec);
+      const bool inr = (unsigned)c < (unsigned)xrows;  // guard against a corrupted index
+      col[u] = inr ? c : 0;
+      v[u] = (ok && inr) ? __ldcs(va + ec) : T(0);
+    }
+    T x[U][B];
+#pragma unroll
+    for (int u = 0; u < U; ++u) load_row<T, B>(X + (size_t)col[u] * B, x[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int q = 0; q < B; ++q) acc[q] = fma(v[u], x[u][q], acc[q]);
   }
   if constexpr (L > 1) {
     const unsigned mask = 0xffffffffu;
@@ -39,10 +58,11 @@ __global__ void __launch_bounds__(256) k_csr_rows(int nrows, const int* __restri
   if (active && lane == 0) store_row<T, B>(Z + (size_t)row * B, acc);
 }
 
-// Fused single pass Y += A^T (A X): a group computes z = a_i^T X for its row,
-// keeps it in registers and scatters a_ij * z into Y with L2 atomics.
-template <typename T, int B, int L>
-__global__ void __launch_bounds__(256) k_ata_fused(int nrows, const int* __restrict__ rp,
+// Fused single pass Y += A^T (A X): a group computes z = a_i^T X for its row
+// (same batched loads as above), keeps it in registers and scatters a_ij * z
+// into Y with L2 atomics (128-bit vector atomics for FP32).
+template <typename T, int B, int L, int U>
+__global__ void __launch_bounds__(256) k_ata_fused(int nrows, int xrows, const int* __restrict__ rp,
                                                    const int* __restrict__ ci, const T* __restrict__ va,
                                                    const T* __restrict__ X, T* __restrict__ Y) {
   const int lane = threadIdx.x % L;
@@ -52,12 +72,26 @@ __global__ void __launch_bounds__(256) k_ata_fused(int nrows, const int* __restr
 #pragma unroll
   for (int q = 0; q < B; ++q) z[q] = T(0);
   const int e0 = active ? rp[row] : 0, e1 = active ? rp[row + 1] : 0;
-  for (int e = e0 + lane; e < e1; e += L) {
-    const T a = va[e];
-    T x[B];
-    load_row<T, B>(X + (size_t)ci[e] * B, x);
+  for (int base = e0; base < e1; base += L * U) {
+    int col[U];
+    T v[U];
 #pragma unroll
-    for (int q = 0; q < B; ++q) z[q] = fma(a, x[q], z[q]);
+    for (int u = 0; u < U; ++u) {
+      const int e = base + u * L + lane;
+      const bool ok = e < e1;
+      const int ec = ok ? e : e0;
+      const int c = ci[ec];
+      const bool inr = (unsigned)c < (unsigned)xrows;
+      col[u] = inr ? c : 0;
+      v[u] = (ok && inr) ? va[ec] : T(0);
+    }
+    T x[U][B];
+#pragma unroll
+    for (int u = 0; u < U; ++u) load_row<T, B>(X + (size_t)col[u] * B, x[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int q = 0; q < B; ++q) z[q] = fma(v[u], x[u][q], z[q]);
   }
   if constexpr (L > 1) {
 #pragma unroll
@@ -66,39 +100,44 @@ __global__ void __launch_bounds__(256) k_ata_fused(int nrows, const int* __restr
       for (int q = 0; q < B; ++q) z[q] += __shfl_xor_sync(0xffffffffu, z[q], o, L);
   }
   for (int e = e0 + lane; e < e1; e += L) {
+    const int c = ci[e];
+    if ((unsigned)c >= (unsigned)xrows) continue;
     const T a = va[e];
     T y[B];
 #pragma unroll
     for (int q = 0; q < B; ++q) y[q] = a * z[q];
-    atomic_add_row<T, B>(Y + (size_t)ci[e] * B, y);
+    atomic_add_row<T, B>(Y + (size_t)c * B, y);
   }
 }
 
+// U (loads in flight per lane): 4, or 2 for 8-wide FP64 rows (register budget)
+template <typename T, int B> constexpr int unroll_for() { return (sizeof(T) == 8 && B == 8) ? 2 : 4; }
+
 template <typename T, int B>
-static void rows_dispatch_L(cudaStream_t s, int L, int nrows, const int* rp, const int* ci, const T* va,
+static void rows_dispatch_L(cudaStream_t s, int L, int nrows, int xrows, const int* rp, const int* ci, const T* va,
                             const T* X, T* Z) {
   const int th = 256;
   const int blocks = ceil_div((int64_t)nrows * L, th);
   if (nrows <= 0) return;
   switch (L) {
-    case 1: k_csr_rows<T, B, 1><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Z); count_launch(); break;
-    case 2: k_csr_rows<T, B, 2><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Z); count_launch(); break;
-    case 4: k_csr_rows<T, B, 4><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Z); count_launch(); break;
-    default: k_csr_rows<T, B, 8><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Z); count_launch(); break;
+    case 1: k_csr_rows<T, B, 1, unroll_for<T, B>()><<<blocks, th, 0, s>>>(nrows, xrows, rp, ci, va, X, Z); count_launch(); break;
+    case 2: k_csr_rows<T, B, 2, unroll_for<T, B>()><<<blocks, th, 0, s>>>(nrows, xrows, rp, ci, va, X, Z); count_launch(); break;
+    case 4: k_csr_rows<T, B, 4, unroll_for<T, B>()><<<blocks, th, 0, s>>>(nrows, xrows, rp, ci, va, X, Z); count_launch(); break;
+    default: k_csr_rows<T, B, 8, unroll_for<T, B>()><<<blocks, th, 0, s>>>(nrows, xrows, rp, ci, va, X, Z); count_launch(); break;
   }
 }
 
 template <typename T, int B>
-static void fused_dispatch_L(cudaStream_t s, int L, int nrows, const int* rp, const int* ci, const T* va,
+static void fused_dispatch_L(cudaStream_t s, int L, int nrows, int xrows, const int* rp, const int* ci, const T* va,
                              const T* X, T* Y) {
   const int th = 256;
   const int blocks = ceil_div((int64_t)nrows * L, th);
   if (nrows <= 0) return;
   switch (L) {
-    case 1: k_ata_fused<T, B, 1><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Y); count_launch(); break;
-    case 2: k_ata_fused<T, B, 2><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Y); count_launch(); break;
-    case 4: k_ata_fused<T, B, 4><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Y); count_launch(); break;
-    default: k_ata_fused<T, B, 8><<<blocks, th, 0, s>>>(nrows, rp, ci, va, X, Y); count_launch(); break;
+    case 1: k_ata_fused<T, B, 1, unroll_for<T, B>()><<<blocks, th, 0, s>>>(nrows, xrows, rp, ci, va, X, Y); count_launch(); break;
+    case 2: k_ata_fused<T, B, 2, unroll_for<T, B>()><<<blocks, th, 0, s>>>(nrows, xrows, rp, ci, va, X, Y); count_launch(); break;
+    case 4: k_ata_fused<T, B, 4, unroll_for<T, B>()><<<blocks, th, 0, s>>>(nrows, xrows, rp, ci, va, X, Y); count_launch(); break;
+    default: k_ata_fused<T, B, 8, unroll_for<T, B>()><<<blocks, th, 0, s>>>(nrows, xrows, rp, ci, va, X, Y); count_launch(); break;
   }
 }
 
@@ -114,10 +153,10 @@ void csr_spmm(cudaStream_t s, const SparseView<T>& A, int b, const T* X, T* Z) {
   ProfScope ps(s, PROF_SPMV);
   const int L = lanes_for(A.avg_row());
   switch (b) {
-    case 1: rows_dispatch_L<T, 1>(s, L, A.nrows, A.ptr, A.idx, A.val, X, Z); break;
-    case 2: rows_dispatch_L<T, 2>(s, L, A.nrows, A.ptr, A.idx, A.val, X, Z); break;
-    case 4: rows_dispatch_L<T, 4>(s, L, A.nrows, A.ptr, A.idx, A.val, X, Z); break;
-    case 8: rows_dispatch_L<T, 8>(s, L, A.nrows, A.ptr, A.idx, A.val, X, Z); break;
+    case 1: rows_dispatch_L<T, 1>(s, L, A.nrows, A.ncols, A.ptr, A.idx, A.val, X, Z); break;
+    case 2: rows_dispatch_L<T, 2>(s, L, A.nrows, A.ncols, A.ptr, A.idx, A.val, X, Z); break;
+    case 4: rows_dispatch_L<T, 4>(s, L, A.nrows, A.ncols, A.ptr, A.idx, A.val, X, Z); break;
+    case 8: rows_dispatch_L<T, 8>(s, L, A.nrows, A.ncols, A.ptr, A.idx, A.val, X, Z); break;
     default: break;
   }
 }
@@ -128,10 +167,10 @@ void ata_fused(cudaStream_t s, const SparseView<T>& A, int ncols, int b, const T
   cudaMemsetAsync(Y, 0, sizeof(T) * (size_t)ncols * b, s);
   const int L = lanes_for(A.avg_row());
   switch (b) {
-    case 1: fused_dispatch_L<T, 1>(s, L, A.nrows, A.ptr, A.idx, A.val, X, Y); break;
-    case 2: fused_dispatch_L<T, 2>(s, L, A.nrows, A.ptr, A.idx, A.val, X, Y); break;
-    case 4: fused_dispatch_L<T, 4>(s, L, A.nrows, A.ptr, A.idx, A.val, X, Y); break;
-    case 8: fused_dispatch_L<T, 8>(s, L, A.nrows, A.ptr, A.idx, A.val, X, Y); break;
+    case 1: fused_dispatch_L<T, 1>(s, L, A.nrows, A.ncols, A.ptr, A.idx, A.val, X, Y); break;
+    case 2: fused_dispatch_L<T, 2>(s, L, A.nrows, A.ncols, A.ptr, A.idx, A.val, X, Y); break;
+    case 4: fused_dispatch_L<T, 4>(s, L, A.nrows, A.ncols, A.ptr, A.idx, A.val, X, Y); break;
+    case 8: fused_dispatch_L<T, 8>(s, L, A.nrows, A.ncols, A.ptr, A.idx, A.val, X, Y); break;
     default: break;
   }
 }
