@@ -154,6 +154,44 @@ phsvds_status phsvds_ata_spmm_f32(phsvds_handle h, int schedule, int64_t m, int6
                                   const int32_t* csc_ptr, const int32_t* csc_row, const float* csc_val,
                                   int b, const float* X, float* Y, float* z);
 
+/* Capacity, in doubles, of the fixed scratch of phsvds_ata_spmm_static_f64
+ * (2 MiB): m * b may not exceed it. */
+#define PHSVDS_STATIC_Z_MAX 262144
+
+/*
+ * Allocation-free variant of phsvds_ata_spmm_f64 with the two-phase schedule:
+ * Y = A^T (A X) through Z = A X.  The paper has no counterpart to this entry
+ * point; it serves callers that cannot allocate device memory while they run
+ * it -- a program that has handed all device memory to its own pool, or a
+ * latency-critical loop in which a cudaMalloc (which may synchronise the
+ * device) is not acceptable -- and so cannot provide the m x b buffer z that
+ * phsvds_ata_spmm_f64 needs.  Here Z lives in a fixed array of
+ * PHSVDS_STATIC_Z_MAX doubles inside the library's device memory, and no call
+ * allocates anything.
+ *
+ * Arguments as phsvds_ata_spmm_f64 (all DEVICE pointers, X and Y n x b
+ * row-major, b in {1, 2, 4, 8}, CSR and CSC copies of A), except: no schedule
+ * and no z; nnz is passed by the caller (it picks the lanes per row, and
+ * taking it as an argument avoids reading row_ptr[m] back to the host).
+ * Errors: PHSVDS_ERR_INVALID, with nothing launched, for bad arguments or when
+ * m * b > PHSVDS_STATIC_Z_MAX (use phsvds_ata_spmm_f64 then);
+ * PHSVDS_ERR_CUDA when the scratch cannot be located or a launch fails.
+ * Runs on the handle's stream; asynchronous.
+ *
+ * The first call on each device makes that device current and looks up the
+ * array's address (cudaGetSymbolAddress), which may also load the library's
+ * device code; make this first call before any stream capture begins.  The
+ * scratch needs no clearing, since the first phase writes every entry the
+ * second reads.  There is ONE scratch per device, shared by all handles and
+ * threads: calls whose executions can overlap (different streams, or handles
+ * used from several threads) race on it and give wrong results.  Order them on
+ * one stream.
+ */
+phsvds_status phsvds_ata_spmm_static_f64(phsvds_handle h, int64_t m, int64_t n, int64_t nnz,
+                                         const int32_t* row_ptr, const int32_t* col_idx, const double* val,
+                                         const int32_t* csc_ptr, const int32_t* csc_row, const double* csc_val,
+                                         int b, const double* X, double* Y);
+
 /*
  * Kernel-level entry point: CSR -> CSC transpose on the device (setup step of the
  * two-phase SpMM).  Inputs/outputs are DEVICE pointers: row_ptr (m+1), col_idx,

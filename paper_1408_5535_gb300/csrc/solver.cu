@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1475,3 +1476,54 @@ phsvds_status phsvds_jacobi_svd_f64(phsvds_handle h, int j, double* G, double* S
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free A^T (A X): the two-phase product with its intermediate
+// Z = A X held in a fixed array of the library's own device memory.  The array
+// is placed in device memory when the library's device code is loaded, so a
+// call allocates nothing; its address is looked up once per device.
+// ===========================================================================
+static __device__ __align__(256) double g_static_z[PHSVDS_STATIC_Z_MAX];
+
+namespace {
+constexpr int kStaticZDevices = 64;
+std::mutex g_static_z_mu;
+double* g_static_z_addr[kStaticZDevices] = {};
+}  // namespace
+
+extern "C" phsvds_status phsvds_ata_spmm_static_f64(phsvds_handle h, int64_t m, int64_t n, int64_t nnz,
+                                                    const int32_t* row_ptr, const int32_t* col_idx, const double* val,
+                                                    const int32_t* csc_ptr, const int32_t* csc_row,
+                                                    const double* csc_val, int b, const double* X, double* Y) {
+  if (!h || m < 1 || n < 1 || n > INT32_MAX || nnz < 0 || nnz > INT32_MAX || !row_ptr || !csc_ptr || !X || !Y ||
+      (b != 1 && b != 2 && b != 4 && b != 8))
+    return set_err(h, PHSVDS_ERR_INVALID, "invalid SpMM arguments");
+  if (m * b > PHSVDS_STATIC_Z_MAX)
+    return set_err(h, PHSVDS_ERR_INVALID,
+                   "m * b = " + std::to_string(m * b) + " exceeds the fixed scratch of " +
+                       std::to_string(PHSVDS_STATIC_Z_MAX) + " doubles; use phsvds_ata_spmm_f64 with a caller buffer");
+  if (h->device < 0 || h->device >= kStaticZDevices)
+    return set_err(h, PHSVDS_ERR_INVALID, "device ordinal out of range for the fixed scratch");
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return set_err(h, PHSVDS_ERR_CUDA, cudaGetErrorString(e));
+  double* z = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_static_z_mu);
+    z = g_static_z_addr[h->device];
+    if (!z) {
+      // first call on this device (h->device is current): find the array
+      e = cudaGetSymbolAddress(reinterpret_cast<void**>(&z), g_static_z);
+      if (e != cudaSuccess || !z)
+        return set_err(h, PHSVDS_ERR_CUDA,
+                       std::string("cannot locate the fixed SpMM scratch: ") + cudaGetErrorString(e));
+      g_static_z_addr[h->device] = z;
+    }
+  }
+  // Z needs no clearing: the first phase writes all m x b entries before the
+  // second phase reads any of them.
+  SparseView<double> A{(int)m, (int)n, nnz, row_ptr, col_idx, val};
+  SparseView<double> At{(int)n, (int)m, nnz, csc_ptr, csc_row, csc_val};
+  ata_two_phase<double>(h->stream, A, At, b, X, Y, z);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? PHSVDS_OK : set_err(h, PHSVDS_ERR_CUDA, cudaGetErrorString(e));
+}

@@ -63,6 +63,7 @@ def _load() -> C.CDLL:
                           C.POINTER(Stats)], I),
         "phsvds_ata_spmm_f64": ([P, I, I64, I64, P, P, P, P, P, P, I, P, P, P], I),
         "phsvds_ata_spmm_f32": ([P, I, I64, I64, P, P, P, P, P, P, I, P, P, P], I),
+        "phsvds_ata_spmm_static_f64": ([P, I64, I64, I64, P, P, P, P, P, P, I, P, P], I),
         "phsvds_csr_to_csc_f64": ([P, I64, I64, I64, P, P, P, P, P, P], I),
         "phsvds_jacobi_eig_f64": ([P, I, P, P, P, D, I, P], I),
         "phsvds_jacobi_eig_cluster_f64": ([P, I, P, P, P, D, I, P], I),
@@ -90,7 +91,7 @@ def lib() -> C.CDLL:
 
 
 EXPORTED = ["phsvds_create", "phsvds_default_opts", "phsvds_solve", "phsvds_ata_spmm_f64",
-            "phsvds_ata_spmm_f32", "phsvds_csr_to_csc_f64", "phsvds_jacobi_eig_f64", "phsvds_jacobi_eig_cluster_f64",
+            "phsvds_ata_spmm_f32", "phsvds_ata_spmm_static_f64", "phsvds_csr_to_csc_f64", "phsvds_jacobi_eig_f64", "phsvds_jacobi_eig_cluster_f64",
             "phsvds_jacobi_svd_f64", "phsvds_sync", "phsvds_last_error", "phsvds_status_string",
             "phsvds_destroy"]
 
@@ -173,6 +174,18 @@ def phsvds_ata_spmm(h: Handle, schedule, m, n, rp32, ci, va, cp, ri, cv, b, X, Y
     f = lib().phsvds_ata_spmm_f32 if fp32 else lib().phsvds_ata_spmm_f64
     h.check(f(h.h, schedule, m, n, _ptr(rp32), _ptr(ci), _ptr(va), _ptr(cp), _ptr(ri), _ptr(cv), b,
               _ptr(X), _ptr(Y), _ptr(z)))
+
+
+# Capacity (doubles) of the fixed scratch of phsvds_ata_spmm_static_f64: m * b <= this.
+STATIC_Z_MAX = 262144
+
+
+def phsvds_ata_spmm_static(h: Handle, m, n, nnz, rp32, ci, va, cp, ri, cv, b, X, Y):
+    """Y = A^T (A X) in FP64 without any device allocation (two-phase schedule,
+    intermediate A X in the library's fixed scratch; needs m * b <= STATIC_Z_MAX).
+    Calls that can overlap in time race on that one scratch per device."""
+    h.check(lib().phsvds_ata_spmm_static_f64(h.h, m, n, nnz, _ptr(rp32), _ptr(ci), _ptr(va), _ptr(cp), _ptr(ri),
+                                             _ptr(cv), b, _ptr(X), _ptr(Y)))
 
 
 def phsvds_csr_to_csc(h: Handle, m, n, nnz, rp32, ci, va, cp, ri, cv):

@@ -1,0 +1,92 @@
+"""The allocation-free A^T (A X) entry point (phsvds_ata_spmm_static_f64).
+
+It is meant for callers that cannot allocate device memory while it runs (all
+memory handed to their own pool, or a loop where a cudaMalloc is not
+acceptable), so it keeps the intermediate A X in a fixed device array of the
+library.  These tests call it through the C ABI twice in a row and compare
+each result with the existing two-phase entry point (which takes a caller
+buffer) within the same rounding bound as the SpMM parity tests; they also
+check that oversized inputs are refused before anything runs, and that a
+repeated call leaves the device's free memory unchanged.  The file name keeps
+it last in collection, so it runs both after the other GPU tests and alone.
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1408_5535_gb300 import native, synth
+from tests.gpu_util import torch, need_gpu, dev, device_csr
+
+pytestmark = pytest.mark.gpu
+EPS64 = 2.0 ** -52
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def h():
+    need_gpu()
+    with native.Handle(0) as hh:
+        yield hh
+
+
+def _bound(A, S, X):
+    absA = abs(S)
+    rowmax = max(np.diff(A.row_ptr).max(), 1) + 2
+    return 4 * rowmax * EPS64 * (absA.T @ (absA @ np.abs(X)))
+
+
+def _existing(h, A, d, b, X):
+    """The same product through phsvds_ata_spmm_f64, two-phase, caller scratch."""
+    Yd = torch.empty((A.n, b), dtype=torch.float64, device="cuda")
+    z = torch.empty((A.m, b), dtype=torch.float64, device="cuda")
+    native.phsvds_ata_spmm(h, 2, A.m, A.n, d["rp"], d["ci"], d["va"], d["cp"], d["ri"], d["cv"], b, dev(X), Yd, z)
+    native.phsvds_sync(h)
+    return Yd.cpu().numpy()
+
+
+def test_capacity_matches_header():
+    txt = open(os.path.join(ROOT, "include", "phsvds.h")).read()
+    assert int(re.search(r"#define\s+PHSVDS_STATIC_Z_MAX\s+(\d+)", txt).group(1)) == native.STATIC_Z_MAX
+
+
+@pytest.mark.parametrize("case,b", [(0, 8), (1, 4), (2, 1), (3, 8)])
+def test_two_calls_in_a_row_match_existing_entry_point(h, case, b):
+    cases = [lambda: synth.random_sparse(3001, 1499, 12.0, 3),            # ragged tails, several tiles
+             lambda: synth.grid_gradient(23, 1.0, 2),                      # 1-2 entries per row
+             lambda: synth.random_sparse(777, 333, 30.0, 4, values="gaussian", shift=0.0),
+             lambda: synth.random_sparse(native.STATIC_Z_MAX // 8, 16000, 6.0, 5)]   # m * b at the limit
+    A = cases[case]()
+    assert A.m * b <= native.STATIC_Z_MAX
+    d = device_csr(A)
+    nnz = int(A.row_ptr[-1])
+    Xs = [(synth.uniform(7, 30 + t, A.n * b) * 2 - 1).reshape(A.n, b) for t in range(2)]
+    refs = [_existing(h, A, d, b, X) for X in Xs]
+    Xd = [dev(X) for X in Xs]
+    Yd = [torch.full((A.n, b), float("nan"), dtype=torch.float64, device="cuda") for _ in Xs]
+    free = []
+    for t in range(2):
+        native.phsvds_ata_spmm_static(h, A.m, A.n, nnz, d["rp"], d["ci"], d["va"], d["cp"], d["ri"], d["cv"], b,
+                                      Xd[t], Yd[t])
+        native.phsvds_sync(h)
+        free.append(torch.cuda.mem_get_info()[0])
+    assert free[1] == free[0]
+    for t in range(2):
+        Y = Yd[t].cpu().numpy()
+        assert np.all(np.isfinite(Y))
+        assert np.all(np.abs(Y - refs[t]) <= _bound(A, d["scipy"], Xs[t]) + 1e-300)
+
+
+def test_oversized_input_is_refused_before_launch(h):
+    A = synth.random_sparse(native.STATIC_Z_MAX // 4 + 1, 2000, 3.0, 6)
+    d = device_csr(A)
+    b = 4
+    X = dev(np.ones((A.n, b)))
+    Y = torch.full((A.n, b), 7.0, dtype=torch.float64, device="cuda")
+    with pytest.raises(native.PhsvdsError) as ei:
+        native.phsvds_ata_spmm_static(h, A.m, A.n, int(A.row_ptr[-1]), d["rp"], d["ci"], d["va"], d["cp"], d["ri"],
+                                      d["cv"], b, X, Y)
+    assert ei.value.status == 1 and "exceeds the fixed scratch" in str(ei.value)
+    native.phsvds_sync(h)
+    assert bool(torch.all(Y == 7.0))
