@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--spmm-only", action="store_true", help="only the full-size fused A^T A SpMM timings")
     p.add_argument("--spmm-cases", default="c2,c3", help="full-size SpMM workloads: c2 (512^2 grid), c3 (1e6 x 5e5)")
     p.add_argument("--spmm-reps", type=int, default=10)
+    p.add_argument("--spmm-sweep", action="store_true", help="time every group width around the automatic one")
     return p.parse_args()
 
 
@@ -154,9 +155,10 @@ def spmm_bytes(m, n, nnz, b, p):
 
 
 def spmm_full(a):
-    """Fused A^T A SpMM (products with C) on the full-size configurations,
-    both schedules, FP64 and FP32; CUDA events over spmm_reps launches with a
-    256 MiB L2 flush between launches."""
+    """Fused A^T A SpMM (products with C) on the full-size configurations:
+    both schedules, FP64 and FP32, over the group widths (threads per sparse
+    row: the automatic choice and its neighbours); CUDA events around each
+    launch set on the library's stream, a 256 MiB L2 flush before each."""
     import numpy as np
     import torch
     from paper_1408_5535_gb300 import native, synth
@@ -169,46 +171,63 @@ def spmm_full(a):
     cases = {"c2": ("weighted grid gradient 512x512 (sigma_log=1, seed 2)", lambda: synth.grid_gradient(512, 1.0, 2), 4),
              "c3": ("random 1e6 x 5e5, Poisson(12)/row, lognormal(2) +-, +1e-3[I;0], seed 3",
                     lambda: synth.random_sparse(1000000, 500000, 12.0, 3), 8)}
-    for key in [c for c in a.spmm_cases.split(",") if c]:
-        name, gen, b = cases[key]
-        A = gen()
-        rp = torch.from_numpy(A.row_ptr.astype(np.int32)).cuda()
-        ci = torch.from_numpy(A.col).cuda()
-        va = torch.from_numpy(A.val).cuda()
-        cp = torch.empty(A.n + 1, dtype=torch.int32, device="cuda")
-        ri = torch.empty(A.nnz, dtype=torch.int32, device="cuda")
-        cv = torch.empty(A.nnz, dtype=torch.float64, device="cuda")
-        native.phsvds_csr_to_csc(h, A.m, A.n, A.nnz, rp, ci, va, cp, ri, cv)
-        native.phsvds_sync(h)
-        for fp32 in (True, False):
-            vt = torch.float32 if fp32 else torch.float64
-            v1, v2 = (va.float(), cv.float()) if fp32 else (va, cv)
-            X = torch.rand((A.n, b), dtype=vt, device="cuda")
-            Y = torch.empty((A.n, b), dtype=vt, device="cuda")
-            Z = torch.empty((A.m, b), dtype=vt, device="cuda")
-            p_bytes = 4 if fp32 else 8
-            alg = spmm_bytes(A.m, A.n, A.nnz, b, p_bytes)
-            for sch in (1, 2):
-                for _ in range(3):
-                    native.phsvds_ata_spmm(h, sch, A.m, A.n, rp, ci, v1, cp, ri, v2, b, X, Y, Z, fp32=fp32)
-                ts = []
-                for _ in range(a.spmm_reps):
-                    flush.fill_(1.0)
-                    torch.cuda.synchronize()
-                    e0 = torch.cuda.Event(enable_timing=True)
-                    e1 = torch.cuda.Event(enable_timing=True)
-                    e0.record(stream)
-                    native.phsvds_ata_spmm(h, sch, A.m, A.n, rp, ci, v1, cp, ri, v2, b, X, Y, Z, fp32=fp32)
-                    e1.record(stream)
-                    torch.cuda.synchronize()
-                    ts.append(e0.elapsed_time(e1))
-                ms = float(np.mean(ts))
-                gbs = alg / (ms * 1e-3) / 1e9
-                out.append({"case": key, "workload": name, "m": A.m, "n": A.n, "nnz": A.nnz, "b": b,
-                            "dtype": "f32" if fp32 else "f64",
-                            "schedule": "fused-atomic" if sch == 1 else "two-phase (Z=AX, CSC)",
-                            "avg_launch_ms": ms, "alg_bytes": alg, "GBps": gbs, "frac_of_hbm": gbs / hbm})
-        del A
+
+    def lanes_for(avg):
+        return 1 if avg <= 2.5 else 2 if avg <= 6 else 4 if avg <= 16 else 8
+
+    def around(l0):
+        return [x for x in (l0 // 2, l0, 2 * l0) if 1 <= x <= 16]
+
+    with torch.cuda.stream(stream):
+        for key in [c for c in a.spmm_cases.split(",") if c]:
+            name, gen, b = cases[key]
+            A = gen()
+            rp = torch.from_numpy(A.row_ptr.astype(np.int32)).cuda()
+            ci = torch.from_numpy(A.col).cuda()
+            va = torch.from_numpy(A.val).cuda()
+            cp = torch.empty(A.n + 1, dtype=torch.int32, device="cuda")
+            ri = torch.empty(A.nnz, dtype=torch.int32, device="cuda")
+            cv = torch.empty(A.nnz, dtype=torch.float64, device="cuda")
+            native.phsvds_csr_to_csc(h, A.m, A.n, A.nnz, rp, ci, va, cp, ri, cv)
+            native.phsvds_sync(h)
+            la0, lt0 = lanes_for(A.nnz / A.m), lanes_for(A.nnz / A.n)
+            for fp32 in (True, False):
+                vt = torch.float32 if fp32 else torch.float64
+                v1, v2 = (va.float(), cv.float()) if fp32 else (va, cv)
+                X = torch.rand((A.n, b), dtype=vt, device="cuda")
+                Y = torch.empty((A.n, b), dtype=vt, device="cuda")
+                Z = torch.empty((A.m, b), dtype=vt, device="cuda")
+                alg = spmm_bytes(A.m, A.n, A.nnz, b, 4 if fp32 else 8)
+                plans = [(1, l, 0) for l in around(la0)] + [(2, l, lt0) for l in around(la0)] + \
+                        [(2, la0, l) for l in around(lt0) if l != lt0]
+                plans += [(1, -la0, 0), (2, -la0, -lt0)]
+                if not a.spmm_sweep:
+                    plans = [(1, la0, 0), (2, la0, lt0)]
+                for sch, la, lt in plans:
+                    def run():
+                        native.phsvds_ata_spmm(h, sch, A.m, A.n, A.nnz, rp, ci, v1, cp, ri, v2, b, X, Y, Z,
+                                               fp32=fp32, lanes_a=la, lanes_at=lt)
+                    for _ in range(3):
+                        run()
+                    ts = []
+                    for _ in range(a.spmm_reps):
+                        flush.fill_(1.0)
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        run()
+                        e1.record(stream)
+                        stream.synchronize()
+                        ts.append(e0.elapsed_time(e1))
+                    ms = float(np.mean(ts))
+                    gbs = alg / (ms * 1e-3) / 1e9
+                    out.append({"case": key, "workload": name, "m": A.m, "n": A.n, "nnz": A.nnz, "b": b,
+                                "dtype": "f32" if fp32 else "f64",
+                                "schedule": "fused-atomic" if sch == 1 else "two-phase (Z=AX, CSC)",
+                                "lanes_a": la, "lanes_at": lt if sch == 2 else None,
+                                "avg_launch_ms": ms, "min_launch_ms": float(np.min(ts)), "alg_bytes": alg,
+                                "GBps": gbs, "frac_of_hbm": gbs / hbm})
+            del A
     h.close()
     return out
 

@@ -141,16 +141,24 @@ phsvds_status phsvds_solve(phsvds_handle h, int64_t m, int64_t n, int64_t nnz,
  * schedule 1 = fused single pass with atomics (Y is overwritten: the call zeroes
  * it first), 2 = two phases through Z = A X (z: caller-provided m x b device
  * scratch) using the CSC copy (csc_ptr n+1, csc_row nnz, csc_val nnz).
- * b in {1, 2, 4, 8}.  Runs on the handle's stream; asynchronous.
+ * lanes_a: threads per row of A (fused, or the first phase), lanes_at: threads
+ * per row of A^T (second phase); each in {1, 2, 4, 8, 16}, or 0 to pick it from
+ * the mean row length nnz/m (resp. nnz/n), or the negated width to keep the
+ * 32-byte row gathers out of L1.  nnz is used for nothing else.
+ * b in {1, 2, 4, 8}.  A 32-byte aligned X with 32-byte rows (b = 4 FP64,
+ * b = 8 FP32) is gathered with 256-bit loads.  Runs on the handle's stream;
+ * asynchronous (nothing is read back).
+ * Errors: PHSVDS_ERR_INVALID (nothing launched) for bad sizes, b, schedule or
+ * lanes; PHSVDS_ERR_CUDA for a failed launch.
  */
-phsvds_status phsvds_ata_spmm_f64(phsvds_handle h, int schedule, int64_t m, int64_t n,
-                                  const int32_t* row_ptr, const int32_t* col_idx, const double* val,
+phsvds_status phsvds_ata_spmm_f64(phsvds_handle h, int schedule, int lanes_a, int lanes_at, int64_t m, int64_t n,
+                                  int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx, const double* val,
                                   const int32_t* csc_ptr, const int32_t* csc_row, const double* csc_val,
                                   int b, const double* X, double* Y, double* z);
 
 /* Same in FP32 (values, X, Y and z float). */
-phsvds_status phsvds_ata_spmm_f32(phsvds_handle h, int schedule, int64_t m, int64_t n,
-                                  const int32_t* row_ptr, const int32_t* col_idx, const float* val,
+phsvds_status phsvds_ata_spmm_f32(phsvds_handle h, int schedule, int lanes_a, int lanes_at, int64_t m, int64_t n,
+                                  int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx, const float* val,
                                   const int32_t* csc_ptr, const int32_t* csc_row, const float* csc_val,
                                   int b, const float* X, float* Y, float* z);
 

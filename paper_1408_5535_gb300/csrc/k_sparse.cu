@@ -9,12 +9,105 @@
 
 namespace ph {
 
-// One group of L lanes per sparse row.  Each pass a lane first loads U
-// (column, value) pairs of its row (streaming: the matrix is read once and
-// should not evict the gathered vectors from L2), then issues the U gathers of
-// X rows back to back, so U independent loads are in flight per lane; the B
-// partial sums are reduced inside the group at the end.
-template <typename T, int B, int L, int U>
+// 256-bit gather of one 32-byte row (8 floats or 4 doubles); p must be
+// 32-byte aligned.  Read-only path: X is not written by the kernel.  NA: do
+// not allocate the row in L1 (rows of an unstructured matrix are rarely
+// re-read by the same SM; skipping L1 keeps its lines for the index stream).
+template <typename T, int B, bool NA>
+__device__ inline void load_row_256(const T* p, T (&r)[B]) {
+  static_assert(sizeof(T) * B == 32, "32-byte rows only");
+  if constexpr (sizeof(T) == 4) {
+    if constexpr (NA)
+      asm volatile("ld.global.nc.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                   : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7])
+                   : "l"(p));
+    else
+      asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                   : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7])
+                   : "l"(p));
+  } else {
+    if constexpr (NA)
+      asm volatile("ld.global.nc.L1::no_allocate.v4.f64 {%0,%1,%2,%3}, [%4];"
+                   : "=d"(r[0]), "=d"(r[1]), "=d"(r[2]), "=d"(r[3])
+                   : "l"(p));
+    else
+      asm volatile("ld.global.nc.v4.f64 {%0,%1,%2,%3}, [%4];"
+                   : "=d"(r[0]), "=d"(r[1]), "=d"(r[2]), "=d"(r[3])
+                   : "l"(p));
+  }
+}
+
+// Loads of the matrix stream (indices, values): L1-allocating, so the
+// sector shared by consecutive slot loads of a row is fetched from L2 once,
+// with an L2 evict-first policy (the matrix is read once per product and
+// should not push the gathered rows out of L2).
+__device__ inline uint64_t l2_evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ inline int ld_stream(const int* p, uint64_t pol) {
+  int v;
+  asm volatile("ld.global.nc.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ inline float ld_stream(const float* p, uint64_t pol) {
+  float v;
+  asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ inline double ld_stream(const double* p, uint64_t pol) {
+  double v;
+  asm volatile("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+  return v;
+}
+
+// Gathers of the U rows X(col[u], :) whose slot is live; a dead slot issues
+// no load (so it costs no L1 wavefront) and contributes zeros.  W: rows are 32
+// bytes and X is 32-byte aligned -> one 256-bit load per row.
+template <typename T, int B, int U, bool W, bool NA>
+__device__ inline void gather_rows(const T* __restrict__ X, const int (&col)[U], const bool (&ok)[U], T (&x)[U][B]) {
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    if (ok[u]) {
+      if constexpr (W)
+        load_row_256<T, B, NA>(X + (size_t)col[u] * B, x[u]);
+      else
+        load_row<T, B>(X + (size_t)col[u] * B, x[u]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < B; ++q) x[u][q] = T(0);
+    }
+  }
+}
+
+// Loads U (column, value) slots of one row for this lane: slot u is entry
+// base + u*L + lane.  Every address stays inside the row (e0 < e1 here): a
+// dead slot re-reads entry e0 and is marked not live; a column index outside
+// [0, xrows) is never gathered (guard against a corrupted index).
+template <typename T, int L, int U>
+__device__ inline void load_slots(const int* __restrict__ ci, const T* __restrict__ va, int base, int lane, int e0,
+                                  int e1, int xrows, uint64_t pol, int (&col)[U], T (&v)[U], bool (&ok)[U]) {
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int e = base + u * L + lane;
+    const bool live = e < e1;
+    const int ec = live ? e : e0;
+    const int c = ld_stream(ci + ec, pol);
+    const bool inr = (unsigned)c < (unsigned)xrows;
+    ok[u] = live && inr;
+    col[u] = inr ? c : 0;
+    const T a = ld_stream(va + ec, pol);
+    v[u] = ok[u] ? a : T(0);
+  }
+}
+
+// Z = A X: one group of L lanes per sparse row.  Each pass a lane loads U
+// (column, value) slots (streaming loads: the matrix is read once and should
+// not evict the gathered rows from L2), then issues the live gathers back to
+// back so up to U independent loads are in flight per lane; the B partial
+// sums are reduced inside the group at the end.
+template <typename T, int B, int L, int U, bool W, bool NA>
 __global__ void __launch_bounds__(256) k_csr_rows(int nrows, int xrows, const int* __restrict__ rp,
                                                   const int* __restrict__ ci, const T* __restrict__ va,
                                                   const T* __restrict__ X, T* __restrict__ Z) {
@@ -25,69 +118,54 @@ __global__ void __launch_bounds__(256) k_csr_rows(int nrows, int xrows, const in
 #pragma unroll
   for (int q = 0; q < B; ++q) acc[q] = T(0);
   const int e0 = active ? rp[row] : 0, e1 = active ? rp[row + 1] : 0;
+  const uint64_t pol = l2_evict_first_policy();
   for (int base = e0; base < e1; base += L * U) {
     int col[U];
     T v[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      // every address stays inside the row (e0 < e1 here): dead slots re-read
-      // entry e0 and get the value zero
-      const int e = base + u * L + lane;
-      const bool ok = e < e1;
-      const int ec = ok ? e : e0;
-      const int c = __ldcs(ci + ec);
-      const bool inr = (unsigned)c < (unsigned)xrows;  // guard against a corrupted index
-      col[u] = inr ? c : 0;
-      v[u] = (ok && inr) ? __ldcs(va + ec) : T(0);
-    }
+    bool ok[U];
+    load_slots<T, L, U>(ci, va, base, lane, e0, e1, xrows, pol, col, v, ok);
     T x[U][B];
-#pragma unroll
-    for (int u = 0; u < U; ++u) load_row<T, B>(X + (size_t)col[u] * B, x[u]);
+    gather_rows<T, B, U, W, NA>(X, col, ok, x);
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
       for (int q = 0; q < B; ++q) acc[q] = fma(v[u], x[u][q], acc[q]);
   }
   if constexpr (L > 1) {
-    const unsigned mask = 0xffffffffu;
 #pragma unroll
     for (int o = L / 2; o > 0; o >>= 1)
 #pragma unroll
-      for (int q = 0; q < B; ++q) acc[q] += __shfl_xor_sync(mask, acc[q], o, L);
+      for (int q = 0; q < B; ++q) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o, L);
   }
   if (active && lane == 0) store_row<T, B>(Z + (size_t)row * B, acc);
 }
 
 // Fused single pass Y += A^T (A X): a group computes z = a_i^T X for its row
-// (same batched loads as above), keeps it in registers and scatters a_ij * z
-// into Y with L2 atomics (128-bit vector atomics for FP32).
-template <typename T, int B, int L, int U>
+// (same slots and gathers as above), keeps it in registers and scatters
+// a_ij * z into Y with L2 atomics (128-bit vector atomics for FP32).  A row
+// that fits in one pass (length <= L*U) scatters from the slots already in
+// registers; longer rows re-read their entries.
+template <typename T, int B, int L, int U, bool W, bool NA>
 __global__ void __launch_bounds__(256) k_ata_fused(int nrows, int xrows, const int* __restrict__ rp,
                                                    const int* __restrict__ ci, const T* __restrict__ va,
                                                    const T* __restrict__ X, T* __restrict__ Y) {
   const int lane = threadIdx.x % L;
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) / L;
-  const bool active = row < nrows;  // inactive groups still take part in the shuffles
+  const bool active = row < nrows;
   T z[B];
 #pragma unroll
   for (int q = 0; q < B; ++q) z[q] = T(0);
   const int e0 = active ? rp[row] : 0, e1 = active ? rp[row + 1] : 0;
+  int col[U];
+  T v[U];
+  bool ok[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) ok[u] = false;
+  const uint64_t pol = l2_evict_first_policy();
   for (int base = e0; base < e1; base += L * U) {
-    int col[U];
-    T v[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int e = base + u * L + lane;
-      const bool ok = e < e1;
-      const int ec = ok ? e : e0;
-      const int c = ci[ec];
-      const bool inr = (unsigned)c < (unsigned)xrows;
-      col[u] = inr ? c : 0;
-      v[u] = (ok && inr) ? va[ec] : T(0);
-    }
+    load_slots<T, L, U>(ci, va, base, lane, e0, e1, xrows, pol, col, v, ok);
     T x[U][B];
-#pragma unroll
-    for (int u = 0; u < U; ++u) load_row<T, B>(X + (size_t)col[u] * B, x[u]);
+    gather_rows<T, B, U, W, NA>(X, col, ok, x);
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
@@ -98,6 +176,17 @@ __global__ void __launch_bounds__(256) k_ata_fused(int nrows, int xrows, const i
     for (int o = L / 2; o > 0; o >>= 1)
 #pragma unroll
       for (int q = 0; q < B; ++q) z[q] += __shfl_xor_sync(0xffffffffu, z[q], o, L);
+  }
+  if (e1 - e0 <= L * U) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!ok[u]) continue;
+      T y[B];
+#pragma unroll
+      for (int q = 0; q < B; ++q) y[q] = v[u] * z[q];
+      atomic_add_row<T, B>(Y + (size_t)col[u] * B, y);
+    }
+    return;
   }
   for (int e = e0 + lane; e < e1; e += L) {
     const int c = ci[e];
@@ -113,31 +202,65 @@ __global__ void __launch_bounds__(256) k_ata_fused(int nrows, int xrows, const i
 // U (loads in flight per lane): 4, or 2 for 8-wide FP64 rows (register budget)
 template <typename T, int B> constexpr int unroll_for() { return (sizeof(T) == 8 && B == 8) ? 2 : 4; }
 
-template <typename T, int B>
-static void rows_dispatch_L(cudaStream_t s, int L, int nrows, int xrows, const int* rp, const int* ci, const T* va,
-                            const T* X, T* Z) {
+// wide (256-bit) gathers apply to 32-byte rows of a 32-byte aligned block
+template <typename T, int B> constexpr bool wide_rows() { return sizeof(T) * B == 32; }
+template <typename T> static bool aligned32(const T* p) { return ((uintptr_t)p & 31) == 0; }
+
+template <typename T, int B, bool FUSED, int L>
+static void launch_rows(cudaStream_t s, int nrows, int xrows, const int* rp, const int* ci, const T* va, const T* X,
+                        T* out, bool l1_gather) {
   const int th = 256;
   const int blocks = ceil_div((int64_t)nrows * L, th);
+  constexpr int U = unroll_for<T, B>();
+  if constexpr (wide_rows<T, B>()) {
+    if (aligned32(X)) {
+      if (l1_gather) {
+        if constexpr (FUSED)
+          k_ata_fused<T, B, L, U, true, false><<<blocks, th, 0, s>>>(nrows, xrows, rp, ci, va, X, out);
+        else
+          k_csr_rows<T, B, L, U, true, false><<<blocks, th, 0, s>>>(nrows, xrows, rp, ci, va, X, out);
+      } else {
+        if constexpr (FUSED)
+          k_ata_fused<T, B, L, U, true, true><<<blocks, th, 0, s>>>(nrows, xrows, rp, ci, va, X, out);
+        else
+          k_csr_rows<T, B, L, U, true, true><<<blocks, th, 0, s>>>(nrows, xrows, rp, ci, va, X, out);
+      }
+      count_launch();
+      return;
+    }
+  }
+  if constexpr (FUSED)
+    k_ata_fused<T, B, L, U, false, false><<<blocks, th, 0, s>>>(nrows, xrows, rp, ci, va, X, out);
+  else
+    k_csr_rows<T, B, L, U, false, false><<<blocks, th, 0, s>>>(nrows, xrows, rp, ci, va, X, out);
+  count_launch();
+}
+
+template <typename T, int B, bool FUSED>
+static void dispatch_L(cudaStream_t s, int L, int nrows, int xrows, const int* rp, const int* ci, const T* va,
+                       const T* X, T* out, bool l1) {
   if (nrows <= 0) return;
   switch (L) {
-    case 1: k_csr_rows<T, B, 1, unroll_for<T, B>()><<<blocks, th, 0, s>>>(nrows, xrows, rp, ci, va, X, Z); count_launch(); break;
-    case 2: k_csr_rows<T, B, 2, unroll_for<T, B>()><<<blocks, th, 0, s>>>(nrows, xrows, rp, ci, va, X, Z); count_launch(); break;
-    case 4: k_csr_rows<T, B, 4, unroll_for<T, B>()><<<blocks, th, 0, s>>>(nrows, xrows, rp, ci, va, X, Z); count_launch(); break;
-    default: k_csr_rows<T, B, 8, unroll_for<T, B>()><<<blocks, th, 0, s>>>(nrows, xrows, rp, ci, va, X, Z); count_launch(); break;
+    case 1: launch_rows<T, B, FUSED, 1>(s, nrows, xrows, rp, ci, va, X, out, l1); break;
+    case 2: launch_rows<T, B, FUSED, 2>(s, nrows, xrows, rp, ci, va, X, out, l1); break;
+    case 4: launch_rows<T, B, FUSED, 4>(s, nrows, xrows, rp, ci, va, X, out, l1); break;
+    case 8: launch_rows<T, B, FUSED, 8>(s, nrows, xrows, rp, ci, va, X, out, l1); break;
+    default: launch_rows<T, B, FUSED, 16>(s, nrows, xrows, rp, ci, va, X, out, l1); break;
   }
 }
 
-template <typename T, int B>
-static void fused_dispatch_L(cudaStream_t s, int L, int nrows, int xrows, const int* rp, const int* ci, const T* va,
-                             const T* X, T* Y) {
-  const int th = 256;
-  const int blocks = ceil_div((int64_t)nrows * L, th);
-  if (nrows <= 0) return;
-  switch (L) {
-    case 1: k_ata_fused<T, B, 1, unroll_for<T, B>()><<<blocks, th, 0, s>>>(nrows, xrows, rp, ci, va, X, Y); count_launch(); break;
-    case 2: k_ata_fused<T, B, 2, unroll_for<T, B>()><<<blocks, th, 0, s>>>(nrows, xrows, rp, ci, va, X, Y); count_launch(); break;
-    case 4: k_ata_fused<T, B, 4, unroll_for<T, B>()><<<blocks, th, 0, s>>>(nrows, xrows, rp, ci, va, X, Y); count_launch(); break;
-    default: k_ata_fused<T, B, 8, unroll_for<T, B>()><<<blocks, th, 0, s>>>(nrows, xrows, rp, ci, va, X, Y); count_launch(); break;
+// lanes: group width; a negative value -l means width l with the row
+// gathers not allocated in L1 (32-byte rows only).
+template <typename T, bool FUSED>
+static void dispatch_B(cudaStream_t s, int b, int lanes, const SparseView<T>& A, const T* X, T* out) {
+  const bool l1 = lanes > 0;
+  const int L = lanes > 0 ? lanes : -lanes;
+  switch (b) {
+    case 1: dispatch_L<T, 1, FUSED>(s, L, A.nrows, A.ncols, A.ptr, A.idx, A.val, X, out, l1); break;
+    case 2: dispatch_L<T, 2, FUSED>(s, L, A.nrows, A.ncols, A.ptr, A.idx, A.val, X, out, l1); break;
+    case 4: dispatch_L<T, 4, FUSED>(s, L, A.nrows, A.ncols, A.ptr, A.idx, A.val, X, out, l1); break;
+    case 8: dispatch_L<T, 8, FUSED>(s, L, A.nrows, A.ncols, A.ptr, A.idx, A.val, X, out, l1); break;
+    default: break;
   }
 }
 
@@ -149,48 +272,34 @@ int lanes_for(double avg_row) {
 }
 
 template <typename T>
-void csr_spmm(cudaStream_t s, const SparseView<T>& A, int b, const T* X, T* Z) {
+void csr_spmm(cudaStream_t s, const SparseView<T>& A, int b, const T* X, T* Z, int lanes) {
   ProfScope ps(s, PROF_SPMV);
-  const int L = lanes_for(A.avg_row());
-  switch (b) {
-    case 1: rows_dispatch_L<T, 1>(s, L, A.nrows, A.ncols, A.ptr, A.idx, A.val, X, Z); break;
-    case 2: rows_dispatch_L<T, 2>(s, L, A.nrows, A.ncols, A.ptr, A.idx, A.val, X, Z); break;
-    case 4: rows_dispatch_L<T, 4>(s, L, A.nrows, A.ncols, A.ptr, A.idx, A.val, X, Z); break;
-    case 8: rows_dispatch_L<T, 8>(s, L, A.nrows, A.ncols, A.ptr, A.idx, A.val, X, Z); break;
-    default: break;
-  }
+  dispatch_B<T, false>(s, b, lanes != 0 ? lanes : lanes_for(A.avg_row()), A, X, Z);
 }
 
 template <typename T>
-void ata_fused(cudaStream_t s, const SparseView<T>& A, int ncols, int b, const T* X, T* Y) {
+void ata_fused(cudaStream_t s, const SparseView<T>& A, int ncols, int b, const T* X, T* Y, int lanes) {
   ProfScope ps(s, PROF_CSPMM);
   cudaMemsetAsync(Y, 0, sizeof(T) * (size_t)ncols * b, s);
-  const int L = lanes_for(A.avg_row());
-  switch (b) {
-    case 1: fused_dispatch_L<T, 1>(s, L, A.nrows, A.ncols, A.ptr, A.idx, A.val, X, Y); break;
-    case 2: fused_dispatch_L<T, 2>(s, L, A.nrows, A.ncols, A.ptr, A.idx, A.val, X, Y); break;
-    case 4: fused_dispatch_L<T, 4>(s, L, A.nrows, A.ncols, A.ptr, A.idx, A.val, X, Y); break;
-    case 8: fused_dispatch_L<T, 8>(s, L, A.nrows, A.ncols, A.ptr, A.idx, A.val, X, Y); break;
-    default: break;
-  }
+  dispatch_B<T, true>(s, b, lanes != 0 ? lanes : lanes_for(A.avg_row()), A, X, Y);
 }
 
 template <typename T>
 void ata_two_phase(cudaStream_t s, const SparseView<T>& A, const SparseView<T>& At, int b, const T* X, T* Y,
-                   T* Z) {
+                   T* Z, int lanes_a, int lanes_at) {
   ProfScope ps(s, PROF_CSPMM);
-  csr_spmm<T>(s, A, b, X, Z);
-  csr_spmm<T>(s, At, b, Z, Y);
+  csr_spmm<T>(s, A, b, X, Z, lanes_a);
+  csr_spmm<T>(s, At, b, Z, Y, lanes_at);
 }
 
-template void csr_spmm<double>(cudaStream_t, const SparseView<double>&, int, const double*, double*);
-template void csr_spmm<float>(cudaStream_t, const SparseView<float>&, int, const float*, float*);
-template void ata_fused<double>(cudaStream_t, const SparseView<double>&, int, int, const double*, double*);
-template void ata_fused<float>(cudaStream_t, const SparseView<float>&, int, int, const float*, float*);
+template void csr_spmm<double>(cudaStream_t, const SparseView<double>&, int, const double*, double*, int);
+template void csr_spmm<float>(cudaStream_t, const SparseView<float>&, int, const float*, float*, int);
+template void ata_fused<double>(cudaStream_t, const SparseView<double>&, int, int, const double*, double*, int);
+template void ata_fused<float>(cudaStream_t, const SparseView<float>&, int, int, const float*, float*, int);
 template void ata_two_phase<double>(cudaStream_t, const SparseView<double>&, const SparseView<double>&, int,
-                                    const double*, double*, double*);
+                                    const double*, double*, double*, int, int);
 template void ata_two_phase<float>(cudaStream_t, const SparseView<float>&, const SparseView<float>&, int,
-                                   const float*, float*, float*);
+                                   const float*, float*, float*, int, int);
 
 // ---------------------------------------------------------------------------
 // CSR -> CSC on the device: count, scan, scatter, then sort each column by row.

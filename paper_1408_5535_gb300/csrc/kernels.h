@@ -33,10 +33,14 @@ struct ProfScope {
 };
 
 // ---- sparse (k_sparse.cu)
-template <typename T> void csr_spmm(cudaStream_t s, const SparseView<T>& A, int b, const T* X, T* Z);
-template <typename T> void ata_fused(cudaStream_t s, const SparseView<T>& A, int ncols, int b, const T* X, T* Y);
+// lanes: sparse-row group width (1, 2, 4, 8, 16); 0 picks it from the mean row
+// length; -l: width l with 32-byte row gathers that do not allocate in L1.
+template <typename T> void csr_spmm(cudaStream_t s, const SparseView<T>& A, int b, const T* X, T* Z, int lanes = 0);
 template <typename T>
-void ata_two_phase(cudaStream_t s, const SparseView<T>& A, const SparseView<T>& At, int b, const T* X, T* Y, T* Z);
+void ata_fused(cudaStream_t s, const SparseView<T>& A, int ncols, int b, const T* X, T* Y, int lanes = 0);
+template <typename T>
+void ata_two_phase(cudaStream_t s, const SparseView<T>& A, const SparseView<T>& At, int b, const T* X, T* Y, T* Z,
+                   int lanes_a = 0, int lanes_at = 0);
 template <typename T>
 void csr_to_csc(cudaStream_t s, int m, int n, int64_t nnz, const int* rp, const int* ci, const T* va, int* cp,
                 int* ri, T* cv, int* work_n);

@@ -214,46 +214,83 @@ template <typename T> struct COp {
   const SparseView<T>* At;
   T* Z;
   int n;
-  int schedule;  // 1 fused atomic, 2 two-phase
+  int schedule;      // 1 fused atomic, 2 two-phase
+  int lanes = 0;     // fused: lanes per row of A (0 = from the mean row length)
+  int lanes_a = 0;   // two-phase: lanes per row of A (Z = A X) and of A^T (Y = A^T Z)
+  int lanes_at = 0;
   mutable int64_t calls = 0;
   void apply(cudaStream_t s, int b, const T* X, T* Y) const {
     ++calls;
     if (schedule == 1)
-      ata_fused<T>(s, *A, n, b, X, Y);
+      ata_fused<T>(s, *A, n, b, X, Y, lanes);
     else
-      ata_two_phase<T>(s, *A, *At, b, X, Y, Z);
+      ata_two_phase<T>(s, *A, *At, b, X, Y, Z, lanes_a, lanes_at);
   }
 };
 
-// Pick the faster SpMM schedule for this matrix and block size by timing both.
+// Mean time (ms) of f() over 3 launches after one warm-up, on stream s.
+template <typename F>
+static float time_launches(cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, F&& f) {
+  f();
+  CUCHK(cudaEventRecord(e0, s));
+  for (int r = 0; r < 3; ++r) f();
+  CUCHK(cudaEventRecord(e1, s));
+  CUCHK(cudaEventSynchronize(e1));
+  float ms = 0;
+  CUCHK(cudaEventElapsedTime(&ms, e0, e1));
+  return ms / 3;
+}
+
+// Candidate group widths around the one picked from the mean row length;
+// for 32-byte rows also each width with the row gathers kept out of L1
+// (negative value).
+static std::vector<int> lane_candidates(double avg, bool rows32) {
+  const int l0 = lanes_for(avg);
+  std::vector<int> c;
+  for (int l : {l0 / 2, l0, l0 * 2})
+    if (l >= 1 && l <= 16 && std::find(c.begin(), c.end(), l) == c.end()) c.push_back(l);
+  if (rows32)
+    for (size_t i = 0, k = c.size(); i < k; ++i) c.push_back(-c[i]);
+  return c;
+}
+
+// The SpMM autotuner: times the fused schedule over its lane widths, each
+// phase of the two-phase schedule over its lane widths, then the best
+// two-phase pair, on this matrix and block width, and keeps the fastest.
 template <typename T>
-static int autotune_spmm(cudaStream_t s, Pool& pool, const SparseView<T>& A, const SparseView<T>& At, T* Z, int n,
-                         int b) {
+static COp<T> autotune_spmm(cudaStream_t s, Pool& pool, const SparseView<T>& A, const SparseView<T>& At, T* Z, int n,
+                            int b) {
   T* X = pool.get<T>((size_t)n * b);
   T* Y = pool.get<T>((size_t)n * b);
   fill_random<T>(s, n * b, X, 7, 0x77);
   cudaEvent_t e0, e1;
   CUCHK(cudaEventCreate(&e0));
   CUCHK(cudaEventCreate(&e1));
-  float best = 1e30f;
-  int pick = 2;
-  for (int sch = 1; sch <= 2; ++sch) {
-    COp<T> op{&A, &At, Z, n, sch};
-    op.apply(s, b, X, Y);  // warm
-    CUCHK(cudaEventRecord(e0, s));
-    for (int r = 0; r < 3; ++r) op.apply(s, b, X, Y);
-    CUCHK(cudaEventRecord(e1, s));
-    CUCHK(cudaEventSynchronize(e1));
-    float ms = 0;
-    CUCHK(cudaEventElapsedTime(&ms, e0, e1));
-    if (ms < best) {
-      best = ms;
-      pick = sch;
-    }
+  COp<T> best{&A, &At, Z, n, 2};
+  float tbest = 1e30f;
+  const bool rows32 = sizeof(T) * b == 32;
+  for (int l : lane_candidates(A.avg_row(), rows32)) {
+    COp<T> op{&A, &At, Z, n, 1, l};
+    const float t = time_launches(s, e0, e1, [&] { op.apply(s, b, X, Y); });
+    if (t < tbest) tbest = t, best = op;
   }
+  int la = 0, lat = 0;
+  float ta = 1e30f, tat = 1e30f;
+  for (int l : lane_candidates(A.avg_row(), rows32)) {
+    const float t = time_launches(s, e0, e1, [&] { csr_spmm<T>(s, A, b, X, Z, l); });
+    if (t < ta) ta = t, la = l;
+  }
+  for (int l : lane_candidates(At.avg_row(), rows32)) {
+    const float t = time_launches(s, e0, e1, [&] { csr_spmm<T>(s, At, b, Z, Y, l); });
+    if (t < tat) tat = t, lat = l;
+  }
+  COp<T> two{&A, &At, Z, n, 2, 0, la, lat};
+  const float t2 = time_launches(s, e0, e1, [&] { two.apply(s, b, X, Y); });
+  if (t2 < tbest) best = two;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  return pick;
+  best.calls = 0;
+  return best;
 }
 
 static inline int spmm_width(int nb) { return nb >= 8 ? 8 : nb >= 4 ? 4 : nb >= 2 ? 2 : 1; }
@@ -1128,13 +1165,13 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
   const int64_t launches0 = g_launch_count;
   upload_matrix(ctx, pool, A, m, n, nnz, rp, ci, va, on_dev, mixed, precond == PHSVDS_PREC_JACOBI, 8);
   // SpMM schedule
-  int sch64 = o.spmm, sch32 = o.spmm;
+  COp<double> op64{&A.A64, &A.At64, A.Z64, A.n, (int)o.spmm};
+  COp<float> op32{&A.A32, &A.At32, A.Z32, A.n, (int)o.spmm};
   if (o.spmm == PHSVDS_SPMM_AUTO) {
-    sch64 = autotune_spmm<double>(s, pool, A.A64, A.At64, A.Z64, A.n, spmm_width(b));
-    if (mixed) sch32 = autotune_spmm<float>(s, pool, A.A32, A.At32, A.Z32, A.n, spmm_width(b));
+    op64 = autotune_spmm<double>(s, pool, A.A64, A.At64, A.Z64, A.n, spmm_width(b));
+    if (mixed) op32 = autotune_spmm<float>(s, pool, A.A32, A.At32, A.Z32, A.n, spmm_width(b));
   }
-  COp<double> op64{&A.A64, &A.At64, A.Z64, A.n, sch64};
-  COp<float> op32{&A.A32, &A.At32, A.Z32, A.n, sch32};
+  const int sch64 = op64.schedule;
   if (st) {
     std::memset(st, 0, sizeof(*st));
     st->spmm_schedule = sch64;
@@ -1287,25 +1324,27 @@ static phsvds_status set_err(phsvds_ctx* c, phsvds_status st, const std::string&
 }
 
 template <typename T>
-static phsvds_status ata_api(phsvds_handle h, int schedule, int64_t m, int64_t n, const int32_t* rp, const int32_t* ci,
-                             const T* va, const int32_t* cp, const int32_t* ri, const T* cv, int b, const T* X, T* Y,
-                             T* z) {
-  if (!h || m < 1 || n < 1 || !rp || !X || !Y || (b != 1 && b != 2 && b != 4 && b != 8) ||
-      (schedule != 1 && schedule != 2) || (schedule == 2 && (!cp || !z)))
+static phsvds_status ata_api(phsvds_handle h, int schedule, int lanes_a, int lanes_at, int64_t m, int64_t n,
+                             int64_t nnz, const int32_t* rp, const int32_t* ci, const T* va, const int32_t* cp,
+                             const int32_t* ri, const T* cv, int b, const T* X, T* Y, T* z) {
+  auto lanes_ok = [](int l) {
+    const int a = l < 0 ? -l : l;
+    return a == 0 || a == 1 || a == 2 || a == 4 || a == 8 || a == 16;
+  };
+  if (!h || m < 1 || n < 1 || m > INT32_MAX || n > INT32_MAX || nnz < 0 || nnz > INT32_MAX || !rp || !X || !Y ||
+      (b != 1 && b != 2 && b != 4 && b != 8) || (schedule != 1 && schedule != 2) ||
+      (schedule == 2 && (!cp || !z)) || !lanes_ok(lanes_a) || !lanes_ok(lanes_at))
     return set_err(h, PHSVDS_ERR_INVALID, "invalid SpMM arguments");
-  // nnz from the offsets is not needed by the kernels; the views carry it for the lane choice
-  SparseView<T> A{(int)m, (int)n, 0, rp, ci, va};
-  SparseView<T> At{(int)n, (int)m, 0, cp, ri, cv};
-  int last = 0;
-  if (cudaMemcpy(&last, rp + m, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
-    return set_err(h, PHSVDS_ERR_CUDA, "cannot read row_ptr[m]");
-  A.nnz = last;
-  At.nnz = last;
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return set_err(h, PHSVDS_ERR_CUDA, cudaGetErrorString(e));
+  // nnz only picks the automatic lane width (mean row length)
+  SparseView<T> A{(int)m, (int)n, nnz, rp, ci, va};
+  SparseView<T> At{(int)n, (int)m, nnz, cp, ri, cv};
   if (schedule == 1)
-    ata_fused<T>(h->stream, A, (int)n, b, X, Y);
+    ata_fused<T>(h->stream, A, (int)n, b, X, Y, lanes_a);
   else
-    ata_two_phase<T>(h->stream, A, At, b, X, Y, z);
-  cudaError_t e = cudaGetLastError();
+    ata_two_phase<T>(h->stream, A, At, b, X, Y, z, lanes_a, lanes_at);
+  e = cudaGetLastError();
   return e == cudaSuccess ? PHSVDS_OK : set_err(h, PHSVDS_ERR_CUDA, cudaGetErrorString(e));
 }
 
@@ -1437,18 +1476,20 @@ phsvds_status phsvds_csr_to_csc_f64(phsvds_handle h, int64_t m, int64_t n, int64
   return PHSVDS_OK;
 }
 
-phsvds_status phsvds_ata_spmm_f64(phsvds_handle h, int schedule, int64_t m, int64_t n, const int32_t* row_ptr,
-                                  const int32_t* col_idx, const double* val, const int32_t* csc_ptr,
-                                  const int32_t* csc_row, const double* csc_val, int b, const double* X, double* Y,
-                                  double* z) {
-  return ata_api<double>(h, schedule, m, n, row_ptr, col_idx, val, csc_ptr, csc_row, csc_val, b, X, Y, z);
+phsvds_status phsvds_ata_spmm_f64(phsvds_handle h, int schedule, int lanes_a, int lanes_at, int64_t m, int64_t n,
+                                  int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx, const double* val,
+                                  const int32_t* csc_ptr, const int32_t* csc_row, const double* csc_val, int b,
+                                  const double* X, double* Y, double* z) {
+  return ata_api<double>(h, schedule, lanes_a, lanes_at, m, n, nnz, row_ptr, col_idx, val, csc_ptr, csc_row, csc_val,
+                         b, X, Y, z);
 }
 
-phsvds_status phsvds_ata_spmm_f32(phsvds_handle h, int schedule, int64_t m, int64_t n, const int32_t* row_ptr,
-                                  const int32_t* col_idx, const float* val, const int32_t* csc_ptr,
-                                  const int32_t* csc_row, const float* csc_val, int b, const float* X, float* Y,
-                                  float* z) {
-  return ata_api<float>(h, schedule, m, n, row_ptr, col_idx, val, csc_ptr, csc_row, csc_val, b, X, Y, z);
+phsvds_status phsvds_ata_spmm_f32(phsvds_handle h, int schedule, int lanes_a, int lanes_at, int64_t m, int64_t n,
+                                  int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx, const float* val,
+                                  const int32_t* csc_ptr, const int32_t* csc_row, const float* csc_val, int b,
+                                  const float* X, float* Y, float* z) {
+  return ata_api<float>(h, schedule, lanes_a, lanes_at, m, n, nnz, row_ptr, col_idx, val, csc_ptr, csc_row, csc_val,
+                        b, X, Y, z);
 }
 
 phsvds_status phsvds_jacobi_eig_f64(phsvds_handle h, int j, double* H, double* S, double* theta, double tol,

@@ -61,8 +61,8 @@ def _load() -> C.CDLL:
         "phsvds_default_opts": ([C.POINTER(Opts)], I),
         "phsvds_solve": ([P, I64, I64, I64, P, P, P, I, I, I, D, I, C.POINTER(Opts), P, P, P, P,
                           C.POINTER(Stats)], I),
-        "phsvds_ata_spmm_f64": ([P, I, I64, I64, P, P, P, P, P, P, I, P, P, P], I),
-        "phsvds_ata_spmm_f32": ([P, I, I64, I64, P, P, P, P, P, P, I, P, P, P], I),
+        "phsvds_ata_spmm_f64": ([P, I, I, I, I64, I64, I64, P, P, P, P, P, P, I, P, P, P], I),
+        "phsvds_ata_spmm_f32": ([P, I, I, I, I64, I64, I64, P, P, P, P, P, P, I, P, P, P], I),
         "phsvds_ata_spmm_static_f64": ([P, I64, I64, I64, P, P, P, P, P, P, I, P, P], I),
         "phsvds_csr_to_csc_f64": ([P, I64, I64, I64, P, P, P, P, P, P], I),
         "phsvds_jacobi_eig_f64": ([P, I, P, P, P, D, I, P], I),
@@ -169,11 +169,12 @@ def phsvds_solve(h: Handle, m, n, row_ptr, col_idx, val, k, target=SMALLEST, tol
     return sigma, (U.T if U is not None else None), (V.T if V is not None else None), resid, st.as_dict(), status
 
 
-def phsvds_ata_spmm(h: Handle, schedule, m, n, rp32, ci, va, cp, ri, cv, b, X, Y, z=None, fp32=False):
+def phsvds_ata_spmm(h: Handle, schedule, m, n, nnz, rp32, ci, va, cp, ri, cv, b, X, Y, z=None, fp32=False,
+                    lanes_a=0, lanes_at=0):
     """Kernel-level Y = A^T (A X) on device tensors (row-major n x b blocks)."""
     f = lib().phsvds_ata_spmm_f32 if fp32 else lib().phsvds_ata_spmm_f64
-    h.check(f(h.h, schedule, m, n, _ptr(rp32), _ptr(ci), _ptr(va), _ptr(cp), _ptr(ri), _ptr(cv), b,
-              _ptr(X), _ptr(Y), _ptr(z)))
+    h.check(f(h.h, schedule, lanes_a, lanes_at, m, n, nnz, _ptr(rp32), _ptr(ci), _ptr(va), _ptr(cp), _ptr(ri),
+              _ptr(cv), b, _ptr(X), _ptr(Y), _ptr(z)))
 
 
 # Capacity (doubles) of the fixed scratch of phsvds_ata_spmm_static_f64: m * b <= this.

@@ -40,13 +40,53 @@ def test_ata_spmm_vs_oracle(h, case, b, schedule, fp32):
     Xd = dev(X, vt)
     Yd = torch.empty((A.n, b), dtype=vt, device="cuda")
     z = torch.empty((A.m, b), dtype=vt, device="cuda")
-    native.phsvds_ata_spmm(h, schedule, A.m, A.n, d["rp"], d["ci"], d["va"], d["cp"], d["ri"], d["cv"], b, Xd, Yd,
-                           z, fp32=fp32)
+    native.phsvds_ata_spmm(h, schedule, A.m, A.n, A.nnz, d["rp"], d["ci"], d["va"], d["cp"], d["ri"], d["cv"], b,
+                           Xd, Yd, z, fp32=fp32)
     native.phsvds_sync(h)
     Y = Yd.double().cpu().numpy()
     rowmax = np.diff(A.row_ptr).max() + 2
     eps = EPS32 if fp32 else EPS64
     assert np.all(np.abs(Y - ref) <= 4 * rowmax * eps * bound + 1e-300)
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, -2, -8])
+@pytest.mark.parametrize("fp32", [False, True])
+@pytest.mark.parametrize("offset", [0, 1])
+def test_ata_spmm_lane_widths_and_narrow_gathers(h, lanes, fp32, offset):
+    """Every group width, both schedules, and 32-byte rows (b=8 FP32, b=4 FP64)
+    gathered wide (X 32-byte aligned) and narrow (X shifted by 16 bytes)."""
+    A = synth.random_sparse(3001, 1499, 12.0, 3)
+    d = device_csr(A, fp32)
+    b = 8 if fp32 else 4
+    vt = torch.float32 if fp32 else torch.float64
+    X = (synth.uniform(5, 40 + lanes, A.n * b) * 2 - 1).reshape(A.n, b)
+    ref = R.Ops(d["scipy"]).C(X)
+    absA = abs(d["scipy"])
+    bound = 4 * (np.diff(A.row_ptr).max() + 2) * (EPS32 if fp32 else EPS64) * (absA.T @ (absA @ np.abs(X)))
+    half = 16 // (4 if fp32 else 8)                    # elements in 16 bytes
+    buf = torch.empty(A.n * b + 2 * half, dtype=vt, device="cuda")
+    assert buf.data_ptr() % 32 == 0
+    Xd = buf[offset * half: offset * half + A.n * b].view(A.n, b)
+    Xd.copy_(torch.from_numpy(X).to(vt))
+    assert (Xd.data_ptr() % 32 == 0) == (offset == 0)
+    for schedule in (1, 2):
+        Yd = torch.full((A.n, b), float("nan"), dtype=vt, device="cuda")
+        z = torch.empty((A.m, b), dtype=vt, device="cuda")
+        native.phsvds_ata_spmm(h, schedule, A.m, A.n, A.nnz, d["rp"], d["ci"], d["va"], d["cp"], d["ri"], d["cv"], b,
+                               Xd, Yd, z, fp32=fp32, lanes_a=lanes, lanes_at=lanes)
+        native.phsvds_sync(h)
+        Y = Yd.double().cpu().numpy()
+        assert np.all(np.abs(Y - ref) <= bound + 1e-300), (schedule, lanes)
+
+
+def test_ata_spmm_rejects_bad_lanes(h):
+    A = synth.random_sparse(300, 100, 4.0, 3)
+    d = device_csr(A)
+    X = torch.zeros((A.n, 2), dtype=torch.float64, device="cuda")
+    Y = torch.zeros_like(X)
+    with pytest.raises(native.PhsvdsError):
+        native.phsvds_ata_spmm(h, 1, A.m, A.n, A.nnz, d["rp"], d["ci"], d["va"], d["cp"], d["ri"], d["cv"], 2, X, Y,
+                               lanes_a=3)
 
 
 def test_csr_to_csc_exact(h):

@@ -41,7 +41,8 @@ def _existing(h, A, d, b, X):
     """The same product through phsvds_ata_spmm_f64, two-phase, caller scratch."""
     Yd = torch.empty((A.n, b), dtype=torch.float64, device="cuda")
     z = torch.empty((A.m, b), dtype=torch.float64, device="cuda")
-    native.phsvds_ata_spmm(h, 2, A.m, A.n, d["rp"], d["ci"], d["va"], d["cp"], d["ri"], d["cv"], b, dev(X), Yd, z)
+    native.phsvds_ata_spmm(h, 2, A.m, A.n, A.nnz, d["rp"], d["ci"], d["va"], d["cp"], d["ri"], d["cv"], b, dev(X),
+                           Yd, z)
     native.phsvds_sync(h)
     return Yd.cpu().numpy()
 
