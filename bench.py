@@ -36,7 +36,7 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--grid", type=int, default=64, help="grid side of the weighted gradient workload")
+    p.add_argument("--grid", type=int, default=32, help="grid side of the weighted gradient workload")
     p.add_argument("--sigma-log", type=float, default=1.0)
     p.add_argument("--k", type=int, default=10)
     p.add_argument("--block", type=int, default=4)
@@ -49,6 +49,14 @@ def parse():
     p.add_argument("--spmm-cases", default="c2,c3", help="full-size SpMM workloads: c2 (512^2 grid), c3 (1e6 x 5e5)")
     p.add_argument("--spmm-reps", type=int, default=10)
     p.add_argument("--spmm-sweep", action="store_true", help="time every group width around the automatic one")
+    p.add_argument("--batched", action="store_true",
+                   help="batched workload: many uneven random sparse matrices, batched mixed vs sequential FP64")
+    p.add_argument("--batch-count", type=int, default=64)
+    p.add_argument("--batch-nlo", type=int, default=2000)
+    p.add_argument("--batch-nhi", type=int, default=60000)
+    p.add_argument("--batch-k", type=int, default=5)
+    p.add_argument("--batch-concurrency", type=int, default=0)
+    p.add_argument("--batch-no-seq", action="store_true", help="skip the sequential FP64 reference solves")
     return p.parse_args()
 
 
@@ -232,11 +240,24 @@ def spmm_full(a):
     return out
 
 
-def cpu_baseline(A, a, gpu_stats, k):
-    """Oracle (plain CPU FP64) on a bounded sample of the same solve: its stage-1
-    iterations are timed for about --cpu-seconds, and the per-iteration time is
-    scaled by the outer iterations the GPU solve needed."""
-    import numpy as np
+def golden_iters(a):
+    """The oracle's own outer-iteration count (stage 1 + stage 2) on this
+    workload, recorded by tests/golden/make_oracle_counts.py, or None."""
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "oracle_counts.json")) as f:
+            g = json.load(f).get(f"grid{a.grid}")
+    except Exception:
+        return None
+    if not g or g["k"] != a.k or g["block"] != a.block or abs(a.sigma_log - 1.0) > 0 or a.precond != "none":
+        return None
+    return g["iters_stage1"] + g["iters_stage2"]
+
+
+def cpu_baseline(A, a, k, fallback_iters):
+    """The oracle (plain CPU FP64 PHSVDS, as it stands) on the host cores, on a
+    bounded sample of the same solve: it runs for at most --cpu-seconds; if it
+    has not finished, its time per outer iteration is scaled by the oracle's
+    own recorded iteration count for the workload (else by fallback_iters)."""
     from oracle import phsvds_ref as R
     threads = os.environ.get("OMP_NUM_THREADS") or str(os.cpu_count() or 1)
 
@@ -246,7 +267,7 @@ def cpu_baseline(A, a, gpu_stats, k):
     state = {"it": 0, "t0": None}
 
     def tr(stage, it, d):
-        state["it"] = it
+        state["it"] += 1
         if time.perf_counter() - state["t0"] > a.cpu_seconds:
             raise Stop()
 
@@ -259,13 +280,14 @@ def cpu_baseline(A, a, gpu_stats, k):
         done = False
     el = time.perf_counter() - state["t0"]
     iters = max(state["it"], 1)
-    total_iters = gpu_stats["iters_stage1"] + gpu_stats["iters_stage2"]
-    est = el if done else el / iters * total_iters
+    gi = golden_iters(a)
+    total = gi if gi else fallback_iters
+    est = el if done else el / iters * total
     return {"value": k / est, "unit": "triplets/s", "cores": int(threads), "kind": "oracle",
-            "sample": (f"oracle solved the workload in {el:.1f} s" if done else
-                       f"{iters} oracle stage-1 iterations in {el:.1f} s, scaled to the "
-                       f"{total_iters} outer iterations of the GPU solve ({est:.0f} s estimated)"),
-            "seconds": el}
+            "sample": (f"the whole oracle solve of the workload ({iters} outer iterations) in {el:.1f} s" if done
+                       else f"{iters} oracle outer iterations in {el:.1f} s, scaled to "
+                            f"{'the oracle' if gi else 'the GPU solve'}'s {total} iterations ({est:.0f} s estimated)"),
+            "seconds": el, "iterations_sampled": iters, "finished": done}
 
 
 def run_ours(a, rank, world):
@@ -330,9 +352,108 @@ def run_ours(a, rank, world):
             e2e = {"value": world * a.k / (e_ms / 1e3), "unit": "triplets/s", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h, "ms_per_step": e_ms}
         results[prec] = dict(ms=ms, sigma=sig.tolist(), resid_rel=(resid / st["norm_A_est"]).tolist(), stats=st,
-                             prof=prof, e2e=e2e, clocks=clk.summary(), launches=launches // max(a.steps, 1))
+                             prof=prof, e2e=e2e, clocks=clk.summary(), launches=launches)
     h.close()
     return A, cfg, results
+
+
+# FP64 peak of one GB300 (nominal 1.25 TFLOP/s: 152 SMs x 2 FP64 FMA per clock
+# per SM x 2 flop x ~2.06 GHz); the cluster Jacobi occupies 8 of the 152 SMs.
+FP64_PEAK_GFLOPS = 1250.0
+JACOBI_CTAS = 8
+
+
+def measured_traffic(kernel_file, summary):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel's source
+    file is unchanged since the capture (its sha256 is recorded there)."""
+    import hashlib
+    try:
+        txt = open(os.path.join(ROOT, "profiles", summary)).read()
+        src = open(os.path.join(ROOT, "paper_1408_5535_gb300", "csrc", kernel_file), "rb").read()
+    except OSError:
+        return None
+    kv = dict(l.split(":", 1) for l in txt.splitlines() if ":" in l)
+    if kv.get("source_sha256", "").strip() != hashlib.sha256(src).hexdigest():
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def roofline_for(A, prof, dom, hbm, peak_kind):
+    """Roofline of the dominant kernel class of one profiled solve.
+    Cluster Jacobi: algorithmic flops per launch = 18 j per rotation (rows and
+    columns of H and the columns of S, 6 j each) x rotations per launch, against
+    the GPU's FP64 peak.  Otherwise the fused SpMM against the measured HBM copy
+    rate with the one-read-of-A byte count."""
+    if dom == 5 and prof["n_class"][5] and prof["jacobi_calls"]:
+        calls = prof["n_class"][5]
+        avg_ms = prof["t_class_ms"][5] / calls
+        j_avg = prof["jacobi_dim_sum"] / prof["jacobi_calls"]
+        rot = prof["jacobi_rotations"] / prof["jacobi_calls"]
+        flops = 18.0 * j_avg * rot
+        ach = flops / (avg_ms * 1e-3) / 1e9
+        tr = measured_traffic("k_small.cu", "jacobi_cluster_grid32.txt")
+        return {"bound": "alu", "kernel": "k_jacobi_eig_cluster (FP64, 8-CTA cluster)", "achieved": ach / 1e3,
+                "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_GFLOPS,
+                "traffic": tr, "peak_source": "nominal FP64 rate of the GPU (152 SMs x 2 FMA/clk)",
+                "frac_of_cluster_sms": ach / (FP64_PEAK_GFLOPS * JACOBI_CTAS / 152),
+                "flops_per_launch": flops, "avg_launch_ms": avg_ms, "j_avg": j_avg, "rotations_per_launch": rot}
+    calls = prof["n_class"][0]
+    avg_ms = prof["t_class_ms"][0] / calls if calls else None
+    width = prof["spmm_c_width"]
+    p_bytes = 4 if prof["iters_stage1_fp32"] > 0 else 8
+    bytes_per = spmm_bytes(A.m, A.n, A.nnz, width, p_bytes)
+    ach = bytes_per / (avg_ms * 1e-3) / 1e9 if avg_ms else None
+    return {"bound": "hbm", "kernel": "fused A^T A SpMM (products with C)", "achieved": ach, "peak": hbm,
+            "unit": "GB/s", "frac": (ach / hbm) if ach else None, "traffic": None, "peak_source": peak_kind,
+            "bytes_per_launch": bytes_per, "avg_launch_ms": avg_ms}
+
+
+def run_batched(a):
+    """Batched workload: the solves of --batch-count uneven random sparse
+    matrices (n ~ U[nlo, nhi], m ~ U[1.2n, 2n], Poisson(8) per row, N(0,1),
+    +1e-2 diagonal, seed 5), k smallest and k largest each, as two batched
+    mixed-precision calls, against the same solves one after another in FP64.
+    Wall-clock of each whole set (host buffers, the call blocks)."""
+    import numpy as np
+    import torch
+    from paper_1408_5535_gb300 import native, synth
+    mats = synth.batched_set(a.batch_count, seed=5, n_lo=a.batch_nlo, n_hi=a.batch_nhi)
+    tup = [(A.m, A.n, A.row_ptr, A.col, A.val) for A in mats]
+    h = native.Handle(0)
+    k = a.batch_k
+    om = native.default_opts(precision=native.MIXED)
+    of = native.default_opts(precision=native.FP64)
+    # warm-up: one small batched call (module load, pools)
+    native.phsvds_solve_batched(h, tup[:2], k, native.SMALLEST, TOL, native.PREC_NONE, om, concurrency=2)
+    res = {}
+    t0 = time.perf_counter()
+    for tgt in (native.SMALLEST, native.LARGEST):
+        res[tgt] = native.phsvds_solve_batched(h, tup, k, tgt, TOL, native.PREC_NONE, om,
+                                               concurrency=a.batch_concurrency)[0]
+    t_b = time.perf_counter() - t0
+    worst = max(max(o[3]) / o[4]["norm_A_est"] for tgt in res for o in res[tgt])
+    out = {"metric": "triplets/s over the batched set (k smallest + k largest per matrix)",
+           "count": len(mats), "k": k, "n_range": [a.batch_nlo, a.batch_nhi],
+           "nnz_total": int(sum(A.nnz for A in mats)), "batched_mixed_s": t_b,
+           "batched_triplets_per_s": 2 * k * len(mats) / t_b, "max_resid_over_normA": worst,
+           "concurrency": a.batch_concurrency or min(len(mats), 16),
+           "iters_total": int(sum(o[4]["iters_stage1"] + o[4]["iters_stage2"] for t in res for o in res[t]))}
+    if not a.batch_no_seq:
+        t0 = time.perf_counter()
+        diff = 0.0
+        for tgt in (native.SMALLEST, native.LARGEST):
+            for i, (m, n, rp, ci, va) in enumerate(tup):
+                sig = native.phsvds_solve(h, m, n, rp, ci, va, k, tgt, TOL, native.PREC_NONE, of,
+                                          want_vectors=False)[0]
+                diff = max(diff, float(np.max(np.abs(res[tgt][i][0] - sig) / sig)))
+        t_s = time.perf_counter() - t0
+        out.update(sequential_fp64_s=t_s, sequential_triplets_per_s=2 * k * len(mats) / t_s,
+                   speedup_batched_mixed_over_sequential_fp64=t_s / t_b, max_sigma_rel_diff_vs_sequential=diff)
+    h.close()
+    return out
 
 
 def main():
@@ -342,6 +463,10 @@ def main():
         return run_reference(a, rank, world)
     import torch
     from paper_1408_5535_gb300 import native
+    if a.batched:
+        if rank == 0:
+            print(json.dumps({"batched": run_batched(a)}), flush=True)
+        return
     if a.spmm_only:
         r = spmm_full(a)
         if rank == 0:
@@ -352,16 +477,14 @@ def main():
     r = res[head]
     st, prof = r["stats"], r["prof"]
     hbm, peak_kind = peaks()
-    # dominant kernel class of the profiled solve and the fused SpMM roofline
-    names = ["fused A^T A SpMM", "Gram / CGS2 passes", "basis transforms / Ritz", "one-CTA Jacobi eig/SVD",
-             "A / A^T products (stage 2)"]
+    names = ["fused A^T A SpMM", "Gram / CGS2 passes", "basis transforms / Ritz",
+             "small projected problems (SVD of R, Cholesky, transforms)", "A / A^T products (stage 2)",
+             "stage-1 projected eigensolver (8-CTA cluster Jacobi)"]
     cls = prof["t_class_ms"]
-    dom = int(max(range(5), key=lambda i: cls[i]))
-    p_bytes = 4 if head == native.MIXED and prof["iters_stage1_fp32"] > 0 else 8
-    calls = prof["n_class"][0]
-    avg_ms = prof["t_class_ms"][0] / calls if calls else None
-    bytes_per = spmm_bytes(A.m, A.n, A.nnz, prof["spmm_c_width"], 8)
-    achieved = bytes_per / (avg_ms * 1e-3) / 1e9 if avg_ms else None
+    dom = int(max(range(len(cls)), key=lambda i: cls[i]))
+    roof = roofline_for(A, prof, dom, hbm, peak_kind)
+    roof.update(dominant_class=names[dom], class_ms=dict(zip(names, cls)),
+                class_calls=dict(zip(names, prof["n_class"])))
     line = {
         "metric": METRIC,
         "value": world * cfg["k"] / (r["ms"] / 1e3),
@@ -375,13 +498,9 @@ def main():
         "data": "synthetic",
         "config": dict(cfg, precision="mixed" if head == native.MIXED else "fp64",
                        parallelism=f"replicas{world}"),
-        "roofline": {"bound": "hbm", "kernel": "fused A^T A SpMM (products with C)",
-                     "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": (achieved / hbm) if achieved else None, "traffic": None,
-                     "peak_source": peak_kind, "bytes_per_launch": bytes_per, "avg_launch_ms": avg_ms,
-                     "dominant_class": names[dom],
-                     "class_ms": dict(zip(names, cls)), "class_calls": dict(zip(names, prof["n_class"]))},
+        "roofline": roof,
         "gpu_launches": r["launches"],
+        "gpu_launches_per_step": r["launches"] // max(a.steps, 1),
         "clocks": r["clocks"],
         "e2e": r["e2e"],
         "solve": {"iters_stage1": st["iters_stage1"], "iters_stage1_fp32": st["iters_stage1_fp32"],
@@ -409,29 +528,27 @@ def main():
                                      "unit": "GB/s", "frac": best["GBps"] / hbm, "traffic": None,
                                      "bytes_per_launch": best["alg_bytes"], "avg_launch_ms": best["avg_launch_ms"]}
     if rank == 0 and not a.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(A, a, st, cfg["k"])
+        line["cpu_baseline"] = cpu_baseline(A, a, cfg["k"], st["iters_stage1"] + st["iters_stage2"])
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
 def run_reference(a, rank, world):
-    """The oracle (plain CPU FP64 PHSVDS) on the host cores; rank 0 only."""
+    """The oracle (plain CPU FP64 PHSVDS, as it stands) on the host cores, on the
+    same workload; rank 0 only, the other ranks exit without work."""
     if rank != 0:
         return
     A, cfg = workload(a)
-    from oracle import phsvds_ref as R
-    # each step: a bounded sample of the solve (see cpu_baseline), scaled to one solve
-    est = None
     steps = []
     for i in range(a.warmup + a.steps):
-        cb = cpu_baseline(A, a, {"iters_stage1": a.ref_iters, "iters_stage2": 0} if hasattr(a, "ref_iters")
-                          else {"iters_stage1": 20000, "iters_stage2": 2000}, cfg["k"])
+        cb = cpu_baseline(A, a, cfg["k"], fallback_iters=golden_iters(a) or 4000)
         if i >= a.warmup:
             steps.append(cb)
-    v = sum(s["value"] for s in steps) / len(steps)
+    v = sum(x["value"] for x in steps) / len(steps)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "triplets/s", "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * cfg["k"] / v, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(cfg, precision="fp64", parallelism="host cores"),
             "cpu_baseline": dict(steps[-1], value=v),
             "e2e": {"value": v, "unit": "triplets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

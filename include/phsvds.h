@@ -93,15 +93,19 @@ typedef struct {
     int64_t kernel_launches;   /* CUDA kernels this solve launched */
     /* with opts.profile: device time (CUDA events) and call counts per kernel
      * class: [0] fused A^T A SpMM (products with C), [1] Gram / CGS passes,
-     * [2] basis transforms and Ritz vectors, [3] one-CTA projected eigen/SVD
-     * problems, [4] single products with A or A^T (products with B) */
-    double t_class_ms[5];
-    int64_t n_class[5];
+     * [2] basis transforms and Ritz vectors, [3] other small projected
+     * problems (SVD of R, Cholesky, transforms), [4] single products with A or
+     * A^T (products with B), [5] the stage-1 projected eigensolver (cluster
+     * Jacobi) */
+    double t_class_ms[6];
+    int64_t n_class[6];
     int64_t spmm_c_calls;      /* C-products, each one fused A^T A SpMM launch set */
     double spmm_c_ms;          /* their summed device time (opts.profile) */
     int spmm_c_width;          /* block width of the stage-1 C-products */
     int64_t jacobi_sweeps;     /* stage-1 projected eigensolver: sweeps and rotations */
     int64_t jacobi_rotations;
+    int64_t jacobi_calls;      /* its launches, and the sum of their matrix orders j */
+    int64_t jacobi_dim_sum;
 } phsvds_stats;
 
 /* Create a context on CUDA device `device`.  cuda_stream: a cudaStream_t to run
@@ -133,6 +137,45 @@ phsvds_status phsvds_solve(phsvds_handle h, int64_t m, int64_t n, int64_t nnz,
                            phsvds_precond precond, const phsvds_opts* opts,
                            double* sigma, double* U, double* V, double* resid,
                            phsvds_stats* stats);
+
+/* One matrix of a batch: CSR as in phsvds_solve. */
+typedef struct {
+    int64_t m, n, nnz;
+    const int64_t* row_ptr;
+    const int32_t* col_idx;
+    const double* val;
+} phsvds_csr;
+
+/* One result of a batch: output buffers provided by the caller (host; sigma
+ * and resid k entries, U m x k and V n x k column-major; U, V, resid may be
+ * NULL), and what the solve reports. */
+typedef struct {
+    double* sigma;
+    double* U;
+    double* V;
+    double* resid;
+    phsvds_status status;   /* this matrix's status */
+    char message[160];      /* its phsvds_last_error() text when status != OK */
+    phsvds_stats stats;
+} phsvds_result;
+
+/*
+ * Batched form of phsvds_solve (the method of Sections 3-5 applied to many
+ * independent matrices): the `count` matrices are solved concurrently on the
+ * handle's device by `concurrency` worker threads (0 = min(count, 16)), each
+ * with its own stream and workspace, taking matrices largest (nnz) first.
+ * Every matrix gets the same k, target, tol, precond and opts as phsvds_solve,
+ * and its own autotuned SpMM plan.  ptr_on_device applies to every matrix;
+ * device inputs are read only after the work already queued on the handle's
+ * stream has finished.  Blocks until all solves are done.
+ * Returns PHSVDS_OK when every matrix converged, else the status of the first
+ * failing matrix in index order (each out[i].status and message tell which);
+ * PHSVDS_ERR_INVALID for bad arguments, PHSVDS_ERR_CUDA if no worker could
+ * create its context.
+ */
+phsvds_status phsvds_solve_batched(phsvds_handle h, int count, const phsvds_csr* mats, int ptr_on_device,
+                                   int k, phsvds_target target, double tol, phsvds_precond precond,
+                                   const phsvds_opts* opts, int concurrency, phsvds_result* out);
 
 /*
  * Kernel-level entry point: Y = A^T (A X) for a block of b vectors (Section 1,

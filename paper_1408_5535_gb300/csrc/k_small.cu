@@ -250,11 +250,10 @@ void jacobi_eig_ld(cudaStream_t s, int j, double* H, int ldh, double* S, int lds
                    int* rot_out) {
   ProfScope ps(s, PROF_SMALL);
   const size_t smem = sizeof(double) * 2 * SM_MAXJ * (SM_MAXJ + 1);
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<uint64_t> attr_done{0};
+  once_per_device(attr_done, [&] {
     cudaFuncSetAttribute(k_jacobi_eig<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+  });
   k_jacobi_eig<double><<<1, SM_THREADS, smem, s>>>(j, H, ldh, S, lds, theta, tol, max_sweeps, sweeps_out,
                                                     tol_loose, ntarget, tmode, tshift, rot_out); count_launch();
 }
@@ -449,13 +448,12 @@ __global__ void __cluster_dims__(JC_CTAS, 1, 1) __launch_bounds__(SM_THREADS)
 void jacobi_eig_cluster_ld(cudaStream_t s, int j, double* H, int ldh, double* S, int lds, double* theta, double tol,
                            int max_sweeps, int* sweeps_out, double tol_rel, int ntarget, int tmode, double tshift,
                            int* rot_out) {
-  ProfScope ps(s, PROF_SMALL);
+  ProfScope ps(s, PROF_JACOBI);
   const size_t smem = sizeof(double) * 2 * SM_MAXJ * (SM_MAXJ + 1);
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<uint64_t> attr_done{0};
+  once_per_device(attr_done, [&] {
     cudaFuncSetAttribute(k_jacobi_eig_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+  });
   k_jacobi_eig_cluster<<<JC_CTAS, SM_THREADS, smem, s>>>(j, H, ldh, S, lds, theta, tol, max_sweeps, sweeps_out,
                                                           tol_rel, ntarget, tmode, tshift, rot_out); count_launch();
 }
@@ -569,11 +567,10 @@ void jacobi_svd_ld(cudaStream_t s, int j, double* G, int ldg, double* S, int lds
                    int max_sweeps, int* sweeps_out) {
   ProfScope ps(s, PROF_SMALL);
   const size_t smem = sizeof(double) * 2 * SM_MAXJ * (SM_MAXJ + 1);
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<uint64_t> attr_done{0};
+  once_per_device(attr_done, [&] {
     cudaFuncSetAttribute(k_jacobi_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+  });
   k_jacobi_svd<<<1, SM_THREADS, smem, s>>>(j, G, ldg, S, lds, sig, tol, max_sweeps, sweeps_out); count_launch();
 }
 void jacobi_svd(cudaStream_t s, int j, double* G, double* S, double* sig, double tol, int max_sweeps,
@@ -917,11 +914,10 @@ void build_transform(cudaStream_t s, int j, const double* S, int lds, const doub
                      int ldc, int nc, int nc_a, int lim_a, int a_orth, const double* excl, int lde, int ne, int nmax,
                      double* Y, int ldy, int* jn_out, double* A2, int lda2) {
   const size_t smem = sizeof(double) * 3 * SM_MAXJ * SM_MAXJ;
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<uint64_t> attr_done{0};
+  once_per_device(attr_done, [&] {
     cudaFuncSetAttribute(k_transform, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
+  });
   k_transform<<<1, SM_THREADS, smem, s>>>(j, S, lds, A, lda, cand, ldc, nc, nc_a, lim_a, a_orth, excl, lde, ne,
                                           nmax, Y, ldy, jn_out, A2, lda2); count_launch();
 }

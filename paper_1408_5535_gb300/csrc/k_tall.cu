@@ -12,15 +12,17 @@
 
 namespace ph {
 
-static int g_num_sms = 0;
+static std::atomic<int> g_num_sms{0};
 static int num_sms() {
-  if (!g_num_sms) {
+  int v = g_num_sms.load(std::memory_order_relaxed);
+  if (!v) {
     int dev = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = 152;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    if (v <= 0) v = 152;
+    g_num_sms.store(v, std::memory_order_relaxed);
   }
-  return g_num_sms;
+  return v;
 }
 
 constexpr int CG_ROWS = 256;   // rows per chunk (one per thread in phase A)
@@ -146,12 +148,11 @@ static void cgs_launch(cudaStream_t s, int n, const Basis<T>& P, T* Tb, int ldt,
   int rows = CG_ROWS;
   while (rows > 32 && (int64_t)ceil_div(n, rows) < 2LL * num_sms()) rows >>= 1;
   const size_t smem = sizeof(T) * ((size_t)p * rows + (size_t)Q * rows + (size_t)p * Q);
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<uint64_t> attr_done{0};
+  once_per_device(attr_done, [&] {
     cudaFuncSetAttribute(k_cgs_pass<T, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)(sizeof(T) * ((size_t)CG_MAXP * CG_ROWS + 8 * CG_ROWS + CG_MAXP * 8)));
-    attr = true;
-  }
+  });
   int grid = ceil_div(n, rows);
   const int cap = num_sms() * (sizeof(T) == 8 ? 2 : 4);
   if (grid > cap) grid = cap;
@@ -229,11 +230,10 @@ void tall_times_small(cudaStream_t s, int n, const T* P, int ldp, int p, const d
   int R = TS_ROWS;
   while (R > 32 && (int64_t)ceil_div(n, R) < 2LL * num_sms()) R >>= 1;
   const size_t smem = sizeof(double) * (size_t)r + sizeof(T) * ((size_t)p * r + (size_t)p * R);
-  static bool attr = false;
-  if (!attr) {
+  static std::atomic<uint64_t> attr_done{0};
+  once_per_device(attr_done, [&] {
     cudaFuncSetAttribute(k_tall_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
+  });
   int grid = ceil_div(n, R);
   const int cap = num_sms() * 8;
   if (grid > cap) grid = cap;

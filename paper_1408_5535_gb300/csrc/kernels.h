@@ -3,7 +3,28 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
+struct phsvds_ctx;
+
 namespace ph {
+
+// Device and stream of a library handle (defined with the handle).
+int handle_device(const phsvds_ctx* h);
+cudaStream_t handle_stream(const phsvds_ctx* h);
+
+// Runs f() once per CUDA device (the current one), safely from several host
+// threads; used for per-function attributes such as the dynamic shared memory
+// limit.  Two threads may both run f(): it must be idempotent.
+template <typename F>
+inline void once_per_device(std::atomic<uint64_t>& done, F&& f) {
+  int d = 0;
+  cudaGetDevice(&d);
+  const uint64_t bit = 1ull << (d & 63);
+  if (done.load(std::memory_order_acquire) & bit) return;
+  f();
+  done.fetch_or(bit, std::memory_order_acq_rel);
+}
 
 // A CSR view: nrows rows, ptr (nrows+1), idx, val (T).  The CSC copy of A is
 // the CSR view of A^T.
@@ -21,7 +42,7 @@ int lanes_for(double avg_row);
 
 // Instrumentation (per host thread): kernel launch count, and optional CUDA
 // events around kernel classes when a solve runs with opts.profile = 1.
-enum ProfCat { PROF_CSPMM = 0, PROF_GRAM = 1, PROF_TALL = 2, PROF_SMALL = 3, PROF_SPMV = 4, PROF_NCAT = 5 };
+enum ProfCat { PROF_CSPMM = 0, PROF_GRAM = 1, PROF_TALL = 2, PROF_SMALL = 3, PROF_SPMV = 4, PROF_JACOBI = 5, PROF_NCAT = 6 };
 void count_launch();
 void prof_begin(cudaStream_t s, int cat);
 void prof_end(cudaStream_t s, int cat);

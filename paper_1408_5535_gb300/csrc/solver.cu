@@ -72,6 +72,9 @@ struct phsvds_ctx {
 
 namespace ph {
 
+int handle_device(const phsvds_ctx* h) { return h->device; }
+cudaStream_t handle_stream(const phsvds_ctx* h) { return h->stream; }
+
 // Pinned staging area of the context (readbacks of a few scalars per iteration).
 struct Host {
   phsvds_ctx* c;
@@ -87,7 +90,7 @@ void count_launch() { ++g_launch_count; }
 
 struct Profiler {
   bool on = false;
-  int depth[PROF_NCAT] = {0, 0, 0, 0, 0};
+  int depth[PROF_NCAT] = {};
   std::vector<cudaEvent_t> ev;
   std::vector<int> evcat;
   size_t used = 0;
@@ -130,9 +133,8 @@ void prof_begin(cudaStream_t s, int cat) { g_prof.mark(s, cat, true); }
 void prof_end(cudaStream_t s, int cat) { g_prof.mark(s, cat, false); }
 
 static bool trace_on() {
-  static int t = -1;
-  if (t < 0) t = getenv("PHSVDS_TRACE") ? 1 : 0;
-  return t == 1;
+  static const bool t = getenv("PHSVDS_TRACE") != nullptr;  // initialised once, thread-safe
+  return t;
 }
 
 static void sync(cudaStream_t s) {
@@ -377,7 +379,7 @@ struct Stage1Out {
   std::vector<double> lam;   // k eigenvalues of C (target order)
   double theta_max = 0.0;
   int64_t iters = 0, restarts = 0, mv = 0;
-  int64_t jac_sweeps = 0, jac_rot = 0;
+  int64_t jac_sweeps = 0, jac_rot = 0, jac_calls = 0, jac_dim = 0;
 };
 
 template <typename T>
@@ -583,6 +585,8 @@ struct Stage1 {
       out.iters++;
       out.jac_sweeps += *h.at<int>(960);
       out.jac_rot += *h.at<int>(964);
+      out.jac_calls += 1;
+      out.jac_dim += j;
       for (int i = 0; i < j; ++i) {
         ord[i] = hord[i];
         thv[i] = hth[hord[i]];
@@ -1181,7 +1185,7 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
   const auto t1a = clk::now();
   const double tol_in = TOL_MARGIN * tol;
   Stage1<double> s1(ctx, pool, A.n, k, o, largest, tol_in, EPS64, precond, A.diagC, op64);
-  int64_t iters32 = 0, mv32 = 0, jac32[2] = {0, 0};
+  int64_t iters32 = 0, mv32 = 0, jac32[4] = {0, 0, 0, 0};
   double theta_max32 = 0.0;
   if (mixed) {
     Stage1<float> s1f(ctx, pool, A.n, k, o, largest, tol_in, EPS32, precond, A.diagC, op32);
@@ -1190,6 +1194,8 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
     mv32 = s1f.out.mv;
     jac32[0] = s1f.out.jac_sweeps;
     jac32[1] = s1f.out.jac_rot;
+    jac32[2] = s1f.out.jac_calls;
+    jac32[3] = s1f.out.jac_dim;
     theta_max32 = s1f.out.theta_max;
     // continue in FP64 from the FP32 eigenvectors (promoted)
     double* X0 = pool.get<double>((size_t)A.n * k);
@@ -1281,8 +1287,8 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
                                  cudaMemcpyDeviceToHost, s));
   }
   sync(s);
-  double cls_ms[PROF_NCAT] = {0, 0, 0, 0, 0};
-  int64_t cls_n[PROF_NCAT] = {0, 0, 0, 0, 0};
+  double cls_ms[PROF_NCAT] = {};
+  int64_t cls_n[PROF_NCAT] = {};
   if (o.profile) g_prof.finish(cls_ms, cls_n);
   if (st) {
     for (int c = 0; c < PROF_NCAT; ++c) {
@@ -1295,6 +1301,8 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
     st->spmm_c_width = spmm_width(b);
     st->jacobi_sweeps = s1.out.jac_sweeps + jac32[0];
     st->jacobi_rotations = s1.out.jac_rot + jac32[1];
+    st->jacobi_calls = s1.out.jac_calls + jac32[2];
+    st->jacobi_dim_sum = s1.out.jac_dim + jac32[3];
     st->matvecs_A = mvA;
     st->matvecs_At = mvAt;
     st->iters_stage1 = s1.out.iters + iters32;

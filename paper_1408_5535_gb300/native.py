@@ -33,9 +33,10 @@ class Stats(C.Structure):
                 ("iters_stage1_fp32", C.c_int64), ("iters_stage2", C.c_int64), ("restarts", C.c_int64),
                 ("switched", C.c_int), ("norm_A_est", C.c_double), ("t_stage1_ms", C.c_double),
                 ("t_stage2_ms", C.c_double), ("t_total_ms", C.c_double), ("spmm_schedule", C.c_int),
-                ("kernel_launches", C.c_int64), ("t_class_ms", C.c_double * 5), ("n_class", C.c_int64 * 5),
+                ("kernel_launches", C.c_int64), ("t_class_ms", C.c_double * 6), ("n_class", C.c_int64 * 6),
                 ("spmm_c_calls", C.c_int64), ("spmm_c_ms", C.c_double), ("spmm_c_width", C.c_int),
-                ("jacobi_sweeps", C.c_int64), ("jacobi_rotations", C.c_int64)]
+                ("jacobi_sweeps", C.c_int64), ("jacobi_rotations", C.c_int64), ("jacobi_calls", C.c_int64),
+                ("jacobi_dim_sum", C.c_int64)]
 
     def as_dict(self) -> dict:
         d = {}
@@ -43,6 +44,16 @@ class Stats(C.Structure):
             v = getattr(self, f)
             d[f] = list(v) if hasattr(v, "__len__") else v
         return d
+
+
+class Csr(C.Structure):
+    _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.c_void_p),
+                ("col_idx", C.c_void_p), ("val", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("sigma", C.c_void_p), ("U", C.c_void_p), ("V", C.c_void_p), ("resid", C.c_void_p),
+                ("status", C.c_int), ("message", C.c_char * 160), ("stats", Stats)]
 
 
 class PhsvdsError(RuntimeError):
@@ -61,6 +72,7 @@ def _load() -> C.CDLL:
         "phsvds_default_opts": ([C.POINTER(Opts)], I),
         "phsvds_solve": ([P, I64, I64, I64, P, P, P, I, I, I, D, I, C.POINTER(Opts), P, P, P, P,
                           C.POINTER(Stats)], I),
+        "phsvds_solve_batched": ([P, I, C.POINTER(Csr), I, I, I, D, I, C.POINTER(Opts), I, C.POINTER(Result)], I),
         "phsvds_ata_spmm_f64": ([P, I, I, I, I64, I64, I64, P, P, P, P, P, P, I, P, P, P], I),
         "phsvds_ata_spmm_f32": ([P, I, I, I, I64, I64, I64, P, P, P, P, P, P, I, P, P, P], I),
         "phsvds_ata_spmm_static_f64": ([P, I64, I64, I64, P, P, P, P, P, P, I, P, P], I),
@@ -90,7 +102,7 @@ def lib() -> C.CDLL:
     return _lib
 
 
-EXPORTED = ["phsvds_create", "phsvds_default_opts", "phsvds_solve", "phsvds_ata_spmm_f64",
+EXPORTED = ["phsvds_create", "phsvds_default_opts", "phsvds_solve", "phsvds_solve_batched", "phsvds_ata_spmm_f64",
             "phsvds_ata_spmm_f32", "phsvds_ata_spmm_static_f64", "phsvds_csr_to_csc_f64", "phsvds_jacobi_eig_f64", "phsvds_jacobi_eig_cluster_f64",
             "phsvds_jacobi_svd_f64", "phsvds_sync", "phsvds_last_error", "phsvds_status_string",
             "phsvds_destroy"]
@@ -167,6 +179,40 @@ def phsvds_solve(h: Handle, m, n, row_ptr, col_idx, val, k, target=SMALLEST, tol
     if raise_on_error:
         h.check(status)
     return sigma, (U.T if U is not None else None), (V.T if V is not None else None), resid, st.as_dict(), status
+
+
+def phsvds_solve_batched(h: Handle, mats, k, target=SMALLEST, tol=1e-14, precond=PREC_NONE,
+                         opts: Opts | None = None, concurrency=0, on_device=False, want_vectors=False,
+                         raise_on_error=True):
+    """phsvds_solve_batched over a list of (m, n, row_ptr, col_idx, val) CSR
+    matrices (numpy host arrays, or torch CUDA tensors with on_device=True).
+    Returns (list of per-matrix (sigma, U, V, resid, stats, status, message),
+    overall status)."""
+    cnt = len(mats)
+    arr = (Csr * cnt)()
+    res = (Result * cnt)()
+    keep = []
+    for i, (m, n, rp, ci, va) in enumerate(mats):
+        nnz = int(rp[-1]) if isinstance(rp, np.ndarray) else int(rp[-1].item())
+        arr[i] = Csr(m, n, nnz, _ptr(rp), _ptr(ci), _ptr(va))
+        sig, rs = np.zeros(k), np.zeros(k)
+        U = np.zeros((k, m)) if want_vectors else None
+        V = np.zeros((k, n)) if want_vectors else None
+        keep.append((sig, U, V, rs))
+        res[i].sigma, res[i].resid = _ptr(sig), _ptr(rs)
+        res[i].U, res[i].V = _ptr(U), _ptr(V)
+    o = opts if opts is not None else default_opts()
+    status = lib().phsvds_solve_batched(h.h, cnt, arr, 1 if on_device else 0, k, target, tol, precond, C.byref(o),
+                                        concurrency, res)
+    if raise_on_error and status != PHSVDS_OK:
+        bad = [(i, res[i].status, res[i].message.decode()) for i in range(cnt) if res[i].status != PHSVDS_OK]
+        raise PhsvdsError(status, f"batched solve: {len(bad)} failed, first {bad[:1]}")
+    out = []
+    for i in range(cnt):
+        sig, U, V, rs = keep[i]
+        out.append((sig, U.T if U is not None else None, V.T if V is not None else None, rs,
+                    res[i].stats.as_dict(), res[i].status, res[i].message.decode()))
+    return out, status
 
 
 def phsvds_ata_spmm(h: Handle, schedule, m, n, nnz, rp32, ci, va, cp, ri, cv, b, X, Y, z=None, fp32=False,
