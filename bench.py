@@ -57,6 +57,13 @@ def parse():
     p.add_argument("--batch-k", type=int, default=5)
     p.add_argument("--batch-concurrency", type=int, default=0)
     p.add_argument("--batch-no-seq", action="store_true", help="skip the sequential FP64 reference solves")
+    p.add_argument("--learned", action="store_true",
+                   help="learned-preconditioner workload: train, then none / Jacobi / network on held-out operators")
+    p.add_argument("--learned-grid", type=int, default=32)
+    p.add_argument("--learned-train", type=int, default=200)
+    p.add_argument("--learned-test", type=int, default=10)
+    p.add_argument("--learned-epochs", type=int, default=100)
+    p.add_argument("--learned-cg-steps", type=int, default=3)
     return p.parse_args()
 
 
@@ -456,6 +463,70 @@ def run_batched(a):
     return out
 
 
+def run_learned(a):
+    """Learned-preconditioner workload: convection-diffusion operators on an
+    N x N grid (seeds 1000.. for training, 1200.. held out), k = 5 smallest at
+    tol 1e-14 ||A||; training data from the plain method's recorded residuals
+    and device-CG inner solves; time to solution per correction operator."""
+    import numpy as np
+    import torch
+    from paper_1408_5535_gb300 import learned, native, synth
+    h = native.Handle(0)
+    N = a.learned_grid
+    t0 = time.perf_counter()
+    train_ops = [synth.convdiff_stencil(N, 1000 + i) for i in range(a.learned_train)]
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    data = learned.record_samples(h, train_ops, k=5, per_op=8, every=15, cg_steps=a.learned_cg_steps)
+    t_rec = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    tr = learned.train(h, data, epochs=a.learned_epochs, batch=32, lr=2e-3)
+    t_train = time.perf_counter() - t0
+    modes = {"none": native.PREC_NONE, "jacobi": native.PREC_JACOBI, "learned": native.PREC_LEARNED}
+    res = {m: {"iters": [], "seconds": [], "resid": [], "fell_back": 0} for m in modes}
+    sig_ref = {}
+    for i in range(a.learned_test):
+        A = synth.convdiff_stencil(N, 1200 + i)
+        for name, pc in modes.items():
+            if pc == native.PREC_LEARNED:
+                o, keep = learned.solve_opts(A, tr.params_bf16)
+            else:
+                o = native.default_opts()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            sig, _, _, rs, st, status = native.phsvds_solve(h, A.m, A.n, A.row_ptr, A.col, A.val, 5,
+                                                            native.SMALLEST, TOL, pc, o, want_vectors=False,
+                                                            raise_on_error=False)
+            el = time.perf_counter() - t1
+            r = res[name]
+            r["iters"].append(int(st["iters_stage1"] + st["iters_stage2"]))
+            r["seconds"].append(el)
+            r["resid"].append(float(max(rs) / st["norm_A_est"]) if status == 0 else float("nan"))
+            r["fell_back"] += int(st["fell_back"])
+            if name == "none":
+                sig_ref[i] = sig
+            elif status == 0:
+                r.setdefault("max_sigma_rel_diff_vs_none", 0.0)
+                r["max_sigma_rel_diff_vs_none"] = max(r["max_sigma_rel_diff_vs_none"],
+                                                       float(np.max(np.abs(sig - sig_ref[i]) / sig_ref[i])))
+    summ = {}
+    for m, r in res.items():
+        summ[m] = {"mean_iters": float(np.mean(r["iters"])), "mean_seconds": float(np.mean(r["seconds"])),
+                   "max_resid_over_normA": float(np.nanmax(r["resid"])), "all_converged": bool(
+                       np.all(np.isfinite(r["resid"]))), "fell_back": r["fell_back"],
+                   "max_sigma_rel_diff_vs_none": r.get("max_sigma_rel_diff_vs_none")}
+    h.close()
+    return {"workload": f"convection-diffusion {N}x{N}, GRF diffusion, |beta| <= 20; k=5 smallest, tol 1e-14",
+            "train_ops": a.learned_train, "test_ops": a.learned_test, "samples": int(data.x.shape[0]),
+            "cg_iters_mean": float(np.mean(data.cg_iters)) if data.cg_iters else None,
+            "seconds_generate": t_gen, "seconds_record_and_inner_solves": t_rec, "seconds_train": t_train,
+            "target": f"{a.learned_cg_steps} CG steps" if a.learned_cg_steps else "converged CG (rtol 1e-6)",
+            "train_steps": tr.steps, "loss_first_epoch": tr.loss_history[0], "loss_last_epoch": tr.loss_history[-1],
+            "modes": summ,
+            "speedup_learned_over_none": summ["none"]["mean_seconds"] / summ["learned"]["mean_seconds"],
+            "speedup_learned_over_jacobi": summ["jacobi"]["mean_seconds"] / summ["learned"]["mean_seconds"]}
+
+
 def main():
     a = parse()
     rank, world = dist_init(a)
@@ -463,6 +534,10 @@ def main():
         return run_reference(a, rank, world)
     import torch
     from paper_1408_5535_gb300 import native
+    if a.learned:
+        if rank == 0:
+            print(json.dumps({"learned": run_learned(a)}), flush=True)
+        return
     if a.batched:
         if rank == 0:
             print(json.dumps({"batched": run_batched(a)}), flush=True)

@@ -51,8 +51,18 @@ typedef enum { PHSVDS_SMALLEST = 0, PHSVDS_LARGEST = 1 } phsvds_target;
 
 /* Correction operator of stage 1 (Section 4): identity (plain GD+k), or the
  * Jacobi preconditioner M = (diag(C) - theta I)^{-1}, diag(C)_j = ||A e_j||^2,
- * applied in the Olsen form t = M r - e M x, e = x^T M r / x^T M x. */
-typedef enum { PHSVDS_PREC_NONE = 0, PHSVDS_PREC_JACOBI = 1 } phsvds_precond;
+ * applied in the Olsen form t = M r - e M x, e = x^T M r / x^T M x, or the
+ * learned correction network (no counterpart in the paper: a 3-layer 3x3
+ * convolution network on the grid of a grid-structured operator, mapping
+ * [r / ||r|| * sqrt(n), feature channels] to the correction t; opts.learned_*). */
+typedef enum { PHSVDS_PREC_NONE = 0, PHSVDS_PREC_JACOBI = 1, PHSVDS_PREC_LEARNED = 2 } phsvds_precond;
+
+/* Parameters of the learned correction network: 3024 BF16 values, layer-major
+ * (16x4x3x3, 16x16x3x3, 1x16x3x3), each [out][in][row][col]. */
+#define PHSVDS_CNN_NPARAM 3024
+/* Floats of the workspace of phsvds_cnn_forward / _backward for a batch of B
+ * images of npix pixels (8-byte aligned). */
+#define PHSVDS_CNN_WORK_FLOATS(B, npix) (65 * (int64_t)(B) * (int64_t)(npix) + 2 * PHSVDS_CNN_NPARAM + 2 * (int64_t)(B))
 
 /* PHSVDS_FP64: every step in FP64.  PHSVDS_MIXED: stage 1 first runs with FP32
  * storage, FP32 SpMM and Gram products (FP64 reduction across thread blocks) to
@@ -77,6 +87,29 @@ typedef struct {
     uint64_t seed;         /* SplitMix64 seed of the random vectors the method draws */
     double time_limit_s;   /* 0 = none */
     int profile;           /* 1 = time kernel classes with CUDA events (stats.t_*_ms), default 0 */
+    /* PHSVDS_PREC_LEARNED: host pointers, copied at the start of the solve.
+     * learned_params: PHSVDS_CNN_NPARAM BF16 values; learned_features: 3 planes
+     * of n floats (log diffusion, beta_x, beta_y per grid cell); the grid is
+     * grid_nx x grid_ny = n, cell (x, y) = column y*grid_nx + x of A. */
+    const void* learned_params;
+    const float* learned_features;
+    int grid_nx, grid_ny;
+    /* learned correction falls back (to Jacobi, else none) when a window of
+     * this many stage-1 iterations neither locks a vector nor halves the
+     * smallest target residual; default 200, 0 = never */
+    int stall_window;
+    /* recording of the plain method's residuals (training data of the learned
+     * correction): every record_every-th FP64 stage-1 iteration, the residual
+     * of the first target is written to host record_r + i*n (record_max
+     * vectors at most); stats.recorded counts them.  NULL = off. */
+    double* record_r;
+    int record_max;
+    int record_every;
+    /* projected eigensolver of stage 1: 0 = FP64 Jacobi spread over an 8-CTA
+     * cluster (default), 1 = one-CTA Jacobi with each round's work compacted
+     * to its rotating pairs (same results; measured slower on GB300, where a
+     * round is bound by its serial rotation-parameter chain) */
+    int projected_solver;
 } phsvds_opts;
 
 typedef struct {
@@ -106,10 +139,16 @@ typedef struct {
     int64_t jacobi_rotations;
     int64_t jacobi_calls;      /* its launches, and the sum of their matrix orders j */
     int64_t jacobi_dim_sum;
+    int fell_back;             /* 1 if the learned correction was replaced (stall) */
+    int64_t fell_back_at;      /* stage-1 iteration of the fallback */
+    int64_t recorded;          /* residuals written to opts.record_r */
+    int64_t stage1_stagnation_locks;  /* targets locked on their rounding floor, finished by stage 2 */
 } phsvds_stats;
 
 /* Create a context on CUDA device `device`.  cuda_stream: a cudaStream_t to run
- * on, or NULL to let the library create its own. */
+ * on, or NULL to let the library create its own (an ordinary stream, ordered
+ * with the legacy default stream like one from cudaStreamCreate, so inputs
+ * written there by the caller are complete before the library reads them). */
 phsvds_status phsvds_create(phsvds_handle* out, int device, void* cuda_stream);
 
 /* Fill *opts with the defaults listed above. */
@@ -176,6 +215,53 @@ typedef struct {
 phsvds_status phsvds_solve_batched(phsvds_handle h, int count, const phsvds_csr* mats, int ptr_on_device,
                                    int k, phsvds_target target, double tol, phsvds_precond precond,
                                    const phsvds_opts* opts, int concurrency, phsvds_result* out);
+
+/*
+ * Inner solve for the training data of the learned correction (no
+ * counterpart in the paper; its corrections are Sec. 4's preconditioned
+ * ones): x_i = (A^T A - shift I)^{-1} r_i for `count` right-hand sides by
+ * conjugate gradients in FP64 on the device, up to 8 in lockstep, each to
+ * ||r - (A^T A - shift I) x|| <= rtol ||r|| or maxit iterations.
+ * shift must lie below the smallest eigenvalue of A^T A (the system SPD).
+ * A as in phsvds_solve; R and X: host, n x count column-major; iters (host,
+ * count, may be NULL) receives the iterations each needed.
+ * Errors: INVALID (bad arguments), NOT_CONVERGED (some rhs needed more than
+ * maxit; X still holds the last iterates), CUDA.
+ */
+phsvds_status phsvds_normal_cg(phsvds_handle h, int64_t m, int64_t n, int64_t nnz,
+                               const int64_t* row_ptr, const int32_t* col_idx, const double* val,
+                               int ptr_on_device, double shift, int count, const double* R, double* X,
+                               double rtol, int maxit, int* iters);
+
+/*
+ * The learned correction network on a batch of grid images (no counterpart in
+ * the paper).  All pointers DEVICE.  x: batch x 4 x ny x nx floats (planes:
+ * residual, log diffusion, beta_x, beta_y); y: batch x ny x nx floats;
+ * params: PHSVDS_CNN_NPARAM BF16; work: PHSVDS_CNN_WORK_FLOATS(batch, nx*ny)
+ * floats, 8-byte aligned, which keeps the activations for a following
+ * phsvds_cnn_backward.  FP32 arithmetic with the BF16 weights.
+ */
+phsvds_status phsvds_cnn_forward(phsvds_handle h, int batch, int nx, int ny, const void* params,
+                                 const float* x, float* y, float* work);
+
+/*
+ * Backward pass after phsvds_cnn_forward(x, y, work) with the same arguments:
+ * the loss L = (1/batch) sum_b ||y_b - t_b||^2 / ||t_b||^2 (t: batch x ny x nx
+ * targets) is ADDED to *loss (device double) and dL/dparams (FP32, at the
+ * BF16 weights) is ADDED to grad (PHSVDS_CNN_NPARAM floats).  DEVICE pointers.
+ */
+phsvds_status phsvds_cnn_backward(phsvds_handle h, int batch, int nx, int ny, const void* params,
+                                  const float* x, const float* y, const float* t, float* work,
+                                  float* grad, double* loss);
+
+/*
+ * One Adam step (Kingma & Ba) on FP32 master weights w with gradient grad and
+ * moments m, v (PHSVDS_CNN_NPARAM floats each, DEVICE), step >= 1 (bias
+ * correction), then params (BF16, DEVICE) = round-to-nearest(w); grad is
+ * zeroed for the next accumulation.
+ */
+phsvds_status phsvds_cnn_adam(phsvds_handle h, float* w, float* grad, float* m, float* v, int step,
+                              float lr, float beta1, float beta2, float eps, void* params);
 
 /*
  * Kernel-level entry point: Y = A^T (A X) for a block of b vectors (Section 1,
@@ -256,11 +342,12 @@ phsvds_status phsvds_csr_to_csc_f64(phsvds_handle h, int64_t m, int64_t n, int64
 /*
  * Kernel-level entry point: one-CTA FP64 cyclic Jacobi eigensolver for a
  * symmetric j x j matrix (the projected problem H = V^T C V of the Rayleigh-Ritz
- * step; Algorithm 2 step 7).  DEVICE pointers.  H (j x j, column-major,
+ * step; Algorithm 2 step 7), each round's work compacted to its rotating
+ * pairs.  DEVICE pointers.  H (j x j, column-major,
  * overwritten by the rotated matrix, whose diagonal holds the eigenvalues),
  * S (j x j, on entry the accumulated rotation -- identity for a cold start --
  * on exit S * J, so that S^T H_in S = diag(theta) for a cold start), theta (j).
- * 1 <= j <= 64.  Sweeps until every |h_pq| <= tol * sqrt(|h_pp h_qq|) or
+ * 1 <= j <= 64.  Sweeps until every |h_pq| <= tol * max_ij |h_ij| or
  * max_sweeps; *sweeps_out (device int) receives the sweep count.
  */
 phsvds_status phsvds_jacobi_eig_f64(phsvds_handle h, int j, double* H, double* S, double* theta,

@@ -39,18 +39,21 @@ __device__ inline void rr_pair(int jj, int r, int k, int& p, int& q) {
 // Rotation of the pair (p, q) that (nearly) annihilates a_pq.  The angle is
 // computed in FP32 from the entries scaled by 1/scale (FP64 division and square
 // root are long dependent chains on GB300's FP64 pipe); c and s are then made
-// orthonormal in FP64 (two Newton steps for c = (1 + t^2)^(-1/2), s = t c), so
-// every rotation is exact to FP64 rounding while a_pq shrinks by ~1e-7 per
-// rotation (the next sweep removes the rest).
+// orthonormal in FP64, so every rotation is exact to FP64 rounding while a_pq
+// shrinks by ~1e-7 per rotation (the next sweep removes the rest).
+// c = x^(-1/2), x = 1 + t^2, from the FP32 estimate y by one Halley step,
+// y (15 - 10 h + 3 h^2) / 8 with h = x y^2 (cubic convergence: 24 bits to
+// well past 53), then s = t c.
 __device__ inline void rot_params(double app, double aqq, double apq, double inv_scale, double& c, double& s_) {
   const float fpp = (float)(app * inv_scale), fqq = (float)(aqq * inv_scale), fpq = (float)(apq * inv_scale);
   const float ftau = (fqq - fpp) / (2.0f * fpq);
   const float ft = copysignf(1.0f, ftau) / (fabsf(ftau) + sqrtf(1.0f + ftau * ftau));
   const double t = (double)ft;
-  const double x = 1.0 + t * t;
-  double cc = (double)rsqrtf((float)x);
-  cc = cc * (1.5 - 0.5 * x * cc * cc);
-  cc = cc * (1.5 - 0.5 * x * cc * cc);
+  const double x = fma(t, t, 1.0);
+  const double y = (double)rsqrtf((float)x);
+  const double h = x * (y * y);
+  const double q = y * 0.125;
+  const double cc = q * fma(h, fma(h, 3.0, -10.0), 15.0);
   c = cc;
   s_ = t * cc;
 }
@@ -376,48 +379,68 @@ __global__ void __cluster_dims__(JC_CTAS, 1, 1) __launch_bounds__(SM_THREADS)
         for (int k2 = 0; k2 < np; ++k2) cnt += rot[k2];
         nrot += cnt;
       }
-      // this CTA's column pairs: l = crank, crank + JC_CTAS, ...
+      // this CTA's column pairs: l = crank, crank + JC_CTAS, ...; four threads
+      // per 2 x 2 block (k, l), one per output element (a, c): a thread issues
+      // 6 FP64 instructions instead of a whole block's 16, and 8 remote stores
+      // instead of 32 (one FP64 warp instruction holds a sub-partition's FP64
+      // pipe for many cycles on GB300, so instructions per warp set the time)
       const int nl = (np - crank + JC_CTAS - 1) / JC_CTAS;
-      for (int it = tid; it < np * nl; it += SM_THREADS) {
-        const int k = it % np, l = crank + (it / np) * JC_CTAS;
-        const int rk = rot[k], rl = rot[l];
-        if (!rk && !rl) continue;
-        const int pk = pp[k], qk = qq[k], pl = pp[l], ql = qq[l];
-        if (k == l) {
-          if (qk < j) {  // full 2 x 2 update J^T B J (the angle is not exact)
-            const double c = cs[k], sv = sn[k];
-            const double app = A[pk + pk * LA], aqq = A[qk + qk * LA], apq = A[pk + qk * LA];
-            const double r00 = c * app - sv * apq, r01 = c * apq - sv * aqq;
-            const double r10 = sv * app + c * apq, r11 = sv * apq + c * aqq;
-            const double n00 = c * r00 - sv * r01, n11 = sv * r10 + c * r11;
-            const double n01 = (sv * r00 + c * r01 + c * r10 - sv * r11) * 0.5;
-#pragma unroll
-            for (int r = 0; r < JC_CTAS; ++r) {
-              Ar[r][pk + pk * LA] = n00;
-              Ar[r][qk + qk * LA] = n11;
-              Ar[r][pk + qk * LA] = n01;
-              Ar[r][qk + pk * LA] = n01;
+      const int nitems = np * nl * 4;
+      // warp-uniform trip count: the four threads of a block are lanes of one
+      // warp, and every lane reads its block's inputs before any lane writes
+      // (__syncwarp between the two)
+      for (int it0 = tid & ~31; it0 < nitems; it0 += SM_THREADS) {
+        const int it = it0 + (tid & 31);
+        const int blk = it >> 2, ea = (it >> 1) & 1, ec = it & 1;
+        const int k = blk % np, l = crank + (blk / np) * JC_CTAS;
+        bool upd = false, diag = false;
+        int pk = 0, qk = 0, pl = 0, ql = 0;
+        double out = 0.0, n00 = 0.0, n11 = 0.0, n01 = 0.0;
+        if (it < nitems && (rot[k] || rot[l])) {
+          pk = pp[k];
+          qk = qq[k];
+          pl = pp[l];
+          ql = qq[l];
+          const bool vqk = qk < j, vql = ql < j;
+          if (k == l) {
+            if (vqk && ea == 0 && ec == 0) {  // full 2 x 2 update J^T B J (the angle is not exact)
+              const double c = cs[k], sv = sn[k];
+              const double app = A[pk + pk * LA], aqq = A[qk + qk * LA], apq = A[pk + qk * LA];
+              const double r00 = c * app - sv * apq, r01 = c * apq - sv * aqq;
+              const double r10 = sv * app + c * apq, r11 = sv * apq + c * aqq;
+              n00 = c * r00 - sv * r01;
+              n11 = sv * r10 + c * r11;
+              n01 = (sv * r00 + c * r01 + c * r10 - sv * r11) * 0.5;
+              diag = true;
             }
+          } else if (!((ea && !vqk) || (ec && !vql))) {  // skip outputs outside the matrix (odd j)
+            const int rk = rot[k], rl = rot[l];
+            const double ck = rk ? cs[k] : 1.0, sk = rk ? sn[k] : 0.0;
+            const double cl2 = rl ? cs[l] : 1.0, sl = rl ? sn[l] : 0.0;
+            const double b00 = A[pk + pl * LA];
+            const double b01 = vql ? A[pk + ql * LA] : 0.0;
+            const double b10 = vqk ? A[qk + pl * LA] : 0.0;
+            const double b11 = (vqk && vql) ? A[qk + ql * LA] : 0.0;
+            // rows: [p'; q'] = [c -s; s c] [p; q]; columns: [p' q'] = [p q] [c s; -s c]
+            const double ra0 = ea ? sk * b00 + ck * b10 : ck * b00 - sk * b10;
+            const double ra1 = ea ? sk * b01 + ck * b11 : ck * b01 - sk * b11;
+            out = ec ? sl * ra0 + cl2 * ra1 : cl2 * ra0 - sl * ra1;
+            upd = true;
           }
-          continue;
         }
-        const double ck = rk ? cs[k] : 1.0, sk = rk ? sn[k] : 0.0;
-        const double cl2 = rl ? cs[l] : 1.0, sl = rl ? sn[l] : 0.0;
-        const bool vqk = qk < j, vql = ql < j;
-        const double b00 = A[pk + pl * LA];
-        const double b01 = vql ? A[pk + ql * LA] : 0.0;
-        const double b10 = vqk ? A[qk + pl * LA] : 0.0;
-        const double b11 = (vqk && vql) ? A[qk + ql * LA] : 0.0;
-        const double r00 = ck * b00 - sk * b10, r01 = ck * b01 - sk * b11;
-        const double r10 = sk * b00 + ck * b10, r11 = sk * b01 + ck * b11;
-        const double n00 = cl2 * r00 - sl * r01, n01 = sl * r00 + cl2 * r01;
-        const double n10 = cl2 * r10 - sl * r11, n11 = sl * r10 + cl2 * r11;
+        __syncwarp();
+        if (diag) {
 #pragma unroll
-        for (int r = 0; r < JC_CTAS; ++r) {
-          Ar[r][pk + pl * LA] = n00;
-          if (vql) Ar[r][pk + ql * LA] = n01;
-          if (vqk) Ar[r][qk + pl * LA] = n10;
-          if (vqk && vql) Ar[r][qk + ql * LA] = n11;
+          for (int r = 0; r < JC_CTAS; ++r) {
+            Ar[r][pk + pk * LA] = n00;
+            Ar[r][qk + qk * LA] = n11;
+            Ar[r][pk + qk * LA] = n01;
+            Ar[r][qk + pk * LA] = n01;
+          }
+        } else if (upd) {
+          const int ri = ea ? qk : pk, cj = ec ? ql : pl;
+#pragma unroll
+          for (int r = 0; r < JC_CTAS; ++r) Ar[r][ri + cj * LA] = out;
         }
       }
       // the rows of S this CTA owns
@@ -465,6 +488,203 @@ void jacobi_eig32_ld(cudaStream_t s, int j, const double* H, int ldh, double* Sf
   k_jacobi_eig<float><<<1, SM_THREADS, smem, s>>>(j, const_cast<double*>(H), ldh, Sf, lds, theta, tol, max_sweeps,
                                                    sweeps_out, tol, 0, 0, 0.0, rot_out); count_launch();
 }
+// ---------------------------------------------------------------------------
+// The same two-sided Jacobi (same pairing, thresholds, targets and update
+// formulas) in one CTA with each round's work compacted:
+//  * the rotation parameters of the round's pairs are spread over 4 warps
+//    (one per SM sub-partition): pair k is lane k/4 of warp k%4;
+//  * only the 2 x 2 blocks (k, l) with a rotating pair are updated, the
+//    upper triangle of them (k rotating; (l, k) written as the transpose),
+//    packed densely into as few warps as possible;
+//  * S is updated for the rotating pairs only;
+//  * a round has two CTA barriers and no cluster barrier.
+// Measured on GB300 it is no faster than the 8-CTA cluster kernel (about
+// 0.6 ms against 0.55 ms per stage-1 call at j ~ 27): a round is bound by
+// the serial chain of its rotation parameters and barriers, not by the
+// update flops, so it is the kernel-level one-CTA entry point and an option
+// of the solver, not its default.
+// Pair k has the bit position (k % 4) * 8 + k / 4 in the round's mask M.
+// ---------------------------------------------------------------------------
+__device__ inline int jf_pair_of_bit(int b) { return (b & 7) * 4 + (b >> 3); }
+__device__ inline int jf_bit_of_pair(int k) { return (k & 3) * 8 + (k >> 2); }
+
+__global__ void __launch_bounds__(SM_THREADS)
+    k_jacobi_eig_fast(int j, double* H, int ldh, double* S, int lds, double* theta, double tol, int max_sweeps,
+                      int* sweeps_out, double tol_rel, int ntarget, int tmode, double tshift, int* rot_out) {
+  extern __shared__ __align__(16) double dsm[];
+  double* A = dsm;                              // [SM_MAXJ * (SM_MAXJ + 1)]
+  double* Sm = A + SM_MAXJ * (SM_MAXJ + 1);
+  __shared__ double cs[SM_MAXJ / 2], sn[SM_MAXJ / 2];
+  __shared__ int pp[SM_MAXJ / 2], qq[SM_MAXJ / 2];
+  __shared__ unsigned pmask[2][4];  // by round parity: a round without rotations skips the closing barrier
+  __shared__ unsigned char is_t[SM_MAXJ];
+  __shared__ double scale_s;
+  __shared__ double wmx[SM_THREADS / 32];
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int LA = SM_MAXJ + 1;
+  for (int e = tid; e < j * j; e += SM_THREADS) {
+    const int r = e % j, c = e / j;
+    A[r + c * LA] = H[r + (size_t)c * ldh];
+    Sm[r + c * LA] = S[r + (size_t)c * lds];
+  }
+  __syncthreads();
+  double mx = 0.0;
+  for (int e = tid; e < j * j; e += SM_THREADS) mx = fmax(mx, fabs(A[(e % j) + (e / j) * LA]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) wmx[w] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    double m2 = 0.0;
+    for (int k = 0; k < SM_THREADS / 32; ++k) m2 = fmax(m2, wmx[k]);
+    scale_s = m2;
+  }
+  __syncthreads();
+  const double thr_t = tol * scale_s;
+  const double inv_scale = scale_s > 0.0 ? 1.0 / scale_s : 1.0;
+  const double rel = ntarget > 0 ? tol_rel : 0.0;
+  auto need = [&](int p, int q, double apq) -> bool {
+    if (is_t[p] | is_t[q]) return fabs(apq) > thr_t;
+    if (rel == 0.0) return fabs(apq) > thr_t;
+    const float r2 =
+        (float)rel * sqrtf(fabsf((float)(A[p + p * LA] * inv_scale) * (float)(A[q + q * LA] * inv_scale)));
+    return fabs(apq) > fmax((double)r2 * scale_s, thr_t);
+  };
+  const int jj = j + (j & 1);
+  const int np = jj / 2;
+  int sweep = 0, nrot = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tid < j) {
+      int rr = 1;
+      if (ntarget > 0) {
+        auto key = [&](int t2) {
+          const double d = A[t2 + t2 * LA];
+          return tmode == 0 ? d : (tmode == 1 ? -d : fabs(d - tshift));
+        };
+        const double ki = key(tid);
+        int rank = 0;
+        for (int t2 = 0; t2 < j; ++t2) {
+          const double kt = key(t2);
+          if (kt < ki || (kt == ki && t2 < tid)) ++rank;
+        }
+        rr = rank < ntarget;
+      }
+      is_t[tid] = (unsigned char)rr;
+    }
+    __syncthreads();
+    int any = 0;
+    for (int e = tid; e < j * j; e += SM_THREADS) {
+      const int r = e % j, c = e / j;
+      if (r < c && need(r, c, A[r + c * LA])) any = 1;
+    }
+    if (!__syncthreads_or(any)) break;
+    for (int round = 0; round < jj - 1; ++round) {
+      bool mine = false;
+      if (w < 4 && lane < 8) {
+        const int k = lane * 4 + w;
+        if (k < np) {
+          int p, q;
+          rr_pair(jj, round, k, p, q);
+          pp[k] = p;
+          qq[k] = q;
+          if (q < j) {
+            const double apq = A[p + q * LA];
+            if (need(p, q, apq)) {
+              double c, sv;
+              rot_params(A[p + p * LA], A[q + q * LA], apq, inv_scale, c, sv);
+              cs[k] = c;
+              sn[k] = sv;
+              mine = true;
+            }
+          }
+        }
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, mine);
+      unsigned* pm = pmask[round & 1];
+      if (w < 4 && lane == 0) pm[w] = bal & 0xffu;
+      __syncthreads();
+      const unsigned M = pm[0] | (pm[1] << 8) | (pm[2] << 16) | (pm[3] << 24);
+      if (M == 0) continue;  // the same M in every thread
+      const int nr = __popc(M);
+      if (tid == 0) nrot += nr;
+      // 2 x 2 blocks (k, l), k rotating: rows of pair k, columns of pair l
+      for (int it = tid; it < nr * np; it += SM_THREADS) {
+        const int a = it / np, l = it % np;
+        const int k = jf_pair_of_bit(__fns(M, 0, a + 1));
+        const int bl = jf_bit_of_pair(l);
+        const bool rl = (M >> bl) & 1u;
+        if (rl && __popc(M & ((1u << bl) - 1u)) < a) continue;  // (l, k) is the transpose of a done block
+        const int pk = pp[k], qk = qq[k], pl = pp[l], ql = qq[l];
+        const double ck = cs[k], sk = sn[k];
+        if (l == k) {  // full 2 x 2 update J^T B J (the angle is not exact)
+          const double app = A[pk + pk * LA], aqq = A[qk + qk * LA], apq = A[pk + qk * LA];
+          const double r00 = ck * app - sk * apq, r01 = ck * apq - sk * aqq;
+          const double r10 = sk * app + ck * apq, r11 = sk * apq + ck * aqq;
+          const double n00 = ck * r00 - sk * r01, n11 = sk * r10 + ck * r11;
+          const double n01 = (sk * r00 + ck * r01 + ck * r10 - sk * r11) * 0.5;
+          A[pk + pk * LA] = n00;
+          A[qk + qk * LA] = n11;
+          A[pk + qk * LA] = n01;
+          A[qk + pk * LA] = n01;
+          continue;
+        }
+        const double cl2 = rl ? cs[l] : 1.0, sl = rl ? sn[l] : 0.0;
+        const bool vql = ql < j;
+        const double b00 = A[pk + pl * LA];
+        const double b01 = vql ? A[pk + ql * LA] : 0.0;
+        const double b10 = A[qk + pl * LA];
+        const double b11 = vql ? A[qk + ql * LA] : 0.0;
+        const double r00 = ck * b00 - sk * b10, r01 = ck * b01 - sk * b11;
+        const double r10 = sk * b00 + ck * b10, r11 = sk * b01 + ck * b11;
+        const double n00 = cl2 * r00 - sl * r01, n01 = sl * r00 + cl2 * r01;
+        const double n10 = cl2 * r10 - sl * r11, n11 = sl * r10 + cl2 * r11;
+        A[pk + pl * LA] = n00;
+        A[qk + pl * LA] = n10;
+        A[pl + pk * LA] = n00;
+        A[pl + qk * LA] = n10;
+        if (vql) {
+          A[pk + ql * LA] = n01;
+          A[qk + ql * LA] = n11;
+          A[ql + pk * LA] = n01;
+          A[ql + qk * LA] = n11;
+        }
+      }
+      // S <- S J on the columns of the rotating pairs (packed from warp 7 down,
+      // so they share the sub-partitions with the fewest block updates)
+      for (int it = SM_THREADS - 1 - tid; it < nr * j; it += SM_THREADS) {
+        const int a = it / j, row = it % j;
+        const int k = jf_pair_of_bit(__fns(M, 0, a + 1));
+        const int p = pp[k], q = qq[k];
+        const double sp = Sm[row + p * LA], sq = Sm[row + q * LA];
+        Sm[row + p * LA] = cs[k] * sp - sn[k] * sq;
+        Sm[row + q * LA] = sn[k] * sp + cs[k] * sq;
+      }
+      __syncthreads();
+    }
+  }
+  for (int e = tid; e < j * j; e += SM_THREADS) {
+    const int r = e % j, c = e / j;
+    H[r + (size_t)c * ldh] = A[r + c * LA];
+    S[r + (size_t)c * lds] = Sm[r + c * LA];
+  }
+  for (int i = tid; i < j; i += SM_THREADS) theta[i] = A[i + i * LA];
+  if (tid == 0 && sweeps_out) sweeps_out[0] = sweep;
+  if (tid == 0 && rot_out) rot_out[0] = nrot;
+}
+
+void jacobi_eig_fast_ld(cudaStream_t s, int j, double* H, int ldh, double* S, int lds, double* theta, double tol,
+                        int max_sweeps, int* sweeps_out, double tol_rel, int ntarget, int tmode, double tshift,
+                        int* rot_out) {
+  ProfScope ps(s, PROF_JACOBI);
+  const size_t smem = sizeof(double) * 2 * SM_MAXJ * (SM_MAXJ + 1);
+  static std::atomic<uint64_t> attr_done{0};
+  once_per_device(attr_done, [&] {
+    cudaFuncSetAttribute(k_jacobi_eig_fast, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  k_jacobi_eig_fast<<<1, SM_THREADS, smem, s>>>(j, H, ldh, S, lds, theta, tol, max_sweeps, sweeps_out, tol_rel,
+                                                ntarget, tmode, tshift, rot_out);
+  count_launch();
+}
+
 void jacobi_eig(cudaStream_t s, int j, double* H, double* S, double* theta, double tol, int max_sweeps,
                 int* sweeps_out) {
   jacobi_eig_ld(s, j, H, j, S, j, theta, tol, max_sweeps, sweeps_out, tol, 0, 0, 0.0, nullptr);
@@ -731,10 +951,16 @@ void symmetrise(cudaStream_t s, int j, double* A, int lda) {
 }
 
 // Sort order of theta (j <= 64): mode 0 ascending, 1 descending, 2 ascending |theta - shift|.
+// A NaN key ranks last (as +inf, ties by index), so order is always a
+// permutation of 0..j-1 even when the values are not finite: the gathers that
+// read it never see an unwritten slot (the host rejects the NaN afterwards).
 __global__ void k_order(int j, const double* __restrict__ th, int mode, double shift, int* __restrict__ order) {
   const int i = threadIdx.x;
   if (i >= j) return;
-  auto key = [&](int t) { return mode == 0 ? th[t] : (mode == 1 ? -th[t] : fabs(th[t] - shift)); };
+  auto key = [&](int t) {
+    const double k = mode == 0 ? th[t] : (mode == 1 ? -th[t] : fabs(th[t] - shift));
+    return isnan(k) ? INFINITY : k;
+  };
   const double ki = key(i);
   int rank = 0;
   for (int t = 0; t < j; ++t) {
@@ -747,18 +973,29 @@ void order_theta(cudaStream_t s, int j, const double* th, int mode, double shift
   k_order<<<1, SM_MAXJ, 0, s>>>(j, th, mode, shift, order); count_launch();
 }
 
-// out[:, c] = S[:, idx[c]] (j rows), th_out[c] = th[idx[c]]
+// out[:, c] = S[:, idx[c]] (j rows), th_out[c] = th[idx[c]].  An index
+// outside [0, j) (a corrupted ordering) is not followed: column 0 is read
+// instead and *bad (when given) is set, for the host to reject the step.
 __global__ void k_gather(int j, const double* __restrict__ S, int lds, const int* __restrict__ idx, int nc,
-                         double* __restrict__ out, int ldo, const double* __restrict__ th, double* __restrict__ th_out) {
+                         double* __restrict__ out, int ldo, const double* __restrict__ th, double* __restrict__ th_out,
+                         int* __restrict__ bad) {
   for (int e = threadIdx.x; e < j * nc; e += blockDim.x) {
     const int r = e % j, c = e / j;
-    out[r + (size_t)c * ldo] = S[r + (size_t)idx[c] * lds];
+    int ic = idx[c];
+    if ((unsigned)ic >= (unsigned)j) {
+      if (bad) *bad = 1;
+      ic = 0;
+    }
+    out[r + (size_t)c * ldo] = S[r + (size_t)ic * lds];
   }
-  if (th && threadIdx.x < nc) th_out[threadIdx.x] = th[idx[threadIdx.x]];
+  if (th && threadIdx.x < nc) {
+    const int ic = idx[threadIdx.x];
+    th_out[threadIdx.x] = th[(unsigned)ic < (unsigned)j ? ic : 0];
+  }
 }
 void gather_cols(cudaStream_t s, int j, const double* S, int lds, const int* idx, int nc, double* out, int ldo,
-                 const double* th, double* th_out) {
-  k_gather<<<1, SM_THREADS, 0, s>>>(j, S, lds, idx, nc, out, ldo, th, th_out); count_launch();
+                 const double* th, double* th_out, int* bad) {
+  k_gather<<<1, SM_THREADS, 0, s>>>(j, S, lds, idx, nc, out, ldo, th, th_out, bad); count_launch();
 }
 
 // ---------------------------------------------------------------------------

@@ -7,6 +7,8 @@
 // product accumulates per thread in T and across thread blocks in FP64.
 // On GB300 the FP64 variants are bound by the FP64 pipe (~1.2 TFLOP/s), the
 // FP32 variants by HBM bandwidth.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -441,5 +443,114 @@ template void fill_const<float>(cudaStream_t, int64_t, float, float*);
   template void col_norms2_dense<T>(cudaStream_t, int, const T*, int, int, double*);
 PH_INST(double)
 PH_INST(float)
+
+}  // namespace ph
+
+namespace ph {
+
+// ---------------------------------------------------------------------------
+// Conjugate gradients on (A^T A - shift I) x = r for up to 8 right-hand sides
+// in lockstep: row-major n x b blocks, per-column FP64 scalars on the device
+// (rr = ||r||^2, rrn = the next ||r||^2, pq = p^T q, act = still iterating).
+// ---------------------------------------------------------------------------
+template <int B>
+__device__ inline void block_reduce_add(double (&v)[B], double* out, int b) {
+  __shared__ double red[8][B];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < B; ++c) v[c] = warp_sum(v[c]);
+  if (lane == 0)
+#pragma unroll
+    for (int c = 0; c < B; ++c) red[w][c] = v[c];
+  __syncthreads();
+  if (threadIdx.x < b) {
+    double s = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += red[k][threadIdx.x];
+    atomicAdd(out + threadIdx.x, s);
+  }
+}
+
+// q <- q - shift p; pq[c] += p_c^T q_c
+__global__ void __launch_bounds__(256) k_cg_pq(int n, int b, double shift, const double* __restrict__ P,
+                                               double* __restrict__ Q, double* __restrict__ pq) {
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    for (int c = 0; c < b; ++c) {
+      const size_t k = (size_t)i * b + c;
+      const double q = Q[k] - shift * P[k];
+      Q[k] = q;
+      acc[c] += P[k] * q;
+    }
+  block_reduce_add<8>(acc, pq, b);
+}
+
+// alpha = rr / pq; x += alpha p; r -= alpha q; rrn[c] += ||r_c||^2
+__global__ void __launch_bounds__(256) k_cg_update(int n, int b, const double* __restrict__ P,
+                                                   const double* __restrict__ Q, double* __restrict__ X,
+                                                   double* __restrict__ R, const double* __restrict__ rr,
+                                                   const double* __restrict__ pq, const int* __restrict__ act,
+                                                   double* __restrict__ rrn) {
+  double al[8], acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int c = 0; c < b; ++c) al[c] = (act[c] && pq[c] > 0.0) ? rr[c] / pq[c] : 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    for (int c = 0; c < b; ++c) {
+      const size_t k = (size_t)i * b + c;
+      X[k] += al[c] * P[k];
+      const double r = R[k] - al[c] * Q[k];
+      R[k] = r;
+      acc[c] += r * r;
+    }
+  block_reduce_add<8>(acc, rrn, b);
+}
+
+// beta = rrn / rr; p = r + beta p (active columns)
+__global__ void __launch_bounds__(256) k_cg_dir(int n, int b, const double* __restrict__ R, double* __restrict__ P,
+                                                const double* __restrict__ rr, const double* __restrict__ rrn,
+                                                const int* __restrict__ act) {
+  double be[8];
+  for (int c = 0; c < b; ++c) be[c] = (act[c] && rr[c] > 0.0) ? rrn[c] / rr[c] : 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    for (int c = 0; c < b; ++c) {
+      if (!act[c]) continue;
+      const size_t k = (size_t)i * b + c;
+      P[k] = R[k] + be[c] * P[k];
+    }
+}
+
+// per column: count the iteration, rr <- rrn, stop when rr <= tol2 rr0 (or a
+// non-positive curvature p^T q <= 0), clear the accumulators
+__global__ void k_cg_next(int b, double* rr, double* rrn, const double* rr0, double tol2, double* pq, int* act,
+                          int* iters, int* bad) {
+  const int c = threadIdx.x;
+  if (c >= b) return;
+  if (act[c]) {
+    iters[c] += 1;
+    if (!(pq[c] > 0.0)) bad[0] = 1;
+    rr[c] = rrn[c];
+    act[c] = (pq[c] > 0.0 && rrn[c] > tol2 * rr0[c]) ? 1 : 0;
+  }
+  rrn[c] = 0.0;
+  pq[c] = 0.0;
+}
+
+void cg_pq(cudaStream_t s, int n, int b, double shift, const double* P, double* Q, double* pq) {
+  k_cg_pq<<<std::min(ceil_div(n, 256), 4 * num_sms()), 256, 0, s>>>(n, b, shift, P, Q, pq);
+  count_launch();
+}
+void cg_update(cudaStream_t s, int n, int b, const double* P, const double* Q, double* X, double* R,
+               const double* rr, const double* pq, const int* act, double* rrn) {
+  k_cg_update<<<std::min(ceil_div(n, 256), 4 * num_sms()), 256, 0, s>>>(n, b, P, Q, X, R, rr, pq, act, rrn);
+  count_launch();
+}
+void cg_dir(cudaStream_t s, int n, int b, const double* R, double* P, const double* rr, const double* rrn,
+            const int* act) {
+  k_cg_dir<<<std::min(ceil_div(n, 256), 4 * num_sms()), 256, 0, s>>>(n, b, R, P, rr, rrn, act);
+  count_launch();
+}
+void cg_next(cudaStream_t s, int b, double* rr, double* rrn, const double* rr0, double tol2, double* pq, int* act,
+             int* iters, int* bad) {
+  k_cg_next<<<1, 32, 0, s>>>(b, rr, rrn, rr0, tol2, pq, act, iters, bad);
+  count_launch();
+}
 
 }  // namespace ph

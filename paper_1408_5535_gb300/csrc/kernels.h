@@ -159,6 +159,11 @@ void jacobi_eig_ld(cudaStream_t s, int j, double* H, int ldh, double* S, int lds
 void jacobi_eig_cluster_ld(cudaStream_t s, int j, double* H, int ldh, double* S, int lds, double* theta, double tol,
                            int max_sweeps, int* sweeps_out, double tol_rel, int ntarget, int tmode, double tshift,
                            int* rot_out);
+// Same as jacobi_eig_ld in one CTA with the round's work compacted to the
+// rotating pairs (shaped for GB300's narrow FP64 pipe).
+void jacobi_eig_fast_ld(cudaStream_t s, int j, double* H, int ldh, double* S, int lds, double* theta, double tol,
+                        int max_sweeps, int* sweeps_out, double tol_rel, int ntarget, int tmode, double tshift,
+                        int* rot_out);
 // FP32 bulk pass: Sf (FP64 out) = the FP32 Jacobi rotation diagonalising H to
 // ~tol * ||H||; H is not modified.
 void jacobi_eig32_ld(cudaStream_t s, int j, const double* H, int ldh, double* Sf, int lds, double* theta, double tol,
@@ -167,8 +172,9 @@ void jacobi_svd_ld(cudaStream_t s, int j, double* G, int ldg, double* S, int lds
                    int max_sweeps, int* sweeps_out);
 void frame_append(cudaStream_t s, int j0, int nb, double* A, int lda, double* S, int lds, const double* Hn);
 void order_theta(cudaStream_t s, int j, const double* th, int mode, double shift, int* order);
+// bad (device int, may be null) is set when an index lies outside [0, j)
 void gather_cols(cudaStream_t s, int j, const double* S, int lds, const int* idx, int nc, double* out, int ldo,
-                 const double* th, double* th_out);
+                 const double* th, double* th_out, int* bad = nullptr);
 void build_transform(cudaStream_t s, int j, const double* S, int lds, const double* A, int lda, const double* cand,
                      int ldc, int nc, int nc_a, int lim_a, int a_orth, const double* excl, int lde, int ne, int nmax,
                      double* Y, int ldy, int* jn_out, double* A2, int lda2);
@@ -180,5 +186,28 @@ void refined_vector(cudaStream_t s, int j, const double* SR, int ldr, const doub
                     const double* A, int lda, double* s1_out, double* out);
 void qr_column(cudaStream_t s, int c, const double* g1, const double* g2, const double* tnorm2, double* R, int ldr,
                double* G, int ldg, double* SR, int ldsr, double* minv, int update_g);
+
+// ---- conjugate gradients on (A^T A - shift I) x = r, up to 8 rhs in lockstep (k_tall.cu)
+void cg_pq(cudaStream_t s, int n, int b, double shift, const double* P, double* Q, double* pq);
+void cg_update(cudaStream_t s, int n, int b, const double* P, const double* Q, double* X, double* R,
+               const double* rr, const double* pq, const int* act, double* rrn);
+void cg_dir(cudaStream_t s, int n, int b, const double* R, double* P, const double* rr, const double* rrn,
+            const int* act);
+void cg_next(cudaStream_t s, int b, double* rr, double* rrn, const double* rr0, double tol2, double* pq, int* act,
+             int* iters, int* bad);
+
+// ---- learned correction network (k_cnn.cu)
+constexpr int CNN_NPARAM_H = 3024;
+void cnn_weights(cudaStream_t s, const void* params_bf16, float* wf, float* wt);
+void cnn_forward(cudaStream_t s, int B, int nx, int ny, const float* wf, const float* x, float* a1, float* a2,
+                 float* y);
+void cnn_backward(cudaStream_t s, int B, int nx, int ny, const float* wt, const float* x, const float* a1,
+                  const float* a2, const float* y, const float* t, float* g3, float* g2, float* g1, double* tn2,
+                  float* grad, double* loss);
+void cnn_adam(cudaStream_t s, float* w, float* grad, float* m, float* v, int step, float lr, float b1, float b2,
+              float eps, void* params_bf16);
+template <typename T>
+void cnn_pack(cudaStream_t s, int n, int nb, const T* R, int ldr, const double* norms2, const float* feat, float* x);
+template <typename T> void cnn_unpack(cudaStream_t s, int n, int nb, const float* y, T* Tb, int ldt);
 
 }  // namespace ph

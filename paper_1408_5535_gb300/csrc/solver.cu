@@ -28,6 +28,10 @@ constexpr double JAC_TOL = 5e-17;         // Jacobi threshold for pairs touching
 constexpr double TOL_MARGIN = 0.9;        // stopping tests use 0.9 delta: the residual the test sees and an
                                           // independent recomputation differ by rounding of order eps ||C||
 constexpr double JAC_REL = 1e-8;          // relative threshold of the other pairs (they span the restart space)
+constexpr int W_REFRESH = 16;             // stage-1 restarts between recomputations of W = C V
+constexpr double STAG_NEAR = 2.0;         // stage-1 stagnation: residual within 2x of its tolerance ...
+constexpr double STAG_RATIO = 100.0;      // ... or within 100x for STAG_LONG iterations without halving
+constexpr int64_t STAG_LONG = 2000;
 
 struct PhError {
   phsvds_status st;
@@ -380,6 +384,17 @@ struct Stage1Out {
   double theta_max = 0.0;
   int64_t iters = 0, restarts = 0, mv = 0;
   int64_t jac_sweeps = 0, jac_rot = 0, jac_calls = 0, jac_dim = 0;
+  int fell_back = 0;
+  int64_t fell_back_at = 0, recorded = 0, stag_locks = 0;
+};
+
+// Device state of the learned correction (PHSVDS_PREC_LEARNED) for one solve.
+struct LearnedDev {
+  const float* feat = nullptr;  // 3 planes of n floats
+  int nx = 0, ny = 0;
+  float *wf = nullptr, *wt = nullptr, *xin = nullptr, *a1 = nullptr, *a2 = nullptr, *yout = nullptr;
+  double* nrm2 = nullptr;
+  int stall_window = 0;
 };
 
 template <typename T>
@@ -396,6 +411,7 @@ struct Stage1 {
   uint64_t seed;
   int max_restarts;
   double time_limit_s;
+  bool cluster_eig;
   std::chrono::steady_clock::time_point t0;
   // device
   T *V, *W, *Xl, *Tb, *Xrm, *Yrm, *Xr, *Rr, *XU;
@@ -406,6 +422,19 @@ struct Stage1 {
   int j = 0, nlock = 0, nsp = 0, rand_ctr = 0;
   bool s_ident = true;
   Stage1Out out;
+  // learned correction: stall watch (progress = a lock or a halved smallest
+  // target residual within stall_window iterations)
+  const LearnedDev* lp = nullptr;
+  int64_t stall_it0 = 0;
+  double stall_best = 0.0;
+  int stall_locks = -1;
+  // stagnation watch of the stage-1 targets
+  double stag_best = INFINITY;
+  int64_t stag_it = 0;
+  int stag_window = 50;
+  // residual recording (FP64 pass only)
+  double* rec_r = nullptr;
+  int rec_max = 0, rec_every = 0;
 
   Stage1(phsvds_ctx* c, Pool& p, int n_, int k_, const phsvds_opts& o, bool largest_, double delta_, double eps,
          int precond_, const double* diag, COp<T> op_)
@@ -419,6 +448,8 @@ struct Stage1 {
     seed = o.seed;
     max_restarts = o.max_restarts;
     time_limit_s = o.time_limit_s;
+    cluster_eig = o.projected_solver == 0;
+    stag_window = std::max(100, 6 * (maxb - mins));
     const size_t nn = (size_t)n;
     V = pool.get<T>(nn * maxb);
     W = pool.get<T>(nn * maxb);
@@ -459,6 +490,7 @@ struct Stage1 {
     jn = pool.get<int>(4);
     idx = pool.get<int>(2 * LD);
     zero(s, sprev, LD * 8);
+    zero(s, flags, 48);
   }
 
   void check_time() {
@@ -566,11 +598,12 @@ struct Stage1 {
       if (nb > 0) expand(nb);
       frame_from_true(s, j, Ht, S, Aw, w1, w2, s_ident ? -1 : 1);
       s_ident = false;
-      jacobi_eig_cluster_ld(s, j, Aw, LD, S, LD, theta, JAC_TOL, 60, flags + 12, JAC_REL,
-                            std::min(b, k - nlock) + 1, largest ? 1 : 0, 0.0, flags + 13);
+      (cluster_eig ? jacobi_eig_cluster_ld : jacobi_eig_fast_ld)(s, j, Aw, LD, S, LD, theta, JAC_TOL, 60, flags + 12,
+                                                                 JAC_REL, std::min(b, k - nlock) + 1,
+                                                                 largest ? 1 : 0, 0.0, flags + 13);
       order_theta(s, j, theta, largest ? 1 : 0, 0.0, order);
       const int nt = std::min(std::min(b, k - nlock), j);
-      gather_cols(s, j, S, LD, order, nt, Scols, LD, theta, thcols);
+      gather_cols(s, j, S, LD, order, nt, Scols, LD, theta, thcols, flags + 14);
       tall_times_small<T>(s, n, V, n, j, Scols, LD, nt, Xr, n, nullptr, 0, nullptr, nullptr);
       zero(s, norms, nt);
       tall_times_small<T>(s, n, W, n, j, Scols, LD, nt, Rr, n, Xr, n, thcols, norms);
@@ -583,6 +616,7 @@ struct Stage1 {
       CUCHK(cudaMemcpyAsync(h.at<int>(960), flags + 12, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
       sync(s);
       out.iters++;
+      if (*h.at<int>(968)) throw PhError{PHSVDS_ERR_NAN, "stage 1: corrupted ordering of the Ritz values"};
       out.jac_sweeps += *h.at<int>(960);
       out.jac_rot += *h.at<int>(964);
       out.jac_calls += 1;
@@ -594,15 +628,58 @@ struct Stage1 {
         out.theta_max = std::max(out.theta_max, thv[i]);
       }
       std::vector<int> conv, unconv;
+      double best_ratio = INFINITY;
+      int best_t = -1;
       for (int t = 0; t < nt; ++t) {
         const double rn = std::sqrt(std::max(hn[t], 0.0));
         if (!std::isfinite(rn)) throw PhError{PHSVDS_ERR_NAN, "stage 1: non-finite residual"};
-        (rn < tol_of(thv[t], out.theta_max) ? conv : unconv).push_back(t);
+        const double tl = tol_of(thv[t], out.theta_max);
+        (rn < tl ? conv : unconv).push_back(t);
+        if (rn >= tl && rn / tl < best_ratio) best_ratio = rn / tl, best_t = t;
+      }
+      // Stage 1 stops at the accuracy it can attain (Sec. 3.1): a target whose
+      // residual has stopped halving sits on the rounding floor of the
+      // products with C -- within STAG_NEAR of its tolerance for a window of
+      // iterations, or within STAG_RATIO for STAG_LONG iterations; it is
+      // locked, and the switch test hands it to stage 2.
+      if (!conv.empty() || best_t < 0) {
+        stag_best = INFINITY;
+        stag_it = out.iters;
+      } else if (best_ratio < 0.5 * stag_best) {
+        stag_best = best_ratio;
+        stag_it = out.iters;
+      } else if ((best_ratio < STAG_NEAR && out.iters - stag_it >= stag_window) ||
+                 (best_ratio < STAG_RATIO && out.iters - stag_it >= STAG_LONG)) {
+        conv.push_back(best_t);
+        unconv.erase(std::find(unconv.begin(), unconv.end(), best_t));
+        ++out.stag_locks;
+        stag_best = INFINITY;
+        stag_it = out.iters;
       }
       if (trace_on())
         fprintf(stderr, "s1[%d] it=%lld j=%d nlock=%d th0=%.17g rn0=%.6e thmax=%.6e nconv=%d\n", (int)sizeof(T),
                 (long long)out.iters, j, nlock, thv[0], std::sqrt(std::max(hn[0], 0.0)), out.theta_max,
                 (int)conv.size());
+      if (rec_r && rec_every > 0 && out.recorded < rec_max && out.iters % rec_every == 0 && nt > 0) {
+        if constexpr (sizeof(T) == 8) {
+          CUCHK(cudaMemcpyAsync(rec_r + (size_t)out.recorded * n, Rr, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+          sync(s);
+          ++out.recorded;
+        }
+      }
+      if (precond == PHSVDS_PREC_LEARNED && lp && lp->stall_window > 0 && nt > 0) {
+        double cur = INFINITY;
+        for (int t = 0; t < nt; ++t) cur = std::min(cur, std::sqrt(std::max(hn[t], 0.0)));
+        if (nlock + (int)conv.size() > stall_locks || cur < 0.5 * stall_best) {
+          stall_locks = nlock + (int)conv.size();
+          stall_best = cur;
+          stall_it0 = out.iters;
+        } else if (out.iters - stall_it0 >= lp->stall_window) {
+          precond = diagC ? PHSVDS_PREC_JACOBI : PHSVDS_PREC_NONE;
+          out.fell_back = 1;
+          out.fell_back_at = out.iters;
+        }
+      }
       for (int t : conv) {
         CUCHK(cudaMemcpyAsync(Xl + (size_t)nlock * n, Xr + (size_t)t * n, sizeof(T) * n, cudaMemcpyDeviceToDevice, s));
         out.lam.push_back(thv[t]);
@@ -626,6 +703,14 @@ struct Stage1 {
         if (precond == PHSVDS_PREC_JACOBI)
           CUCHK(cudaMemcpyAsync(XU + (size_t)c * n, Xr + (size_t)unconv[c] * n, sizeof(T) * n,
                                 cudaMemcpyDeviceToDevice, s));
+      }
+      if (precond == PHSVDS_PREC_LEARNED && lp && nu > 0) {
+        double* hu2 = h.at<double>(1088);    // bytes [1088, 1152): ||r||^2 of the corrected columns
+        for (int c = 0; c < nu; ++c) hu2[c] = std::max(hn[unconv[c]], 0.0);
+        CUCHK(cudaMemcpyAsync(lp->nrm2, hu2, sizeof(double) * nu, cudaMemcpyHostToDevice, s));
+        cnn_pack<T>(s, n, nu, Tb, n, lp->nrm2, lp->feat, lp->xin);
+        cnn_forward(s, nu, lp->nx, lp->ny, lp->wf, lp->xin, lp->a1, lp->a2, lp->yout);
+        cnn_unpack<T>(s, n, nu, lp->yout, Tb, n);
       }
       if (precond == PHSVDS_PREC_JACOBI && nu > 0) {
         double* hu = h.at<double>(1024);     // bytes [1024, 1088)
@@ -664,9 +749,13 @@ struct Stage1 {
           CUCHK(cudaMemcpyAsync(h.at<int>(12288), jn, sizeof(int), cudaMemcpyDeviceToHost, s));
           sync(s);
           jnew = *h.at<int>(12288);
+          if (jnew < 1 || jnew > maxb) throw PhError{PHSVDS_ERR_BREAKDOWN, "stage 1: restart basis size out of range"};
         }
         tall_times_small<T>(s, n, V, n, j, Yt, LD, jnew, V, n, nullptr, 0, nullptr, nullptr);
-        tall_times_small<T>(s, n, W, n, j, Yt, LD, jnew, W, n, nullptr, 0, nullptr, nullptr);
+        if (restart && out.restarts % W_REFRESH == 0)
+          apply_C(0, jnew);  // W = C V afresh: W <- W Y drifts from C V by rounding at every restart
+        else
+          tall_times_small<T>(s, n, W, n, j, Yt, LD, jnew, W, n, nullptr, 0, nullptr, nullptr);
         gram_full<T>(s, n, V, W, jnew, Ht, w1);
         set_identity(s, jnew, S, LD);
         s_ident = true;
@@ -1077,6 +1166,7 @@ struct Stage2 {
         CUCHK(cudaMemcpyAsync(h.at<int>(12288), jn, sizeof(int), cudaMemcpyDeviceToHost, s));
         sync(s);
         const int jnew = *h.at<int>(12288);
+        if (jnew < 1 || jnew > maxb) throw PhError{PHSVDS_ERR_BREAKDOWN, "stage 2: restart basis size out of range"};
         transform(jnew);
         // s1 is the first new basis vector
         double* hs = h.at<double>(10240);    // bytes [10240, 10752)
@@ -1167,7 +1257,27 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
   Pool pool(s);
   DevA A;
   const int64_t launches0 = g_launch_count;
-  upload_matrix(ctx, pool, A, m, n, nnz, rp, ci, va, on_dev, mixed, precond == PHSVDS_PREC_JACOBI, 8);
+  upload_matrix(ctx, pool, A, m, n, nnz, rp, ci, va, on_dev, mixed, precond != PHSVDS_PREC_NONE, 8);
+  // learned correction: network weights (FP32 from BF16) and feature planes on the device
+  LearnedDev ld;
+  if (precond == PHSVDS_PREC_LEARNED) {
+    void* pdev = pool.get<uint16_t>(3024);
+    CUCHK(cudaMemcpyAsync(pdev, o.learned_params, sizeof(uint16_t) * 3024, cudaMemcpyHostToDevice, s));
+    float* feat = pool.get<float>((size_t)3 * A.n);
+    CUCHK(cudaMemcpyAsync(feat, o.learned_features, sizeof(float) * 3 * A.n, cudaMemcpyHostToDevice, s));
+    ld.feat = feat;
+    ld.nx = o.grid_nx;
+    ld.ny = o.grid_ny;
+    ld.wf = pool.get<float>(3024);
+    ld.wt = pool.get<float>(3024);
+    ld.xin = pool.get<float>((size_t)8 * 4 * A.n);
+    ld.a1 = pool.get<float>((size_t)8 * 16 * A.n);
+    ld.a2 = pool.get<float>((size_t)8 * 16 * A.n);
+    ld.yout = pool.get<float>((size_t)8 * A.n);
+    ld.nrm2 = pool.get<double>(8);
+    ld.stall_window = o.stall_window;
+    cnn_weights(s, pdev, ld.wf, ld.wt);
+  }
   // SpMM schedule
   COp<double> op64{&A.A64, &A.At64, A.Z64, A.n, (int)o.spmm};
   COp<float> op32{&A.A32, &A.At32, A.Z32, A.n, (int)o.spmm};
@@ -1185,11 +1295,41 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
   const auto t1a = clk::now();
   const double tol_in = TOL_MARGIN * tol;
   Stage1<double> s1(ctx, pool, A.n, k, o, largest, tol_in, EPS64, precond, A.diagC, op64);
-  int64_t iters32 = 0, mv32 = 0, jac32[4] = {0, 0, 0, 0};
+  s1.lp = &ld;
+  s1.rec_r = o.record_r;
+  s1.rec_max = o.record_r ? o.record_max : 0;
+  s1.rec_every = o.record_every;
+  int64_t iters32 = 0, mv32 = 0, jac32[4] = {0, 0, 0, 0}, stag32 = 0;
   double theta_max32 = 0.0;
+  // on a stage-1 error the counters so far still reach the caller
+  auto partial_stats = [&](const Stage1Out& a, const Stage1Out* b32) {
+    if (!st) return;
+    st->iters_stage1 = a.iters + (b32 ? b32->iters : 0);
+    st->iters_stage1_fp32 = b32 ? b32->iters : 0;
+    st->restarts = a.restarts + (b32 ? b32->restarts : 0);
+    st->matvecs_A = st->matvecs_At = a.mv + (b32 ? b32->mv : 0);
+    st->recorded = a.recorded;
+    st->fell_back = a.fell_back | (b32 ? b32->fell_back : 0);
+    st->fell_back_at = b32 && b32->fell_back ? b32->fell_back_at : a.fell_back_at;
+    st->norm_A_est = std::sqrt(std::max(a.theta_max, b32 ? b32->theta_max : 0.0));
+    st->kernel_launches = g_launch_count - launches0;
+    st->t_stage1_ms = std::chrono::duration<double, std::milli>(clk::now() - t1a).count();
+    st->t_total_ms = std::chrono::duration<double, std::milli>(clk::now() - tstart).count();
+  };
   if (mixed) {
     Stage1<float> s1f(ctx, pool, A.n, k, o, largest, tol_in, EPS32, precond, A.diagC, op32);
-    s1f.run(nullptr, 0);
+    s1f.lp = &ld;
+    try {
+      s1f.run(nullptr, 0);
+    } catch (const PhError&) {
+      partial_stats(s1.out, &s1f.out);
+      throw;
+    }
+    if (s1f.out.fell_back) {
+      s1.precond = s1f.precond;  // the FP64 continuation keeps the fallback
+      s1.out.fell_back = 1;
+      s1.out.fell_back_at = s1f.out.fell_back_at;
+    }
     iters32 = s1f.out.iters;
     mv32 = s1f.out.mv;
     jac32[0] = s1f.out.jac_sweeps;
@@ -1197,14 +1337,27 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
     jac32[2] = s1f.out.jac_calls;
     jac32[3] = s1f.out.jac_dim;
     theta_max32 = s1f.out.theta_max;
+    stag32 = s1f.out.stag_locks;
     // continue in FP64 from the FP32 eigenvectors (promoted)
     double* X0 = pool.get<double>((size_t)A.n * k);
     convert_f32_to_f64(s, (int64_t)A.n * k, s1f.Xl, X0);
     s1.out.restarts = s1f.out.restarts;
     s1.out.theta_max = s1f.out.theta_max;  // the ||C|| estimate carries over
-    s1.run(X0, k);
+    try {
+      s1.run(X0, k);
+    } catch (const PhError&) {
+      Stage1Out f = s1f.out;
+      f.restarts = 0;  // already carried into s1
+      partial_stats(s1.out, &f);
+      throw;
+    }
   } else {
-    s1.run(nullptr, 0);
+    try {
+      s1.run(nullptr, 0);
+    } catch (const PhError&) {
+      partial_stats(s1.out, nullptr);
+      throw;
+    }
   }
   sync(s);
   const auto t1b = clk::now();
@@ -1311,6 +1464,10 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
     st->restarts = s1.out.restarts + rs2;
     st->switched = need2 && o.stage2;
     st->norm_A_est = normA;
+    st->fell_back = s1.out.fell_back;
+    st->fell_back_at = s1.out.fell_back_at;
+    st->recorded = s1.out.recorded;
+    st->stage1_stagnation_locks = s1.out.stag_locks + stag32;
     st->t_stage1_ms = std::chrono::duration<double, std::milli>(t1b - t1a).count();
     st->t_stage2_ms = t2ms;
     st->t_total_ms = std::chrono::duration<double, std::milli>(clk::now() - tstart).count();
@@ -1372,6 +1529,14 @@ phsvds_status phsvds_default_opts(phsvds_opts* o) {
   o->seed = 0;
   o->time_limit_s = 0.0;
   o->profile = 0;
+  o->learned_params = nullptr;
+  o->learned_features = nullptr;
+  o->grid_nx = o->grid_ny = 0;
+  o->stall_window = 200;
+  o->record_r = nullptr;
+  o->record_max = 0;
+  o->record_every = 0;
+  o->projected_solver = 0;
   return PHSVDS_OK;
 }
 
@@ -1386,7 +1551,9 @@ phsvds_status phsvds_create(phsvds_handle* out, int device, void* stream) {
   if (stream) {
     c->stream = static_cast<cudaStream_t>(stream);
   } else {
-    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    // an ordinary stream: ordered with the legacy default stream, so work the
+    // caller queued there (input preparation) completes before the library's
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamDefault) != cudaSuccess) {
       delete c;
       return PHSVDS_ERR_CUDA;
     }
@@ -1450,8 +1617,15 @@ phsvds_status phsvds_solve(phsvds_handle h, int64_t m, int64_t n, int64_t nnz, c
   if (o.block_size < 1 || o.block_size > 8 || o.max_basis < 4 || o.max_basis + 8 > LD ||
       o.min_restart < 2 * std::min(o.block_size, k) || o.min_restart >= o.max_basis || !(tol > 0) ||
       o.max_restarts < 1 || (target != PHSVDS_SMALLEST && target != PHSVDS_LARGEST) ||
-      (precond != PHSVDS_PREC_NONE && precond != PHSVDS_PREC_JACOBI) || o.max_basis > n)
+      (precond != PHSVDS_PREC_NONE && precond != PHSVDS_PREC_JACOBI && precond != PHSVDS_PREC_LEARNED) ||
+      o.max_basis > n)
     return set_err(h, PHSVDS_ERR_INVALID, "invalid options (block 1..8, 2b <= min_restart < max_basis <= min(n,56))");
+  if (precond == PHSVDS_PREC_LEARNED &&
+      (!o.learned_params || !o.learned_features || o.grid_nx < 1 || o.grid_ny < 1 ||
+       (int64_t)o.grid_nx * o.grid_ny != n || o.stall_window < 0))
+    return set_err(h, PHSVDS_ERR_INVALID, "learned correction needs params, features and grid_nx * grid_ny = n");
+  if (o.record_r && (o.record_max < 0 || o.record_every < 1))
+    return set_err(h, PHSVDS_ERR_INVALID, "recording needs record_max >= 0 and record_every >= 1");
   try {
     CUCHK(cudaSetDevice(h->device));
     solve_impl(h, m, n, nnz, row_ptr, col_idx, val, ptr_on_device, k, target, tol, precond, o, sigma, U, V, resid,
@@ -1503,7 +1677,7 @@ phsvds_status phsvds_ata_spmm_f32(phsvds_handle h, int schedule, int lanes_a, in
 phsvds_status phsvds_jacobi_eig_f64(phsvds_handle h, int j, double* H, double* S, double* theta, double tol,
                                     int max_sweeps, int* sweeps_out) {
   if (!h || j < 1 || j > LD || !H || !S || !theta) return PHSVDS_ERR_INVALID;
-  jacobi_eig(h->stream, j, H, S, theta, tol, max_sweeps, sweeps_out);
+  jacobi_eig_fast_ld(h->stream, j, H, j, S, j, theta, tol, max_sweeps, sweeps_out, tol, 0, 0, 0.0, nullptr);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? PHSVDS_OK : set_err(h, PHSVDS_ERR_CUDA, cudaGetErrorString(e));
 }
@@ -1575,4 +1749,82 @@ extern "C" phsvds_status phsvds_ata_spmm_static_f64(phsvds_handle h, int64_t m, 
   ata_two_phase<double>(h->stream, A, At, b, X, Y, z);
   e = cudaGetLastError();
   return e == cudaSuccess ? PHSVDS_OK : set_err(h, PHSVDS_ERR_CUDA, cudaGetErrorString(e));
+}
+
+// ===========================================================================
+// Inner solves for the training data of the learned correction: CG on the
+// normal operator, up to 8 right-hand sides in lockstep.
+// ===========================================================================
+extern "C" phsvds_status phsvds_normal_cg(phsvds_handle h, int64_t m, int64_t n, int64_t nnz, const int64_t* row_ptr,
+                                          const int32_t* col_idx, const double* val, int ptr_on_device, double shift,
+                                          int count, const double* R, double* X, double rtol, int maxit, int* iters) {
+  if (!h || m < 1 || n < 1 || m < n || nnz < 0 || !row_ptr || count < 1 || !R || !X || !(rtol > 0) || maxit < 1 ||
+      !std::isfinite(shift))
+    return set_err(h, PHSVDS_ERR_INVALID, "invalid CG arguments");
+  phsvds_status result = PHSVDS_OK;
+  try {
+    CUCHK(cudaSetDevice(h->device));
+    cudaStream_t s = h->stream;
+    Pool pool(s);
+    DevA A;
+    upload_matrix(h, pool, A, m, n, nnz, row_ptr, col_idx, val, ptr_on_device, false, false, 8);
+    COp<double> op{&A.A64, &A.At64, A.Z64, A.n, 2};
+    const size_t nn = (size_t)n;
+    double* cm = pool.get<double>(nn * 8);   // column-major staging
+    double *Xb = pool.get<double>(nn * 8), *Rb = pool.get<double>(nn * 8), *Pb = pool.get<double>(nn * 8),
+           *Qb = pool.get<double>(nn * 8);
+    double* sc = pool.get<double>(32);       // rr | rrn | rr0 | pq
+    int* ic = pool.get<int>(32);             // act | iters | bad
+    Host hb(h);
+    for (int c0 = 0; c0 < count; c0 += 8) {
+      const int bw = std::min(8, count - c0);
+      const int b = bw <= 1 ? 1 : bw <= 2 ? 2 : bw <= 4 ? 4 : 8;  // SpMM widths; extra columns stay zero
+      zero(s, cm, nn * b);
+      CUCHK(cudaMemcpyAsync(cm, R + (size_t)c0 * n, sizeof(double) * nn * bw, cudaMemcpyHostToDevice, s));
+      cm_to_rm<double>(s, (int)n, cm, (int)n, b, Rb);
+      CUCHK(cudaMemcpyAsync(Pb, Rb, sizeof(double) * nn * b, cudaMemcpyDeviceToDevice, s));
+      zero(s, Xb, nn * b);
+      zero(s, sc, 32);
+      CUCHK(cudaMemsetAsync(ic, 0, sizeof(int) * 32, s));
+      // rr0 = rr = ||r||^2 (through the update kernel with alpha = 0: act = 0)
+      cg_update(s, (int)n, b, Pb, Pb, Xb, Rb, sc, sc + 24, ic, sc);
+      CUCHK(cudaMemcpyAsync(sc + 16, sc, sizeof(double) * 8, cudaMemcpyDeviceToDevice, s));
+      int* ha = hb.at<int>(0);
+      for (int c = 0; c < 8; ++c) ha[c] = c < bw ? 1 : 0;
+      CUCHK(cudaMemcpyAsync(ic, ha, sizeof(int) * 8, cudaMemcpyHostToDevice, s));
+      sync(s);
+      const double tol2 = rtol * rtol;
+      int it = 0;
+      while (it < maxit) {
+        op.apply(s, b, Pb, Qb);
+        cg_pq(s, (int)n, b, shift, Pb, Qb, sc + 24);
+        cg_update(s, (int)n, b, Pb, Qb, Xb, Rb, sc, sc + 24, ic, sc + 8);
+        cg_dir(s, (int)n, b, Rb, Pb, sc, sc + 8, ic);
+        cg_next(s, b, sc, sc + 8, sc + 16, tol2, sc + 24, ic, ic + 8, ic + 16);
+        ++it;
+        if (it % 10 == 0 || it == maxit) {
+          CUCHK(cudaMemcpyAsync(ha, ic, sizeof(int) * 24, cudaMemcpyDeviceToHost, s));
+          sync(s);
+          if (ha[16]) throw PhError{PHSVDS_ERR_INVALID, "CG: A^T A - shift I is not positive definite"};
+          bool any = false;
+          for (int c = 0; c < b; ++c) any = any || ha[c];
+          if (!any) break;
+        }
+      }
+      CUCHK(cudaMemcpyAsync(ha, ic, sizeof(int) * 24, cudaMemcpyDeviceToHost, s));
+      rm_to_cm<double>(s, (int)n, Xb, b, cm, (int)n);
+      CUCHK(cudaMemcpyAsync(X + (size_t)c0 * n, cm, sizeof(double) * nn * bw, cudaMemcpyDeviceToHost, s));
+      sync(s);
+      for (int c = 0; c < bw; ++c) {
+        if (iters) iters[c0 + c] = ha[8 + c];
+        if (ha[c]) result = PHSVDS_ERR_NOT_CONVERGED;
+      }
+    }
+  } catch (const PhError& e) {
+    cudaStreamSynchronize(h->stream);
+    cudaGetLastError();
+    return set_err(h, e.st, e.msg);
+  }
+  if (result != PHSVDS_OK) set_err(h, result, "CG: maxit reached before rtol");
+  return result;
 }

@@ -16,7 +16,13 @@ LIB_PATH = os.path.join(_HERE, "libphsvds.so")
 PHSVDS_OK, PHSVDS_ERR_INVALID, PHSVDS_ERR_NOT_CONVERGED, PHSVDS_ERR_BREAKDOWN = 0, 1, 2, 3
 PHSVDS_ERR_NAN, PHSVDS_ERR_TIMEOUT, PHSVDS_ERR_CUDA, PHSVDS_ERR_OOM = 4, 5, 6, 7
 SMALLEST, LARGEST = 0, 1
-PREC_NONE, PREC_JACOBI = 0, 1
+PREC_NONE, PREC_JACOBI, PREC_LEARNED = 0, 1, 2
+CNN_NPARAM = 3024
+
+
+def cnn_work_floats(batch: int, npix: int) -> int:
+    """Floats of the phsvds_cnn_forward / _backward workspace."""
+    return 65 * batch * npix + 2 * CNN_NPARAM + 2 * batch
 FP64, MIXED = 0, 1
 SPMM_AUTO, SPMM_FUSED_ATOMIC, SPMM_TWO_PHASE = 0, 1, 2
 
@@ -25,7 +31,10 @@ class Opts(C.Structure):
     _fields_ = [("block_size", C.c_int), ("max_basis", C.c_int), ("min_restart", C.c_int),
                 ("max_restarts", C.c_int), ("eps_factor", C.c_double), ("precision", C.c_int),
                 ("spmm", C.c_int), ("stage2", C.c_int), ("rayleigh_ritz", C.c_int),
-                ("seed", C.c_uint64), ("time_limit_s", C.c_double), ("profile", C.c_int)]
+                ("seed", C.c_uint64), ("time_limit_s", C.c_double), ("profile", C.c_int),
+                ("learned_params", C.c_void_p), ("learned_features", C.c_void_p), ("grid_nx", C.c_int),
+                ("grid_ny", C.c_int), ("stall_window", C.c_int), ("record_r", C.c_void_p), ("record_max", C.c_int),
+                ("record_every", C.c_int), ("projected_solver", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -36,7 +45,8 @@ class Stats(C.Structure):
                 ("kernel_launches", C.c_int64), ("t_class_ms", C.c_double * 6), ("n_class", C.c_int64 * 6),
                 ("spmm_c_calls", C.c_int64), ("spmm_c_ms", C.c_double), ("spmm_c_width", C.c_int),
                 ("jacobi_sweeps", C.c_int64), ("jacobi_rotations", C.c_int64), ("jacobi_calls", C.c_int64),
-                ("jacobi_dim_sum", C.c_int64)]
+                ("jacobi_dim_sum", C.c_int64), ("fell_back", C.c_int), ("fell_back_at", C.c_int64),
+                ("recorded", C.c_int64), ("stage1_stagnation_locks", C.c_int64)]
 
     def as_dict(self) -> dict:
         d = {}
@@ -72,6 +82,10 @@ def _load() -> C.CDLL:
         "phsvds_default_opts": ([C.POINTER(Opts)], I),
         "phsvds_solve": ([P, I64, I64, I64, P, P, P, I, I, I, D, I, C.POINTER(Opts), P, P, P, P,
                           C.POINTER(Stats)], I),
+        "phsvds_normal_cg": ([P, I64, I64, I64, P, P, P, I, D, I, P, P, D, I, P], I),
+        "phsvds_cnn_forward": ([P, I, I, I, P, P, P, P], I),
+        "phsvds_cnn_backward": ([P, I, I, I, P, P, P, P, P, P, P], I),
+        "phsvds_cnn_adam": ([P, P, P, P, P, I, C.c_float, C.c_float, C.c_float, C.c_float, P], I),
         "phsvds_solve_batched": ([P, I, C.POINTER(Csr), I, I, I, D, I, C.POINTER(Opts), I, C.POINTER(Result)], I),
         "phsvds_ata_spmm_f64": ([P, I, I, I, I64, I64, I64, P, P, P, P, P, P, I, P, P, P], I),
         "phsvds_ata_spmm_f32": ([P, I, I, I, I64, I64, I64, P, P, P, P, P, P, I, P, P, P], I),
@@ -102,7 +116,8 @@ def lib() -> C.CDLL:
     return _lib
 
 
-EXPORTED = ["phsvds_create", "phsvds_default_opts", "phsvds_solve", "phsvds_solve_batched", "phsvds_ata_spmm_f64",
+EXPORTED = ["phsvds_create", "phsvds_default_opts", "phsvds_solve", "phsvds_solve_batched", "phsvds_normal_cg",
+            "phsvds_cnn_forward", "phsvds_cnn_backward", "phsvds_cnn_adam", "phsvds_ata_spmm_f64",
             "phsvds_ata_spmm_f32", "phsvds_ata_spmm_static_f64", "phsvds_csr_to_csc_f64", "phsvds_jacobi_eig_f64", "phsvds_jacobi_eig_cluster_f64",
             "phsvds_jacobi_svd_f64", "phsvds_sync", "phsvds_last_error", "phsvds_status_string",
             "phsvds_destroy"]
@@ -213,6 +228,38 @@ def phsvds_solve_batched(h: Handle, mats, k, target=SMALLEST, tol=1e-14, precond
         out.append((sig, U.T if U is not None else None, V.T if V is not None else None, rs,
                     res[i].stats.as_dict(), res[i].status, res[i].message.decode()))
     return out, status
+
+
+def phsvds_normal_cg(h: Handle, m, n, row_ptr, col_idx, val, R, shift=0.0, rtol=1e-6, maxit=10000,
+                     on_device=False, raise_on_error=True):
+    """x_i = (A^T A - shift I)^{-1} r_i for the columns of R (host n x count)
+    by device CG; returns (X, iterations, status)."""
+    R = np.asfortranarray(np.asarray(R, dtype=np.float64).reshape(n, -1))
+    cnt = R.shape[1]
+    X = np.zeros((n, cnt), order="F")
+    its = np.zeros(cnt, dtype=np.int32)
+    nnz = int(row_ptr[-1]) if isinstance(row_ptr, np.ndarray) else int(row_ptr[-1].item())
+    st = lib().phsvds_normal_cg(h.h, m, n, nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(val), 1 if on_device else 0,
+                                shift, cnt, _ptr(R), _ptr(X), rtol, maxit, _ptr(its))
+    if raise_on_error:
+        h.check(st)
+    return X, its, st
+
+
+def phsvds_cnn_forward(h: Handle, batch, nx, ny, params, x, y, work):
+    """Network forward on device tensors (x: batch x 4 x ny x nx float32, y:
+    batch x ny x nx, params: 3024 bf16, work: cnn_work_floats floats)."""
+    h.check(lib().phsvds_cnn_forward(h.h, batch, nx, ny, _ptr(params), _ptr(x), _ptr(y), _ptr(work)))
+
+
+def phsvds_cnn_backward(h: Handle, batch, nx, ny, params, x, y, t, work, grad, loss):
+    h.check(lib().phsvds_cnn_backward(h.h, batch, nx, ny, _ptr(params), _ptr(x), _ptr(y), _ptr(t), _ptr(work),
+                                      _ptr(grad), _ptr(loss)))
+
+
+def phsvds_cnn_adam(h: Handle, w, grad, m, v, step, lr, params, beta1=0.9, beta2=0.999, eps=1e-8):
+    h.check(lib().phsvds_cnn_adam(h.h, _ptr(w), _ptr(grad), _ptr(m), _ptr(v), step, lr, beta1, beta2, eps,
+                                  _ptr(params)))
 
 
 def phsvds_ata_spmm(h: Handle, schedule, m, n, nnz, rp32, ci, va, cp, ri, cv, b, X, Y, z=None, fp32=False,
