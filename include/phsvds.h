@@ -106,9 +106,11 @@ typedef struct {
     int record_max;
     int record_every;
     /* projected eigensolver of stage 1: 0 = FP64 Jacobi spread over an 8-CTA
-     * cluster (default), 1 = one-CTA Jacobi with each round's work compacted
-     * to its rotating pairs (same results; measured slower on GB300, where a
-     * round is bound by its serial rotation-parameter chain) */
+     * cluster; 1 = one-CTA FP64 Jacobi with each round's work compacted to
+     * its rotating pairs; 2 (default) = an FP32 Jacobi pass, the exact FP64
+     * frame rebuilt from it, and an FP64 Jacobi clean-up of the pairs touching
+     * the targets, whenever the last targets were >= 1e-5 theta_max (FP32
+     * resolves them; GB300's FP64 latency is ~14x its FP32 latency), else 0 */
     int projected_solver;
 } phsvds_opts;
 
@@ -128,8 +130,8 @@ typedef struct {
      * class: [0] fused A^T A SpMM (products with C), [1] Gram / CGS passes,
      * [2] basis transforms and Ritz vectors, [3] other small projected
      * problems (SVD of R, Cholesky, transforms), [4] single products with A or
-     * A^T (products with B), [5] the stage-1 projected eigensolver (cluster
-     * Jacobi) */
+     * A^T (products with B), [5] the projected eigensolvers (Jacobi, FP64 and
+     * FP32 passes) */
     double t_class_ms[6];
     int64_t n_class[6];
     int64_t spmm_c_calls;      /* C-products, each one fused A^T A SpMM launch set */

@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(SM_THREADS) k_jacobi_eig(int j, double* H, int
 void jacobi_eig_ld(cudaStream_t s, int j, double* H, int ldh, double* S, int lds, double* theta, double tol,
                    int max_sweeps, int* sweeps_out, double tol_loose, int ntarget, int tmode, double tshift,
                    int* rot_out) {
-  ProfScope ps(s, PROF_SMALL);
+  ProfScope ps(s, PROF_JACOBI);
   const size_t smem = sizeof(double) * 2 * SM_MAXJ * (SM_MAXJ + 1);
   static std::atomic<uint64_t> attr_done{0};
   once_per_device(attr_done, [&] {
@@ -483,7 +483,7 @@ void jacobi_eig_cluster_ld(cudaStream_t s, int j, double* H, int ldh, double* S,
 
 void jacobi_eig32_ld(cudaStream_t s, int j, const double* H, int ldh, double* Sf, int lds, double* theta, double tol,
                      int max_sweeps, int* sweeps_out, int* rot_out) {
-  ProfScope ps(s, PROF_SMALL);
+  ProfScope ps(s, PROF_JACOBI);
   const size_t smem = sizeof(float) * 2 * SM_MAXJ * (SM_MAXJ + 1);
   k_jacobi_eig<float><<<1, SM_THREADS, smem, s>>>(j, const_cast<double*>(H), ldh, Sf, lds, theta, tol, max_sweeps,
                                                    sweeps_out, tol, 0, 0, 0.0, rot_out); count_launch();

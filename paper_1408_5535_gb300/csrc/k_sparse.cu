@@ -102,25 +102,16 @@ __device__ inline void load_slots(const int* __restrict__ ci, const T* __restric
   }
 }
 
-// Z = A X: one group of L lanes per sparse row.  The rows of a warp are
-// consecutive, so their (column, value) entries are one contiguous range of
-// the matrix stream: when it fits (ST_CAP entries), the warp first copies it
-// into shared memory with coalesced loads (one or two L1 wavefronts per 32
-// entries, instead of one per row segment per slot), then each group reads its
-// row's slots from there.  Then the live gathers of X rows are issued back to
-// back, so up to U independent loads are in flight per lane, and the B partial
-// sums are reduced inside the group.  A warp whose range does not fit loads
-// its slots directly (streaming loads, L2 evict-first).
-constexpr int ST_CAP = 192;
-
+// Z = A X: one group of L lanes per sparse row.  Each pass a lane loads U
+// (column, value) slots (streaming loads: the matrix is read once and should
+// not evict the gathered rows from L2), then issues the live gathers back to
+// back so up to U independent loads are in flight per lane; the B partial
+// sums are reduced inside the group at the end.
 template <typename T, int B, int L, int U, bool W, bool NA>
 __global__ void __launch_bounds__(256) k_csr_rows(int nrows, int xrows, const int* __restrict__ rp,
                                                   const int* __restrict__ ci, const T* __restrict__ va,
                                                   const T* __restrict__ X, T* __restrict__ Z) {
-  __shared__ int s_ci[8][ST_CAP];
-  __shared__ T s_va[8][ST_CAP];
   const int lane = threadIdx.x % L;
-  const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31;
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) / L;
   const bool active = row < nrows;  // inactive groups still take part in the shuffles
   T acc[B];
@@ -128,53 +119,17 @@ __global__ void __launch_bounds__(256) k_csr_rows(int nrows, int xrows, const in
   for (int q = 0; q < B; ++q) acc[q] = T(0);
   const int e0 = active ? rp[row] : 0, e1 = active ? rp[row + 1] : 0;
   const uint64_t pol = l2_evict_first_policy();
-  // the warp's rows [rw0, rw1) and their entries [E0, E1)
-  const int rw0 = (blockIdx.x * blockDim.x + warp * 32) / L;
-  const int nrw = min(32 / L, nrows - rw0);
-  const int E0 = __shfl_sync(0xffffffffu, e0, 0);
-  const int E1 = __shfl_sync(0xffffffffu, e1, nrw > 0 ? (nrw - 1) * L : 0);
-  const bool staged = nrw > 0 && E1 >= E0 && E1 - E0 <= ST_CAP;  // the same in every lane of the warp
-  if (staged) {
-    for (int e = E0 + wl; e < E1; e += 32) {
-      s_ci[warp][e - E0] = ld_stream(ci + e, pol);
-      s_va[warp][e - E0] = ld_stream(va + e, pol);
-    }
-    __syncwarp();
-    for (int base = e0; base < e1; base += L * U) {
-      int col[U];
-      T v[U];
-      bool ok[U];
+  for (int base = e0; base < e1; base += L * U) {
+    int col[U];
+    T v[U];
+    bool ok[U];
+    load_slots<T, L, U>(ci, va, base, lane, e0, e1, xrows, pol, col, v, ok);
+    T x[U][B];
+    gather_rows<T, B, U, W, NA>(X, col, ok, x);
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int e = base + u * L + lane;
-        // inside the row and the staged range (always both for a valid CSR)
-        const bool live = e < e1 && (unsigned)(e - E0) < (unsigned)(E1 - E0);
-        const int c = live ? s_ci[warp][e - E0] : 0;
-        const bool inr = (unsigned)c < (unsigned)xrows;  // guard against a corrupted index
-        ok[u] = live && inr;
-        col[u] = inr ? c : 0;
-        v[u] = ok[u] ? s_va[warp][e - E0] : T(0);
-      }
-      T x[U][B];
-      gather_rows<T, B, U, W, NA>(X, col, ok, x);
+    for (int u = 0; u < U; ++u)
 #pragma unroll
-      for (int u = 0; u < U; ++u)
-#pragma unroll
-        for (int q = 0; q < B; ++q) acc[q] = fma(v[u], x[u][q], acc[q]);
-    }
-  } else {
-    for (int base = e0; base < e1; base += L * U) {
-      int col[U];
-      T v[U];
-      bool ok[U];
-      load_slots<T, L, U>(ci, va, base, lane, e0, e1, xrows, pol, col, v, ok);
-      T x[U][B];
-      gather_rows<T, B, U, W, NA>(X, col, ok, x);
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-#pragma unroll
-        for (int q = 0; q < B; ++q) acc[q] = fma(v[u], x[u][q], acc[q]);
-    }
+      for (int q = 0; q < B; ++q) acc[q] = fma(v[u], x[u][q], acc[q]);
   }
   if constexpr (L > 1) {
 #pragma unroll

@@ -29,6 +29,8 @@ constexpr double TOL_MARGIN = 0.9;        // stopping tests use 0.9 delta: the r
                                           // independent recomputation differ by rounding of order eps ||C||
 constexpr double JAC_REL = 1e-8;          // relative threshold of the other pairs (they span the restart space)
 constexpr int W_REFRESH = 16;             // stage-1 restarts between recomputations of W = C V
+constexpr double EIG32_GATE = 1e-5;       // FP32-first projected solve when the targets are >= this x theta_max
+constexpr double JAC_REL32 = 1e-6;        // its FP64 clean-up: relative threshold of the non-target pairs
 constexpr double STAG_NEAR = 2.0;         // stage-1 stagnation: residual within 2x of its tolerance ...
 constexpr double STAG_RATIO = 100.0;      // ... or within 100x for STAG_LONG iterations without halving
 constexpr int64_t STAG_LONG = 2000;
@@ -333,7 +335,7 @@ static void frame_from_true(cudaStream_t s, int j, const double* Ht, double* S, 
 // FP64 accuracy.  theta = diagonal of the final frame, S = its rotation.
 static void eig_mixed(cudaStream_t s, int j, const double* Ht, double* S, double* Aw, double* Sf, double* theta,
                       double* w1, double* w2, bool s_ident, bool fp64_cleanup, int ntarget, int tmode, double tshift,
-                      int* counters) {
+                      int* counters, double rel = JAC_REL) {
   frame_from_true(s, j, Ht, S, Aw, w1, w2, s_ident ? -1 : 0);
   jacobi_eig32_ld(s, j, Aw, LD, Sf, LD, theta, 1e-6, 30, counters, counters + 1);
   if (s_ident) {
@@ -346,7 +348,7 @@ static void eig_mixed(cudaStream_t s, int j, const double* Ht, double* S, double
   }
   frame_from_true(s, j, Ht, S, Aw, w1, w2, fp64_cleanup ? 2 : 1);
   if (fp64_cleanup)
-    jacobi_eig_ld(s, j, Aw, LD, S, LD, theta, JAC_TOL, 60, counters + 2, JAC_REL, ntarget, tmode, tshift,
+    jacobi_eig_ld(s, j, Aw, LD, S, LD, theta, JAC_TOL, 60, counters + 2, rel, ntarget, tmode, tshift,
                   counters + 3);
   else
     jacobi_eig32_ld(s, j, Aw, LD, Sf, LD, theta, 1e-6, 0, nullptr, nullptr);  // theta = diag of the rebuilt frame
@@ -412,6 +414,8 @@ struct Stage1 {
   int max_restarts;
   double time_limit_s;
   bool cluster_eig;
+  int eig_mode = 0;
+  bool eig32_ok = false;  // the last targets are resolvable in FP32 (>= EIG32_GATE theta_max)
   std::chrono::steady_clock::time_point t0;
   // device
   T *V, *W, *Xl, *Tb, *Xrm, *Yrm, *Xr, *Rr, *XU;
@@ -448,7 +452,8 @@ struct Stage1 {
     seed = o.seed;
     max_restarts = o.max_restarts;
     time_limit_s = o.time_limit_s;
-    cluster_eig = o.projected_solver == 0;
+    cluster_eig = o.projected_solver != 1;
+    eig_mode = o.projected_solver;
     stag_window = std::max(100, 6 * (maxb - mins));
     const size_t nn = (size_t)n;
     V = pool.get<T>(nn * maxb);
@@ -596,11 +601,20 @@ struct Stage1 {
     while (true) {
       check_time();
       if (nb > 0) expand(nb);
-      frame_from_true(s, j, Ht, S, Aw, w1, w2, s_ident ? -1 : 1);
+      // projected eigensolve: an FP32 bulk pass and an FP64 clean-up of the
+      // target pairs when the targets are resolvable in FP32, else FP64
+      // Jacobi throughout (GB300's FP64 latency is ~14x its FP32 latency)
+      const bool mixed_eig = eig_mode == 2 && (largest || eig32_ok);
+      if (mixed_eig) {
+        eig_mixed(s, j, Ht, S, Aw, Sf, theta, w1, w2, s_ident, true, std::min(b, k - nlock) + 1, largest ? 1 : 0,
+                  0.0, flags + 16, JAC_REL32);
+      } else {
+        frame_from_true(s, j, Ht, S, Aw, w1, w2, s_ident ? -1 : 1);
+        (cluster_eig ? jacobi_eig_cluster_ld : jacobi_eig_fast_ld)(s, j, Aw, LD, S, LD, theta, JAC_TOL, 60,
+                                                                   flags + 12, JAC_REL, std::min(b, k - nlock) + 1,
+                                                                   largest ? 1 : 0, 0.0, flags + 13);
+      }
       s_ident = false;
-      (cluster_eig ? jacobi_eig_cluster_ld : jacobi_eig_fast_ld)(s, j, Aw, LD, S, LD, theta, JAC_TOL, 60, flags + 12,
-                                                                 JAC_REL, std::min(b, k - nlock) + 1,
-                                                                 largest ? 1 : 0, 0.0, flags + 13);
       order_theta(s, j, theta, largest ? 1 : 0, 0.0, order);
       const int nt = std::min(std::min(b, k - nlock), j);
       gather_cols(s, j, S, LD, order, nt, Scols, LD, theta, thcols, flags + 14);
@@ -613,12 +627,17 @@ struct Stage1 {
       CUCHK(cudaMemcpyAsync(hth, theta, sizeof(double) * j, cudaMemcpyDeviceToHost, s));
       CUCHK(cudaMemcpyAsync(hord, order, sizeof(int) * j, cudaMemcpyDeviceToHost, s));
       CUCHK(cudaMemcpyAsync(hn, norms, sizeof(double) * nt, cudaMemcpyDeviceToHost, s));
-      CUCHK(cudaMemcpyAsync(h.at<int>(960), flags + 12, sizeof(int) * 4, cudaMemcpyDeviceToHost, s));
+      CUCHK(cudaMemcpyAsync(h.at<int>(960), flags + 12, sizeof(int) * 8, cudaMemcpyDeviceToHost, s));
       sync(s);
       out.iters++;
       if (*h.at<int>(968)) throw PhError{PHSVDS_ERR_NAN, "stage 1: corrupted ordering of the Ritz values"};
-      out.jac_sweeps += *h.at<int>(960);
-      out.jac_rot += *h.at<int>(964);
+      if (mixed_eig) {  // FP32 pass + FP64 clean-up
+        out.jac_sweeps += *h.at<int>(976) + *h.at<int>(984);
+        out.jac_rot += *h.at<int>(980) + *h.at<int>(988);
+      } else {
+        out.jac_sweeps += *h.at<int>(960);
+        out.jac_rot += *h.at<int>(964);
+      }
       out.jac_calls += 1;
       out.jac_dim += j;
       for (int i = 0; i < j; ++i) {
@@ -626,6 +645,14 @@ struct Stage1 {
         thv[i] = hth[hord[i]];
         if (!std::isfinite(thv[i])) throw PhError{PHSVDS_ERR_NAN, "stage 1: non-finite Ritz value"};
         out.theta_max = std::max(out.theta_max, thv[i]);
+      }
+      {
+        // the FP32-first projected solve resolves eigenvalues to ~1e-7 theta_max:
+        // allowed next iteration only if the coming targets sit well above that
+        const int nx = std::min(std::min(b, k - nlock) + 1, j);
+        double tmin = INFINITY;
+        for (int i = 0; i < nx; ++i) tmin = std::min(tmin, std::fabs(thv[i]));
+        eig32_ok = tmin >= EIG32_GATE * out.theta_max;
       }
       std::vector<int> conv, unconv;
       double best_ratio = INFINITY;
@@ -1536,7 +1563,7 @@ phsvds_status phsvds_default_opts(phsvds_opts* o) {
   o->record_r = nullptr;
   o->record_max = 0;
   o->record_every = 0;
-  o->projected_solver = 0;
+  o->projected_solver = 2;
   return PHSVDS_OK;
 }
 

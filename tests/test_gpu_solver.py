@@ -84,9 +84,13 @@ def test_grid_closed_form(h):
     _check(A, sig, U, V, res, 6, A.sigma_exact[:6], A.sigma_exact[-1])
 
 
-def test_weighted_grid_vs_oracle(h):
+@pytest.mark.parametrize("projected_solver", [0, 1, 2])
+def test_weighted_grid_vs_oracle(h, projected_solver):
+    """Every projected eigensolver of stage 1 (FP64 cluster Jacobi, one-CTA
+    compacted FP64 Jacobi, gated FP32 pass + FP64 clean-up) gives the oracle's
+    triplets."""
     A = synth.grid_gradient(24, 1.0, 2)
-    sig, U, V, res, st, _ = _solve(h, A, 10, block_size=4)
+    sig, U, V, res, st, _ = _solve(h, A, 10, block_size=4, projected_solver=projected_solver)
     ref = R.phsvds(A, 10, delta=DELTA, o=R.Opts(block=4))
     nA = np.linalg.norm(A.to_dense(), 2)
     _check(A, sig, U, V, res, 10, ref.sigma, nA)
