@@ -13,6 +13,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "kernels.h"
@@ -381,6 +382,68 @@ static void transform_h(cudaStream_t s, int j, int jn, double* Ht, const double*
 // ---------------------------------------------------------------------------
 // Stage 1: block GD+k on C (storage precision T)
 // ---------------------------------------------------------------------------
+// Cached CUDA graphs of the launch-heavy, host-sync-free segments of an outer
+// iteration, keyed by everything host-side the segment depends on (the
+// buffers of a solve stay put).  A key's first occurrence runs eagerly (so
+// function attributes and lazy module loads happen outside any capture), its
+// second is captured and instantiated, later ones replay the graph.  If a
+// capture cannot be made (a caller stream that cannot be captured, say) the
+// cache switches itself off and every segment runs eagerly.
+struct GraphCache {
+  struct Entry {
+    int seen = 0;
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0;
+  };
+  std::unordered_map<uint64_t, Entry> map;
+  bool enabled = true;
+  ~GraphCache() {
+    for (auto& kv : map)
+      if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  }
+  template <typename F>
+  void run(cudaStream_t s, uint64_t key, F&& issue) {
+    if (!enabled) return issue();
+    Entry& e = map[key];
+    if (e.exec) {
+      CUCHK(cudaGraphLaunch(e.exec, s));
+      g_launch_count += e.launches;
+      return;
+    }
+    if (e.seen++ == 0) return issue();
+    const int64_t l0 = g_launch_count;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      enabled = false;
+      return issue();
+    }
+    try {
+      issue();
+    } catch (...) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(s, &g);
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      throw;
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t st = cudaStreamEndCapture(s, &g);
+    if (st == cudaSuccess && g) st = cudaGraphInstantiate(&e.exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    const int64_t captured = g_launch_count - l0;
+    g_launch_count = l0;
+    if (st != cudaSuccess || !e.exec) {  // nothing ran: switch off and run eagerly
+      cudaGetLastError();
+      e.exec = nullptr;
+      enabled = false;
+      return issue();
+    }
+    e.launches = captured;
+    CUCHK(cudaGraphLaunch(e.exec, s));
+    g_launch_count += e.launches;
+  }
+};
+
 struct Stage1Out {
   std::vector<double> lam;   // k eigenvalues of C (target order)
   double theta_max = 0.0;
@@ -416,6 +479,7 @@ struct Stage1 {
   bool cluster_eig;
   int eig_mode = 0;
   bool eig32_ok = false;  // the last targets are resolvable in FP32 (>= EIG32_GATE theta_max)
+  GraphCache graphs;
   std::chrono::steady_clock::time_point t0;
   // device
   T *V, *W, *Xl, *Tb, *Xrm, *Yrm, *Xr, *Rr, *XU;
@@ -454,6 +518,7 @@ struct Stage1 {
     time_limit_s = o.time_limit_s;
     cluster_eig = o.projected_solver != 1;
     eig_mode = o.projected_solver;
+    graphs.enabled = !o.profile;  // the per-class timing events are not captured
     stag_window = std::max(100, 6 * (maxb - mins));
     const size_t nn = (size_t)n;
     V = pool.get<T>(nn * maxb);
@@ -512,16 +577,21 @@ struct Stage1 {
     Basis<T> P{Xl, n, nlock, V, n, j};
     const int p = P.cols();
     for (int attempt = 0;; ++attempt) {
-      zero(s, innorm, nb);
-      col_norms2_dense<T>(s, n, Tb, n, nb, innorm);
-      zero(s, G1, (size_t)p * nb);
-      zero(s, G2, (size_t)p * nb);
-      zero(s, P1, (size_t)nb * nb);
-      cgs_pass<T>(s, n, P, Tb, n, nb, nullptr, G1, nullptr);
-      cgs_pass<T>(s, n, P, Tb, n, nb, G1, G2, nullptr);
-      cgs_pass<T>(s, n, P, Tb, n, nb, G2, nullptr, P1);
-      chol_factor(s, nb, P1, innorm, 1e-10, M1, flags);
-      CUCHK(cudaMemcpyAsync(h.at<int>(0), flags, sizeof(int) * (nb + 1), cudaMemcpyDeviceToHost, s));
+      // two CGS passes against [locked, basis], the Gram of the remainder and
+      // its Cholesky (graph-cached: one segment without host syncs)
+      auto pass = [&]() {
+        zero(s, innorm, nb);
+        col_norms2_dense<T>(s, n, Tb, n, nb, innorm);
+        zero(s, G1, (size_t)p * nb);
+        zero(s, G2, (size_t)p * nb);
+        zero(s, P1, (size_t)nb * nb);
+        cgs_pass<T>(s, n, P, Tb, n, nb, nullptr, G1, nullptr);
+        cgs_pass<T>(s, n, P, Tb, n, nb, G1, G2, nullptr);
+        cgs_pass<T>(s, n, P, Tb, n, nb, G2, nullptr, P1);
+        chol_factor(s, nb, P1, innorm, 1e-10, M1, flags);
+        CUCHK(cudaMemcpyAsync(h.at<int>(0), flags, sizeof(int) * (nb + 1), cudaMemcpyDeviceToHost, s));
+      };
+      graphs.run(s, (1ull << 40) | ((uint64_t)nb << 8) | (uint64_t)nlock << 16 | (uint64_t)j, pass);
       sync(s);
       int* f = h.at<int>(0);
       if (!f[nb]) break;
@@ -529,6 +599,10 @@ struct Stage1 {
       for (int c = 0; c < nb; ++c)
         if (f[c]) fill_random<T>(s, n, Tb + (size_t)c * n, seed, RS_BREAK + (uint64_t)(rand_ctr++));
     }
+  }
+
+  // The accepted block, orthonormalised (CholQR, twice for nb > 1), into V.
+  void orth_scale(int nb) {
     if (nb == 1) {
       scale_block<T>(s, n, Tb, n, 1, M1, V + (size_t)j * n, n);
     } else {
@@ -551,18 +625,24 @@ struct Stage1 {
       rm_to_cm<T>(s, n, Yrm, w, W + (size_t)(j0 + c) * n, n);
       c += w;
     }
-    out.mv += nb;
   }
 
   // Append nb columns (already in Tb) to the basis and the Jacobi frame.
   void expand(int nb) {
     orth_append(nb);
-    apply_C(j, nb);
-    zero(s, Hn, (size_t)(j + nb) * nb);
-    Basis<T> Pv{V, n, j + nb, nullptr, 0, 0};
-    cgs_pass<T>(s, n, Pv, W + (size_t)j * n, n, nb, nullptr, Hn, nullptr);
-    h_append(s, j, nb, Ht, LD, S, LD, Hn);
-    if (nsp) CUCHK(cudaMemset2DAsync(sprev + j, LD * sizeof(double), 0, nb * sizeof(double), nsp, s));
+    // W's new columns, the new Gram column of H and the frame append: one
+    // segment without host syncs (graph-cached)
+    auto tail = [&]() {
+      orth_scale(nb);
+      apply_C(j, nb);
+      zero(s, Hn, (size_t)(j + nb) * nb);
+      Basis<T> Pv{V, n, j + nb, nullptr, 0, 0};
+      cgs_pass<T>(s, n, Pv, W + (size_t)j * n, n, nb, nullptr, Hn, nullptr);
+      h_append(s, j, nb, Ht, LD, S, LD, Hn);
+      if (nsp) CUCHK(cudaMemset2DAsync(sprev + j, LD * sizeof(double), 0, nb * sizeof(double), nsp, s));
+    };
+    graphs.run(s, (2ull << 40) | ((uint64_t)nsp << 24) | ((uint64_t)nb << 8) | (uint64_t)j, tail);
+    out.mv += nb;
     j += nb;
   }
 
@@ -605,29 +685,37 @@ struct Stage1 {
       // target pairs when the targets are resolvable in FP32, else FP64
       // Jacobi throughout (GB300's FP64 latency is ~14x its FP32 latency)
       const bool mixed_eig = eig_mode == 2 && (largest || eig32_ok);
-      if (mixed_eig) {
-        eig_mixed(s, j, Ht, S, Aw, Sf, theta, w1, w2, s_ident, true, std::min(b, k - nlock) + 1, largest ? 1 : 0,
-                  0.0, flags + 16, JAC_REL32);
-      } else {
-        frame_from_true(s, j, Ht, S, Aw, w1, w2, s_ident ? -1 : 1);
-        (cluster_eig ? jacobi_eig_cluster_ld : jacobi_eig_fast_ld)(s, j, Aw, LD, S, LD, theta, JAC_TOL, 60,
-                                                                   flags + 12, JAC_REL, std::min(b, k - nlock) + 1,
-                                                                   largest ? 1 : 0, 0.0, flags + 13);
-      }
-      s_ident = false;
-      order_theta(s, j, theta, largest ? 1 : 0, 0.0, order);
+      const int ntg = std::min(b, k - nlock) + 1;
       const int nt = std::min(std::min(b, k - nlock), j);
-      gather_cols(s, j, S, LD, order, nt, Scols, LD, theta, thcols, flags + 14);
-      tall_times_small<T>(s, n, V, n, j, Scols, LD, nt, Xr, n, nullptr, 0, nullptr, nullptr);
-      zero(s, norms, nt);
-      tall_times_small<T>(s, n, W, n, j, Scols, LD, nt, Rr, n, Xr, n, thcols, norms);
+      const bool sid = s_ident;
       double* hth = h.at<double>(0);        // bytes [0, 512)
       int* hord = h.at<int>(512);            // bytes [512, 768)
       double* hn = h.at<double>(768);        // bytes [768, 832)
-      CUCHK(cudaMemcpyAsync(hth, theta, sizeof(double) * j, cudaMemcpyDeviceToHost, s));
-      CUCHK(cudaMemcpyAsync(hord, order, sizeof(int) * j, cudaMemcpyDeviceToHost, s));
-      CUCHK(cudaMemcpyAsync(hn, norms, sizeof(double) * nt, cudaMemcpyDeviceToHost, s));
-      CUCHK(cudaMemcpyAsync(h.at<int>(960), flags + 12, sizeof(int) * 8, cudaMemcpyDeviceToHost, s));
+      // projected eigensolve, Ritz vectors and residuals, readbacks: one
+      // segment without host syncs, replayed as a cached graph
+      auto segment = [&]() {
+        if (mixed_eig) {
+          eig_mixed(s, j, Ht, S, Aw, Sf, theta, w1, w2, sid, true, ntg, largest ? 1 : 0, 0.0, flags + 16, JAC_REL32);
+        } else {
+          frame_from_true(s, j, Ht, S, Aw, w1, w2, sid ? -1 : 1);
+          (cluster_eig ? jacobi_eig_cluster_ld : jacobi_eig_fast_ld)(s, j, Aw, LD, S, LD, theta, JAC_TOL, 60,
+                                                                     flags + 12, JAC_REL, ntg, largest ? 1 : 0, 0.0,
+                                                                     flags + 13);
+        }
+        order_theta(s, j, theta, largest ? 1 : 0, 0.0, order);
+        gather_cols(s, j, S, LD, order, nt, Scols, LD, theta, thcols, flags + 14);
+        tall_times_small<T>(s, n, V, n, j, Scols, LD, nt, Xr, n, nullptr, 0, nullptr, nullptr);
+        zero(s, norms, nt);
+        tall_times_small<T>(s, n, W, n, j, Scols, LD, nt, Rr, n, Xr, n, thcols, norms);
+        CUCHK(cudaMemcpyAsync(hth, theta, sizeof(double) * j, cudaMemcpyDeviceToHost, s));
+        CUCHK(cudaMemcpyAsync(hord, order, sizeof(int) * j, cudaMemcpyDeviceToHost, s));
+        CUCHK(cudaMemcpyAsync(hn, norms, sizeof(double) * nt, cudaMemcpyDeviceToHost, s));
+        CUCHK(cudaMemcpyAsync(h.at<int>(960), flags + 12, sizeof(int) * 8, cudaMemcpyDeviceToHost, s));
+      };
+      const uint64_t key = (uint64_t)j | ((uint64_t)nt << 8) | ((uint64_t)ntg << 16) | ((uint64_t)mixed_eig << 24) |
+                           ((uint64_t)sid << 25);
+      graphs.run(s, key, segment);
+      s_ident = false;
       sync(s);
       out.iters++;
       if (*h.at<int>(968)) throw PhError{PHSVDS_ERR_NAN, "stage 1: corrupted ordering of the Ritz values"};
@@ -779,8 +867,10 @@ struct Stage1 {
           if (jnew < 1 || jnew > maxb) throw PhError{PHSVDS_ERR_BREAKDOWN, "stage 1: restart basis size out of range"};
         }
         tall_times_small<T>(s, n, V, n, j, Yt, LD, jnew, V, n, nullptr, 0, nullptr, nullptr);
-        if (restart && out.restarts % W_REFRESH == 0)
+        if (restart && out.restarts % W_REFRESH == 0) {
           apply_C(0, jnew);  // W = C V afresh: W <- W Y drifts from C V by rounding at every restart
+          out.mv += jnew;
+        }
         else
           tall_times_small<T>(s, n, W, n, j, Yt, LD, jnew, W, n, nullptr, 0, nullptr, nullptr);
         gram_full<T>(s, n, V, W, jnew, Ht, w1);
