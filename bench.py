@@ -36,7 +36,7 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--grid", type=int, default=32, help="grid side of the weighted gradient workload")
+    p.add_argument("--grid", type=int, default=64, help="grid side of the weighted gradient workload")
     p.add_argument("--sigma-log", type=float, default=1.0)
     p.add_argument("--k", type=int, default=10)
     p.add_argument("--block", type=int, default=4)
@@ -64,6 +64,7 @@ def parse():
     p.add_argument("--learned-test", type=int, default=10)
     p.add_argument("--learned-epochs", type=int, default=100)
     p.add_argument("--learned-cg-steps", type=int, default=3)
+    p.add_argument("--learned-stall", type=int, default=200, help="stall window of the learned correction")
     return p.parse_args()
 
 
@@ -313,7 +314,9 @@ def run_ours(a, rank, world):
     precs = {"mixed": [native.MIXED], "fp64": [native.FP64], "both": [native.MIXED, native.FP64]}[a.precision]
     prec_id = native.PREC_JACOBI if a.precond == "jacobi" else native.PREC_NONE
     results = {}
-    for prec in precs:
+    for pi, prec in enumerate(precs):
+        head = pi == 0                 # the headline precision; the second is the comparison leg
+        steps = a.steps if head else max(1, min(a.steps, 2))
         o = native.default_opts(block_size=a.block, precision=prec, profile=0)
         op = native.default_opts(block_size=a.block, precision=prec, profile=1)
 
@@ -326,7 +329,7 @@ def run_ours(a, rank, world):
             solve(o)
         times, launches, last = [], 0, None
         with Clocks(dev) as clk:
-            for _ in range(a.steps):
+            for _ in range(steps):
                 flush.fill_(1.0)
                 torch.cuda.synchronize()
                 barrier(world)
@@ -347,7 +350,7 @@ def run_ours(a, rank, world):
         e2e = None
         if not a.no_e2e:
             ee = []
-            for _ in range(max(1, min(a.steps, 2))):
+            for _ in range(1):
                 flush.fill_(1.0)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
@@ -359,7 +362,7 @@ def run_ours(a, rank, world):
             e2e = {"value": world * a.k / (e_ms / 1e3), "unit": "triplets/s", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h, "ms_per_step": e_ms}
         results[prec] = dict(ms=ms, sigma=sig.tolist(), resid_rel=(resid / st["norm_A_est"]).tolist(), stats=st,
-                             prof=prof, e2e=e2e, clocks=clk.summary(), launches=launches)
+                             prof=prof, e2e=e2e, clocks=clk.summary(), launches=launches, steps=steps)
     h.close()
     return A, cfg, results
 
@@ -492,7 +495,7 @@ def run_learned(a):
         A = synth.convdiff_stencil(N, 1200 + i)
         for name, pc in modes.items():
             if pc == native.PREC_LEARNED:
-                o, keep = learned.solve_opts(A, tr.params_bf16)
+                o, keep = learned.solve_opts(A, tr.params_bf16, stall_window=a.learned_stall)
             else:
                 o = native.default_opts()
             torch.cuda.synchronize()
@@ -524,6 +527,7 @@ def run_learned(a):
             "cg_iters_mean": float(np.mean(data.cg_iters)) if data.cg_iters else None,
             "seconds_generate": t_gen, "seconds_record_and_inner_solves": t_rec, "seconds_train": t_train,
             "target": f"{a.learned_cg_steps} CG steps" if a.learned_cg_steps else "converged CG (rtol 1e-6)",
+            "stall_window": a.learned_stall,
             "train_steps": tr.steps, "loss_first_epoch": tr.loss_history[0], "loss_last_epoch": tr.loss_history[-1],
             "modes": summ,
             "speedup_learned_over_none": summ["none"]["mean_seconds"] / summ["learned"]["mean_seconds"],
@@ -578,7 +582,7 @@ def main():
                        parallelism=f"replicas{world}"),
         "roofline": roof,
         "gpu_launches": r["launches"],
-        "gpu_launches_per_step": r["launches"] // max(a.steps, 1),
+        "gpu_launches_per_step": r["launches"] // max(r["steps"], 1),
         "clocks": r["clocks"],
         "e2e": r["e2e"],
         "solve": {"iters_stage1": st["iters_stage1"], "iters_stage1_fp32": st["iters_stage1_fp32"],
@@ -589,7 +593,7 @@ def main():
     }
     if native.FP64 in res and head != native.FP64:
         f = res[native.FP64]
-        line["fp64"] = {"value": world * cfg["k"] / (f["ms"] / 1e3), "ms_per_step": f["ms"],
+        line["fp64"] = {"value": world * cfg["k"] / (f["ms"] / 1e3), "ms_per_step": f["ms"], "steps": f["steps"],
                         "iters_stage1": f["stats"]["iters_stage1"], "iters_stage2": f["stats"]["iters_stage2"],
                         "speedup_mixed_over_fp64": f["ms"] / r["ms"],
                         "max_sigma_rel_diff_vs_mixed": max(abs(x - y) / y for x, y in zip(r["sigma"], f["sigma"])),

@@ -671,6 +671,223 @@ __global__ void __launch_bounds__(SM_THREADS)
   if (tid == 0 && rot_out) rot_out[0] = nrot;
 }
 
+// ---------------------------------------------------------------------------
+// FP64 clean-up of the target pairs after an FP32 Jacobi pass: only pairs that
+// touch one of the ntarget targets (smallest diagonal entries for tmode 0,
+// largest for 1, closest to tshift for 2, ranked once per sweep) are rotated,
+// to the absolute threshold tol * max|a_ij|; pairs between two non-targets are
+// left as the FP32 pass made them.  A sweep is (a) nN rounds in which target i
+// pairs with non-target N[(r + i) mod nN] (disjoint, nt <= nN) and (b) the
+// round-robin rounds of the target-target pairs.  Each round: rotation
+// parameters of its <= 8 pairs in one warp, then the row rotations (and S's
+// columns), then the column rotations -- two-sided J^T A J with disjoint
+// pairs.  After the FP32 pass the angles are small: for |t| < 2^-10 the
+// cosine is the series 1 - t^2/2 + 3 t^4/8 (error below 2^-60) instead of
+// the rsqrt refinement, which shortens the serial FP64 chain of a round.
+// ---------------------------------------------------------------------------
+constexpr int JT_MAXT = 8;
+
+__device__ inline void rot_params_small(double app, double aqq, double apq, double inv_scale, double& c, double& s_) {
+  const float fpp = (float)(app * inv_scale), fqq = (float)(aqq * inv_scale), fpq = (float)(apq * inv_scale);
+  const float ftau = (fqq - fpp) / (2.0f * fpq);
+  const float ft = copysignf(1.0f, ftau) / (fabsf(ftau) + sqrtf(1.0f + ftau * ftau));
+  if (fabsf(ft) < 0.0009765625f) {
+    const double t = (double)ft;
+    const double t2 = t * t;
+    const double cc = fma(t2, fma(t2, 0.375, -0.5), 1.0);
+    c = cc;
+    s_ = t * cc;
+  } else {
+    rot_params(app, aqq, apq, inv_scale, c, s_);
+  }
+}
+
+__global__ void __launch_bounds__(SM_THREADS)
+    k_jacobi_targets(int j, double* H, int ldh, double* S, int lds, double* theta, double tol, int max_sweeps,
+                     int* sweeps_out, int ntarget, int tmode, double tshift, int* rot_out) {
+  extern __shared__ __align__(16) double dsm[];
+  double* A = dsm;                              // [SM_MAXJ * (SM_MAXJ + 1)]
+  double* Sm = A + SM_MAXJ * (SM_MAXJ + 1);
+  __shared__ double cs[JT_MAXT], sn[JT_MAXT];
+  __shared__ int pp[JT_MAXT], qq[JT_MAXT], rotf[JT_MAXT];
+  __shared__ int tgt[JT_MAXT], non[SM_MAXJ];
+  __shared__ int nt_s, nn_s;
+  __shared__ double scale_s;
+  __shared__ double wmx[SM_THREADS / 32];
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int LA = SM_MAXJ + 1;
+  for (int e = tid; e < j * j; e += SM_THREADS) {
+    const int r = e % j, c = e / j;
+    A[r + c * LA] = H[r + (size_t)c * ldh];
+    Sm[r + c * LA] = S[r + (size_t)c * lds];
+  }
+  __syncthreads();
+  double mx = 0.0;
+  for (int e = tid; e < j * j; e += SM_THREADS) mx = fmax(mx, fabs(A[(e % j) + (e / j) * LA]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) wmx[w] = mx;
+  __syncthreads();
+  if (tid == 0) {
+    double m2 = 0.0;
+    for (int k = 0; k < SM_THREADS / 32; ++k) m2 = fmax(m2, wmx[k]);
+    scale_s = m2;
+  }
+  __syncthreads();
+  const double thr = tol * scale_s;
+  const double inv_scale = scale_s > 0.0 ? 1.0 / scale_s : 1.0;
+  int sweep = 0, nrot = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    // rank the targets on the current diagonal
+    if (tid == 0) {
+      nt_s = 0;
+      nn_s = 0;
+    }
+    __syncthreads();
+    if (tid < j) {
+      auto key = [&](int t2) {
+        const double d = A[t2 + t2 * LA];
+        const double k = tmode == 0 ? d : (tmode == 1 ? -d : fabs(d - tshift));
+        return isnan(k) ? INFINITY : k;
+      };
+      const double ki = key(tid);
+      int rank = 0;
+      for (int t2 = 0; t2 < j; ++t2) {
+        const double kt = key(t2);
+        if (kt < ki || (kt == ki && t2 < tid)) ++rank;
+      }
+      const int ntg = ntarget < JT_MAXT ? ntarget : JT_MAXT;
+      if (rank < ntg && rank < j - 1) tgt[rank] = tid;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const int ntg = min(min(ntarget, JT_MAXT), j - 1);
+      nt_s = ntg > 0 ? ntg : 0;
+      int c = 0;
+      for (int i = 0; i < j; ++i) {
+        bool is_t = false;
+        for (int a = 0; a < nt_s; ++a) is_t |= tgt[a] == i;
+        if (!is_t) non[c++] = i;
+      }
+      nn_s = c;
+    }
+    __syncthreads();
+    const int nt = nt_s, nn = nn_s;
+    // converged: every pair touching a target below the threshold
+    int any = 0;
+    for (int e = tid; e < nt * j; e += SM_THREADS) {
+      const int a = e / j, x = e % j, t = tgt[a];
+      if (x != t && fabs(A[t + x * LA]) > thr) any = 1;
+    }
+    if (!__syncthreads_or(any)) break;
+    // (a) every target-non-target pair once: max(nt, nn) rounds of disjoint
+    // pairs (the smaller side by lane, the larger one shifted each round)
+    // (b) the target-target pairs, round robin
+    const int ntt = nt + (nt & 1);
+    const int na = nt > 0 ? (nt > nn ? nt : nn) : 0;
+    const int nrounds = na + (nt > 1 ? ntt - 1 : 0);
+    for (int round = 0; round < nrounds; ++round) {
+      bool mine = false;
+      if (w == 0 && lane < JT_MAXT) {
+        int p = -1, q = -1;
+        if (round < na) {
+          if (nt <= nn) {
+            if (lane < nt) {
+              p = tgt[lane];
+              q = non[(round + lane) % nn];
+            }
+          } else if (lane < nn) {
+            p = tgt[(round + lane) % nt];
+            q = non[lane];
+          }
+        } else if (lane < ntt / 2) {
+          int a, b;
+          rr_pair(ntt, round - na, lane, a, b);
+          if (b < nt) {
+            p = tgt[a];
+            q = tgt[b];
+          }
+        }
+        rotf[lane] = 0;
+        if (p >= 0) {
+          if (p > q) {
+            const int tmp = p;
+            p = q;
+            q = tmp;
+          }
+          pp[lane] = p;
+          qq[lane] = q;
+          const double apq = A[p + q * LA];
+          if (fabs(apq) > thr) {
+            double c, sv;
+            rot_params_small(A[p + p * LA], A[q + q * LA], apq, inv_scale, c, sv);
+            cs[lane] = c;
+            sn[lane] = sv;
+            rotf[lane] = 1;
+            mine = true;
+          }
+        }
+      }
+      if (!__syncthreads_or(mine)) continue;
+      if (tid == 0)
+        for (int k = 0; k < JT_MAXT; ++k) nrot += rotf[k];
+      // rows p, q of A and columns p, q of S
+      for (int it = tid; it < JT_MAXT * j; it += SM_THREADS) {
+        const int k = it / j, x = it % j;
+        if (!rotf[k]) continue;
+        const int p = pp[k], q = qq[k];
+        const double c = cs[k], sv = sn[k];
+        const double ap = A[p + x * LA], aq = A[q + x * LA];
+        A[p + x * LA] = c * ap - sv * aq;
+        A[q + x * LA] = sv * ap + c * aq;
+        const double sp = Sm[x + p * LA], sq = Sm[x + q * LA];
+        Sm[x + p * LA] = c * sp - sv * sq;
+        Sm[x + q * LA] = sv * sp + c * sq;
+      }
+      __syncthreads();
+      // columns p, q of A
+      for (int it = tid; it < JT_MAXT * j; it += SM_THREADS) {
+        const int k = it / j, x = it % j;
+        if (!rotf[k]) continue;
+        const int p = pp[k], q = qq[k];
+        const double c = cs[k], sv = sn[k];
+        const double ap = A[x + p * LA], aq = A[x + q * LA];
+        A[x + p * LA] = c * ap - sv * aq;
+        A[x + q * LA] = sv * ap + c * aq;
+      }
+      __syncthreads();
+      // keep each rotated 2 x 2 diagonal block exactly symmetric
+      if (tid < JT_MAXT && rotf[tid]) {
+        const int p = pp[tid], q = qq[tid];
+        const double v = 0.5 * (A[p + q * LA] + A[q + p * LA]);
+        A[p + q * LA] = v;
+        A[q + p * LA] = v;
+      }
+      __syncthreads();
+    }
+  }
+  for (int e = tid; e < j * j; e += SM_THREADS) {
+    const int r = e % j, c = e / j;
+    H[r + (size_t)c * ldh] = A[r + c * LA];
+    S[r + (size_t)c * lds] = Sm[r + c * LA];
+  }
+  for (int i = tid; i < j; i += SM_THREADS) theta[i] = A[i + i * LA];
+  if (tid == 0 && sweeps_out) sweeps_out[0] = sweep;
+  if (tid == 0 && rot_out) rot_out[0] = nrot;
+}
+
+void jacobi_eig_targets_ld(cudaStream_t s, int j, double* H, int ldh, double* S, int lds, double* theta, double tol,
+                           int max_sweeps, int* sweeps_out, int ntarget, int tmode, double tshift, int* rot_out) {
+  ProfScope ps(s, PROF_JACOBI);
+  const size_t smem = sizeof(double) * 2 * SM_MAXJ * (SM_MAXJ + 1);
+  static std::atomic<uint64_t> attr_done{0};
+  once_per_device(attr_done, [&] {
+    cudaFuncSetAttribute(k_jacobi_targets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  k_jacobi_targets<<<1, SM_THREADS, smem, s>>>(j, H, ldh, S, lds, theta, tol, max_sweeps, sweeps_out, ntarget,
+                                               tmode, tshift, rot_out);
+  count_launch();
+}
+
 void jacobi_eig_fast_ld(cudaStream_t s, int j, double* H, int ldh, double* S, int lds, double* theta, double tol,
                         int max_sweeps, int* sweeps_out, double tol_rel, int ntarget, int tmode, double tshift,
                         int* rot_out) {

@@ -164,6 +164,10 @@ void jacobi_eig_cluster_ld(cudaStream_t s, int j, double* H, int ldh, double* S,
 void jacobi_eig_fast_ld(cudaStream_t s, int j, double* H, int ldh, double* S, int lds, double* theta, double tol,
                         int max_sweeps, int* sweeps_out, double tol_rel, int ntarget, int tmode, double tshift,
                         int* rot_out);
+// FP64 clean-up after an FP32 pass: Jacobi rotations of the pairs touching
+// the ntarget targets only, to |a_tx| <= tol * max|a_ij|.
+void jacobi_eig_targets_ld(cudaStream_t s, int j, double* H, int ldh, double* S, int lds, double* theta, double tol,
+                           int max_sweeps, int* sweeps_out, int ntarget, int tmode, double tshift, int* rot_out);
 // FP32 bulk pass: Sf (FP64 out) = the FP32 Jacobi rotation diagonalising H to
 // ~tol * ||H||; H is not modified.
 void jacobi_eig32_ld(cudaStream_t s, int j, const double* H, int ldh, double* Sf, int lds, double* theta, double tol,

@@ -101,9 +101,11 @@ struct Profiler {
   std::vector<cudaEvent_t> ev;
   std::vector<int> evcat;
   size_t used = 0;
+  double acc_ms[PROF_NCAT] = {};  // intervals already folded in (the buffer is reused)
+  int64_t acc_n[PROF_NCAT] = {};
   void start(size_t cap) {
     on = true;
-    for (int c = 0; c < PROF_NCAT; ++c) depth[c] = 0;
+    for (int c = 0; c < PROF_NCAT; ++c) depth[c] = 0, acc_ms[c] = 0.0, acc_n[c] = 0;
     while (ev.size() < cap) {
       cudaEvent_t e;
       if (cudaEventCreate(&e) != cudaSuccess) break;
@@ -112,27 +114,33 @@ struct Profiler {
     evcat.assign(ev.size(), 0);
     used = 0;
   }
+  // times of the recorded intervals into acc (waits for the last one)
+  void fold() {
+    for (size_t i = 0; i + 1 < used; i += 2) {
+      float t = 0.f;
+      if (cudaEventSynchronize(ev[i + 1]) == cudaSuccess && cudaEventElapsedTime(&t, ev[i], ev[i + 1]) == cudaSuccess) {
+        acc_ms[evcat[i]] += t;
+        acc_n[evcat[i]] += 1;
+      }
+    }
+    used = 0;
+  }
   void mark(cudaStream_t s, int cat, bool begin) {
     if (!on) return;
     if (begin && depth[cat]++ > 0) return;
     if (!begin && --depth[cat] > 0) return;
-    if (used >= ev.size()) return;
     if (!begin && (used & 1) == 0) return;  // unmatched end
     if (begin && (used & 1) == 1) return;   // another class is open: skip nested
+    if (begin && used + 2 > ev.size()) fold();  // full: fold the finished intervals, reuse the events
+    if (used >= ev.size()) return;
     cudaEventRecord(ev[used], s);
     evcat[used] = cat;
     ++used;
   }
   void finish(double* ms, int64_t* cnt) {
+    fold();
     on = false;
-    for (size_t i = 0; i + 1 < used; i += 2) {
-      float t = 0.f;
-      if (cudaEventSynchronize(ev[i + 1]) == cudaSuccess && cudaEventElapsedTime(&t, ev[i], ev[i + 1]) == cudaSuccess) {
-        ms[evcat[i]] += t;
-        cnt[evcat[i]] += 1;
-      }
-    }
-    used = 0;
+    for (int c = 0; c < PROF_NCAT; ++c) ms[c] += acc_ms[c], cnt[c] += acc_n[c];
   }
 };
 static thread_local Profiler g_prof;
@@ -295,7 +303,10 @@ static COp<T> autotune_spmm(cudaStream_t s, Pool& pool, const SparseView<T>& A, 
   }
   COp<T> two{&A, &At, Z, n, 2, 0, la, lat};
   const float t2 = time_launches(s, e0, e1, [&] { two.apply(s, b, X, Y); });
-  if (t2 < tbest) best = two;
+  // the two-phase schedule sums in a fixed order (the fused one's atomics do
+  // not): keep it unless the fused schedule is clearly faster, so repeated
+  // solves take the same path
+  if (t2 <= tbest / 0.85f) best = two;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   best.calls = 0;
@@ -336,7 +347,7 @@ static void frame_from_true(cudaStream_t s, int j, const double* Ht, double* S, 
 // FP64 accuracy.  theta = diagonal of the final frame, S = its rotation.
 static void eig_mixed(cudaStream_t s, int j, const double* Ht, double* S, double* Aw, double* Sf, double* theta,
                       double* w1, double* w2, bool s_ident, bool fp64_cleanup, int ntarget, int tmode, double tshift,
-                      int* counters, double rel = JAC_REL) {
+                      int* counters, double rel = JAC_REL, bool targets_only = false) {
   frame_from_true(s, j, Ht, S, Aw, w1, w2, s_ident ? -1 : 0);
   jacobi_eig32_ld(s, j, Aw, LD, Sf, LD, theta, 1e-6, 30, counters, counters + 1);
   if (s_ident) {
@@ -348,7 +359,10 @@ static void eig_mixed(cudaStream_t s, int j, const double* Ht, double* S, double
                             cudaMemcpyDeviceToDevice, s));
   }
   frame_from_true(s, j, Ht, S, Aw, w1, w2, fp64_cleanup ? 2 : 1);
-  if (fp64_cleanup)
+  if (fp64_cleanup && targets_only)
+    jacobi_eig_targets_ld(s, j, Aw, LD, S, LD, theta, JAC_TOL, 60, counters + 2, ntarget, tmode, tshift,
+                          counters + 3);
+  else if (fp64_cleanup)
     jacobi_eig_ld(s, j, Aw, LD, S, LD, theta, JAC_TOL, 60, counters + 2, rel, ntarget, tmode, tshift,
                   counters + 3);
   else
@@ -695,7 +709,8 @@ struct Stage1 {
       // segment without host syncs, replayed as a cached graph
       auto segment = [&]() {
         if (mixed_eig) {
-          eig_mixed(s, j, Ht, S, Aw, Sf, theta, w1, w2, sid, true, ntg, largest ? 1 : 0, 0.0, flags + 16, JAC_REL32);
+          eig_mixed(s, j, Ht, S, Aw, Sf, theta, w1, w2, sid, true, ntg, largest ? 1 : 0, 0.0, flags + 16, JAC_REL32,
+                    true);
         } else {
           frame_from_true(s, j, Ht, S, Aw, w1, w2, sid ? -1 : 1);
           (cluster_eig ? jacobi_eig_cluster_ld : jacobi_eig_fast_ld)(s, j, Aw, LD, S, LD, theta, JAC_TOL, 60,

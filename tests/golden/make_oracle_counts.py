@@ -19,8 +19,8 @@ sys.path.insert(0, ROOT)
 from paper_1408_5535_gb300 import synth  # noqa: E402
 from oracle import phsvds_ref as R  # noqa: E402
 
-# (grid side, sigma_log, seed, k, block): the benchmark solve is grid 32
-CASES = [(16, 1.0, 2, 10, 4), (32, 1.0, 2, 10, 4)]
+# (grid side, sigma_log, seed, k, block): the benchmark solve is grid 64
+CASES = [(16, 1.0, 2, 10, 4), (32, 1.0, 2, 10, 4), (64, 1.0, 2, 10, 4)]
 
 
 def run(N, sl, seed, k, b):
