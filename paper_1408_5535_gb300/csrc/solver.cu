@@ -384,15 +384,6 @@ static void gram_full(cudaStream_t s, int n, const T* V, T* W, int j, double* Ht
   symmetrise(s, j, Ht, LD);
 }
 
-// Ht <- Y^T Ht Y for an orthonormal Y (j x jn, basis coordinates).
-static void transform_h(cudaStream_t s, int j, int jn, double* Ht, const double* Y, double* w1, double* w2) {
-  small_gemm_nn(s, j, j, jn, Ht, LD, Y, LD, w1, LD);
-  small_gemm_tn(s, j, jn, jn, Y, LD, w1, LD, w2, LD);
-  CUCHK(cudaMemcpy2DAsync(Ht, LD * sizeof(double), w2, LD * sizeof(double), jn * sizeof(double), jn,
-                          cudaMemcpyDeviceToDevice, s));
-  symmetrise(s, jn, Ht, LD);
-}
-
 // ---------------------------------------------------------------------------
 // Stage 1: block GD+k on C (storage precision T)
 // ---------------------------------------------------------------------------
