@@ -18,6 +18,7 @@ import argparse
 import json
 import math
 import os
+import re
 import subprocess
 import sys
 import time
@@ -373,20 +374,46 @@ FP64_PEAK_GFLOPS = 1250.0
 JACOBI_CTAS = 8
 
 
-def measured_traffic(kernel_file, summary):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel's source
-    file is unchanged since the capture (its sha256 is recorded there)."""
+# the stage-1 projected eigensolve of a call: the FP32 pass and the FP64
+# clean-up of the target pairs, with the device helpers they call
+JACOBI_FUNCS = ["rr_pair", "rot_params", "rot_params_small", "k_jacobi_eig", "k_jacobi_targets"]
+
+
+def kernel_source_sha256(kernel_file, names):
+    """sha256 of the source text of the named functions of a .cu file (each
+    from the line that declares it to its closing brace in column 0), so that
+    edits elsewhere in the file do not invalidate a capture."""
     import hashlib
     try:
-        txt = open(os.path.join(ROOT, "profiles", summary)).read()
-        src = open(os.path.join(ROOT, "paper_1408_5535_gb300", "csrc", kernel_file), "rb").read()
+        lines = open(os.path.join(ROOT, "paper_1408_5535_gb300", "csrc", kernel_file)).read().splitlines()
     except OSError:
         return None
-    kv = dict(l.split(":", 1) for l in txt.splitlines() if ":" in l)
-    if kv.get("source_sha256", "").strip() != hashlib.sha256(src).hexdigest():
+    h = hashlib.sha256()
+    for name in names:
+        pat = re.compile(r"\b" + re.escape(name) + r"\(")
+        starts = [i for i, l in enumerate(lines) if re.match(r"(__global__|__device__)\b", l)
+                  and (pat.search(l) or (i + 1 < len(lines) and pat.search(lines[i + 1])))]
+        if len(starts) != 1:
+            return None
+        i = starts[0]
+        while i < len(lines) and lines[i] != "}":
+            h.update(lines[i].encode() + b"\n")
+            i += 1
+    return h.hexdigest()
+
+
+def measured_traffic(kernel_file, names, summary, key):
+    """DRAM bytes from a committed ncu summary, if the captured kernels' source
+    is unchanged since the capture (the summary records its sha256)."""
+    try:
+        txt = open(os.path.join(ROOT, "profiles", summary)).read()
+    except OSError:
+        return None
+    kv = dict(l.split(":", 1) for l in txt.splitlines() if ":" in l and not l.startswith("#"))
+    if kv.get("kernel_sha256", "").strip() != kernel_source_sha256(kernel_file, names):
         return None
     try:
-        return float(kv["dram_bytes_per_launch"])
+        return float(kv[key])
     except (KeyError, ValueError):
         return None
 
@@ -406,7 +433,7 @@ def roofline_for(A, prof, dom, hbm, peak_kind):
         flops = 18.0 * j_avg * rot
         per_call_ms = prof["t_class_ms"][5] / calls
         ach = flops / (per_call_ms * 1e-3) / 1e9
-        tr = measured_traffic("k_small.cu", "jacobi_cluster_grid32.txt")
+        tr = measured_traffic("k_small.cu", JACOBI_FUNCS, "jacobi_fp32_targets_grid32.txt", "dram_bytes_per_call")
         return {"bound": "alu", "kernel": "stage-1 projected eigensolve (Jacobi kernels of k_small.cu)",
                 "achieved": ach / 1e3, "peak": FP64_PEAK_GFLOPS / 1e3, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_GFLOPS, "traffic": tr,
@@ -560,7 +587,7 @@ def main():
     st, prof = r["stats"], r["prof"]
     hbm, peak_kind = peaks()
     names = ["fused A^T A SpMM", "Gram / CGS2 passes", "basis transforms / Ritz",
-             "small projected problems (SVD of R, Cholesky, transforms)", "A / A^T products (stage 2)",
+             "refined vector of stage 2 (inverse iteration on R)", "A / A^T products (stage 2)",
              "projected eigensolvers (Jacobi: FP32 pass + FP64 clean-up, or FP64 cluster)"]
     cls = prof["t_class_ms"]
     dom = int(max(range(len(cls)), key=lambda i: cls[i]))

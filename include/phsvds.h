@@ -128,8 +128,9 @@ typedef struct {
     int64_t kernel_launches;   /* CUDA kernels this solve launched */
     /* with opts.profile: device time (CUDA events) and call counts per kernel
      * class: [0] fused A^T A SpMM (products with C), [1] Gram / CGS passes,
-     * [2] basis transforms and Ritz vectors, [3] other small projected
-     * problems (SVD of R, Cholesky, transforms), [4] single products with A or
+     * [2] basis transforms and Ritz vectors, [3] the refined vector of stage
+     * 2 (inverse iteration on R; also the Jacobi SVD entry point), [4] single
+     * products with A or
      * A^T (products with B), [5] the projected eigensolvers (Jacobi, FP64 and
      * FP32 passes) */
     double t_class_ms[6];

@@ -1418,51 +1418,145 @@ __global__ void k_identity(int j, double* S, int lds) {
 }
 void set_identity(cudaStream_t s, int j, double* S, int lds) { k_identity<<<1, SM_THREADS, 0, s>>>(j, S, lds); count_launch(); }
 
-// Refined vector of stage 2: s1 = S_R[:, argmin sig] (basis coordinates), the
-// Rayleigh quotient theta1 = s1^T H s1 = (S^T s1)^T A (S^T s1), written to
-// out[0] = theta1, out[1] = sigma_min(R), s1 to s1_out (j).
-__global__ void k_refined(int j, const double* __restrict__ SR, int ldr, const double* __restrict__ sig,
-                          const double* __restrict__ S, int lds, const double* __restrict__ A, int lda,
-                          double* __restrict__ s1_out, double* __restrict__ out) {
-  __shared__ double s1[SM_MAXJ], y[SM_MAXJ], ay[SM_MAXJ];
-  __shared__ int imin;
-  const int tid = threadIdx.x;
-  if (tid == 0) {
-    int b = 0;
-    for (int c = 1; c < j; ++c)
-      if (sig[c] < sig[b]) b = c;
-    imin = b;
+// ---------------------------------------------------------------------------
+// Refined vector of stage 2 by inverse iteration on the triangular factor R
+// of W - shift V (Sec. 3.2 needs only the smallest right singular vector of
+// R, not the whole SVD): x <- (R^T R)^{-1} x, i.e. a forward solve with R^T
+// and a back solve with R, each followed by normalisation, from the start x0
+// (the previous refined coordinates; a fixed all-positive vector when x0 is
+// null, zero or not finite).  A pivot |r_kk| below 2^-52 max |r_ab| is raised
+// to that value, the usual guard of inverse iteration: it only acts when R is
+// singular to working precision, and the guarded solve then returns the null
+// direction.  The steps stop once rho = ||R x|| falls by less than a relative
+// tau, or after maxit steps; the x with the smallest rho is kept.  Each step
+// multiplies the components off the smallest singular direction by
+// (sigma_min / sigma_2)^2, so near convergence of the outer iteration one
+// step settles it.
+// One warp; lane l holds rows l and l + 32 (j <= 64).  All branch decisions
+// are taken on warp-uniform values (butterfly sums, broadcasts from lane 0).
+// Outputs: s1_out (j, unit norm), out[0] = theta1 = s1^T H s1, out[1] = rho,
+// steps_out (optional) = steps taken.
+// ---------------------------------------------------------------------------
+constexpr int RI_LA = SM_MAXJ + 1;
+
+__device__ inline double warp_bcast0(double v) { return __shfl_sync(0xffffffffu, v, 0); }
+
+__global__ void __launch_bounds__(32) k_refined_inv(int j, const double* __restrict__ R, int ldr,
+                                                   const double* __restrict__ x0, const double* __restrict__ H,
+                                                   int ldh, int maxit, double tau, double* __restrict__ s1_out,
+                                                   double* __restrict__ out, int* __restrict__ steps_out) {
+  __shared__ double Rs[SM_MAXJ * RI_LA];
+  __shared__ double invd[SM_MAXJ];
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x;
+  const int i0 = lane, i1 = lane + 32;
+  const bool h0 = i0 < j, h1 = i1 < j;
+  double rmax = 0.0;
+  for (int e = lane; e < j * j; e += 32) {
+    const int r = e % j, c = e / j;
+    const double v = r <= c ? R[r + (size_t)c * ldr] : 0.0;
+    Rs[r + c * RI_LA] = v;
+    rmax = fmax(rmax, fabs(v));
   }
-  __syncthreads();
-  for (int r = tid; r < j; r += blockDim.x) s1[r] = SR[r + (size_t)imin * ldr];
-  __syncthreads();
-  for (int i = tid; i < j; i += blockDim.x) {
-    double acc = 0.0;
-    if (S) {
-      for (int r = 0; r < j; ++r) acc = fma(S[r + (size_t)i * lds], s1[r], acc);
-    } else {
-      acc = s1[i];
+  for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(FULL, rmax, o));
+  rmax = warp_bcast0(rmax);
+  __syncwarp();
+  const double tiny = rmax > 0.0 ? rmax * 0x1p-52 : 1.0;
+  for (int i = lane; i < j; i += 32) {
+    double d = Rs[i + i * RI_LA];
+    if (!(fabs(d) >= tiny)) d = d < 0.0 ? -tiny : tiny;
+    invd[i] = 1.0 / d;
+  }
+  __syncwarp();
+  // start vector
+  double x_0 = 0.0, x_1 = 0.0;
+  if (x0) {
+    x_0 = h0 ? x0[i0] : 0.0;
+    x_1 = h1 ? x0[i1] : 0.0;
+  }
+  double nx = warp_bcast0(sqrt(warp_sum(x_0 * x_0 + x_1 * x_1)));
+  if (!(nx > 0.0) || !isfinite(nx)) {
+    const double g = 0.6180339887498949;
+    x_0 = h0 ? 1.0 + (i0 * g - floor(i0 * g)) : 0.0;
+    x_1 = h1 ? 1.0 + (i1 * g - floor(i1 * g)) : 0.0;
+    nx = warp_bcast0(sqrt(warp_sum(x_0 * x_0 + x_1 * x_1)));
+  }
+  x_0 /= nx;
+  x_1 /= nx;
+  // rho(x) = ||R x||
+  auto rnorm = [&](double a0, double a1) {
+    double w0 = 0.0, w1 = 0.0;
+    for (int c = 0; c < j; ++c) {
+      const double xc = __shfl_sync(FULL, c < 32 ? a0 : a1, c & 31);
+      if (i0 <= c) w0 = fma(Rs[i0 + c * RI_LA], xc, w0);
+      if (i1 <= c) w1 = fma(Rs[i1 + c * RI_LA], xc, w1);
     }
-    y[i] = acc;
+    return warp_bcast0(sqrt(warp_sum(w0 * w0 + w1 * w1)));
+  };
+  double rho = rnorm(x_0, x_1);
+  int step = 0;
+  while (step < maxit) {
+    ++step;
+    double b0 = x_0, b1 = x_1;
+    // R^T y = x (forward substitution; row k of R is column k of R^T)
+    for (int k = 0; k < j; ++k) {
+      const double yk = __shfl_sync(FULL, k < 32 ? b0 : b1, k & 31) * invd[k];
+      if (lane == (k & 31)) {
+        if (k < 32) b0 = yk;
+        else b1 = yk;
+      }
+      if (h0 && i0 > k) b0 = fma(-Rs[k + i0 * RI_LA], yk, b0);
+      if (h1 && i1 > k) b1 = fma(-Rs[k + i1 * RI_LA], yk, b1);
+    }
+    double nb = warp_bcast0(sqrt(warp_sum(b0 * b0 + b1 * b1)));
+    if (!(nb > 0.0) || !isfinite(nb)) break;
+    b0 /= nb;
+    b1 /= nb;
+    // R z = y (back substitution)
+    for (int k = j - 1; k >= 0; --k) {
+      const double zk = __shfl_sync(FULL, k < 32 ? b0 : b1, k & 31) * invd[k];
+      if (lane == (k & 31)) {
+        if (k < 32) b0 = zk;
+        else b1 = zk;
+      }
+      if (i0 < k) b0 = fma(-Rs[i0 + k * RI_LA], zk, b0);
+      if (i1 < k) b1 = fma(-Rs[i1 + k * RI_LA], zk, b1);
+    }
+    nb = warp_bcast0(sqrt(warp_sum(b0 * b0 + b1 * b1)));
+    if (!(nb > 0.0) || !isfinite(nb)) break;
+    b0 /= nb;
+    b1 /= nb;
+    const double rn = rnorm(b0, b1);
+    if (!isfinite(rn)) break;
+    const bool better = rn < rho;
+    const bool stalled = !(rn < rho * (1.0 - tau));
+    if (better) {
+      x_0 = b0;
+      x_1 = b1;
+      rho = rn;
+    }
+    if (stalled) break;
   }
-  __syncthreads();
-  for (int i = tid; i < j; i += blockDim.x) {
-    double acc = 0.0;
-    for (int r = 0; r < j; ++r) acc = fma(A[i + (size_t)r * lda], y[r], acc);
-    ay[i] = acc;
+  // theta1 = s1^T H s1
+  double a0 = 0.0, a1 = 0.0;
+  for (int c = 0; c < j; ++c) {
+    const double xc = __shfl_sync(FULL, c < 32 ? x_0 : x_1, c & 31);
+    if (h0) a0 = fma(H[i0 + (size_t)c * ldh], xc, a0);
+    if (h1) a1 = fma(H[i1 + (size_t)c * ldh], xc, a1);
   }
-  __syncthreads();
-  if (tid == 0) {
-    double th = 0.0;
-    for (int r = 0; r < j; ++r) th = fma(y[r], ay[r], th);
+  const double th = warp_bcast0(warp_sum(x_0 * a0 + x_1 * a1));
+  if (h0) s1_out[i0] = x_0;
+  if (h1) s1_out[i1] = x_1;
+  if (lane == 0) {
     out[0] = th;
-    out[1] = sig[imin];
+    out[1] = rho;
+    if (steps_out) *steps_out = step;
   }
-  for (int r = tid; r < j; r += blockDim.x) s1_out[r] = s1[r];
 }
-void refined_vector(cudaStream_t s, int j, const double* SR, int ldr, const double* sig, const double* S, int lds,
-                    const double* A, int lda, double* s1_out, double* out) {
-  k_refined<<<1, SM_MAXJ, 0, s>>>(j, SR, ldr, sig, S, lds, A, lda, s1_out, out); count_launch();
+void refined_inverse(cudaStream_t s, int j, const double* R, int ldr, const double* x0, const double* H, int ldh,
+                     int maxit, double tau, double* s1_out, double* out, int* steps_out) {
+  ProfScope ps(s, PROF_SMALL);
+  k_refined_inv<<<1, 32, 0, s>>>(j, R, ldr, x0, H, ldh, maxit, tau, s1_out, out, steps_out); count_launch();
 }
 
 }  // namespace ph

@@ -186,8 +186,8 @@ void set_identity(cudaStream_t s, int j, double* S, int lds);
 void h_append(cudaStream_t s, int j0, int nb, double* H, int ldh, double* S, int lds, const double* Hn);
 void ns_factor(cudaStream_t s, int j, double* F, int ldf);
 void symmetrise(cudaStream_t s, int j, double* A, int lda);
-void refined_vector(cudaStream_t s, int j, const double* SR, int ldr, const double* sig, const double* S, int lds,
-                    const double* A, int lda, double* s1_out, double* out);
+void refined_inverse(cudaStream_t s, int j, const double* R, int ldr, const double* x0, const double* H, int ldh,
+                     int maxit, double tau, double* s1_out, double* out, int* steps_out);
 void qr_column(cudaStream_t s, int c, const double* g1, const double* g2, const double* tnorm2, double* R, int ldr,
                double* G, int ldg, double* SR, int ldsr, double* minv, int update_g);
 

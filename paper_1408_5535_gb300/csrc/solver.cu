@@ -32,6 +32,8 @@ constexpr double JAC_REL = 1e-8;          // relative threshold of the other pai
 constexpr int W_REFRESH = 16;             // stage-1 restarts between recomputations of W = C V
 constexpr double EIG32_GATE = 1e-5;       // FP32-first projected solve when the targets are >= this x theta_max
 constexpr double JAC_REL32 = 1e-6;        // its FP64 clean-up: relative threshold of the non-target pairs
+constexpr int RI_MAXIT = 24;               // stage 2: inverse-iteration steps for the refined vector (at most)
+constexpr double RI_TAU = 1e-10;          // ... which stop once ||R x|| falls by less than this (relative)
 constexpr double STAG_NEAR = 2.0;         // stage-1 stagnation: residual within 2x of its tolerance ...
 constexpr double STAG_RATIO = 100.0;      // ... or within 100x for STAG_LONG iterations without halving
 constexpr int64_t STAG_LONG = 2000;
@@ -1046,10 +1048,10 @@ struct Stage2 {
   double time_limit_s;
   std::chrono::steady_clock::time_point t0;
   double *V, *W, *Q, *Xl, *x0, *tv, *xr, *rr;
-  double *Aw, *S, *Ht, *w1, *w2, *Sf, *theta, *R, *G, *SR, *sig, *s1, *rq, *Hn, *Hfull, *Yt, *A2, *cand, *excl,
+  double *Aw, *S, *Ht, *w1, *w2, *Sf, *theta, *R, *s1, *rq, *Hn, *Hfull, *Yt, *A2, *cand, *excl,
       *sprev, *nrm, *G1, *G2, *tn2, *minv, *thl;
-  bool s_ident = true, sr_ident = true;
-  int *order, *sw, *jn, *idx_lock;
+  bool s_ident = true;
+  int *order, *sw, *jn;
   Orth1 orth;
   int j = 0, nl = 0;
   int64_t iters = 0, restarts = 0, mv = 0;
@@ -1076,9 +1078,6 @@ struct Stage2 {
     Sf = pool.get<double>(LD * LD);
     theta = pool.get<double>(LD);
     R = pool.get<double>(LD * LD);
-    G = pool.get<double>(LD * LD);
-    SR = pool.get<double>(LD * LD);
-    sig = pool.get<double>(LD);
     s1 = pool.get<double>(LD);
     rq = pool.get<double>(4);
     Hn = pool.get<double>(LD);
@@ -1097,7 +1096,6 @@ struct Stage2 {
     order = pool.get<int>(LD);
     sw = pool.get<int>(16);
     jn = pool.get<int>(4);
-    idx_lock = pool.get<int>(LD);
   }
 
   void check_time() {
@@ -1121,8 +1119,8 @@ struct Stage2 {
     ++j;
   }
 
-  // QR column c of Z = W - shift V into Q(:, c), R(:, c) (update_g: also G, S_R).
-  void qr_col(int c, double shift, int update_g) {
+  // QR column c of Z = W - shift V into Q(:, c), R(:, c).
+  void qr_col(int c, double shift) {
     double* z = Q + (size_t)c * N;
     CUCHK(cudaMemcpyAsync(z, W + (size_t)c * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
     axpby(s, N, -shift, V + (size_t)c * N, 1.0, z);
@@ -1133,31 +1131,13 @@ struct Stage2 {
     cgs_pass<double>(s, N, P, z, N, 1, nullptr, G1, nullptr);
     cgs_pass<double>(s, N, P, z, N, 1, G1, G2, nullptr);
     cgs_pass<double>(s, N, P, z, N, 1, G2, nullptr, tn2);
-    qr_column(s, c, c ? G1 : nullptr, c ? G2 : nullptr, tn2, R, LD, G, LD, SR, LD, minv, update_g);
+    qr_column(s, c, c ? G1 : nullptr, c ? G2 : nullptr, tn2, R, LD, nullptr, 0, nullptr, 0, minv, 0);
     scal(s, N, 0.0, minv, z);
   }
 
   void full_qr(double shift) {
     zero(s, R, LD * LD);  // the strictly lower triangle stays zero
-    for (int c = 0; c < j; ++c) qr_col(c, shift, 0);
-    set_identity(s, j, SR, LD);
-    sr_ident = true;
-  }
-
-  // Working matrix of the one-sided Jacobi SVD, rebuilt from the exact R:
-  // S_R <- S_R (3I - S_R^T S_R)/2, G = R S_R.
-  void svd_frame() {
-    if (sr_ident) {
-      CUCHK(cudaMemcpy2DAsync(G, LD * sizeof(double), R, LD * sizeof(double), j * sizeof(double), j,
-                              cudaMemcpyDeviceToDevice, s));
-      return;
-    }
-    small_gemm_tn(s, j, j, j, SR, LD, SR, LD, w1, LD);
-    ns_factor(s, j, w1, LD);
-    small_gemm_nn(s, j, j, j, SR, LD, w1, LD, w2, LD);
-    CUCHK(cudaMemcpy2DAsync(SR, LD * sizeof(double), w2, LD * sizeof(double), j * sizeof(double), j,
-                            cudaMemcpyDeviceToDevice, s));
-    small_gemm_nn(s, j, j, j, R, LD, SR, LD, G, LD);
+    for (int c = 0; c < j; ++c) qr_col(c, shift);
   }
 
   // Transform the basis by Y (j x jn basis coordinates, from build_transform).
@@ -1221,19 +1201,13 @@ struct Stage2 {
         full_qr(shift);
         qr_full = false;
       }
-      eig_mixed(s, j, Ht, S, Aw, Sf, theta, w1, w2, s_ident, false, 1, 2, shift, sw + 2);
-      s_ident = false;
-      order_theta(s, j, theta, 2, shift, order);
-      svd_frame();
-      sr_ident = false;
-      jacobi_svd_ld(s, j, G, LD, SR, LD, sig, 1e-15, 60, sw + 1);
-      refined_vector(s, j, SR, LD, sig, nullptr, 0, Ht, LD, s1, rq);
+      // refined vector: smallest right singular vector of R (Sec. 3.2)
+      refined_inverse(s, j, R, LD, have_prev ? sprev : nullptr, Ht, LD, RI_MAXIT, RI_TAU, s1, rq, sw + 1);
       tall_times_small<double>(s, N, V, N, j, s1, LD, 1, xr, N, nullptr, 0, nullptr, nullptr);
       zero(s, nrm, 1);
       tall_times_small<double>(s, N, W, N, j, s1, LD, 1, rr, N, xr, N, rq, nrm);
       CUCHK(cudaMemcpyAsync(h.at<double>(0), rq, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
       CUCHK(cudaMemcpyAsync(h.at<double>(16), nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
-      CUCHK(cudaMemcpyAsync(h.at<double>(32), theta, sizeof(double) * j, cudaMemcpyDeviceToHost, s));
       sync(s);
       const double th1 = *h.at<double>(0);
       const double rn = std::sqrt(std::max(*h.at<double>(16), 0.0));
@@ -1248,23 +1222,20 @@ struct Stage2 {
         th_lock.push_back(th1);
         ++target;
         if (target >= k) break;
-        // drop s1 from the basis: the other right singular vectors of R
-        {
-          double* hs = h.at<double>(8192);   // bytes [8192, 8704)
-          CUCHK(cudaMemcpyAsync(hs, sig, sizeof(double) * j, cudaMemcpyDeviceToHost, s));
+        // drop s1 from the basis: keep an orthonormal basis of its complement
+        // (the span of the other right singular vectors of R), built by
+        // Gram-Schmidt of the unit vectors against s1
+        if (j > 1) {
+          set_identity(s, j, cand, LD);
+          build_transform(s, j, S, LD, Aw, LD, cand, LD, j, 0, 0, 0, s1, LD, 1, j - 1, Yt, LD, jn, nullptr, LD);
+          CUCHK(cudaMemcpyAsync(h.at<int>(12288), jn, sizeof(int), cudaMemcpyDeviceToHost, s));
           sync(s);
-          int imin = 0;
-          for (int c = 1; c < j; ++c)
-            if (hs[c] < hs[imin]) imin = c;
-          int* hi = h.at<int>(9216);         // bytes [9216, 9472)
-          int nc = 0;
-          for (int c = 0; c < j; ++c)
-            if (c != imin) hi[nc++] = c;
-          int* idx = idx_lock;
-          CUCHK(cudaMemcpyAsync(idx, hi, sizeof(int) * nc, cudaMemcpyHostToDevice, s));
-          gather_cols(s, j, SR, LD, idx, nc, cand, LD, nullptr, nullptr);
-          build_transform(s, j, S, LD, Aw, LD, cand, LD, nc, nc, nc, 1, excl, LD, 0, nc, Yt, LD, jn, nullptr, LD);
+          const int nc = *h.at<int>(12288);
+          if (nc < 1 || nc > j - 1) throw PhError{PHSVDS_ERR_BREAKDOWN, "stage 2: locking complement size out of range"};
           transform(nc);
+        } else {
+          j = 0;  // the basis was s1 alone
+          s_ident = true;
         }
         CUCHK(cudaMemcpyAsync(tv, x0 + (size_t)target * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
         append(tv);
@@ -1276,6 +1247,11 @@ struct Stage2 {
       }
       if (j >= maxb) {
         if (++restarts > max_restarts) throw PhError{PHSVDS_ERR_NOT_CONVERGED, "stage 2: restart limit reached"};
+        // Ritz pairs of H ordered by closeness to the shift (only the
+        // restart needs them)
+        eig_mixed(s, j, Ht, S, Aw, Sf, theta, w1, w2, s_ident, true, 1, 2, shift, sw + 2);
+        s_ident = false;
+        order_theta(s, j, theta, 2, shift, order);
         // candidates: s1, Ritz vectors by closeness to the shift, then the previous s1
         CUCHK(cudaMemcpyAsync(cand, s1, sizeof(double) * j, cudaMemcpyDeviceToDevice, s));
         gather_cols(s, j, S, LD, order, j, cand + LD, LD, nullptr, nullptr);
@@ -1306,7 +1282,7 @@ struct Stage2 {
       CUCHK(cudaMemcpyAsync(tv, rr, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
       append(tv);
       CUCHK(cudaMemsetAsync(sprev + (j - 1), 0, sizeof(double), s));
-      if (!qr_full) qr_col(j - 1, shift, 1);
+      if (!qr_full) qr_col(j - 1, shift);
     }
   }
 };
