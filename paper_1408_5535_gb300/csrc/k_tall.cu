@@ -34,9 +34,41 @@ constexpr int CG_PC = CG_MAXP / (CG_THREADS / 32);  // columns per warp
 
 __device__ inline double atomic_add_f64(double* p, double v) { return atomicAdd(p, v); }
 
-// Block CGS pass.  Phase A: one thread per row loads the row of P (into smem)
-// and of T, applies T -= P Gsub, stores T.  Phase B: warp w accumulates the
-// P^T T entries of columns w, w+8, ... and the T^T T pairs k = w, w+8, ...
+// Butterfly reduce-scatter of the N values each lane holds (N a power of two):
+// at the level with lane offset O, a lane keeps the half of its live values
+// selected by its lane bit O and adds the partner's copy of that half, so a
+// warp sum of N values costs N - 1 adds per lane instead of 5 N.  Afterwards
+// (N >= 32) lane l holds the warp sums of values l * (N / 32) + u in v[u],
+// u < N / 32; (N < 32) v[0] of lane l holds the warp sum of value l / (32 / N).
+template <typename T, int N, int O, int CUR>
+__device__ __forceinline__ void reduce_scatter_step(T (&v)[N], int lane) {
+  if constexpr (O > 0) {
+    if constexpr (CUR > 1) {
+      constexpr int H = CUR / 2;
+      const bool up = (lane & O) != 0;
+#pragma unroll
+      for (int i = 0; i < H; ++i) {
+        const T send = up ? v[i] : v[i + H];
+        const T keep = up ? v[i + H] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+      }
+      reduce_scatter_step<T, N, O / 2, H>(v, lane);
+    } else {
+      v[0] += __shfl_xor_sync(0xffffffffu, v[0], O);
+      reduce_scatter_step<T, N, O / 2, 1>(v, lane);
+    }
+  }
+}
+template <typename T, int N>
+__device__ __forceinline__ void reduce_scatter(T (&v)[N], int lane) {
+  reduce_scatter_step<T, N, 16, N>(v, lane);
+}
+
+// Block CGS pass.  Phase A: all threads load the chunk of P into shared memory
+// (independent loads, so short vectors do not wait on one load per column),
+// then one thread per row applies T -= P Gsub and stores T.  Phase B: warp w
+// accumulates the P^T T entries of columns w, w+8, ... and the T^T T pairs
+// k = w, w+8, ...
 template <typename T, int Q>
 __global__ void __launch_bounds__(CG_THREADS) k_cgs_pass(int n, Basis<T> P, T* __restrict__ Tb, int ldt, int q,
                                                          const double* __restrict__ Gsub, double* __restrict__ Gout,
@@ -65,14 +97,21 @@ __global__ void __launch_bounds__(CG_THREADS) k_cgs_pass(int n, Basis<T> P, T* _
     const int i = row0 + tid;
     const bool act = tid < rows && i < n;
     // ---- phase A
+#pragma unroll 4
+    for (int e = tid; e < p * rows; e += CG_THREADS) {
+      const int c = e / rows, rr = e - c * rows;
+      const int ii = row0 + rr;
+      T pc = T(0);
+      if (ii < n) pc = c < P.c1 ? P.p1[(size_t)c * P.ld1 + ii] : P.p2[(size_t)(c - P.c1) * P.ld2 + ii];
+      Ps[(size_t)c * rows + rr] = pc;
+    }
     T t[Q];
 #pragma unroll
     for (int r = 0; r < Q; ++r) t[r] = (act && r < q) ? Tb[(size_t)r * ldt + i] : T(0);
-    for (int c = 0; c < p; ++c) {
-      T pc = T(0);
-      if (act) pc = c < P.c1 ? P.p1[(size_t)c * P.ld1 + i] : P.p2[(size_t)(c - P.c1) * P.ld2 + i];
-      if (tid < rows) Ps[(size_t)c * rows + tid] = pc;
-      if (Gsub) {
+    __syncthreads();
+    if (Gsub && tid < rows) {
+      for (int c = 0; c < p; ++c) {
+        const T pc = Ps[(size_t)c * rows + tid];
 #pragma unroll
         for (int r = 0; r < Q; ++r) t[r] = fma(-pc, Gs[c + r * p], t[r]);
       }
@@ -114,13 +153,18 @@ __global__ void __launch_bounds__(CG_THREADS) k_cgs_pass(int n, Basis<T> P, T* _
   }
   // ---- reduce and accumulate into the FP64 outputs
   if (Gout) {
+    constexpr int NV = CG_PC * Q;
+    constexpr int PER = NV >= 32 ? NV / 32 : 1;   // sums held per lane
+    constexpr int REP = NV >= 32 ? 1 : 32 / NV;   // lanes holding the same sum
+    T (&v)[NV] = reinterpret_cast<T (&)[NV]>(accG);
+    reduce_scatter<T, NV>(v, lane);
+    if (lane % REP == 0) {
 #pragma unroll
-    for (int a = 0; a < CG_PC; ++a) {
-      const int c = warp + a * (CG_THREADS / 32);
-#pragma unroll
-      for (int r = 0; r < Q; ++r) {
-        double v = (double)warp_sum(accG[a][r]);
-        if (lane == 0 && c < p && r < q) atomic_add_f64(&Gout[c + (size_t)r * p], v);
+      for (int u = 0; u < PER; ++u) {
+        const int idx = NV >= 32 ? lane * PER + u : lane / REP;
+        const int a = idx / Q, r = idx % Q;
+        const int c = warp + a * (CG_THREADS / 32);
+        if (c < p && r < q) atomic_add_f64(&Gout[c + (size_t)r * p], (double)v[u]);
       }
     }
   }
@@ -203,17 +247,32 @@ __global__ void __launch_bounds__(TS_ROWS) k_tall_small(int n, const T* P, int l
   for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const int i = ch * R + tid;
     const bool act = i < n;
+#pragma unroll 4
     for (int a = 0; a < p; ++a) Ps[(size_t)a * R + tid] = act ? P[(size_t)a * ldp + i] : T(0);
     __syncthreads();  // every row of the chunk is read before any (in-place) write
-    for (int c = 0; c < r; ++c) {
-      T acc = T(0);
-      const T* yc = Ys + (size_t)c * p;
-      for (int a = 0; a < p; ++a) acc = fma(Ps[(size_t)a * R + tid], yc[a], acc);
-      if (theta && act) acc = fma((T)(-theta[c]), Xs[(size_t)c * ldx + i], acc);
-      if (act) Out[(size_t)c * ldo + i] = acc;
-      if (norms2) {
-        double v = warp_sum((double)acc * (double)acc);
-        if ((tid & 31) == 0) atomicAdd(&nrm[c], v);
+    // four output columns at a time: four independent FMA chains per thread
+    for (int c0 = 0; c0 < r; c0 += 4) {
+      const int nc = r - c0 < 4 ? r - c0 : 4;
+      T acc[4] = {T(0), T(0), T(0), T(0)};
+      const T* y0 = Ys + (size_t)c0 * p;
+      for (int a = 0; a < p; ++a) {
+        const T pa = Ps[(size_t)a * R + tid];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (u < nc) acc[u] = fma(pa, y0[(size_t)u * p + a], acc[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (u < nc) {
+          const int c = c0 + u;
+          T o = acc[u];
+          if (theta && act) o = fma((T)(-theta[c]), Xs[(size_t)c * ldx + i], o);
+          if (act) Out[(size_t)c * ldo + i] = o;
+          if (norms2) {
+            double v = warp_sum((double)o * (double)o);
+            if ((tid & 31) == 0) atomicAdd(&nrm[c], v);
+          }
+        }
       }
     }
     __syncthreads();
