@@ -368,7 +368,9 @@ phsvds_status phsvds_jacobi_eig_cluster_f64(phsvds_handle h, int j, double* H, d
 /*
  * Kernel-level entry point: one-CTA FP64 one-sided (Hestenes) Jacobi SVD of a
  * j x j matrix G (refined projection, Algorithm 2 step 8: R = U Sigma S^T).
- * DEVICE pointers.  G (column-major, overwritten by G * J = U Sigma), S (on
+ * The solver itself needs only the smallest right singular vector of R per
+ * iteration and computes it by inverse iteration; this entry point gives the
+ * whole SVD.  DEVICE pointers.  G (column-major, overwritten by G * J = U Sigma), S (on
  * entry an orthogonal start -- identity for a cold start -- on exit S * J),
  * sig (j) the column norms of the result.  1 <= j <= 64.
  */
