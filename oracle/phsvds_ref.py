@@ -194,6 +194,8 @@ class Opts:
     seed: int = 0
     max_iters: int = 10 ** 7
     trace: object = None        # optional callable(stage, iteration, info dict)
+    stage2_inner: str = "none"  # "none": GD, t = r; "qmr": JDQMR, t from the correction equation (Sec. 4)
+    inner_maxit: int = 40       # READING: inner QMR steps per outer iteration, at most
 
 
 @dataclass
@@ -387,6 +389,89 @@ def rayleigh_ritz_post(ops: Ops, Xl: np.ndarray, state: dict, k: int, largest: b
 # stage 2: refined projection on B (Algorithm 2)
 # ---------------------------------------------------------------------------
 
+def symmetric_qmr(apply_M, b: np.ndarray, Qd: np.ndarray, steps: int):
+    """Symmetric QMR iterates for M t = b, M symmetric on the complement of
+    Qd (orthonormal columns), b orthogonal to Qd; a generator yielding, after
+    step k, (t_k, ||b - M t_k||, the Lanczos basis, the coefficients y_k).
+
+    Lanczos on M from b / ||b|| (each new vector orthogonalised twice against
+    Qd and every earlier Lanczos vector), T_k the (k+1) x k tridiagonal, and
+    y_k = argmin ||beta e_1 - T_k y||.  With a symmetric M and no
+    preconditioner the Lanczos vectors are orthonormal, so the quasi-residual
+    that QMR minimises is the true residual (the iterates are MINRES's).
+    apply_M(q) returns (M q, extra) and the extras are handed back per step.
+    """
+    beta0 = float(np.linalg.norm(b))
+    if not beta0 > 0:
+        return
+    Qs = [b / beta0]
+    extras = []
+    T = np.zeros((steps + 1, steps))
+    for k in range(steps):
+        w, extra = apply_M(Qs[k])
+        extras.append(extra)
+        T[k, k] = float(Qs[k] @ w)
+        basis = np.column_stack([Qd] + Qs) if Qd.shape[1] else np.column_stack(Qs)
+        for _ in range(2):
+            w = w - basis @ (basis.T @ w)
+        T[k + 1, k] = float(np.linalg.norm(w))
+        if k + 1 < steps:
+            T[k, k + 1] = T[k + 1, k]
+        rhs = np.zeros(k + 2)
+        rhs[0] = beta0
+        y = np.linalg.lstsq(T[:k + 2, :k + 1], rhs, rcond=None)[0]
+        g = float(np.linalg.norm(rhs - T[:k + 2, :k + 1] @ y))
+        t = np.column_stack(Qs) @ y
+        yield t, g, extras, y
+        if not T[k + 1, k] > 1e-300:
+            return
+        Qs.append(w / T[k + 1, k])
+
+
+def jd_correction(ops: "Ops", Xl: np.ndarray, x: np.ndarray, Bx: np.ndarray, mu: float, r: np.ndarray,
+                  tol: float, maxit: int, stats: dict, patience: int = 2) -> np.ndarray:
+    """Correction of the Jacobi-Davidson method on B (Sec. 4, the correction
+    equation (I - w w^T)(B - mu I)(I - w w^T) t = sigma~ w - B w with w the
+    refined vector x, here also deflating the locked vectors Xl), solved
+    inexactly by symmetric QMR with a dynamic stop.
+    READING (the paper names JDQMR and its near-optimal inner stopping but
+    states neither): after each inner step the updated vector
+    z = (x + t_k) / ||x + t_k|| is scored by its eigen-residual
+    eta_k = ||B z - (z^T B z) z|| (B t_k from the products the Lanczos steps
+    already made); the steps stop once eta_k < tol, or once eta has not
+    fallen below 0.9 times its best value for `patience` steps in a row, or
+    after maxit steps; the iterate with the smallest eta is returned."""
+    Qd = np.column_stack([Xl, x]) if Xl.shape[1] else x[:, None]
+
+    def apply_M(q):
+        bq = ops.B(q)[:, 0]
+        w = bq - mu * q
+        w = w - Qd @ (Qd.T @ w)
+        return w, bq
+
+    b = -(r - Qd @ (Qd.T @ r))
+    best_t, best_eta, since = None, math.inf, 0
+    k = 0
+    for t, g, extras, y in symmetric_qmr(apply_M, b, Qd, maxit):
+        k += 1
+        z = x + t
+        Bz = Bx + np.column_stack(extras) @ y
+        nz = float(np.linalg.norm(z))
+        z, Bz = z / nz, Bz / nz
+        rho = float(z @ Bz)
+        eta = float(np.linalg.norm(Bz - rho * z))
+        if eta < 0.9 * best_eta:
+            since = 0
+        else:
+            since += 1
+        if eta < best_eta:
+            best_t, best_eta = t, eta
+        if best_eta < tol or since >= patience:
+            break
+    stats["inner2"] = stats.get("inner2", 0) + k
+    return best_t if best_t is not None else r
+
+
 def stage2(ops: Ops, sig: np.ndarray, Vt: np.ndarray, normA: float, delta: float, o: Opts,
            stats: dict):
     """Algorithm 2 with a GD outer loop (the PHSVDS(GD+k) variant of Sec. 5).
@@ -520,8 +605,13 @@ def stage2(ops: Ops, sig: np.ndarray, Vt: np.ndarray, normA: float, delta: float
                 shift = th1
             qr_full = True
         s_prev = s1.copy()
-        # ---- expand with t = r (Algorithm 2 step 4)
-        t = orth_append(np.hstack([Xl, V]), r[:, None], o.seed, counter)
+        # ---- expand with t = r (Algorithm 2 step 4), or with the JD correction
+        if o.stage2_inner == "qmr":
+            corr = jd_correction(ops, Xl, x, W @ s1, th1, r, delta * normA / math.sqrt(2.0),
+                                 o.inner_maxit, stats)
+        else:
+            corr = r
+        t = orth_append(np.hstack([Xl, V]), corr[:, None], o.seed, counter)
         wt = ops.B(t)
         H = np.block([[H, V.T @ wt], [wt.T @ V, t.T @ wt]])
         H = 0.5 * (H + H.T)
