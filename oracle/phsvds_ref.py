@@ -17,6 +17,9 @@ Steps, in the paper's order:
 * stage 2 (Algorithm 2): GD on B = [0 A^T; A 0] with the refined projection
   min ||(B - s I) V y|| through an incrementally updated QR of W - s V, one
   target at a time, locking and re-introduction of the next initial guess;
+  the basis grows by the residual (GD) or, in the JDQMR form of Sec. 4, by
+  an inexact solution of the Jacobi-Davidson correction equation (symmetric
+  QMR with a dynamic stop: a READING);
 * final triplet test sqrt(||r_u||^2 + ||r_v||^2) < ||A|| delta (Sec. 5).
 
 GD+k itself is named but not defined in the paper (Sec. 2.2, Sec. 5: "GD+k",
