@@ -1048,8 +1048,8 @@ struct Stage2 {
   double time_limit_s;
   std::chrono::steady_clock::time_point t0;
   double *V, *W, *Q, *Xl, *x0, *tv, *xr, *rr;
-  double *Aw, *S, *Ht, *w1, *w2, *Sf, *theta, *R, *s1, *rq, *Hn, *Hfull, *Yt, *A2, *cand, *excl,
-      *sprev, *nrm, *G1, *G2, *tn2, *minv, *thl;
+  double *Aw, *S, *Ht, *w1, *w2, *Sf, *theta, *R, *s1, *rq, *Hn, *Yt, *cand, *excl,
+      *sprev, *nrm, *G1, *G2, *tn2, *minv;
   bool s_ident = true;
   int *order, *sw, *jn;
   Orth1 orth;
@@ -1081,9 +1081,7 @@ struct Stage2 {
     s1 = pool.get<double>(LD);
     rq = pool.get<double>(4);
     Hn = pool.get<double>(LD);
-    Hfull = pool.get<double>(LD * LD);
     Yt = pool.get<double>(LD * LD);
-    A2 = pool.get<double>(LD * LD);
     cand = pool.get<double>(LD * (2 * LD + 2));
     excl = pool.get<double>(LD);
     sprev = pool.get<double>(LD);
@@ -1092,7 +1090,6 @@ struct Stage2 {
     G2 = pool.get<double>(LD);
     tn2 = pool.get<double>(4);
     minv = pool.get<double>(4);
-    thl = pool.get<double>(LD);
     order = pool.get<int>(LD);
     sw = pool.get<int>(16);
     jn = pool.get<int>(4);
