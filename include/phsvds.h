@@ -377,6 +377,23 @@ phsvds_status phsvds_jacobi_eig_cluster_f64(phsvds_handle h, int j, double* H, d
 phsvds_status phsvds_jacobi_svd_f64(phsvds_handle h, int j, double* G, double* S, double* sig,
                                     double tol, int max_sweeps, int* sweeps_out);
 
+/*
+ * Kernel-level entry point: the refined vector of stage 2 (Algorithm 2 step 8,
+ * Sec. 3.2), as the solver computes it.  s1 = the right singular vector of
+ * the smallest singular value of the j x j upper-triangular R, by inverse
+ * iteration (a forward solve with R^T and a back solve with R per step) from
+ * x0, stopping once ||R s1|| falls by less than a relative tau or after maxit
+ * steps; theta1 = s1^T H s1.  A pivot below 2^-52 max |r_ab| is raised to
+ * that value.  DEVICE pointers: R (column-major, leading dimension ldr >= j;
+ * its strictly lower triangle is ignored), x0 (j, or NULL for a fixed
+ * all-positive start), H (j x j symmetric, leading dimension ldh >= j), s1
+ * (j, unit norm on return), out (2 doubles: theta1, ||R s1||), steps_out (1
+ * int, or NULL).  1 <= j <= 64, maxit >= 1.  Nothing is allocated.
+ */
+phsvds_status phsvds_refined_vector_f64(phsvds_handle h, int j, const double* R, int ldr, const double* x0,
+                                        const double* H, int ldh, int maxit, double tau, double* s1,
+                                        double* out, int* steps_out);
+
 /* Synchronise the handle's stream. */
 phsvds_status phsvds_sync(phsvds_handle h);
 

@@ -1794,6 +1794,16 @@ phsvds_status phsvds_jacobi_svd_f64(phsvds_handle h, int j, double* G, double* S
   return e == cudaSuccess ? PHSVDS_OK : set_err(h, PHSVDS_ERR_CUDA, cudaGetErrorString(e));
 }
 
+phsvds_status phsvds_refined_vector_f64(phsvds_handle h, int j, const double* R, int ldr, const double* x0,
+                                        const double* H, int ldh, int maxit, double tau, double* s1,
+                                        double* out, int* steps_out) {
+  if (!h || j < 1 || j > LD || ldr < j || ldh < j || maxit < 1 || !(tau >= 0.0) || !R || !H || !s1 || !out)
+    return PHSVDS_ERR_INVALID;
+  refined_inverse(h->stream, j, R, ldr, x0, H, ldh, maxit, tau, s1, out, steps_out);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? PHSVDS_OK : set_err(h, PHSVDS_ERR_CUDA, cudaGetErrorString(e));
+}
+
 }  // extern "C"
 
 // ===========================================================================

@@ -94,6 +94,7 @@ def _load() -> C.CDLL:
         "phsvds_jacobi_eig_f64": ([P, I, P, P, P, D, I, P], I),
         "phsvds_jacobi_eig_cluster_f64": ([P, I, P, P, P, D, I, P], I),
         "phsvds_jacobi_svd_f64": ([P, I, P, P, P, D, I, P], I),
+        "phsvds_refined_vector_f64": ([P, I, P, I, P, P, I, I, D, P, P, P], I),
         "phsvds_sync": ([P], I),
         "phsvds_last_error": ([P], C.c_char_p),
         "phsvds_status_string": ([I], C.c_char_p),
@@ -119,7 +120,7 @@ def lib() -> C.CDLL:
 EXPORTED = ["phsvds_create", "phsvds_default_opts", "phsvds_solve", "phsvds_solve_batched", "phsvds_normal_cg",
             "phsvds_cnn_forward", "phsvds_cnn_backward", "phsvds_cnn_adam", "phsvds_ata_spmm_f64",
             "phsvds_ata_spmm_f32", "phsvds_ata_spmm_static_f64", "phsvds_csr_to_csc_f64", "phsvds_jacobi_eig_f64", "phsvds_jacobi_eig_cluster_f64",
-            "phsvds_jacobi_svd_f64", "phsvds_sync", "phsvds_last_error", "phsvds_status_string",
+            "phsvds_jacobi_svd_f64", "phsvds_refined_vector_f64", "phsvds_sync", "phsvds_last_error", "phsvds_status_string",
             "phsvds_destroy"]
 
 
@@ -294,6 +295,12 @@ def phsvds_jacobi_eig(h: Handle, j, H, S, theta, tol=1e-17, max_sweeps=60, sweep
 
 def phsvds_jacobi_svd(h: Handle, j, G, S, sig, tol=1e-15, max_sweeps=60, sweeps=None):
     h.check(lib().phsvds_jacobi_svd_f64(h.h, j, _ptr(G), _ptr(S), _ptr(sig), tol, max_sweeps, _ptr(sweeps)))
+
+
+def phsvds_refined_vector(h: Handle, j, R, ldr, x0, H, ldh, s1, out, maxit=24, tau=1e-10, steps=None):
+    """Refined vector of R (device tensors): s1, out = (theta1, ||R s1||)."""
+    h.check(lib().phsvds_refined_vector_f64(h.h, j, _ptr(R), ldr, _ptr(x0), _ptr(H), ldh, maxit, tau, _ptr(s1),
+                                            _ptr(out), _ptr(steps)))
 
 
 def phsvds_sync(h: Handle):

@@ -154,3 +154,56 @@ def test_jacobi_svd_vs_oracle(h, j):
     i = int(np.argmin(s))
     _, _, Vt = np.linalg.svd(G)
     assert abs(abs(S[:, i] @ Vt[-1]) - 1) < 1e-8
+
+
+@pytest.mark.parametrize("j,warm", [(1, False), (2, False), (21, False), (33, True), (35, False), (64, True)])
+def test_refined_vector_vs_oracle(h, j, warm):
+    """The stage-2 refined vector kernel (inverse iteration on R) against the
+    oracle's dense Jacobi SVD: the smallest singular value of R as ||R s1||,
+    the smallest right singular vector, and theta1 = s1^T H s1.  R is graded
+    like the refined projection near convergence (one tiny singular value);
+    the leading dimension is that of the solver's workspaces (64)."""
+    rng = np.random.default_rng(300 + j)
+    U = np.linalg.qr(rng.standard_normal((j, j)))[0]
+    V = np.linalg.qr(rng.standard_normal((j, j)))[0]
+    s = np.logspace(0, -2, j)
+    s[-1] = 1e-12
+    R = np.linalg.qr(U @ np.diag(s) @ V.T)[1]
+    Hs = rng.standard_normal((j, j))
+    Hs = Hs + Hs.T
+    LDp = 64
+    Rp = np.zeros((LDp, LDp))
+    Rp[:j, :j] = R
+    Rp[j:, :] = np.nan                      # rows past j must not be read
+    Hp = np.zeros((LDp, LDp))
+    Hp[:j, :j] = Hs
+    sig_ref, _, Vref = jacobi_svd(R)        # oracle: ascending singular values
+    vmin = Vref[:, 0]
+    x0 = None
+    if warm:
+        x0 = dev(vmin + 1e-3 * rng.standard_normal(j))
+    s1 = torch.empty(j, dtype=torch.float64, device="cuda")
+    out = torch.empty(2, dtype=torch.float64, device="cuda")
+    steps = torch.zeros(1, dtype=torch.int32, device="cuda")
+    native.phsvds_refined_vector(h, j, dev(Rp.ravel(order="F")), LDp, x0, dev(Hp.ravel(order="F")), LDp, s1, out,
+                                 24, 1e-10, steps)
+    native.phsvds_sync(h)
+    x = s1.cpu().numpy()
+    th, rho = out.cpu().numpy()
+    nrm = np.linalg.norm(R, 2)
+    assert abs(np.linalg.norm(x) - 1) <= 1e-14
+    assert abs(rho - sig_ref[0]) <= 1e-10 * sig_ref[0] + 4 * j * EPS64 * nrm
+    assert abs(rho - np.linalg.norm(R @ x)) <= 4 * j * EPS64 * nrm
+    if j > 1:
+        assert abs(abs(x @ vmin) - 1) <= 1e-12
+    assert abs(th - x @ Hs @ x) <= 4 * j * EPS64 * np.linalg.norm(Hs, 2)
+    assert 1 <= int(steps.item()) <= 4
+
+
+def test_refined_vector_rejects_bad_arguments(h):
+    R = dev(np.eye(4).ravel())
+    s1 = torch.empty(4, dtype=torch.float64, device="cuda")
+    out = torch.empty(2, dtype=torch.float64, device="cuda")
+    for j, ldr, maxit in [(0, 4, 1), (65, 65, 1), (4, 3, 1), (4, 4, 0)]:
+        with pytest.raises(native.PhsvdsError):
+            native.phsvds_refined_vector(h, j, R, ldr, None, R, 4, s1, out, maxit)
