@@ -199,6 +199,7 @@ class Opts:
     trace: object = None        # optional callable(stage, iteration, info dict)
     stage2_inner: str = "none"  # "none": GD, t = r; "qmr": JDQMR, t from the correction equation (Sec. 4)
     inner_maxit: int = 40       # READING: inner QMR steps per outer iteration, at most
+    stage2_precond: bool = False  # smallest targets: GD stage 2 preconditioned by [0 M A^T; A M 0], M = diag(C)^-1 (Sec. 4)
 
 
 @dataclass
@@ -475,8 +476,18 @@ def jd_correction(ops: "Ops", Xl: np.ndarray, x: np.ndarray, Bx: np.ndarray, mu:
     return best_t if best_t is not None else r
 
 
+def b_precond(ops: Ops, apply_M, y: np.ndarray) -> np.ndarray:
+    """The stage-2 preconditioner built from a preconditioner M ~ C^{-1} of
+    the first stage (Sec. 4): [0 A M; M A^T 0] in the paper's [u; v] order,
+    i.e. y = [y_v; y_u] -> [M A^T y_u; A M y_v] in the [v; u] order used
+    here.  With M = C^{-1} exactly it is a generalised inverse of B
+    (B P B = B for A of full column rank)."""
+    n = ops.n
+    return np.concatenate([apply_M(ops.Atu(y[n:])), ops.Av(apply_M(y[:n]))])
+
+
 def stage2(ops: Ops, sig: np.ndarray, Vt: np.ndarray, normA: float, delta: float, o: Opts,
-           stats: dict):
+           stats: dict, diagC=None):
     """Algorithm 2 with a GD outer loop (the PHSVDS(GD+k) variant of Sec. 5).
 
     Targets are the k stage-1 values in the given order, one at a time, with
@@ -612,6 +623,19 @@ def stage2(ops: Ops, sig: np.ndarray, Vt: np.ndarray, normA: float, delta: float
         if o.stage2_inner == "qmr":
             corr = jd_correction(ops, Xl, x, W @ s1, th1, r, delta * normA / math.sqrt(2.0),
                                  o.inner_maxit, stats)
+        elif o.stage2_precond and diagC is not None:
+            # READING: M = diag(C)^{-1}, the unshifted Jacobi preconditioner of
+            # C, so that P = [0 M A^T; A M 0] approximates B^{-1} (the targets
+            # are the smallest singular values; a shifted (diag(C) - shift^2)
+            # is indefinite across the spectrum and slowed stage 2 down), in
+            # the Olsen form t = P r - e P x, e = x^T P r / x^T P x
+            d = diagC.copy()
+            guard = EPS64 * normA * normA
+            d = np.where(np.abs(d) < guard, np.where(d < 0, -guard, guard), d)
+            Pr = b_precond(ops, lambda z: z / d, r)
+            Px = b_precond(ops, lambda z: z / d, x)
+            den = float(x @ Px)
+            corr = Pr - (float(x @ Pr) / den) * Px if den != 0.0 else Pr
         else:
             corr = r
         t = orth_append(np.hstack([Xl, V]), corr[:, None], o.seed, counter)
@@ -669,7 +693,9 @@ def phsvds(csr, k: int, largest: bool = False, delta: float = 1e-14, o: Opts | N
         lam, Xv = rayleigh_ritz_post(ops, Xv, state, k, largest, o)
     sig_s = np.sqrt(np.maximum(lam, 0.0))
     # stage 2 in ascending (smallest) or descending (largest) order of the shifts
-    th, X2, normA2 = stage2(ops, sig_s, Xv, normA, delta, o, stats)
+    th, X2, normA2 = stage2(ops, sig_s, Xv, normA, delta, o, stats,
+                            diagC=np.asarray(A.multiply(A).sum(axis=0)).ravel()
+                            if o.stage2_precond and not largest else None)
     Vv = X2[:n]
     Uu = X2[n:]
     Vv = Vv / np.linalg.norm(Vv, axis=0)
