@@ -20,6 +20,9 @@ Steps, in the paper's order:
   the basis grows by the residual (GD) or, in the JDQMR form of Sec. 4, by
   an inexact solution of the Jacobi-Davidson correction equation (symmetric
   QMR with a dynamic stop: a READING);
+* preconditioning (Sec. 4): Jacobi on C with the Olsen correction; from a
+  given M ~ A, M^-1 M^-T for C and [0 M^-1; M^-T 0] for B; from C's Jacobi
+  M ~ C^-1, [0 A M; M A^T 0] for B in stage 2;
 * final triplet test sqrt(||r_u||^2 + ||r_v||^2) < ||A|| delta (Sec. 5).
 
 GD+k itself is named but not defined in the paper (Sec. 2.2, Sec. 5: "GD+k",
@@ -193,7 +196,8 @@ class Opts:
     stage1_eps: float = EPS64   # unit roundoff of stage 1 (EPS32 for the mixed form)
     rr: bool = True             # Algorithm 1 step 3
     stage2: bool = True         # False: stage 1 only
-    precond: str = "none"       # "none" or "jacobi" (diag(C) - theta)^-1 with Olsen
+    precond: str = "none"       # "none", "jacobi" (diag(C) - theta)^-1, or "given" (below); Olsen form
+    precond_M: object = None    # "given": diagonal of M ~ A (square A); C gets M^-1 M^-T, B gets [0 M^-1; M^-T 0]
     seed: int = 0
     max_iters: int = 10 ** 7
     trace: object = None        # optional callable(stage, iteration, info dict)
@@ -335,7 +339,15 @@ def gdk(apply_op, n: int, k: int, largest: bool, tol_fn, o: Opts, diagC=None, X0
         if unconv:
             Ru = R[:, unconv]
             Xu = X[:, unconv]
-            if o.precond == "jacobi" and diagC is not None:
+            if o.precond == "given" and o.precond_M is not None:
+                # M^-1 M^-T for C (Sec. 4), shift-free, Olsen form
+                m2 = np.asarray(o.precond_M, dtype=np.float64) ** 2
+                T = np.empty_like(Ru)
+                for c in range(len(unconv)):
+                    Mr = Ru[:, c] / m2
+                    Mx = Xu[:, c] / m2
+                    T[:, c] = Mr - (float(Xu[:, c] @ Mr) / float(Xu[:, c] @ Mx)) * Mx
+            elif o.precond == "jacobi" and diagC is not None:
                 T = np.empty_like(Ru)
                 for c, i in enumerate(unconv):
                     d = diagC - theta[i]
@@ -486,6 +498,14 @@ def b_precond(ops: Ops, apply_M, y: np.ndarray) -> np.ndarray:
     return np.concatenate([apply_M(ops.Atu(y[n:])), ops.Av(apply_M(y[:n]))])
 
 
+def given_b_precond(Mdiag, n: int, y: np.ndarray) -> np.ndarray:
+    """Stage-2 preconditioner from a given M ~ A (square A, diagonal M here):
+    [0 M^-1; M^-T 0] (Sec. 4), which is B^-1 when M = A; in the [v; u] order,
+    y = [y_v; y_u] -> [M^-1 y_u; M^-T y_v]."""
+    mv = np.asarray(Mdiag, dtype=np.float64)
+    return np.concatenate([y[n:] / mv, y[:n] / mv])
+
+
 def stage2(ops: Ops, sig: np.ndarray, Vt: np.ndarray, normA: float, delta: float, o: Opts,
            stats: dict, diagC=None):
     """Algorithm 2 with a GD outer loop (the PHSVDS(GD+k) variant of Sec. 5).
@@ -623,6 +643,12 @@ def stage2(ops: Ops, sig: np.ndarray, Vt: np.ndarray, normA: float, delta: float
         if o.stage2_inner == "qmr":
             corr = jd_correction(ops, Xl, x, W @ s1, th1, r, delta * normA / math.sqrt(2.0),
                                  o.inner_maxit, stats)
+        elif o.precond == "given" and o.precond_M is not None:
+            # [0 M^-1; M^-T 0] for B (Sec. 4), in the [v; u] order, Olsen form
+            Pr = given_b_precond(o.precond_M, ops.n, r)
+            Px = given_b_precond(o.precond_M, ops.n, x)
+            den = float(x @ Px)
+            corr = Pr - (float(x @ Pr) / den) * Px if den != 0.0 else Pr
         elif o.stage2_precond and diagC is not None:
             # READING: M = diag(C)^{-1}, the unshifted Jacobi preconditioner of
             # C, so that P = [0 M A^T; A M 0] approximates B^{-1} (the targets

@@ -206,6 +206,16 @@ def diag_matrix(sigma, m: int | None = None, name: str = "diag") -> Csr:
     return A
 
 
+def e3_diag(seed: int = 9) -> tuple:
+    """The two-stage demonstration of Sec. 5.1: A = diag([1:10, 1000:100:1e6])
+    (square, n = 10,001) and the approximation M = A + diag(1e4 * U[0, 1))
+    that serves as its preconditioner.  Returns (A as Csr, diagonal of M)."""
+    sigma = np.concatenate([np.arange(1.0, 11.0), np.arange(1000.0, 1e6 + 1.0, 100.0)])
+    A = diag_matrix(sigma, name="e3 diag")
+    M = sigma + 1e4 * uniform(seed, 900, sigma.size)
+    return A, M
+
+
 def table1_sigma() -> np.ndarray:
     """diag([1e-14, 1e-12, 1e-8:1e-8:4e-8, 1e-3:1e-3:1]) of Section 5.1, Table 1."""
     return np.concatenate([[1e-14, 1e-12], 1e-8 * np.arange(1, 5), 1e-3 * np.arange(1, 1001)])
