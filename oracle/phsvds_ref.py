@@ -23,6 +23,8 @@ Steps, in the paper's order:
 * preconditioning (Sec. 4): Jacobi on C with the Olsen correction; from a
   given M ~ A, M^-1 M^-T for C and [0 M^-1; M^-T 0] for B; from C's Jacobi
   M ~ C^-1, [0 A M; M A^T 0] for B in stage 2;
+* Algorithm 3 (Sec. 4): dynamic switching between GD+k on C and on B under
+  preconditioning (dynamic_phsvds);
 * final triplet test sqrt(||r_u||^2 + ||r_v||^2) < ||A|| delta (Sec. 5).
 
 GD+k itself is named but not defined in the paper (Sec. 2.2, Sec. 5: "GD+k",
@@ -221,7 +223,7 @@ class Result:
 # ---------------------------------------------------------------------------
 
 def gdk(apply_op, n: int, k: int, largest: bool, tol_fn, o: Opts, diagC=None, X0=None,
-        stats=None):
+        stats=None, order_key=None, apply_prec=None, stop_after=None, history=None):
     """Block GD+k for the k extreme eigenpairs of a symmetric operator.
 
     Per iteration: Rayleigh-Ritz on the basis V (H = V^T W, W = op(V)); the
@@ -237,6 +239,14 @@ def gdk(apply_op, n: int, k: int, largest: bool, tol_fn, o: Opts, diagC=None, X0
     tol_fn(theta_i, theta_max) gives the residual threshold of Ritz value
     theta_i, theta_max being the largest Ritz value seen (the ||C|| estimate).
     Returns (lam (k,), X (n x k), state) with the final basis in ``state``.
+
+    Hooks for the dynamic method (Algorithm 3; all default to the plain
+    behaviour): order_key(theta) -> sort keys replaces the smallest/largest
+    target order (interior targets of B); apply_prec(r, x) -> t replaces the
+    correction; stop_after = N ends the run after N iterations and returns
+    the k best current approximations (locked ones first) with
+    state["nconv"] = the number locked; history collects the residual norm
+    of the first unconverged target at every iteration.
     """
     stats = {} if stats is None else stats
     b = max(1, min(o.block, k))
@@ -276,9 +286,12 @@ def gdk(apply_op, n: int, k: int, largest: bool, tol_fn, o: Opts, diagC=None, X0
         j = V.shape[1]
         # ---- Rayleigh-Ritz
         theta, S = np.linalg.eigh(H)
-        if largest:
+        if order_key is not None:
+            o_ = np.argsort(order_key(theta), kind="stable")
+            theta, S = theta[o_], S[:, o_]
+        elif largest:
             theta, S = theta[::-1], S[:, ::-1]
-        theta_max = max(theta_max, float(np.max(theta)))
+        theta_max = max(theta_max, float(np.max(np.abs(theta))))
         it += 1
         nt = min(b, k - len(lam_l), j)
         X = V @ S[:, :nt]
@@ -286,6 +299,8 @@ def gdk(apply_op, n: int, k: int, largest: bool, tol_fn, o: Opts, diagC=None, X0
         rn = np.linalg.norm(R, axis=0)
         conv = [i for i in range(nt) if rn[i] < tol_fn(theta[i], theta_max)]
         unconv = [i for i in range(nt) if i not in conv]
+        if history is not None and unconv:
+            history.append(float(rn[unconv[0]]))
         if o.trace is not None:
             o.trace(1, it, dict(j=j, nlock=len(lam_l), theta0=float(theta[0]), rnorm0=float(rn[0]),
                                 theta_max=theta_max, nconv=len(conv)))
@@ -299,6 +314,13 @@ def gdk(apply_op, n: int, k: int, largest: bool, tol_fn, o: Opts, diagC=None, X0
                 order = order[::-1]
             state = dict(V=V, W=W, theta=theta, S=S, conv=conv)
             return np.array(lam_l)[order], Xl[:, order], state
+        if stop_after is not None and it >= stop_after:
+            nfree = k - len(lam_l)
+            cand = [c for c in range(j) if c not in conv][:nfree]
+            Xk = np.column_stack([Xl, V @ S[:, cand]]) if Xl.shape[1] else V @ S[:, cand]
+            lk = np.concatenate([np.array(lam_l), theta[cand]])
+            stats.update(iters=it, restarts=restarts, theta_max=theta_max)
+            return lk, Xk, dict(V=V, W=W, theta=theta, S=S, conv=conv, nconv=len(lam_l), partial=True)
         if it >= o.max_iters:
             raise RuntimeError("stage 1: iteration limit")
         keep_all = [c for c in range(j) if c not in conv]
@@ -339,7 +361,9 @@ def gdk(apply_op, n: int, k: int, largest: bool, tol_fn, o: Opts, diagC=None, X0
         if unconv:
             Ru = R[:, unconv]
             Xu = X[:, unconv]
-            if o.precond == "given" and o.precond_M is not None:
+            if apply_prec is not None:
+                T = np.column_stack([apply_prec(Ru[:, c], Xu[:, c]) for c in range(len(unconv))])
+            elif o.precond == "given" and o.precond_M is not None:
                 # M^-1 M^-T for C (Sec. 4), shift-free, Olsen form
                 m2 = np.asarray(o.precond_M, dtype=np.float64) ** 2
                 T = np.empty_like(Ru)
@@ -682,6 +706,154 @@ def stage2(ops: Ops, sig: np.ndarray, Vt: np.ndarray, normA: float, delta: float
 # driver
 # ---------------------------------------------------------------------------
 
+def next_max_iter(init_iter: int, j: int, same: bool) -> tuple:
+    """Algorithm 3 steps 9-13: the same approach again doubles maxIter
+    (j <- j + 1), a switch cuts it back (j <- floor(j / 2));
+    maxIter = initIter * 2^j.  Returns (j, maxIter)."""
+    j = j + 1 if same else j // 2
+    return j, init_iter * 2 ** j
+
+
+def convergence_rate(history: list) -> float:
+    """Average reduction per iteration of the residual norm (Sec. 4), as the
+    mean slope of log ||r|| over a run; more negative is faster."""
+    h = [x for x in history if x > 0]
+    if len(h) < 2:
+        return 0.0
+    return (math.log(h[-1]) - math.log(h[0])) / (len(h) - 1)
+
+
+def dynamic_phsvds(csr, k: int, delta: float = 1e-14, o: Opts | None = None, init_iter: int = 50,
+                   max_switch: int = 8, log: list | None = None) -> Result:
+    """Algorithm 3 (Sec. 4): dynamic switching between C and B under
+    preconditioning, GD+k on both, for the k smallest triplets.
+
+    The runs alternate between GD+k on C (the stage-1 operator with its
+    preconditioner) and GD+k on B (targets: the positive eigenvalues
+    nearest zero, with the B preconditioner of the same family), each
+    starting from the other's approximations; the convergence rate of each
+    is the mean log-reduction of the residual per iteration.  The loop and
+    its maxIter rule follow the algorithm's steps; the end follows its
+    final branches (all found on B / all found on C / faster C: the
+    two-stage method / faster B: B to the end).
+    READINGS: the initial tests run C then B, so the first choice compares
+    against B; numConverged is the number locked in the latest run; the
+    preconditioners are the shift-free forms of Sec. 4 (given M ~ A:
+    M^-1 M^-T and [0 M^-1; M^-T 0]; Jacobi: diag(C)^-1 and [0 M A^T; A M 0]),
+    in the Olsen form; a B run locks at ||r_B|| < delta ||A|| / sqrt 2; B's
+    targets are its eigenvalues above 1e-12 of the largest, so that the
+    m - n zero eigenvalues of a rectangular A are not taken for singular
+    values.
+    """
+    o = Opts() if o is None else o
+    A = as_scipy(csr)
+    m, n = A.shape
+    if m < n:
+        raise ValueError("PHSVDS needs m >= n")
+    ops = Ops(A)
+    diagC = np.asarray(A.multiply(A).sum(axis=0)).ravel()
+    guard = EPS64 * float(np.max(diagC))
+    dC = np.where(diagC < guard, guard, diagC)
+
+    def olsen(Pr, Px, x):
+        den = float(x @ Px)
+        return Pr - (float(x @ Pr) / den) * Px if den != 0.0 else Pr
+
+    if o.precond == "given" and o.precond_M is not None:
+        m2 = np.asarray(o.precond_M, dtype=np.float64) ** 2
+        prec_C = lambda r, x: olsen(r / m2, x / m2, x)
+        prec_B = lambda r, x: olsen(given_b_precond(o.precond_M, n, r), given_b_precond(o.precond_M, n, x), x)
+    elif o.precond == "jacobi":
+        prec_C = lambda r, x: olsen(r / dC, x / dC, x)
+        prec_B = lambda r, x: olsen(b_precond(ops, lambda z: z / dC, r), b_precond(ops, lambda z: z / dC, x), x)
+    else:
+        prec_C = prec_B = None
+    tolC = stage1_tol(delta, o)
+    tolB = lambda th, thmax: delta * thmax / math.sqrt(2.0)
+    # the zero eigenvalues of B (m > n) are not singular values: only
+    # eigenvalues above 1e-12 max |theta| are targets (READING)
+    keyB = lambda th: np.where(th > 1e-12 * np.max(np.abs(th)), th, np.inf)
+    log = [] if log is None else log
+    cur = {"X": None, "normA": 0.0}
+
+    def run(approach: str, iters):
+        h: list = []
+        st: dict = {}
+        if approach == "C":
+            lam, X, state = gdk(ops.C, n, k, False, tolC, o, X0=cur["X"], stats=st, apply_prec=prec_C,
+                                stop_after=iters, history=h)
+            cur["normA"] = max(cur["normA"], math.sqrt(st["theta_max"]))
+            Xv = X
+        else:
+            X0 = None
+            if cur["X"] is not None:
+                AV = A @ cur["X"]
+                AV = AV / np.maximum(np.linalg.norm(AV, axis=0), 1e-300)
+                X0 = np.vstack([cur["X"], AV]) / math.sqrt(2.0)
+            lam, X, state = gdk(ops.B, m + n, k, False, tolB, o, X0=X0, stats=st, order_key=keyB,
+                                apply_prec=prec_B, stop_after=iters, history=h)
+            cur["normA"] = max(cur["normA"], st["theta_max"])
+            Xv = X[:n] / np.maximum(np.linalg.norm(X[:n], axis=0), 1e-300)
+        cur["X"] = Xv
+        done = not state.get("partial", False)
+        nconv = k if done else int(state["nconv"])
+        rate = convergence_rate(h)
+        log.append(dict(approach=approach, max_iter=iters, iters=st["iters"], rate=rate, nconv=nconv))
+        return dict(lam=lam, X=X, state=state, stats=st, done=done, nconv=nconv, rate=rate)
+
+    # step 3: initial tests on C and on B
+    last = {"C": run("C", init_iter), "B": run("B", init_iter)}
+    num_conv = max(last["C"]["nconv"], last["B"]["nconv"])
+    prev, num_switch, j, max_iter, undecided = "B", 0, 0, init_iter, True
+    while num_switch < max_switch and undecided:
+        choice = "C" if last["C"]["rate"] < last["B"]["rate"] else "B"
+        if (num_switch == 0 and num_conv > 0) or num_conv > 1:
+            undecided = False
+        else:
+            j, max_iter = next_max_iter(init_iter, j, choice == prev)
+        num_switch += 1
+        last[choice] = run(choice, max_iter)
+        num_conv = last[choice]["nconv"]
+        prev = choice
+        if last[choice]["done"]:
+            break
+    faster = "C" if last["C"]["rate"] < last["B"]["rate"] else "B"
+    stats = dict(dynamic=log, switches=num_switch, faster=faster)
+    if last[prev]["done"] and prev == "B":
+        res = last["B"]
+        X = res["X"]
+        route = "B"
+    elif last[prev]["done"] and prev == "C":
+        st = dict(last["C"]["stats"])
+        st.update(stats)
+        out = _after_stage1(A, ops, k, False, delta, o, last["C"]["lam"], last["C"]["X"], last["C"]["state"], st)
+        out.stats["route"] = "C then B"
+        return out
+    elif faster == "C":
+        st: dict = {}
+        lam, Xv, state = gdk(ops.C, n, k, False, tolC, o, X0=cur["X"], stats=st, apply_prec=prec_C)
+        st.update(stats)
+        out = _after_stage1(A, ops, k, False, delta, o, lam, Xv, state, st)
+        out.stats["route"] = "two-stage"
+        return out
+    else:
+        AV = A @ cur["X"]
+        AV = AV / np.maximum(np.linalg.norm(AV, axis=0), 1e-300)
+        X0 = np.vstack([cur["X"], AV]) / math.sqrt(2.0)
+        st = {}
+        lam, X, state = gdk(ops.B, m + n, k, False, tolB, o, X0=X0, stats=st, order_key=keyB, apply_prec=prec_B)
+        route = "B to the end"
+    Vv = X[:n] / np.linalg.norm(X[:n], axis=0)
+    Uu = X[n:] / np.linalg.norm(X[n:], axis=0)
+    sig = np.einsum("ij,ij->j", Uu, A @ Vv)
+    Uu[:, sig < 0] *= -1.0
+    sig = np.abs(sig)
+    ru, rv, res_ = triplet_residuals(A, sig, Uu, Vv)
+    order = np.argsort(sig)
+    stats.update(route=route, mv_A=ops.mv_A, mv_At=ops.mv_At)
+    return Result(sig[order], Uu[:, order], Vv[:, order], res_[order], max(cur["normA"], float(np.max(sig))), stats)
+
+
 def triplet_residuals(A: sp.csr_matrix, sigma, U, V):
     """||A v - s u||, ||A^T u - s v|| and their root-sum-square (Sec. 5 criterion)."""
     rv = np.linalg.norm(A @ V - U * sigma, axis=0)
@@ -700,6 +872,13 @@ def phsvds(csr, k: int, largest: bool = False, delta: float = 1e-14, o: Opts | N
     stats: dict = {}
     diagC = np.asarray(A.multiply(A).sum(axis=0)).ravel() if o.precond == "jacobi" else None
     lam, Xv, state = gdk(ops.C, n, k, largest, stage1_tol(delta, o), o, diagC=diagC, stats=stats)
+    return _after_stage1(A, ops, k, largest, delta, o, lam, Xv, state, stats)
+
+
+def _after_stage1(A, ops: Ops, k: int, largest: bool, delta: float, o: Opts, lam, Xv, state, stats) -> Result:
+    """Switch test (Sec. 3.1), optional Rayleigh-Ritz (Algorithm 1 step 3) and
+    stage 2 (Algorithm 2) after a converged stage 1; the final triplets."""
+    m, n = A.shape
     theta_max = stats["theta_max"]
     normA = math.sqrt(theta_max)
     # stage-1 triplets: s = ||A v||, u = A v / s (r_v = 0)
