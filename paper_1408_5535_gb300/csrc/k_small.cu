@@ -1,11 +1,13 @@
-// One-CTA FP64 kernels for the projected (small) problems of PHSVDS:
-//  * cyclic two-sided Jacobi eigensolver for the Rayleigh-Ritz matrix
-//    H = V^T W (Algorithm 2 step 7; the projected problem of GD+k in stage 1),
-//    warm-startable: the working matrix A = S^T H S and the accumulated
-//    rotation S are kept between outer iterations, so only the entries coupled
-//    to the newly added basis vectors need rotating;
-//  * one-sided (Hestenes) Jacobi SVD of the refined-projection factor R
-//    (Algorithm 2 step 8), warm-startable the same way (G = R S);
+// Kernels for the projected (small) problems of PHSVDS:
+//  * cyclic two-sided Jacobi eigensolvers for the Rayleigh-Ritz matrix
+//    H = V^T W (the projected problem of GD+k in stage 1, Algorithm 2 step 7
+//    in stage 2), run in a warm frame (the working matrix A = S^T H S and the
+//    accumulated rotation S are kept between outer iterations): an FP32 pass
+//    followed by an FP64 clean-up of the target pairs, or FP64 in one CTA or
+//    over an 8-CTA cluster;
+//  * the refined vector of stage 2 (Algorithm 2 step 8): the smallest right
+//    singular vector of the triangular factor R by inverse iteration, and the
+//    whole one-sided (Hestenes) Jacobi SVD of R as an entry point;
 //  * Cholesky of a block Gram matrix (CholQR of the new block), the restart /
 //    locking transform builder and small gathers.
 // Small matrices are column-major with a leading dimension ld (<= 64).
