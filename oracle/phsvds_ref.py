@@ -204,7 +204,7 @@ class Opts:
     max_iters: int = 10 ** 7
     trace: object = None        # optional callable(stage, iteration, info dict)
     stage2_inner: str = "none"  # "none": GD, t = r; "qmr": JDQMR, t from the correction equation (Sec. 4)
-    inner_maxit: int = 40       # READING: inner QMR steps per outer iteration, at most
+    inner_maxit: int = 300      # READING: inner QMR steps per outer iteration, at most
     stage2_precond: bool = False  # smallest targets: GD stage 2 preconditioned by [0 M A^T; A M 0], M = diag(C)^-1 (Sec. 4)
 
 
@@ -469,7 +469,7 @@ def symmetric_qmr(apply_M, b: np.ndarray, Qd: np.ndarray, steps: int):
 
 
 def jd_correction(ops: "Ops", Xl: np.ndarray, x: np.ndarray, Bx: np.ndarray, mu: float, r: np.ndarray,
-                  tol: float, maxit: int, stats: dict, patience: int = 2) -> np.ndarray:
+                  tol: float, maxit: int, stats: dict, patience: int = 25) -> np.ndarray:
     """Correction of the Jacobi-Davidson method on B (Sec. 4, the correction
     equation (I - w w^T)(B - mu I)(I - w w^T) t = sigma~ w - B w with w the
     refined vector x, here also deflating the locked vectors Xl), solved
@@ -479,8 +479,10 @@ def jd_correction(ops: "Ops", Xl: np.ndarray, x: np.ndarray, Bx: np.ndarray, mu:
     z = (x + t_k) / ||x + t_k|| is scored by its eigen-residual
     eta_k = ||B z - (z^T B z) z|| (B t_k from the products the Lanczos steps
     already made); the steps stop once eta_k < tol, or once eta has not
-    fallen below 0.9 times its best value for `patience` steps in a row, or
-    after maxit steps; the iterate with the smallest eta is returned."""
+    fallen below 0.9 times its best value for `patience` (25) steps in a
+    row, or after maxit steps; the iterate with the smallest eta is
+    returned.  A short patience cuts the solve off before it resolves a
+    cluster near mu (the corrections then act like GD's)."""
     Qd = np.column_stack([Xl, x]) if Xl.shape[1] else x[:, None]
 
     def apply_M(q):
