@@ -576,6 +576,7 @@ def stage2(ops: Ops, sig: np.ndarray, Vt: np.ndarray, normA: float, delta: float
     H = V.T @ W
     H = 0.5 * (H + H.T)
     Xl = np.zeros((N, 0))
+    Xd = []            # JDQMR form: mirrors [v; -u] of locked tiny pairs, deflated too
     th_l = []
     target = 0
     shift = float(sig[0])
@@ -614,11 +615,26 @@ def stage2(ops: Ops, sig: np.ndarray, Vt: np.ndarray, normA: float, delta: float
             if target >= k:
                 break
             Y = SRt[:-1].T                     # orthonormal complement of s1
-            V, W = V @ Y, W @ Y
-            H = Y.T @ H @ Y
+            if o.stage2_inner == "qmr" and abs(th1) <= math.sqrt(EPS64) * normA:
+                # READING (JDQMR form): for a tiny sigma the pair +-sigma of B
+                # is not separable at the tolerance, and both eigenvectors
+                # [v; +-u] belong to the same triplet: the mirror [v; -u] is
+                # deflated as well, from the basis and from later directions
+                mir = np.concatenate([x[:n], -x[n:]])
+                Xd.append((mir / np.linalg.norm(mir))[:, None])
+                D = np.column_stack([Xl] + Xd)
+                V = V @ Y
+                for _ in range(2):
+                    V = V - D @ (D.T @ V)
+                V = np.linalg.qr(V)[0]
+                W = ops.B(V)
+                H = V.T @ W
+            else:
+                V, W = V @ Y, W @ Y
+                H = Y.T @ H @ Y
             H = 0.5 * (H + H.T)
             # re-introduce the next initial guess (Algorithm 2 step 9)
-            t = orth_append(np.hstack([Xl, V]), x0[:, target:target + 1], o.seed, counter)
+            t = orth_append(np.hstack([Xl] + Xd + [V]), x0[:, target:target + 1], o.seed, counter)
             wt = ops.B(t)
             H = np.block([[H, V.T @ wt], [wt.T @ V, t.T @ wt]])
             H = 0.5 * (H + H.T)
@@ -667,7 +683,8 @@ def stage2(ops: Ops, sig: np.ndarray, Vt: np.ndarray, normA: float, delta: float
         s_prev = s1.copy()
         # ---- expand with t = r (Algorithm 2 step 4), or with the JD correction
         if o.stage2_inner == "qmr":
-            corr = jd_correction(ops, Xl, x, W @ s1, th1, r, delta * normA / math.sqrt(2.0),
+            corr = jd_correction(ops, np.column_stack([Xl] + Xd) if Xd else Xl, x, W @ s1, th1, r,
+                                 delta * normA / math.sqrt(2.0),
                                  o.inner_maxit, stats)
         elif o.precond == "given" and o.precond_M is not None:
             # [0 M^-1; M^-T 0] for B (Sec. 4), in the [v; u] order, Olsen form
@@ -690,7 +707,7 @@ def stage2(ops: Ops, sig: np.ndarray, Vt: np.ndarray, normA: float, delta: float
             corr = Pr - (float(x @ Pr) / den) * Px if den != 0.0 else Pr
         else:
             corr = r
-        t = orth_append(np.hstack([Xl, V]), corr[:, None], o.seed, counter)
+        t = orth_append(np.hstack([Xl] + Xd + [V]), corr[:, None], o.seed, counter)
         wt = ops.B(t)
         H = np.block([[H, V.T @ wt], [wt.T @ V, t.T @ wt]])
         H = 0.5 * (H + H.T)
@@ -899,6 +916,15 @@ def _after_stage1(A, ops: Ops, k: int, largest: bool, delta: float, o: Opts, lam
     if o.rr:
         lam, Xv = rayleigh_ritz_post(ops, Xv, state, k, largest, o)
     sig_s = np.sqrt(np.maximum(lam, 0.0))
+    if o.stage2_inner == "qmr":
+        # READING (JDQMR form): the targets that stage 1 resolved go first and
+        # the tiny ones (sigma~ <= sqrt(eps) ||A||, Sec. 4's "extremely small"
+        # values, whose u~ is random) last, each group in the given order, so
+        # that the accurate guesses are locked before the ambiguous shifts
+        # near zero are worked on
+        tiny = sig_s <= math.sqrt(EPS64) * normA
+        order2 = np.concatenate([np.where(~tiny)[0], np.where(tiny)[0]])
+        sig_s, Xv = sig_s[order2], Xv[:, order2]
     # stage 2 in ascending (smallest) or descending (largest) order of the shifts
     th, X2, normA2 = stage2(ops, sig_s, Xv, normA, delta, o, stats,
                             diagC=np.asarray(A.multiply(A).sum(axis=0)).ravel()

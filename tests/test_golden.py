@@ -57,3 +57,17 @@ def test_oracle_counts_cover_the_benchmark_workload():
     for v in g.values():
         assert v["iters_stage1"] > 0 and max(v["resid_over_normA"]) <= 1e-14
         assert v["switched"]            # smallest triplets of a grid need stage 2
+
+
+def test_oracle_jdqmr_form_reproduces_table1():
+    """The paper's worked example (Sec. 5.1, Table 1) run by the oracle's
+    JDQMR form of stage 2 at the printed settings (block 2 in stage 1,
+    identity preconditioner, delta = 1e-15): all ten clustered tiny values,
+    each within the printed ||r_B|| of the exact one (the accuracy Weyl's
+    bound gives the printed run) and with a triplet residual <= 1e-15 ||A||."""
+    t = _table1()
+    A = synth.diag_matrix(synth.table1_sigma())
+    res = R.phsvds(A, 10, largest=False, delta=1e-15, o=R.Opts(block=2, stage2_inner="qmr"))
+    assert np.all(np.abs(res.sigma - t[:, 0]) <= t[:, 2])
+    assert np.all(res.resid <= 1e-15 * res.normA)
+    assert res.stats["switched"]
