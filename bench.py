@@ -420,10 +420,12 @@ def measured_traffic(kernel_file, names, summary, key):
 
 def roofline_for(A, prof, dom, hbm, peak_kind):
     """Roofline of the dominant kernel class of one profiled solve.
-    Cluster Jacobi: algorithmic flops per launch = 18 j per rotation (rows and
-    columns of H and the columns of S, 6 j each) x rotations per launch, against
-    the GPU's FP64 peak.  Otherwise the fused SpMM against the measured HBM copy
-    rate with the one-read-of-A byte count."""
+    Stage-1 projected eigensolve (class 5: the FP32 Jacobi pass with its FP64
+    clean-up of the target pairs, or the FP64 cluster Jacobi): algorithmic
+    flops per call = 18 j per rotation (rows and columns of H and the columns
+    of S, 6 j each) x rotations per call, against the GPU's FP64 peak.
+    Otherwise the fused SpMM against the measured HBM copy rate with the
+    one-read-of-A byte count."""
     if dom == 5 and prof["n_class"][5] and prof["jacobi_calls"]:
         # whole-solve algorithmic flops of the stage-1 projected solves over
         # the class's whole device time (a solve is one or two launches)
