@@ -105,3 +105,18 @@ def test_dynamic_switching_on_the_e3_demonstration():
         j, mi = R.next_max_iter(50, j, e["approach"] == prev)
         assert e["max_iter"] == mi
         prev = e["approach"]
+
+
+@pytest.mark.parametrize("precond", ["jacobi", "none"])
+def test_dynamic_switching_on_a_rectangular_matrix(precond):
+    """120 x 60 random sparse A (B has 60 zero eigenvalues, which must not be
+    taken for singular values): the three smallest triplets match the dense
+    SVD whichever route the switching takes."""
+    from oracle.dense_jacobi import jacobi_svd
+    A = synth.random_sparse(120, 60, 5.0, 11, values="gaussian", shift=0.05)
+    res = R.dynamic_phsvds(A, 3, delta=1e-14, o=R.Opts(precond=precond, max_basis=20, min_restart=10),
+                           init_iter=20)
+    s = np.sort(jacobi_svd(A.to_dense())[0])[:3]
+    assert np.max(np.abs(res.sigma - s) / s) <= 1e-10
+    assert np.all(res.resid <= 1e-14 * res.normA)
+    assert res.stats["route"] in ("B to the end", "two-stage", "C then B")
