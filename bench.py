@@ -171,6 +171,12 @@ def spmm_bytes(m, n, nnz, b, p):
     return nnz * (p + 4) + 4 * (m + 1) + 2 * p * n * b
 
 
+def spmm_lanes(avg):
+    """Threads per sparse row (or CSC column) for a mean length avg: the
+    group width the benchmark times by default."""
+    return 1 if avg <= 2.5 else 2 if avg <= 6 else 4 if avg <= 16 else 8
+
+
 def spmm_full(a):
     """Fused A^T A SpMM (products with C) on the full-size configurations:
     both schedules, FP64 and FP32, over the group widths (threads per sparse
@@ -189,9 +195,6 @@ def spmm_full(a):
              "c3": ("random 1e6 x 5e5, Poisson(12)/row, lognormal(2) +-, +1e-3[I;0], seed 3",
                     lambda: synth.random_sparse(1000000, 500000, 12.0, 3), 8)}
 
-    def lanes_for(avg):
-        return 1 if avg <= 2.5 else 2 if avg <= 6 else 4 if avg <= 16 else 8
-
     def around(l0):
         return [x for x in (l0 // 2, l0, 2 * l0) if 1 <= x <= 16]
 
@@ -207,7 +210,7 @@ def spmm_full(a):
             cv = torch.empty(A.nnz, dtype=torch.float64, device="cuda")
             native.phsvds_csr_to_csc(h, A.m, A.n, A.nnz, rp, ci, va, cp, ri, cv)
             native.phsvds_sync(h)
-            la0, lt0 = lanes_for(A.nnz / A.m), lanes_for(A.nnz / A.n)
+            la0, lt0 = spmm_lanes(A.nnz / A.m), spmm_lanes(A.nnz / A.n)
             for fp32 in (True, False):
                 vt = torch.float32 if fp32 else torch.float64
                 v1, v2 = (va.float(), cv.float()) if fp32 else (va, cv)
