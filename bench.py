@@ -2,15 +2,18 @@
 
 One step = one complete PHSVDS solve (stage 1 GD+k on A^T A, switch test,
 Rayleigh-Ritz post-process, stage 2 refined projection on the augmented matrix,
-final residuals) of the synthetic workload, through the C ABI.
+final residuals) of the synthetic workload, through the C ABI.  The default
+workload is the random sparse 1,000,000 x 500,000 matrix (Poisson(12) entries
+per row, log-normal(2) values with random signs, + 1e-3 [I; 0], seed 3), k = 20
+largest triplets to 1e-14 ||A||, block 8, mixed precision against plain FP64.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--grid G] [--precision mixed|fp64|both]
+                  [--workload c3|grid] [--grid G] [--precision mixed|fp64|both]
 
 Prints one JSON line (rank 0).  ``value`` = whole-job triplets/s with the CSR
 already resident in device memory; ``e2e`` = the same solve through the same
-call with host buffers (host->device copy of A and device->host copy of the
-singular triplets inside the timed region).
+call with pinned host buffers (host->device copy of A and device->host copy of
+the singular triplets inside the timed region).
 """
 from __future__ import annotations
 
@@ -37,15 +40,21 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="c3", choices=["c3", "grid"],
+                   help="c3: random sparse 1e6 x 5e5, k=20 largest (default); grid: weighted grid gradient, "
+                        "k=10 smallest")
     p.add_argument("--grid", type=int, default=64, help="grid side of the weighted gradient workload")
     p.add_argument("--sigma-log", type=float, default=1.0)
-    p.add_argument("--k", type=int, default=10)
-    p.add_argument("--block", type=int, default=4)
+    p.add_argument("--k", type=int, default=0, help="triplets (0: the workload's own, 20 for c3, 10 for grid)")
+    p.add_argument("--block", type=int, default=0, help="block size (0: the workload's own, 8 for c3, 4 for grid)")
     p.add_argument("--precision", default="both", choices=["mixed", "fp64", "both"])
     p.add_argument("--precond", default="none", choices=["none", "jacobi"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="bound of each oracle sample (CPU baseline)")
+    p.add_argument("--ref-iters", type=int, default=0,
+                   help="oracle outer iterations per reference-arm step (0: 4 for c3, 1000 for grid)")
+    p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--spmm-only", action="store_true", help="only the full-size fused A^T A SpMM timings")
     p.add_argument("--spmm-cases", default="c2,c3", help="full-size SpMM workloads: c2 (512^2 grid), c3 (1e6 x 5e5)")
     p.add_argument("--spmm-reps", type=int, default=10)
@@ -66,15 +75,34 @@ def parse():
     p.add_argument("--learned-epochs", type=int, default=100)
     p.add_argument("--learned-cg-steps", type=int, default=3)
     p.add_argument("--learned-stall", type=int, default=200, help="stall window of the learned correction")
-    return p.parse_args()
+    a = p.parse_args()
+    if a.k <= 0:
+        a.k = 20 if a.workload == "c3" else 10
+    if a.block <= 0:
+        a.block = 8 if a.workload == "c3" else 4
+    if a.ref_iters <= 0:
+        a.ref_iters = 4 if a.workload == "c3" else 1000
+    return a
 
 
 def workload(a):
+    """The synthetic matrix and the JSON config of the benchmark workload."""
     from paper_1408_5535_gb300 import synth
+    if a.workload == "c3":
+        A = synth.random_sparse(1000000, 500000, 12.0, 3)
+        cfg = {"workload": f"random sparse 1000000x500000, Poisson(12) entries per row at uniform columns, "
+                           f"log-normal(sigma=2) values with random signs, + 1e-3 [I; 0] (seed 3), nnz={A.nnz}; "
+                           f"k={a.k} largest, block {a.block}, tol 1e-14*||A||, precond {a.precond}",
+               "matrix": "random_sparse(1000000, 500000, 12.0, 3)", "target": "largest", "golden": "c3_largest",
+               "m": A.m, "n": A.n, "nnz": A.nnz, "k": a.k, "block": a.block, "tol": TOL, "precond": a.precond,
+               "l2": "inputs larger than L2 (CSR 150 MB + CSC copy), and a 256 MiB buffer written between "
+                     "timed steps"}
+        return A, cfg
     A = synth.grid_gradient(a.grid, a.sigma_log, 2)
     cfg = {"workload": f"weighted Dirichlet grid gradient {a.grid}x{a.grid} (log-normal sigma_log={a.sigma_log}, "
                        f"seed 2), m={A.m}, n={A.n}, nnz={A.nnz}; k={a.k} smallest, block {a.block}, "
                        f"tol 1e-14*||A||, precond {a.precond}",
+           "matrix": f"grid_gradient({a.grid}, {a.sigma_log}, 2)", "target": "smallest", "golden": f"grid{a.grid}",
            "grid": a.grid, "m": A.m, "n": A.n, "nnz": A.nnz, "k": a.k, "block": a.block, "tol": TOL,
            "precond": a.precond, "l2": "256 MiB buffer written between timed steps"}
     return A, cfg
@@ -252,54 +280,134 @@ def spmm_full(a):
     return out
 
 
-def golden_iters(a):
-    """The oracle's own outer-iteration count (stage 1 + stage 2) on this
-    workload, recorded by tests/golden/make_oracle_counts.py, or None."""
+def golden(a):
+    """The oracle's recorded run of this workload (tests/golden/oracle_counts.json,
+    written by tests/golden/make_oracle_counts.py from oracle/ only), or None."""
     try:
         with open(os.path.join(ROOT, "tests", "golden", "oracle_counts.json")) as f:
-            g = json.load(f).get(f"grid{a.grid}")
+            gd = json.load(f)
     except Exception:
         return None
-    if not g or g["k"] != a.k or g["block"] != a.block or abs(a.sigma_log - 1.0) > 0 or a.precond != "none":
+    key = "c3_largest" if a.workload == "c3" else f"grid{a.grid}"
+    g = gd.get(key)
+    if not g or g["k"] != a.k or g["block"] != a.block or a.precond != "none":
         return None
-    return g["iters_stage1"] + g["iters_stage2"]
+    if a.workload == "grid" and abs(a.sigma_log - 1.0) > 0:
+        return None
+    return g
 
 
-def cpu_baseline(A, a, k, fallback_iters):
-    """The oracle (plain CPU FP64 PHSVDS, as it stands) on the host cores, on a
-    bounded sample of the same solve: it runs for at most --cpu-seconds; if it
-    has not finished, its time per outer iteration is scaled by the oracle's
-    own recorded iteration count for the workload (else by fallback_iters)."""
+def golden_iters(a):
+    """The oracle's own outer-iteration count (stage 1 + stage 2) on this workload, or None."""
+    g = golden(a)
+    return g["iters_stage1"] + g["iters_stage2"] if g else None
+
+
+def oracle_sample(a):
+    """Runs the oracle (plain CPU FP64 PHSVDS, as it stands) on the workload in
+    THIS process until it finishes, or has run --cpu-seconds, or (reference
+    arm) --ref-iters outer iterations; prints {"seconds", "iters", "finished"}.
+    Matrix generation is outside the timed region."""
     from oracle import phsvds_ref as R
-    threads = os.environ.get("OMP_NUM_THREADS") or str(os.cpu_count() or 1)
+    A, cfg = workload(a)
 
     class Stop(Exception):
         pass
 
     state = {"it": 0, "t0": None}
+    cap_it = a.ref_iters if a.impl == "reference" else 0
 
     def tr(stage, it, d):
         state["it"] += 1
-        if time.perf_counter() - state["t0"] > a.cpu_seconds:
+        if (cap_it and state["it"] >= cap_it) or time.perf_counter() - state["t0"] > a.cpu_seconds:
             raise Stop()
 
     o = R.Opts(block=a.block, precond=a.precond, trace=tr)
     state["t0"] = time.perf_counter()
     try:
-        R.phsvds(A, k, delta=TOL, o=o)
+        R.phsvds(A, cfg["k"], largest=cfg["target"] == "largest", delta=TOL, o=o)
         done = True
     except Stop:
         done = False
     el = time.perf_counter() - state["t0"]
-    iters = max(state["it"], 1)
+    print(json.dumps({"seconds": el, "iters": max(state["it"], 1), "finished": done}), flush=True)
+
+
+def _oracle_subprocess(a, threads, extra=()):
+    """oracle_sample in a child process whose BLAS pools have `threads` threads
+    (set before numpy loads), so the thread count reported is the one used."""
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[v] = str(threads)
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-sample", "--workload", a.workload,
+           "--grid", str(a.grid), "--sigma-log", str(a.sigma_log), "--k", str(a.k), "--block", str(a.block),
+           "--precond", a.precond, "--cpu-seconds", str(a.cpu_seconds), "--ref-iters", str(a.ref_iters), *extra]
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True, cwd=ROOT)
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    if r.returncode != 0 or not lines:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-500:])
+    return json.loads(lines[-1])
+
+
+def _scaled(a, k, smp, fallback_iters):
+    """Triplets/s of a whole oracle solve from a sample: its time per outer
+    iteration times the oracle's recorded iteration count for the workload."""
     gi = golden_iters(a)
     total = gi if gi else fallback_iters
-    est = el if done else el / iters * total
-    return {"value": k / est, "unit": "triplets/s", "cores": int(threads), "kind": "oracle",
-            "sample": (f"the whole oracle solve of the workload ({iters} outer iterations) in {el:.1f} s" if done
-                       else f"{iters} oracle outer iterations in {el:.1f} s, scaled to "
-                            f"{'the oracle' if gi else 'the GPU solve'}'s {total} iterations ({est:.0f} s estimated)"),
-            "seconds": el, "iterations_sampled": iters, "finished": done}
+    est = smp["seconds"] if smp["finished"] else smp["seconds"] / smp["iters"] * total
+    return k / est, est, total, gi is not None
+
+
+def cpu_baseline(a, k, fallback_iters):
+    """The oracle on the host cores, on bounded samples of the same solve (at
+    most --cpu-seconds each): with all host cores as BLAS threads (the value)
+    and single-threaded.  An unfinished sample is scaled to a whole solve by
+    the oracle's own recorded iteration count (else the GPU's) and labelled
+    extrapolated."""
+    ncpu = os.cpu_count() or 1
+    out = {}
+    for key, th in (("all", ncpu), ("one", 1)):
+        smp = _oracle_subprocess(a, th)
+        v, est, total, gold = _scaled(a, k, smp, fallback_iters)
+        out[key] = dict(value=v, threads=th, seconds=smp["seconds"], iters=smp["iters"], finished=smp["finished"],
+                        whole_solve_s=est, iters_whole=total)
+    al, one = out["all"], out["one"]
+
+    def text(d):
+        if d["finished"]:
+            return f"the whole oracle solve ({d['iters']} outer iterations) in {d['seconds']:.1f} s"
+        return (f"EXTRAPOLATED: {d['iters']} of the oracle's {d['iters_whole']} outer iterations in "
+                f"{d['seconds']:.1f} s, scaled to {d['whole_solve_s']:.0f} s per solve")
+
+    return {"value": al["value"], "unit": "triplets/s", "cores": al["threads"], "kind": "oracle",
+            "sample": text(al) + f"; {al['threads']} BLAS threads (scipy sparse products single-threaded)",
+            "extrapolated": not al["finished"], "seconds": al["seconds"], "iterations_sampled": al["iters"],
+            "single_thread": {"value": one["value"], "cores": 1, "sample": text(one),
+                              "extrapolated": not one["finished"]}}
+
+
+def _pinned_solve(native, h, A, cfg, target, prec_id, opts):
+    """One solve through the C ABI from pinned host buffers: the CSR is copied
+    host -> device and the triplets device -> host inside the call."""
+    import ctypes as C
+    import numpy as np
+    import torch
+    k = cfg["k"]
+    if not hasattr(_pinned_solve, "buf"):
+        pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+        _pinned_solve.buf = dict(rp=pin(A.row_ptr), ci=pin(A.col), va=pin(A.val),
+                                 sigma=torch.zeros(k, dtype=torch.float64).pin_memory(),
+                                 U=torch.zeros(k * A.m, dtype=torch.float64).pin_memory(),
+                                 V=torch.zeros(k * A.n, dtype=torch.float64).pin_memory(),
+                                 resid=torch.zeros(k, dtype=torch.float64).pin_memory())
+    b = _pinned_solve.buf
+    st = native.Stats()
+    status = native.lib().phsvds_solve(h.h, A.m, A.n, A.nnz, b["rp"].data_ptr(), b["ci"].data_ptr(),
+                                       b["va"].data_ptr(), 0, k, target, TOL, prec_id, C.byref(opts),
+                                       b["sigma"].data_ptr(), b["U"].data_ptr(), b["V"].data_ptr(),
+                                       b["resid"].data_ptr(), C.byref(st))
+    h.check(status)
+    return b["sigma"].numpy().copy(), st.as_dict()
 
 
 def run_ours(a, rank, world):
@@ -309,6 +417,7 @@ def run_ours(a, rank, world):
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     A, cfg = workload(a)
+    target = native.LARGEST if cfg["target"] == "largest" else native.SMALLEST
     stream = torch.cuda.Stream(device=dev)
     h = native.Handle(dev, stream.cuda_stream)
     rp = torch.from_numpy(A.row_ptr).cuda()
@@ -317,17 +426,17 @@ def run_ours(a, rank, world):
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
     precs = {"mixed": [native.MIXED], "fp64": [native.FP64], "both": [native.MIXED, native.FP64]}[a.precision]
     prec_id = native.PREC_JACOBI if a.precond == "jacobi" else native.PREC_NONE
+    g = golden(a)
     results = {}
     for pi, prec in enumerate(precs):
         head = pi == 0                 # the headline precision; the second is the comparison leg
-        steps = a.steps if head else max(1, min(a.steps, 2))
+        steps = a.steps if head else max(2, min(a.steps, 5))
         o = native.default_opts(block_size=a.block, precision=prec, profile=0)
         op = native.default_opts(block_size=a.block, precision=prec, profile=1)
 
-        def solve(opts, on_device=True, vectors=False):
-            return native.phsvds_solve(h, A.m, A.n, rp if on_device else A.row_ptr, ci if on_device else A.col,
-                                       va if on_device else A.val, a.k, native.SMALLEST, TOL, prec_id, opts,
-                                       on_device=on_device, want_vectors=vectors)
+        def solve(opts, vectors=False):
+            return native.phsvds_solve(h, A.m, A.n, rp, ci, va, cfg["k"], target, TOL, prec_id, opts,
+                                       on_device=True, want_vectors=vectors)
 
         for _ in range(a.warmup):
             solve(o)
@@ -350,36 +459,52 @@ def run_ours(a, rank, world):
         ms = max_over_ranks(float(np.mean(times)), world)
         # per-class device times of one profiled solve (CUDA events inside the library)
         prof = solve(op)[4]
-        # end to end: host CSR in, host triplets out, through the same call
+        # end to end: pinned host CSR in, host triplets out, through the same call
         e2e = None
         if not a.no_e2e:
             ee = []
-            for _ in range(1):
+            for _ in range(2):
                 flush.fill_(1.0)
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                solve(o, on_device=False, vectors=True)
+                _pinned_solve(native, h, A, cfg, target, prec_id, o)
                 ee.append((time.perf_counter() - t0) * 1e3)
             e_ms = max_over_ranks(float(np.mean(ee)), world)
             h2d = 8 * (A.m + 1) + 4 * A.nnz + 8 * A.nnz
-            d2h = 8 * a.k * (2 + A.m + A.n)
-            e2e = {"value": world * a.k / (e_ms / 1e3), "unit": "triplets/s", "h2d_bytes_per_step": h2d,
-                   "d2h_bytes_per_step": d2h, "ms_per_step": e_ms}
-        results[prec] = dict(ms=ms, sigma=sig.tolist(), resid_rel=(resid / st["norm_A_est"]).tolist(), stats=st,
-                             prof=prof, e2e=e2e, clocks=clk.summary(), launches=launches, steps=steps)
+            d2h = 8 * cfg["k"] * (2 + A.m + A.n)
+            e2e = {"value": world * cfg["k"] / (e_ms / 1e3), "unit": "triplets/s", "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": d2h, "ms_per_step": e_ms, "host_buffers": "pinned"}
+        err = None
+        if g:
+            ref = np.asarray(g["sigma"])
+            err = (np.abs(sig - ref) / ref).tolist()
+        results[prec] = dict(ms=ms, times=times, sigma=sig.tolist(), resid_rel=(resid / st["norm_A_est"]).tolist(),
+                             stats=st, prof=prof, e2e=e2e, clocks=clk.summary(), launches=launches, steps=steps,
+                             err_vs_oracle=err)
     h.close()
     return A, cfg, results
 
 
-# FP64 peak of one GB300 (nominal 1.25 TFLOP/s: 152 SMs x 2 FP64 FMA per clock
-# per SM x 2 flop x ~2.06 GHz); the cluster Jacobi occupies 8 of the 152 SMs.
+# FP64 peak of one GB300: nominal 1.25 TFLOP/s (the recipe's table), i.e.
+# 152 SMs x 2 FP64 FMA per clock x 2 flop x ~2.06 GHz.
 FP64_PEAK_GFLOPS = 1250.0
 JACOBI_CTAS = 8
+
+CLASS_NAMES = ["fused A^T A SpMM (FP64)", "Gram / CGS passes (FP64)", "basis transforms / Ritz vectors (FP64)",
+               "refined vector of stage 2 (inverse iteration on R)", "A / A^T products (FP64)",
+               "projected eigensolvers (Jacobi)",
+               "fused A^T A SpMM (FP32)", "Gram / CGS passes (FP32)", "basis transforms / Ritz vectors (FP32)",
+               "(unused FP32 small)", "A / A^T products (FP32)", "(unused FP32 Jacobi)"]
+CLASS_KERNELS = {0: "k_csr_rows / k_ata_fused <double>", 1: "k_cgs_pass<double>", 2: "k_tall_small<double>",
+                 4: "k_csr_rows<double, 1>", 6: "k_csr_rows / k_ata_fused <float>", 7: "k_cgs_pass<float>",
+                 8: "k_tall_small<float>", 10: "k_csr_rows<float, 1>"}
 
 
 # the stage-1 projected eigensolve of a call: the FP32 pass and the FP64
 # clean-up of the target pairs, with the device helpers they call
 JACOBI_FUNCS = ["rr_pair", "rot_params", "rot_params_small", "k_jacobi_eig", "k_jacobi_targets"]
+# the block Gram-Schmidt pass (its ncu capture: profiles/cgs_pass_f64_1e6x5e5.txt)
+CGS_FUNCS = ["reduce_scatter_step", "k_cgs_pass"]
 
 
 def kernel_source_sha256(kernel_file, names):
@@ -406,7 +531,7 @@ def kernel_source_sha256(kernel_file, names):
 
 
 def measured_traffic(kernel_file, names, summary, key):
-    """DRAM bytes from a committed ncu summary, if the captured kernels' source
+    """A figure from a committed ncu summary, if the captured kernels' source
     is unchanged since the capture (the summary records its sha256)."""
     try:
         txt = open(os.path.join(ROOT, "profiles", summary)).read()
@@ -423,20 +548,28 @@ def measured_traffic(kernel_file, names, summary, key):
 
 def roofline_for(A, prof, dom, hbm, peak_kind):
     """Roofline of the dominant kernel class of one profiled solve.
-    Stage-1 projected eigensolve (class 5: the FP32 Jacobi pass with its FP64
-    clean-up of the target pairs, or the FP64 cluster Jacobi): algorithmic
-    flops per call = 18 j per rotation (rows and columns of H and the columns
-    of S, 6 j each) x rotations per call, against the GPU's FP64 peak.
-    Otherwise the fused SpMM against the measured HBM copy rate with the
-    one-read-of-A byte count."""
-    if dom == 5 and prof["n_class"][5] and prof["jacobi_calls"]:
-        # whole-solve algorithmic flops of the stage-1 projected solves over
-        # the class's whole device time (a solve is one or two launches)
-        calls = prof["jacobi_calls"]
-        j_avg = prof["jacobi_dim_sum"] / calls
-        rot = prof["jacobi_rotations"] / calls
+
+    * Projected eigensolve (class 5): algorithmic flops per call = 18 j per
+      rotation (rows and columns of H and the columns of S, 6 j each) x
+      rotations per call, against the FP64 peak.
+    * FP64 classes (0-4: products with C or B, Gram/CGS passes, basis
+      transforms): the algorithmic flops the library counts at each launch
+      (stats.class_flops) over the class's device time, against the FP64
+      peak.  At these shapes they do >= 1.7 flop per algorithmic byte, far
+      above GB300's FP64 ridge (1.25 TFLOP/s / 6.7 TB/s = 0.19 flop/B), so the
+      FP64 pipe, not HBM, bounds them.
+    * FP32 classes (6-10, the mixed-precision stage 1): the algorithmic bytes
+      (stats.class_bytes: each operand read once, each result written once)
+      over the class's time, against the measured HBM copy rate; their
+      <= 4 flop/B lies below the FP32 ridge (~10 flop/B)."""
+    calls = prof["n_class"][dom]
+    t_ms = prof["t_class_ms"][dom]
+    if dom in (5, 11) and calls and prof["jacobi_calls"]:
+        jc = prof["jacobi_calls"]
+        j_avg = prof["jacobi_dim_sum"] / jc
+        rot = prof["jacobi_rotations"] / jc
         flops = 18.0 * j_avg * rot
-        per_call_ms = prof["t_class_ms"][5] / calls
+        per_call_ms = t_ms / jc
         ach = flops / (per_call_ms * 1e-3) / 1e9
         tr = measured_traffic("k_small.cu", JACOBI_FUNCS, "jacobi_fp32_targets_grid32.txt", "dram_bytes_per_call")
         return {"bound": "alu", "kernel": "stage-1 projected eigensolve (Jacobi kernels of k_small.cu)",
@@ -444,16 +577,28 @@ def roofline_for(A, prof, dom, hbm, peak_kind):
                 "frac": ach / FP64_PEAK_GFLOPS, "traffic": tr,
                 "peak_source": "nominal FP64 rate of the GPU (152 SMs x 2 FMA/clk)",
                 "flops_per_solve_call": flops, "ms_per_solve_call": per_call_ms,
-                "launches_per_call": prof["n_class"][5] / calls, "j_avg": j_avg, "rotations_per_call": rot}
-    calls = prof["n_class"][0]
-    avg_ms = prof["t_class_ms"][0] / calls if calls else None
-    width = prof["spmm_c_width"]
-    p_bytes = 4 if prof["iters_stage1_fp32"] > 0 else 8
-    bytes_per = spmm_bytes(A.m, A.n, A.nnz, width, p_bytes)
-    ach = bytes_per / (avg_ms * 1e-3) / 1e9 if avg_ms else None
-    return {"bound": "hbm", "kernel": "fused A^T A SpMM (products with C)", "achieved": ach, "peak": hbm,
-            "unit": "GB/s", "frac": (ach / hbm) if ach else None, "traffic": None, "peak_source": peak_kind,
-            "bytes_per_launch": bytes_per, "avg_launch_ms": avg_ms}
+                "launches_per_call": calls / jc, "j_avg": j_avg, "rotations_per_call": rot}
+    fl = prof.get("class_flops", [0.0] * 12)[dom]
+    by = prof.get("class_bytes", [0.0] * 12)[dom]
+    avg_ms = t_ms / calls if calls else None
+    out = {"kernel": CLASS_KERNELS.get(dom, CLASS_NAMES[dom]), "avg_launch_ms": avg_ms, "launches": calls,
+           "flops_per_launch": fl / calls if calls else None, "bytes_per_launch": by / calls if calls else None,
+           "traffic": None}
+    if dom == 1:
+        out["traffic"] = measured_traffic("k_tall.cu", CGS_FUNCS, "cgs_pass_f64_1e6x5e5.txt", "dram_bytes_per_launch")
+        if out["traffic"] is not None:
+            out["traffic_launch"] = "the captured launch: n = 500,000, p = 55 basis columns, q = 8 (profiles/)"
+    if dom < 6:
+        ach = fl / (t_ms * 1e-3) / 1e12 if t_ms else None
+        out.update(bound="alu", achieved=ach, peak=FP64_PEAK_GFLOPS / 1e3, unit="TFLOP/s",
+                   frac=(ach * 1e3 / FP64_PEAK_GFLOPS) if ach else None,
+                   peak_source="nominal FP64 rate of the GPU (152 SMs x 2 FMA/clk x 2.06 GHz)")
+    else:
+        ach = by / (t_ms * 1e-3) / 1e9 if t_ms else None
+        out.update(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=(ach / hbm) if ach else None,
+                   peak_source=peak_kind)
+    return out
+
 
 
 def run_batched(a):
@@ -568,6 +713,8 @@ def run_learned(a):
 
 def main():
     a = parse()
+    if a.oracle_sample:
+        return oracle_sample(a)
     rank, world = dist_init(a)
     if a.impl == "reference":
         return run_reference(a, rank, world)
@@ -591,14 +738,16 @@ def main():
     r = res[head]
     st, prof = r["stats"], r["prof"]
     hbm, peak_kind = peaks()
-    names = ["fused A^T A SpMM", "Gram / CGS2 passes", "basis transforms / Ritz",
-             "refined vector of stage 2 (inverse iteration on R)", "A / A^T products (stage 2)",
-             "projected eigensolvers (Jacobi: FP32 pass + FP64 clean-up, or FP64 cluster)"]
     cls = prof["t_class_ms"]
     dom = int(max(range(len(cls)), key=lambda i: cls[i]))
     roof = roofline_for(A, prof, dom, hbm, peak_kind)
-    roof.update(dominant_class=names[dom], class_ms=dict(zip(names, cls)),
-                class_calls=dict(zip(names, prof["n_class"])))
+    per_class = {}
+    for c in range(len(cls)):
+        if cls[c] > 0 and prof["n_class"][c]:
+            rc = roofline_for(A, prof, c, hbm, peak_kind)
+            per_class[CLASS_NAMES[c]] = {"ms": cls[c], "launches": prof["n_class"][c], "bound": rc["bound"],
+                                         "achieved": rc["achieved"], "unit": rc["unit"], "frac": rc["frac"]}
+    roof.update(dominant_class=CLASS_NAMES[dom], classes=per_class)
     line = {
         "metric": METRIC,
         "value": world * cfg["k"] / (r["ms"] / 1e3),
@@ -610,8 +759,8 @@ def main():
         "vs_baseline": None,
         "dtype": "f32+f64" if head == native.MIXED else "f64",
         "data": "synthetic",
-        "config": dict(cfg, precision="mixed" if head == native.MIXED else "fp64",
-                       parallelism=f"replicas{world}"),
+        "config": dict({k: v for k, v in cfg.items() if k != "golden"},
+                       precision="mixed" if head == native.MIXED else "fp64", parallelism=f"replicas{world}"),
         "roofline": roof,
         "gpu_launches": r["launches"],
         "gpu_launches_per_step": r["launches"] // max(r["steps"], 1),
@@ -620,16 +769,30 @@ def main():
         "solve": {"iters_stage1": st["iters_stage1"], "iters_stage1_fp32": st["iters_stage1_fp32"],
                   "iters_stage2": st["iters_stage2"], "matvecs_A": st["matvecs_A"], "switched": st["switched"],
                   "max_resid_over_normA": max(r["resid_rel"]), "spmm_schedule": st["spmm_schedule"],
-                  "jacobi_sweeps": st["jacobi_sweeps"], "jacobi_rotations": st["jacobi_rotations"],
-                  "restarts": st["restarts"]},
+                  "spmm_plan_cached": st["spmm_plan_cached"], "jacobi_sweeps": st["jacobi_sweeps"],
+                  "jacobi_rotations": st["jacobi_rotations"], "restarts": st["restarts"],
+                  "ms_min": min(r["times"]), "ms_max": max(r["times"])},
     }
+    g = golden(a)
+    if g:
+        par = {"oracle": f"tests/golden/oracle_counts.json[{cfg['golden']}] (FP64 oracle, {g['iters_stage1']} + "
+                         f"{g['iters_stage2']} outer iterations)",
+               "sigma_oracle": g["sigma"]}
+        for p_, nm in ((native.MIXED, "mixed"), (native.FP64, "fp64")):
+            if p_ in res and res[p_]["err_vs_oracle"] is not None:
+                e = res[p_]["err_vs_oracle"]
+                par[f"sigma_rel_err_{nm}"] = e
+                par[f"max_sigma_rel_err_{nm}"] = max(e)
+                par[f"max_resid_over_normA_{nm}"] = max(res[p_]["resid_rel"])
+        line["parity"] = par
     if native.FP64 in res and head != native.FP64:
         f = res[native.FP64]
         line["fp64"] = {"value": world * cfg["k"] / (f["ms"] / 1e3), "ms_per_step": f["ms"], "steps": f["steps"],
                         "iters_stage1": f["stats"]["iters_stage1"], "iters_stage2": f["stats"]["iters_stage2"],
                         "speedup_mixed_over_fp64": f["ms"] / r["ms"],
                         "max_sigma_rel_diff_vs_mixed": max(abs(x - y) / y for x, y in zip(r["sigma"], f["sigma"])),
-                        "class_ms": dict(zip(names, f["prof"]["t_class_ms"]))}
+                        "class_ms": {CLASS_NAMES[i]: v for i, v in enumerate(f["prof"]["t_class_ms"]) if v > 0},
+                        "e2e": f["e2e"]}
     if a.spmm_cases:
         sp = spmm_full(a)
         line["spmm"] = sp
@@ -642,28 +805,69 @@ def main():
                                      "unit": "GB/s", "frac": best["GBps"] / hbm, "traffic": None,
                                      "bytes_per_launch": best["alg_bytes"], "avg_launch_ms": best["avg_launch_ms"]}
     if rank == 0 and not a.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(A, a, cfg["k"], st["iters_stage1"] + st["iters_stage2"])
+        line["cpu_baseline"] = cpu_baseline(a, cfg["k"], st["iters_stage1"] + st["iters_stage2"])
     if rank == 0:
         print(json.dumps(line), flush=True)
 
 
 def run_reference(a, rank, world):
     """The oracle (plain CPU FP64 PHSVDS, as it stands) on the host cores, on the
-    same workload; rank 0 only, the other ranks exit without work."""
+    same workload; rank 0 only, the other ranks exit without work.  Each step
+    is a bounded sample: the first --ref-iters outer iterations of the solve,
+    with every host core as a BLAS thread; its triplets/s is the sample's time
+    per iteration scaled to the oracle's own recorded iteration count for the
+    workload (labelled extrapolated), its ms_per_step the sample's real time."""
     if rank != 0:
         return
+    ncpu = os.cpu_count() or 1
+    if "numpy" not in sys.modules:      # the BLAS pool size is fixed when numpy loads
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+            os.environ.setdefault(v, str(ncpu))
+    threads = int(os.environ.get("OPENBLAS_NUM_THREADS", ncpu))
+    from oracle import phsvds_ref as R
     A, cfg = workload(a)
-    steps = []
+    k = cfg["k"]
+    gi = golden_iters(a)
+    total = gi if gi else 4000
+
+    class Stop(Exception):
+        pass
+
+    vals, secs, its = [], [], []
     for i in range(a.warmup + a.steps):
-        cb = cpu_baseline(A, a, cfg["k"], fallback_iters=golden_iters(a) or 4000)
+        state = {"it": 0}
+
+        def tr(stage, it, d):
+            state["it"] += 1
+            if state["it"] >= a.ref_iters:
+                raise Stop()
+
+        t0 = time.perf_counter()
+        try:
+            R.phsvds(A, k, largest=cfg["target"] == "largest", delta=TOL, o=R.Opts(block=a.block,
+                                                                                  precond=a.precond, trace=tr))
+            done = True
+        except Stop:
+            done = False
+        el = time.perf_counter() - t0
         if i >= a.warmup:
-            steps.append(cb)
-    v = sum(x["value"] for x in steps) / len(steps)
+            n_it = max(state["it"], 1)
+            est = el if done else el / n_it * total
+            vals.append(k / est)
+            secs.append(el)
+            its.append(n_it)
+    v = sum(vals) / len(vals)
+    ms = 1e3 * sum(secs) / len(secs)
+    sample = (f"EXTRAPOLATED: each step runs the first {its[-1]} of the oracle's {total} outer iterations "
+              f"({ms / 1e3:.1f} s), scaled to a whole solve ({k / v:.0f} s); {threads} BLAS threads "
+              f"(scipy sparse products single-threaded)")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "triplets/s", "n_gpus": world,
-            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * cfg["k"] / v, "higher_is_better": True,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(cfg, precision="fp64", parallelism="host cores"),
-            "cpu_baseline": dict(steps[-1], value=v),
+            "config": dict({kk: vv for kk, vv in cfg.items() if kk != "golden"}, precision="fp64",
+                           parallelism="host cores"),
+            "cpu_baseline": {"value": v, "unit": "triplets/s", "cores": threads, "kind": "oracle",
+                             "sample": sample, "extrapolated": True},
             "e2e": {"value": v, "unit": "triplets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

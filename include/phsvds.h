@@ -112,6 +112,15 @@ typedef struct {
      * the targets, whenever the last targets were >= 1e-5 theta_max (FP32
      * resolves them; GB300's FP64 latency is ~14x its FP32 latency), else 0 */
     int projected_solver;
+    /* optional initial guess of stage 1 (the hand-off between runs of
+     * Sec. 3.3: e.g. the right singular vectors of an earlier solve): host
+     * pointer to init_nv columns of length n, column-major, that replace the
+     * default start (ones(n,1)/sqrt(n) plus random columns, Sec. 5); they are
+     * copied at the start of the solve and orthonormalised on the device.
+     * NULL = default start; init_nv = 0 means k columns; 0 <= init_nv <=
+     * max_basis. */
+    const double* init_V;
+    int init_nv;
 } phsvds_opts;
 
 typedef struct {
@@ -130,11 +139,11 @@ typedef struct {
      * class: [0] fused A^T A SpMM (products with C), [1] Gram / CGS passes,
      * [2] basis transforms and Ritz vectors, [3] the refined vector of stage
      * 2 (inverse iteration on R; also the Jacobi SVD entry point), [4] single
-     * products with A or
-     * A^T (products with B), [5] the projected eigensolvers (Jacobi, FP64 and
-     * FP32 passes) */
-    double t_class_ms[6];
-    int64_t n_class[6];
+     * products with A or A^T (products with B), [5] the projected
+     * eigensolvers (Jacobi, FP64 and FP32 passes); [6 + c] is class c of the
+     * FP32-storage launches of the mixed-precision stage 1 ([0..5] FP64) */
+    double t_class_ms[12];
+    int64_t n_class[12];
     int64_t spmm_c_calls;      /* C-products, each one fused A^T A SpMM launch set */
     double spmm_c_ms;          /* their summed device time (opts.profile) */
     int spmm_c_width;          /* block width of the stage-1 C-products */
@@ -146,6 +155,13 @@ typedef struct {
     int64_t fell_back_at;      /* stage-1 iteration of the fallback */
     int64_t recorded;          /* residuals written to opts.record_r */
     int64_t stage1_stagnation_locks;  /* targets locked on their rounding floor, finished by stage 2 */
+    int spmm_plan_cached;      /* 1 if the autotuned SpMM schedule came from an earlier solve on this
+                                  handle of a matrix with the same m, n, nnz (and block width) */
+    /* algorithmic work per kernel class (the classes of t_class_ms): flops,
+     * and the bytes the operations must move at least (each operand read
+     * once, each result written once); filled with or without opts.profile */
+    double class_flops[12];
+    double class_bytes[12];
 } phsvds_stats;
 
 /* Create a context on CUDA device `device`.  cuda_stream: a cudaStream_t to run
@@ -281,7 +297,9 @@ phsvds_status phsvds_cnn_adam(phsvds_handle h, float* w, float* grad, float* m, 
  * b = 8 FP32) is gathered with 256-bit loads.  Runs on the handle's stream;
  * asynchronous (nothing is read back).
  * Errors: PHSVDS_ERR_INVALID (nothing launched) for bad sizes, b, schedule or
- * lanes; PHSVDS_ERR_CUDA for a failed launch.
+ * lanes, or a NULL pointer the schedule reads (col_idx and val when nnz > 0;
+ * for schedule 2 also csc_ptr, z, and csc_row and csc_val when nnz > 0);
+ * PHSVDS_ERR_CUDA for a failed launch.
  */
 phsvds_status phsvds_ata_spmm_f64(phsvds_handle h, int schedule, int lanes_a, int lanes_at, int64_t m, int64_t n,
                                   int64_t nnz, const int32_t* row_ptr, const int32_t* col_idx, const double* val,
@@ -313,14 +331,18 @@ phsvds_status phsvds_ata_spmm_f32(phsvds_handle h, int schedule, int lanes_a, in
  * row-major, b in {1, 2, 4, 8}, CSR and CSC copies of A), except: no schedule
  * and no z; nnz is passed by the caller (it picks the lanes per row, and
  * taking it as an argument avoids reading row_ptr[m] back to the host).
- * Errors: PHSVDS_ERR_INVALID, with nothing launched, for bad arguments or when
- * m * b > PHSVDS_STATIC_Z_MAX (use phsvds_ata_spmm_f64 then);
+ * Errors: PHSVDS_ERR_INVALID, with nothing launched, for bad arguments (a NULL
+ * pointer, among them a NULL col_idx, val, csc_row or csc_val when nnz > 0) or
+ * when m * b > PHSVDS_STATIC_Z_MAX (use phsvds_ata_spmm_f64 then);
  * PHSVDS_ERR_CUDA when the scratch cannot be located or a launch fails.
  * Runs on the handle's stream; asynchronous.
  *
  * The first call on each device makes that device current and looks up the
  * array's address (cudaGetSymbolAddress), which may also load the library's
  * device code; make this first call before any stream capture begins.  The
+ * address is kept for the life of the process: after a cudaDeviceReset of
+ * that device the library's device code may be loaded elsewhere, so the
+ * entry point must not be called again on that device in the same process.  The
  * scratch needs no clearing, since the first phase writes every entry the
  * second reads.  There is ONE scratch per device, shared by all handles and
  * threads: calls whose executions can overlap (different streams, or handles
@@ -393,6 +415,49 @@ phsvds_status phsvds_jacobi_svd_f64(phsvds_handle h, int j, double* G, double* S
 phsvds_status phsvds_refined_vector_f64(phsvds_handle h, int j, const double* R, int ldr, const double* x0,
                                         const double* H, int ldh, int maxit, double tau, double* s1,
                                         double* out, int* steps_out);
+
+/*
+ * Kernel-level entry point: one pass of block classical Gram-Schmidt, the
+ * step that orthonormalises the new basis vectors of Algorithms 1 and 2
+ * against the locked vectors and the basis (two passes, "CGS2"), and that
+ * forms the projected matrix V^T W of the Rayleigh-Ritz step (Algorithm 2
+ * step 7).  With P = [P1 | P2] (n x p1 and n x p2, column-major, leading
+ * dimensions ld1, ld2 >= n; p = p1 + p2 <= 64) and the block T (n x q,
+ * leading dimension ldt >= n, 1 <= q <= 8), in this order:
+ *   if Gsub: T <- T - P Gsub      (Gsub p x q, column-major, leading dim p);
+ *   if Gout: Gout += P^T T        (p x q, column-major, leading dim p);
+ *   if Tout: Tout += T^T T        (q x q, column-major).
+ * Gsub, Gout, Tout are FP64 (each may be NULL); Gout and Tout accumulate, so
+ * the caller zeroes them first.  Products accumulate per thread in the
+ * storage precision and across thread blocks in FP64.  All pointers DEVICE.
+ * Asynchronous on the handle's stream.  Errors: PHSVDS_ERR_INVALID (nothing
+ * launched) for bad sizes or NULL pointers; PHSVDS_ERR_CUDA for a failed launch.
+ */
+phsvds_status phsvds_block_cgs_f64(phsvds_handle h, int64_t n, const double* P1, int ld1, int p1,
+                                   const double* P2, int ld2, int p2, double* T, int ldt, int q,
+                                   const double* Gsub, double* Gout, double* Tout);
+/* Same with FP32 storage of P and T (the mixed-precision stage 1). */
+phsvds_status phsvds_block_cgs_f32(phsvds_handle h, int64_t n, const float* P1, int ld1, int p1,
+                                   const float* P2, int ld2, int p2, float* T, int ldt, int q,
+                                   const double* Gsub, double* Gout, double* Tout);
+
+/*
+ * Kernel-level entry point: Out = P Y - Xs diag(theta) (the Ritz vectors
+ * X = V S and residuals R = W S - X Theta of the targeted pairs, and the basis
+ * transforms V <- V Y of thick restart and locking, Algorithm 2 steps 7-10).
+ * P n x p (ld ldp >= n, 1 <= p <= 64), Y p x r FP64 (ld ldy >= p,
+ * 1 <= r <= 64), Out n x r (ld ldo >= n); theta (r, FP64) and Xs (n x r, ld
+ * ldx) may be NULL together (no subtraction); Out may equal P when r <= p (in
+ * place).  norms2 (r, FP64, or NULL): norms2[c] += ||Out(:, c)||^2.  All
+ * pointers DEVICE; asynchronous.  Errors as phsvds_block_cgs_f64.
+ */
+phsvds_status phsvds_tall_small_f64(phsvds_handle h, int64_t n, const double* P, int ldp, int p, const double* Y,
+                                    int ldy, int r, double* Out, int ldo, const double* Xs, int ldx,
+                                    const double* theta, double* norms2);
+/* Same with FP32 storage of P, Out and Xs. */
+phsvds_status phsvds_tall_small_f32(phsvds_handle h, int64_t n, const float* P, int ldp, int p, const double* Y,
+                                    int ldy, int r, float* Out, int ldo, const float* Xs, int ldx,
+                                    const double* theta, double* norms2);
 
 /* Synchronise the handle's stream. */
 phsvds_status phsvds_sync(phsvds_handle h);

@@ -271,15 +271,27 @@ int lanes_for(double avg_row) {
   return 8;
 }
 
+// Algorithmic work of one product with C = A^T A on b vectors (the SpMM unit):
+// one read of the CSR (values and column indices, row offsets), X read once,
+// Y written once; 4 nnz b flops.
+template <typename T>
+static void count_ata(const SparseView<T>& A, int ncols, int b) {
+  count_work(pcat<T>(PROF_CSPMM), 4.0 * (double)A.nnz * b,
+             (double)A.nnz * (sizeof(T) + 4) + 4.0 * (A.nrows + 1) + 2.0 * sizeof(T) * ncols * b);
+}
+
 template <typename T>
 void csr_spmm(cudaStream_t s, const SparseView<T>& A, int b, const T* X, T* Z, int lanes) {
-  ProfScope ps(s, PROF_SPMV);
+  ProfScope ps(s, pcat<T>(PROF_SPMV));
+  count_work(pcat<T>(PROF_SPMV), 2.0 * (double)A.nnz * b,
+             (double)A.nnz * (sizeof(T) + 4) + 4.0 * (A.nrows + 1) + (double)sizeof(T) * b * (A.ncols + A.nrows));
   dispatch_B<T, false>(s, b, lanes != 0 ? lanes : lanes_for(A.avg_row()), A, X, Z);
 }
 
 template <typename T>
 void ata_fused(cudaStream_t s, const SparseView<T>& A, int ncols, int b, const T* X, T* Y, int lanes) {
-  ProfScope ps(s, PROF_CSPMM);
+  ProfScope ps(s, pcat<T>(PROF_CSPMM));
+  count_ata(A, ncols, b);
   cudaMemsetAsync(Y, 0, sizeof(T) * (size_t)ncols * b, s);
   dispatch_B<T, true>(s, b, lanes != 0 ? lanes : lanes_for(A.avg_row()), A, X, Y);
 }
@@ -287,9 +299,10 @@ void ata_fused(cudaStream_t s, const SparseView<T>& A, int ncols, int b, const T
 template <typename T>
 void ata_two_phase(cudaStream_t s, const SparseView<T>& A, const SparseView<T>& At, int b, const T* X, T* Y,
                    T* Z, int lanes_a, int lanes_at) {
-  ProfScope ps(s, PROF_CSPMM);
-  csr_spmm<T>(s, A, b, X, Z, lanes_a);
-  csr_spmm<T>(s, At, b, Z, Y, lanes_at);
+  ProfScope ps(s, pcat<T>(PROF_CSPMM));
+  count_ata(A, At.nrows, b);
+  dispatch_B<T, false>(s, b, lanes_a != 0 ? lanes_a : lanes_for(A.avg_row()), A, X, Z);
+  dispatch_B<T, false>(s, b, lanes_at != 0 ? lanes_at : lanes_for(At.avg_row()), At, Z, Y);
 }
 
 template void csr_spmm<double>(cudaStream_t, const SparseView<double>&, int, const double*, double*, int);

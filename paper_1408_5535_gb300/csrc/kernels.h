@@ -42,8 +42,15 @@ int lanes_for(double avg_row);
 
 // Instrumentation (per host thread): kernel launch count, and optional CUDA
 // events around kernel classes when a solve runs with opts.profile = 1.
-enum ProfCat { PROF_CSPMM = 0, PROF_GRAM = 1, PROF_TALL = 2, PROF_SMALL = 3, PROF_SPMV = 4, PROF_JACOBI = 5, PROF_NCAT = 6 };
+// Classes 0-5 are the FP64 launches; 6-11 the same classes in FP32 storage.
+enum ProfCat { PROF_CSPMM = 0, PROF_GRAM = 1, PROF_TALL = 2, PROF_SMALL = 3, PROF_SPMV = 4, PROF_JACOBI = 5, PROF_NCAT = 6,
+               PROF_F32 = 6, PROF_NALL = 12 };
+template <typename T> constexpr int pcat(int c) { return sizeof(T) == 4 ? c + PROF_F32 : c; }
 void count_launch();
+// Algorithmic work of a launch (per host thread, per kernel class): flops and
+// the bytes the operation must move at least (each operand read once, each
+// result written once), for the roofline of a profiled solve.
+void count_work(int cat, double flops, double bytes);
 void prof_begin(cudaStream_t s, int cat);
 void prof_end(cudaStream_t s, int cat);
 struct ProfScope {
@@ -85,9 +92,14 @@ struct Basis {
 //   if Gsub:  T <- T - P * Gsub      (Gsub: p x q, column-major ld p, FP64)
 //   if Gout:  Gout += P^T T          (p x q, FP64, must be zeroed by caller)
 //   if Tout:  Tout += T^T T          (q x q, FP64, must be zeroed by caller)
+// With cond (device int) the pass runs only when *cond == run_if (decided on
+// the device, so the sequence can be replayed in a graph).
 template <typename T>
 void cgs_pass(cudaStream_t s, int n, const Basis<T>& P, T* Tb, int ldt, int q, const double* Gsub, double* Gout,
-              double* Tout);
+              double* Tout, const int* cond = nullptr, int run_if = 0);
+// *flag = 1 when some column c of the first-pass projection G (p x q) has
+// ||G(:,c)||^2 > tn2[c] / 2, i.e. a second Gram-Schmidt pass is needed.
+void reorth_test(cudaStream_t s, int p, int q, const double* G, const double* tn2, int* flag);
 
 // Out (n x r, column-major ld ldo) = P (n x p) * Y (p x r, FP64 column-major ld ldy)
 // [- Xs (n x r) * diag(theta)] when theta != nullptr.  In-place allowed when

@@ -68,6 +68,14 @@ struct Pool {
   }
 };
 
+// An SpMM schedule picked by the autotuner for one matrix shape and block
+// width (kept by the handle, reused by its later solves of that shape).
+struct SpmmPlan {
+  int64_t m = 0, n = 0, nnz = 0;
+  int b = 0, bytes = 0;
+  int schedule = 2, lanes = 0, lanes_a = 0, lanes_at = 0;
+};
+
 }  // namespace ph
 
 struct phsvds_ctx {
@@ -77,6 +85,7 @@ struct phsvds_ctx {
   std::string err;
   unsigned char* host = nullptr;  // pinned readback / upload area
   size_t host_bytes = 0;
+  std::vector<ph::SpmmPlan> plans;  // autotuned SpMM schedules of earlier solves
 };
 
 namespace ph {
@@ -96,18 +105,23 @@ struct Host {
 // ---- instrumentation (per host thread)
 static thread_local int64_t g_launch_count = 0;
 void count_launch() { ++g_launch_count; }
+static thread_local double g_work[2][PROF_NALL] = {};  // [0] flops, [1] bytes per kernel class
+void count_work(int cat, double flops, double bytes) {
+  g_work[0][cat] += flops;
+  g_work[1][cat] += bytes;
+}
 
 struct Profiler {
   bool on = false;
-  int depth[PROF_NCAT] = {};
+  int depth[PROF_NALL] = {};
   std::vector<cudaEvent_t> ev;
   std::vector<int> evcat;
   size_t used = 0;
-  double acc_ms[PROF_NCAT] = {};  // intervals already folded in (the buffer is reused)
-  int64_t acc_n[PROF_NCAT] = {};
+  double acc_ms[PROF_NALL] = {};  // intervals already folded in (the buffer is reused)
+  int64_t acc_n[PROF_NALL] = {};
   void start(size_t cap) {
     on = true;
-    for (int c = 0; c < PROF_NCAT; ++c) depth[c] = 0, acc_ms[c] = 0.0, acc_n[c] = 0;
+    for (int c = 0; c < PROF_NALL; ++c) depth[c] = 0, acc_ms[c] = 0.0, acc_n[c] = 0;
     while (ev.size() < cap) {
       cudaEvent_t e;
       if (cudaEventCreate(&e) != cudaSuccess) break;
@@ -142,7 +156,7 @@ struct Profiler {
   void finish(double* ms, int64_t* cnt) {
     fold();
     on = false;
-    for (int c = 0; c < PROF_NCAT; ++c) ms[c] += acc_ms[c], cnt[c] += acc_n[c];
+    for (int c = 0; c < PROF_NALL; ++c) ms[c] += acc_ms[c], cnt[c] += acc_n[c];
   }
 };
 static thread_local Profiler g_prof;
@@ -317,6 +331,29 @@ static COp<T> autotune_spmm(cudaStream_t s, Pool& pool, const SparseView<T>& A, 
 
 static inline int spmm_width(int nb) { return nb >= 8 ? 8 : nb >= 4 ? 4 : nb >= 2 ? 2 : 1; }
 
+// The autotuned schedule for this matrix shape and block width: the handle's
+// plan from an earlier solve of the same m, n, nnz, b and precision, else a
+// fresh autotune, which is then kept.  Any plan computes the same product
+// (the schedules differ only in summation order), so a plan taken from
+// another matrix of the same shape costs at most speed.
+template <typename T>
+static COp<T> tuned_spmm(phsvds_ctx* ctx, Pool& pool, const SparseView<T>& A, const SparseView<T>& At, T* Z, int n,
+                         int b, bool* cached) {
+  for (const SpmmPlan& p : ctx->plans)
+    if (p.m == A.nrows && p.n == n && p.nnz == A.nnz && p.b == b && p.bytes == (int)sizeof(T)) {
+      *cached = true;
+      return COp<T>{&A, &At, Z, n, p.schedule, p.lanes, p.lanes_a, p.lanes_at};
+    }
+  COp<T> op = autotune_spmm<T>(ctx->stream, pool, A, At, Z, n, b);
+  SpmmPlan p;
+  p.m = A.nrows, p.n = n, p.nnz = A.nnz, p.b = b, p.bytes = (int)sizeof(T);
+  p.schedule = op.schedule, p.lanes = op.lanes, p.lanes_a = op.lanes_a, p.lanes_at = op.lanes_at;
+  if (ctx->plans.size() >= 64) ctx->plans.erase(ctx->plans.begin());
+  ctx->plans.push_back(p);
+  *cached = false;
+  return op;
+}
+
 // Jacobi frame of the projected problem, rebuilt from the exact projected
 // matrix Ht (basis coordinates): ns_steps Newton-Schulz steps
 // S <- S (3I - S^T S)/2 keep the accumulated rotation orthonormal (each step
@@ -401,7 +438,12 @@ struct GraphCache {
     int seen = 0;
     cudaGraphExec_t exec = nullptr;
     int64_t launches = 0;
+    double work[2][PROF_NALL] = {};  // algorithmic work of one replay
   };
+  static void add_work(const Entry& e) {
+    for (int a = 0; a < 2; ++a)
+      for (int c = 0; c < PROF_NALL; ++c) g_work[a][c] += e.work[a][c];
+  }
   std::unordered_map<uint64_t, Entry> map;
   bool enabled = true;
   ~GraphCache() {
@@ -415,10 +457,13 @@ struct GraphCache {
     if (e.exec) {
       CUCHK(cudaGraphLaunch(e.exec, s));
       g_launch_count += e.launches;
+      add_work(e);
       return;
     }
     if (e.seen++ == 0) return issue();
     const int64_t l0 = g_launch_count;
+    double w0[2][PROF_NALL];
+    std::memcpy(w0, g_work, sizeof(w0));
     if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
       cudaGetLastError();
       enabled = false;
@@ -439,6 +484,9 @@ struct GraphCache {
     if (g) cudaGraphDestroy(g);
     const int64_t captured = g_launch_count - l0;
     g_launch_count = l0;
+    for (int a = 0; a < 2; ++a)
+      for (int c = 0; c < PROF_NALL; ++c) e.work[a][c] = g_work[a][c] - w0[a][c];
+    std::memcpy(g_work, w0, sizeof(w0));
     if (st != cudaSuccess || !e.exec) {  // nothing ran: switch off and run eagerly
       cudaGetLastError();
       e.exec = nullptr;
@@ -448,6 +496,7 @@ struct GraphCache {
     e.launches = captured;
     CUCHK(cudaGraphLaunch(e.exec, s));
     g_launch_count += e.launches;
+    add_work(e);
   }
 };
 
@@ -584,8 +633,11 @@ struct Stage1 {
     Basis<T> P{Xl, n, nlock, V, n, j};
     const int p = P.cols();
     for (int attempt = 0;; ++attempt) {
-      // two CGS passes against [locked, basis], the Gram of the remainder and
-      // its Cholesky (graph-cached: one segment without host syncs)
+      // CGS against [locked, basis]: the projection, then either the
+      // subtraction with the Gram of the remainder, or (when the device-side
+      // test finds a column that lost more than 1/sqrt(2) of its norm) a
+      // second pass; then the Cholesky of the remainder's Gram (graph-cached:
+      // one segment without host syncs)
       auto pass = [&]() {
         zero(s, innorm, nb);
         col_norms2_dense<T>(s, n, Tb, n, nb, innorm);
@@ -593,8 +645,14 @@ struct Stage1 {
         zero(s, G2, (size_t)p * nb);
         zero(s, P1, (size_t)nb * nb);
         cgs_pass<T>(s, n, P, Tb, n, nb, nullptr, G1, nullptr);
-        cgs_pass<T>(s, n, P, Tb, n, nb, G1, G2, nullptr);
-        cgs_pass<T>(s, n, P, Tb, n, nb, G2, nullptr, P1);
+        if (p > 0) {
+          reorth_test(s, p, nb, G1, innorm, flags + 40);
+          cgs_pass<T>(s, n, P, Tb, n, nb, G1, nullptr, P1, flags + 40, 0);
+          cgs_pass<T>(s, n, P, Tb, n, nb, G1, G2, nullptr, flags + 40, 1);
+          cgs_pass<T>(s, n, P, Tb, n, nb, G2, nullptr, P1, flags + 40, 1);
+        } else {
+          cgs_pass<T>(s, n, P, Tb, n, nb, nullptr, nullptr, P1);
+        }
         chol_factor(s, nb, P1, innorm, 1e-10, M1, flags);
         CUCHK(cudaMemcpyAsync(h.at<int>(0), flags, sizeof(int) * (nb + 1), cudaMemcpyDeviceToHost, s));
       };
@@ -933,6 +991,7 @@ struct Orth1 {
   phsvds_ctx* ctx;
   cudaStream_t s;
   double *G1, *G2, *tn, *inn, *minv;
+  int* flag;
   uint64_t seed;
   int rand_ctr = 0;
   Orth1(phsvds_ctx* c, Pool& p, uint64_t sd) : ctx(c), s(c->stream), seed(sd) {
@@ -941,6 +1000,7 @@ struct Orth1 {
     tn = p.get<double>(4);
     inn = p.get<double>(4);
     minv = p.get<double>(4);
+    flag = p.get<int>(4);
   }
   void run(int N, const Basis<double>& P, double* t, double* dst) {
     Host h(ctx);
@@ -952,8 +1012,14 @@ struct Orth1 {
       zero(s, G2, p);
       zero(s, tn, 1);
       cgs_pass<double>(s, N, P, t, N, 1, nullptr, G1, nullptr);
-      cgs_pass<double>(s, N, P, t, N, 1, G1, G2, nullptr);
-      cgs_pass<double>(s, N, P, t, N, 1, G2, nullptr, tn);
+      if (p > 0) {  // the second pass only where the first lost more than 1/sqrt(2) of the norm
+        reorth_test(s, p, 1, G1, inn, flag);
+        cgs_pass<double>(s, N, P, t, N, 1, G1, nullptr, tn, flag, 0);
+        cgs_pass<double>(s, N, P, t, N, 1, G1, G2, nullptr, flag, 1);
+        cgs_pass<double>(s, N, P, t, N, 1, G2, nullptr, tn, flag, 1);
+      } else {
+        cgs_pass<double>(s, N, P, t, N, 1, nullptr, nullptr, tn);
+      }
       CUCHK(cudaMemcpyAsync(h.at<double>(0), tn, sizeof(double), cudaMemcpyDeviceToHost, s));
       CUCHK(cudaMemcpyAsync(h.at<double>(8), inn, sizeof(double), cudaMemcpyDeviceToHost, s));
       sync(s);
@@ -1377,15 +1443,18 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
   // SpMM schedule
   COp<double> op64{&A.A64, &A.At64, A.Z64, A.n, (int)o.spmm};
   COp<float> op32{&A.A32, &A.At32, A.Z32, A.n, (int)o.spmm};
+  bool cached64 = false, cached32 = false;
   if (o.spmm == PHSVDS_SPMM_AUTO) {
-    op64 = autotune_spmm<double>(s, pool, A.A64, A.At64, A.Z64, A.n, spmm_width(b));
-    if (mixed) op32 = autotune_spmm<float>(s, pool, A.A32, A.At32, A.Z32, A.n, spmm_width(b));
+    op64 = tuned_spmm<double>(ctx, pool, A.A64, A.At64, A.Z64, A.n, spmm_width(b), &cached64);
+    if (mixed) op32 = tuned_spmm<float>(ctx, pool, A.A32, A.At32, A.Z32, A.n, spmm_width(b), &cached32);
   }
   const int sch64 = op64.schedule;
   if (st) {
     std::memset(st, 0, sizeof(*st));
     st->spmm_schedule = sch64;
   }
+  double work0[2][PROF_NALL];
+  std::memcpy(work0, g_work, sizeof(work0));
   if (o.profile) g_prof.start(1 << 16);
   // ---- stage 1
   const auto t1a = clk::now();
@@ -1412,11 +1481,23 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
     st->t_stage1_ms = std::chrono::duration<double, std::milli>(clk::now() - t1a).count();
     st->t_total_ms = std::chrono::duration<double, std::milli>(clk::now() - tstart).count();
   };
+  // optional initial guess (opts.init_V): host n x init_nv, column-major
+  const int nx0 = o.init_V ? std::min(o.init_nv > 0 ? o.init_nv : k, A.n) : 0;
+  double* X0d = nullptr;
+  if (nx0) {
+    X0d = pool.get<double>((size_t)A.n * nx0);
+    CUCHK(cudaMemcpyAsync(X0d, o.init_V, sizeof(double) * A.n * nx0, cudaMemcpyHostToDevice, s));
+  }
   if (mixed) {
     Stage1<float> s1f(ctx, pool, A.n, k, o, largest, tol_in, EPS32, precond, A.diagC, op32);
     s1f.lp = &ld;
+    float* X0f = nullptr;
+    if (nx0) {
+      X0f = pool.get<float>((size_t)A.n * nx0);
+      convert_f64_to_f32(s, (int64_t)A.n * nx0, X0d, X0f);
+    }
     try {
-      s1f.run(nullptr, 0);
+      s1f.run(X0f, nx0);
     } catch (const PhError&) {
       partial_stats(s1.out, &s1f.out);
       throw;
@@ -1449,7 +1530,7 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
     }
   } else {
     try {
-      s1.run(nullptr, 0);
+      s1.run(X0d, nx0);
     } catch (const PhError&) {
       partial_stats(s1.out, nullptr);
       throw;
@@ -1536,17 +1617,18 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
                                  cudaMemcpyDeviceToHost, s));
   }
   sync(s);
-  double cls_ms[PROF_NCAT] = {};
-  int64_t cls_n[PROF_NCAT] = {};
+  double cls_ms[PROF_NALL] = {};
+  int64_t cls_n[PROF_NALL] = {};
   if (o.profile) g_prof.finish(cls_ms, cls_n);
   if (st) {
-    for (int c = 0; c < PROF_NCAT; ++c) {
+    for (int c = 0; c < PROF_NALL; ++c) {
       st->t_class_ms[c] = cls_ms[c];
       st->n_class[c] = cls_n[c];
     }
     st->kernel_launches = g_launch_count - launches0;
-    st->spmm_c_calls = cls_n[PROF_CSPMM] ? cls_n[PROF_CSPMM] : s1.out.mv / std::max(1, spmm_width(b));
-    st->spmm_c_ms = cls_ms[PROF_CSPMM];
+    const int64_t nc_c = cls_n[PROF_CSPMM] + cls_n[PROF_CSPMM + PROF_F32];
+    st->spmm_c_calls = nc_c ? nc_c : (s1.out.mv + mv32) / std::max(1, spmm_width(b));
+    st->spmm_c_ms = cls_ms[PROF_CSPMM] + cls_ms[PROF_CSPMM + PROF_F32];
     st->spmm_c_width = spmm_width(b);
     st->jacobi_sweeps = s1.out.jac_sweeps + jac32[0];
     st->jacobi_rotations = s1.out.jac_rot + jac32[1];
@@ -1568,6 +1650,11 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
     st->t_stage2_ms = t2ms;
     st->t_total_ms = std::chrono::duration<double, std::milli>(clk::now() - tstart).count();
     st->spmm_schedule = sch64;
+    st->spmm_plan_cached = (o.spmm == PHSVDS_SPMM_AUTO) && cached64 && (!mixed || cached32);
+    for (int c = 0; c < PROF_NALL; ++c) {
+      st->class_flops[c] = g_work[0][c] - work0[0][c];
+      st->class_bytes[c] = g_work[1][c] - work0[1][c];
+    }
   }
   (void)iters32;
 }
@@ -1594,7 +1681,8 @@ static phsvds_status ata_api(phsvds_handle h, int schedule, int lanes_a, int lan
   };
   if (!h || m < 1 || n < 1 || m > INT32_MAX || n > INT32_MAX || nnz < 0 || nnz > INT32_MAX || !rp || !X || !Y ||
       (b != 1 && b != 2 && b != 4 && b != 8) || (schedule != 1 && schedule != 2) ||
-      (schedule == 2 && (!cp || !z)) || !lanes_ok(lanes_a) || !lanes_ok(lanes_at))
+      (schedule == 2 && (!cp || !z)) || (nnz > 0 && (!ci || !va)) ||
+      (schedule == 2 && nnz > 0 && (!ri || !cv)) || !lanes_ok(lanes_a) || !lanes_ok(lanes_at))
     return set_err(h, PHSVDS_ERR_INVALID, "invalid SpMM arguments");
   cudaError_t e = cudaSetDevice(h->device);
   if (e != cudaSuccess) return set_err(h, PHSVDS_ERR_CUDA, cudaGetErrorString(e));
@@ -1633,6 +1721,8 @@ phsvds_status phsvds_default_opts(phsvds_opts* o) {
   o->record_max = 0;
   o->record_every = 0;
   o->projected_solver = 2;
+  o->init_V = nullptr;
+  o->init_nv = 0;
   return PHSVDS_OK;
 }
 
@@ -1722,6 +1812,8 @@ phsvds_status phsvds_solve(phsvds_handle h, int64_t m, int64_t n, int64_t nnz, c
     return set_err(h, PHSVDS_ERR_INVALID, "learned correction needs params, features and grid_nx * grid_ny = n");
   if (o.record_r && (o.record_max < 0 || o.record_every < 1))
     return set_err(h, PHSVDS_ERR_INVALID, "recording needs record_max >= 0 and record_every >= 1");
+  if (o.init_V && (o.init_nv < 0 || o.init_nv > o.max_basis || (o.init_nv == 0 && k > o.max_basis)))
+    return set_err(h, PHSVDS_ERR_INVALID, "init_V needs 0 <= init_nv <= max_basis (0 = k columns)");
   try {
     CUCHK(cudaSetDevice(h->device));
     solve_impl(h, m, n, nnz, row_ptr, col_idx, val, ptr_on_device, k, target, tol, precond, o, sigma, U, V, resid,
@@ -1729,8 +1821,8 @@ phsvds_status phsvds_solve(phsvds_handle h, int64_t m, int64_t n, int64_t nnz, c
   } catch (const PhError& e) {
     cudaStreamSynchronize(h->stream);
     cudaGetLastError();
-    double ms[PROF_NCAT] = {0, 0, 0, 0, 0};
-    int64_t cnt[PROF_NCAT] = {0, 0, 0, 0, 0};
+    double ms[PROF_NALL] = {};
+    int64_t cnt[PROF_NALL] = {};
     g_prof.finish(ms, cnt);
     return set_err(h, e.st, e.msg);
   }
@@ -1807,6 +1899,65 @@ phsvds_status phsvds_refined_vector_f64(phsvds_handle h, int j, const double* R,
 }  // extern "C"
 
 // ===========================================================================
+// Kernel-level entry points of the tall-skinny dense steps
+// ===========================================================================
+template <typename T>
+static phsvds_status block_cgs_api(phsvds_handle h, int64_t n, const T* P1, int ld1, int p1, const T* P2, int ld2,
+                                   int p2, T* Tb, int ldt, int q, const double* Gsub, double* Gout, double* Tout) {
+  if (!h || n < 1 || n > INT32_MAX || p1 < 0 || p2 < 0 || p1 + p2 > 64 || q < 1 || q > 8 || !Tb || ldt < n ||
+      (p1 > 0 && (!P1 || ld1 < n)) || (p2 > 0 && (!P2 || ld2 < n)) || ((Gsub || Gout) && p1 + p2 == 0))
+    return set_err(h, PHSVDS_ERR_INVALID, "invalid block Gram-Schmidt arguments");
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return set_err(h, PHSVDS_ERR_CUDA, cudaGetErrorString(e));
+  Basis<T> P{P1, ld1, p1, P2, ld2, p2};
+  cgs_pass<T>(h->stream, (int)n, P, Tb, ldt, q, Gsub, Gout, Tout);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? PHSVDS_OK : set_err(h, PHSVDS_ERR_CUDA, cudaGetErrorString(e));
+}
+
+template <typename T>
+static phsvds_status tall_small_api(phsvds_handle h, int64_t n, const T* P, int ldp, int p, const double* Y, int ldy,
+                                    int r, T* Out, int ldo, const T* Xs, int ldx, const double* theta,
+                                    double* norms2) {
+  if (!h || n < 1 || n > INT32_MAX || p < 1 || p > 64 || r < 1 || r > 64 || !P || ldp < n || !Y || ldy < p ||
+      !Out || ldo < n || (theta && (!Xs || ldx < n)) || (Out == P && r > p))
+    return set_err(h, PHSVDS_ERR_INVALID, "invalid tall-times-small arguments");
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) return set_err(h, PHSVDS_ERR_CUDA, cudaGetErrorString(e));
+  tall_times_small<T>(h->stream, (int)n, P, ldp, p, Y, ldy, r, Out, ldo, theta ? Xs : nullptr, ldx, theta, norms2);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? PHSVDS_OK : set_err(h, PHSVDS_ERR_CUDA, cudaGetErrorString(e));
+}
+
+extern "C" {
+
+phsvds_status phsvds_block_cgs_f64(phsvds_handle h, int64_t n, const double* P1, int ld1, int p1, const double* P2,
+                                   int ld2, int p2, double* T, int ldt, int q, const double* Gsub, double* Gout,
+                                   double* Tout) {
+  return block_cgs_api<double>(h, n, P1, ld1, p1, P2, ld2, p2, T, ldt, q, Gsub, Gout, Tout);
+}
+
+phsvds_status phsvds_block_cgs_f32(phsvds_handle h, int64_t n, const float* P1, int ld1, int p1, const float* P2,
+                                   int ld2, int p2, float* T, int ldt, int q, const double* Gsub, double* Gout,
+                                   double* Tout) {
+  return block_cgs_api<float>(h, n, P1, ld1, p1, P2, ld2, p2, T, ldt, q, Gsub, Gout, Tout);
+}
+
+phsvds_status phsvds_tall_small_f64(phsvds_handle h, int64_t n, const double* P, int ldp, int p, const double* Y,
+                                    int ldy, int r, double* Out, int ldo, const double* Xs, int ldx,
+                                    const double* theta, double* norms2) {
+  return tall_small_api<double>(h, n, P, ldp, p, Y, ldy, r, Out, ldo, Xs, ldx, theta, norms2);
+}
+
+phsvds_status phsvds_tall_small_f32(phsvds_handle h, int64_t n, const float* P, int ldp, int p, const double* Y,
+                                    int ldy, int r, float* Out, int ldo, const float* Xs, int ldx,
+                                    const double* theta, double* norms2) {
+  return tall_small_api<float>(h, n, P, ldp, p, Y, ldy, r, Out, ldo, Xs, ldx, theta, norms2);
+}
+
+}  // extern "C"
+
+// ===========================================================================
 // Allocation-free A^T (A X): the two-phase product with its intermediate
 // Z = A X held in a fixed array of the library's own device memory.  The array
 // is placed in device memory when the library's device code is loaded, so a
@@ -1825,7 +1976,7 @@ extern "C" phsvds_status phsvds_ata_spmm_static_f64(phsvds_handle h, int64_t m, 
                                                     const int32_t* csc_ptr, const int32_t* csc_row,
                                                     const double* csc_val, int b, const double* X, double* Y) {
   if (!h || m < 1 || n < 1 || n > INT32_MAX || nnz < 0 || nnz > INT32_MAX || !row_ptr || !csc_ptr || !X || !Y ||
-      (b != 1 && b != 2 && b != 4 && b != 8))
+      (nnz > 0 && (!col_idx || !val || !csc_row || !csc_val)) || (b != 1 && b != 2 && b != 4 && b != 8))
     return set_err(h, PHSVDS_ERR_INVALID, "invalid SpMM arguments");
   if (m * b > PHSVDS_STATIC_Z_MAX)
     return set_err(h, PHSVDS_ERR_INVALID,

@@ -34,7 +34,8 @@ class Opts(C.Structure):
                 ("seed", C.c_uint64), ("time_limit_s", C.c_double), ("profile", C.c_int),
                 ("learned_params", C.c_void_p), ("learned_features", C.c_void_p), ("grid_nx", C.c_int),
                 ("grid_ny", C.c_int), ("stall_window", C.c_int), ("record_r", C.c_void_p), ("record_max", C.c_int),
-                ("record_every", C.c_int), ("projected_solver", C.c_int)]
+                ("record_every", C.c_int), ("projected_solver", C.c_int), ("init_V", C.c_void_p),
+                ("init_nv", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -42,11 +43,12 @@ class Stats(C.Structure):
                 ("iters_stage1_fp32", C.c_int64), ("iters_stage2", C.c_int64), ("restarts", C.c_int64),
                 ("switched", C.c_int), ("norm_A_est", C.c_double), ("t_stage1_ms", C.c_double),
                 ("t_stage2_ms", C.c_double), ("t_total_ms", C.c_double), ("spmm_schedule", C.c_int),
-                ("kernel_launches", C.c_int64), ("t_class_ms", C.c_double * 6), ("n_class", C.c_int64 * 6),
+                ("kernel_launches", C.c_int64), ("t_class_ms", C.c_double * 12), ("n_class", C.c_int64 * 12),
                 ("spmm_c_calls", C.c_int64), ("spmm_c_ms", C.c_double), ("spmm_c_width", C.c_int),
                 ("jacobi_sweeps", C.c_int64), ("jacobi_rotations", C.c_int64), ("jacobi_calls", C.c_int64),
                 ("jacobi_dim_sum", C.c_int64), ("fell_back", C.c_int), ("fell_back_at", C.c_int64),
-                ("recorded", C.c_int64), ("stage1_stagnation_locks", C.c_int64)]
+                ("recorded", C.c_int64), ("stage1_stagnation_locks", C.c_int64), ("spmm_plan_cached", C.c_int),
+                ("class_flops", C.c_double * 12), ("class_bytes", C.c_double * 12)]
 
     def as_dict(self) -> dict:
         d = {}
@@ -95,6 +97,10 @@ def _load() -> C.CDLL:
         "phsvds_jacobi_eig_cluster_f64": ([P, I, P, P, P, D, I, P], I),
         "phsvds_jacobi_svd_f64": ([P, I, P, P, P, D, I, P], I),
         "phsvds_refined_vector_f64": ([P, I, P, I, P, P, I, I, D, P, P, P], I),
+        "phsvds_block_cgs_f64": ([P, I64, P, I, I, P, I, I, P, I, I, P, P, P], I),
+        "phsvds_block_cgs_f32": ([P, I64, P, I, I, P, I, I, P, I, I, P, P, P], I),
+        "phsvds_tall_small_f64": ([P, I64, P, I, I, P, I, I, P, I, P, I, P, P], I),
+        "phsvds_tall_small_f32": ([P, I64, P, I, I, P, I, I, P, I, P, I, P, P], I),
         "phsvds_sync": ([P], I),
         "phsvds_last_error": ([P], C.c_char_p),
         "phsvds_status_string": ([I], C.c_char_p),
@@ -120,8 +126,9 @@ def lib() -> C.CDLL:
 EXPORTED = ["phsvds_create", "phsvds_default_opts", "phsvds_solve", "phsvds_solve_batched", "phsvds_normal_cg",
             "phsvds_cnn_forward", "phsvds_cnn_backward", "phsvds_cnn_adam", "phsvds_ata_spmm_f64",
             "phsvds_ata_spmm_f32", "phsvds_ata_spmm_static_f64", "phsvds_csr_to_csc_f64", "phsvds_jacobi_eig_f64", "phsvds_jacobi_eig_cluster_f64",
-            "phsvds_jacobi_svd_f64", "phsvds_refined_vector_f64", "phsvds_sync", "phsvds_last_error", "phsvds_status_string",
-            "phsvds_destroy"]
+            "phsvds_jacobi_svd_f64", "phsvds_refined_vector_f64", "phsvds_block_cgs_f64", "phsvds_block_cgs_f32",
+            "phsvds_tall_small_f64", "phsvds_tall_small_f32", "phsvds_sync", "phsvds_last_error",
+            "phsvds_status_string", "phsvds_destroy"]
 
 
 def _ptr(x) -> int | None:
@@ -176,11 +183,13 @@ def default_opts(**kw) -> Opts:
 
 def phsvds_solve(h: Handle, m, n, row_ptr, col_idx, val, k, target=SMALLEST, tol=1e-14,
                  precond=PREC_NONE, opts: Opts | None = None, on_device=False, want_vectors=True,
-                 raise_on_error=True):
+                 raise_on_error=True, init_V=None):
     """phsvds_solve: k smallest / largest triplets of the m x n CSR matrix.
 
     row_ptr int64 (m+1), col_idx int32, val float64, as numpy arrays (host) or
-    torch CUDA tensors (on_device=True).  Returns (sigma, U, V, resid, stats, status).
+    torch CUDA tensors (on_device=True).  init_V: optional n x c host array,
+    the initial guess of stage 1 (opts.init_V / init_nv).
+    Returns (sigma, U, V, resid, stats, status).
     """
     nnz = int(row_ptr[-1]) if isinstance(row_ptr, np.ndarray) else int(row_ptr[-1].item())
     sigma = np.zeros(k)
@@ -189,6 +198,13 @@ def phsvds_solve(h: Handle, m, n, row_ptr, col_idx, val, k, target=SMALLEST, tol
     resid = np.zeros(k)
     st = Stats()
     o = opts if opts is not None else default_opts()
+    x0 = None
+    if init_V is not None:
+        x0 = np.asfortranarray(np.asarray(init_V, dtype=np.float64).reshape(n, -1))
+        o2 = Opts.from_buffer_copy(o)
+        o2.init_V = x0.ctypes.data
+        o2.init_nv = x0.shape[1]
+        o = o2
     status = lib().phsvds_solve(h.h, m, n, nnz, _ptr(row_ptr), _ptr(col_idx), _ptr(val), 1 if on_device else 0,
                                 k, target, tol, precond, C.byref(o), _ptr(sigma), _ptr(U), _ptr(V),
                                 _ptr(resid), C.byref(st))
@@ -301,6 +317,22 @@ def phsvds_refined_vector(h: Handle, j, R, ldr, x0, H, ldh, s1, out, maxit=24, t
     """Refined vector of R (device tensors): s1, out = (theta1, ||R s1||)."""
     h.check(lib().phsvds_refined_vector_f64(h.h, j, _ptr(R), ldr, _ptr(x0), _ptr(H), ldh, maxit, tau, _ptr(s1),
                                             _ptr(out), _ptr(steps)))
+
+
+def phsvds_block_cgs(h: Handle, n, P1, ld1, p1, T, ldt, q, Gsub=None, Gout=None, Tout=None, P2=None, ld2=0, p2=0,
+                     fp32=False):
+    """One block CGS pass on device tensors (column-major blocks given by
+    pointer, leading dimension and column count; Gsub/Gout/Tout FP64)."""
+    f = lib().phsvds_block_cgs_f32 if fp32 else lib().phsvds_block_cgs_f64
+    h.check(f(h.h, n, _ptr(P1), ld1, p1, _ptr(P2), ld2, p2, _ptr(T), ldt, q, _ptr(Gsub), _ptr(Gout), _ptr(Tout)))
+
+
+def phsvds_tall_small(h: Handle, n, P, ldp, p, Y, ldy, r, Out, ldo, Xs=None, ldx=0, theta=None, norms2=None,
+                      fp32=False):
+    """Out = P Y - Xs diag(theta) (+ column norms^2) on device tensors."""
+    f = lib().phsvds_tall_small_f32 if fp32 else lib().phsvds_tall_small_f64
+    h.check(f(h.h, n, _ptr(P), ldp, p, _ptr(Y), ldy, r, _ptr(Out), ldo, _ptr(Xs), ldx, _ptr(theta),
+              _ptr(norms2)))
 
 
 def phsvds_sync(h: Handle):

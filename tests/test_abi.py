@@ -48,3 +48,9 @@ def test_create_without_gpu_fails_cleanly(lib):
         pytest.skip("a GPU is present")
     with pytest.raises(native.PhsvdsError):
         native.Handle(0)
+
+
+def test_static_scratch_capacity_matches_header():
+    """The binding's capacity of the allocation-free SpMM scratch is the header's."""
+    txt = open(os.path.join(ROOT, "include", "phsvds.h")).read()
+    assert int(re.search(r"#define\s+PHSVDS_STATIC_Z_MAX\s+(\d+)", txt).group(1)) == native.STATIC_Z_MAX

@@ -51,8 +51,9 @@ def test_measured_traffic_is_voided_by_a_source_change(tmp_path, monkeypatch):
 
 
 def test_roofline_of_the_projected_eigensolve_class():
-    prof = {"n_class": [10, 0, 0, 0, 0, 300], "t_class_ms": [1.0, 0, 0, 0, 0, 60.0], "jacobi_calls": 200,
-            "jacobi_dim_sum": 200 * 27, "jacobi_rotations": 200 * 700, "spmm_c_width": 4, "iters_stage1_fp32": 0}
+    prof = {"n_class": [10, 0, 0, 0, 0, 300] + [0] * 6, "t_class_ms": [1.0, 0, 0, 0, 0, 60.0] + [0] * 6,
+            "jacobi_calls": 200, "jacobi_dim_sum": 200 * 27, "jacobi_rotations": 200 * 700, "spmm_c_width": 4,
+            "iters_stage1_fp32": 0}
     r = bench.roofline_for(None, prof, 5, 6761.6, "measured")
     flops = 18.0 * 27 * 700
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
@@ -62,13 +63,38 @@ def test_roofline_of_the_projected_eigensolve_class():
     assert r["launches_per_call"] == pytest.approx(1.5)
 
 
-def test_roofline_of_the_spmm_class():
-    class A:
-        m, n, nnz = 1000, 500, 4000
-    prof = {"n_class": [10, 0, 0, 0, 0, 0], "t_class_ms": [2.0, 0, 0, 0, 0, 0], "jacobi_calls": 0,
-            "spmm_c_width": 4, "iters_stage1_fp32": 3}
-    r = bench.roofline_for(A, prof, 0, 6761.6, "measured")
+def test_roofline_of_an_fp32_class_is_bandwidth():
+    """FP32 classes (mixed stage 1): the counted algorithmic bytes over the
+    class's device time, against the measured HBM rate."""
     b = bench.spmm_bytes(1000, 500, 4000, 4, 4)
+    prof = {"n_class": [0] * 6 + [10, 0, 0, 0, 0, 0], "t_class_ms": [0.0] * 6 + [2.0, 0, 0, 0, 0, 0],
+            "class_flops": [0.0] * 6 + [10 * 4 * 4000 * 4.0] + [0.0] * 5,
+            "class_bytes": [0.0] * 6 + [10.0 * b] + [0.0] * 5, "jacobi_calls": 0}
+    r = bench.roofline_for(None, prof, 6, 6761.6, "measured")
     assert r["bound"] == "hbm" and r["bytes_per_launch"] == b
     assert r["achieved"] == pytest.approx(b / 0.2e-3 / 1e9)
     assert r["frac"] == pytest.approx(r["achieved"] / 6761.6)
+
+
+def test_roofline_of_an_fp64_class_is_the_fp64_pipe():
+    """FP64 classes: counted algorithmic flops over the class's device time,
+    against GB300's FP64 peak (they lie far above its FP64 ridge)."""
+    prof = {"n_class": [0, 4, 0, 0, 0, 0] + [0] * 6, "t_class_ms": [0.0, 8.0, 0, 0, 0, 0] + [0.0] * 6,
+            "class_flops": [0.0, 4 * 8.8e8, 0, 0, 0, 0] + [0.0] * 6,
+            "class_bytes": [0.0, 4 * 2.4e8, 0, 0, 0, 0] + [0.0] * 6, "jacobi_calls": 0}
+    r = bench.roofline_for(None, prof, 1, 6761.6, "measured")
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert r["achieved"] == pytest.approx(4 * 8.8e8 / 8e-3 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / 1.25)
+    assert r["flops_per_launch"] == pytest.approx(8.8e8)
+
+
+def test_oracle_samples_are_scaled_by_the_recorded_iterations():
+    import argparse
+    ns = argparse.Namespace(workload="c3", grid=64, sigma_log=1.0, k=20, block=8, precond="none")
+    gi = bench.golden_iters(ns)
+    assert gi and gi > 0
+    v, est, total, gold = bench._scaled(ns, 20, {"seconds": 10.0, "iters": 5, "finished": False}, 999)
+    assert gold and total == gi and est == pytest.approx(10.0 / 5 * gi) and v == pytest.approx(20 / est)
+    v, est, total, gold = bench._scaled(ns, 20, {"seconds": 10.0, "iters": 5, "finished": True}, 999)
+    assert est == 10.0

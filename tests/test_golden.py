@@ -53,10 +53,15 @@ def test_oracle_counts_rerun_smallest_case():
 
 def test_oracle_counts_cover_the_benchmark_workload():
     g = json.load(open(os.path.join(GOLD, "oracle_counts.json")))
-    assert {"grid16", "grid32"} <= set(g)
-    for v in g.values():
+    assert {"grid16", "grid32", "c3_largest"} <= set(g)
+    for name, v in g.items():
         assert v["iters_stage1"] > 0 and max(v["resid_over_normA"]) <= 1e-14
-        assert v["switched"]            # smallest triplets of a grid need stage 2
+        if name.startswith("grid"):
+            assert v["switched"]        # smallest triplets of a grid need stage 2
+    c3 = g["c3_largest"]
+    assert c3["target"] == "largest" and c3["k"] == 20 and c3["n"] == 500000 and c3["nnz"] == 12495439
+    sig = np.asarray(c3["sigma"])
+    assert np.all(np.diff(sig) < 0) and abs(c3["normA"] - sig[0]) <= 1e-12 * sig[0]
 
 
 def test_oracle_jdqmr_form_reproduces_table1():

@@ -132,6 +132,46 @@ def test_device_pointer_input(h):
     _check(A, sig, U, V, res, 3, sd, np.linalg.norm(A.to_dense(), 2))
 
 
+def test_warm_start_from_an_earlier_solve(h):
+    """opts.init_V, the hand-off between runs (Sec. 3.3): the right singular
+    vectors of a finished solve, given as the initial guess of stage 1, give
+    the same triplets in far fewer stage-1 iterations; a bad init_nv is
+    refused before anything runs."""
+    A = synth.grid_gradient(20, 1.0, 2)
+    sig, U, V, res, st, _ = _solve(h, A, 5, block_size=2)
+    o = native.default_opts(block_size=2)
+    sig2, U2, V2, res2, st2, _ = native.phsvds_solve(h, A.m, A.n, A.row_ptr, A.col, A.val, 5, native.SMALLEST,
+                                                     DELTA, native.PREC_NONE, o, init_V=V)
+    ref = R.phsvds(A, 5, delta=DELTA, o=R.Opts(block=2))
+    nA = np.linalg.norm(A.to_dense(), 2)
+    _check(A, sig2, U2, V2, res2, 5, ref.sigma, nA)
+    assert st2["iters_stage1"] * 4 <= st["iters_stage1"], (st2["iters_stage1"], st["iters_stage1"])
+    bad = native.default_opts(block_size=2, max_basis=20)
+    x0 = np.ascontiguousarray(np.ones((A.n, 1)))
+    bad.init_V = x0.ctypes.data
+    bad.init_nv = 21
+    *_, status = native.phsvds_solve(h, A.m, A.n, A.row_ptr, A.col, A.val, 5, native.SMALLEST, DELTA,
+                                     native.PREC_NONE, bad, raise_on_error=False)
+    assert status == native.PHSVDS_ERR_INVALID
+
+
+def test_spmm_plan_is_kept_by_the_handle(h):
+    """The autotuned SpMM schedule of a matrix shape is reused by the next
+    solve of that shape on the same handle, with the same triplets."""
+    A = synth.random_sparse(500, 250, 7.0, 31, values="gaussian", shift=0.1)
+    with native.Handle(0) as h2:
+        o = native.default_opts(block_size=2)
+        r1 = native.phsvds_solve(h2, A.m, A.n, A.row_ptr, A.col, A.val, 3, native.SMALLEST, DELTA, opts=o)
+        r2 = native.phsvds_solve(h2, A.m, A.n, A.row_ptr, A.col, A.val, 3, native.SMALLEST, DELTA, opts=o)
+    assert r1[4]["spmm_plan_cached"] == 0 and r2[4]["spmm_plan_cached"] == 1
+    assert r1[4]["spmm_schedule"] == r2[4]["spmm_schedule"]
+    sd, _, _ = dense_triplets(A.to_dense(), 3)
+    _check(A, r2[0], r2[1], r2[2], r2[3], 3, sd, np.linalg.norm(A.to_dense(), 2))
+    # the work counters of the roofline: products with C counted at 4 nnz b flops each
+    st = r2[4]
+    assert st["class_flops"][0] > 0 and st["class_bytes"][1] > 0
+
+
 # ---- edge cases and failure paths (host-side, no GPU fault)
 _OK = dict(max_basis=14, min_restart=8)
 

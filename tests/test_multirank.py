@@ -48,11 +48,13 @@ def test_reference_arm_prints_from_rank_zero_only():
     """bench.py --impl reference under two ranks: one JSON line (rank 0), the
     oracle timed on a bounded sample of the 16 x 16 grid solve."""
     pytest.importorskip("torch")
-    r = _launch(2, ["bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0", "--grid", "16",
-                    "--cpu-seconds", "3"], 29612)
+    r = _launch(2, ["bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0", "--workload", "grid",
+                    "--grid", "16", "--ref-iters", "50"], 29612)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [json.loads(l) for l in r.stdout.splitlines() if l.startswith("{")]
     assert len(lines) == 1
     d = lines[0]
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+    assert d["cpu_baseline"]["extrapolated"] and "EXTRAPOLATED" in d["cpu_baseline"]["sample"]
+    assert d["ms_per_step"] > 0 and d["cpu_baseline"]["cores"] >= 1

@@ -5,23 +5,23 @@ memory handed to their own pool, or a loop where a cudaMalloc is not
 acceptable), so it keeps the intermediate A X in a fixed device array of the
 library.  These tests call it through the C ABI twice in a row and compare
 each result with the existing two-phase entry point (which takes a caller
-buffer) within the same rounding bound as the SpMM parity tests; they also
-check that oversized inputs are refused before anything runs, and that a
-repeated call leaves the device's free memory unchanged.  The file name keeps
-it last in collection, so it runs both after the other GPU tests and alone.
+buffer) and with the CPU product A^T (A X) of the oracle's sparse operator,
+both within the rounding bound of the SpMM parity tests; they also check that
+oversized inputs and NULL arrays are refused before anything runs, and that
+the calls leave the device's free memory unchanged from before the first one.
+The file name keeps it last in collection, so it runs both after the other GPU
+tests and alone.  (The header constant is checked against the binding on the
+CPU, in test_abi.py.)
 """
-import os
-import re
-
 import numpy as np
 import pytest
 
 from paper_1408_5535_gb300 import native, synth
+from oracle import phsvds_ref as R
 from tests.gpu_util import torch, need_gpu, dev, device_csr
 
 pytestmark = pytest.mark.gpu
 EPS64 = 2.0 ** -52
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.fixture(scope="module")
@@ -47,11 +47,6 @@ def _existing(h, A, d, b, X):
     return Yd.cpu().numpy()
 
 
-def test_capacity_matches_header():
-    txt = open(os.path.join(ROOT, "include", "phsvds.h")).read()
-    assert int(re.search(r"#define\s+PHSVDS_STATIC_Z_MAX\s+(\d+)", txt).group(1)) == native.STATIC_Z_MAX
-
-
 @pytest.mark.parametrize("case,b", [(0, 8), (1, 4), (2, 1), (3, 8)])
 def test_two_calls_in_a_row_match_existing_entry_point(h, case, b):
     cases = [lambda: synth.random_sparse(3001, 1499, 12.0, 3),            # ragged tails, several tiles
@@ -64,19 +59,42 @@ def test_two_calls_in_a_row_match_existing_entry_point(h, case, b):
     nnz = int(A.row_ptr[-1])
     Xs = [(synth.uniform(7, 30 + t, A.n * b) * 2 - 1).reshape(A.n, b) for t in range(2)]
     refs = [_existing(h, A, d, b, X) for X in Xs]
+    ops = R.Ops(R.as_scipy(A))
+    cpu = [ops.C(X) for X in Xs]                      # the oracle's A^T (A X), FP64 on the CPU
     Xd = [dev(X) for X in Xs]
     Yd = [torch.full((A.n, b), float("nan"), dtype=torch.float64, device="cuda") for _ in Xs]
-    free = []
+    torch.cuda.synchronize()
+    free = [torch.cuda.mem_get_info()[0]]              # library loaded, before the first static call
     for t in range(2):
         native.phsvds_ata_spmm_static(h, A.m, A.n, nnz, d["rp"], d["ci"], d["va"], d["cp"], d["ri"], d["cv"], b,
                                       Xd[t], Yd[t])
         native.phsvds_sync(h)
         free.append(torch.cuda.mem_get_info()[0])
-    assert free[1] == free[0]
+    assert free[1] == free[0] and free[2] == free[0]
     for t in range(2):
         Y = Yd[t].cpu().numpy()
+        bound = _bound(A, d["scipy"], Xs[t]) + 1e-300
         assert np.all(np.isfinite(Y))
-        assert np.all(np.abs(Y - refs[t]) <= _bound(A, d["scipy"], Xs[t]) + 1e-300)
+        assert np.all(np.abs(Y - refs[t]) <= bound)
+        assert np.all(np.abs(Y - cpu[t]) <= bound)
+
+
+def test_null_arrays_are_refused_before_launch(h):
+    A = synth.random_sparse(300, 120, 5.0, 8)
+    d = device_csr(A)
+    b = 2
+    X = dev(np.ones((A.n, b)))
+    Y = torch.full((A.n, b), 7.0, dtype=torch.float64, device="cuda")
+    nnz = int(A.row_ptr[-1])
+    for drop in ("ci", "va", "ri", "cv"):
+        args = {k: d[k] for k in ("rp", "ci", "va", "cp", "ri", "cv")}
+        args[drop] = None
+        with pytest.raises(native.PhsvdsError) as ei:
+            native.phsvds_ata_spmm_static(h, A.m, A.n, nnz, args["rp"], args["ci"], args["va"], args["cp"],
+                                          args["ri"], args["cv"], b, X, Y)
+        assert ei.value.status == 1
+    native.phsvds_sync(h)
+    assert bool(torch.all(Y == 7.0))
 
 
 def test_oversized_input_is_refused_before_launch(h):
