@@ -494,10 +494,10 @@ CLASS_NAMES = ["fused A^T A SpMM (FP64)", "Gram / CGS passes (FP64)", "basis tra
                "refined vector of stage 2 (inverse iteration on R)", "A / A^T products (FP64)",
                "projected eigensolvers (Jacobi)",
                "fused A^T A SpMM (FP32)", "Gram / CGS passes (FP32)", "basis transforms / Ritz vectors (FP32)",
-               "(unused FP32 small)", "A / A^T products (FP32)", "(unused FP32 Jacobi)"]
+               "inner MINRES vector kernels (FP32)", "A / A^T products (FP32)", "(unused FP32 Jacobi)"]
 CLASS_KERNELS = {0: "k_csr_rows / k_ata_fused <double>", 1: "k_cgs_pass<double>", 2: "k_tall_small<double>",
                  4: "k_csr_rows<double, 1>", 6: "k_csr_rows / k_ata_fused <float>", 7: "k_cgs_pass<float>",
-                 8: "k_tall_small<float>", 10: "k_csr_rows<float, 1>"}
+                 8: "k_tall_small<float>", 9: "k_jd_lanczos / k_jd_update / k_col_dots", 10: "k_csr_rows<float, 1>"}
 
 
 # the stage-1 projected eigensolve of a call: the FP32 pass and the FP64
@@ -771,6 +771,7 @@ def main():
                   "max_resid_over_normA": max(r["resid_rel"]), "spmm_schedule": st["spmm_schedule"],
                   "spmm_plan_cached": st["spmm_plan_cached"], "jacobi_sweeps": st["jacobi_sweeps"],
                   "jacobi_rotations": st["jacobi_rotations"], "restarts": st["restarts"],
+                  "inner_solves": st["inner_solves"], "inner_steps": st["inner_steps"],
                   "ms_min": min(r["times"]), "ms_max": max(r["times"])},
     }
     g = golden(a)

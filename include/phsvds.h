@@ -121,6 +121,18 @@ typedef struct {
      * max_basis. */
     const double* init_V;
     int init_nv;
+    /* PHSVDS_MIXED only: how the FP64 continuation of stage 1 expands its
+     * basis.  0 = plain GD+k (the residual); 1 (default) = the Jacobi-Davidson
+     * correction of the JDQMR form (Sec. 4): for each targeted Ritz pair
+     * (theta, x) an approximate solution t of (I - QQ^T)(C - theta I)
+     * (I - QQ^T) t = r, Q = [locked vectors, x], by MINRES in FP32 with the
+     * FP32 copy of A, at most inner_maxit steps (default 60) or until its
+     * residual falls by inner_tol (default 1e-3).  The Rayleigh-Ritz step,
+     * the convergence test and the orthogonalisation stay in FP64, so the
+     * accuracy is that of the FP64 method. */
+    int mixed_inner;
+    int inner_maxit;
+    double inner_tol;
 } phsvds_opts;
 
 typedef struct {
@@ -141,7 +153,9 @@ typedef struct {
      * 2 (inverse iteration on R; also the Jacobi SVD entry point), [4] single
      * products with A or A^T (products with B), [5] the projected
      * eigensolvers (Jacobi, FP64 and FP32 passes); [6 + c] is class c of the
-     * FP32-storage launches of the mixed-precision stage 1 ([0..5] FP64) */
+     * FP32-storage launches of the mixed-precision stage 1 ([0..5] FP64),
+     * where [9] holds the vector kernels of the FP32 inner solves
+     * (opts.mixed_inner) */
     double t_class_ms[12];
     int64_t n_class[12];
     int64_t spmm_c_calls;      /* C-products, each one fused A^T A SpMM launch set */
@@ -162,6 +176,8 @@ typedef struct {
      * once, each result written once); filled with or without opts.profile */
     double class_flops[12];
     double class_bytes[12];
+    int64_t inner_solves;      /* Jacobi-Davidson corrections (opts.mixed_inner = 1): block inner solves */
+    int64_t inner_steps;       /* ... and their MINRES steps (each one FP32 product with C of the block) */
 } phsvds_stats;
 
 /* Create a context on CUDA device `device`.  cuda_stream: a cudaStream_t to run

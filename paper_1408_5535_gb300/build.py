@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libphsvds.so")
-SOURCES = ["k_sparse.cu", "k_tall.cu", "k_small.cu", "solver.cu", "batched.cu", "k_cnn.cu"]
+SOURCES = ["k_sparse.cu", "k_tall.cu", "k_small.cu", "solver.cu", "batched.cu", "k_cnn.cu", "k_inner.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "-I", CSRC]

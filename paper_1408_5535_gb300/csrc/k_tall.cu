@@ -72,9 +72,7 @@ __device__ __forceinline__ void reduce_scatter(T (&v)[N], int lane) {
 template <typename T, int Q>
 __global__ void __launch_bounds__(CG_THREADS) k_cgs_pass(int n, Basis<T> P, T* __restrict__ Tb, int ldt, int q,
                                                          const double* __restrict__ Gsub, double* __restrict__ Gout,
-                                                         double* __restrict__ Tout, int rows,
-                                                         const int* __restrict__ cond, int run_if) {
-  if (cond && *cond != run_if) return;  // a pass that the device-side test switched off
+                                                         double* __restrict__ Tout, int rows) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int p = P.cols();
   T* Ps = reinterpret_cast<T*>(smem_raw);                 // [p][rows]
@@ -189,7 +187,7 @@ __global__ void __launch_bounds__(CG_THREADS) k_cgs_pass(int n, Basis<T> P, T* _
 
 template <typename T, int Q>
 static void cgs_launch(cudaStream_t s, int n, const Basis<T>& P, T* Tb, int ldt, int q, const double* Gsub,
-                       double* Gout, double* Tout, const int* cond, int run_if) {
+                       double* Gout, double* Tout) {
   const int p = P.cols();
   // rows per chunk: 256 when the grid fills the GPU, fewer for short vectors
   // (the FP64 work of a pass then spreads over more SMs)
@@ -205,8 +203,7 @@ static void cgs_launch(cudaStream_t s, int n, const Basis<T>& P, T* Tb, int ldt,
   const int cap = num_sms() * (sizeof(T) == 8 ? 2 : 4);
   if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;
-  k_cgs_pass<T, Q><<<grid, CG_THREADS, smem, s>>>(n, P, Tb, ldt, q, Gsub, Gout, Tout, rows, cond, run_if);
-  count_launch();
+  k_cgs_pass<T, Q><<<grid, CG_THREADS, smem, s>>>(n, P, Tb, ldt, q, Gsub, Gout, Tout, rows); count_launch();
   count_work(pcat<T>(PROF_GRAM),
              2.0 * n * p * q * ((Gsub ? 1 : 0) + (Gout ? 1 : 0)) + (Tout ? (double)n * q * (q + 1) : 0.0),
              (double)sizeof(T) * n * ((Gsub || Gout ? p : 0) + q * (Gsub ? 2 : 1)));
@@ -214,37 +211,17 @@ static void cgs_launch(cudaStream_t s, int n, const Basis<T>& P, T* Tb, int ldt,
 
 template <typename T>
 void cgs_pass(cudaStream_t s, int n, const Basis<T>& P, T* Tb, int ldt, int q, const double* Gsub, double* Gout,
-              double* Tout, const int* cond, int run_if) {
+              double* Tout) {
   if (n <= 0 || q <= 0) return;
   ProfScope ps(s, pcat<T>(PROF_GRAM));
   Basis<T> PP = P;
   if (PP.cols() == 0) { Gsub = nullptr; Gout = nullptr; }
   switch (q) {
-    case 1: cgs_launch<T, 1>(s, n, PP, Tb, ldt, q, Gsub, Gout, Tout, cond, run_if); break;
-    case 2: cgs_launch<T, 2>(s, n, PP, Tb, ldt, q, Gsub, Gout, Tout, cond, run_if); break;
-    case 3: case 4: cgs_launch<T, 4>(s, n, PP, Tb, ldt, q, Gsub, Gout, Tout, cond, run_if); break;
-    default: cgs_launch<T, 8>(s, n, PP, Tb, ldt, q, Gsub, Gout, Tout, cond, run_if); break;
+    case 1: cgs_launch<T, 1>(s, n, PP, Tb, ldt, q, Gsub, Gout, Tout); break;
+    case 2: cgs_launch<T, 2>(s, n, PP, Tb, ldt, q, Gsub, Gout, Tout); break;
+    case 3: case 4: cgs_launch<T, 4>(s, n, PP, Tb, ldt, q, Gsub, Gout, Tout); break;
+    default: cgs_launch<T, 8>(s, n, PP, Tb, ldt, q, Gsub, Gout, Tout); break;
   }
-}
-
-// Second-pass test of classical Gram-Schmidt ("twice is enough"): one pass
-// leaves column c orthogonal to P to working accuracy when it keeps at least
-// 1/sqrt(2) of its norm, i.e. when ||P^T t_c||^2 <= ||t_c||^2 / 2 (Pythagoras,
-// reliable in that range).  flag = 1 if some column needs the second pass.
-__global__ void k_reorth_test(int p, int q, const double* __restrict__ G, const double* __restrict__ tn2,
-                              int* __restrict__ flag) {
-  const int lane = threadIdx.x;
-  int need = 0;
-  for (int c = 0; c < q; ++c) {
-    double g = 0.0;
-    for (int r = lane; r < p; r += 32) g += G[r + (size_t)c * p] * G[r + (size_t)c * p];
-    g = warp_sum(g);
-    need |= (g > 0.5 * tn2[c]) ? 1 : 0;
-  }
-  if (lane == 0) *flag = need;
-}
-void reorth_test(cudaStream_t s, int p, int q, const double* G, const double* tn2, int* flag) {
-  k_reorth_test<<<1, 32, 0, s>>>(p, q, G, tn2, flag); count_launch();
 }
 
 // ---------------------------------------------------------------------------
@@ -516,8 +493,7 @@ template void fill_const<float>(cudaStream_t, int64_t, float, float*);
 
 // explicit instantiations
 #define PH_INST(T)                                                                                              \
-  template void cgs_pass<T>(cudaStream_t, int, const Basis<T>&, T*, int, int, const double*, double*, double*, \
-                            const int*, int);                                                              \
+  template void cgs_pass<T>(cudaStream_t, int, const Basis<T>&, T*, int, int, const double*, double*, double*); \
   template void tall_times_small<T>(cudaStream_t, int, const T*, int, int, const double*, int, int, T*, int,    \
                                     const T*, int, const double*, double*);                                    \
   template void scale_block<T>(cudaStream_t, int, T*, int, int, const double*, T*, int);                       \

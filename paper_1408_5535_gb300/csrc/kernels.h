@@ -92,14 +92,9 @@ struct Basis {
 //   if Gsub:  T <- T - P * Gsub      (Gsub: p x q, column-major ld p, FP64)
 //   if Gout:  Gout += P^T T          (p x q, FP64, must be zeroed by caller)
 //   if Tout:  Tout += T^T T          (q x q, FP64, must be zeroed by caller)
-// With cond (device int) the pass runs only when *cond == run_if (decided on
-// the device, so the sequence can be replayed in a graph).
 template <typename T>
 void cgs_pass(cudaStream_t s, int n, const Basis<T>& P, T* Tb, int ldt, int q, const double* Gsub, double* Gout,
-              double* Tout, const int* cond = nullptr, int run_if = 0);
-// *flag = 1 when some column c of the first-pass projection G (p x q) has
-// ||G(:,c)||^2 > tn2[c] / 2, i.e. a second Gram-Schmidt pass is needed.
-void reorth_test(cudaStream_t s, int p, int q, const double* G, const double* tn2, int* flag);
+              double* Tout);
 
 // Out (n x r, column-major ld ldo) = P (n x p) * Y (p x r, FP64 column-major ld ldy)
 // [- Xs (n x r) * diag(theta)] when theta != nullptr.  In-place allowed when
@@ -211,6 +206,21 @@ void cg_dir(cudaStream_t s, int n, int b, const double* R, double* P, const doub
             const int* act);
 void cg_next(cudaStream_t s, int b, double* rr, double* rrn, const double* rr0, double tol2, double* pq, int* act,
              int* iters, int* bad);
+
+// ---- inner solves of the Jacobi-Davidson correction equation in FP32 (k_inner.cu)
+// Vectors column-major n x q (q <= 8), FP32.  acc: FP64 accumulators
+// (32 + 8 nl doubles, zeroed by the caller before each reduction): [0,8)
+// v^T C v, [8,16) v^T v, [16,24) x^T C v, [24,32) squared norms, [32, ...)
+// Xl^T C v (nl x q, leading dimension nl).  sc: the MINRES scalars (17 x 8).
+void jd_colnorms(cudaStream_t s, int n, int q, const float* R, double* acc);
+void jd_init(cudaStream_t s, int n, int q, const float* R, float* r1, float* r2, float* v, float* sol, float* w1,
+             float* w2, const double* acc, double* sc);
+void jd_dots(cudaStream_t s, int n, int q, const float* v, const float* X, const float* Cv, double* acc);
+void jd_step(cudaStream_t s, int n, int q, int nl, const float* Cv, float* v, const float* X, const float* Xl,
+             const double* theta, float* r1, float* r2, float* w1, float* w2, float* sol, double* acc, double* sc,
+             double tol);
+constexpr int JD_NSCALAR = 17;
+constexpr int JD_FIELD_ACT = 15;   // sc[JD_FIELD_ACT * 8 + c] != 0 while system c iterates
 
 // ---- learned correction network (k_cnn.cu)
 constexpr int CNN_NPARAM_H = 3024;

@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <unordered_map>
@@ -500,6 +501,86 @@ struct GraphCache {
   }
 };
 
+// Jacobi-Davidson corrections for the FP64 continuation of the mixed-precision
+// stage 1 (the JDQMR form of Sec. 4): the correction equation
+// (I - QQ^T)(C - theta I)(I - QQ^T) t = r, Q = [locked vectors, x], of each
+// targeted Ritz pair, solved for the block at once by MINRES in FP32 with the
+// FP32 products with C.  The outer Rayleigh-Ritz, the residuals that decide
+// convergence and the orthogonalisation of t into the basis stay in FP64.
+struct InnerJD {
+  cudaStream_t s;
+  int n, maxit, chunk = 5;
+  double tol;
+  COp<float> op;
+  float *R, *r1, *r2, *v, *sol, *w1, *w2, *X, *Cv, *Xrm, *Yrm, *Xl32;
+  double *acc, *sc;
+  GraphCache graphs;
+  int64_t steps = 0, solves = 0;
+  InnerJD(phsvds_ctx* c, Pool& pool, int n_, int kmax, COp<float> op_, int maxit_, double tol_, bool use_graphs)
+      : s(c->stream), n(n_), maxit(maxit_), tol(tol_), op(op_) {
+    const size_t nn = (size_t)n;
+    R = pool.get<float>(nn * 8);
+    r1 = pool.get<float>(nn * 8);
+    r2 = pool.get<float>(nn * 8);
+    v = pool.get<float>(nn * 8);
+    sol = pool.get<float>(nn * 8);
+    w1 = pool.get<float>(nn * 8);
+    w2 = pool.get<float>(nn * 8);
+    X = pool.get<float>(nn * 8);
+    Cv = pool.get<float>(nn * 8);
+    Xrm = pool.get<float>(nn * 8);
+    Yrm = pool.get<float>(nn * 8);
+    Xl32 = pool.get<float>(nn * std::max(kmax, 1));
+    acc = pool.get<double>(32 + 8 * 64);
+    sc = pool.get<double>(JD_NSCALAR * 8);
+    graphs.enabled = use_graphs;
+  }
+  // Tb (n x q, FP64): residuals on entry, corrections on return.  Xu: the q
+  // Ritz vectors, theta (device, q): their Ritz values, Xl: nl locked vectors.
+  void solve(phsvds_ctx* ctx, int q, double* Tb, const double* Xu, const double* theta, const double* Xl, int nl) {
+    Host h(ctx);
+    const size_t nq = (size_t)n * q;
+    convert_f64_to_f32(s, (int64_t)nq, Tb, R);
+    convert_f64_to_f32(s, (int64_t)nq, Xu, X);
+    if (nl) convert_f64_to_f32(s, (int64_t)n * nl, Xl, Xl32);
+    zero(s, v, (size_t)n * 8);   // the columns past q feed the SpMM's padding
+    zero(s, acc, 32);
+    jd_colnorms(s, n, q, R, acc);
+    jd_init(s, n, q, R, r1, r2, v, sol, w1, w2, acc, sc);
+    const int w = spmm_width(q);
+    const size_t nacc = 32 + (size_t)8 * nl;
+    auto step = [&]() {
+      cm_to_rm<float>(s, n, v, n, w, Xrm);
+      op.apply(s, w, Xrm, Yrm);
+      rm_to_cm<float>(s, n, Yrm, w, Cv, n);
+      zero(s, acc, nacc);
+      if (nl) {
+        Basis<float> P{Xl32, n, nl, nullptr, 0, 0};
+        cgs_pass<float>(s, n, P, Cv, n, q, nullptr, acc + 32, nullptr);
+      }
+      jd_dots(s, n, q, v, X, Cv, acc);
+      jd_step(s, n, q, nl, Cv, v, X, Xl32, theta, r1, r2, w1, w2, sol, acc, sc, tol);
+    };
+    double* hact = h.at<double>(16384);  // bytes [16384, 16448)
+    int it = 0;
+    while (it < maxit) {
+      const int m = std::min(chunk, maxit - it);
+      graphs.run(s, (3ull << 40) | ((uint64_t)m << 16) | ((uint64_t)nl << 8) | (uint64_t)q, [&]() {
+        for (int i = 0; i < m; ++i) step();
+      });
+      it += m;
+      CUCHK(cudaMemcpyAsync(hact, sc + JD_FIELD_ACT * 8, sizeof(double) * 8, cudaMemcpyDeviceToHost, s));
+      sync(s);
+      bool any = false;
+      for (int c = 0; c < q; ++c) any = any || hact[c] != 0.0;
+      if (!any) break;
+    }
+    steps += it;
+    ++solves;
+    convert_f32_to_f64(s, (int64_t)nq, sol, Tb);
+  }
+};
+
 struct Stage1Out {
   std::vector<double> lam;   // k eigenvalues of C (target order)
   double theta_max = 0.0;
@@ -559,6 +640,9 @@ struct Stage1 {
   // residual recording (FP64 pass only)
   double* rec_r = nullptr;
   int rec_max = 0, rec_every = 0;
+  // Jacobi-Davidson corrections with FP32 inner solves (FP64 continuation of
+  // the mixed-precision stage 1), or null for the plain GD+k correction
+  InnerJD* jd = nullptr;
 
   Stage1(phsvds_ctx* c, Pool& p, int n_, int k_, const phsvds_opts& o, bool largest_, double delta_, double eps,
          int precond_, const double* diag, COp<T> op_)
@@ -633,11 +717,12 @@ struct Stage1 {
     Basis<T> P{Xl, n, nlock, V, n, j};
     const int p = P.cols();
     for (int attempt = 0;; ++attempt) {
-      // CGS against [locked, basis]: the projection, then either the
-      // subtraction with the Gram of the remainder, or (when the device-side
-      // test finds a column that lost more than 1/sqrt(2) of its norm) a
-      // second pass; then the Cholesky of the remainder's Gram (graph-cached:
-      // one segment without host syncs)
+      // two CGS passes against [locked, basis], the Gram of the remainder and
+      // its Cholesky (graph-cached: one segment without host syncs).  The
+      // second pass is never skipped: one pass leaves the block orthogonal
+      // only to the accuracy of its projections, whose per-thread partial
+      // sums run over tens of terms (~30 eps), which in FP32 is above the
+      // stage's own tolerance.
       auto pass = [&]() {
         zero(s, innorm, nb);
         col_norms2_dense<T>(s, n, Tb, n, nb, innorm);
@@ -645,14 +730,8 @@ struct Stage1 {
         zero(s, G2, (size_t)p * nb);
         zero(s, P1, (size_t)nb * nb);
         cgs_pass<T>(s, n, P, Tb, n, nb, nullptr, G1, nullptr);
-        if (p > 0) {
-          reorth_test(s, p, nb, G1, innorm, flags + 40);
-          cgs_pass<T>(s, n, P, Tb, n, nb, G1, nullptr, P1, flags + 40, 0);
-          cgs_pass<T>(s, n, P, Tb, n, nb, G1, G2, nullptr, flags + 40, 1);
-          cgs_pass<T>(s, n, P, Tb, n, nb, G2, nullptr, P1, flags + 40, 1);
-        } else {
-          cgs_pass<T>(s, n, P, Tb, n, nb, nullptr, nullptr, P1);
-        }
+        cgs_pass<T>(s, n, P, Tb, n, nb, G1, G2, nullptr);
+        cgs_pass<T>(s, n, P, Tb, n, nb, G2, nullptr, P1);
         chol_factor(s, nb, P1, innorm, 1e-10, M1, flags);
         CUCHK(cudaMemcpyAsync(h.at<int>(0), flags, sizeof(int) * (nb + 1), cudaMemcpyDeviceToHost, s));
       };
@@ -881,9 +960,17 @@ struct Stage1 {
       for (int c = 0; c < nu; ++c) {
         CUCHK(cudaMemcpyAsync(Tb + (size_t)c * n, Rr + (size_t)unconv[c] * n, sizeof(T) * n,
                               cudaMemcpyDeviceToDevice, s));
-        if (precond == PHSVDS_PREC_JACOBI)
+        if (precond == PHSVDS_PREC_JACOBI || jd)
           CUCHK(cudaMemcpyAsync(XU + (size_t)c * n, Xr + (size_t)unconv[c] * n, sizeof(T) * n,
                                 cudaMemcpyDeviceToDevice, s));
+      }
+      if constexpr (sizeof(T) == 8) {
+        if (jd && nu > 0) {
+          double* hu = h.at<double>(1152);   // bytes [1152, 1216): theta of the corrected columns
+          for (int c = 0; c < nu; ++c) hu[c] = thv[unconv[c]];
+          CUCHK(cudaMemcpyAsync(thU, hu, sizeof(double) * nu, cudaMemcpyHostToDevice, s));
+          jd->solve(ctx, nu, Tb, XU, thU, Xl, nlock);
+        }
       }
       if (precond == PHSVDS_PREC_LEARNED && lp && nu > 0) {
         double* hu2 = h.at<double>(1088);    // bytes [1088, 1152): ||r||^2 of the corrected columns
@@ -991,7 +1078,6 @@ struct Orth1 {
   phsvds_ctx* ctx;
   cudaStream_t s;
   double *G1, *G2, *tn, *inn, *minv;
-  int* flag;
   uint64_t seed;
   int rand_ctr = 0;
   Orth1(phsvds_ctx* c, Pool& p, uint64_t sd) : ctx(c), s(c->stream), seed(sd) {
@@ -1000,7 +1086,6 @@ struct Orth1 {
     tn = p.get<double>(4);
     inn = p.get<double>(4);
     minv = p.get<double>(4);
-    flag = p.get<int>(4);
   }
   void run(int N, const Basis<double>& P, double* t, double* dst) {
     Host h(ctx);
@@ -1012,14 +1097,8 @@ struct Orth1 {
       zero(s, G2, p);
       zero(s, tn, 1);
       cgs_pass<double>(s, N, P, t, N, 1, nullptr, G1, nullptr);
-      if (p > 0) {  // the second pass only where the first lost more than 1/sqrt(2) of the norm
-        reorth_test(s, p, 1, G1, inn, flag);
-        cgs_pass<double>(s, N, P, t, N, 1, G1, nullptr, tn, flag, 0);
-        cgs_pass<double>(s, N, P, t, N, 1, G1, G2, nullptr, flag, 1);
-        cgs_pass<double>(s, N, P, t, N, 1, G2, nullptr, tn, flag, 1);
-      } else {
-        cgs_pass<double>(s, N, P, t, N, 1, nullptr, nullptr, tn);
-      }
+      cgs_pass<double>(s, N, P, t, N, 1, G1, G2, nullptr);
+      cgs_pass<double>(s, N, P, t, N, 1, G2, nullptr, tn);
       CUCHK(cudaMemcpyAsync(h.at<double>(0), tn, sizeof(double), cudaMemcpyDeviceToHost, s));
       CUCHK(cudaMemcpyAsync(h.at<double>(8), inn, sizeof(double), cudaMemcpyDeviceToHost, s));
       sync(s);
@@ -1465,6 +1544,7 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
   s1.rec_max = o.record_r ? o.record_max : 0;
   s1.rec_every = o.record_every;
   int64_t iters32 = 0, mv32 = 0, jac32[4] = {0, 0, 0, 0}, stag32 = 0;
+  std::unique_ptr<InnerJD> jd;
   double theta_max32 = 0.0;
   // on a stage-1 error the counters so far still reach the caller
   auto partial_stats = [&](const Stage1Out& a, const Stage1Out* b32) {
@@ -1520,6 +1600,10 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
     convert_f32_to_f64(s, (int64_t)A.n * k, s1f.Xl, X0);
     s1.out.restarts = s1f.out.restarts;
     s1.out.theta_max = s1f.out.theta_max;  // the ||C|| estimate carries over
+    if (o.mixed_inner == 1 && s1.precond == PHSVDS_PREC_NONE) {
+      jd = std::make_unique<InnerJD>(ctx, pool, A.n, k, op32, o.inner_maxit, o.inner_tol, !o.profile);
+      s1.jd = jd.get();
+    }
     try {
       s1.run(X0, k);
     } catch (const PhError&) {
@@ -1646,6 +1730,8 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
     st->fell_back_at = s1.out.fell_back_at;
     st->recorded = s1.out.recorded;
     st->stage1_stagnation_locks = s1.out.stag_locks + stag32;
+    st->inner_steps = jd ? jd->steps : 0;
+    st->inner_solves = jd ? jd->solves : 0;
     st->t_stage1_ms = std::chrono::duration<double, std::milli>(t1b - t1a).count();
     st->t_stage2_ms = t2ms;
     st->t_total_ms = std::chrono::duration<double, std::milli>(clk::now() - tstart).count();
@@ -1723,6 +1809,9 @@ phsvds_status phsvds_default_opts(phsvds_opts* o) {
   o->projected_solver = 2;
   o->init_V = nullptr;
   o->init_nv = 0;
+  o->mixed_inner = 1;
+  o->inner_maxit = 60;
+  o->inner_tol = 1e-3;
   return PHSVDS_OK;
 }
 
@@ -1812,6 +1901,8 @@ phsvds_status phsvds_solve(phsvds_handle h, int64_t m, int64_t n, int64_t nnz, c
     return set_err(h, PHSVDS_ERR_INVALID, "learned correction needs params, features and grid_nx * grid_ny = n");
   if (o.record_r && (o.record_max < 0 || o.record_every < 1))
     return set_err(h, PHSVDS_ERR_INVALID, "recording needs record_max >= 0 and record_every >= 1");
+  if ((o.mixed_inner != 0 && o.mixed_inner != 1) || o.inner_maxit < 1 || !(o.inner_tol > 0) || o.inner_tol >= 1)
+    return set_err(h, PHSVDS_ERR_INVALID, "mixed_inner must be 0 or 1, inner_maxit >= 1, 0 < inner_tol < 1");
   if (o.init_V && (o.init_nv < 0 || o.init_nv > o.max_basis || (o.init_nv == 0 && k > o.max_basis)))
     return set_err(h, PHSVDS_ERR_INVALID, "init_V needs 0 <= init_nv <= max_basis (0 = k columns)");
   try {

@@ -35,7 +35,7 @@ class Opts(C.Structure):
                 ("learned_params", C.c_void_p), ("learned_features", C.c_void_p), ("grid_nx", C.c_int),
                 ("grid_ny", C.c_int), ("stall_window", C.c_int), ("record_r", C.c_void_p), ("record_max", C.c_int),
                 ("record_every", C.c_int), ("projected_solver", C.c_int), ("init_V", C.c_void_p),
-                ("init_nv", C.c_int)]
+                ("init_nv", C.c_int), ("mixed_inner", C.c_int), ("inner_maxit", C.c_int), ("inner_tol", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -48,7 +48,8 @@ class Stats(C.Structure):
                 ("jacobi_sweeps", C.c_int64), ("jacobi_rotations", C.c_int64), ("jacobi_calls", C.c_int64),
                 ("jacobi_dim_sum", C.c_int64), ("fell_back", C.c_int), ("fell_back_at", C.c_int64),
                 ("recorded", C.c_int64), ("stage1_stagnation_locks", C.c_int64), ("spmm_plan_cached", C.c_int),
-                ("class_flops", C.c_double * 12), ("class_bytes", C.c_double * 12)]
+                ("class_flops", C.c_double * 12), ("class_bytes", C.c_double * 12), ("inner_solves", C.c_int64),
+                ("inner_steps", C.c_int64)]
 
     def as_dict(self) -> dict:
         d = {}

@@ -8,7 +8,8 @@ each result with the existing two-phase entry point (which takes a caller
 buffer) and with the CPU product A^T (A X) of the oracle's sparse operator,
 both within the rounding bound of the SpMM parity tests; they also check that
 oversized inputs and NULL arrays are refused before anything runs, and that
-the calls leave the device's free memory unchanged from before the first one.
+the calls take no device memory beyond the fixed array itself (which the
+driver may place at the process's first call).
 The file name keeps it last in collection, so it runs both after the other GPU
 tests and alone.  (The header constant is checked against the binding on the
 CPU, in test_abi.py.)
@@ -22,6 +23,7 @@ from tests.gpu_util import torch, need_gpu, dev, device_csr
 
 pytestmark = pytest.mark.gpu
 EPS64 = 2.0 ** -52
+STATIC_BYTES = 8 * native.STATIC_Z_MAX          # the fixed array: 2 MiB
 
 
 @pytest.fixture(scope="module")
@@ -70,7 +72,12 @@ def test_two_calls_in_a_row_match_existing_entry_point(h, case, b):
                                       Xd[t], Yd[t])
         native.phsvds_sync(h)
         free.append(torch.cuda.mem_get_info()[0])
-    assert free[1] == free[0] and free[2] == free[0]
+    # The first call of a process looks the fixed array up, and with lazy
+    # module loading that is when the driver places it: free memory may drop
+    # by the array itself (2 MiB) then, and by nothing more; later calls do
+    # not change it at all.
+    assert 0 <= free[0] - free[1] <= STATIC_BYTES, free
+    assert free[2] == free[1], free
     for t in range(2):
         Y = Yd[t].cpu().numpy()
         bound = _bound(A, d["scipy"], Xs[t]) + 1e-300
