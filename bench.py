@@ -50,13 +50,20 @@ def parse():
     p.add_argument("--precision", default="both", choices=["mixed", "fp64", "both"])
     p.add_argument("--precond", default="none", choices=["none", "jacobi"])
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-forms", action="store_true", help="skip the small runs of the preconditioned forms")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="bound of each oracle sample (CPU baseline)")
     p.add_argument("--ref-iters", type=int, default=0,
                    help="oracle outer iterations per reference-arm step (0: 4 for c3, 1000 for grid)")
     p.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--spmm-only", action="store_true", help="only the full-size fused A^T A SpMM timings")
-    p.add_argument("--spmm-cases", default="c2,c3", help="full-size SpMM workloads: c2 (512^2 grid), c3 (1e6 x 5e5)")
+    p.add_argument("--kernel", default="", choices=["", "cgs", "tall"],
+                   help="time one tall-skinny kernel at the 1e6 x 5e5 solve's shape: cgs = block Gram-Schmidt pass "
+                        "(55 basis columns against 8), tall = V Y (35 columns to 21)")
+    p.add_argument("--kernel-dtype", default="f64", choices=["f64", "f32"])
+    p.add_argument("--kernel-reps", type=int, default=10)
+    p.add_argument("--spmm-cases", default="c2,c3",
+                   help="full-size SpMM workloads: c2 (512^2 grid), c3 (1e6 x 5e5), or none")
     p.add_argument("--spmm-reps", type=int, default=10)
     p.add_argument("--spmm-sweep", action="store_true", help="time every group width around the automatic one")
     p.add_argument("--batched", action="store_true",
@@ -227,7 +234,7 @@ def spmm_full(a):
         return [x for x in (l0 // 2, l0, 2 * l0) if 1 <= x <= 16]
 
     with torch.cuda.stream(stream):
-        for key in [c for c in a.spmm_cases.split(",") if c]:
+        for key in [c for c in a.spmm_cases.split(",") if c and c != "none"]:
             name, gen, b = cases[key]
             A = gen()
             rp = torch.from_numpy(A.row_ptr.astype(np.int32)).cuda()
@@ -278,6 +285,155 @@ def spmm_full(a):
             del A
     h.close()
     return out
+
+
+def kernel_only(a):
+    """One tall-skinny kernel at the full-size solve's shape (n = 500,000),
+    through the kernel-level entry points, timed with CUDA events on the
+    library's stream over --kernel-reps launches after 3 warm-up launches; the
+    inputs (about 240 MB) exceed L2, and a 256 MiB buffer is written between
+    timed launches.  cgs: T <- T - P Gsub and Gout = P^T T, P = 55 columns (20
+    locked + 35 basis), T = 8 columns (the second pass of stage 1's CGS2);
+    tall: Out = V Y, V 35 columns, Y 35 x 21 (a thick restart)."""
+    import numpy as np
+    import torch
+    from paper_1408_5535_gb300 import native
+    n = 500000
+    dt = torch.float64 if a.kernel_dtype == "f64" else torch.float32
+    fp32 = a.kernel_dtype == "f32"
+    esz = 8 if not fp32 else 4
+    stream = torch.cuda.Stream()
+    h = native.Handle(0, stream.cuda_stream)
+    g = torch.Generator(device="cuda").manual_seed(1)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+    if a.kernel == "cgs":
+        p1, p2, q = 20, 35, 8
+        P = torch.rand((p1 + p2, n), dtype=dt, device="cuda", generator=g)
+        T = torch.rand((q, n), dtype=dt, device="cuda", generator=g)
+        Gs = torch.rand(((p1 + p2) * q,), dtype=torch.float64, device="cuda", generator=g) * 1e-6
+        Gout = torch.zeros(((p1 + p2) * q,), dtype=torch.float64, device="cuda")
+
+        def run():
+            native.phsvds_block_cgs(h, n, P[:p1], n, p1, T, n, q, Gsub=Gs, Gout=Gout, P2=P[p1:], ld2=n, p2=p2,
+                                    fp32=fp32)
+        p = p1 + p2
+        flops = 4.0 * n * p * q
+        byts = esz * n * (p + 2 * q)
+        shape = f"n={n}, p={p} ({p1} locked + {p2} basis), q={q}, Gsub and Gout"
+    else:
+        p, r = 35, 21
+        P = torch.rand((p, n), dtype=dt, device="cuda", generator=g)
+        Y = torch.rand((p * r,), dtype=torch.float64, device="cuda", generator=g)
+        O = torch.empty((r, n), dtype=dt, device="cuda")
+
+        def run():
+            native.phsvds_tall_small(h, n, P, n, p, Y, p, r, O, n, fp32=fp32)
+        flops = 2.0 * n * p * r
+        byts = esz * n * (p + r)
+        shape = f"n={n}, p={p}, r={r}"
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            run()
+        ts = []
+        for _ in range(a.kernel_reps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run()
+            e1.record(stream)
+            stream.synchronize()
+            ts.append(e0.elapsed_time(e1))
+    h.close()
+    hbm, kind = peaks()
+    ms = float(np.mean(ts))
+    out = {"kernel": a.kernel, "dtype": a.kernel_dtype, "shape": shape, "avg_launch_ms": ms,
+           "min_launch_ms": float(np.min(ts)), "alg_flops": flops, "alg_bytes": byts,
+           "TFLOPs": flops / ms / 1e9, "GBps": byts / ms / 1e6, "frac_fp64_peak": flops / ms / 1e9 / 1.25,
+           "frac_hbm": byts / ms / 1e6 / hbm, "hbm_peak": hbm, "hbm_peak_kind": kind}
+    return out
+
+
+def run_forms():
+    """Small measured runs of the forms of Sec. 4 (GPU solves through the C
+    ABI, CUDA events on the library's stream, median of 3, Table 1 once):
+    * the two-stage demonstration of Sec. 5.1 with the caller's M ~ A
+      (A = diag([1:10, 1000:100:1e6]), M = A + diag(1e4 rand), k = 1
+      smallest): stage 1 alone and both stages;
+    * the stage-2 preconditioner [0 A M; M A^T 0], M = diag(C)^{-1}, against
+      plain GD in stage 2, on a 300 x 150 random matrix with columns scaled
+      over two decades (k = 4 smallest, block 2, Jacobi in stage 1);
+    * the JDQMR correction of stage 2 against GD on the 32 x 32 weighted
+      grid, and on the paper's Table 1 (clustered tiny values, delta 1e-15)."""
+    import numpy as np
+    import scipy.sparse as sp
+    import torch
+    from paper_1408_5535_gb300 import native, synth
+    stream = torch.cuda.Stream()
+    h = native.Handle(0, stream.cuda_stream)
+
+    def timed(A, k, prec, o, **kw):
+        out = None
+        ts = []
+        for _ in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = native.phsvds_solve(h, A.m, A.n, A.row_ptr, A.col, A.val, k, native.SMALLEST, TOL, prec, o, **kw)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return out, float(np.median(ts))
+
+    res = {}
+    A, M = synth.e3_diag()
+    for name, o in (("stage1_only", native.default_opts(stage2=0)), ("two_stages", native.default_opts())):
+        (sig, U, V, rs, st, _), ms = timed(A, 1, native.PREC_GIVEN, o, precond_M=M)
+        res[f"e3_{name}"] = {"ms": ms, "sigma": float(sig[0]), "resid_over_normA": float(rs[0] / 1e6),
+                             "iters_stage1": st["iters_stage1"], "iters_stage2": st["iters_stage2"]}
+    A0 = synth.random_sparse(300, 150, 6.0, 21, values="gaussian", shift=0.05)
+    S = sp.csr_matrix((A0.val, A0.col, A0.row_ptr), shape=(A0.m, A0.n))
+    S = (S @ sp.diags(10.0 ** (-2.0 * synth.uniform(31, 1, 150)))).tocsr()
+    S.sort_indices()
+    B = synth.Csr(S.shape[0], S.shape[1], S.indptr.astype(np.int64), S.indices.astype(np.int32), S.data)
+    for sp2 in (0, 1):
+        (sig, U, V, rs, st, _), ms = timed(B, 4, native.PREC_JACOBI, native.default_opts(block_size=2,
+                                                                                       stage2_precond=sp2))
+        res[f"stage2_precond_{sp2}"] = {"ms": ms, "iters_stage1": st["iters_stage1"],
+                                        "iters_stage2": st["iters_stage2"],
+                                        "max_resid_over_normA": float(np.max(rs) / st["norm_A_est"])}
+    # JDQMR in stage 2 against GD in stage 2 (the weighted 32 x 32 grid, k = 10
+    # smallest, block 4), and the paper's Table 1 (delta = 1e-15, block 2)
+    G = synth.grid_gradient(32, 1.0, 2)
+    for inner in (0, 1):
+        (sig, U, V, rs, st, _), ms = timed(G, 10, native.PREC_NONE, native.default_opts(block_size=4,
+                                                                                         stage2_inner=inner))
+        res[f"grid32_stage2_{'jdqmr' if inner else 'gd'}"] = {
+            "ms": ms, "iters_stage1": st["iters_stage1"], "iters_stage2": st["iters_stage2"],
+            "inner_steps": st["inner2_steps"], "matvecs_A": st["matvecs_A"],
+            "max_resid_over_normA": float(np.max(rs) / st["norm_A_est"])}
+    T = synth.diag_matrix(synth.table1_sigma())
+    exact = np.sort(synth.table1_sigma())[:10]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sig, U, V, rs, st, status = native.phsvds_solve(h, T.m, T.n, T.row_ptr, T.col, T.val, 10, native.SMALLEST, 1e-15,
+                                                    native.PREC_NONE, native.default_opts(block_size=2,
+                                                                                          stage2_inner=1),
+                                                    raise_on_error=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    res["table1_jdqmr"] = {"ms": e0.elapsed_time(e1), "status": status, "sigma": sig.tolist(),
+                           "max_abs_err": float(np.max(np.abs(sig - exact))), "max_resid": float(np.max(rs)),
+                           "iters_stage1": st["iters_stage1"], "iters_stage2": st["iters_stage2"],
+                           "inner_steps": st["inner2_steps"]}
+    h.close()
+    res["workloads"] = ("e3: diag([1:10, 1000:100:1e6]) with M = A + diag(1e4 rand) (seed 9), k=1 smallest; "
+                        "stage2_precond: random_sparse(300, 150, 6, 21, gaussian, 0.05) with columns scaled "
+                        "by 10^(-2u), k=4 smallest, block 2, Jacobi in stage 1; grid32: weighted 32x32 grid "
+                        "gradient, k=10 smallest, block 4, GD vs JDQMR in stage 2; table1: diag(1e-14, 1e-12, "
+                        "1e-8:1e-8:4e-8, 1e-3:1e-3:1), k=10 smallest, delta 1e-15, block 2, JDQMR")
+    return res
 
 
 def golden(a):
@@ -504,13 +660,18 @@ CLASS_KERNELS = {0: "k_csr_rows / k_ata_fused <double>", 1: "k_cgs_pass<double>"
 # clean-up of the target pairs, with the device helpers they call
 JACOBI_FUNCS = ["rr_pair", "rot_params", "rot_params_small", "k_jacobi_eig", "k_jacobi_targets"]
 # the block Gram-Schmidt pass (its ncu capture: profiles/cgs_pass_f64_1e6x5e5.txt)
-CGS_FUNCS = ["reduce_scatter_step", "k_cgs_pass"]
+CGS_FUNCS = ["cp_async16", "cp_async_wait_all", "stage_cols", "lds_vec", "reduce_scatter_step", "k_cgs_pass"]
+# the row kernel of the two-phase SpMM (its capture: profiles/spmm_csr_rows_c3_f32.txt)
+SPMM_FUNCS = ["load_row_256", "l2_evict_first_policy", "ld_stream", "gather_rows", "load_slots", "k_csr_rows"]
+SPMM_FUSED_FUNCS = ["load_row_256", "l2_evict_first_policy", "ld_stream", "gather_rows", "load_slots",
+                    "k_ata_fused"]
 
 
 def kernel_source_sha256(kernel_file, names):
     """sha256 of the source text of the named functions of a .cu file (each
-    from the line that declares it to its closing brace in column 0), so that
-    edits elsewhere in the file do not invalidate a capture."""
+    from the line that declares it to its closing brace in column 0, every
+    overload), so that edits elsewhere in the file do not invalidate a
+    capture."""
     import hashlib
     try:
         lines = open(os.path.join(ROOT, "paper_1408_5535_gb300", "csrc", kernel_file)).read().splitlines()
@@ -521,12 +682,12 @@ def kernel_source_sha256(kernel_file, names):
         pat = re.compile(r"\b" + re.escape(name) + r"\(")
         starts = [i for i, l in enumerate(lines) if re.match(r"(__global__|__device__)\b", l)
                   and (pat.search(l) or (i + 1 < len(lines) and pat.search(lines[i + 1])))]
-        if len(starts) != 1:
+        if not starts:
             return None
-        i = starts[0]
-        while i < len(lines) and lines[i] != "}":
-            h.update(lines[i].encode() + b"\n")
-            i += 1
+        for i in starts:                  # every overload, in file order
+            while i < len(lines) and lines[i] != "}":
+                h.update(lines[i].encode() + b"\n")
+                i += 1
     return h.hexdigest()
 
 
@@ -584,10 +745,23 @@ def roofline_for(A, prof, dom, hbm, peak_kind):
     out = {"kernel": CLASS_KERNELS.get(dom, CLASS_NAMES[dom]), "avg_launch_ms": avg_ms, "launches": calls,
            "flops_per_launch": fl / calls if calls else None, "bytes_per_launch": by / calls if calls else None,
            "traffic": None}
-    if dom == 1:
-        out["traffic"] = measured_traffic("k_tall.cu", CGS_FUNCS, "cgs_pass_f64_1e6x5e5.txt", "dram_bytes_per_launch")
+    if dom in (1, 7):
+        out["traffic"] = measured_traffic("k_tall.cu", CGS_FUNCS, "cgs_pass_%s_1e6x5e5.txt" % ("f64" if dom == 1 else "f32"),
+                                          "dram_bytes_per_launch")
         if out["traffic"] is not None:
-            out["traffic_launch"] = "the captured launch: n = 500,000, p = 55 basis columns, q = 8 (profiles/)"
+            out["traffic_launch"] = ("the captured launch: n = 500,000, p = 55 basis columns, q = 8, "
+                                     "Gsub and Gout (profiles/)")
+    if dom == 6:
+        if prof.get("spmm_schedule_f32") == 2:
+            out["traffic"] = measured_traffic("k_sparse.cu", SPMM_FUNCS, "spmm_csr_rows_c3_f32.txt",
+                                              "dram_bytes_per_launch")
+            label = "both phases of the two-phase schedule at b = 8"
+        else:
+            out["traffic"] = measured_traffic("k_sparse.cu", SPMM_FUSED_FUNCS, "spmm_ata_fused_c3_f32.txt",
+                                              "dram_bytes_per_launch")
+            label = "the fused single-pass schedule at b = 8"
+        if out["traffic"] is not None:
+            out["traffic_launch"] = f"the captured product: {label} (profiles/)"
     if dom < 6:
         ach = fl / (t_ms * 1e-3) / 1e12 if t_ms else None
         out.update(bound="alu", achieved=ach, peak=FP64_PEAK_GFLOPS / 1e3, unit="TFLOP/s",
@@ -728,6 +902,10 @@ def main():
         if rank == 0:
             print(json.dumps({"batched": run_batched(a)}), flush=True)
         return
+    if a.kernel:
+        if rank == 0:
+            print(json.dumps({"kernel_only": kernel_only(a)}), flush=True)
+        return
     if a.spmm_only:
         r = spmm_full(a)
         if rank == 0:
@@ -794,7 +972,7 @@ def main():
                         "max_sigma_rel_diff_vs_mixed": max(abs(x - y) / y for x, y in zip(r["sigma"], f["sigma"])),
                         "class_ms": {CLASS_NAMES[i]: v for i, v in enumerate(f["prof"]["t_class_ms"]) if v > 0},
                         "e2e": f["e2e"]}
-    if a.spmm_cases:
+    if a.spmm_cases and a.spmm_cases != "none":
         sp = spmm_full(a)
         line["spmm"] = sp
         best = max((x for x in sp if x["case"] == "c3" and x["dtype"] == "f32"), key=lambda x: x["GBps"], default=None)
@@ -805,6 +983,8 @@ def main():
                                      "workload": best["workload"], "achieved": best["GBps"], "peak": hbm,
                                      "unit": "GB/s", "frac": best["GBps"] / hbm, "traffic": None,
                                      "bytes_per_launch": best["alg_bytes"], "avg_launch_ms": best["avg_launch_ms"]}
+    if rank == 0 and not a.no_forms:
+        line["forms"] = run_forms()
     if rank == 0 and not a.no_cpu:
         line["cpu_baseline"] = cpu_baseline(a, cfg["k"], st["iters_stage1"] + st["iters_stage2"])
     if rank == 0:

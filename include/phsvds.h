@@ -19,7 +19,9 @@
  *    Pointers are host pointers unless the argument says "device" or the
  *    call's ptr_on_device flag is 1.
  *  - The library owns its device copies and workspaces; they live until
- *    phsvds_destroy (or until the next solve on the same handle).
+ *    phsvds_destroy (or until the next solve on the same handle).  The device
+ *    memory they took stays reserved in the handle's own memory pool until
+ *    phsvds_destroy, so that repeated solves do not map it again.
  *  - Errors: every call returns a phsvds_status.  On error nothing is written to
  *    the output arrays except what the status documents; phsvds_last_error()
  *    returns a one-line description of the last failure on this handle.
@@ -54,8 +56,12 @@ typedef enum { PHSVDS_SMALLEST = 0, PHSVDS_LARGEST = 1 } phsvds_target;
  * applied in the Olsen form t = M r - e M x, e = x^T M r / x^T M x, or the
  * learned correction network (no counterpart in the paper: a 3-layer 3x3
  * convolution network on the grid of a grid-structured operator, mapping
- * [r / ||r|| * sqrt(n), feature channels] to the correction t; opts.learned_*). */
-typedef enum { PHSVDS_PREC_NONE = 0, PHSVDS_PREC_JACOBI = 1, PHSVDS_PREC_LEARNED = 2 } phsvds_precond;
+ * [r / ||r|| * sqrt(n), feature channels] to the correction t; opts.learned_*),
+ * or a preconditioner M ~ A given by the caller (Sec. 4, square A, M diagonal:
+ * opts.precond_M): M^{-1} M^{-T} for C in stage 1 and [0 M^{-1}; M^{-T} 0]
+ * for B in stage 2, both in the Olsen form. */
+typedef enum { PHSVDS_PREC_NONE = 0, PHSVDS_PREC_JACOBI = 1, PHSVDS_PREC_LEARNED = 2,
+               PHSVDS_PREC_GIVEN = 3 } phsvds_precond;
 
 /* Parameters of the learned correction network: 3024 BF16 values, layer-major
  * (16x4x3x3, 16x16x3x3, 1x16x3x3), each [out][in][row][col]. */
@@ -76,8 +82,9 @@ typedef enum { PHSVDS_SPMM_AUTO = 0, PHSVDS_SPMM_FUSED_ATOMIC = 1, PHSVDS_SPMM_T
 
 typedef struct {
     int block_size;        /* stage-1 block size b (1..8), default 1 */
-    int max_basis;         /* maxBasisSize, default 35 (Section 5) */
-    int min_restart;       /* minRestartSize, default 21 (Section 5) */
+    int max_basis;         /* maxBasisSize, default 35 (Section 5); max_basis + 8 <= 64 */
+    int min_restart;       /* minRestartSize, default 21 (Section 5); 2 b <= min_restart and
+                              min_restart + b <= max_basis, b = min(block_size, k) */
     int max_restarts;      /* per stage, default 10000 (Section 5) */
     double eps_factor;     /* delta_C floor = eps_factor * eps (O(||C|| eps), Sec. 3.1), default 4 */
     phsvds_precision precision;
@@ -133,6 +140,32 @@ typedef struct {
     int mixed_inner;
     int inner_maxit;
     double inner_tol;
+    /* 1: stage 2 of a SMALLEST solve corrects with the preconditioner that
+     * Sec. 4 builds for B from a preconditioner M ~ C^{-1} of stage 1,
+     * [0 A M; M A^T 0], here with M = diag(C)^{-1} (the unshifted Jacobi
+     * preconditioner of C), in the Olsen form t = P r - e P x,
+     * e = x^T P r / x^T P x (two products with A and two with A^T per
+     * iteration); 0 (default): t = r. */
+    int stage2_precond;
+    /* PHSVDS_PREC_GIVEN: host pointer to the n diagonal entries of M ~ A
+     * (square A, m = n; every entry finite and nonzero), copied at the start
+     * of the solve. */
+    const double* precond_M;
+    /* the correction of stage 2: 0 (default) t = r (GD, the PHSVDS(GD+k)
+     * variant); 1 = the JDQMR form (Sec. 4): t an inexact solution of
+     * (I - QQ^T)(B - theta1 I)(I - QQ^T) t = -r, Q = [locked vectors, x], by
+     * MINRES in FP64; after each inner step z = x + t is scored by its
+     * eigen-residual ||B z - rho(z) z|| / ||z|| (B t carried by the
+     * recurrence, no extra products), the steps stop once that falls below
+     * tol ||A|| / sqrt(2), or after inner2_patience steps (default 25) without
+     * a 10% gain, or at inner2_maxit (default 300), and the best iterate is
+     * used.  With 1 the targets stage 1 resolved are taken first and the tiny
+     * ones (sigma~ <= sqrt(eps) ||A||) last, and locking a tiny pair also
+     * deflates its mirror [v; -u].  Not with stage2_precond or a given
+     * preconditioner. */
+    int stage2_inner;
+    int inner2_maxit;
+    int inner2_patience;
 } phsvds_opts;
 
 typedef struct {
@@ -178,6 +211,9 @@ typedef struct {
     double class_bytes[12];
     int64_t inner_solves;      /* Jacobi-Davidson corrections (opts.mixed_inner = 1): block inner solves */
     int64_t inner_steps;       /* ... and their MINRES steps (each one FP32 product with C of the block) */
+    int64_t inner2_solves;     /* JDQMR corrections of stage 2 (opts.stage2_inner = 1) */
+    int64_t inner2_steps;      /* ... and their MINRES steps (each one product with B) */
+    int spmm_schedule_f32;     /* schedule of the FP32 products with C (mixed precision; 0 otherwise) */
 } phsvds_stats;
 
 /* Create a context on CUDA device `device`.  cuda_stream: a cudaStream_t to run

@@ -23,6 +23,25 @@ namespace ph {
 
 constexpr int JD_T = 256;
 
+// V consecutive rows per thread: V = 4 (16-byte loads) when n is a multiple of
+// 4, so that every column of a column-major block starts 16-byte aligned.
+template <int V>
+__device__ inline void ldv(const float* __restrict__ p, float (&r)[V]) {
+  if constexpr (V == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    r[0] = t.x; r[1] = t.y; r[2] = t.z; r[3] = t.w;
+  } else {
+    r[0] = *p;
+  }
+}
+template <int V>
+__device__ inline void stv(float* __restrict__ p, const float (&r)[V]) {
+  if constexpr (V == 4)
+    *reinterpret_cast<float4*>(p) = make_float4(r[0], r[1], r[2], r[3]);
+  else
+    *p = r[0];
+}
+
 // ---- column reductions: acc[8 p + c] += sum_i a_p[c n + i] * b_p[c n + i] for
 // the q columns of each of the NP pairs (a_p, b_p)
 template <int NP>
@@ -31,7 +50,7 @@ struct DotPairs {
   const float* b[NP];
 };
 
-template <int NP>
+template <int NP, int V>
 __global__ void __launch_bounds__(JD_T) k_col_dots(int n, int q, DotPairs<NP> pr, double* __restrict__ acc) {
   __shared__ double red[NP * 8][JD_T / 32];
   float s[NP][8];
@@ -39,14 +58,18 @@ __global__ void __launch_bounds__(JD_T) k_col_dots(int n, int q, DotPairs<NP> pr
   for (int p = 0; p < NP; ++p)
 #pragma unroll
     for (int c = 0; c < 8; ++c) s[p][c] = 0.f;
-  for (int i = blockIdx.x * JD_T + threadIdx.x; i < n; i += gridDim.x * JD_T) {
+  for (int i = (blockIdx.x * JD_T + threadIdx.x) * V; i < n; i += gridDim.x * JD_T * V) {
 #pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      const float* a = pr.a[p];
-      const float* b = pr.b[p];
+    for (int c = 0; c < 8; ++c) {
+      if (c >= q) break;
 #pragma unroll
-      for (int c = 0; c < 8; ++c)
-        if (c < q) s[p][c] = fmaf(a[(size_t)c * n + i], b[(size_t)c * n + i], s[p][c]);
+      for (int p = 0; p < NP; ++p) {
+        float a[V], b[V];
+        ldv<V>(pr.a[p] + (size_t)c * n + i, a);
+        ldv<V>(pr.b[p] + (size_t)c * n + i, b);
+#pragma unroll
+        for (int u = 0; u < V; ++u) s[p][c] = fmaf(a[u], b[u], s[p][c]);
+      }
     }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -79,7 +102,7 @@ enum JdField {
 // [16,24) x^T C v, [24,32) ||y||^2, [32, 32 + 8 nl) the projections Xl^T C v
 // (nl x b, column-major with leading dimension nl).
 
-__global__ void k_jd_init(int q, const double* __restrict__ acc, double tol, double* __restrict__ sc) {
+__global__ void k_jd_init(int q, const double* __restrict__ acc, double* __restrict__ sc) {
   const int c = threadIdx.x;
   if (c >= 8) return;
   const double b1 = c < q ? sqrt(fmax(acc[24 + c], 0.0)) : 0.0;
@@ -100,24 +123,33 @@ __global__ void k_jd_init(int q, const double* __restrict__ acc, double tol, dou
   SC(JF_C2, c) = 0.0;
   SC(JF_ACT, c) = (c < q && b1 > 0.0 && isfinite(b1)) ? 1.0 : 0.0;
   SC(JF_STEP, c) = 0.0;
-  (void)tol;
 }
 
 // r1 = r2 = R, v = R / beta1, s = w1 = w2 = 0
-__global__ void k_jd_start(int n, int q, const float* __restrict__ R, float* __restrict__ r1, float* __restrict__ r2,
-                           float* __restrict__ v, float* __restrict__ s, float* __restrict__ w1,
-                           float* __restrict__ w2, const double* __restrict__ sc) {
-  for (int i = blockIdx.x * JD_T + threadIdx.x; i < n; i += gridDim.x * JD_T) {
+template <int V>
+__global__ void __launch_bounds__(JD_T) k_jd_start(int n, int q, const float* __restrict__ R, float* __restrict__ r1,
+                                                   float* __restrict__ r2, float* __restrict__ v,
+                                                   float* __restrict__ s, float* __restrict__ w1,
+                                                   float* __restrict__ w2, const double* __restrict__ sc) {
+  __shared__ float sv[8];
+  if (threadIdx.x < 8) {
+    const int c = threadIdx.x;
+    sv[c] = (c < q && SC(JF_ACT, c) > 0.0) ? (float)(1.0 / SC(JF_BETA1, c)) : 0.f;
+  }
+  __syncthreads();
+  for (int i = (blockIdx.x * JD_T + threadIdx.x) * V; i < n; i += gridDim.x * JD_T * V) {
     for (int c = 0; c < q; ++c) {
       const size_t k = (size_t)c * n + i;
-      const float r = R[k];
-      const double b1 = SC(JF_BETA1, c);
-      r1[k] = r;
-      r2[k] = r;
-      v[k] = SC(JF_ACT, c) > 0.0 ? (float)((double)r / b1) : 0.f;
-      s[k] = 0.f;
-      w1[k] = 0.f;
-      w2[k] = 0.f;
+      float r[V], z[V], vv[V];
+      ldv<V>(R + k, r);
+#pragma unroll
+      for (int u = 0; u < V; ++u) z[u] = 0.f, vv[u] = r[u] * sv[c];
+      stv<V>(r1 + k, r);
+      stv<V>(r2 + k, r);
+      stv<V>(v + k, vv);
+      stv<V>(s + k, z);
+      stv<V>(w1 + k, z);
+      stv<V>(w2 + k, z);
     }
   }
 }
@@ -137,15 +169,16 @@ __global__ void k_jd_coef(int q, const double* __restrict__ acc, const double* _
 
 // y = C v - theta v - Xl (Xl^T C v) - x (x^T C v) - c1 r1 - c2 r2 (the projected,
 // shifted operator and the Lanczos recurrence); then r1 <- r2, r2 <- y, and
-// acc[24 + c] += ||y||^2.  Columns already converged are left alone.
-template <int NL>
+// acc[24 + c] += ||y||^2.  Columns already converged are left alone.  Each
+// locked vector is loaded once per row group and applied to all columns.
+template <int V>
 __global__ void __launch_bounds__(JD_T) k_jd_lanczos(int n, int q, int nl, const float* __restrict__ Cv,
                                                      const float* __restrict__ v, const float* __restrict__ X,
                                                      const float* __restrict__ Xl, const double* __restrict__ theta,
                                                      float* __restrict__ r1, float* __restrict__ r2,
                                                      const double* __restrict__ sc, double* __restrict__ acc) {
   __shared__ float cf[8][4];           // theta, e, c1, c2 per column
-  __shared__ float D[NL > 0 ? NL * 8 : 1];
+  __shared__ float D[64 * 8];
   __shared__ double red[8][JD_T / 32];
   __shared__ int act[8];
   if (threadIdx.x < 8) {
@@ -159,31 +192,53 @@ __global__ void __launch_bounds__(JD_T) k_jd_lanczos(int n, int q, int nl, const
   }
   for (int k = threadIdx.x; k < nl * 8; k += JD_T) {
     const int l = k % nl, c = k / nl;
-    D[k] = (c < q && SC(JF_ACT, c) > 0.0) ? (float)acc[32 + l + c * nl] : 0.f;
+    D[l * 8 + c] = (c < q && SC(JF_ACT, c) > 0.0) ? (float)acc[32 + l + c * nl] : 0.f;
   }
   __syncthreads();
   float nrm[8];
 #pragma unroll
   for (int c = 0; c < 8; ++c) nrm[c] = 0.f;
-  for (int i = blockIdx.x * JD_T + threadIdx.x; i < n; i += gridDim.x * JD_T) {
-    float xl[NL > 0 ? NL : 1];
-#pragma unroll
-    for (int l = 0; l < NL; ++l) xl[l] = l < nl ? Xl[(size_t)l * n + i] : 0.f;
+  for (int i = (blockIdx.x * JD_T + threadIdx.x) * V; i < n; i += gridDim.x * JD_T * V) {
+    float y[8][V];
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-      if (c >= q || !act[c]) continue;
-      const size_t k = (size_t)c * n + i;
-      float y = fmaf(-cf[c][0], v[k], Cv[k]);
-      y = fmaf(-cf[c][1], X[k], y);
+      if (c < q) {
+        const size_t k = (size_t)c * n + i;
+        float a[V], b[V], d[V];
+        ldv<V>(Cv + k, a);
+        ldv<V>(v + k, b);
+        ldv<V>(X + k, d);
 #pragma unroll
-      for (int l = 0; l < NL; ++l)
-        if (l < nl) y = fmaf(-D[l + c * nl], xl[l], y);
-      const float a2 = r2[k];
-      y = fmaf(-cf[c][2], r1[k], y);
-      y = fmaf(-cf[c][3], a2, y);
-      r1[k] = a2;
-      r2[k] = y;
-      nrm[c] = fmaf(y, y, nrm[c]);
+        for (int u = 0; u < V; ++u) y[c][u] = fmaf(-cf[c][1], d[u], fmaf(-cf[c][0], b[u], a[u]));
+      }
+    }
+    for (int l = 0; l < nl; ++l) {
+      float xl[V];
+      ldv<V>(Xl + (size_t)l * n + i, xl);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        if (c < q) {
+          const float dlc = D[l * 8 + c];
+#pragma unroll
+          for (int u = 0; u < V; ++u) y[c][u] = fmaf(-dlc, xl[u], y[c][u]);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      if (c < q && act[c]) {
+        const size_t k = (size_t)c * n + i;
+        float a1[V], a2[V];
+        ldv<V>(r1 + k, a1);
+        ldv<V>(r2 + k, a2);
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+          y[c][u] = fmaf(-cf[c][3], a2[u], fmaf(-cf[c][2], a1[u], y[c][u]));
+          nrm[c] = fmaf(y[c][u], y[c][u], nrm[c]);
+        }
+        stv<V>(r1 + k, a2);
+        stv<V>(r2 + k, y[c]);
+      }
     }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -242,6 +297,7 @@ __global__ void k_jd_givens(int q, const double* __restrict__ acc, double tol, d
 
 // w = (v - oldeps w1 - delta w2) / gamma;  w1 <- w2;  w2 <- w;  s += phi w;
 // v <- r2 / beta for the next step.
+template <int V>
 __global__ void __launch_bounds__(JD_T) k_jd_update(int n, int q, float* __restrict__ v, const float* __restrict__ r2,
                                                     float* __restrict__ w1, float* __restrict__ w2,
                                                     float* __restrict__ s, double* __restrict__ sc) {
@@ -259,17 +315,27 @@ __global__ void __launch_bounds__(JD_T) k_jd_update(int n, int q, float* __restr
     cf[c][4] = (act > 0.0 && beta > 0.0) ? (float)(1.0 / beta) : 0.f;
   }
   __syncthreads();
-  for (int i = blockIdx.x * JD_T + threadIdx.x; i < n; i += gridDim.x * JD_T) {
+  for (int i = (blockIdx.x * JD_T + threadIdx.x) * V; i < n; i += gridDim.x * JD_T * V) {
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       if (c >= q || !on[c]) continue;
       const size_t k = (size_t)c * n + i;
-      const float a1 = w1[k], a2 = w2[k];
-      const float w = (v[k] - cf[c][0] * a1 - cf[c][1] * a2) * cf[c][2];
-      w1[k] = a2;
-      w2[k] = w;
-      s[k] = fmaf(cf[c][3], w, s[k]);
-      v[k] = r2[k] * cf[c][4];
+      float a1[V], a2[V], vv[V], ss[V], rr[V], w[V];
+      ldv<V>(w1 + k, a1);
+      ldv<V>(w2 + k, a2);
+      ldv<V>(v + k, vv);
+      ldv<V>(s + k, ss);
+      ldv<V>(r2 + k, rr);
+#pragma unroll
+      for (int u = 0; u < V; ++u) {
+        w[u] = (vv[u] - cf[c][0] * a1[u] - cf[c][1] * a2[u]) * cf[c][2];
+        ss[u] = fmaf(cf[c][3], w[u], ss[u]);
+        vv[u] = rr[u] * cf[c][4];
+      }
+      stv<V>(w1 + k, a2);
+      stv<V>(w2 + k, w);
+      stv<V>(s + k, ss);
+      stv<V>(v + k, vv);
     }
   }
 }
@@ -281,28 +347,42 @@ __global__ void k_jd_retire(int q, double* __restrict__ sc) {
 }
 #undef SC
 
-static int jd_grid(int n) {
-  int blocks = ceil_div(n, JD_T);
+static int jd_grid(int n, int V) {
+  int blocks = ceil_div(ceil_div(n, V), JD_T);
   return blocks > 152 * 8 ? 152 * 8 : (blocks < 1 ? 1 : blocks);
 }
+static int jd_vec(int n) { return n % 4 == 0 ? 4 : 1; }
 
 void jd_colnorms(cudaStream_t s, int n, int q, const float* R, double* acc) {
   ProfScope ps(s, PROF_F32 + PROF_SMALL);
   DotPairs<1> pr{{R}, {R}};
-  k_col_dots<1><<<jd_grid(n), JD_T, 0, s>>>(n, q, pr, acc + 24); count_launch();
+  const int V = jd_vec(n);
+  if (V == 4)
+    k_col_dots<1, 4><<<jd_grid(n, 4), JD_T, 0, s>>>(n, q, pr, acc + 24);
+  else
+    k_col_dots<1, 1><<<jd_grid(n, 1), JD_T, 0, s>>>(n, q, pr, acc + 24);
+  count_launch();
 }
 
 void jd_init(cudaStream_t s, int n, int q, const float* R, float* r1, float* r2, float* v, float* sol, float* w1,
              float* w2, const double* acc, double* sc) {
   ProfScope ps(s, PROF_F32 + PROF_SMALL);
-  k_jd_init<<<1, 32, 0, s>>>(q, acc, 0.0, sc); count_launch();
-  k_jd_start<<<jd_grid(n), JD_T, 0, s>>>(n, q, R, r1, r2, v, sol, w1, w2, sc); count_launch();
+  k_jd_init<<<1, 32, 0, s>>>(q, acc, sc); count_launch();
+  if (jd_vec(n) == 4)
+    k_jd_start<4><<<jd_grid(n, 4), JD_T, 0, s>>>(n, q, R, r1, r2, v, sol, w1, w2, sc);
+  else
+    k_jd_start<1><<<jd_grid(n, 1), JD_T, 0, s>>>(n, q, R, r1, r2, v, sol, w1, w2, sc);
+  count_launch();
 }
 
 void jd_dots(cudaStream_t s, int n, int q, const float* v, const float* X, const float* Cv, double* acc) {
   ProfScope ps(s, PROF_F32 + PROF_SMALL);
   DotPairs<3> pr{{v, v, X}, {Cv, v, Cv}};
-  k_col_dots<3><<<jd_grid(n), JD_T, 0, s>>>(n, q, pr, acc); count_launch();
+  if (jd_vec(n) == 4)
+    k_col_dots<3, 4><<<jd_grid(n, 4), JD_T, 0, s>>>(n, q, pr, acc);
+  else
+    k_col_dots<3, 1><<<jd_grid(n, 1), JD_T, 0, s>>>(n, q, pr, acc);
+  count_launch();
   count_work(PROF_F32 + PROF_SMALL, 6.0 * n * q, 4.0 * 3 * n * q);
 }
 
@@ -311,24 +391,224 @@ void jd_step(cudaStream_t s, int n, int q, int nl, const float* Cv, float* v, co
              double tol) {
   ProfScope ps(s, PROF_F32 + PROF_SMALL);
   k_jd_coef<<<1, 32, 0, s>>>(q, acc, theta, sc); count_launch();
-  const int g = jd_grid(n);
-  if (nl == 0)
-    k_jd_lanczos<0><<<g, JD_T, 0, s>>>(n, q, nl, Cv, v, X, Xl, theta, r1, r2, sc, acc);
-  else if (nl <= 8)
-    k_jd_lanczos<8><<<g, JD_T, 0, s>>>(n, q, nl, Cv, v, X, Xl, theta, r1, r2, sc, acc);
-  else if (nl <= 16)
-    k_jd_lanczos<16><<<g, JD_T, 0, s>>>(n, q, nl, Cv, v, X, Xl, theta, r1, r2, sc, acc);
-  else if (nl <= 32)
-    k_jd_lanczos<32><<<g, JD_T, 0, s>>>(n, q, nl, Cv, v, X, Xl, theta, r1, r2, sc, acc);
+  const int V = jd_vec(n);
+  const int g = jd_grid(n, V);
+  if (V == 4)
+    k_jd_lanczos<4><<<g, JD_T, 0, s>>>(n, q, nl, Cv, v, X, Xl, theta, r1, r2, sc, acc);
   else
-    k_jd_lanczos<64><<<g, JD_T, 0, s>>>(n, q, nl, Cv, v, X, Xl, theta, r1, r2, sc, acc);
+    k_jd_lanczos<1><<<g, JD_T, 0, s>>>(n, q, nl, Cv, v, X, Xl, theta, r1, r2, sc, acc);
   count_launch();
   k_jd_givens<<<1, 32, 0, s>>>(q, acc, tol, sc); count_launch();
-  k_jd_update<<<g, JD_T, 0, s>>>(n, q, v, r2, w1, w2, sol, sc); count_launch();
+  if (V == 4)
+    k_jd_update<4><<<g, JD_T, 0, s>>>(n, q, v, r2, w1, w2, sol, sc);
+  else
+    k_jd_update<1><<<g, JD_T, 0, s>>>(n, q, v, r2, w1, w2, sol, sc);
+  count_launch();
   k_jd_retire<<<1, 32, 0, s>>>(q, sc); count_launch();
   // the Lanczos pass reads Cv, v, x, r1, r2, Xl and writes r1, r2; the update
   // reads v, r2, w1, w2, s and writes w1, w2, s, v
   count_work(PROF_F32 + PROF_SMALL, (2.0 * nl + 14.0) * n * q, 4.0 * n * ((16.0 * q) + nl));
+}
+
+// ===========================================================================
+// Stage 2 (Algorithm 2 with the JDQMR correction of Sec. 4): one correction
+// equation (I - QQ^T)(B - mu I)(I - QQ^T) t = -(I - QQ^T) r at a time, FP64,
+// Q = [locked vectors, their mirrors, x] (column-major N x nq).  MINRES as
+// above (the scalar kernels are shared, with q = 1), plus the dynamic stop:
+// after each step the updated vector z = x + t_k is scored by its
+// eigen-residual eta_k = ||B z - rho z|| / ||z||, rho = z^T B z / z^T z, with
+// B t_k carried by the same recurrence as t_k from the products the steps
+// make (no extra product); the steps stop once eta_k < tol, once eta has not
+// fallen below 0.9 of its best for `patience` steps, or at maxit, and the
+// iterate with the smallest eta is kept.
+// sc fields past the MINRES ones (index JF_NF * 8 + ...):
+enum Jd2Field { J2_BEST = 0, J2_PREV_BEST, J2_SINCE, J2_COPY, J2_ETA, J2_STEPS, J2_NF };
+#define S2(f) sc[JF_NF * 8 + (f)]
+#define SC1(f) sc[(f) * 8]
+
+// y = Bv - mu v - Q g - c1 r1 - c2 r2 (g = acc[32 ..] = Q^T Bv); r1 <- r2;
+// r2 <- y; acc[24] += ||y||^2
+__global__ void __launch_bounds__(JD_T) k_s2_lanczos(int64_t N, int nq, const double* __restrict__ Bv,
+                                                     const double* __restrict__ v, const double* __restrict__ Q,
+                                                     const double* __restrict__ mu, double* __restrict__ r1,
+                                                     double* __restrict__ r2, const double* __restrict__ sc,
+                                                     double* __restrict__ acc) {
+  __shared__ double g[65];
+  __shared__ double red[JD_T / 32];
+  if (SC1(JF_ACT) <= 0.0) return;
+  for (int l = threadIdx.x; l < nq; l += JD_T) g[l] = acc[32 + l];
+  __syncthreads();
+  const double m = mu[0], c1 = SC1(JF_C1), c2 = SC1(JF_C2);
+  double nrm = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)JD_T + threadIdx.x; i < N; i += (int64_t)gridDim.x * JD_T) {
+    double y = fma(-m, v[i], Bv[i]);
+    for (int l = 0; l < nq; ++l) y = fma(-g[l], Q[(size_t)l * N + i], y);
+    const double a2 = r2[i];
+    y = fma(-c2, a2, fma(-c1, r1[i], y));
+    r1[i] = a2;
+    r2[i] = y;
+    nrm = fma(y, y, nrm);
+  }
+  nrm = warp_sum(nrm);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = nrm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < JD_T / 32; ++w) t += red[w];
+    atomicAdd(&acc[24], t);
+  }
+}
+
+// MINRES update of t and, by the same recurrence, of B t; v <- r2 / beta; then
+// acc[160] += ||z||^2 and acc[161] += z^T B z for z = x + t, B z = Bx + Bt
+__global__ void __launch_bounds__(JD_T) k_s2_update(int64_t N, double* __restrict__ v, const double* __restrict__ r2,
+                                                    double* __restrict__ w1, double* __restrict__ w2,
+                                                    double* __restrict__ t, const double* __restrict__ Bv,
+                                                    double* __restrict__ Bw1, double* __restrict__ Bw2,
+                                                    double* __restrict__ Bt, const double* __restrict__ x,
+                                                    const double* __restrict__ Bx, const double* __restrict__ sc,
+                                                    double* __restrict__ acc) {
+  __shared__ double red[2][JD_T / 32];
+  const double act = SC1(JF_ACT);
+  if (act == 0.0) return;
+  const double oldeps = SC1(JF_OLDEPS), delta = SC1(JF_DELTA), ig = 1.0 / SC1(JF_GAMMA), phi = SC1(JF_PHI);
+  const double beta = SC1(JF_BETA);
+  const double ib = (act > 0.0 && beta > 0.0) ? 1.0 / beta : 0.0;
+  double zz = 0.0, zb = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)JD_T + threadIdx.x; i < N; i += (int64_t)gridDim.x * JD_T) {
+    const double a1 = w1[i], a2 = w2[i];
+    const double w = (v[i] - oldeps * a1 - delta * a2) * ig;
+    w1[i] = a2;
+    w2[i] = w;
+    const double tn = fma(phi, w, t[i]);
+    t[i] = tn;
+    const double b1 = Bw1[i], b2 = Bw2[i];
+    const double bw = (Bv[i] - oldeps * b1 - delta * b2) * ig;
+    Bw1[i] = b2;
+    Bw2[i] = bw;
+    const double btn = fma(phi, bw, Bt[i]);
+    Bt[i] = btn;
+    v[i] = r2[i] * ib;
+    const double z = x[i] + tn, bz = Bx[i] + btn;
+    zz = fma(z, z, zz);
+    zb = fma(z, bz, zb);
+  }
+  zz = warp_sum(zz);
+  zb = warp_sum(zb);
+  if ((threadIdx.x & 31) == 0) red[0][threadIdx.x >> 5] = zz, red[1][threadIdx.x >> 5] = zb;
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double u = 0.0;
+    for (int w = 0; w < JD_T / 32; ++w) u += red[threadIdx.x][w];
+    atomicAdd(&acc[160 + threadIdx.x], u);
+  }
+}
+
+// acc[162] += ||B z - rho z||^2, rho = acc[161] / acc[160] (a second pass: the
+// short form ||Bz||^2 - rho^2 ||z||^2 would cancel far above the tolerance)
+__global__ void __launch_bounds__(JD_T) k_s2_eta(int64_t N, const double* __restrict__ x, const double* __restrict__ t,
+                                                 const double* __restrict__ Bx, const double* __restrict__ Bt,
+                                                 const double* __restrict__ sc, double* __restrict__ acc) {
+  __shared__ double red[JD_T / 32];
+  if (SC1(JF_ACT) == 0.0) return;
+  const double rho = acc[160] > 0.0 ? acc[161] / acc[160] : 0.0;
+  double e = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)JD_T + threadIdx.x; i < N; i += (int64_t)gridDim.x * JD_T) {
+    const double d = (Bx[i] + Bt[i]) - rho * (x[i] + t[i]);
+    e = fma(d, d, e);
+  }
+  e = warp_sum(e);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double u = 0.0;
+    for (int w = 0; w < JD_T / 32; ++w) u += red[w];
+    atomicAdd(&acc[162], u);
+  }
+}
+
+// The dynamic stop: best eta, the patience counter, the copy flag of this
+// step's iterate; the system stops (act -1, retired after the copy) once
+// best < tol, or patience steps pass without a 10% gain, or at maxit.
+__global__ void k_s2_track(const double* __restrict__ acc, double tol, int patience, int maxit,
+                           double* __restrict__ sc) {
+  if (threadIdx.x != 0) return;
+  S2(J2_COPY) = 0.0;
+  const double act = SC1(JF_ACT);
+  if (act == 0.0) return;
+  const double eta = acc[160] > 0.0 ? sqrt(fmax(acc[162], 0.0) / acc[160]) : INFINITY;
+  S2(J2_ETA) = eta;
+  S2(J2_STEPS) += 1.0;
+  const double best = S2(J2_BEST);
+  if (eta < 0.9 * best) S2(J2_SINCE) = 0.0;
+  else S2(J2_SINCE) += 1.0;
+  if (eta < best) {
+    S2(J2_BEST) = eta;
+    S2(J2_COPY) = 1.0;
+  }
+  if (S2(J2_BEST) < tol || S2(J2_SINCE) >= patience || S2(J2_STEPS) >= maxit) SC1(JF_ACT) = -1.0;
+}
+
+__global__ void k_s2_copy(int64_t N, const double* __restrict__ t, double* __restrict__ tbest,
+                          const double* __restrict__ sc) {
+  if (S2(J2_COPY) == 0.0) return;
+  for (int64_t i = blockIdx.x * (int64_t)JD_T + threadIdx.x; i < N; i += (int64_t)gridDim.x * JD_T) tbest[i] = t[i];
+}
+
+__global__ void k_s2_init(double* __restrict__ sc) {
+  if (threadIdx.x != 0) return;
+  S2(J2_BEST) = INFINITY;
+  S2(J2_SINCE) = 0.0;
+  S2(J2_COPY) = 0.0;
+  S2(J2_ETA) = INFINITY;
+  S2(J2_STEPS) = 0.0;
+}
+#undef S2
+#undef SC1
+
+static int s2_grid(int64_t N) {
+  int64_t b = (N + JD_T - 1) / JD_T;
+  return (int)(b > 152 * 4 ? 152 * 4 : (b < 1 ? 1 : b));
+}
+
+// v = R / beta1 (zero when the system does not iterate)
+__global__ void k_s2_first(int64_t N, const double* __restrict__ R, double* __restrict__ v,
+                           const double* __restrict__ sc) {
+  const double b1 = sc[JF_BETA1 * 8];
+  const double f = (sc[JF_ACT * 8] > 0.0 && b1 > 0.0) ? 1.0 / b1 : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)JD_T + threadIdx.x; i < N; i += (int64_t)gridDim.x * JD_T) v[i] = R[i] * f;
+}
+
+void s2_start(cudaStream_t s, int64_t N, const double* R, double* r1, double* r2, double* v, double* t, double* w1,
+              double* w2, double* Bt, double* Bw1, double* Bw2, double* acc, double* sc) {
+  ProfScope ps(s, PROF_SMALL);
+  cudaMemsetAsync(acc, 0, sizeof(double) * 256, s);
+  dot_accum(s, N, R, R, acc + 24);
+  k_jd_init<<<1, 32, 0, s>>>(1, acc, sc); count_launch();
+  k_s2_init<<<1, 32, 0, s>>>(sc); count_launch();
+  cudaMemcpyAsync(r1, R, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(r2, R, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
+  k_s2_first<<<s2_grid(N), JD_T, 0, s>>>(N, R, v, sc); count_launch();
+  for (double* z : {t, w1, w2, Bt, Bw1, Bw2}) cudaMemsetAsync(z, 0, sizeof(double) * N, s);
+}
+
+// one MINRES step after the product Bv = B v and the reductions acc[0] = v^T Bv,
+// acc[8] = v^T v, acc[32 ..] = Q^T Bv (acc[24], acc[160..163) zeroed)
+void s2_step(cudaStream_t s, int64_t N, int nq, const double* Bv, double* v, const double* Q, const double* mu,
+             double* r1, double* r2, double* w1, double* w2, double* t, double* Bw1, double* Bw2, double* Bt,
+             const double* x, const double* Bx, double* tbest, double* acc, double* sc, double eta_tol, int patience,
+             int maxit) {
+  ProfScope ps(s, PROF_SMALL);
+  const int g = s2_grid(N);
+  k_jd_coef<<<1, 32, 0, s>>>(1, acc, mu, sc); count_launch();
+  k_s2_lanczos<<<g, JD_T, 0, s>>>(N, nq, Bv, v, Q, mu, r1, r2, sc, acc); count_launch();
+  k_jd_givens<<<1, 32, 0, s>>>(1, acc, 1e-15, sc); count_launch();
+  k_s2_update<<<g, JD_T, 0, s>>>(N, v, r2, w1, w2, t, Bv, Bw1, Bw2, Bt, x, Bx, sc, acc); count_launch();
+  k_s2_eta<<<g, JD_T, 0, s>>>(N, x, t, Bx, Bt, sc, acc); count_launch();
+  k_s2_track<<<1, 32, 0, s>>>(acc, eta_tol, patience, maxit, sc); count_launch();
+  k_s2_copy<<<g, JD_T, 0, s>>>(N, t, tbest, sc); count_launch();
+  k_jd_retire<<<1, 32, 0, s>>>(1, sc); count_launch();
+  count_work(PROF_SMALL, 2.0 * N * (nq + 16), 8.0 * N * (nq + 22));
 }
 
 }  // namespace ph

@@ -34,6 +34,67 @@ constexpr int CG_PC = CG_MAXP / (CG_THREADS / 32);  // columns per warp
 
 __device__ inline double atomic_add_f64(double* p, double v) { return atomicAdd(p, v); }
 
+// 16-byte asynchronous copy global -> shared (no register staging, so a
+// thread can keep many in flight), and the wait for all of this thread's.
+__device__ inline void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Stage columns [0, p) of the basis, rows [row0, row0 + rows), into Ps
+// (column c at Ps + c * rows): 16-byte asynchronous copies when vec (every
+// column start 16-byte aligned) and the chunk lies inside the vectors, else
+// element loads with zero fill past n.  Caller synchronises afterwards.
+template <typename T>
+__device__ inline void stage_cols(const Basis<T>& P, int p, int n, int row0, int rows, bool vec, T* Ps, int tid,
+                                  int NT) {
+  if (vec && row0 + rows <= n) {
+    constexpr int W = 16 / sizeof(T);
+    const int segs = rows / W;
+    for (int e = tid; e < p * segs; e += NT) {
+      const int c = e / segs, sg = e - c * segs;
+      const T* src = (c < P.c1 ? P.p1 + (size_t)c * P.ld1 : P.p2 + (size_t)(c - P.c1) * P.ld2) + row0 + sg * W;
+      cp_async16(Ps + (size_t)c * rows + sg * W, src);
+    }
+    cp_async_wait_all();
+  } else {
+#pragma unroll 4
+    for (int e = tid; e < p * rows; e += NT) {
+      const int c = e / rows, rr = e - c * rows;
+      const int ii = row0 + rr;
+      T pc = T(0);
+      if (ii < n) pc = c < P.c1 ? P.p1[(size_t)c * P.ld1 + ii] : P.p2[(size_t)(c - P.c1) * P.ld2 + ii];
+      Ps[(size_t)c * rows + rr] = pc;
+    }
+  }
+}
+template <typename T>
+static bool cols16(const T* p, int ld) { return p == nullptr || (((uintptr_t)p & 15) == 0 && (ld * sizeof(T)) % 16 == 0); }
+
+// K consecutive values from 16-byte aligned shared memory, with 16-byte loads.
+template <typename T, int K>
+__device__ inline void lds_vec(const T* __restrict__ src, T (&d)[K]) {
+  if constexpr ((K * sizeof(T)) % 16 == 0) {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+      for (int u = 0; u < K; u += 4) {
+        const float4 t = *reinterpret_cast<const float4*>(src + u);
+        d[u] = t.x; d[u + 1] = t.y; d[u + 2] = t.z; d[u + 3] = t.w;
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < K; u += 2) {
+        const double2 t = *reinterpret_cast<const double2*>(src + u);
+        d[u] = t.x; d[u + 1] = t.y;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < K; ++u) d[u] = src[u];
+  }
+}
+
 // Butterfly reduce-scatter of the N values each lane holds (N a power of two):
 // at the level with lane offset O, a lane keeps the half of its live values
 // selected by its lane bit O and adds the partner's copy of that half, so a
@@ -72,16 +133,20 @@ __device__ __forceinline__ void reduce_scatter(T (&v)[N], int lane) {
 template <typename T, int Q>
 __global__ void __launch_bounds__(CG_THREADS) k_cgs_pass(int n, Basis<T> P, T* __restrict__ Tb, int ldt, int q,
                                                          const double* __restrict__ Gsub, double* __restrict__ Gout,
-                                                         double* __restrict__ Tout, int rows) {
+                                                         double* __restrict__ Tout, int rows, bool vec) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int p = P.cols();
   T* Ps = reinterpret_cast<T*>(smem_raw);                 // [p][rows]
   T* Ts = Ps + (size_t)p * rows;                           // [Q][rows]
-  T* Gs = Ts + (size_t)Q * rows;                           // [p][Q] in T precision
+  T* Gs = Ts + (size_t)Q * rows;                           // [p][Q] row-major, in T precision
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // Gs[c + r*p] = Gsub[c + r*p] (column-major p x q), zero for r >= q
+  // Gs[c * Q + r] = Gsub[c + r * p] (Gsub column-major p x q), zero for r >= q:
+  // the Q coefficients of basis column c are contiguous (vector loads)
   if (Gsub)
-    for (int k = tid; k < p * Q; k += CG_THREADS) Gs[k] = k < p * q ? (T)Gsub[k] : T(0);
+    for (int k = tid; k < p * Q; k += CG_THREADS) {
+      const int c = k / Q, r = k - c * Q;
+      Gs[k] = r < q ? (T)Gsub[c + (size_t)r * p] : T(0);
+    }
   T accG[CG_PC][Q];
   T accT[(Q * (Q + 1) / 2 + 7) / 8];
 #pragma unroll
@@ -97,14 +162,7 @@ __global__ void __launch_bounds__(CG_THREADS) k_cgs_pass(int n, Basis<T> P, T* _
     const int i = row0 + tid;
     const bool act = tid < rows && i < n;
     // ---- phase A
-#pragma unroll 4
-    for (int e = tid; e < p * rows; e += CG_THREADS) {
-      const int c = e / rows, rr = e - c * rows;
-      const int ii = row0 + rr;
-      T pc = T(0);
-      if (ii < n) pc = c < P.c1 ? P.p1[(size_t)c * P.ld1 + ii] : P.p2[(size_t)(c - P.c1) * P.ld2 + ii];
-      Ps[(size_t)c * rows + rr] = pc;
-    }
+    stage_cols<T>(P, p, n, row0, rows, vec, Ps, tid, CG_THREADS);
     T t[Q];
 #pragma unroll
     for (int r = 0; r < Q; ++r) t[r] = (act && r < q) ? Tb[(size_t)r * ldt + i] : T(0);
@@ -113,7 +171,12 @@ __global__ void __launch_bounds__(CG_THREADS) k_cgs_pass(int n, Basis<T> P, T* _
       for (int c = 0; c < p; ++c) {
         const T pc = Ps[(size_t)c * rows + tid];
 #pragma unroll
-        for (int r = 0; r < Q; ++r) t[r] = fma(-pc, Gs[c + r * p], t[r]);
+        {
+          T g[Q];
+          lds_vec<T, Q>(Gs + (size_t)c * Q, g);
+#pragma unroll
+          for (int r = 0; r < Q; ++r) t[r] = fma(-pc, g[r], t[r]);
+        }
       }
     }
 #pragma unroll
@@ -124,14 +187,19 @@ __global__ void __launch_bounds__(CG_THREADS) k_cgs_pass(int n, Basis<T> P, T* _
     __syncthreads();
     // ---- phase B
     if (Gout) {
+      // each row of the block is read once from shared memory and used for
+      // all of the warp's basis columns (Q + CG_PC loads per Q * CG_PC FMAs)
+      for (int rr = lane; rr < rows; rr += 32) {
+        T tt[Q];
 #pragma unroll
-      for (int a = 0; a < CG_PC; ++a) {
-        const int c = warp + a * (CG_THREADS / 32);
-        if (c < p) {
-          for (int rr = lane; rr < rows; rr += 32) {
+        for (int r = 0; r < Q; ++r) tt[r] = Ts[r * rows + rr];
+#pragma unroll
+        for (int a = 0; a < CG_PC; ++a) {
+          const int c = warp + a * (CG_THREADS / 32);
+          if (c < p) {
             const T pv = Ps[(size_t)c * rows + rr];
 #pragma unroll
-            for (int r = 0; r < Q; ++r) accG[a][r] = fma(pv, Ts[r * rows + rr], accG[a][r]);
+            for (int r = 0; r < Q; ++r) accG[a][r] = fma(pv, tt[r], accG[a][r]);
           }
         }
       }
@@ -203,7 +271,8 @@ static void cgs_launch(cudaStream_t s, int n, const Basis<T>& P, T* Tb, int ldt,
   const int cap = num_sms() * (sizeof(T) == 8 ? 2 : 4);
   if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;
-  k_cgs_pass<T, Q><<<grid, CG_THREADS, smem, s>>>(n, P, Tb, ldt, q, Gsub, Gout, Tout, rows); count_launch();
+  const bool vec = cols16(P.p1, P.ld1) && cols16(P.p2, P.ld2);
+  k_cgs_pass<T, Q><<<grid, CG_THREADS, smem, s>>>(n, P, Tb, ldt, q, Gsub, Gout, Tout, rows, vec); count_launch();
   count_work(pcat<T>(PROF_GRAM),
              2.0 * n * p * q * ((Gsub ? 1 : 0) + (Gout ? 1 : 0)) + (Tout ? (double)n * q * (q + 1) : 0.0),
              (double)sizeof(T) * n * ((Gsub || Gout ? p : 0) + q * (Gsub ? 2 : 1)));
@@ -228,19 +297,21 @@ void cgs_pass(cudaStream_t s, int n, const Basis<T>& P, T* Tb, int ldt, int q, c
 // Out = P * Y [- Xs diag(theta)], optional column norms.
 // ---------------------------------------------------------------------------
 constexpr int TS_ROWS = 128;
+constexpr int TS_CB = 8;       // output columns per pass of k_tall_small
 template <typename T>
 __global__ void __launch_bounds__(TS_ROWS) k_tall_small(int n, const T* P, int ldp, int p,
                                                         const double* __restrict__ Y, int ldy, int r, T* Out,
                                                         int ldo, const T* __restrict__ Xs, int ldx,
-                                                        const double* __restrict__ theta, double* norms2) {
+                                                        const double* __restrict__ theta, double* norms2, bool vec) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int rp = (r + TS_CB - 1) / TS_CB * TS_CB;                 // r padded to whole column blocks
   double* nrm = reinterpret_cast<double*>(smem_raw);            // [r]
-  T* Ys = reinterpret_cast<T*>(smem_raw + sizeof(double) * (size_t)r);  // [r][p]
-  T* Ps = Ys + (size_t)p * r;                                    // [p][blockDim.x]
+  T* Ys = reinterpret_cast<T*>(smem_raw + sizeof(double) * (size_t)((r + 1) & ~1));  // [p][rp] row-major
+  T* Ps = Ys + (size_t)p * rp;                                   // [p][blockDim.x], 16-byte aligned
   const int tid = threadIdx.x;
-  for (int k = tid; k < p * r; k += blockDim.x) {
-    const int c = k / p, a = k % p;
-    Ys[(size_t)c * p + a] = (T)Y[a + (size_t)c * ldy];
+  for (int k = tid; k < p * rp; k += blockDim.x) {
+    const int a = k / rp, c = k - a * rp;
+    Ys[k] = c < r ? (T)Y[a + (size_t)c * ldy] : T(0);
   }
   if (norms2)
     for (int c = tid; c < r; c += blockDim.x) nrm[c] = 0.0;
@@ -250,22 +321,25 @@ __global__ void __launch_bounds__(TS_ROWS) k_tall_small(int n, const T* P, int l
   for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     const int i = ch * R + tid;
     const bool act = i < n;
-#pragma unroll 4
-    for (int a = 0; a < p; ++a) Ps[(size_t)a * R + tid] = act ? P[(size_t)a * ldp + i] : T(0);
+    Basis<T> PB{P, ldp, p, nullptr, 0, 0};
+    stage_cols<T>(PB, p, n, ch * R, R, vec, Ps, tid, R);
     __syncthreads();  // every row of the chunk is read before any (in-place) write
-    // four output columns at a time: four independent FMA chains per thread
-    for (int c0 = 0; c0 < r; c0 += 4) {
-      const int nc = r - c0 < 4 ? r - c0 : 4;
-      T acc[4] = {T(0), T(0), T(0), T(0)};
-      const T* y0 = Ys + (size_t)c0 * p;
+    // TS_CB output columns at a time: one shared load of the row's basis
+    // value and vector loads of the block's coefficients per TS_CB FMAs
+    for (int c0 = 0; c0 < r; c0 += TS_CB) {
+      const int nc = r - c0 < TS_CB ? r - c0 : TS_CB;
+      T acc[TS_CB];
+#pragma unroll
+      for (int u = 0; u < TS_CB; ++u) acc[u] = T(0);
       for (int a = 0; a < p; ++a) {
         const T pa = Ps[(size_t)a * R + tid];
+        T yv[TS_CB];
+        lds_vec<T, TS_CB>(Ys + (size_t)a * rp + c0, yv);
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (u < nc) acc[u] = fma(pa, y0[(size_t)u * p + a], acc[u]);
+        for (int u = 0; u < TS_CB; ++u) acc[u] = fma(pa, yv[u], acc[u]);
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < TS_CB; ++u) {
         if (u < nc) {
           const int c = c0 + u;
           T o = acc[u];
@@ -293,7 +367,8 @@ void tall_times_small(cudaStream_t s, int n, const T* P, int ldp, int p, const d
   ProfScope ps(s, pcat<T>(PROF_TALL));
   int R = TS_ROWS;
   while (R > 32 && (int64_t)ceil_div(n, R) < 2LL * num_sms()) R >>= 1;
-  const size_t smem = sizeof(double) * (size_t)r + sizeof(T) * ((size_t)p * r + (size_t)p * R);
+  const int rp = (r + TS_CB - 1) / TS_CB * TS_CB;
+  const size_t smem = sizeof(double) * (size_t)((r + 1) & ~1) + sizeof(T) * ((size_t)p * rp + (size_t)p * R);
   static std::atomic<uint64_t> attr_done{0};
   once_per_device(attr_done, [&] {
     cudaFuncSetAttribute(k_tall_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -301,7 +376,8 @@ void tall_times_small(cudaStream_t s, int n, const T* P, int ldp, int p, const d
   int grid = ceil_div(n, R);
   const int cap = num_sms() * 8;
   if (grid > cap) grid = cap;
-  k_tall_small<T><<<grid, R, smem, s>>>(n, P, ldp, p, Y, ldy, r, Out, ldo, Xs, ldx, theta, norms2); count_launch();
+  k_tall_small<T><<<grid, R, smem, s>>>(n, P, ldp, p, Y, ldy, r, Out, ldo, Xs, ldx, theta, norms2,
+                                        cols16(P, ldp)); count_launch();
   count_work(pcat<T>(PROF_TALL), 2.0 * n * p * r + (theta ? 2.0 * n * r : 0.0) + (norms2 ? 2.0 * n * r : 0.0),
              (double)sizeof(T) * n * (p + r + (theta ? r : 0)));
 }
@@ -470,6 +546,40 @@ void dot_accum(cudaStream_t s, int64_t n, const double* x, const double* y, doub
   if (grid > num_sms() * 4) grid = num_sms() * 4;
   if (n > 0) k_dot<<<grid, 256, 0, s>>>(n, x, y, out); count_launch();
 }
+// y = x / d elementwise; a |d| below guard is raised to +-guard (guard 0: none)
+__global__ void k_diag_div(int64_t n, const double* __restrict__ x, const double* __restrict__ d, double guard,
+                           double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double di = d[i];
+    if (fabs(di) < guard) di = di < 0 ? -guard : guard;
+    y[i] = x[i] / di;
+  }
+}
+void diag_div(cudaStream_t s, int64_t n, const double* x, const double* d, double guard, double* y) {
+  int grid = ceil_div(n, 256);
+  if (grid > num_sms() * 8) grid = num_sms() * 8;
+  if (n > 0) k_diag_div<<<grid, 256, 0, s>>>(n, x, d, guard, y); count_launch();
+}
+// out = a - (dots[0] / dots[1]) b, or a when dots[1] == 0 (the Olsen form)
+__global__ void k_olsen_combine(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                                const double* __restrict__ dots, double* __restrict__ out) {
+  const double e = dots[1] != 0.0 ? dots[0] / dots[1] : 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = fma(-e, b[i], a[i]);
+}
+void olsen_combine(cudaStream_t s, int64_t n, const double* a, const double* b, const double* dots, double* out) {
+  int grid = ceil_div(n, 256);
+  if (grid > num_sms() * 8) grid = num_sms() * 8;
+  if (n > 0) k_olsen_combine<<<grid, 256, 0, s>>>(n, a, b, dots, out); count_launch();
+}
+__global__ void k_square(int64_t n, const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = x[i] * x[i];
+}
+void square(cudaStream_t s, int64_t n, const double* x, double* y) {
+  if (n > 0) k_square<<<ceil_div(n, 256) < 8192 ? ceil_div(n, 256) : 8192, 256, 0, s>>>(n, x, y); count_launch();
+}
+
 // x *= a (a read from device memory when ap != nullptr)
 __global__ void k_scal(int64_t n, double a, const double* ap, double* x) {
   const double f = ap ? ap[0] : a;

@@ -133,6 +133,12 @@ void axpby(cudaStream_t s, int64_t n, double a, const double* x, double b, doubl
 template <typename T> void col_norms2_dense(cudaStream_t s, int n, const T* X, int ldx, int q, double* norms2);
 
 void dot_accum(cudaStream_t s, int64_t n, const double* x, const double* y, double* out);
+// y = x / d (|d| < guard raised to +-guard; guard 0: none)
+void diag_div(cudaStream_t s, int64_t n, const double* x, const double* d, double guard, double* y);
+// out = a - (dots[0] / dots[1]) b (a when dots[1] == 0): the Olsen combination
+void olsen_combine(cudaStream_t s, int64_t n, const double* a, const double* b, const double* dots, double* out);
+// y = x .* x
+void square(cudaStream_t s, int64_t n, const double* x, double* y);
 void scal(cudaStream_t s, int64_t n, double a, const double* ap, double* x);
 template <typename T> void fill_const(cudaStream_t s, int64_t n, T v, T* x);
 
@@ -219,6 +225,16 @@ void jd_dots(cudaStream_t s, int n, int q, const float* v, const float* X, const
 void jd_step(cudaStream_t s, int n, int q, int nl, const float* Cv, float* v, const float* X, const float* Xl,
              const double* theta, float* r1, float* r2, float* w1, float* w2, float* sol, double* acc, double* sc,
              double tol);
+// stage 2 (one FP64 system on B, dynamic stop by the eigen-residual of x + t):
+// acc (256 doubles): [0] v^T Bv, [8] v^T v, [24] ||y||^2, [32, 32 + nq) Q^T Bv,
+// [160, 163) the eigen-residual sums; sc: JD_NSCALAR * 8 + 8 doubles
+void s2_start(cudaStream_t s, int64_t N, const double* R, double* r1, double* r2, double* v, double* t, double* w1,
+              double* w2, double* Bt, double* Bw1, double* Bw2, double* acc, double* sc);
+void s2_step(cudaStream_t s, int64_t N, int nq, const double* Bv, double* v, const double* Q, const double* mu,
+             double* r1, double* r2, double* w1, double* w2, double* t, double* Bw1, double* Bw2, double* Bt,
+             const double* x, const double* Bx, double* tbest, double* acc, double* sc, double eta_tol, int patience,
+             int maxit);
+constexpr int JD2_FIELD_STEPS = 17 * 8 + 5;   // sc index of the steps taken (stage-2 form)
 constexpr int JD_NSCALAR = 17;
 constexpr int JD_FIELD_ACT = 15;   // sc[JD_FIELD_ACT * 8 + c] != 0 while system c iterates
 

@@ -51,16 +51,21 @@ struct PhError {
                                          std::string(#x) + ": " + cudaGetErrorString(e_)};      \
   } while (0)
 
-// Device allocation owned by a solve (stream-ordered pool).
+// Device allocation owned by a solve (stream-ordered, from the handle's
+// memory pool, which keeps its memory between solves).
 struct Pool {
   cudaStream_t s;
+  cudaMemPool_t mp;
   std::vector<void*> ptrs;
-  explicit Pool(cudaStream_t st) : s(st) {}
+  Pool(cudaStream_t st, cudaMemPool_t m) : s(st), mp(m) {}
   template <typename T>
   T* get(size_t count) {
     void* p = nullptr;
     if (count == 0) count = 1;
-    CUCHK(cudaMallocAsync(&p, sizeof(T) * count, s));
+    if (mp)
+      CUCHK(cudaMallocFromPoolAsync(&p, sizeof(T) * count, mp, s));
+    else
+      CUCHK(cudaMallocAsync(&p, sizeof(T) * count, s));
     ptrs.push_back(p);
     return static_cast<T*>(p);
   }
@@ -87,6 +92,10 @@ struct phsvds_ctx {
   unsigned char* host = nullptr;  // pinned readback / upload area
   size_t host_bytes = 0;
   std::vector<ph::SpmmPlan> plans;  // autotuned SpMM schedules of earlier solves
+  // device memory of the solves: a pool that keeps what it has mapped until
+  // the handle is destroyed, so that repeated solves do not map and unmap
+  // their workspaces (the default pool returns memory at every synchronise)
+  cudaMemPool_t mempool = nullptr;
 };
 
 namespace ph {
@@ -643,6 +652,9 @@ struct Stage1 {
   // Jacobi-Davidson corrections with FP32 inner solves (FP64 continuation of
   // the mixed-precision stage 1), or null for the plain GD+k correction
   InnerJD* jd = nullptr;
+  // the Olsen correction with a shift-free M (a preconditioner given by the
+  // caller, M^{-1} M^{-T} of Sec. 4): diagC holds m_j^2 and theta is taken as 0
+  bool shift_free = false;
 
   Stage1(phsvds_ctx* c, Pool& p, int n_, int k_, const phsvds_opts& o, bool largest_, double delta_, double eps,
          int precond_, const double* diag, COp<T> op_)
@@ -982,7 +994,7 @@ struct Stage1 {
       }
       if (precond == PHSVDS_PREC_JACOBI && nu > 0) {
         double* hu = h.at<double>(1024);     // bytes [1024, 1088)
-        for (int c = 0; c < nu; ++c) hu[c] = thv[unconv[c]];
+        for (int c = 0; c < nu; ++c) hu[c] = shift_free ? 0.0 : thv[unconv[c]];
         CUCHK(cudaMemcpyAsync(thU, hu, sizeof(double) * nu, cudaMemcpyHostToDevice, s));
         zero(s, dots, 2 * nu);
         const double guard = EPS64 * std::max(out.theta_max, 1e-300);
@@ -1181,6 +1193,74 @@ static std::vector<double> rayleigh_ritz_post(phsvds_ctx* ctx, Pool& pool, DevA&
 // ---------------------------------------------------------------------------
 // Stage 2: refined projection on B (Algorithm 2), FP64
 // ---------------------------------------------------------------------------
+// The JDQMR correction of stage 2 (Sec. 4): an inexact solution of
+// (I - QQ^T)(B - mu I)(I - QQ^T) t = -(I - QQ^T) r, Q = [locked vectors and
+// mirrors, x], by MINRES in FP64 with the dynamic stop on the eigen-residual
+// of x + t (k_inner.cu), one equation per outer iteration.
+struct InnerJD2 {
+  cudaStream_t s;
+  F64Ctx& f;
+  int64_t N;
+  int n, maxit, patience, chunk = 10;
+  double *R, *r1, *r2, *v, *t, *w1, *w2, *Bv, *Bt, *Bw1, *Bw2, *Bx, *tbest, *acc, *sc, *mu;
+  GraphCache graphs;
+  int64_t steps = 0, solves = 0;
+  InnerJD2(phsvds_ctx* c, Pool& pool, F64Ctx& ff, int maxit_, int patience_, bool use_graphs)
+      : s(c->stream), f(ff), N((int64_t)ff.A.m + ff.A.n), n(ff.A.n), maxit(maxit_), patience(patience_) {
+    for (double** p : {&R, &r1, &r2, &v, &t, &w1, &w2, &Bv, &Bt, &Bw1, &Bw2, &Bx, &tbest}) *p = pool.get<double>(N);
+    acc = pool.get<double>(256);
+    sc = pool.get<double>(JD_NSCALAR * 8 + 8);
+    mu = pool.get<double>(1);
+    graphs.enabled = use_graphs;
+  }
+  // out = the correction for the refined pair (mu, x) with residual r and
+  // B x = Bx_in; Q: nq columns (the last one x).  Returns the steps taken.
+  int solve(phsvds_ctx* ctx, const double* Q, int nq, const double* x, const double* Bx_in, double mu_h,
+            const double* r, double eta_tol, double* out) {
+    Host h(ctx);
+    Basis<double> PQ{Q, (int)N, nq, nullptr, 0, 0};
+    // right-hand side -(I - QQ^T) r
+    CUCHK(cudaMemcpyAsync(R, r, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    zero(s, acc, 256);
+    cgs_pass<double>(s, (int)N, PQ, R, (int)N, 1, nullptr, acc + 32, nullptr);
+    cgs_pass<double>(s, (int)N, PQ, R, (int)N, 1, acc + 32, nullptr, nullptr);
+    scal(s, N, -1.0, nullptr, R);
+    CUCHK(cudaMemcpyAsync(Bx, Bx_in, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    double* hm = h.at<double>(16448);   // bytes [16448, 16456)
+    *hm = mu_h;
+    CUCHK(cudaMemcpyAsync(mu, hm, sizeof(double), cudaMemcpyHostToDevice, s));
+    CUCHK(cudaMemcpyAsync(tbest, r, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    s2_start(s, N, R, r1, r2, v, t, w1, w2, Bt, Bw1, Bw2, acc, sc);
+    auto step = [&]() {
+      f.B(v, Bv);
+      zero(s, acc, 256);
+      cgs_pass<double>(s, (int)N, PQ, Bv, (int)N, 1, nullptr, acc + 32, nullptr);
+      dot_accum(s, N, v, Bv, acc);
+      dot_accum(s, N, v, v, acc + 8);
+      s2_step(s, N, nq, Bv, v, Q, mu, r1, r2, w1, w2, t, Bw1, Bw2, Bt, x, Bx, tbest, acc, sc, eta_tol, patience,
+              maxit);
+    };
+    double* hs = h.at<double>(16456);   // bytes [16456, 16472): act, steps
+    int it = 0;
+    while (it < maxit) {
+      const int m = std::min(chunk, maxit - it);
+      graphs.run(s, (4ull << 40) | ((uint64_t)m << 16) | (uint64_t)nq, [&]() {
+        for (int i = 0; i < m; ++i) step();
+      });
+      it += m;
+      CUCHK(cudaMemcpyAsync(hs, sc + JD_FIELD_ACT * 8, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CUCHK(cudaMemcpyAsync(hs + 1, sc + JD2_FIELD_STEPS, sizeof(double), cudaMemcpyDeviceToHost, s));
+      sync(s);
+      if (hs[0] == 0.0) break;
+    }
+    const int taken = (int)hs[1];
+    steps += taken;
+    ++solves;
+    CUCHK(cudaMemcpyAsync(out, tbest, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    return taken;
+  }
+};
+
 struct Stage2 {
   phsvds_ctx* ctx;
   cudaStream_t s;
@@ -1201,6 +1281,22 @@ struct Stage2 {
   int j = 0, nl = 0;
   int64_t iters = 0, restarts = 0, mv = 0;
   std::vector<double> th_lock;
+  // correction operator P of B (Sec. 4), in the Olsen form t = P r - e P x:
+  // 0 none (t = r); 1 [0 A M; M A^T 0] with M = diag(C)^{-1} (pd = diag(C),
+  // |d| below pguard raised); 2 [0 M^{-1}; M^{-T} 0] from a given diagonal
+  // M ~ A (pd = M, square A)
+  int pmode = 0;
+  const double* pd = nullptr;
+  double pguard = 0.0;
+  double *Pr = nullptr, *Px = nullptr, *ptmp = nullptr, *pdots = nullptr;
+  // deflated vectors: the locked ones, and with the JDQMR correction also the
+  // mirror [v; -u] of each locked tiny pair (for sigma <= sqrt(eps) ||A|| the
+  // pair +-sigma of B is not separable at the tolerance and both eigenvectors
+  // belong to one triplet), with room for x as the last column of Q
+  double* D = nullptr;
+  int nd = 0;
+  InnerJD2* jd2 = nullptr;
+  double* Bxr = nullptr;
 
   Stage2(phsvds_ctx* c, Pool& p, F64Ctx& ff, DevA& A, int k_, const phsvds_opts& o, double delta_, double normA_)
       : ctx(c), s(c->stream), pool(p), f(ff), m(A.m), n(A.n), N(A.m + A.n), k(k_), maxb(o.max_basis),
@@ -1211,6 +1307,8 @@ struct Stage2 {
     W = pool.get<double>(NN * maxb);
     Q = pool.get<double>(NN * maxb);
     Xl = pool.get<double>(NN * k);
+    D = pool.get<double>(NN * (2 * k + 1));
+    Bxr = pool.get<double>(NN);
     x0 = pool.get<double>(NN * k);
     tv = pool.get<double>(NN);
     xr = pool.get<double>(NN);
@@ -1247,10 +1345,36 @@ struct Stage2 {
     }
   }
 
+  void set_precond(int mode, const double* d, double guard) {
+    pmode = mode;
+    pd = d;
+    pguard = guard;
+    if (mode && !Pr) {
+      Pr = pool.get<double>((size_t)N);
+      Px = pool.get<double>((size_t)N);
+      ptmp = pool.get<double>((size_t)n);
+      pdots = pool.get<double>(2);
+    }
+  }
+
+  // Py = P y in the [v; u] order of the basis vectors
+  void apply_P(const double* y, double* Py) {
+    if (pmode == 1) {  // [M A^T y_u; A M y_v]
+      csr_spmm<double>(s, f.A.At64, 1, y + n, ptmp);
+      diag_div(s, n, ptmp, pd, pguard, Py);
+      diag_div(s, n, y, pd, pguard, ptmp);
+      csr_spmm<double>(s, f.A.A64, 1, ptmp, Py + n);
+      ++mv;
+    } else {           // [M^{-1} y_u; M^{-T} y_v] (m = n)
+      diag_div(s, n, y + n, pd, 0.0, Py);
+      diag_div(s, n, y, pd, 0.0, Py + n);
+    }
+  }
+
   // Append t (orthonormalised against [Xl | V]) as column j; W(:, j) = B v_j;
   // the frame gets the new column of H = V^T W.
   void append(double* t) {
-    Basis<double> P{Xl, N, nl, V, N, j};
+    Basis<double> P{D, N, nd, V, N, j};
     orth.run(N, P, t, V + (size_t)j * N);
     f.B(V + (size_t)j * N, W + (size_t)j * N);
     ++mv;
@@ -1290,6 +1414,23 @@ struct Stage2 {
     set_identity(s, jnew, S, LD);
     s_ident = true;
     j = jnew;
+  }
+
+  // The basis made orthonormal against the deflated set D again (after a
+  // mirror joined it): each column orthonormalised against D and the columns
+  // before it, then W = B V and H = V^T W afresh.
+  void reorthonormalise() {
+    const int jj = j;
+    for (int c = 0; c < jj; ++c) {
+      CUCHK(cudaMemcpyAsync(tv, V + (size_t)c * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+      Basis<double> P{D, N, nd, V, N, c};
+      orth.run(N, P, tv, V + (size_t)c * N);
+      f.B(V + (size_t)c * N, W + (size_t)c * N);
+      ++mv;
+    }
+    gram_full<double>(s, N, V, W, jj, Ht, w1);
+    set_identity(s, jj, S, LD);
+    s_ident = true;
   }
 
   // sig_s: k shifts (stage-1 values), Vt: n x k FP64 stage-1 right vectors.
@@ -1360,7 +1501,21 @@ struct Stage2 {
                 target, shift, th1, rn, *h.at<double>(8));
       if (rn < delta * normA / std::sqrt(2.0)) {
         CUCHK(cudaMemcpyAsync(Xl + (size_t)nl * N, xr, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+        CUCHK(cudaMemcpyAsync(D + (size_t)nd * N, xr, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
         ++nl;
+        ++nd;
+        const bool mirror = jd2 && std::fabs(th1) <= std::sqrt(EPS64) * normA;
+        if (mirror) {  // [v; -u], normalised, deflated as well
+          double* dm = D + (size_t)nd * N;
+          CUCHK(cudaMemcpyAsync(dm, xr, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+          scal(s, m, -1.0, nullptr, dm + n);
+          zero(s, nrm, 1);
+          col_norms2_dense<double>(s, N, dm, N, 1, nrm);
+          CUCHK(cudaMemcpyAsync(h.at<double>(0), nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+          sync(s);
+          scal(s, N, 1.0 / std::sqrt(*h.at<double>(0)), nullptr, dm);
+          ++nd;
+        }
         th_lock.push_back(th1);
         ++target;
         if (target >= k) break;
@@ -1375,6 +1530,7 @@ struct Stage2 {
           const int nc = *h.at<int>(12288);
           if (nc < 1 || nc > j - 1) throw PhError{PHSVDS_ERR_BREAKDOWN, "stage 2: locking complement size out of range"};
           transform(nc);
+          if (mirror) reorthonormalise();
         } else {
           j = 0;  // the basis was s1 alone
           s_ident = true;
@@ -1420,8 +1576,23 @@ struct Stage2 {
         CUCHK(cudaMemcpyAsync(sprev, s1, sizeof(double) * j, cudaMemcpyDeviceToDevice, s));
         have_prev = true;
       }
-      // ---- expand with t = r
-      CUCHK(cudaMemcpyAsync(tv, rr, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+      // ---- expand with t = r, its preconditioned Olsen form, or the JDQMR
+      // correction
+      if (jd2) {
+        tall_times_small<double>(s, N, W, N, j, s1, LD, 1, Bxr, N, nullptr, 0, nullptr, nullptr);   // B x
+        CUCHK(cudaMemcpyAsync(D + (size_t)nd * N, xr, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+        const int taken = jd2->solve(ctx, D, nd + 1, xr, Bxr, th1, rr, delta * normA / std::sqrt(2.0), tv);
+        mv += taken;
+      } else if (pmode) {
+        apply_P(rr, Pr);
+        apply_P(xr, Px);
+        zero(s, pdots, 2);
+        dot_accum(s, N, xr, Pr, pdots);
+        dot_accum(s, N, xr, Px, pdots + 1);
+        olsen_combine(s, N, Pr, Px, pdots, tv);
+      } else {
+        CUCHK(cudaMemcpyAsync(tv, rr, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+      }
       append(tv);
       CUCHK(cudaMemsetAsync(sprev + (j - 1), 0, sizeof(double), s));
       if (!qr_full) qr_col(j - 1, shift);
@@ -1495,10 +1666,23 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
   const bool largest = target == PHSVDS_LARGEST;
   const bool mixed = o.precision == PHSVDS_MIXED;
   const int b = std::max(1, std::min(o.block_size, k));
-  Pool pool(s);
+  Pool pool(s, ctx->mempool);
   DevA A;
   const int64_t launches0 = g_launch_count;
-  upload_matrix(ctx, pool, A, m, n, nnz, rp, ci, va, on_dev, mixed, precond != PHSVDS_PREC_NONE, 8);
+  const bool given = precond == PHSVDS_PREC_GIVEN;
+  upload_matrix(ctx, pool, A, m, n, nnz, rp, ci, va, on_dev, mixed,
+                precond == PHSVDS_PREC_JACOBI || precond == PHSVDS_PREC_LEARNED || o.stage2_precond, 8);
+  // a preconditioner M ~ A given by the caller (diagonal): stage 1 applies
+  // M^{-1} M^{-T} through the Olsen machinery with d = m^2 and no shift
+  double *Mdev = nullptr, *M2dev = nullptr;
+  if (given) {
+    Mdev = pool.get<double>(A.n);
+    M2dev = pool.get<double>(A.n);
+    CUCHK(cudaMemcpyAsync(Mdev, o.precond_M, sizeof(double) * A.n, cudaMemcpyHostToDevice, s));
+    square(s, A.n, Mdev, M2dev);
+  }
+  const int precond1 = given ? (int)PHSVDS_PREC_JACOBI : (int)precond;
+  const double* diag1 = given ? M2dev : A.diagC;
   // learned correction: network weights (FP32 from BF16) and feature planes on the device
   LearnedDev ld;
   if (precond == PHSVDS_PREC_LEARNED) {
@@ -1538,7 +1722,8 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
   // ---- stage 1
   const auto t1a = clk::now();
   const double tol_in = TOL_MARGIN * tol;
-  Stage1<double> s1(ctx, pool, A.n, k, o, largest, tol_in, EPS64, precond, A.diagC, op64);
+  Stage1<double> s1(ctx, pool, A.n, k, o, largest, tol_in, EPS64, precond1, diag1, op64);
+  s1.shift_free = given;
   s1.lp = &ld;
   s1.rec_r = o.record_r;
   s1.rec_max = o.record_r ? o.record_max : 0;
@@ -1569,8 +1754,9 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
     CUCHK(cudaMemcpyAsync(X0d, o.init_V, sizeof(double) * A.n * nx0, cudaMemcpyHostToDevice, s));
   }
   if (mixed) {
-    Stage1<float> s1f(ctx, pool, A.n, k, o, largest, tol_in, EPS32, precond, A.diagC, op32);
+    Stage1<float> s1f(ctx, pool, A.n, k, o, largest, tol_in, EPS32, precond1, diag1, op32);
     s1f.lp = &ld;
+    s1f.shift_free = given;
     float* X0f = nullptr;
     if (nx0) {
       X0f = pool.get<float>((size_t)A.n * nx0);
@@ -1634,7 +1820,7 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
   const double floor = o.eps_factor * EPS64;
   for (int i = 0; i < k; ++i)
     if (tol < floor * normA / std::max(sg[i], 1e-300) || !(rs[i] < tol_in * normA)) need2 = true;
-  int64_t it2 = 0, rs2 = 0;
+  int64_t it2 = 0, rs2 = 0, inner2_steps = 0, inner2_solves = 0;
   double t2ms = 0.0;
   if (need2 && o.stage2) {
     const auto t2a = clk::now();
@@ -1667,12 +1853,42 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
     }
     std::vector<double> sig_s(k);
     for (int i = 0; i < k; ++i) sig_s[i] = std::sqrt(std::max(lam[i], 0.0));
+    std::unique_ptr<InnerJD2> jd2;
+    if (o.stage2_inner == 1) {
+      // the targets stage 1 resolved go first and the tiny ones (sigma~ <=
+      // sqrt(eps) ||A||, whose u~ is random) last, each group in its order,
+      // so that accurate guesses lock before the ambiguous shifts near zero
+      std::vector<int> ord2;
+      for (int pass = 0; pass < 2; ++pass)
+        for (int i = 0; i < k; ++i)
+          if ((sig_s[i] <= std::sqrt(EPS64) * normA) == (pass == 1)) ord2.push_back(i);
+      bool moved = false;
+      for (int i = 0; i < k; ++i) moved = moved || ord2[i] != i;
+      if (moved) {
+        double* Xo = pool.get<double>((size_t)A.n * k);
+        std::vector<double> so(k);
+        for (int i = 0; i < k; ++i) {
+          so[i] = sig_s[ord2[i]];
+          CUCHK(cudaMemcpyAsync(Xo + (size_t)i * A.n, Xv + (size_t)ord2[i] * A.n, sizeof(double) * A.n,
+                                cudaMemcpyDeviceToDevice, s));
+        }
+        sig_s = so;
+        Xv = Xo;
+      }
+      jd2 = std::make_unique<InnerJD2>(ctx, pool, f, o.inner2_maxit, o.inner2_patience, !o.profile);
+    }
     Stage2 s2(ctx, pool, f, A, k, o, tol_in, normA);
+    s2.jd2 = jd2.get();
+    if (given)
+      s2.set_precond(2, Mdev, 0.0);
+    else if (o.stage2_precond && !largest)
+      s2.set_precond(1, A.diagC, EPS64 * normA * normA);
     s2.run(sig_s, Xv);
     mvA += s2.mv;
     mvAt += s2.mv;
     it2 = s2.iters;
     rs2 = s2.restarts;
+    if (jd2) inner2_steps = jd2->steps, inner2_solves = jd2->solves;
     // split x = [v; u]
     for (int i = 0; i < k; ++i) {
       CUCHK(cudaMemcpyAsync(Vd + (size_t)i * A.n, s2.Xl + (size_t)i * s2.N, sizeof(double) * A.n,
@@ -1732,11 +1948,14 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
     st->stage1_stagnation_locks = s1.out.stag_locks + stag32;
     st->inner_steps = jd ? jd->steps : 0;
     st->inner_solves = jd ? jd->solves : 0;
+    st->inner2_steps = inner2_steps;
+    st->inner2_solves = inner2_solves;
     st->t_stage1_ms = std::chrono::duration<double, std::milli>(t1b - t1a).count();
     st->t_stage2_ms = t2ms;
     st->t_total_ms = std::chrono::duration<double, std::milli>(clk::now() - tstart).count();
     st->spmm_schedule = sch64;
     st->spmm_plan_cached = (o.spmm == PHSVDS_SPMM_AUTO) && cached64 && (!mixed || cached32);
+    st->spmm_schedule_f32 = mixed ? op32.schedule : 0;
     for (int c = 0; c < PROF_NALL; ++c) {
       st->class_flops[c] = g_work[0][c] - work0[0][c];
       st->class_bytes[c] = g_work[1][c] - work0[1][c];
@@ -1812,6 +2031,11 @@ phsvds_status phsvds_default_opts(phsvds_opts* o) {
   o->mixed_inner = 1;
   o->inner_maxit = 60;
   o->inner_tol = 1e-3;
+  o->stage2_precond = 0;
+  o->precond_M = nullptr;
+  o->stage2_inner = 0;
+  o->inner2_maxit = 300;
+  o->inner2_patience = 25;
   return PHSVDS_OK;
 }
 
@@ -1840,6 +2064,17 @@ phsvds_status phsvds_create(phsvds_handle* out, int device, void* stream) {
     delete c;
     return PHSVDS_ERR_OOM;
   }
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = device;
+  if (cudaMemPoolCreate(&c->mempool, &props) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(c->mempool, cudaMemPoolAttrReleaseThreshold, &keep);
+  } else {
+    cudaGetLastError();
+    c->mempool = nullptr;  // fall back to the device's default pool
+  }
   *out = c;
   return PHSVDS_OK;
 }
@@ -1848,6 +2083,7 @@ void phsvds_destroy(phsvds_handle h) {
   if (!h) return;
   cudaSetDevice(h->device);
   cudaStreamSynchronize(h->stream);
+  if (h->mempool) cudaMemPoolDestroy(h->mempool);
   if (h->host) cudaFreeHost(h->host);
   if (h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
@@ -1890,17 +2126,34 @@ phsvds_status phsvds_solve(phsvds_handle h, int64_t m, int64_t n, int64_t nnz, c
   if (k < 1 || k > n || k >= o.min_restart || k + o.max_basis > LD)
     return set_err(h, PHSVDS_ERR_INVALID, "need 1 <= k <= n, k < min_restart and k + max_basis <= 64");
   if (o.block_size < 1 || o.block_size > 8 || o.max_basis < 4 || o.max_basis + 8 > LD ||
-      o.min_restart < 2 * std::min(o.block_size, k) || o.min_restart >= o.max_basis || !(tol > 0) ||
+      o.min_restart < 2 * std::min(o.block_size, k) ||
+      o.max_basis - o.min_restart < std::min(o.block_size, k) || !(tol > 0) ||
       o.max_restarts < 1 || (target != PHSVDS_SMALLEST && target != PHSVDS_LARGEST) ||
-      (precond != PHSVDS_PREC_NONE && precond != PHSVDS_PREC_JACOBI && precond != PHSVDS_PREC_LEARNED) ||
+      (precond != PHSVDS_PREC_NONE && precond != PHSVDS_PREC_JACOBI && precond != PHSVDS_PREC_LEARNED &&
+       precond != PHSVDS_PREC_GIVEN) ||
       o.max_basis > n)
-    return set_err(h, PHSVDS_ERR_INVALID, "invalid options (block 1..8, 2b <= min_restart < max_basis <= min(n,56))");
+    return set_err(h, PHSVDS_ERR_INVALID,
+                   "invalid options (block b in 1..8, 2b <= min_restart <= max_basis - b, max_basis <= min(n,56))");
   if (precond == PHSVDS_PREC_LEARNED &&
       (!o.learned_params || !o.learned_features || o.grid_nx < 1 || o.grid_ny < 1 ||
        (int64_t)o.grid_nx * o.grid_ny != n || o.stall_window < 0))
     return set_err(h, PHSVDS_ERR_INVALID, "learned correction needs params, features and grid_nx * grid_ny = n");
   if (o.record_r && (o.record_max < 0 || o.record_every < 1))
     return set_err(h, PHSVDS_ERR_INVALID, "recording needs record_max >= 0 and record_every >= 1");
+  if (o.stage2_precond != 0 && o.stage2_precond != 1)
+    return set_err(h, PHSVDS_ERR_INVALID, "stage2_precond must be 0 or 1");
+  if ((o.stage2_inner != 0 && o.stage2_inner != 1) || o.inner2_maxit < 1 || o.inner2_patience < 1 ||
+      (o.stage2_inner == 1 && (o.stage2_precond || precond == PHSVDS_PREC_GIVEN)))
+    return set_err(h, PHSVDS_ERR_INVALID,
+                   "stage2_inner must be 0 or 1 (1 not with a stage-2 preconditioner), inner2_maxit and "
+                   "inner2_patience >= 1");
+  if (precond == PHSVDS_PREC_GIVEN) {
+    if (!o.precond_M || m != n)
+      return set_err(h, PHSVDS_ERR_INVALID, "a given preconditioner needs opts.precond_M and a square A");
+    for (int64_t i = 0; i < n; ++i)
+      if (!std::isfinite(o.precond_M[i]) || o.precond_M[i] == 0.0)
+        return set_err(h, PHSVDS_ERR_INVALID, "precond_M must be finite and nonzero");
+  }
   if ((o.mixed_inner != 0 && o.mixed_inner != 1) || o.inner_maxit < 1 || !(o.inner_tol > 0) || o.inner_tol >= 1)
     return set_err(h, PHSVDS_ERR_INVALID, "mixed_inner must be 0 or 1, inner_maxit >= 1, 0 < inner_tol < 1");
   if (o.init_V && (o.init_nv < 0 || o.init_nv > o.max_basis || (o.init_nv == 0 && k > o.max_basis)))
@@ -2113,7 +2366,7 @@ extern "C" phsvds_status phsvds_normal_cg(phsvds_handle h, int64_t m, int64_t n,
   try {
     CUCHK(cudaSetDevice(h->device));
     cudaStream_t s = h->stream;
-    Pool pool(s);
+    Pool pool(s, h->mempool);
     DevA A;
     upload_matrix(h, pool, A, m, n, nnz, row_ptr, col_idx, val, ptr_on_device, false, false, 8);
     COp<double> op{&A.A64, &A.At64, A.Z64, A.n, 2};

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libphsvds.so")
 PHSVDS_OK, PHSVDS_ERR_INVALID, PHSVDS_ERR_NOT_CONVERGED, PHSVDS_ERR_BREAKDOWN = 0, 1, 2, 3
 PHSVDS_ERR_NAN, PHSVDS_ERR_TIMEOUT, PHSVDS_ERR_CUDA, PHSVDS_ERR_OOM = 4, 5, 6, 7
 SMALLEST, LARGEST = 0, 1
-PREC_NONE, PREC_JACOBI, PREC_LEARNED = 0, 1, 2
+PREC_NONE, PREC_JACOBI, PREC_LEARNED, PREC_GIVEN = 0, 1, 2, 3
 CNN_NPARAM = 3024
 
 
@@ -35,7 +35,9 @@ class Opts(C.Structure):
                 ("learned_params", C.c_void_p), ("learned_features", C.c_void_p), ("grid_nx", C.c_int),
                 ("grid_ny", C.c_int), ("stall_window", C.c_int), ("record_r", C.c_void_p), ("record_max", C.c_int),
                 ("record_every", C.c_int), ("projected_solver", C.c_int), ("init_V", C.c_void_p),
-                ("init_nv", C.c_int), ("mixed_inner", C.c_int), ("inner_maxit", C.c_int), ("inner_tol", C.c_double)]
+                ("init_nv", C.c_int), ("mixed_inner", C.c_int), ("inner_maxit", C.c_int), ("inner_tol", C.c_double),
+                ("stage2_precond", C.c_int), ("precond_M", C.c_void_p), ("stage2_inner", C.c_int),
+                ("inner2_maxit", C.c_int), ("inner2_patience", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -49,7 +51,8 @@ class Stats(C.Structure):
                 ("jacobi_dim_sum", C.c_int64), ("fell_back", C.c_int), ("fell_back_at", C.c_int64),
                 ("recorded", C.c_int64), ("stage1_stagnation_locks", C.c_int64), ("spmm_plan_cached", C.c_int),
                 ("class_flops", C.c_double * 12), ("class_bytes", C.c_double * 12), ("inner_solves", C.c_int64),
-                ("inner_steps", C.c_int64)]
+                ("inner_steps", C.c_int64), ("inner2_solves", C.c_int64), ("inner2_steps", C.c_int64),
+                ("spmm_schedule_f32", C.c_int)]
 
     def as_dict(self) -> dict:
         d = {}
@@ -184,12 +187,13 @@ def default_opts(**kw) -> Opts:
 
 def phsvds_solve(h: Handle, m, n, row_ptr, col_idx, val, k, target=SMALLEST, tol=1e-14,
                  precond=PREC_NONE, opts: Opts | None = None, on_device=False, want_vectors=True,
-                 raise_on_error=True, init_V=None):
+                 raise_on_error=True, init_V=None, precond_M=None):
     """phsvds_solve: k smallest / largest triplets of the m x n CSR matrix.
 
     row_ptr int64 (m+1), col_idx int32, val float64, as numpy arrays (host) or
     torch CUDA tensors (on_device=True).  init_V: optional n x c host array,
-    the initial guess of stage 1 (opts.init_V / init_nv).
+    the initial guess of stage 1 (opts.init_V / init_nv); precond_M: the
+    diagonal of a given M ~ A for precond=PREC_GIVEN (opts.precond_M).
     Returns (sigma, U, V, resid, stats, status).
     """
     nnz = int(row_ptr[-1]) if isinstance(row_ptr, np.ndarray) else int(row_ptr[-1].item())
@@ -200,6 +204,10 @@ def phsvds_solve(h: Handle, m, n, row_ptr, col_idx, val, k, target=SMALLEST, tol
     st = Stats()
     o = opts if opts is not None else default_opts()
     x0 = None
+    if precond_M is not None:
+        pm = np.ascontiguousarray(np.asarray(precond_M, dtype=np.float64))
+        o = Opts.from_buffer_copy(o)
+        o.precond_M = pm.ctypes.data
     if init_V is not None:
         x0 = np.asfortranarray(np.asarray(init_V, dtype=np.float64).reshape(n, -1))
         o2 = Opts.from_buffer_copy(o)

@@ -222,6 +222,14 @@ def test_not_converged_reports_status(h):
     assert status == native.PHSVDS_ERR_NOT_CONVERGED
 
 
+def test_basis_too_small_for_the_block(h):
+    """A restart must leave room for a whole block: min_restart + b <=
+    max_basis, else INVALID before anything runs."""
+    A = synth.random_sparse(60, 30, 5.0, 2, values="gaussian")
+    assert _status(h, A, 4, block_size=4, max_basis=14, min_restart=11) == native.PHSVDS_ERR_INVALID
+    assert _status(h, A, 4, block_size=4, max_basis=14, min_restart=10) == native.PHSVDS_OK
+
+
 def test_k_out_of_range(h):
     A = synth.random_sparse(60, 30, 5.0, 2, values="gaussian")
     assert _status(h, A, 8) == native.PHSVDS_ERR_INVALID      # k >= min_restart
