@@ -166,6 +166,28 @@ typedef struct {
     int stage2_inner;
     int inner2_maxit;
     int inner2_patience;
+    /* 1: Algorithm 3 (Sec. 4), dynamic switching between GD+k on C and on B
+     * under preconditioning (SMALLEST, FP64): runs of at most maxIter
+     * iterations alternate between C (with the shift-free form of the
+     * preconditioner: diag(C)^{-1} for PHSVDS_PREC_JACOBI, M^{-1} M^{-T} for
+     * PHSVDS_PREC_GIVEN, none for PHSVDS_PREC_NONE) and B (targets the
+     * positive eigenvalues nearest zero, preconditioner [0 A M; M A^T 0] or
+     * [0 M^{-1}; M^{-T} 0]), each from the other's approximations; the faster
+     * by the mean log-reduction of the residual per iteration runs again,
+     * maxIter = dyn_init_iter (default 50) x 2^j, j raised on a repeat and
+     * halved on a switch, at most dyn_max_switch (default 8) times; the end
+     * is B's result or the two-stage method from C's vectors
+     * (stats.dynamic_route). */
+    int dynamic;
+    int dyn_init_iter;
+    int dyn_max_switch;
+    /* 1 (default): a solve repeats bit for bit on the same device and build
+     * (every cross-block reduction sums in a fixed order, and the autotuner
+     * leaves out the fused SpMM schedule, whose atomics sum in arrival
+     * order); 0: the autotuner may take the fused schedule when it is
+     * faster (the triplets then vary in the last bits between runs, and the
+     * iteration counts a little). */
+    int deterministic;
 } phsvds_opts;
 
 typedef struct {
@@ -214,6 +236,12 @@ typedef struct {
     int64_t inner2_solves;     /* JDQMR corrections of stage 2 (opts.stage2_inner = 1) */
     int64_t inner2_steps;      /* ... and their MINRES steps (each one product with B) */
     int spmm_schedule_f32;     /* schedule of the FP32 products with C (mixed precision; 0 otherwise) */
+    /* opts.dynamic = 1: how Algorithm 3 ended (1 all found on C, then the
+     * two-stage method; 2 C faster: the two-stage method from C's vectors;
+     * 3 all found on B; 4 B faster: B to the end), its runs and switches */
+    int dynamic_route;
+    int dynamic_runs;
+    int dynamic_switches;
 } phsvds_stats;
 
 /* Create a context on CUDA device `device`.  cuda_stream: a cudaStream_t to run
@@ -226,7 +254,15 @@ phsvds_status phsvds_create(phsvds_handle* out, int device, void* cuda_stream);
 phsvds_status phsvds_default_opts(phsvds_opts* opts);
 
 /*
- * k smallest (target = PHSVDS_SMALLEST) or largest singular triplets of A.
+ * k smallest (target = PHSVDS_SMALLEST) or largest singular triplets of A
+ * (Section 1, eq. 1.1): stage 1 is Algorithm 1 (GD+k on C = A^T A to the
+ * tolerance delta_C of Section 3.1, then the Rayleigh-Ritz step of
+ * Algorithm 1 step 3); the switch test of Section 3.1 (delta < eps ||A|| /
+ * sigma_i, or a stage-1 residual above the tolerance) decides whether stage 2,
+ * Algorithm 2 (the refined projection on B of Section 3.2, initial guesses
+ * [v; A v / sigma] / sqrt(2) of Section 3.3), runs; a triplet is accepted
+ * when sqrt(||r_u||^2 + ||r_v||^2) <= tol ||A|| (Section 5), with ||A|| the
+ * largest Ritz value seen (Algorithm 1).
  *  m, n, nnz     : A is m x n (m >= n >= 1) with nnz stored entries;
  *  row_ptr       : m+1 int64 offsets; col_idx: nnz int32; val: nnz doubles (CSR);
  *  ptr_on_device : 1 if row_ptr/col_idx/val are device pointers, else host;

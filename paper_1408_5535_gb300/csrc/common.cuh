@@ -85,4 +85,5 @@ __device__ inline void atomic_add_row(T* p, const T (&r)[B]) {
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+
 }  // namespace ph

@@ -51,8 +51,10 @@ struct DotPairs {
 };
 
 template <int NP, int V>
-__global__ void __launch_bounds__(JD_T) k_col_dots(int n, int q, DotPairs<NP> pr, double* __restrict__ acc) {
+__global__ void __launch_bounds__(JD_T) k_col_dots(int n, int q, DotPairs<NP> pr, double* __restrict__ acc,
+                                                   RedWs rw) {
   __shared__ double red[NP * 8][JD_T / 32];
+  __shared__ double part[NP * 8];
   float s[NP][8];
 #pragma unroll
   for (int p = 0; p < NP; ++p)
@@ -82,13 +84,13 @@ __global__ void __launch_bounds__(JD_T) k_col_dots(int n, int q, DotPairs<NP> pr
     }
   __syncthreads();
   if (threadIdx.x < NP * 8) {
-    const int p = threadIdx.x / 8, c = threadIdx.x % 8;
-    if (c < q) {
-      double v = 0.0;
+    double v = 0.0;
+    if (threadIdx.x % 8 < q)
       for (int w = 0; w < JD_T / 32; ++w) v += red[threadIdx.x][w];
-      atomicAdd(&acc[p * 8 + c], v);
-    }
+    part[threadIdx.x] = v;
   }
+  __syncthreads();
+  ordered_commit(part, NP * 8, acc, 0, nullptr, rw);
 }
 
 // ---- MINRES state of the b systems: sc[field * 8 + c]
@@ -176,9 +178,11 @@ __global__ void __launch_bounds__(JD_T) k_jd_lanczos(int n, int q, int nl, const
                                                      const float* __restrict__ v, const float* __restrict__ X,
                                                      const float* __restrict__ Xl, const double* __restrict__ theta,
                                                      float* __restrict__ r1, float* __restrict__ r2,
-                                                     const double* __restrict__ sc, double* __restrict__ acc) {
+                                                     const double* __restrict__ sc, double* __restrict__ acc,
+                                                     RedWs rw) {
   __shared__ float cf[8][4];           // theta, e, c1, c2 per column
   __shared__ float D[64 * 8];
+  __shared__ double part[8];
   __shared__ double red[8][JD_T / 32];
   __shared__ int act[8];
   if (threadIdx.x < 8) {
@@ -248,11 +252,14 @@ __global__ void __launch_bounds__(JD_T) k_jd_lanczos(int n, int q, int nl, const
     if (lane == 0) red[c][warp] = t;
   }
   __syncthreads();
-  if (threadIdx.x < q) {
+  if (threadIdx.x < 8) {
     double t = 0.0;
-    for (int w = 0; w < JD_T / 32; ++w) t += red[threadIdx.x][w];
-    atomicAdd(&acc[24 + threadIdx.x], t);
+    if (threadIdx.x < q)
+      for (int w = 0; w < JD_T / 32; ++w) t += red[threadIdx.x][w];
+    part[threadIdx.x] = t;
   }
+  __syncthreads();
+  ordered_commit(part, 8, acc + 24, 0, nullptr, rw);
 }
 
 // The Givens step of MINRES for each active system: the previous rotation
@@ -357,11 +364,14 @@ void jd_colnorms(cudaStream_t s, int n, int q, const float* R, double* acc) {
   ProfScope ps(s, PROF_F32 + PROF_SMALL);
   DotPairs<1> pr{{R}, {R}};
   const int V = jd_vec(n);
+  const int g = jd_grid(n, V);
+  const RedWs rw = red_ws((size_t)g * 8);
   if (V == 4)
-    k_col_dots<1, 4><<<jd_grid(n, 4), JD_T, 0, s>>>(n, q, pr, acc + 24);
+    k_col_dots<1, 4><<<g, JD_T, 0, s>>>(n, q, pr, acc + 24, rw);
   else
-    k_col_dots<1, 1><<<jd_grid(n, 1), JD_T, 0, s>>>(n, q, pr, acc + 24);
+    k_col_dots<1, 1><<<g, JD_T, 0, s>>>(n, q, pr, acc + 24, rw);
   count_launch();
+  reduce_partials(s, rw, g, 8, acc + 24, 0, nullptr);
 }
 
 void jd_init(cudaStream_t s, int n, int q, const float* R, float* r1, float* r2, float* v, float* sol, float* w1,
@@ -378,11 +388,14 @@ void jd_init(cudaStream_t s, int n, int q, const float* R, float* r1, float* r2,
 void jd_dots(cudaStream_t s, int n, int q, const float* v, const float* X, const float* Cv, double* acc) {
   ProfScope ps(s, PROF_F32 + PROF_SMALL);
   DotPairs<3> pr{{v, v, X}, {Cv, v, Cv}};
-  if (jd_vec(n) == 4)
-    k_col_dots<3, 4><<<jd_grid(n, 4), JD_T, 0, s>>>(n, q, pr, acc);
+  const int V = jd_vec(n), g = jd_grid(n, V);
+  const RedWs rw = red_ws((size_t)g * 24);
+  if (V == 4)
+    k_col_dots<3, 4><<<g, JD_T, 0, s>>>(n, q, pr, acc, rw);
   else
-    k_col_dots<3, 1><<<jd_grid(n, 1), JD_T, 0, s>>>(n, q, pr, acc);
+    k_col_dots<3, 1><<<g, JD_T, 0, s>>>(n, q, pr, acc, rw);
   count_launch();
+  reduce_partials(s, rw, g, 24, acc, 0, nullptr);
   count_work(PROF_F32 + PROF_SMALL, 6.0 * n * q, 4.0 * 3 * n * q);
 }
 
@@ -393,11 +406,13 @@ void jd_step(cudaStream_t s, int n, int q, int nl, const float* Cv, float* v, co
   k_jd_coef<<<1, 32, 0, s>>>(q, acc, theta, sc); count_launch();
   const int V = jd_vec(n);
   const int g = jd_grid(n, V);
+  const RedWs rw = red_ws((size_t)g * 8);
   if (V == 4)
-    k_jd_lanczos<4><<<g, JD_T, 0, s>>>(n, q, nl, Cv, v, X, Xl, theta, r1, r2, sc, acc);
+    k_jd_lanczos<4><<<g, JD_T, 0, s>>>(n, q, nl, Cv, v, X, Xl, theta, r1, r2, sc, acc, rw);
   else
-    k_jd_lanczos<1><<<g, JD_T, 0, s>>>(n, q, nl, Cv, v, X, Xl, theta, r1, r2, sc, acc);
+    k_jd_lanczos<1><<<g, JD_T, 0, s>>>(n, q, nl, Cv, v, X, Xl, theta, r1, r2, sc, acc, rw);
   count_launch();
+  reduce_partials(s, rw, g, 8, acc + 24, 0, nullptr);
   k_jd_givens<<<1, 32, 0, s>>>(q, acc, tol, sc); count_launch();
   if (V == 4)
     k_jd_update<4><<<g, JD_T, 0, s>>>(n, q, v, r2, w1, w2, sol, sc);
@@ -432,10 +447,14 @@ __global__ void __launch_bounds__(JD_T) k_s2_lanczos(int64_t N, int nq, const do
                                                      const double* __restrict__ v, const double* __restrict__ Q,
                                                      const double* __restrict__ mu, double* __restrict__ r1,
                                                      double* __restrict__ r2, const double* __restrict__ sc,
-                                                     double* __restrict__ acc) {
+                                                     double* __restrict__ acc, RedWs rw) {
   __shared__ double g[65];
   __shared__ double red[JD_T / 32];
-  if (SC1(JF_ACT) <= 0.0) return;
+  __shared__ double part[1];
+  if (SC1(JF_ACT) <= 0.0) {
+    ordered_commit_zero(1, rw);
+    return;
+  }
   for (int l = threadIdx.x; l < nq; l += JD_T) g[l] = acc[32 + l];
   __syncthreads();
   const double m = mu[0], c1 = SC1(JF_C1), c2 = SC1(JF_C2);
@@ -455,8 +474,10 @@ __global__ void __launch_bounds__(JD_T) k_s2_lanczos(int64_t N, int nq, const do
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < JD_T / 32; ++w) t += red[w];
-    atomicAdd(&acc[24], t);
+    part[0] = t;
   }
+  __syncthreads();
+  ordered_commit(part, 1, acc + 24, 0, nullptr, rw);
 }
 
 // MINRES update of t and, by the same recurrence, of B t; v <- r2 / beta; then
@@ -467,10 +488,14 @@ __global__ void __launch_bounds__(JD_T) k_s2_update(int64_t N, double* __restric
                                                     double* __restrict__ Bw1, double* __restrict__ Bw2,
                                                     double* __restrict__ Bt, const double* __restrict__ x,
                                                     const double* __restrict__ Bx, const double* __restrict__ sc,
-                                                    double* __restrict__ acc) {
+                                                    double* __restrict__ acc, RedWs rw) {
   __shared__ double red[2][JD_T / 32];
+  __shared__ double part[2];
   const double act = SC1(JF_ACT);
-  if (act == 0.0) return;
+  if (act == 0.0) {
+    ordered_commit_zero(2, rw);
+    return;
+  }
   const double oldeps = SC1(JF_OLDEPS), delta = SC1(JF_DELTA), ig = 1.0 / SC1(JF_GAMMA), phi = SC1(JF_PHI);
   const double beta = SC1(JF_BETA);
   const double ib = (act > 0.0 && beta > 0.0) ? 1.0 / beta : 0.0;
@@ -500,17 +525,24 @@ __global__ void __launch_bounds__(JD_T) k_s2_update(int64_t N, double* __restric
   if (threadIdx.x < 2) {
     double u = 0.0;
     for (int w = 0; w < JD_T / 32; ++w) u += red[threadIdx.x][w];
-    atomicAdd(&acc[160 + threadIdx.x], u);
+    part[threadIdx.x] = u;
   }
+  __syncthreads();
+  ordered_commit(part, 2, acc + 160, 0, nullptr, rw);
 }
 
 // acc[162] += ||B z - rho z||^2, rho = acc[161] / acc[160] (a second pass: the
 // short form ||Bz||^2 - rho^2 ||z||^2 would cancel far above the tolerance)
 __global__ void __launch_bounds__(JD_T) k_s2_eta(int64_t N, const double* __restrict__ x, const double* __restrict__ t,
                                                  const double* __restrict__ Bx, const double* __restrict__ Bt,
-                                                 const double* __restrict__ sc, double* __restrict__ acc) {
+                                                 const double* __restrict__ sc, double* __restrict__ acc,
+                                                 RedWs rw) {
   __shared__ double red[JD_T / 32];
-  if (SC1(JF_ACT) == 0.0) return;
+  __shared__ double part[1];
+  if (SC1(JF_ACT) == 0.0) {
+    ordered_commit_zero(1, rw);
+    return;
+  }
   const double rho = acc[160] > 0.0 ? acc[161] / acc[160] : 0.0;
   double e = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)JD_T + threadIdx.x; i < N; i += (int64_t)gridDim.x * JD_T) {
@@ -523,8 +555,10 @@ __global__ void __launch_bounds__(JD_T) k_s2_eta(int64_t N, const double* __rest
   if (threadIdx.x == 0) {
     double u = 0.0;
     for (int w = 0; w < JD_T / 32; ++w) u += red[w];
-    atomicAdd(&acc[162], u);
+    part[0] = u;
   }
+  __syncthreads();
+  ordered_commit(part, 1, acc + 162, 0, nullptr, rw);
 }
 
 // The dynamic stop: best eta, the patience counter, the copy flag of this
@@ -601,10 +635,14 @@ void s2_step(cudaStream_t s, int64_t N, int nq, const double* Bv, double* v, con
   ProfScope ps(s, PROF_SMALL);
   const int g = s2_grid(N);
   k_jd_coef<<<1, 32, 0, s>>>(1, acc, mu, sc); count_launch();
-  k_s2_lanczos<<<g, JD_T, 0, s>>>(N, nq, Bv, v, Q, mu, r1, r2, sc, acc); count_launch();
+  const RedWs rw1 = red_ws((size_t)g), rw2 = red_ws((size_t)g * 2);
+  k_s2_lanczos<<<g, JD_T, 0, s>>>(N, nq, Bv, v, Q, mu, r1, r2, sc, acc, rw1); count_launch();
+  reduce_partials(s, rw1, g, 1, acc + 24, 0, nullptr);
   k_jd_givens<<<1, 32, 0, s>>>(1, acc, 1e-15, sc); count_launch();
-  k_s2_update<<<g, JD_T, 0, s>>>(N, v, r2, w1, w2, t, Bv, Bw1, Bw2, Bt, x, Bx, sc, acc); count_launch();
-  k_s2_eta<<<g, JD_T, 0, s>>>(N, x, t, Bx, Bt, sc, acc); count_launch();
+  k_s2_update<<<g, JD_T, 0, s>>>(N, v, r2, w1, w2, t, Bv, Bw1, Bw2, Bt, x, Bx, sc, acc, rw2); count_launch();
+  reduce_partials(s, rw2, g, 2, acc + 160, 0, nullptr);
+  k_s2_eta<<<g, JD_T, 0, s>>>(N, x, t, Bx, Bt, sc, acc, rw1); count_launch();
+  reduce_partials(s, rw1, g, 1, acc + 162, 0, nullptr);
   k_s2_track<<<1, 32, 0, s>>>(acc, eta_tol, patience, maxit, sc); count_launch();
   k_s2_copy<<<g, JD_T, 0, s>>>(N, t, tbest, sc); count_launch();
   k_jd_retire<<<1, 32, 0, s>>>(1, sc); count_launch();

@@ -1176,8 +1176,16 @@ void symmetrise(cudaStream_t s, int j, double* A, int lda) {
 __global__ void k_order(int j, const double* __restrict__ th, int mode, double shift, int* __restrict__ order) {
   const int i = threadIdx.x;
   if (i >= j) return;
+  // mode 3 (the positive eigenvalues of B nearest zero): ascending among the
+  // values above 1e-12 of the largest magnitude, the others after them
+  double big = 0.0;
+  if (mode == 3)
+    for (int t = 0; t < j; ++t) big = fmax(big, fabs(th[t]));
   auto key = [&](int t) {
-    const double k = mode == 0 ? th[t] : (mode == 1 ? -th[t] : fabs(th[t] - shift));
+    const double k = mode == 0 ? th[t]
+                   : mode == 1 ? -th[t]
+                   : mode == 2 ? fabs(th[t] - shift)
+                               : (th[t] > 1e-12 * big ? th[t] : INFINITY);
     return isnan(k) ? INFINITY : k;
   };
   const double ki = key(i);

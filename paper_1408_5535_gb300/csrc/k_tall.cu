@@ -34,6 +34,27 @@ constexpr int CG_PC = CG_MAXP / (CG_THREADS / 32);  // columns per warp
 
 __device__ inline double atomic_add_f64(double* p, double v) { return atomicAdd(p, v); }
 
+__global__ void k_reduce_partials(const double* __restrict__ ws, int blocks, int n1, double* __restrict__ out1,
+                                  int n2, double* __restrict__ out2) {
+  const int no = n1 + n2;
+  const int o = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (o >= no) return;
+  double acc = 0.0;
+  for (int b = lane; b < blocks; b += 32) acc += ws[(size_t)b * no + o];
+  acc = warp_sum(acc);
+  if (lane == 0) {
+    if (o < n1)
+      out1[o] += acc;
+    else
+      out2[o - n1] += acc;
+  }
+}
+void reduce_partials(cudaStream_t s, RedWs rw, int blocks, int n1, double* out1, int n2, double* out2) {
+  const int no = n1 + n2;
+  if (!rw.ws || no <= 0) return;
+  k_reduce_partials<<<ceil_div(no, 8), 256, 0, s>>>(rw.ws, blocks, n1, out1, n2, out2); count_launch();
+}
+
 // 16-byte asynchronous copy global -> shared (no register staging, so a
 // thread can keep many in flight), and the wait for all of this thread's.
 __device__ inline void cp_async16(void* smem, const void* gmem) {
@@ -133,8 +154,9 @@ __device__ __forceinline__ void reduce_scatter(T (&v)[N], int lane) {
 template <typename T, int Q>
 __global__ void __launch_bounds__(CG_THREADS) k_cgs_pass(int n, Basis<T> P, T* __restrict__ Tb, int ldt, int q,
                                                          const double* __restrict__ Gsub, double* __restrict__ Gout,
-                                                         double* __restrict__ Tout, int rows, bool vec) {
+                                                         double* __restrict__ Tout, int rows, bool vec, RedWs rw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double part[CG_MAXP * 8 + 64];               // the block's Gout and Tout partials
   const int p = P.cols();
   T* Ps = reinterpret_cast<T*>(smem_raw);                 // [p][rows]
   T* Ts = Ps + (size_t)p * rows;                           // [Q][rows]
@@ -219,7 +241,8 @@ __global__ void __launch_bounds__(CG_THREADS) k_cgs_pass(int n, Basis<T> P, T* _
     }
     __syncthreads();
   }
-  // ---- reduce and accumulate into the FP64 outputs
+  // ---- reduce within the block (fixed order), then across blocks
+  const int n1 = Gout ? p * q : 0, n2 = Tout ? q * q : 0;
   if (Gout) {
     constexpr int NV = CG_PC * Q;
     constexpr int PER = NV >= 32 ? NV / 32 : 1;   // sums held per lane
@@ -232,7 +255,7 @@ __global__ void __launch_bounds__(CG_THREADS) k_cgs_pass(int n, Basis<T> P, T* _
         const int idx = NV >= 32 ? lane * PER + u : lane / REP;
         const int a = idx / Q, r = idx % Q;
         const int c = warp + a * (CG_THREADS / 32);
-        if (c < p && r < q) atomic_add_f64(&Gout[c + (size_t)r * p], (double)v[u]);
+        if (c < p && r < q) part[c + r * p] = (double)v[u];
       }
     }
   }
@@ -245,12 +268,14 @@ __global__ void __launch_bounds__(CG_THREADS) k_cgs_pass(int n, Basis<T> P, T* _
         if (k % 8 == warp) {
           double v = (double)warp_sum(accT[k / 8]);
           if (lane == 0 && s2 < q) {
-            atomic_add_f64(&Tout[r + s2 * q], v);
-            if (s2 != r) atomic_add_f64(&Tout[s2 + r * q], v);
+            part[n1 + r + s2 * q] = v;
+            if (s2 != r) part[n1 + s2 + r * q] = v;
           }
         }
       }
   }
+  __syncthreads();
+  if (n1 + n2) ordered_commit(part, n1, Gout, n2, Tout, rw);
 }
 
 template <typename T, int Q>
@@ -272,7 +297,10 @@ static void cgs_launch(cudaStream_t s, int n, const Basis<T>& P, T* Tb, int ldt,
   if (grid > cap) grid = cap;
   if (grid < 1) grid = 1;
   const bool vec = cols16(P.p1, P.ld1) && cols16(P.p2, P.ld2);
-  k_cgs_pass<T, Q><<<grid, CG_THREADS, smem, s>>>(n, P, Tb, ldt, q, Gsub, Gout, Tout, rows, vec); count_launch();
+  const int n1 = (Gout && p > 0) ? p * q : 0, n2 = Tout ? q * q : 0;
+  const RedWs rw = red_ws((size_t)grid * (n1 + n2));
+  k_cgs_pass<T, Q><<<grid, CG_THREADS, smem, s>>>(n, P, Tb, ldt, q, Gsub, Gout, Tout, rows, vec, rw); count_launch();
+  reduce_partials(s, rw, grid, n1, Gout, n2, Tout);
   count_work(pcat<T>(PROF_GRAM),
              2.0 * n * p * q * ((Gsub ? 1 : 0) + (Gout ? 1 : 0)) + (Tout ? (double)n * q * (q + 1) : 0.0),
              (double)sizeof(T) * n * ((Gsub || Gout ? p : 0) + q * (Gsub ? 2 : 1)));
@@ -302,8 +330,10 @@ template <typename T>
 __global__ void __launch_bounds__(TS_ROWS) k_tall_small(int n, const T* P, int ldp, int p,
                                                         const double* __restrict__ Y, int ldy, int r, T* Out,
                                                         int ldo, const T* __restrict__ Xs, int ldx,
-                                                        const double* __restrict__ theta, double* norms2, bool vec) {
+                                                        const double* __restrict__ theta, double* norms2, bool vec,
+                                                        RedWs rw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double wn[64][TS_ROWS / 32];                 // per-warp partial norms (fixed order)
   const int rp = (r + TS_CB - 1) / TS_CB * TS_CB;                 // r padded to whole column blocks
   double* nrm = reinterpret_cast<double*>(smem_raw);            // [r]
   T* Ys = reinterpret_cast<T*>(smem_raw + sizeof(double) * (size_t)((r + 1) & ~1));  // [p][rp] row-major
@@ -314,7 +344,7 @@ __global__ void __launch_bounds__(TS_ROWS) k_tall_small(int n, const T* P, int l
     Ys[k] = c < r ? (T)Y[a + (size_t)c * ldy] : T(0);
   }
   if (norms2)
-    for (int c = tid; c < r; c += blockDim.x) nrm[c] = 0.0;
+    for (int c = tid; c < 64 * (TS_ROWS / 32); c += blockDim.x) wn[c / (TS_ROWS / 32)][c % (TS_ROWS / 32)] = 0.0;
   __syncthreads();
   const int R = blockDim.x;
   const int nchunks = (n + R - 1) / R;
@@ -347,7 +377,7 @@ __global__ void __launch_bounds__(TS_ROWS) k_tall_small(int n, const T* P, int l
           if (act) Out[(size_t)c * ldo + i] = o;
           if (norms2) {
             double v = warp_sum((double)o * (double)o);
-            if ((tid & 31) == 0) atomicAdd(&nrm[c], v);
+            if ((tid & 31) == 0) wn[c][tid >> 5] += v;
           }
         }
       }
@@ -356,7 +386,13 @@ __global__ void __launch_bounds__(TS_ROWS) k_tall_small(int n, const T* P, int l
   }
   if (norms2) {
     __syncthreads();
-    for (int c = tid; c < r; c += blockDim.x) atomicAdd(&norms2[c], nrm[c]);
+    for (int c = tid; c < r; c += blockDim.x) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wn[c][w];
+      nrm[c] = t;
+    }
+    __syncthreads();
+    ordered_commit(nrm, r, norms2, 0, nullptr, rw);
   }
 }
 
@@ -376,8 +412,10 @@ void tall_times_small(cudaStream_t s, int n, const T* P, int ldp, int p, const d
   int grid = ceil_div(n, R);
   const int cap = num_sms() * 8;
   if (grid > cap) grid = cap;
+  const RedWs rw = norms2 ? red_ws((size_t)grid * r) : RedWs{};
   k_tall_small<T><<<grid, R, smem, s>>>(n, P, ldp, p, Y, ldy, r, Out, ldo, Xs, ldx, theta, norms2,
-                                        cols16(P, ldp)); count_launch();
+                                        cols16(P, ldp), rw); count_launch();
+  if (norms2) reduce_partials(s, rw, grid, r, norms2, 0, nullptr);
   count_work(pcat<T>(PROF_TALL), 2.0 * n * p * r + (theta ? 2.0 * n * r : 0.0) + (norms2 ? 2.0 * n * r : 0.0),
              (double)sizeof(T) * n * (p + r + (theta ? r : 0)));
 }
@@ -438,7 +476,9 @@ __device__ inline double guarded(double d, double guard) {
 template <typename T>
 __global__ void k_jacobi_dots(int n, const double* __restrict__ d, const T* __restrict__ X, int ldx,
                               const T* __restrict__ R, int ldr, int q, const double* __restrict__ theta, double guard,
-                              double* dots) {
+                              double* dots, RedWs rw) {
+  __shared__ double wp[16][8];
+  __shared__ double part[16];
   double a[8], b[8];
   for (int c = 0; c < q; ++c) a[c] = b[c] = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -452,10 +492,18 @@ __global__ void k_jacobi_dots(int n, const double* __restrict__ d, const T* __re
   for (int c = 0; c < q; ++c) {
     double va = warp_sum(a[c]), vb = warp_sum(b[c]);
     if ((threadIdx.x & 31) == 0) {
-      atomicAdd(&dots[2 * c], va);
-      atomicAdd(&dots[2 * c + 1], vb);
+      wp[2 * c][threadIdx.x >> 5] = va;
+      wp[2 * c + 1][threadIdx.x >> 5] = vb;
     }
   }
+  __syncthreads();
+  if (threadIdx.x < 2 * q) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wp[threadIdx.x][w];
+    part[threadIdx.x] = t;
+  }
+  __syncthreads();
+  ordered_commit(part, 2 * q, dots, 0, nullptr, rw);
 }
 template <typename T>
 __global__ void k_jacobi_apply(int n, const double* __restrict__ d, const T* __restrict__ X, int ldx,
@@ -474,7 +522,10 @@ void jacobi_dots(cudaStream_t s, int n, const double* d, const T* X, int ldx, co
                  const double* theta, double guard, double* dots) {
   int grid = ceil_div(n, 256);
   if (grid > num_sms() * 4) grid = num_sms() * 4;
-  if (n > 0) k_jacobi_dots<T><<<grid, 256, 0, s>>>(n, d, X, ldx, R, ldr, q, theta, guard, dots); count_launch();
+  if (n <= 0) return;
+  const RedWs rw = red_ws((size_t)grid * 2 * q);
+  k_jacobi_dots<T><<<grid, 256, 0, s>>>(n, d, X, ldx, R, ldr, q, theta, guard, dots, rw); count_launch();
+  reduce_partials(s, rw, grid, 2 * q, dots, 0, nullptr);
 }
 template <typename T>
 void jacobi_apply(cudaStream_t s, int n, const double* d, const T* X, int ldx, const T* R, int ldr, int q,
@@ -514,7 +565,9 @@ void axpby(cudaStream_t s, int64_t n, double a, const double* x, double b, doubl
 }
 
 template <typename T>
-__global__ void k_colnorms(int n, const T* __restrict__ X, int ldx, int q, double* norms2) {
+__global__ void k_colnorms(int n, const T* __restrict__ X, int ldx, int q, double* norms2, RedWs rw) {
+  __shared__ double wp[8][8];
+  __shared__ double part[8];
   double a[8];
   for (int c = 0; c < q; ++c) a[c] = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
@@ -524,27 +577,51 @@ __global__ void k_colnorms(int n, const T* __restrict__ X, int ldx, int q, doubl
     }
   for (int c = 0; c < q; ++c) {
     double v = warp_sum(a[c]);
-    if ((threadIdx.x & 31) == 0) atomicAdd(&norms2[c], v);
+    if ((threadIdx.x & 31) == 0) wp[c][threadIdx.x >> 5] = v;
   }
+  __syncthreads();
+  if (threadIdx.x < q) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wp[threadIdx.x][w];
+    part[threadIdx.x] = t;
+  }
+  __syncthreads();
+  ordered_commit(part, q, norms2, 0, nullptr, rw);
 }
 template <typename T> void col_norms2_dense(cudaStream_t s, int n, const T* X, int ldx, int q, double* norms2) {
   int grid = ceil_div(n, 256);
   if (grid > num_sms() * 4) grid = num_sms() * 4;
-  if (n > 0) k_colnorms<T><<<grid, 256, 0, s>>>(n, X, ldx, q, norms2); count_launch();
+  if (n <= 0) return;
+  const RedWs rw = red_ws((size_t)grid * q);
+  k_colnorms<T><<<grid, 256, 0, s>>>(n, X, ldx, q, norms2, rw); count_launch();
+  reduce_partials(s, rw, grid, q, norms2, 0, nullptr);
 }
 
 // out[0] += x^T y (FP64)
-__global__ void k_dot(int64_t n, const double* __restrict__ x, const double* __restrict__ y, double* out) {
+__global__ void k_dot(int64_t n, const double* __restrict__ x, const double* __restrict__ y, double* out, RedWs rw) {
+  __shared__ double wp[8];
+  __shared__ double part[1];
   double a = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     a = fma(x[i], y[i], a);
   a = warp_sum(a);
-  if ((threadIdx.x & 31) == 0) atomicAdd(out, a);
+  if ((threadIdx.x & 31) == 0) wp[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wp[w];
+    part[0] = t;
+  }
+  __syncthreads();
+  ordered_commit(part, 1, out, 0, nullptr, rw);
 }
 void dot_accum(cudaStream_t s, int64_t n, const double* x, const double* y, double* out) {
   int grid = ceil_div(n, 256);
   if (grid > num_sms() * 4) grid = num_sms() * 4;
-  if (n > 0) k_dot<<<grid, 256, 0, s>>>(n, x, y, out); count_launch();
+  if (n <= 0) return;
+  const RedWs rw = red_ws((size_t)grid);
+  k_dot<<<grid, 256, 0, s>>>(n, x, y, out, rw); count_launch();
+  reduce_partials(s, rw, grid, 1, out, 0, nullptr);
 }
 // y = x / d elementwise; a |d| below guard is raised to +-guard (guard 0: none)
 __global__ void k_diag_div(int64_t n, const double* __restrict__ x, const double* __restrict__ d, double guard,

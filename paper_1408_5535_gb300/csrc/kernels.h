@@ -40,6 +40,42 @@ struct SparseView {
 
 int lanes_for(double avg_row);
 
+// Fixed-order reduction across thread blocks, so that repeated runs give the
+// same bits: block b stores its partial results at ws + b * (n1 + n2), and a
+// second launch (reduce_partials) adds them, in a fixed order, to
+// out1[0 .. n1) and out2[0 .. n2).  With ws null the partials are added with
+// atomics (order not fixed).  part: the block's partials in shared memory,
+// complete when called; every thread calls.
+struct RedWs {
+  double* ws = nullptr;
+};
+__device__ inline void ordered_commit(const double* part, int n1, double* out1, int n2, double* out2, RedWs rw) {
+  const int tid = threadIdx.x, nt = blockDim.x, no = n1 + n2;
+  if (!rw.ws) {
+    for (int o = tid; o < no; o += nt) atomicAdd(o < n1 ? &out1[o] : &out2[o - n1], part[o]);
+    return;
+  }
+  double* mine = rw.ws + (size_t)blockIdx.x * no;
+  for (int o = tid; o < no; o += nt) mine[o] = part[o];
+}
+// A block that has nothing to add still writes zeros to its slot (the second
+// launch reads every slot); every thread calls.
+__device__ inline void ordered_commit_zero(int no, RedWs rw) {
+  if (!rw.ws) return;
+  double* mine = rw.ws + (size_t)blockIdx.x * no;
+  for (int o = threadIdx.x; o < no; o += blockDim.x) mine[o] = 0.0;
+}
+// The second half: out1/out2 += the partials of the `blocks` blocks, one warp
+// per output (its lanes sum strided blocks, then a fixed butterfly), spread
+// over as many SMs as there are outputs.  No-op when rw.ws is null.
+void reduce_partials(cudaStream_t s, RedWs rw, int blocks, int n1, double* out1, int n2, double* out2);
+
+// The host thread's scratch of the fixed-order cross-block reductions (set
+// by a solve for its duration): {ws, counter} when it holds `doubles`, else
+// {nullptr, nullptr} (the kernels then reduce with atomics).
+RedWs red_ws(size_t doubles);
+void set_red_ws(double* ws, size_t cap);
+
 // Instrumentation (per host thread): kernel launch count, and optional CUDA
 // events around kernel classes when a solve runs with opts.profile = 1.
 // Classes 0-5 are the FP64 launches; 6-11 the same classes in FP32 storage.
@@ -188,6 +224,8 @@ void jacobi_eig32_ld(cudaStream_t s, int j, const double* H, int ldh, double* Sf
 void jacobi_svd_ld(cudaStream_t s, int j, double* G, int ldg, double* S, int lds, double* sig, double tol,
                    int max_sweeps, int* sweeps_out);
 void frame_append(cudaStream_t s, int j0, int nb, double* A, int lda, double* S, int lds, const double* Hn);
+// order[0..j) = the indices of th by key: mode 0 ascending, 1 descending, 2
+// by |th - shift|, 3 ascending among th > 1e-12 max |th| (the others last)
 void order_theta(cudaStream_t s, int j, const double* th, int mode, double shift, int* order);
 // bad (device int, may be null) is set when an index lies outside [0, j)
 void gather_cols(cudaStream_t s, int j, const double* S, int lds, const int* idx, int nc, double* out, int ldo,

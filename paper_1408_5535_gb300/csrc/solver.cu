@@ -78,8 +78,20 @@ struct Pool {
 // width (kept by the handle, reused by its later solves of that shape).
 struct SpmmPlan {
   int64_t m = 0, n = 0, nnz = 0;
-  int b = 0, bytes = 0;
+  int b = 0, bytes = 0, deterministic = 0;
   int schedule = 2, lanes = 0, lanes_a = 0, lanes_at = 0;
+};
+
+// The fixed-order reduction scratch of one solve (3 MiB from its pool) made
+// this host thread's for the scope's life; the previous scratch comes back
+// at the end (a solve inside Algorithm 3's driver).  A solve's reductions
+// are serial on its stream, so one scratch serves them all.
+constexpr size_t RED_WS_DOUBLES = 393216;
+struct RedScope {
+  RedWs prev;
+  size_t prev_cap;
+  RedScope(Pool& pool, cudaStream_t s);
+  ~RedScope();
 };
 
 }  // namespace ph
@@ -116,6 +128,14 @@ struct Host {
 static thread_local int64_t g_launch_count = 0;
 void count_launch() { ++g_launch_count; }
 static thread_local double g_work[2][PROF_NALL] = {};  // [0] flops, [1] bytes per kernel class
+// scratch of the fixed-order cross-block reductions of this host thread's solve
+static thread_local RedWs g_red{};
+static thread_local size_t g_red_cap = 0;
+RedWs red_ws(size_t doubles) { return doubles <= g_red_cap ? g_red : RedWs{}; }
+void set_red_ws(double* ws, size_t cap) {
+  g_red = RedWs{ws};
+  g_red_cap = ws ? cap : 0;
+}
 void count_work(int cat, double flops, double bytes) {
   g_work[0][cat] += flops;
   g_work[1][cat] += bytes;
@@ -185,6 +205,15 @@ static void sync(cudaStream_t s) {
 
 template <typename T> static void zero(cudaStream_t s, T* p, size_t count) {
   if (count) CUCHK(cudaMemsetAsync(p, 0, sizeof(T) * count, s));
+}
+
+RedScope::RedScope(Pool& pool, cudaStream_t s) : prev(g_red), prev_cap(g_red_cap) {
+  (void)s;
+  set_red_ws(pool.get<double>(RED_WS_DOUBLES), RED_WS_DOUBLES);
+}
+RedScope::~RedScope() {
+  g_red = prev;
+  g_red_cap = prev_cap;
 }
 
 // ---------------------------------------------------------------------------
@@ -271,6 +300,19 @@ template <typename T> struct COp {
   }
 };
 
+// B X = [A^T X_u; A X_v] on a row-major block of b vectors of length n + m
+// (the [v; u] order of the augmented vectors), as GD+k on B needs it
+// (Algorithm 3).
+struct BOp {
+  const SparseView<double>* A;
+  const SparseView<double>* At;
+  int m, n;
+  void apply(cudaStream_t s, int b, const double* X, double* Y) const {
+    csr_spmm<double>(s, *At, b, X + (size_t)n * b, Y);
+    csr_spmm<double>(s, *A, b, X, Y + (size_t)n * b);
+  }
+};
+
 // Mean time (ms) of f() over 3 launches after one warm-up, on stream s.
 template <typename F>
 static float time_launches(cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1, F&& f) {
@@ -302,7 +344,7 @@ static std::vector<int> lane_candidates(double avg, bool rows32) {
 // two-phase pair, on this matrix and block width, and keeps the fastest.
 template <typename T>
 static COp<T> autotune_spmm(cudaStream_t s, Pool& pool, const SparseView<T>& A, const SparseView<T>& At, T* Z, int n,
-                            int b) {
+                            int b, bool deterministic) {
   T* X = pool.get<T>((size_t)n * b);
   T* Y = pool.get<T>((size_t)n * b);
   fill_random<T>(s, n * b, X, 7, 0x77);
@@ -312,11 +354,14 @@ static COp<T> autotune_spmm(cudaStream_t s, Pool& pool, const SparseView<T>& A, 
   COp<T> best{&A, &At, Z, n, 2};
   float tbest = 1e30f;
   const bool rows32 = sizeof(T) * b == 32;
-  for (int l : lane_candidates(A.avg_row(), rows32)) {
-    COp<T> op{&A, &At, Z, n, 1, l};
-    const float t = time_launches(s, e0, e1, [&] { op.apply(s, b, X, Y); });
-    if (t < tbest) tbest = t, best = op;
-  }
+  // the fused schedule sums with atomics (order not fixed): only when results
+  // need not repeat bit for bit
+  if (!deterministic)
+    for (int l : lane_candidates(A.avg_row(), rows32)) {
+      COp<T> op{&A, &At, Z, n, 1, l};
+      const float t = time_launches(s, e0, e1, [&] { op.apply(s, b, X, Y); });
+      if (t < tbest) tbest = t, best = op;
+    }
   int la = 0, lat = 0;
   float ta = 1e30f, tat = 1e30f;
   for (int l : lane_candidates(A.avg_row(), rows32)) {
@@ -348,15 +393,16 @@ static inline int spmm_width(int nb) { return nb >= 8 ? 8 : nb >= 4 ? 4 : nb >= 
 // another matrix of the same shape costs at most speed.
 template <typename T>
 static COp<T> tuned_spmm(phsvds_ctx* ctx, Pool& pool, const SparseView<T>& A, const SparseView<T>& At, T* Z, int n,
-                         int b, bool* cached) {
+                         int b, bool* cached, bool deterministic) {
   for (const SpmmPlan& p : ctx->plans)
-    if (p.m == A.nrows && p.n == n && p.nnz == A.nnz && p.b == b && p.bytes == (int)sizeof(T)) {
+    if (p.m == A.nrows && p.n == n && p.nnz == A.nnz && p.b == b && p.bytes == (int)sizeof(T) &&
+        p.deterministic == (int)deterministic) {
       *cached = true;
       return COp<T>{&A, &At, Z, n, p.schedule, p.lanes, p.lanes_a, p.lanes_at};
     }
-  COp<T> op = autotune_spmm<T>(ctx->stream, pool, A, At, Z, n, b);
+  COp<T> op = autotune_spmm<T>(ctx->stream, pool, A, At, Z, n, b, deterministic);
   SpmmPlan p;
-  p.m = A.nrows, p.n = n, p.nnz = A.nnz, p.b = b, p.bytes = (int)sizeof(T);
+  p.m = A.nrows, p.n = n, p.nnz = A.nnz, p.b = b, p.bytes = (int)sizeof(T), p.deterministic = (int)deterministic;
   p.schedule = op.schedule, p.lanes = op.lanes, p.lanes_a = op.lanes_a, p.lanes_at = op.lanes_at;
   if (ctx->plans.size() >= 64) ctx->plans.erase(ctx->plans.begin());
   ctx->plans.push_back(p);
@@ -608,7 +654,54 @@ struct LearnedDev {
   int stall_window = 0;
 };
 
-template <typename T>
+// A preconditioner P ~ B^{-1} of Sec. 4 applied in the Olsen form (stage 2 and
+// the B runs of Algorithm 3): mode 1 [0 A M; M A^T 0] with M = diag(C)^{-1}
+// (pd = diag(C), |d| below pguard raised), mode 2 [0 M^{-1}; M^{-T} 0] from a
+// given diagonal M ~ A (pd = M, square A); vectors in the [v; u] order.
+struct BPrecond {
+  cudaStream_t s;
+  const DevA* A;
+  int mode = 0;
+  const double* pd = nullptr;
+  double pguard = 0.0;
+  double *Pr = nullptr, *Px = nullptr, *ptmp = nullptr, *pdots = nullptr;
+  void init(cudaStream_t st, Pool& pool, const DevA& a, int md, const double* d, double guard) {
+    s = st;
+    A = &a;
+    mode = md;
+    pd = d;
+    pguard = guard;
+    const size_t N = (size_t)a.m + a.n;
+    Pr = pool.get<double>(N);
+    Px = pool.get<double>(N);
+    ptmp = pool.get<double>((size_t)a.n);
+    pdots = pool.get<double>(2);
+  }
+  void apply(const double* y, double* Py) {
+    const int n = A->n;
+    if (mode == 1) {  // [M A^T y_u; A M y_v]
+      csr_spmm<double>(s, A->At64, 1, y + n, ptmp);
+      diag_div(s, n, ptmp, pd, pguard, Py);
+      diag_div(s, n, y, pd, pguard, ptmp);
+      csr_spmm<double>(s, A->A64, 1, ptmp, Py + n);
+    } else {           // [M^{-1} y_u; M^{-T} y_v] (m = n)
+      diag_div(s, n, y + n, pd, 0.0, Py);
+      diag_div(s, n, y, pd, 0.0, Py + n);
+    }
+  }
+  // t = P r - (x^T P r / x^T P x) P x
+  void olsen(const double* r, const double* x, double* t) {
+    const int64_t N = (int64_t)A->m + A->n;
+    apply(r, Pr);
+    apply(x, Px);
+    zero(s, pdots, 2);
+    dot_accum(s, N, x, Pr, pdots);
+    dot_accum(s, N, x, Px, pdots + 1);
+    olsen_combine(s, N, Pr, Px, pdots, t);
+  }
+};
+
+template <typename T, typename Op = COp<T>>
 struct Stage1 {
   phsvds_ctx* ctx;
   cudaStream_t s;
@@ -618,7 +711,7 @@ struct Stage1 {
   double delta, floor_eps;
   int precond;
   const double* diagC;
-  COp<T> op;
+  Op op;
   uint64_t seed;
   int max_restarts;
   double time_limit_s;
@@ -655,9 +748,25 @@ struct Stage1 {
   // the Olsen correction with a shift-free M (a preconditioner given by the
   // caller, M^{-1} M^{-T} of Sec. 4): diagC holds m_j^2 and theta is taken as 0
   bool shift_free = false;
+  // GD+k on B (the B runs of Algorithm 3): targets are the positive
+  // eigenvalues nearest zero (those above 1e-12 of the largest magnitude, so
+  // that the m - n zero eigenvalues of a rectangular A are not taken), a pair
+  // converges at ||r|| < delta ||A|| / sqrt(2), ||A|| the largest |theta| seen,
+  // and bp (if set) corrects in the Olsen form with a preconditioner of B
+  bool bmode = false;
+  BPrecond* bp = nullptr;
+  // bounded runs (Algorithm 3): stop after stop_after iterations (0: run to
+  // convergence) with partial = true and Xpart = the k current
+  // approximations (locked ones first, then the best unconverged Ritz
+  // vectors in target order); history = ||r|| of the first unconverged
+  // target at every iteration
+  int64_t stop_after = 0;
+  bool partial = false;
+  T* Xpart = nullptr;
+  std::vector<double> history;
 
   Stage1(phsvds_ctx* c, Pool& p, int n_, int k_, const phsvds_opts& o, bool largest_, double delta_, double eps,
-         int precond_, const double* diag, COp<T> op_)
+         int precond_, const double* diag, Op op_)
       : ctx(c), s(c->stream), pool(p), n(n_), k(k_), largest(largest_), delta(delta_), precond(precond_),
         diagC(diag), op(op_) {
     b = std::max(1, std::min(o.block_size, k));
@@ -814,6 +923,7 @@ struct Stage1 {
   }
 
   double tol_of(double th, double thmax) const {
+    if (bmode) return delta * thmax / std::sqrt(2.0);
     const double si = std::sqrt(std::max(th, 0.0)), sn = std::sqrt(std::max(thmax, 0.0));
     return std::max(delta * si * sn, floor_eps * thmax);
   }
@@ -840,8 +950,9 @@ struct Stage1 {
       // projected eigensolve: an FP32 bulk pass and an FP64 clean-up of the
       // target pairs when the targets are resolvable in FP32, else FP64
       // Jacobi throughout (GB300's FP64 latency is ~14x its FP32 latency)
-      const bool mixed_eig = eig_mode == 2 && (largest || eig32_ok);
-      const int ntg = std::min(b, k - nlock) + 1;
+      const bool mixed_eig = !bmode && eig_mode == 2 && (largest || eig32_ok);
+      const int ntg = bmode ? 0 : std::min(b, k - nlock) + 1;   // B: every pair to the tight threshold
+      const int omode = bmode ? 3 : (largest ? 1 : 0);
       const int nt = std::min(std::min(b, k - nlock), j);
       const bool sid = s_ident;
       double* hth = h.at<double>(0);        // bytes [0, 512)
@@ -859,7 +970,7 @@ struct Stage1 {
                                                                      flags + 12, JAC_REL, ntg, largest ? 1 : 0, 0.0,
                                                                      flags + 13);
         }
-        order_theta(s, j, theta, largest ? 1 : 0, 0.0, order);
+        order_theta(s, j, theta, omode, 0.0, order);
         gather_cols(s, j, S, LD, order, nt, Scols, LD, theta, thcols, flags + 14);
         tall_times_small<T>(s, n, V, n, j, Scols, LD, nt, Xr, n, nullptr, 0, nullptr, nullptr);
         zero(s, norms, nt);
@@ -870,7 +981,7 @@ struct Stage1 {
         CUCHK(cudaMemcpyAsync(h.at<int>(960), flags + 12, sizeof(int) * 8, cudaMemcpyDeviceToHost, s));
       };
       const uint64_t key = (uint64_t)j | ((uint64_t)nt << 8) | ((uint64_t)ntg << 16) | ((uint64_t)mixed_eig << 24) |
-                           ((uint64_t)sid << 25);
+                           ((uint64_t)sid << 25) | ((uint64_t)bmode << 26);
       graphs.run(s, key, segment);
       s_ident = false;
       sync(s);
@@ -889,7 +1000,7 @@ struct Stage1 {
         ord[i] = hord[i];
         thv[i] = hth[hord[i]];
         if (!std::isfinite(thv[i])) throw PhError{PHSVDS_ERR_NAN, "stage 1: non-finite Ritz value"};
-        out.theta_max = std::max(out.theta_max, thv[i]);
+        out.theta_max = std::max(out.theta_max, bmode ? std::fabs(thv[i]) : thv[i]);
       }
       {
         // the FP32-first projected solve resolves eigenvalues to ~1e-7 theta_max:
@@ -928,6 +1039,7 @@ struct Stage1 {
         stag_best = INFINITY;
         stag_it = out.iters;
       }
+      if (!unconv.empty()) history.push_back(std::sqrt(std::max(hn[unconv[0]], 0.0)));
       if (trace_on())
         fprintf(stderr, "s1[%d] it=%lld j=%d nlock=%d th0=%.17g rn0=%.6e thmax=%.6e nconv=%d\n", (int)sizeof(T),
                 (long long)out.iters, j, nlock, thv[0], std::sqrt(std::max(hn[0], 0.0)), out.theta_max,
@@ -962,6 +1074,22 @@ struct Stage1 {
         final_ord = ord;
         return;
       }
+      if (stop_after > 0 && out.iters >= stop_after) {
+        // the k current approximations: locked first, then the best
+        // unconverged Ritz vectors in target order
+        partial = true;
+        Xpart = pool.get<T>((size_t)n * k);
+        if (nlock) CUCHK(cudaMemcpyAsync(Xpart, Xl, sizeof(T) * (size_t)n * nlock, cudaMemcpyDeviceToDevice, s));
+        int* hi = h.at<int>(2048);
+        int nf = 0;
+        for (int i = 0; i < j && nf < k - nlock; ++i)
+          if (std::find(conv.begin(), conv.end(), i) == conv.end()) hi[nf++] = ord[i];
+        CUCHK(cudaMemcpyAsync(idx, hi, sizeof(int) * nf, cudaMemcpyHostToDevice, s));
+        gather_cols(s, j, S, LD, idx, nf, cand, LD, nullptr, nullptr);
+        tall_times_small<T>(s, n, V, n, j, cand, LD, nf, Xpart + (size_t)nlock * n, n, nullptr, 0, nullptr, nullptr);
+        sync(s);
+        return;
+      }
       // frame indices kept (sorted order), excluding the converged targets
       std::vector<int> keep;
       for (int i = 0; i < j; ++i)
@@ -991,6 +1119,10 @@ struct Stage1 {
         cnn_pack<T>(s, n, nu, Tb, n, lp->nrm2, lp->feat, lp->xin);
         cnn_forward(s, nu, lp->nx, lp->ny, lp->wf, lp->xin, lp->a1, lp->a2, lp->yout);
         cnn_unpack<T>(s, n, nu, lp->yout, Tb, n);
+      }
+      if constexpr (sizeof(T) == 8) {
+        if (bp && nu > 0)
+          for (int c = 0; c < nu; ++c) bp->olsen(Tb + (size_t)c * n, Xr + (size_t)unconv[c] * n, Tb + (size_t)c * n);
       }
       if (precond == PHSVDS_PREC_JACOBI && nu > 0) {
         double* hu = h.at<double>(1024);     // bytes [1024, 1088)
@@ -1281,14 +1413,8 @@ struct Stage2 {
   int j = 0, nl = 0;
   int64_t iters = 0, restarts = 0, mv = 0;
   std::vector<double> th_lock;
-  // correction operator P of B (Sec. 4), in the Olsen form t = P r - e P x:
-  // 0 none (t = r); 1 [0 A M; M A^T 0] with M = diag(C)^{-1} (pd = diag(C),
-  // |d| below pguard raised); 2 [0 M^{-1}; M^{-T} 0] from a given diagonal
-  // M ~ A (pd = M, square A)
-  int pmode = 0;
-  const double* pd = nullptr;
-  double pguard = 0.0;
-  double *Pr = nullptr, *Px = nullptr, *ptmp = nullptr, *pdots = nullptr;
+  // correction operator P of B (Sec. 4) in the Olsen form, or none (t = r)
+  BPrecond bpre;
   // deflated vectors: the locked ones, and with the JDQMR correction also the
   // mirror [v; -u] of each locked tiny pair (for sigma <= sqrt(eps) ||A|| the
   // pair +-sigma of B is not separable at the tolerance and both eigenvectors
@@ -1345,30 +1471,22 @@ struct Stage2 {
     }
   }
 
-  void set_precond(int mode, const double* d, double guard) {
-    pmode = mode;
-    pd = d;
-    pguard = guard;
-    if (mode && !Pr) {
-      Pr = pool.get<double>((size_t)N);
-      Px = pool.get<double>((size_t)N);
-      ptmp = pool.get<double>((size_t)n);
-      pdots = pool.get<double>(2);
-    }
-  }
+  void set_precond(int mode, const double* d, double guard) { bpre.init(s, pool, f.A, mode, d, guard); }
 
-  // Py = P y in the [v; u] order of the basis vectors
-  void apply_P(const double* y, double* Py) {
-    if (pmode == 1) {  // [M A^T y_u; A M y_v]
-      csr_spmm<double>(s, f.A.At64, 1, y + n, ptmp);
-      diag_div(s, n, ptmp, pd, pguard, Py);
-      diag_div(s, n, y, pd, pguard, ptmp);
-      csr_spmm<double>(s, f.A.A64, 1, ptmp, Py + n);
-      ++mv;
-    } else {           // [M^{-1} y_u; M^{-T} y_v] (m = n)
-      diag_div(s, n, y + n, pd, 0.0, Py);
-      diag_div(s, n, y, pd, 0.0, Py + n);
-    }
+  // The residual of a lock candidate afresh, ||B x - th x|| from a new product
+  // (into tv, free here): the estimate W s1 - th V s1 carries the rounding of
+  // every transform that W went through, which near eps ||A|| can sit on
+  // either side of the tolerance.
+  double fresh_resid(double th) {
+    Host h(ctx);
+    f.B(xr, tv);
+    ++mv;
+    axpby(s, N, -th, xr, 1.0, tv);
+    zero(s, nrm + 1, 1);
+    col_norms2_dense<double>(s, N, tv, N, 1, nrm + 1);
+    CUCHK(cudaMemcpyAsync(h.at<double>(24), nrm + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    sync(s);
+    return std::sqrt(std::max(*h.at<double>(24), 0.0));
   }
 
   // Append t (orthonormalised against [Xl | V]) as column j; W(:, j) = B v_j;
@@ -1496,10 +1614,13 @@ struct Stage2 {
       const double rn = std::sqrt(std::max(*h.at<double>(16), 0.0));
       if (!std::isfinite(th1) || !std::isfinite(rn)) throw PhError{PHSVDS_ERR_NAN, "stage 2: non-finite residual"};
       if (r0 < 0) r0 = rn;
+      const double tolB = delta * normA / std::sqrt(2.0);
+      // near the tolerance the estimate is checked against a fresh residual
+      const double rf = rn < 4.0 * tolB ? fresh_resid(th1) : -1.0;
       if (trace_on())
-        fprintf(stderr, "s2 it=%lld j=%d target=%d shift=%.17g th1=%.17g rn=%.6e sigmin=%.6e\n", (long long)iters, j,
-                target, shift, th1, rn, *h.at<double>(8));
-      if (rn < delta * normA / std::sqrt(2.0)) {
+        fprintf(stderr, "s2 it=%lld j=%d target=%d shift=%.17g th1=%.17g rn=%.6e rf=%.6e sigmin=%.6e\n",
+                (long long)iters, j, target, shift, th1, rn, rf, *h.at<double>(8));
+      if (rf >= 0.0 && rf < tolB) {
         CUCHK(cudaMemcpyAsync(Xl + (size_t)nl * N, xr, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
         CUCHK(cudaMemcpyAsync(D + (size_t)nd * N, xr, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
         ++nl;
@@ -1583,13 +1704,9 @@ struct Stage2 {
         CUCHK(cudaMemcpyAsync(D + (size_t)nd * N, xr, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
         const int taken = jd2->solve(ctx, D, nd + 1, xr, Bxr, th1, rr, delta * normA / std::sqrt(2.0), tv);
         mv += taken;
-      } else if (pmode) {
-        apply_P(rr, Pr);
-        apply_P(xr, Px);
-        zero(s, pdots, 2);
-        dot_accum(s, N, xr, Pr, pdots);
-        dot_accum(s, N, xr, Px, pdots + 1);
-        olsen_combine(s, N, Pr, Px, pdots, tv);
+      } else if (bpre.mode) {
+        bpre.olsen(rr, xr, tv);
+        if (bpre.mode == 1) mv += 2;   // one product with A and one with A^T for each of P r and P x
       } else {
         CUCHK(cudaMemcpyAsync(tv, rr, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
       }
@@ -1667,6 +1784,7 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
   const bool mixed = o.precision == PHSVDS_MIXED;
   const int b = std::max(1, std::min(o.block_size, k));
   Pool pool(s, ctx->mempool);
+  RedScope red(pool, s);
   DevA A;
   const int64_t launches0 = g_launch_count;
   const bool given = precond == PHSVDS_PREC_GIVEN;
@@ -1708,8 +1826,9 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
   COp<float> op32{&A.A32, &A.At32, A.Z32, A.n, (int)o.spmm};
   bool cached64 = false, cached32 = false;
   if (o.spmm == PHSVDS_SPMM_AUTO) {
-    op64 = tuned_spmm<double>(ctx, pool, A.A64, A.At64, A.Z64, A.n, spmm_width(b), &cached64);
-    if (mixed) op32 = tuned_spmm<float>(ctx, pool, A.A32, A.At32, A.Z32, A.n, spmm_width(b), &cached32);
+    op64 = tuned_spmm<double>(ctx, pool, A.A64, A.At64, A.Z64, A.n, spmm_width(b), &cached64, o.deterministic);
+    if (mixed)
+      op32 = tuned_spmm<float>(ctx, pool, A.A32, A.At32, A.Z32, A.n, spmm_width(b), &cached32, o.deterministic);
   }
   const int sch64 = op64.schedule;
   if (st) {
@@ -1964,6 +2083,251 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
   (void)iters32;
 }
 
+// ---------------------------------------------------------------------------
+// Algorithm 3 (Sec. 4): dynamic switching between GD+k on C and on B under
+// preconditioning, for the k smallest triplets
+// ---------------------------------------------------------------------------
+// Runs alternate between GD+k on C (the stage-1 operator with the shift-free
+// preconditioner of its family) and GD+k on B (targets: the positive
+// eigenvalues nearest zero, with the B preconditioner of the same family),
+// each starting from the other's approximations ([v; A v / ||A v||] / sqrt 2
+// into B, the normalised v-part out of it); a run's rate is the mean slope of
+// log ||r|| of its first unconverged target.  The loop follows the
+// algorithm's steps (initial tests on C then B; the faster approach runs
+// again with maxIter doubled when it repeats and halved when it switches; a
+// run that locks a pair ends the deciding), and its end the four final
+// branches: all found on B; all found on C (the two-stage method from those
+// vectors); C faster (the two-stage method from C's current vectors); B
+// faster (B to the end).  The two-stage endings are the ordinary solve with
+// the current vectors as its initial guess (opts.init_V).
+static double convergence_rate(const std::vector<double>& hist) {
+  std::vector<double> h;
+  for (double x : hist)
+    if (x > 0) h.push_back(x);
+  if (h.size() < 2) return 0.0;
+  return (std::log(h.back()) - std::log(h.front())) / (double)(h.size() - 1);
+}
+
+static void dynamic_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const int64_t* rp, const int32_t* ci,
+                         const double* va, int on_dev, int k, double tol, phsvds_precond precond,
+                         const phsvds_opts& o, double* sigma, double* U, double* V, double* resid, phsvds_stats* st) {
+  using clk = std::chrono::steady_clock;
+  const auto tstart = clk::now();
+  cudaStream_t s = ctx->stream;
+  Pool pool(s, ctx->mempool);
+  RedScope red(pool, s);
+  DevA A;
+  const int64_t launches0 = g_launch_count;
+  const bool given = precond == PHSVDS_PREC_GIVEN, jac = precond == PHSVDS_PREC_JACOBI;
+  upload_matrix(ctx, pool, A, m, n, nnz, rp, ci, va, on_dev, false, jac, 8);
+  const int N = A.m + A.n;
+  const double tol_in = TOL_MARGIN * tol;
+  // the shift-free preconditioners of Sec. 4 in the Olsen form
+  double *Mdev = nullptr, *dC = nullptr;
+  BPrecond bpre;
+  if (given) {
+    Mdev = pool.get<double>(A.n);
+    dC = pool.get<double>(A.n);
+    CUCHK(cudaMemcpyAsync(Mdev, o.precond_M, sizeof(double) * A.n, cudaMemcpyHostToDevice, s));
+    square(s, A.n, Mdev, dC);                 // C: M^{-1} M^{-T} = diag(1 / m_j^2)
+    bpre.init(s, pool, A, 2, Mdev, 0.0);      // B: [0 M^{-1}; M^{-T} 0]
+  } else if (jac) {
+    dC = A.diagC;                              // C: diag(C)^{-1}
+    Host h(ctx);
+    // guard of the B form: eps * max diag(C)
+    double* gmax = pool.get<double>(1);
+    zero(s, gmax, 1);
+    col_norms2_dense<double>(s, A.n, A.diagC, A.n, 1, gmax);   // ||diag(C)||^2 >= max^2
+    CUCHK(cudaMemcpyAsync(h.at<double>(0), gmax, sizeof(double), cudaMemcpyDeviceToHost, s));
+    sync(s);
+    bpre.init(s, pool, A, 1, A.diagC, EPS64 * std::sqrt(*h.at<double>(0)));
+  }
+  const int prec1 = (given || jac) ? (int)PHSVDS_PREC_JACOBI : (int)PHSVDS_PREC_NONE;
+  const int b = std::max(1, std::min(o.block_size, k));
+  bool cached = false;
+  COp<double> opC = tuned_spmm<double>(ctx, pool, A.A64, A.At64, A.Z64, A.n, spmm_width(b), &cached,
+                                       o.deterministic);
+  BOp opB{&A.A64, &A.At64, A.m, A.n};
+  double* curX = pool.get<double>((size_t)A.n * k);
+  double* X0B = pool.get<double>((size_t)N * k);
+  double* nrm = pool.get<double>(2);
+  bool have_x = false;
+  double normA = 0.0;
+  int64_t iters_total = 0, mv_total = 0;
+  struct Run {
+    bool done = false;
+    int nconv = 0;
+    double rate = 0.0;
+    int64_t iters = 0;
+  };
+  double* Xfin = nullptr;   // B's final vectors (N x k) for the B endings
+  auto runC = [&](int64_t iters) {
+    Stage1<double> sC(ctx, pool, A.n, k, o, false, tol_in, EPS64, prec1, dC, opC);
+    sC.shift_free = true;
+    sC.stop_after = iters;
+    sC.run(have_x ? curX : nullptr, have_x ? k : 0);
+    sync(s);
+    Run r;
+    r.done = !sC.partial;
+    r.nconv = r.done ? k : sC.nlock;
+    r.rate = convergence_rate(sC.history);
+    r.iters = sC.out.iters;
+    CUCHK(cudaMemcpyAsync(curX, r.done ? sC.Xl : sC.Xpart, sizeof(double) * A.n * k, cudaMemcpyDeviceToDevice, s));
+    have_x = true;
+    normA = std::max(normA, std::sqrt(std::max(sC.out.theta_max, 0.0)));
+    iters_total += sC.out.iters;
+    mv_total += sC.out.mv;
+    return r;
+  };
+  auto runB = [&](int64_t iters) {
+    Host h(ctx);
+    if (have_x) {  // [v; A v / ||A v||] / sqrt(2)
+      for (int c = 0; c < k; ++c) {
+        double* xc = X0B + (size_t)c * N;
+        const double* vc = curX + (size_t)c * A.n;
+        CUCHK(cudaMemcpyAsync(xc, vc, sizeof(double) * A.n, cudaMemcpyDeviceToDevice, s));
+        csr_spmm<double>(s, A.A64, 1, vc, xc + A.n);
+        zero(s, nrm, 2);
+        col_norms2_dense<double>(s, A.n, xc, A.n, 1, nrm);
+        col_norms2_dense<double>(s, A.m, xc + A.n, A.m, 1, nrm + 1);
+        CUCHK(cudaMemcpyAsync(h.at<double>(0), nrm, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+        sync(s);
+        const double nv = std::sqrt(*h.at<double>(0)), nu = std::sqrt(*h.at<double>(8));
+        scal(s, A.n, nv > 0 ? 1.0 / (nv * std::sqrt(2.0)) : 0.0, nullptr, xc);
+        scal(s, A.m, nu > 0 ? 1.0 / (nu * std::sqrt(2.0)) : 0.0, nullptr, xc + A.n);
+      }
+    }
+    Stage1<double, BOp> sB(ctx, pool, N, k, o, false, tol_in, EPS64, PHSVDS_PREC_NONE, nullptr, opB);
+    sB.bmode = true;
+    sB.bp = bpre.mode ? &bpre : nullptr;
+    sB.stop_after = iters;
+    sB.run(have_x ? X0B : nullptr, have_x ? k : 0);
+    sync(s);
+    Run r;
+    r.done = !sB.partial;
+    r.nconv = r.done ? k : sB.nlock;
+    r.rate = convergence_rate(sB.history);
+    r.iters = sB.out.iters;
+    const double* X = r.done ? sB.Xl : sB.Xpart;
+    if (r.done) {
+      if (!Xfin) Xfin = pool.get<double>((size_t)N * k);
+      CUCHK(cudaMemcpyAsync(Xfin, X, sizeof(double) * N * k, cudaMemcpyDeviceToDevice, s));
+    }
+    for (int c = 0; c < k; ++c) {  // the normalised v-parts
+      CUCHK(cudaMemcpyAsync(curX + (size_t)c * A.n, X + (size_t)c * N, sizeof(double) * A.n,
+                            cudaMemcpyDeviceToDevice, s));
+      zero(s, nrm, 1);
+      col_norms2_dense<double>(s, A.n, curX + (size_t)c * A.n, A.n, 1, nrm);
+      CUCHK(cudaMemcpyAsync(h.at<double>(0), nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
+      sync(s);
+      const double nv = std::sqrt(*h.at<double>(0));
+      scal(s, A.n, nv > 0 ? 1.0 / nv : 0.0, nullptr, curX + (size_t)c * A.n);
+    }
+    have_x = true;
+    normA = std::max(normA, sB.out.theta_max);
+    iters_total += sB.out.iters;
+    mv_total += sB.out.mv;
+    return r;
+  };
+  const int init_iter = o.dyn_init_iter;
+  int runs = 0, switches = 0, jexp = 0;
+  int64_t max_iter = init_iter;
+  Run last_C = runC(init_iter), last_B = runB(init_iter);
+  runs = 2;
+  int num_conv = std::max(last_C.nconv, last_B.nconv);
+  char prev = 'B';
+  bool undecided = true;
+  while (switches < o.dyn_max_switch && undecided) {
+    const char choice = last_C.rate < last_B.rate ? 'C' : 'B';
+    if ((switches == 0 && num_conv > 0) || num_conv > 1) {
+      undecided = false;
+    } else {
+      jexp = choice == prev ? jexp + 1 : jexp / 2;   // Algorithm 3: double on a repeat, halve on a switch
+      max_iter = (int64_t)init_iter << jexp;
+    }
+    ++switches;
+    Run r = choice == 'C' ? runC(max_iter) : runB(max_iter);
+    ++runs;
+    (choice == 'C' ? last_C : last_B) = r;
+    num_conv = r.nconv;
+    prev = choice;
+    if (r.done) break;
+  }
+  const char faster = last_C.rate < last_B.rate ? 'C' : 'B';
+  const bool prev_done = prev == 'C' ? last_C.done : last_B.done;
+  int route;
+  if (prev_done && prev == 'B') {
+    route = 3;                                  // all found on B
+  } else if (prev_done && prev == 'C') {
+    route = 1;                                  // all found on C: the two-stage method from them
+  } else if (faster == 'C') {
+    route = 2;                                  // C faster: the two-stage method from C's vectors
+  } else {
+    route = 4;                                  // B faster: B to the end
+    Run r = runB(0);
+    ++runs;
+    (void)r;
+  }
+  if (route == 1 || route == 2) {
+    // the ordinary solve, warm-started from the current approximations
+    Host h(ctx);
+    std::vector<double> hx((size_t)A.n * k);
+    CUCHK(cudaMemcpyAsync(hx.data(), curX, sizeof(double) * A.n * k, cudaMemcpyDeviceToHost, s));
+    sync(s);
+    phsvds_opts o2 = o;
+    o2.dynamic = 0;
+    o2.init_V = hx.data();
+    o2.init_nv = k;
+    phsvds_precond p2 = precond;
+    solve_impl(ctx, m, n, nnz, rp, ci, va, on_dev, k, PHSVDS_SMALLEST, tol, p2, o2, sigma, U, V, resid, st);
+    if (st) {
+      st->iters_stage1 += iters_total;
+      st->matvecs_A += mv_total;
+      st->matvecs_At += mv_total;
+      st->dynamic_route = route;
+      st->dynamic_runs = runs;
+      st->dynamic_switches = switches;
+      st->t_total_ms = std::chrono::duration<double, std::milli>(clk::now() - tstart).count();
+    }
+    return;
+  }
+  // B endings: the triplets from the augmented vectors
+  double* Vd = pool.get<double>((size_t)A.n * k);
+  double* Ud = pool.get<double>((size_t)A.m * k);
+  for (int c = 0; c < k; ++c) {
+    CUCHK(cudaMemcpyAsync(Vd + (size_t)c * A.n, Xfin + (size_t)c * N, sizeof(double) * A.n,
+                          cudaMemcpyDeviceToDevice, s));
+    CUCHK(cudaMemcpyAsync(Ud + (size_t)c * A.m, Xfin + (size_t)c * N + A.n, sizeof(double) * A.m,
+                          cudaMemcpyDeviceToDevice, s));
+  }
+  std::vector<double> sg, rs;
+  final_triplets(ctx, pool, A, k, Vd, Ud, true, sg, rs);
+  std::vector<int> ord(k);
+  for (int i = 0; i < k; ++i) ord[i] = i;
+  std::sort(ord.begin(), ord.end(), [&](int a2, int b2) { return sg[a2] < sg[b2]; });
+  for (int i = 0; i < k; ++i) {
+    const int src = ord[i];
+    sigma[i] = sg[src];
+    if (resid) resid[i] = rs[src];
+    if (V) CUCHK(cudaMemcpyAsync(V + (size_t)i * A.n, Vd + (size_t)src * A.n, sizeof(double) * A.n,
+                                 cudaMemcpyDeviceToHost, s));
+    if (U) CUCHK(cudaMemcpyAsync(U + (size_t)i * A.m, Ud + (size_t)src * A.m, sizeof(double) * A.m,
+                                 cudaMemcpyDeviceToHost, s));
+  }
+  sync(s);
+  if (st) {
+    std::memset(st, 0, sizeof(*st));
+    st->iters_stage1 = iters_total;
+    st->matvecs_A = st->matvecs_At = mv_total + 2 * k;
+    st->norm_A_est = normA;
+    st->dynamic_route = route;
+    st->dynamic_runs = runs;
+    st->dynamic_switches = switches;
+    st->kernel_launches = g_launch_count - launches0;
+    st->t_total_ms = std::chrono::duration<double, std::milli>(clk::now() - tstart).count();
+  }
+}
+
 }  // namespace ph
 
 // ===========================================================================
@@ -2036,6 +2400,10 @@ phsvds_status phsvds_default_opts(phsvds_opts* o) {
   o->stage2_inner = 0;
   o->inner2_maxit = 300;
   o->inner2_patience = 25;
+  o->dynamic = 0;
+  o->dyn_init_iter = 50;
+  o->dyn_max_switch = 8;
+  o->deterministic = 1;
   return PHSVDS_OK;
 }
 
@@ -2142,6 +2510,12 @@ phsvds_status phsvds_solve(phsvds_handle h, int64_t m, int64_t n, int64_t nnz, c
     return set_err(h, PHSVDS_ERR_INVALID, "recording needs record_max >= 0 and record_every >= 1");
   if (o.stage2_precond != 0 && o.stage2_precond != 1)
     return set_err(h, PHSVDS_ERR_INVALID, "stage2_precond must be 0 or 1");
+  if (o.dynamic != 0 && (o.dynamic != 1 || target != PHSVDS_SMALLEST || o.dyn_init_iter < 1 ||
+                         o.dyn_max_switch < 0 || o.precision != PHSVDS_FP64 || precond == PHSVDS_PREC_LEARNED ||
+                         o.init_V))
+    return set_err(h, PHSVDS_ERR_INVALID,
+                   "dynamic = 1 needs SMALLEST, FP64, no learned correction or init_V, dyn_init_iter >= 1, "
+                   "dyn_max_switch >= 0");
   if ((o.stage2_inner != 0 && o.stage2_inner != 1) || o.inner2_maxit < 1 || o.inner2_patience < 1 ||
       (o.stage2_inner == 1 && (o.stage2_precond || precond == PHSVDS_PREC_GIVEN)))
     return set_err(h, PHSVDS_ERR_INVALID,
@@ -2160,8 +2534,12 @@ phsvds_status phsvds_solve(phsvds_handle h, int64_t m, int64_t n, int64_t nnz, c
     return set_err(h, PHSVDS_ERR_INVALID, "init_V needs 0 <= init_nv <= max_basis (0 = k columns)");
   try {
     CUCHK(cudaSetDevice(h->device));
-    solve_impl(h, m, n, nnz, row_ptr, col_idx, val, ptr_on_device, k, target, tol, precond, o, sigma, U, V, resid,
-               stats);
+    if (o.dynamic)
+      dynamic_impl(h, m, n, nnz, row_ptr, col_idx, val, ptr_on_device, k, tol, precond, o, sigma, U, V, resid,
+                   stats);
+    else
+      solve_impl(h, m, n, nnz, row_ptr, col_idx, val, ptr_on_device, k, target, tol, precond, o, sigma, U, V,
+                 resid, stats);
   } catch (const PhError& e) {
     cudaStreamSynchronize(h->stream);
     cudaGetLastError();

@@ -37,7 +37,8 @@ class Opts(C.Structure):
                 ("record_every", C.c_int), ("projected_solver", C.c_int), ("init_V", C.c_void_p),
                 ("init_nv", C.c_int), ("mixed_inner", C.c_int), ("inner_maxit", C.c_int), ("inner_tol", C.c_double),
                 ("stage2_precond", C.c_int), ("precond_M", C.c_void_p), ("stage2_inner", C.c_int),
-                ("inner2_maxit", C.c_int), ("inner2_patience", C.c_int)]
+                ("inner2_maxit", C.c_int), ("inner2_patience", C.c_int), ("dynamic", C.c_int),
+                ("dyn_init_iter", C.c_int), ("dyn_max_switch", C.c_int), ("deterministic", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -52,7 +53,8 @@ class Stats(C.Structure):
                 ("recorded", C.c_int64), ("stage1_stagnation_locks", C.c_int64), ("spmm_plan_cached", C.c_int),
                 ("class_flops", C.c_double * 12), ("class_bytes", C.c_double * 12), ("inner_solves", C.c_int64),
                 ("inner_steps", C.c_int64), ("inner2_solves", C.c_int64), ("inner2_steps", C.c_int64),
-                ("spmm_schedule_f32", C.c_int)]
+                ("spmm_schedule_f32", C.c_int), ("dynamic_route", C.c_int), ("dynamic_runs", C.c_int),
+                ("dynamic_switches", C.c_int)]
 
     def as_dict(self) -> dict:
         d = {}

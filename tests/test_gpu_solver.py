@@ -172,6 +172,24 @@ def test_spmm_plan_is_kept_by_the_handle(h):
     assert st["class_flops"][0] > 0 and st["class_bytes"][1] > 0
 
 
+@pytest.mark.parametrize("kw", [dict(block_size=2), dict(block_size=2, precision=native.MIXED),
+                                dict(block_size=2, stage2_inner=1)])
+def test_solves_repeat_bit_for_bit(kw):
+    """opts.deterministic (the default): every cross-block reduction sums in a
+    fixed order and the SpMM plan of the handle is reused, so a second solve
+    on the same handle gives the same bits and the same iteration counts."""
+    need_gpu()
+    A = synth.grid_gradient(20, 1.0, 2)
+    with native.Handle(0) as h2:
+        o = native.default_opts(**kw)
+        r1 = native.phsvds_solve(h2, A.m, A.n, A.row_ptr, A.col, A.val, 4, native.SMALLEST, DELTA, opts=o)
+        r2 = native.phsvds_solve(h2, A.m, A.n, A.row_ptr, A.col, A.val, 4, native.SMALLEST, DELTA, opts=o)
+    assert r1[4]["spmm_schedule"] == 2
+    assert np.array_equal(r1[0], r2[0]) and np.array_equal(r1[1], r2[1]) and np.array_equal(r1[2], r2[2])
+    for key in ("iters_stage1", "iters_stage2", "matvecs_A", "inner_steps", "inner2_steps"):
+        assert r1[4][key] == r2[4][key], key
+
+
 # ---- edge cases and failure paths (host-side, no GPU fault)
 _OK = dict(max_basis=14, min_restart=8)
 
