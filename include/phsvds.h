@@ -134,9 +134,12 @@ typedef struct {
      * (theta, x) an approximate solution t of (I - QQ^T)(C - theta I)
      * (I - QQ^T) t = r, Q = [locked vectors, x], by MINRES in FP32 with the
      * FP32 copy of A, at most inner_maxit steps (default 60) or until its
-     * residual falls by inner_tol (default 1e-3).  The Rayleigh-Ritz step,
-     * the convergence test and the orthogonalisation stay in FP64, so the
-     * accuracy is that of the FP64 method. */
+     * residual falls by inner_tol (default 1e-3).  With PHSVDS_PREC_JACOBI
+     * the system is preconditioned by D = diag(C), solved symmetrically in
+     * y = D^{1/2} t with Q = [locked vectors, the block's Ritz vectors]
+     * (this replaces the Olsen-Jacobi correction of the FP64 continuation).
+     * The Rayleigh-Ritz step, the convergence test and the orthogonalisation
+     * stay in FP64, so the accuracy is that of the FP64 method. */
     int mixed_inner;
     int inner_maxit;
     double inner_tol;

@@ -169,17 +169,19 @@ __global__ void k_jd_coef(int q, const double* __restrict__ acc, const double* _
   SC(JF_C2, c) = alfa / beta;
 }
 
-// y = C v - theta v - Xl (Xl^T C v) - x (x^T C v) - c1 r1 - c2 r2 (the projected,
-// shifted operator and the Lanczos recurrence); then r1 <- r2, r2 <- y, and
-// acc[24 + c] += ||y||^2.  Columns already converged are left alone.  Each
-// locked vector is loaded once per row group and applied to all columns.
+// y = C u - theta u - Xl (Xl^T C u) - x (x^T C u) - c1 r1 - c2 r2 (the projected,
+// shifted operator and the Lanczos recurrence; u = v, and no x term when X is
+// null); in the scaled form the operator part is multiplied by ds before the
+// recurrence terms.  Then r1 <- r2, r2 <- y, and acc[24 + c] += ||y||^2.
+// Columns already converged are left alone.  Each locked vector is loaded once
+// per row group and applied to all columns.
 template <int V>
 __global__ void __launch_bounds__(JD_T) k_jd_lanczos(int n, int q, int nl, const float* __restrict__ Cv,
                                                      const float* __restrict__ v, const float* __restrict__ X,
                                                      const float* __restrict__ Xl, const double* __restrict__ theta,
-                                                     float* __restrict__ r1, float* __restrict__ r2,
-                                                     const double* __restrict__ sc, double* __restrict__ acc,
-                                                     RedWs rw) {
+                                                     const float* __restrict__ ds, float* __restrict__ r1,
+                                                     float* __restrict__ r2, const double* __restrict__ sc,
+                                                     double* __restrict__ acc, RedWs rw) {
   __shared__ float cf[8][4];           // theta, e, c1, c2 per column
   __shared__ float D[64 * 8];
   __shared__ double part[8];
@@ -190,7 +192,7 @@ __global__ void __launch_bounds__(JD_T) k_jd_lanczos(int n, int q, int nl, const
     const bool on = c < q && SC(JF_ACT, c) > 0.0;
     act[c] = on;
     cf[c][0] = on ? (float)theta[c] : 0.f;
-    cf[c][1] = on ? (float)acc[16 + c] : 0.f;
+    cf[c][1] = (on && X) ? (float)acc[16 + c] : 0.f;
     cf[c][2] = on ? (float)SC(JF_C1, c) : 0.f;
     cf[c][3] = on ? (float)SC(JF_C2, c) : 0.f;
   }
@@ -211,7 +213,12 @@ __global__ void __launch_bounds__(JD_T) k_jd_lanczos(int n, int q, int nl, const
         float a[V], b[V], d[V];
         ldv<V>(Cv + k, a);
         ldv<V>(v + k, b);
-        ldv<V>(X + k, d);
+        if (X) {
+          ldv<V>(X + k, d);
+        } else {
+#pragma unroll
+          for (int u = 0; u < V; ++u) d[u] = 0.f;
+        }
 #pragma unroll
         for (int u = 0; u < V; ++u) y[c][u] = fmaf(-cf[c][1], d[u], fmaf(-cf[c][0], b[u], a[u]));
       }
@@ -227,6 +234,16 @@ __global__ void __launch_bounds__(JD_T) k_jd_lanczos(int n, int q, int nl, const
           for (int u = 0; u < V; ++u) y[c][u] = fmaf(-dlc, xl[u], y[c][u]);
         }
       }
+    }
+    if (ds) {
+      float dd[V];
+      ldv<V>(ds + i, dd);
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        if (c < q) {
+#pragma unroll
+          for (int u = 0; u < V; ++u) y[c][u] *= dd[u];
+        }
     }
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
@@ -399,18 +416,51 @@ void jd_dots(cudaStream_t s, int n, int q, const float* v, const float* X, const
   count_work(PROF_F32 + PROF_SMALL, 6.0 * n * q, 4.0 * 3 * n * q);
 }
 
-void jd_step(cudaStream_t s, int n, int q, int nl, const float* Cv, float* v, const float* X, const float* Xl,
-             const double* theta, float* r1, float* r2, float* w1, float* w2, float* sol, double* acc, double* sc,
-             double tol) {
+__global__ void k_jd_dscale(int n, const double* __restrict__ d, double guard, float* __restrict__ ds) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) ds[i] = (float)(1.0 / sqrt(fmax(d[i], guard)));
+}
+void jd_dscale(cudaStream_t s, int n, const double* d, double guard, float* ds) {
+  if (n > 0) k_jd_dscale<<<ceil_div(n, 256), 256, 0, s>>>(n, d, guard, ds); count_launch();
+}
+
+template <int V>
+__global__ void __launch_bounds__(JD_T) k_jd_rowscale(int n, int q, const float* __restrict__ ds,
+                                                      const float* __restrict__ X, float* __restrict__ Y) {
+  for (int i = (blockIdx.x * JD_T + threadIdx.x) * V; i < n; i += gridDim.x * JD_T * V) {
+    float dd[V];
+    ldv<V>(ds + i, dd);
+    for (int c = 0; c < q; ++c) {
+      float x[V];
+      ldv<V>(X + (size_t)c * n + i, x);
+#pragma unroll
+      for (int u = 0; u < V; ++u) x[u] *= dd[u];
+      stv<V>(Y + (size_t)c * n + i, x);
+    }
+  }
+}
+void jd_rowscale(cudaStream_t s, int n, int q, const float* ds, const float* X, float* Y) {
+  ProfScope ps(s, PROF_F32 + PROF_SMALL);
+  if (n <= 0 || q <= 0) return;
+  if (jd_vec(n) == 4)
+    k_jd_rowscale<4><<<jd_grid(n, 4), JD_T, 0, s>>>(n, q, ds, X, Y);
+  else
+    k_jd_rowscale<1><<<jd_grid(n, 1), JD_T, 0, s>>>(n, q, ds, X, Y);
+  count_launch();
+}
+
+void jd_step(cudaStream_t s, int n, int q, int nl, const float* Cv, float* v, const float* u, const float* X,
+             const float* Xl, const double* theta, const float* ds, float* r1, float* r2, float* w1, float* w2,
+             float* sol, double* acc, double* sc, double tol) {
   ProfScope ps(s, PROF_F32 + PROF_SMALL);
   k_jd_coef<<<1, 32, 0, s>>>(q, acc, theta, sc); count_launch();
   const int V = jd_vec(n);
   const int g = jd_grid(n, V);
   const RedWs rw = red_ws((size_t)g * 8);
   if (V == 4)
-    k_jd_lanczos<4><<<g, JD_T, 0, s>>>(n, q, nl, Cv, v, X, Xl, theta, r1, r2, sc, acc, rw);
+    k_jd_lanczos<4><<<g, JD_T, 0, s>>>(n, q, nl, Cv, u, X, Xl, theta, ds, r1, r2, sc, acc, rw);
   else
-    k_jd_lanczos<1><<<g, JD_T, 0, s>>>(n, q, nl, Cv, v, X, Xl, theta, r1, r2, sc, acc, rw);
+    k_jd_lanczos<1><<<g, JD_T, 0, s>>>(n, q, nl, Cv, u, X, Xl, theta, ds, r1, r2, sc, acc, rw);
   count_launch();
   reduce_partials(s, rw, g, 8, acc + 24, 0, nullptr);
   k_jd_givens<<<1, 32, 0, s>>>(q, acc, tol, sc); count_launch();

@@ -260,9 +260,17 @@ void jd_colnorms(cudaStream_t s, int n, int q, const float* R, double* acc);
 void jd_init(cudaStream_t s, int n, int q, const float* R, float* r1, float* r2, float* v, float* sol, float* w1,
              float* w2, const double* acc, double* sc);
 void jd_dots(cudaStream_t s, int n, int q, const float* v, const float* X, const float* Cv, double* acc);
-void jd_step(cudaStream_t s, int n, int q, int nl, const float* Cv, float* v, const float* X, const float* Xl,
-             const double* theta, float* r1, float* r2, float* w1, float* w2, float* sol, double* acc, double* sc,
-             double tol);
+// One MINRES step.  u: the vector of the theta term (v itself, or in the
+// scaled form the projected P D^{-1/2} v); ds: D^{-1/2} of the scaled form
+// (null: none), applied to the operator's output before the recurrence; X null:
+// no x term (the scaled form projects x as part of Xl).
+void jd_step(cudaStream_t s, int n, int q, int nl, const float* Cv, float* v, const float* u, const float* X,
+             const float* Xl, const double* theta, const float* ds, float* r1, float* r2, float* w1, float* w2,
+             float* sol, double* acc, double* sc, double tol);
+// ds[i] = 1 / sqrt(max(d[i], guard)) (FP32): D^{-1/2} for D = diag(C)
+void jd_dscale(cudaStream_t s, int n, const double* d, double guard, float* ds);
+// Y[:, c] = ds .* X[:, c] for the q columns (column-major, leading dimension n)
+void jd_rowscale(cudaStream_t s, int n, int q, const float* ds, const float* X, float* Y);
 // stage 2 (one FP64 system on B, dynamic stop by the eigen-residual of x + t):
 // acc (256 doubles): [0] v^T Bv, [8] v^T v, [24] ||y||^2, [32, 32 + nq) Q^T Bv,
 // [160, 163) the eigen-residual sums; sc: JD_NSCALAR * 8 + 8 doubles

@@ -562,13 +562,19 @@ struct GraphCache {
 // targeted Ritz pair, solved for the block at once by MINRES in FP32 with the
 // FP32 products with C.  The outer Rayleigh-Ritz, the residuals that decide
 // convergence and the orthogonalisation of t into the basis stay in FP64.
+// With the Jacobi preconditioner D = diag(C) (Sec. 4's preconditioned JDQMR)
+// the equation is solved in the scaled variable y = D^{1/2} t:
+// D^{-1/2} P (C - theta I) P D^{-1/2} y = D^{-1/2} r, a symmetric system, with
+// P = I - QQ^T and Q = [locked vectors, all q Ritz vectors of the block] on
+// both sides (the scaled vectors leave the complement of Q, so the
+// projection is applied to the operator's input as well); t = D^{-1/2} y.
 struct InnerJD {
   cudaStream_t s;
   int n, maxit, chunk = 5;
   double tol;
   COp<float> op;
-  float *R, *r1, *r2, *v, *sol, *w1, *w2, *X, *Cv, *Xrm, *Yrm, *Xl32;
-  double *acc, *sc;
+  float *R, *r1, *r2, *v, *sol, *w1, *w2, *X, *Cv, *Xrm, *Yrm, *Xl32, *U, *ds;
+  double *acc, *sc, *g1;
   GraphCache graphs;
   int64_t steps = 0, solves = 0;
   InnerJD(phsvds_ctx* c, Pool& pool, int n_, int kmax, COp<float> op_, int maxit_, double tol_, bool use_graphs)
@@ -585,42 +591,65 @@ struct InnerJD {
     Cv = pool.get<float>(nn * 8);
     Xrm = pool.get<float>(nn * 8);
     Yrm = pool.get<float>(nn * 8);
-    Xl32 = pool.get<float>(nn * std::max(kmax, 1));
+    Xl32 = pool.get<float>(nn * (kmax + 8));
+    U = pool.get<float>(nn * 8);
+    ds = pool.get<float>(nn);
     acc = pool.get<double>(32 + 8 * 64);
     sc = pool.get<double>(JD_NSCALAR * 8);
+    g1 = pool.get<double>(8 * 64);
     graphs.enabled = use_graphs;
   }
   // Tb (n x q, FP64): residuals on entry, corrections on return.  Xu: the q
-  // Ritz vectors, theta (device, q): their Ritz values, Xl: nl locked vectors.
-  void solve(phsvds_ctx* ctx, int q, double* Tb, const double* Xu, const double* theta, const double* Xl, int nl) {
+  // Ritz vectors, theta (device, q): their Ritz values, Xl: nl locked vectors;
+  // dC (device, n): diag(C) for the scaled form (null: unscaled), entries
+  // below guard raised to it.
+  void solve(phsvds_ctx* ctx, int q, double* Tb, const double* Xu, const double* theta, const double* Xl, int nl,
+             const double* dC = nullptr, double guard = 0.0) {
     Host h(ctx);
     const size_t nq = (size_t)n * q;
+    const bool scaled = dC != nullptr;
     convert_f64_to_f32(s, (int64_t)nq, Tb, R);
     convert_f64_to_f32(s, (int64_t)nq, Xu, X);
     if (nl) convert_f64_to_f32(s, (int64_t)n * nl, Xl, Xl32);
+    // the scaled form projects against Q = [Xl, X]
+    const int nq_ = scaled ? nl + q : nl;
+    if (scaled) {
+      CUCHK(cudaMemcpyAsync(Xl32 + (size_t)n * nl, X, sizeof(float) * nq, cudaMemcpyDeviceToDevice, s));
+      jd_dscale(s, n, dC, guard, ds);
+      jd_rowscale(s, n, q, ds, R, R);
+    }
     zero(s, v, (size_t)n * 8);   // the columns past q feed the SpMM's padding
+    if (scaled) zero(s, U, (size_t)n * 8);
     zero(s, acc, 32);
     jd_colnorms(s, n, q, R, acc);
     jd_init(s, n, q, R, r1, r2, v, sol, w1, w2, acc, sc);
     const int w = spmm_width(q);
-    const size_t nacc = 32 + (size_t)8 * nl;
+    const size_t nacc = 32 + (size_t)8 * nq_;
+    Basis<float> P{Xl32, n, nq_, nullptr, 0, 0};
+    // u: the operator's input (v, or P D^{-1/2} v in the scaled form)
+    float* u = scaled ? U : v;
     auto step = [&]() {
-      cm_to_rm<float>(s, n, v, n, w, Xrm);
+      if (scaled) {
+        jd_rowscale(s, n, q, ds, v, U);
+        zero(s, g1, (size_t)nq_ * q);
+        cgs_pass<float>(s, n, P, U, n, q, nullptr, g1, nullptr);
+        cgs_pass<float>(s, n, P, U, n, q, g1, nullptr, nullptr);
+      }
+      cm_to_rm<float>(s, n, u, n, w, Xrm);
       op.apply(s, w, Xrm, Yrm);
       rm_to_cm<float>(s, n, Yrm, w, Cv, n);
       zero(s, acc, nacc);
-      if (nl) {
-        Basis<float> P{Xl32, n, nl, nullptr, 0, 0};
-        cgs_pass<float>(s, n, P, Cv, n, q, nullptr, acc + 32, nullptr);
-      }
-      jd_dots(s, n, q, v, X, Cv, acc);
-      jd_step(s, n, q, nl, Cv, v, X, Xl32, theta, r1, r2, w1, w2, sol, acc, sc, tol);
+      if (nq_) cgs_pass<float>(s, n, P, Cv, n, q, nullptr, acc + 32, nullptr);
+      jd_dots(s, n, q, u, X, Cv, acc);
+      jd_step(s, n, q, nq_, Cv, v, u, scaled ? nullptr : X, Xl32, theta, scaled ? ds : nullptr, r1, r2, w1, w2, sol,
+              acc, sc, tol);
     };
     double* hact = h.at<double>(16384);  // bytes [16384, 16448)
     int it = 0;
     while (it < maxit) {
       const int m = std::min(chunk, maxit - it);
-      graphs.run(s, (3ull << 40) | ((uint64_t)m << 16) | ((uint64_t)nl << 8) | (uint64_t)q, [&]() {
+      graphs.run(s, (3ull << 40) | ((uint64_t)scaled << 32) | ((uint64_t)m << 16) | ((uint64_t)nq_ << 8) | (uint64_t)q,
+                 [&]() {
         for (int i = 0; i < m; ++i) step();
       });
       it += m;
@@ -632,6 +661,7 @@ struct InnerJD {
     }
     steps += it;
     ++solves;
+    if (scaled) jd_rowscale(s, n, q, ds, sol, sol);
     convert_f32_to_f64(s, (int64_t)nq, sol, Tb);
   }
 };
@@ -1109,7 +1139,10 @@ struct Stage1 {
           double* hu = h.at<double>(1152);   // bytes [1152, 1216): theta of the corrected columns
           for (int c = 0; c < nu; ++c) hu[c] = thv[unconv[c]];
           CUCHK(cudaMemcpyAsync(thU, hu, sizeof(double) * nu, cudaMemcpyHostToDevice, s));
-          jd->solve(ctx, nu, Tb, XU, thU, Xl, nlock);
+          if (precond == PHSVDS_PREC_JACOBI)
+            jd->solve(ctx, nu, Tb, XU, thU, Xl, nlock, diagC, EPS64 * std::max(out.theta_max, 1e-300));
+          else
+            jd->solve(ctx, nu, Tb, XU, thU, Xl, nlock);
         }
       }
       if (precond == PHSVDS_PREC_LEARNED && lp && nu > 0) {
@@ -1124,7 +1157,7 @@ struct Stage1 {
         if (bp && nu > 0)
           for (int c = 0; c < nu; ++c) bp->olsen(Tb + (size_t)c * n, Xr + (size_t)unconv[c] * n, Tb + (size_t)c * n);
       }
-      if (precond == PHSVDS_PREC_JACOBI && nu > 0) {
+      if (precond == PHSVDS_PREC_JACOBI && !jd && nu > 0) {
         double* hu = h.at<double>(1024);     // bytes [1024, 1088)
         for (int c = 0; c < nu; ++c) hu[c] = shift_free ? 0.0 : thv[unconv[c]];
         CUCHK(cudaMemcpyAsync(thU, hu, sizeof(double) * nu, cudaMemcpyHostToDevice, s));
@@ -1231,7 +1264,9 @@ struct Orth1 {
     inn = p.get<double>(4);
     minv = p.get<double>(4);
   }
-  void run(int N, const Basis<double>& P, double* t, double* dst) {
+  // skip_below > 0: a t that keeps at most that fraction of its squared norm
+  // is left out (returns false) instead of replaced by a random vector
+  bool run(int N, const Basis<double>& P, double* t, double* dst, double skip_below = -1.0) {
     Host h(ctx);
     const int p = P.cols();
     for (int attempt = 0;; ++attempt) {
@@ -1248,11 +1283,12 @@ struct Orth1 {
       sync(s);
       const double a = *h.at<double>(0), b0 = *h.at<double>(8);
       if (!std::isfinite(a)) throw PhError{PHSVDS_ERR_NAN, "non-finite vector in orthogonalisation"};
+      if (skip_below > 0 && !(a > skip_below * b0)) return false;
       if (b0 > 0 && a > 1e-20 * b0) {
         const double f = 1.0 / std::sqrt(a);
         scal(s, N, f, nullptr, t);
         if (dst != t) CUCHK(cudaMemcpyAsync(dst, t, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
-        return;
+        return true;
       }
       if (attempt >= 3) throw PhError{PHSVDS_ERR_BREAKDOWN, "cannot extend the basis"};
       fill_random<double>(s, N, t, seed, RS_BREAK + 0x100000 + (uint64_t)(rand_ctr++));
@@ -1626,16 +1662,14 @@ struct Stage2 {
         ++nl;
         ++nd;
         const bool mirror = jd2 && std::fabs(th1) <= std::sqrt(EPS64) * normA;
-        if (mirror) {  // [v; -u], normalised, deflated as well
-          double* dm = D + (size_t)nd * N;
-          CUCHK(cudaMemcpyAsync(dm, xr, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
-          scal(s, m, -1.0, nullptr, dm + n);
-          zero(s, nrm, 1);
-          col_norms2_dense<double>(s, N, dm, N, 1, nrm);
-          CUCHK(cudaMemcpyAsync(h.at<double>(0), nrm, sizeof(double), cudaMemcpyDeviceToHost, s));
-          sync(s);
-          scal(s, N, 1.0 / std::sqrt(*h.at<double>(0)), nullptr, dm);
-          ++nd;
+        if (mirror) {  // [v; -u], orthonormalised against the deflated set, deflated as well
+          // (the mirror is orthogonal to x, but to the other tiny locked
+          // pairs only as far as their v and u parts are separately
+          // orthogonal, i.e. to the accuracy r / gap of the tiny cluster)
+          CUCHK(cudaMemcpyAsync(tv, xr, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+          scal(s, m, -1.0, nullptr, tv + n);
+          Basis<double> P{D, N, nd, nullptr, 0, 0};
+          if (orth.run(N, P, tv, D + (size_t)nd * N, 1e-8)) ++nd;   // (already deflated: left out)
         }
         th_lock.push_back(th1);
         ++target;
@@ -1905,7 +1939,7 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
     convert_f32_to_f64(s, (int64_t)A.n * k, s1f.Xl, X0);
     s1.out.restarts = s1f.out.restarts;
     s1.out.theta_max = s1f.out.theta_max;  // the ||C|| estimate carries over
-    if (o.mixed_inner == 1 && s1.precond == PHSVDS_PREC_NONE) {
+    if (o.mixed_inner == 1 && (s1.precond == PHSVDS_PREC_NONE || s1.precond == PHSVDS_PREC_JACOBI)) {
       jd = std::make_unique<InnerJD>(ctx, pool, A.n, k, op32, o.inner_maxit, o.inner_tol, !o.profile);
       s1.jd = jd.get();
     }

@@ -102,3 +102,35 @@ def test_given_preconditioner_needs_a_square_matrix_and_a_diagonal(h):
     *_, status = native.phsvds_solve(h, D.m, D.n, D.row_ptr, D.col, D.val, 2, native.SMALLEST, DELTA,
                                      native.PREC_GIVEN, o, precond_M=Mz, raise_on_error=False)
     assert status == native.PHSVDS_ERR_INVALID                  # a zero entry
+
+
+def test_scaled_jd_inner_solve_with_jacobi(h):
+    """The Jacobi-preconditioned correction equation of the FP64 continuation
+    (mixed precision, PHSVDS_PREC_JACOBI, opts.mixed_inner = 1: MINRES on
+    D^{-1/2} P (C - theta I) P D^{-1/2}, D = diag(C)) on a matrix whose columns
+    are scaled over three decades: the dense SVD's smallest triplets
+    (1e-10 relative, residuals <= 1e-14 ||A||), as with the Olsen-Jacobi
+    correction (mixed_inner = 0), in fewer FP64 outer iterations."""
+    A0 = synth.random_sparse(3000, 1500, 8.0, 41, values="gaussian", shift=0.05)
+    S = R.as_scipy(A0)
+    S = (S @ sp.diags(10.0 ** (-3.0 * synth.uniform(43, 1, 1500)))).tocsr()
+    S.sort_indices()
+    A = synth.Csr(S.shape[0], S.shape[1], S.indptr.astype(np.int64), S.indices.astype(np.int32), S.data)
+    k = 5
+    dense = S.toarray()
+    sv = np.sort(np.linalg.svd(dense, compute_uv=False))[:k]
+    nA = float(np.linalg.norm(dense, 2))
+    runs = {}
+    for inner in (0, 1):
+        o = native.default_opts(block_size=4, precision=native.MIXED, mixed_inner=inner)
+        runs[inner] = native.phsvds_solve(h, A.m, A.n, A.row_ptr, A.col, A.val, k, native.SMALLEST, DELTA,
+                                          native.PREC_JACOBI, o)
+    for inner, (sig, U, V, res, st, _) in runs.items():
+        assert np.all(np.abs(sig - sv) <= 1e-10 * sv), (inner, sig, sv)
+        assert np.all(_resid(S, sig, U, V) <= DELTA * nA), (inner, _resid(S, sig, U, V) / nA)
+    st0, st1 = runs[0][4], runs[1][4]
+    assert st1["inner_solves"] > 0 and st0["inner_solves"] == 0
+    fp64_its = {i: r[4]["iters_stage1"] - r[4]["iters_stage1_fp32"] for i, r in runs.items()}
+    print("FP64 outer iterations (Olsen-Jacobi, scaled JD):", fp64_its[0], fp64_its[1], "inner steps",
+          st1["inner_steps"])
+    assert fp64_its[1] < fp64_its[0], fp64_its
