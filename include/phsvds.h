@@ -191,6 +191,18 @@ typedef struct {
      * faster (the triplets then vary in the last bits between runs, and the
      * iteration counts a little). */
     int deterministic;
+    /* ||A|| of the user requirement ||r|| < delta ||A|| (Sec. 3.1): the
+     * switch test after stage 1, the stage-2 test delta ||A|| / sqrt(2) and
+     * the tiny-sigma threshold.  0 (default): stage 1's running largest Ritz
+     * value (for the smallest triplets it can sit far below ||A||, which only
+     * tightens the tests); > 0: the caller's value of ||A|| (PRIMME's aNorm),
+     * raised by any larger Ritz value; < 0: the larger of that and the
+     * square root of the largest Ritz value of 30 Lanczos steps on C run
+     * before stage 1 (FP64, seeded start; a lower bound of ||A||, so the tests
+     * stay at least as tight as delta ||A||).  Stage 1's own delta_C keeps
+     * its current largest Ritz value, as Algorithm 1 states.
+     * stats.norm_A_est reports the value used. */
+    double norm_A;
 } phsvds_opts;
 
 typedef struct {
@@ -311,7 +323,7 @@ typedef struct {
 /*
  * Batched form of phsvds_solve (the method of Sections 3-5 applied to many
  * independent matrices): the `count` matrices are solved concurrently on the
- * handle's device by `concurrency` worker threads (0 = min(count, 16)), each
+ * handle's device by `concurrency` worker threads (0 = min(count, 4)), each
  * with its own stream and workspace, taking matrices largest (nnz) first.
  * Every matrix gets the same k, target, tol, precond and opts as phsvds_solve,
  * and its own autotuned SpMM plan.  ptr_on_device applies to every matrix;

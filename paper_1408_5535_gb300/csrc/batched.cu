@@ -33,7 +33,7 @@ extern "C" phsvds_status phsvds_solve_batched(phsvds_handle h, int count, const 
     out[i].message[0] = '\0';
     std::memset(&out[i].stats, 0, sizeof(out[i].stats));
   }
-  int workers = concurrency > 0 ? concurrency : std::min(count, 16);
+  int workers = concurrency > 0 ? concurrency : std::min(count, 4);
   workers = std::max(1, std::min(workers, count));
   // largest work first: the stored entries are the cost of one product
   std::vector<int> order(count);

@@ -25,7 +25,7 @@ namespace ph {
 constexpr int LD = 64;                    // leading dimension of the small matrices
 constexpr double EPS64 = 2.220446049250313e-16;
 constexpr double EPS32 = 1.1920928955078125e-07;
-constexpr uint64_t RS_INIT = 0x1000, RS_BREAK = 0x2000, RS_U = 0x3000;
+constexpr uint64_t RS_INIT = 0x1000, RS_BREAK = 0x2000, RS_U = 0x3000, RS_NORM = 0x4000;
 constexpr double JAC_TOL = 5e-17;         // Jacobi threshold for pairs touching a target, relative to ||H||
 constexpr double TOL_MARGIN = 0.9;        // stopping tests use 0.9 delta: the residual the test sees and an
                                           // independent recomputation differ by rounding of order eps ||C||
@@ -1266,6 +1266,7 @@ struct Orth1 {
   }
   // skip_below > 0: a t that keeps at most that fraction of its squared norm
   // is left out (returns false) instead of replaced by a random vector
+  double last_kept = 0.0;  // squared norm kept by the last run (relative), for the trace
   bool run(int N, const Basis<double>& P, double* t, double* dst, double skip_below = -1.0) {
     Host h(ctx);
     const int p = P.cols();
@@ -1282,6 +1283,7 @@ struct Orth1 {
       CUCHK(cudaMemcpyAsync(h.at<double>(8), inn, sizeof(double), cudaMemcpyDeviceToHost, s));
       sync(s);
       const double a = *h.at<double>(0), b0 = *h.at<double>(8);
+      last_kept = b0 > 0 ? a / b0 : 0.0;
       if (!std::isfinite(a)) throw PhError{PHSVDS_ERR_NAN, "non-finite vector in orthogonalisation"};
       if (skip_below > 0 && !(a > skip_below * b0)) return false;
       if (b0 > 0 && a > 1e-20 * b0) {
@@ -1653,9 +1655,12 @@ struct Stage2 {
       const double tolB = delta * normA / std::sqrt(2.0);
       // near the tolerance the estimate is checked against a fresh residual
       const double rf = rn < 4.0 * tolB ? fresh_resid(th1) : -1.0;
-      if (trace_on())
-        fprintf(stderr, "s2 it=%lld j=%d target=%d shift=%.17g th1=%.17g rn=%.6e rf=%.6e sigmin=%.6e\n",
-                (long long)iters, j, target, shift, th1, rn, rf, *h.at<double>(8));
+      if (trace_on()) {
+        CUCHK(cudaMemcpyAsync(h.at<int>(40), sw + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
+        sync(s);
+        fprintf(stderr, "s2 it=%lld j=%d target=%d shift=%.17g th1=%.17g rn=%.6e rf=%.6e sigmin=%.6e ri=%d\n",
+                (long long)iters, j, target, shift, th1, rn, rf, *h.at<double>(8), *h.at<int>(40));
+      }
       if (rf >= 0.0 && rf < tolB) {
         CUCHK(cudaMemcpyAsync(Xl + (size_t)nl * N, xr, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
         CUCHK(cudaMemcpyAsync(D + (size_t)nd * N, xr, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
@@ -1692,6 +1697,18 @@ struct Stage2 {
         }
         CUCHK(cudaMemcpyAsync(tv, x0 + (size_t)target * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
         append(tv);
+        if (trace_on()) {
+          // the guess's own residual ||B x0 - s x0|| at its shift
+          const double* xg = x0 + (size_t)target * N;
+          f.B(xg, tv);
+          axpby(s, N, -sig_s[target], xg, 1.0, tv);
+          zero(s, nrm + 1, 1);
+          col_norms2_dense<double>(s, N, tv, N, 1, nrm + 1);
+          CUCHK(cudaMemcpyAsync(h.at<double>(24), nrm + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+          sync(s);
+          fprintf(stderr, "s2 new target %d: guess keeps %.3e of its squared norm, its residual %.3e\n", target,
+                  orth.last_kept, std::sqrt(std::max(*h.at<double>(24), 0.0)));
+        }
         shift = sig_s[target];
         qr_full = true;
         have_prev = false;
@@ -1808,6 +1825,72 @@ static void final_triplets(phsvds_ctx* ctx, Pool& pool, DevA& A, int k, double* 
 // ---------------------------------------------------------------------------
 // The whole method
 // ---------------------------------------------------------------------------
+// ||C|| estimated by L Lanczos steps on C (FP64, seeded random start, no
+// reorthogonalisation: the extreme Ritz value needs none): the largest
+// eigenvalue of the tridiagonal T_L, found by the one-CTA Jacobi solver.  A
+// lower bound of ||C|| that converges quickly from below.  The host only
+// gathers the scalars alpha_i, beta_i into T.
+static double lanczos_normC(phsvds_ctx* ctx, Pool& pool, const COp<double>& op, int n, uint64_t seed, int L,
+                            int64_t& mv) {
+  cudaStream_t s = ctx->stream;
+  Host h(ctx);
+  L = std::max(1, std::min(L, std::min(n, LD)));
+  double* v0 = pool.get<double>((size_t)n);
+  double* v1 = pool.get<double>((size_t)n);
+  double* w = pool.get<double>((size_t)n);
+  double* d = pool.get<double>(2);
+  double* T = pool.get<double>(LD * LD);
+  double* S = pool.get<double>(LD * LD);
+  double* th = pool.get<double>(LD);
+  auto to_host = [&](const double* dv) {
+    CUCHK(cudaMemcpyAsync(h.at<double>(0), dv, sizeof(double), cudaMemcpyDeviceToHost, s));
+    sync(s);
+    return *h.at<double>(0);
+  };
+  fill_random<double>(s, n, v1, seed, RS_NORM);
+  zero(s, d, 1);
+  col_norms2_dense<double>(s, n, v1, n, 1, d);
+  const double n0 = std::sqrt(std::max(to_host(d), 0.0));
+  if (!(n0 > 0)) return 0.0;
+  scal(s, n, 1.0 / n0, nullptr, v1);
+  zero(s, v0, (size_t)n);
+  std::vector<double> al, be;
+  double beta = 0.0;
+  for (int i = 0; i < L; ++i) {
+    op.apply(s, 1, v1, w);
+    ++mv;
+    zero(s, d, 1);
+    dot_accum(s, n, v1, w, d);
+    const double alpha = to_host(d);
+    axpby(s, n, -alpha, v1, 1.0, w);
+    if (i > 0) axpby(s, n, -beta, v0, 1.0, w);
+    zero(s, d, 1);
+    col_norms2_dense<double>(s, n, w, n, 1, d);
+    const double b2 = to_host(d);
+    if (!std::isfinite(alpha) || !std::isfinite(b2)) throw PhError{PHSVDS_ERR_NAN, "non-finite value in the norm estimate"};
+    al.push_back(alpha);
+    beta = std::sqrt(std::max(b2, 0.0));
+    if (i + 1 == L || !(beta > 1e-14 * std::fabs(alpha))) break;
+    be.push_back(beta);
+    std::swap(v0, v1);
+    CUCHK(cudaMemcpyAsync(v1, w, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    scal(s, n, 1.0 / beta, nullptr, v1);
+  }
+  const int jl = (int)al.size();
+  double* hT = h.at<double>(1024);   // bytes [1024, 1024 + 8 LD^2)
+  for (int c = 0; c < jl; ++c)
+    for (int r = 0; r < jl; ++r)
+      hT[r + c * jl] = r == c ? al[c] : (r == c + 1 || c == r + 1) ? be[std::min(r, c)] : 0.0;
+  CUCHK(cudaMemcpyAsync(T, hT, sizeof(double) * jl * jl, cudaMemcpyHostToDevice, s));
+  set_identity(s, jl, S, jl);
+  jacobi_eig(s, jl, T, S, th, 1e-15, 30, nullptr);
+  CUCHK(cudaMemcpyAsync(h.at<double>(0), th, sizeof(double) * jl, cudaMemcpyDeviceToHost, s));
+  sync(s);
+  double mx = 0.0;
+  for (int i = 0; i < jl; ++i) mx = std::max(mx, *h.at<double>(8 * i));
+  return mx;
+}
+
 static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const int64_t* rp, const int32_t* ci,
                        const double* va, int on_dev, int k, phsvds_target target, double tol, phsvds_precond precond,
                        const phsvds_opts& o, double* sigma, double* U, double* V, double* resid, phsvds_stats* st) {
@@ -1875,6 +1958,14 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
   // ---- stage 1
   const auto t1a = clk::now();
   const double tol_in = TOL_MARGIN * tol;
+  // ||A|| of the user requirement (opts.norm_A): the switch test and stage 2;
+  // stage 1's delta_C keeps its running largest Ritz value (Algorithm 1)
+  int64_t mv_norm = 0;
+  double thC0 = 0.0;
+  if (o.norm_A > 0)
+    thC0 = o.norm_A * o.norm_A;
+  else if (o.norm_A < 0)
+    thC0 = lanczos_normC(ctx, pool, op64, A.n, o.seed, 30, mv_norm);
   Stage1<double> s1(ctx, pool, A.n, k, o, largest, tol_in, EPS64, precond1, diag1, op64);
   s1.shift_free = given;
   s1.lp = &ld;
@@ -1961,14 +2052,14 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
   }
   sync(s);
   const auto t1b = clk::now();
-  double normA = std::sqrt(std::max(s1.out.theta_max, theta_max32));
+  double normA = std::sqrt(std::max(std::max(s1.out.theta_max, theta_max32), thC0));
   // stage-1 triplets u = A v / ||A v||
   double* Vd = pool.get<double>((size_t)A.n * k);
   double* Ud = pool.get<double>((size_t)A.m * k);
   CUCHK(cudaMemcpyAsync(Vd, s1.Xl, sizeof(double) * A.n * k, cudaMemcpyDeviceToDevice, s));
   std::vector<double> sg, rs;
   final_triplets(ctx, pool, A, k, Vd, Ud, false, sg, rs);
-  int64_t mvA = s1.out.mv + mv32 + k, mvAt = s1.out.mv + mv32 + k;
+  int64_t mvA = s1.out.mv + mv32 + k + mv_norm, mvAt = s1.out.mv + mv32 + k + mv_norm;
   bool need2 = false;
   const double floor = o.eps_factor * EPS64;
   for (int i = 0; i < k; ++i)
@@ -2438,6 +2529,7 @@ phsvds_status phsvds_default_opts(phsvds_opts* o) {
   o->dyn_init_iter = 50;
   o->dyn_max_switch = 8;
   o->deterministic = 1;
+  o->norm_A = 0.0;
   return PHSVDS_OK;
 }
 
@@ -2544,6 +2636,8 @@ phsvds_status phsvds_solve(phsvds_handle h, int64_t m, int64_t n, int64_t nnz, c
     return set_err(h, PHSVDS_ERR_INVALID, "recording needs record_max >= 0 and record_every >= 1");
   if (o.stage2_precond != 0 && o.stage2_precond != 1)
     return set_err(h, PHSVDS_ERR_INVALID, "stage2_precond must be 0 or 1");
+  if (!std::isfinite(o.norm_A) || (o.dynamic != 0 && o.norm_A != 0.0))
+    return set_err(h, PHSVDS_ERR_INVALID, "norm_A must be finite (and 0 with dynamic = 1)");
   if (o.dynamic != 0 && (o.dynamic != 1 || target != PHSVDS_SMALLEST || o.dyn_init_iter < 1 ||
                          o.dyn_max_switch < 0 || o.precision != PHSVDS_FP64 || precond == PHSVDS_PREC_LEARNED ||
                          o.init_V))
