@@ -41,7 +41,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--c3s-steps", type=int, default=2,
-                   help="timed solves of C3's k=20 smallest triplets at full size (0: skip)")
+                   help="timed mixed-precision solves of C3's k=20 smallest triplets at full size (0: skip)")
+    p.add_argument("--c3s-mixed-inner", type=int, default=1, help="opts.mixed_inner of that solve")
     p.add_argument("--workload", default="c3", choices=["c3", "grid"],
                    help="c3: random sparse 1e6 x 5e5, k=20 largest (default); grid: weighted grid gradient, "
                         "k=10 smallest")
@@ -889,13 +890,16 @@ def run_learned(a):
 
 def run_c3_smallest(a):
     """C3's k = 20 smallest triplets at full size (the same 1e6 x 5e5 matrix
-    as the headline, tol 1e-14 ||A||): mixed precision with the Jacobi
-    preconditioner, the scaled Jacobi-Davidson inner solves of stage 1, JDQMR
-    in stage 2, and ||A|| estimated before stage 1 (opts.norm_A = -1).  One
-    untimed solve (autotuner, graphs), then a.c3s_steps solves timed with CUDA
-    events on the library's stream.  The residuals of the returned triplets
-    are recomputed here on the host against the estimate of ||A||, which is a
-    lower bound, so the check is at least as strict as 1e-14 ||A||."""
+    as the headline, tol 1e-14 ||A||), mixed precision against FP64 with the
+    same algorithm: the Jacobi preconditioner with the scaled Jacobi-Davidson
+    inner solves in stage 1 (FP32 MINRES in the mixed form, FP64 MINRES with
+    opts.stage1_inner in the FP64 form), JDQMR in stage 2, and ||A||
+    estimated before stage 1 (opts.norm_A = -1).  Per precision one untimed
+    solve (autotuner, graphs), then timed solves with CUDA events on the
+    library's stream (a.c3s_steps for mixed, one for FP64).  The residuals of
+    the returned triplets are recomputed here on the host against the estimate
+    of ||A||, a lower bound, so the check is at least as strict as
+    1e-14 ||A||; the two precisions' values are compared with each other."""
     import numpy as np
     import scipy.sparse as sp
     import torch
@@ -905,44 +909,51 @@ def run_c3_smallest(a):
     h = native.Handle(0, stream.cuda_stream)
     rp, ci, va = (torch.from_numpy(x).cuda() for x in (A.row_ptr, A.col, A.val))
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
-    k = 20
-    o = native.default_opts(block_size=8, precision=native.MIXED, stage2_inner=1, norm_A=-1.0, time_limit_s=300.0)
-
-    def solve(vectors):
-        return native.phsvds_solve(h, A.m, A.n, rp, ci, va, k, native.SMALLEST, TOL, native.PREC_JACOBI, o,
-                                   on_device=True, want_vectors=vectors)
-
-    solve(False)
-    times, out = [], None
-    for i in range(a.c3s_steps):
-        flush.fill_(1.0)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        out = solve(i == a.c3s_steps - 1)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        times.append(e0.elapsed_time(e1))
-    sig, U, V, res, st, _ = out
     S = sp.csr_matrix((A.val, A.col, A.row_ptr), shape=(A.m, A.n))
-    rv = np.linalg.norm(S @ V - U * sig, axis=0)
-    ru = np.linalg.norm(S.T @ U - V * sig, axis=0)
-    rec = np.sqrt(rv ** 2 + ru ** 2)
-    nA = st["norm_A_est"]
-    ms = float(np.median(times))
-    return {"workload": "the headline matrix, k=20 smallest, block 8, tol 1e-14*||A||, mixed precision, Jacobi "
-                        "preconditioner with scaled Jacobi-Davidson inner solves in stage 1, JDQMR in stage 2, "
-                        "||A|| estimated by 30 Lanczos steps on C (opts.norm_A = -1)",
-            "ms": ms, "ms_all": times, "triplets_per_s": k / (ms / 1e3),
-            "sigma_min": float(sig[0]), "sigma_20": float(sig[-1]), "norm_A_est": nA,
-            "max_resid_over_normA_recomputed": float(np.max(rec) / nA),
-            "iters_stage1": st["iters_stage1"], "iters_stage1_fp32": st["iters_stage1_fp32"],
-            "iters_stage2": st["iters_stage2"], "inner_steps_stage1": st["inner_steps"],
-            "inner_steps_stage2": st["inner2_steps"], "t_stage1_ms": st["t_stage1_ms"],
-            "t_stage2_ms": st["t_stage2_ms"],
-            "fp64": "the plain FP64 method (Olsen-Jacobi GD+k, no inner solves) reaches its restart limit on this "
-                    "family already at 100000 x 50000"}
+    k = 20
+    legs = {"mixed": (native.default_opts(block_size=8, precision=native.MIXED, mixed_inner=a.c3s_mixed_inner,
+                                          stage2_inner=1, norm_A=-1.0, time_limit_s=300.0), max(1, a.c3s_steps)),
+            "fp64": (native.default_opts(block_size=8, precision=native.FP64, stage1_inner=1, stage2_inner=1,
+                                         norm_A=-1.0, time_limit_s=300.0), 1)}
+    out = {}
+    for name, (o, steps) in legs.items():
+        def solve(vectors):
+            return native.phsvds_solve(h, A.m, A.n, rp, ci, va, k, native.SMALLEST, TOL, native.PREC_JACOBI, o,
+                                       on_device=True, want_vectors=vectors)
+        solve(False)
+        times, res = [], None
+        for i in range(steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            res = solve(i == steps - 1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        sig, U, V, _, st, _ = res
+        rv = np.linalg.norm(S @ V - U * sig, axis=0)
+        ru = np.linalg.norm(S.T @ U - V * sig, axis=0)
+        nA = st["norm_A_est"]
+        ms = float(np.median(times))
+        out[name] = {"ms": ms, "ms_all": times, "triplets_per_s": k / (ms / 1e3), "sigma": [float(x) for x in sig],
+                     "norm_A_est": nA,
+                     "max_resid_over_normA_recomputed": float(np.max(np.sqrt(rv ** 2 + ru ** 2)) / nA),
+                     "iters_stage1": st["iters_stage1"], "iters_stage1_fp32": st["iters_stage1_fp32"],
+                     "iters_stage2": st["iters_stage2"], "inner_steps_stage1": st["inner_steps"],
+                     "inner_steps_stage2": st["inner2_steps"], "t_stage1_ms": st["t_stage1_ms"],
+                     "t_stage2_ms": st["t_stage2_ms"]}
+    sm, sf = np.array(out["mixed"]["sigma"]), np.array(out["fp64"]["sigma"])
+    return {"workload": "the headline matrix, k=20 smallest, block 8, tol 1e-14*||A||, Jacobi preconditioner with "
+                        "scaled Jacobi-Davidson inner solves in stage 1, JDQMR in stage 2, ||A|| estimated by 30 "
+                        "Lanczos steps on C (opts.norm_A = -1); mixed (FP32 stage and FP32 inner solves) against "
+                        "FP64 (opts.stage1_inner = 1, FP64 inner solves)",
+            "mixed": out["mixed"], "fp64": out["fp64"],
+            "speedup_mixed_over_fp64": out["fp64"]["ms"] / out["mixed"]["ms"],
+            "max_sigma_rel_diff_mixed_vs_fp64": float(np.max(np.abs(sm - sf) / sf)),
+            "plain_fp64": "the plain FP64 method (GD+k with the Olsen-Jacobi correction, no inner solves) reaches "
+                          "its restart limit on this family already at 100000 x 50000"}
 
 
 def main():

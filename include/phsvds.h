@@ -134,7 +134,12 @@ typedef struct {
      * (theta, x) an approximate solution t of (I - QQ^T)(C - theta I)
      * (I - QQ^T) t = r, Q = [locked vectors, x], by MINRES in FP32 with the
      * FP32 copy of A, at most inner_maxit steps (default 60) or until its
-     * residual falls by inner_tol (default 1e-3).  With PHSVDS_PREC_JACOBI
+     * residual falls by inner_tol (default 1e-3).  2: the FP32 stage too
+     * (FP32 outer Rayleigh-Ritz, FP32 MINRES): faster where the FP32 stage
+     * runs long on ill-conditioned smallest targets, but near the FP32
+     * floor the FP32 correction is rounding noise and the stage can stall
+     * (as on the largest triplets of a matrix with ||A|| ~ 3e4), so it is
+     * not the default.  With PHSVDS_PREC_JACOBI
      * the system is preconditioned by D = diag(C), solved symmetrically in
      * y = D^{1/2} t with Q = [locked vectors, the block's Ritz vectors]
      * (this replaces the Olsen-Jacobi correction of the FP64 continuation).
@@ -203,6 +208,12 @@ typedef struct {
      * its current largest Ritz value, as Algorithm 1 states.
      * stats.norm_A_est reports the value used. */
     double norm_A;
+    /* 1: the FP64 method (PHSVDS_FP64, no or the Jacobi preconditioner)
+     * expands stage 1 by the Jacobi-Davidson correction of the JDQMR form
+     * (Sec. 4) as opts.mixed_inner describes, with the MINRES solves in FP64
+     * on the FP64 products with C (the same algorithm as the mixed form's FP64
+     * continuation, in one precision); 0 (default): plain GD+k. */
+    int stage1_inner;
 } phsvds_opts;
 
 typedef struct {

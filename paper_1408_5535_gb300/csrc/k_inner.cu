@@ -23,54 +23,62 @@ namespace ph {
 
 constexpr int JD_T = 256;
 
-// V consecutive rows per thread: V = 4 (16-byte loads) when n is a multiple of
-// 4, so that every column of a column-major block starts 16-byte aligned.
-template <int V>
-__device__ inline void ldv(const float* __restrict__ p, float (&r)[V]) {
-  if constexpr (V == 4) {
+// V consecutive rows per thread, one 16-byte load (V = 4 for FP32, 2 for
+// FP64) when n is a multiple of V, so that every column of a column-major
+// block starts 16-byte aligned; else V = 1.
+template <typename T, int V>
+__device__ inline void ldv(const T* __restrict__ p, T (&r)[V]) {
+  if constexpr (V == 1) {
+    r[0] = *p;
+  } else if constexpr (sizeof(T) == 4) {
     const float4 t = *reinterpret_cast<const float4*>(p);
     r[0] = t.x; r[1] = t.y; r[2] = t.z; r[3] = t.w;
   } else {
-    r[0] = *p;
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    r[0] = t.x; r[1] = t.y;
   }
 }
-template <int V>
-__device__ inline void stv(float* __restrict__ p, const float (&r)[V]) {
-  if constexpr (V == 4)
+template <typename T, int V>
+__device__ inline void stv(T* __restrict__ p, const T (&r)[V]) {
+  if constexpr (V == 1)
+    *p = r[0];
+  else if constexpr (sizeof(T) == 4)
     *reinterpret_cast<float4*>(p) = make_float4(r[0], r[1], r[2], r[3]);
   else
-    *p = r[0];
+    *reinterpret_cast<double2*>(p) = make_double2(r[0], r[1]);
 }
+// the wide form for element type T
+template <typename T> constexpr int jd_wide() { return sizeof(T) == 4 ? 4 : 2; }
 
 // ---- column reductions: acc[8 p + c] += sum_i a_p[c n + i] * b_p[c n + i] for
 // the q columns of each of the NP pairs (a_p, b_p)
-template <int NP>
+template <typename T, int NP>
 struct DotPairs {
-  const float* a[NP];
-  const float* b[NP];
+  const T* a[NP];
+  const T* b[NP];
 };
 
-template <int NP, int V>
-__global__ void __launch_bounds__(JD_T) k_col_dots(int n, int q, DotPairs<NP> pr, double* __restrict__ acc,
+template <typename T, int NP, int V>
+__global__ void __launch_bounds__(JD_T) k_col_dots(int n, int q, DotPairs<T, NP> pr, double* __restrict__ acc,
                                                    RedWs rw) {
   __shared__ double red[NP * 8][JD_T / 32];
   __shared__ double part[NP * 8];
-  float s[NP][8];
+  T s[NP][8];
 #pragma unroll
   for (int p = 0; p < NP; ++p)
 #pragma unroll
-    for (int c = 0; c < 8; ++c) s[p][c] = 0.f;
+    for (int c = 0; c < 8; ++c) s[p][c] = T(0);
   for (int i = (blockIdx.x * JD_T + threadIdx.x) * V; i < n; i += gridDim.x * JD_T * V) {
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       if (c >= q) break;
 #pragma unroll
       for (int p = 0; p < NP; ++p) {
-        float a[V], b[V];
-        ldv<V>(pr.a[p] + (size_t)c * n + i, a);
-        ldv<V>(pr.b[p] + (size_t)c * n + i, b);
+        T a[V], b[V];
+        ldv<T, V>(pr.a[p] + (size_t)c * n + i, a);
+        ldv<T, V>(pr.b[p] + (size_t)c * n + i, b);
 #pragma unroll
-        for (int u = 0; u < V; ++u) s[p][c] = fmaf(a[u], b[u], s[p][c]);
+        for (int u = 0; u < V; ++u) s[p][c] = fma(a[u], b[u], s[p][c]);
       }
     }
   }
@@ -128,30 +136,30 @@ __global__ void k_jd_init(int q, const double* __restrict__ acc, double* __restr
 }
 
 // r1 = r2 = R, v = R / beta1, s = w1 = w2 = 0
-template <int V>
-__global__ void __launch_bounds__(JD_T) k_jd_start(int n, int q, const float* __restrict__ R, float* __restrict__ r1,
-                                                   float* __restrict__ r2, float* __restrict__ v,
-                                                   float* __restrict__ s, float* __restrict__ w1,
-                                                   float* __restrict__ w2, const double* __restrict__ sc) {
-  __shared__ float sv[8];
+template <typename T, int V>
+__global__ void __launch_bounds__(JD_T) k_jd_start(int n, int q, const T* __restrict__ R, T* __restrict__ r1,
+                                                   T* __restrict__ r2, T* __restrict__ v, T* __restrict__ s,
+                                                   T* __restrict__ w1, T* __restrict__ w2,
+                                                   const double* __restrict__ sc) {
+  __shared__ T sv[8];
   if (threadIdx.x < 8) {
     const int c = threadIdx.x;
-    sv[c] = (c < q && SC(JF_ACT, c) > 0.0) ? (float)(1.0 / SC(JF_BETA1, c)) : 0.f;
+    sv[c] = (c < q && SC(JF_ACT, c) > 0.0) ? (T)(1.0 / SC(JF_BETA1, c)) : T(0);
   }
   __syncthreads();
   for (int i = (blockIdx.x * JD_T + threadIdx.x) * V; i < n; i += gridDim.x * JD_T * V) {
     for (int c = 0; c < q; ++c) {
       const size_t k = (size_t)c * n + i;
-      float r[V], z[V], vv[V];
-      ldv<V>(R + k, r);
+      T r[V], z[V], vv[V];
+      ldv<T, V>(R + k, r);
 #pragma unroll
-      for (int u = 0; u < V; ++u) z[u] = 0.f, vv[u] = r[u] * sv[c];
-      stv<V>(r1 + k, r);
-      stv<V>(r2 + k, r);
-      stv<V>(v + k, vv);
-      stv<V>(s + k, z);
-      stv<V>(w1 + k, z);
-      stv<V>(w2 + k, z);
+      for (int u = 0; u < V; ++u) z[u] = T(0), vv[u] = r[u] * sv[c];
+      stv<T, V>(r1 + k, r);
+      stv<T, V>(r2 + k, r);
+      stv<T, V>(v + k, vv);
+      stv<T, V>(s + k, z);
+      stv<T, V>(w1 + k, z);
+      stv<T, V>(w2 + k, z);
     }
   }
 }
@@ -175,15 +183,15 @@ __global__ void k_jd_coef(int q, const double* __restrict__ acc, const double* _
 // recurrence terms.  Then r1 <- r2, r2 <- y, and acc[24 + c] += ||y||^2.
 // Columns already converged are left alone.  Each locked vector is loaded once
 // per row group and applied to all columns.
-template <int V>
-__global__ void __launch_bounds__(JD_T) k_jd_lanczos(int n, int q, int nl, const float* __restrict__ Cv,
-                                                     const float* __restrict__ v, const float* __restrict__ X,
-                                                     const float* __restrict__ Xl, const double* __restrict__ theta,
-                                                     const float* __restrict__ ds, float* __restrict__ r1,
-                                                     float* __restrict__ r2, const double* __restrict__ sc,
+template <typename T, int V>
+__global__ void __launch_bounds__(JD_T) k_jd_lanczos(int n, int q, int nl, const T* __restrict__ Cv,
+                                                     const T* __restrict__ v, const T* __restrict__ X,
+                                                     const T* __restrict__ Xl, const double* __restrict__ theta,
+                                                     const T* __restrict__ ds, T* __restrict__ r1,
+                                                     T* __restrict__ r2, const double* __restrict__ sc,
                                                      double* __restrict__ acc, RedWs rw) {
-  __shared__ float cf[8][4];           // theta, e, c1, c2 per column
-  __shared__ float D[64 * 8];
+  __shared__ T cf[8][4];               // theta, e, c1, c2 per column
+  __shared__ T D[64 * 8];
   __shared__ double part[8];
   __shared__ double red[8][JD_T / 32];
   __shared__ int act[8];
@@ -191,53 +199,53 @@ __global__ void __launch_bounds__(JD_T) k_jd_lanczos(int n, int q, int nl, const
     const int c = threadIdx.x;
     const bool on = c < q && SC(JF_ACT, c) > 0.0;
     act[c] = on;
-    cf[c][0] = on ? (float)theta[c] : 0.f;
-    cf[c][1] = (on && X) ? (float)acc[16 + c] : 0.f;
-    cf[c][2] = on ? (float)SC(JF_C1, c) : 0.f;
-    cf[c][3] = on ? (float)SC(JF_C2, c) : 0.f;
+    cf[c][0] = on ? (T)theta[c] : T(0);
+    cf[c][1] = (on && X) ? (T)acc[16 + c] : T(0);
+    cf[c][2] = on ? (T)SC(JF_C1, c) : T(0);
+    cf[c][3] = on ? (T)SC(JF_C2, c) : T(0);
   }
   for (int k = threadIdx.x; k < nl * 8; k += JD_T) {
     const int l = k % nl, c = k / nl;
-    D[l * 8 + c] = (c < q && SC(JF_ACT, c) > 0.0) ? (float)acc[32 + l + c * nl] : 0.f;
+    D[l * 8 + c] = (c < q && SC(JF_ACT, c) > 0.0) ? (T)acc[32 + l + c * nl] : T(0);
   }
   __syncthreads();
-  float nrm[8];
+  T nrm[8];
 #pragma unroll
-  for (int c = 0; c < 8; ++c) nrm[c] = 0.f;
+  for (int c = 0; c < 8; ++c) nrm[c] = T(0);
   for (int i = (blockIdx.x * JD_T + threadIdx.x) * V; i < n; i += gridDim.x * JD_T * V) {
-    float y[8][V];
+    T y[8][V];
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       if (c < q) {
         const size_t k = (size_t)c * n + i;
-        float a[V], b[V], d[V];
-        ldv<V>(Cv + k, a);
-        ldv<V>(v + k, b);
+        T a[V], b[V], d[V];
+        ldv<T, V>(Cv + k, a);
+        ldv<T, V>(v + k, b);
         if (X) {
-          ldv<V>(X + k, d);
+          ldv<T, V>(X + k, d);
         } else {
 #pragma unroll
-          for (int u = 0; u < V; ++u) d[u] = 0.f;
+          for (int u = 0; u < V; ++u) d[u] = T(0);
         }
 #pragma unroll
-        for (int u = 0; u < V; ++u) y[c][u] = fmaf(-cf[c][1], d[u], fmaf(-cf[c][0], b[u], a[u]));
+        for (int u = 0; u < V; ++u) y[c][u] = fma(-cf[c][1], d[u], fma(-cf[c][0], b[u], a[u]));
       }
     }
     for (int l = 0; l < nl; ++l) {
-      float xl[V];
-      ldv<V>(Xl + (size_t)l * n + i, xl);
+      T xl[V];
+      ldv<T, V>(Xl + (size_t)l * n + i, xl);
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
         if (c < q) {
-          const float dlc = D[l * 8 + c];
+          const T dlc = D[l * 8 + c];
 #pragma unroll
-          for (int u = 0; u < V; ++u) y[c][u] = fmaf(-dlc, xl[u], y[c][u]);
+          for (int u = 0; u < V; ++u) y[c][u] = fma(-dlc, xl[u], y[c][u]);
         }
       }
     }
     if (ds) {
-      float dd[V];
-      ldv<V>(ds + i, dd);
+      T dd[V];
+      ldv<T, V>(ds + i, dd);
 #pragma unroll
       for (int c = 0; c < 8; ++c)
         if (c < q) {
@@ -249,16 +257,16 @@ __global__ void __launch_bounds__(JD_T) k_jd_lanczos(int n, int q, int nl, const
     for (int c = 0; c < 8; ++c) {
       if (c < q && act[c]) {
         const size_t k = (size_t)c * n + i;
-        float a1[V], a2[V];
-        ldv<V>(r1 + k, a1);
-        ldv<V>(r2 + k, a2);
+        T a1[V], a2[V];
+        ldv<T, V>(r1 + k, a1);
+        ldv<T, V>(r2 + k, a2);
 #pragma unroll
         for (int u = 0; u < V; ++u) {
-          y[c][u] = fmaf(-cf[c][3], a2[u], fmaf(-cf[c][2], a1[u], y[c][u]));
-          nrm[c] = fmaf(y[c][u], y[c][u], nrm[c]);
+          y[c][u] = fma(-cf[c][3], a2[u], fma(-cf[c][2], a1[u], y[c][u]));
+          nrm[c] = fma(y[c][u], y[c][u], nrm[c]);
         }
-        stv<V>(r1 + k, a2);
-        stv<V>(r2 + k, y[c]);
+        stv<T, V>(r1 + k, a2);
+        stv<T, V>(r2 + k, y[c]);
       }
     }
   }
@@ -321,22 +329,22 @@ __global__ void k_jd_givens(int q, const double* __restrict__ acc, double tol, d
 
 // w = (v - oldeps w1 - delta w2) / gamma;  w1 <- w2;  w2 <- w;  s += phi w;
 // v <- r2 / beta for the next step.
-template <int V>
-__global__ void __launch_bounds__(JD_T) k_jd_update(int n, int q, float* __restrict__ v, const float* __restrict__ r2,
-                                                    float* __restrict__ w1, float* __restrict__ w2,
-                                                    float* __restrict__ s, double* __restrict__ sc) {
-  __shared__ float cf[8][5];
+template <typename T, int V>
+__global__ void __launch_bounds__(JD_T) k_jd_update(int n, int q, T* __restrict__ v, const T* __restrict__ r2,
+                                                    T* __restrict__ w1, T* __restrict__ w2, T* __restrict__ s,
+                                                    double* __restrict__ sc) {
+  __shared__ T cf[8][5];
   __shared__ int on[8];
   if (threadIdx.x < 8) {
     const int c = threadIdx.x;
     const double act = c < q ? SC(JF_ACT, c) : 0.0;
     on[c] = act != 0.0;
-    cf[c][0] = (float)SC(JF_OLDEPS, c);
-    cf[c][1] = (float)SC(JF_DELTA, c);
-    cf[c][2] = (float)(1.0 / SC(JF_GAMMA, c));
-    cf[c][3] = (float)SC(JF_PHI, c);
+    cf[c][0] = (T)SC(JF_OLDEPS, c);
+    cf[c][1] = (T)SC(JF_DELTA, c);
+    cf[c][2] = (T)(1.0 / SC(JF_GAMMA, c));
+    cf[c][3] = (T)SC(JF_PHI, c);
     const double beta = SC(JF_BETA, c);
-    cf[c][4] = (act > 0.0 && beta > 0.0) ? (float)(1.0 / beta) : 0.f;
+    cf[c][4] = (act > 0.0 && beta > 0.0) ? (T)(1.0 / beta) : T(0);
   }
   __syncthreads();
   for (int i = (blockIdx.x * JD_T + threadIdx.x) * V; i < n; i += gridDim.x * JD_T * V) {
@@ -344,22 +352,22 @@ __global__ void __launch_bounds__(JD_T) k_jd_update(int n, int q, float* __restr
     for (int c = 0; c < 8; ++c) {
       if (c >= q || !on[c]) continue;
       const size_t k = (size_t)c * n + i;
-      float a1[V], a2[V], vv[V], ss[V], rr[V], w[V];
-      ldv<V>(w1 + k, a1);
-      ldv<V>(w2 + k, a2);
-      ldv<V>(v + k, vv);
-      ldv<V>(s + k, ss);
-      ldv<V>(r2 + k, rr);
+      T a1[V], a2[V], vv[V], ss[V], rr[V], w[V];
+      ldv<T, V>(w1 + k, a1);
+      ldv<T, V>(w2 + k, a2);
+      ldv<T, V>(v + k, vv);
+      ldv<T, V>(s + k, ss);
+      ldv<T, V>(r2 + k, rr);
 #pragma unroll
       for (int u = 0; u < V; ++u) {
         w[u] = (vv[u] - cf[c][0] * a1[u] - cf[c][1] * a2[u]) * cf[c][2];
-        ss[u] = fmaf(cf[c][3], w[u], ss[u]);
+        ss[u] = fma(cf[c][3], w[u], ss[u]);
         vv[u] = rr[u] * cf[c][4];
       }
-      stv<V>(w1 + k, a2);
-      stv<V>(w2 + k, w);
-      stv<V>(s + k, ss);
-      stv<V>(v + k, vv);
+      stv<T, V>(w1 + k, a2);
+      stv<T, V>(w2 + k, w);
+      stv<T, V>(s + k, ss);
+      stv<T, V>(v + k, vv);
     }
   }
 }
@@ -375,105 +383,125 @@ static int jd_grid(int n, int V) {
   int blocks = ceil_div(ceil_div(n, V), JD_T);
   return blocks > 152 * 8 ? 152 * 8 : (blocks < 1 ? 1 : blocks);
 }
-static int jd_vec(int n) { return n % 4 == 0 ? 4 : 1; }
+template <typename T> static int jd_vec(int n) { return n % jd_wide<T>() == 0 ? jd_wide<T>() : 1; }
+template <typename T> static int jd_cls() { return sizeof(T) == 4 ? PROF_F32 + PROF_SMALL : PROF_SMALL; }
 
-void jd_colnorms(cudaStream_t s, int n, int q, const float* R, double* acc) {
-  ProfScope ps(s, PROF_F32 + PROF_SMALL);
-  DotPairs<1> pr{{R}, {R}};
-  const int V = jd_vec(n);
-  const int g = jd_grid(n, V);
+template <typename T>
+void jd_colnorms(cudaStream_t s, int n, int q, const T* R, double* acc) {
+  ProfScope ps(s, jd_cls<T>());
+  DotPairs<T, 1> pr{{R}, {R}};
+  const int V = jd_vec<T>(n), g = jd_grid(n, V);
   const RedWs rw = red_ws((size_t)g * 8);
-  if (V == 4)
-    k_col_dots<1, 4><<<g, JD_T, 0, s>>>(n, q, pr, acc + 24, rw);
+  if (V > 1)
+    k_col_dots<T, 1, jd_wide<T>()><<<g, JD_T, 0, s>>>(n, q, pr, acc + 24, rw);
   else
-    k_col_dots<1, 1><<<g, JD_T, 0, s>>>(n, q, pr, acc + 24, rw);
+    k_col_dots<T, 1, 1><<<g, JD_T, 0, s>>>(n, q, pr, acc + 24, rw);
   count_launch();
   reduce_partials(s, rw, g, 8, acc + 24, 0, nullptr);
 }
 
-void jd_init(cudaStream_t s, int n, int q, const float* R, float* r1, float* r2, float* v, float* sol, float* w1,
-             float* w2, const double* acc, double* sc) {
-  ProfScope ps(s, PROF_F32 + PROF_SMALL);
+template <typename T>
+void jd_init(cudaStream_t s, int n, int q, const T* R, T* r1, T* r2, T* v, T* sol, T* w1, T* w2, const double* acc,
+             double* sc) {
+  ProfScope ps(s, jd_cls<T>());
   k_jd_init<<<1, 32, 0, s>>>(q, acc, sc); count_launch();
-  if (jd_vec(n) == 4)
-    k_jd_start<4><<<jd_grid(n, 4), JD_T, 0, s>>>(n, q, R, r1, r2, v, sol, w1, w2, sc);
+  const int V = jd_vec<T>(n), g = jd_grid(n, V);
+  if (V > 1)
+    k_jd_start<T, jd_wide<T>()><<<g, JD_T, 0, s>>>(n, q, R, r1, r2, v, sol, w1, w2, sc);
   else
-    k_jd_start<1><<<jd_grid(n, 1), JD_T, 0, s>>>(n, q, R, r1, r2, v, sol, w1, w2, sc);
+    k_jd_start<T, 1><<<g, JD_T, 0, s>>>(n, q, R, r1, r2, v, sol, w1, w2, sc);
   count_launch();
 }
 
-void jd_dots(cudaStream_t s, int n, int q, const float* v, const float* X, const float* Cv, double* acc) {
-  ProfScope ps(s, PROF_F32 + PROF_SMALL);
-  DotPairs<3> pr{{v, v, X}, {Cv, v, Cv}};
-  const int V = jd_vec(n), g = jd_grid(n, V);
+template <typename T>
+void jd_dots(cudaStream_t s, int n, int q, const T* v, const T* X, const T* Cv, double* acc) {
+  ProfScope ps(s, jd_cls<T>());
+  DotPairs<T, 3> pr{{v, v, X}, {Cv, v, Cv}};
+  const int V = jd_vec<T>(n), g = jd_grid(n, V);
   const RedWs rw = red_ws((size_t)g * 24);
-  if (V == 4)
-    k_col_dots<3, 4><<<g, JD_T, 0, s>>>(n, q, pr, acc, rw);
+  if (V > 1)
+    k_col_dots<T, 3, jd_wide<T>()><<<g, JD_T, 0, s>>>(n, q, pr, acc, rw);
   else
-    k_col_dots<3, 1><<<g, JD_T, 0, s>>>(n, q, pr, acc, rw);
+    k_col_dots<T, 3, 1><<<g, JD_T, 0, s>>>(n, q, pr, acc, rw);
   count_launch();
   reduce_partials(s, rw, g, 24, acc, 0, nullptr);
-  count_work(PROF_F32 + PROF_SMALL, 6.0 * n * q, 4.0 * 3 * n * q);
+  count_work(jd_cls<T>(), 6.0 * n * q, (double)sizeof(T) * 3 * n * q);
 }
 
-__global__ void k_jd_dscale(int n, const double* __restrict__ d, double guard, float* __restrict__ ds) {
+template <typename T>
+__global__ void k_jd_dscale(int n, const double* __restrict__ d, double guard, T* __restrict__ ds) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) ds[i] = (float)(1.0 / sqrt(fmax(d[i], guard)));
+  if (i < n) ds[i] = (T)(1.0 / sqrt(fmax(d[i], guard)));
 }
-void jd_dscale(cudaStream_t s, int n, const double* d, double guard, float* ds) {
-  if (n > 0) k_jd_dscale<<<ceil_div(n, 256), 256, 0, s>>>(n, d, guard, ds); count_launch();
+template <typename T>
+void jd_dscale(cudaStream_t s, int n, const double* d, double guard, T* ds) {
+  if (n > 0) k_jd_dscale<T><<<ceil_div(n, 256), 256, 0, s>>>(n, d, guard, ds); count_launch();
 }
 
-template <int V>
-__global__ void __launch_bounds__(JD_T) k_jd_rowscale(int n, int q, const float* __restrict__ ds,
-                                                      const float* __restrict__ X, float* __restrict__ Y) {
+template <typename T, int V>
+__global__ void __launch_bounds__(JD_T) k_jd_rowscale(int n, int q, const T* __restrict__ ds, const T* __restrict__ X,
+                                                      T* __restrict__ Y) {
   for (int i = (blockIdx.x * JD_T + threadIdx.x) * V; i < n; i += gridDim.x * JD_T * V) {
-    float dd[V];
-    ldv<V>(ds + i, dd);
+    T dd[V];
+    ldv<T, V>(ds + i, dd);
     for (int c = 0; c < q; ++c) {
-      float x[V];
-      ldv<V>(X + (size_t)c * n + i, x);
+      T x[V];
+      ldv<T, V>(X + (size_t)c * n + i, x);
 #pragma unroll
       for (int u = 0; u < V; ++u) x[u] *= dd[u];
-      stv<V>(Y + (size_t)c * n + i, x);
+      stv<T, V>(Y + (size_t)c * n + i, x);
     }
   }
 }
-void jd_rowscale(cudaStream_t s, int n, int q, const float* ds, const float* X, float* Y) {
-  ProfScope ps(s, PROF_F32 + PROF_SMALL);
+template <typename T>
+void jd_rowscale(cudaStream_t s, int n, int q, const T* ds, const T* X, T* Y) {
+  ProfScope ps(s, jd_cls<T>());
   if (n <= 0 || q <= 0) return;
-  if (jd_vec(n) == 4)
-    k_jd_rowscale<4><<<jd_grid(n, 4), JD_T, 0, s>>>(n, q, ds, X, Y);
+  const int V = jd_vec<T>(n), g = jd_grid(n, V);
+  if (V > 1)
+    k_jd_rowscale<T, jd_wide<T>()><<<g, JD_T, 0, s>>>(n, q, ds, X, Y);
   else
-    k_jd_rowscale<1><<<jd_grid(n, 1), JD_T, 0, s>>>(n, q, ds, X, Y);
+    k_jd_rowscale<T, 1><<<g, JD_T, 0, s>>>(n, q, ds, X, Y);
   count_launch();
 }
 
-void jd_step(cudaStream_t s, int n, int q, int nl, const float* Cv, float* v, const float* u, const float* X,
-             const float* Xl, const double* theta, const float* ds, float* r1, float* r2, float* w1, float* w2,
-             float* sol, double* acc, double* sc, double tol) {
-  ProfScope ps(s, PROF_F32 + PROF_SMALL);
+template <typename T>
+void jd_step(cudaStream_t s, int n, int q, int nl, const T* Cv, T* v, const T* u, const T* X, const T* Xl,
+             const double* theta, const T* ds, T* r1, T* r2, T* w1, T* w2, T* sol, double* acc, double* sc,
+             double tol) {
+  ProfScope ps(s, jd_cls<T>());
   k_jd_coef<<<1, 32, 0, s>>>(q, acc, theta, sc); count_launch();
-  const int V = jd_vec(n);
-  const int g = jd_grid(n, V);
+  const int V = jd_vec<T>(n), g = jd_grid(n, V);
   const RedWs rw = red_ws((size_t)g * 8);
-  if (V == 4)
-    k_jd_lanczos<4><<<g, JD_T, 0, s>>>(n, q, nl, Cv, u, X, Xl, theta, ds, r1, r2, sc, acc, rw);
+  if (V > 1)
+    k_jd_lanczos<T, jd_wide<T>()><<<g, JD_T, 0, s>>>(n, q, nl, Cv, u, X, Xl, theta, ds, r1, r2, sc, acc, rw);
   else
-    k_jd_lanczos<1><<<g, JD_T, 0, s>>>(n, q, nl, Cv, u, X, Xl, theta, ds, r1, r2, sc, acc, rw);
+    k_jd_lanczos<T, 1><<<g, JD_T, 0, s>>>(n, q, nl, Cv, u, X, Xl, theta, ds, r1, r2, sc, acc, rw);
   count_launch();
   reduce_partials(s, rw, g, 8, acc + 24, 0, nullptr);
   k_jd_givens<<<1, 32, 0, s>>>(q, acc, tol, sc); count_launch();
-  if (V == 4)
-    k_jd_update<4><<<g, JD_T, 0, s>>>(n, q, v, r2, w1, w2, sol, sc);
+  if (V > 1)
+    k_jd_update<T, jd_wide<T>()><<<g, JD_T, 0, s>>>(n, q, v, r2, w1, w2, sol, sc);
   else
-    k_jd_update<1><<<g, JD_T, 0, s>>>(n, q, v, r2, w1, w2, sol, sc);
+    k_jd_update<T, 1><<<g, JD_T, 0, s>>>(n, q, v, r2, w1, w2, sol, sc);
   count_launch();
   k_jd_retire<<<1, 32, 0, s>>>(q, sc); count_launch();
   // the Lanczos pass reads Cv, v, x, r1, r2, Xl and writes r1, r2; the update
   // reads v, r2, w1, w2, s and writes w1, w2, s, v
-  count_work(PROF_F32 + PROF_SMALL, (2.0 * nl + 14.0) * n * q, 4.0 * n * ((16.0 * q) + nl));
+  count_work(jd_cls<T>(), (2.0 * nl + 14.0) * n * q, (double)sizeof(T) * n * ((16.0 * q) + nl));
 }
+
+#define JD_INST(T)                                                                                                  \
+  template void jd_colnorms<T>(cudaStream_t, int, int, const T*, double*);                                          \
+  template void jd_init<T>(cudaStream_t, int, int, const T*, T*, T*, T*, T*, T*, T*, const double*, double*);       \
+  template void jd_dots<T>(cudaStream_t, int, int, const T*, const T*, const T*, double*);                          \
+  template void jd_dscale<T>(cudaStream_t, int, const double*, double, T*);                                         \
+  template void jd_rowscale<T>(cudaStream_t, int, int, const T*, const T*, T*);                                     \
+  template void jd_step<T>(cudaStream_t, int, int, int, const T*, T*, const T*, const T*, const T*, const double*,  \
+                           const T*, T*, T*, T*, T*, T*, double*, double*, double);
+JD_INST(float)
+JD_INST(double)
+#undef JD_INST
 
 // ===========================================================================
 // Stage 2 (Algorithm 2 with the JDQMR correction of Sec. 4): one correction

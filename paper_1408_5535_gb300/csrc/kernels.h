@@ -251,26 +251,28 @@ void cg_dir(cudaStream_t s, int n, int b, const double* R, double* P, const doub
 void cg_next(cudaStream_t s, int b, double* rr, double* rrn, const double* rr0, double tol2, double* pq, int* act,
              int* iters, int* bad);
 
-// ---- inner solves of the Jacobi-Davidson correction equation in FP32 (k_inner.cu)
-// Vectors column-major n x q (q <= 8), FP32.  acc: FP64 accumulators
+// ---- inner solves of the Jacobi-Davidson correction equation (k_inner.cu)
+// Vectors column-major n x q (q <= 8), FP32 or FP64.  acc: FP64 accumulators
 // (32 + 8 nl doubles, zeroed by the caller before each reduction): [0,8)
 // v^T C v, [8,16) v^T v, [16,24) x^T C v, [24,32) squared norms, [32, ...)
 // Xl^T C v (nl x q, leading dimension nl).  sc: the MINRES scalars (17 x 8).
-void jd_colnorms(cudaStream_t s, int n, int q, const float* R, double* acc);
-void jd_init(cudaStream_t s, int n, int q, const float* R, float* r1, float* r2, float* v, float* sol, float* w1,
-             float* w2, const double* acc, double* sc);
-void jd_dots(cudaStream_t s, int n, int q, const float* v, const float* X, const float* Cv, double* acc);
+template <typename T> void jd_colnorms(cudaStream_t s, int n, int q, const T* R, double* acc);
+template <typename T>
+void jd_init(cudaStream_t s, int n, int q, const T* R, T* r1, T* r2, T* v, T* sol, T* w1, T* w2, const double* acc,
+             double* sc);
+template <typename T> void jd_dots(cudaStream_t s, int n, int q, const T* v, const T* X, const T* Cv, double* acc);
 // One MINRES step.  u: the vector of the theta term (v itself, or in the
 // scaled form the projected P D^{-1/2} v); ds: D^{-1/2} of the scaled form
 // (null: none), applied to the operator's output before the recurrence; X null:
 // no x term (the scaled form projects x as part of Xl).
-void jd_step(cudaStream_t s, int n, int q, int nl, const float* Cv, float* v, const float* u, const float* X,
-             const float* Xl, const double* theta, const float* ds, float* r1, float* r2, float* w1, float* w2,
-             float* sol, double* acc, double* sc, double tol);
-// ds[i] = 1 / sqrt(max(d[i], guard)) (FP32): D^{-1/2} for D = diag(C)
-void jd_dscale(cudaStream_t s, int n, const double* d, double guard, float* ds);
+template <typename T>
+void jd_step(cudaStream_t s, int n, int q, int nl, const T* Cv, T* v, const T* u, const T* X, const T* Xl,
+             const double* theta, const T* ds, T* r1, T* r2, T* w1, T* w2, T* sol, double* acc, double* sc,
+             double tol);
+// ds[i] = 1 / sqrt(max(d[i], guard)): D^{-1/2} for D = diag(C)
+template <typename T> void jd_dscale(cudaStream_t s, int n, const double* d, double guard, T* ds);
 // Y[:, c] = ds .* X[:, c] for the q columns (column-major, leading dimension n)
-void jd_rowscale(cudaStream_t s, int n, int q, const float* ds, const float* X, float* Y);
+template <typename T> void jd_rowscale(cudaStream_t s, int n, int q, const T* ds, const T* X, T* Y);
 // stage 2 (one FP64 system on B, dynamic stop by the eigen-residual of x + t):
 // acc (256 doubles): [0] v^T Bv, [8] v^T v, [24] ||y||^2, [32, 32 + nq) Q^T Bv,
 // [160, 163) the eigen-residual sums; sc: JD_NSCALAR * 8 + 8 doubles

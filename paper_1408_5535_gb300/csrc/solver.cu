@@ -556,93 +556,133 @@ struct GraphCache {
   }
 };
 
-// Jacobi-Davidson corrections for the FP64 continuation of the mixed-precision
-// stage 1 (the JDQMR form of Sec. 4): the correction equation
-// (I - QQ^T)(C - theta I)(I - QQ^T) t = r, Q = [locked vectors, x], of each
-// targeted Ritz pair, solved for the block at once by MINRES in FP32 with the
-// FP32 products with C.  The outer Rayleigh-Ritz, the residuals that decide
-// convergence and the orthogonalisation of t into the basis stay in FP64.
+// Jacobi-Davidson corrections of stage 1 (the JDQMR form of Sec. 4): the
+// correction equation (I - QQ^T)(C - theta I)(I - QQ^T) t = r, Q = [locked
+// vectors, x], of each targeted Ritz pair, solved for the block at once by
+// MINRES.  In the FP64 continuation of the mixed-precision stage 1 the solve
+// runs in FP32 with the FP32 products with C (InnerJD<float>); in the FP64
+// method (opts.stage1_inner) in FP64 (InnerJD<double>).  The outer
+// Rayleigh-Ritz, the residuals that decide convergence and the
+// orthogonalisation of t into the basis are FP64 either way.
 // With the Jacobi preconditioner D = diag(C) (Sec. 4's preconditioned JDQMR)
 // the equation is solved in the scaled variable y = D^{1/2} t:
 // D^{-1/2} P (C - theta I) P D^{-1/2} y = D^{-1/2} r, a symmetric system, with
 // P = I - QQ^T and Q = [locked vectors, all q Ritz vectors of the block] on
 // both sides (the scaled vectors leave the complement of Q, so the
 // projection is applied to the operator's input as well); t = D^{-1/2} y.
-struct InnerJD {
+struct InnerSolver {
+  int64_t steps = 0, solves = 0;
+  // Tb (n x q, FP64): residuals on entry, corrections on return.  Xu: the q
+  // Ritz vectors, theta (device, q): their Ritz values, Xl: nl locked vectors;
+  // dC (device, n): diag(C) for the scaled form (null: unscaled), entries
+  // below guard raised to it.
+  virtual void solve(phsvds_ctx* ctx, int q, double* Tb, const double* Xu, const double* theta, const double* Xl,
+                     int nl, const double* dC = nullptr, double guard = 0.0) = 0;
+  // the same with FP32 storage (the FP32 stage of the mixed form)
+  virtual void solve(phsvds_ctx* ctx, int q, float* Tb, const float* Xu, const double* theta, const float* Xl, int nl,
+                     const double* dC = nullptr, double guard = 0.0) = 0;
+  virtual ~InnerSolver() = default;
+};
+
+template <typename T>
+struct InnerJD : InnerSolver {
   cudaStream_t s;
   int n, maxit, chunk = 5;
   double tol;
-  COp<float> op;
-  float *R, *r1, *r2, *v, *sol, *w1, *w2, *X, *Cv, *Xrm, *Yrm, *Xl32, *U, *ds;
+  COp<T> op;
+  T *R, *r1, *r2, *v, *sol, *w1, *w2, *X, *Cv, *Xrm, *Yrm, *Xq, *U, *ds;
   double *acc, *sc, *g1;
   GraphCache graphs;
-  int64_t steps = 0, solves = 0;
-  InnerJD(phsvds_ctx* c, Pool& pool, int n_, int kmax, COp<float> op_, int maxit_, double tol_, bool use_graphs)
+  InnerJD(phsvds_ctx* c, Pool& pool, int n_, int kmax, COp<T> op_, int maxit_, double tol_, bool use_graphs)
       : s(c->stream), n(n_), maxit(maxit_), tol(tol_), op(op_) {
     const size_t nn = (size_t)n;
-    R = pool.get<float>(nn * 8);
-    r1 = pool.get<float>(nn * 8);
-    r2 = pool.get<float>(nn * 8);
-    v = pool.get<float>(nn * 8);
-    sol = pool.get<float>(nn * 8);
-    w1 = pool.get<float>(nn * 8);
-    w2 = pool.get<float>(nn * 8);
-    X = pool.get<float>(nn * 8);
-    Cv = pool.get<float>(nn * 8);
-    Xrm = pool.get<float>(nn * 8);
-    Yrm = pool.get<float>(nn * 8);
-    Xl32 = pool.get<float>(nn * (kmax + 8));
-    U = pool.get<float>(nn * 8);
-    ds = pool.get<float>(nn);
+    R = pool.get<T>(nn * 8);
+    r1 = pool.get<T>(nn * 8);
+    r2 = pool.get<T>(nn * 8);
+    v = pool.get<T>(nn * 8);
+    sol = pool.get<T>(nn * 8);
+    w1 = pool.get<T>(nn * 8);
+    w2 = pool.get<T>(nn * 8);
+    X = pool.get<T>(nn * 8);
+    Cv = pool.get<T>(nn * 8);
+    Xrm = pool.get<T>(nn * 8);
+    Yrm = pool.get<T>(nn * 8);
+    Xq = pool.get<T>(nn * (kmax + 8));
+    U = pool.get<T>(nn * 8);
+    ds = pool.get<T>(nn);
     acc = pool.get<double>(32 + 8 * 64);
     sc = pool.get<double>(JD_NSCALAR * 8);
     g1 = pool.get<double>(8 * 64);
     graphs.enabled = use_graphs;
   }
-  // Tb (n x q, FP64): residuals on entry, corrections on return.  Xu: the q
-  // Ritz vectors, theta (device, q): their Ritz values, Xl: nl locked vectors;
-  // dC (device, n): diag(C) for the scaled form (null: unscaled), entries
-  // below guard raised to it.
+  // the caller's vectors into the solve's precision, and the result back
+  template <typename S>
+  void in(int64_t cnt, const S* src, T* dst) {
+    if constexpr (sizeof(S) == sizeof(T))
+      CUCHK(cudaMemcpyAsync(dst, src, sizeof(T) * cnt, cudaMemcpyDeviceToDevice, s));
+    else if constexpr (sizeof(T) == 4)
+      convert_f64_to_f32(s, cnt, src, dst);
+    else
+      convert_f32_to_f64(s, cnt, src, dst);
+  }
+  template <typename S>
+  void out(int64_t cnt, const T* src, S* dst) {
+    if constexpr (sizeof(S) == sizeof(T))
+      CUCHK(cudaMemcpyAsync(dst, src, sizeof(T) * cnt, cudaMemcpyDeviceToDevice, s));
+    else if constexpr (sizeof(T) == 4)
+      convert_f32_to_f64(s, cnt, src, dst);
+    else
+      convert_f64_to_f32(s, cnt, src, dst);
+  }
   void solve(phsvds_ctx* ctx, int q, double* Tb, const double* Xu, const double* theta, const double* Xl, int nl,
-             const double* dC = nullptr, double guard = 0.0) {
+             const double* dC = nullptr, double guard = 0.0) override {
+    run(ctx, q, Tb, Xu, theta, Xl, nl, dC, guard);
+  }
+  void solve(phsvds_ctx* ctx, int q, float* Tb, const float* Xu, const double* theta, const float* Xl, int nl,
+             const double* dC = nullptr, double guard = 0.0) override {
+    run(ctx, q, Tb, Xu, theta, Xl, nl, dC, guard);
+  }
+  template <typename S>
+  void run(phsvds_ctx* ctx, int q, S* Tb, const S* Xu, const double* theta, const S* Xl, int nl, const double* dC,
+           double guard) {
     Host h(ctx);
     const size_t nq = (size_t)n * q;
     const bool scaled = dC != nullptr;
-    convert_f64_to_f32(s, (int64_t)nq, Tb, R);
-    convert_f64_to_f32(s, (int64_t)nq, Xu, X);
-    if (nl) convert_f64_to_f32(s, (int64_t)n * nl, Xl, Xl32);
+    in((int64_t)nq, Tb, R);
+    in((int64_t)nq, Xu, X);
+    if (nl) in((int64_t)n * nl, Xl, Xq);
     // the scaled form projects against Q = [Xl, X]
     const int nq_ = scaled ? nl + q : nl;
     if (scaled) {
-      CUCHK(cudaMemcpyAsync(Xl32 + (size_t)n * nl, X, sizeof(float) * nq, cudaMemcpyDeviceToDevice, s));
-      jd_dscale(s, n, dC, guard, ds);
-      jd_rowscale(s, n, q, ds, R, R);
+      CUCHK(cudaMemcpyAsync(Xq + (size_t)n * nl, X, sizeof(T) * nq, cudaMemcpyDeviceToDevice, s));
+      jd_dscale<T>(s, n, dC, guard, ds);
+      jd_rowscale<T>(s, n, q, ds, R, R);
     }
     zero(s, v, (size_t)n * 8);   // the columns past q feed the SpMM's padding
     if (scaled) zero(s, U, (size_t)n * 8);
     zero(s, acc, 32);
-    jd_colnorms(s, n, q, R, acc);
-    jd_init(s, n, q, R, r1, r2, v, sol, w1, w2, acc, sc);
+    jd_colnorms<T>(s, n, q, R, acc);
+    jd_init<T>(s, n, q, R, r1, r2, v, sol, w1, w2, acc, sc);
     const int w = spmm_width(q);
     const size_t nacc = 32 + (size_t)8 * nq_;
-    Basis<float> P{Xl32, n, nq_, nullptr, 0, 0};
+    Basis<T> P{Xq, n, nq_, nullptr, 0, 0};
     // u: the operator's input (v, or P D^{-1/2} v in the scaled form)
-    float* u = scaled ? U : v;
+    T* u = scaled ? U : v;
     auto step = [&]() {
       if (scaled) {
-        jd_rowscale(s, n, q, ds, v, U);
+        jd_rowscale<T>(s, n, q, ds, v, U);
         zero(s, g1, (size_t)nq_ * q);
-        cgs_pass<float>(s, n, P, U, n, q, nullptr, g1, nullptr);
-        cgs_pass<float>(s, n, P, U, n, q, g1, nullptr, nullptr);
+        cgs_pass<T>(s, n, P, U, n, q, nullptr, g1, nullptr);
+        cgs_pass<T>(s, n, P, U, n, q, g1, nullptr, nullptr);
       }
-      cm_to_rm<float>(s, n, u, n, w, Xrm);
+      cm_to_rm<T>(s, n, u, n, w, Xrm);
       op.apply(s, w, Xrm, Yrm);
-      rm_to_cm<float>(s, n, Yrm, w, Cv, n);
+      rm_to_cm<T>(s, n, Yrm, w, Cv, n);
       zero(s, acc, nacc);
-      if (nq_) cgs_pass<float>(s, n, P, Cv, n, q, nullptr, acc + 32, nullptr);
-      jd_dots(s, n, q, u, X, Cv, acc);
-      jd_step(s, n, q, nq_, Cv, v, u, scaled ? nullptr : X, Xl32, theta, scaled ? ds : nullptr, r1, r2, w1, w2, sol,
-              acc, sc, tol);
+      if (nq_) cgs_pass<T>(s, n, P, Cv, n, q, nullptr, acc + 32, nullptr);
+      jd_dots<T>(s, n, q, u, X, Cv, acc);
+      jd_step<T>(s, n, q, nq_, Cv, v, u, scaled ? nullptr : X, Xq, theta, scaled ? ds : nullptr, r1, r2, w1, w2, sol,
+                 acc, sc, tol);
     };
     double* hact = h.at<double>(16384);  // bytes [16384, 16448)
     int it = 0;
@@ -661,8 +701,8 @@ struct InnerJD {
     }
     steps += it;
     ++solves;
-    if (scaled) jd_rowscale(s, n, q, ds, sol, sol);
-    convert_f32_to_f64(s, (int64_t)nq, sol, Tb);
+    if (scaled) jd_rowscale<T>(s, n, q, ds, sol, sol);
+    out((int64_t)nq, sol, Tb);
   }
 };
 
@@ -774,7 +814,7 @@ struct Stage1 {
   int rec_max = 0, rec_every = 0;
   // Jacobi-Davidson corrections with FP32 inner solves (FP64 continuation of
   // the mixed-precision stage 1), or null for the plain GD+k correction
-  InnerJD* jd = nullptr;
+  InnerSolver* jd = nullptr;
   // the Olsen correction with a shift-free M (a preconditioner given by the
   // caller, M^{-1} M^{-T} of Sec. 4): diagC holds m_j^2 and theta is taken as 0
   bool shift_free = false;
@@ -1134,16 +1174,14 @@ struct Stage1 {
           CUCHK(cudaMemcpyAsync(XU + (size_t)c * n, Xr + (size_t)unconv[c] * n, sizeof(T) * n,
                                 cudaMemcpyDeviceToDevice, s));
       }
-      if constexpr (sizeof(T) == 8) {
-        if (jd && nu > 0) {
-          double* hu = h.at<double>(1152);   // bytes [1152, 1216): theta of the corrected columns
-          for (int c = 0; c < nu; ++c) hu[c] = thv[unconv[c]];
-          CUCHK(cudaMemcpyAsync(thU, hu, sizeof(double) * nu, cudaMemcpyHostToDevice, s));
-          if (precond == PHSVDS_PREC_JACOBI)
-            jd->solve(ctx, nu, Tb, XU, thU, Xl, nlock, diagC, EPS64 * std::max(out.theta_max, 1e-300));
-          else
-            jd->solve(ctx, nu, Tb, XU, thU, Xl, nlock);
-        }
+      if (jd && nu > 0) {
+        double* hu = h.at<double>(1152);   // bytes [1152, 1216): theta of the corrected columns
+        for (int c = 0; c < nu; ++c) hu[c] = thv[unconv[c]];
+        CUCHK(cudaMemcpyAsync(thU, hu, sizeof(double) * nu, cudaMemcpyHostToDevice, s));
+        if (precond == PHSVDS_PREC_JACOBI)
+          jd->solve(ctx, nu, Tb, XU, thU, Xl, nlock, diagC, EPS64 * std::max(out.theta_max, 1e-300));
+        else
+          jd->solve(ctx, nu, Tb, XU, thU, Xl, nlock);
       }
       if (precond == PHSVDS_PREC_LEARNED && lp && nu > 0) {
         double* hu2 = h.at<double>(1088);    // bytes [1088, 1152): ||r||^2 of the corrected columns
@@ -1973,7 +2011,8 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
   s1.rec_max = o.record_r ? o.record_max : 0;
   s1.rec_every = o.record_every;
   int64_t iters32 = 0, mv32 = 0, jac32[4] = {0, 0, 0, 0}, stag32 = 0;
-  std::unique_ptr<InnerJD> jd;
+  std::unique_ptr<InnerSolver> jd;
+  int64_t jd32_steps = 0, jd32_solves = 0;   // the FP32 stage's inner solves (mixed_inner = 2)
   double theta_max32 = 0.0;
   // on a stage-1 error the counters so far still reach the caller
   auto partial_stats = [&](const Stage1Out& a, const Stage1Out* b32) {
@@ -1999,6 +2038,11 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
   }
   if (mixed) {
     Stage1<float> s1f(ctx, pool, A.n, k, o, largest, tol_in, EPS32, precond1, diag1, op32);
+    std::unique_ptr<InnerSolver> jdf;
+    if (o.mixed_inner == 2 && (precond1 == PHSVDS_PREC_NONE || precond1 == PHSVDS_PREC_JACOBI)) {
+      jdf = std::make_unique<InnerJD<float>>(ctx, pool, A.n, k, op32, o.inner_maxit, o.inner_tol, !o.profile);
+      s1f.jd = jdf.get();
+    }
     s1f.lp = &ld;
     s1f.shift_free = given;
     float* X0f = nullptr;
@@ -2019,6 +2063,7 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
     }
     iters32 = s1f.out.iters;
     mv32 = s1f.out.mv;
+    if (jdf) jd32_steps = jdf->steps, jd32_solves = jdf->solves;
     jac32[0] = s1f.out.jac_sweeps;
     jac32[1] = s1f.out.jac_rot;
     jac32[2] = s1f.out.jac_calls;
@@ -2030,8 +2075,8 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
     convert_f32_to_f64(s, (int64_t)A.n * k, s1f.Xl, X0);
     s1.out.restarts = s1f.out.restarts;
     s1.out.theta_max = s1f.out.theta_max;  // the ||C|| estimate carries over
-    if (o.mixed_inner == 1 && (s1.precond == PHSVDS_PREC_NONE || s1.precond == PHSVDS_PREC_JACOBI)) {
-      jd = std::make_unique<InnerJD>(ctx, pool, A.n, k, op32, o.inner_maxit, o.inner_tol, !o.profile);
+    if (o.mixed_inner >= 1 && (s1.precond == PHSVDS_PREC_NONE || s1.precond == PHSVDS_PREC_JACOBI)) {
+      jd = std::make_unique<InnerJD<float>>(ctx, pool, A.n, k, op32, o.inner_maxit, o.inner_tol, !o.profile);
       s1.jd = jd.get();
     }
     try {
@@ -2043,6 +2088,10 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
       throw;
     }
   } else {
+    if (o.stage1_inner == 1) {
+      jd = std::make_unique<InnerJD<double>>(ctx, pool, A.n, k, op64, o.inner_maxit, o.inner_tol, !o.profile);
+      s1.jd = jd.get();
+    }
     try {
       s1.run(X0d, nx0);
     } catch (const PhError&) {
@@ -2190,8 +2239,8 @@ static void solve_impl(phsvds_ctx* ctx, int64_t m, int64_t n, int64_t nnz, const
     st->fell_back_at = s1.out.fell_back_at;
     st->recorded = s1.out.recorded;
     st->stage1_stagnation_locks = s1.out.stag_locks + stag32;
-    st->inner_steps = jd ? jd->steps : 0;
-    st->inner_solves = jd ? jd->solves : 0;
+    st->inner_steps = (jd ? jd->steps : 0) + jd32_steps;
+    st->inner_solves = (jd ? jd->solves : 0) + jd32_solves;
     st->inner2_steps = inner2_steps;
     st->inner2_solves = inner2_solves;
     st->t_stage1_ms = std::chrono::duration<double, std::milli>(t1b - t1a).count();
@@ -2530,6 +2579,7 @@ phsvds_status phsvds_default_opts(phsvds_opts* o) {
   o->dyn_max_switch = 8;
   o->deterministic = 1;
   o->norm_A = 0.0;
+  o->stage1_inner = 0;
   return PHSVDS_OK;
 }
 
@@ -2636,6 +2686,11 @@ phsvds_status phsvds_solve(phsvds_handle h, int64_t m, int64_t n, int64_t nnz, c
     return set_err(h, PHSVDS_ERR_INVALID, "recording needs record_max >= 0 and record_every >= 1");
   if (o.stage2_precond != 0 && o.stage2_precond != 1)
     return set_err(h, PHSVDS_ERR_INVALID, "stage2_precond must be 0 or 1");
+  if ((o.stage1_inner != 0 && o.stage1_inner != 1) ||
+      (o.stage1_inner == 1 && (o.precision != PHSVDS_FP64 || (precond != PHSVDS_PREC_NONE &&
+                                                               precond != PHSVDS_PREC_JACOBI) || o.dynamic)))
+    return set_err(h, PHSVDS_ERR_INVALID,
+                   "stage1_inner must be 0 or 1 (1 with FP64, no or the Jacobi preconditioner, not dynamic)");
   if (!std::isfinite(o.norm_A) || (o.dynamic != 0 && o.norm_A != 0.0))
     return set_err(h, PHSVDS_ERR_INVALID, "norm_A must be finite (and 0 with dynamic = 1)");
   if (o.dynamic != 0 && (o.dynamic != 1 || target != PHSVDS_SMALLEST || o.dyn_init_iter < 1 ||
@@ -2656,8 +2711,8 @@ phsvds_status phsvds_solve(phsvds_handle h, int64_t m, int64_t n, int64_t nnz, c
       if (!std::isfinite(o.precond_M[i]) || o.precond_M[i] == 0.0)
         return set_err(h, PHSVDS_ERR_INVALID, "precond_M must be finite and nonzero");
   }
-  if ((o.mixed_inner != 0 && o.mixed_inner != 1) || o.inner_maxit < 1 || !(o.inner_tol > 0) || o.inner_tol >= 1)
-    return set_err(h, PHSVDS_ERR_INVALID, "mixed_inner must be 0 or 1, inner_maxit >= 1, 0 < inner_tol < 1");
+  if (o.mixed_inner < 0 || o.mixed_inner > 2 || o.inner_maxit < 1 || !(o.inner_tol > 0) || o.inner_tol >= 1)
+    return set_err(h, PHSVDS_ERR_INVALID, "mixed_inner must be 0, 1 or 2, inner_maxit >= 1, 0 < inner_tol < 1");
   if (o.init_V && (o.init_nv < 0 || o.init_nv > o.max_basis || (o.init_nv == 0 && k > o.max_basis)))
     return set_err(h, PHSVDS_ERR_INVALID, "init_V needs 0 <= init_nv <= max_basis (0 = k columns)");
   try {

@@ -39,7 +39,7 @@ class Opts(C.Structure):
                 ("stage2_precond", C.c_int), ("precond_M", C.c_void_p), ("stage2_inner", C.c_int),
                 ("inner2_maxit", C.c_int), ("inner2_patience", C.c_int), ("dynamic", C.c_int),
                 ("dyn_init_iter", C.c_int), ("dyn_max_switch", C.c_int), ("deterministic", C.c_int),
-                ("norm_A", C.c_double)]
+                ("norm_A", C.c_double), ("stage1_inner", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -94,3 +94,31 @@ def test_batched_reports_per_matrix_status(h, batch):
 def test_batched_empty_and_invalid(h):
     out, status = native.phsvds_solve_batched(h, [], 3)
     assert out == [] and status == native.PHSVDS_OK
+
+
+def test_full_size_members_batched_equal_single_solves(h):
+    """The four largest members of the full batched workload (64 matrices,
+    n ~ U[2000, 60000]; here n ~ 5.4e4-5.9e4), k = 5 smallest and k = 5
+    largest, mixed precision, 4 workers: every result meets the plain
+    definition (residual <= 1e-14 ||A||, recomputed here with ||A|| = the
+    largest sigma found) and equals the single FP64 solve of the same matrix
+    to 1e-10 relative."""
+    mats = synth.batched_set(64)
+    big = sorted(mats, key=lambda A: -A.nnz)[:4]
+    tup = [(A.m, A.n, A.row_ptr, A.col, A.val) for A in big]
+    om = native.default_opts(precision=native.MIXED, time_limit_s=120.0)
+    of = native.default_opts(precision=native.FP64, time_limit_s=120.0)
+    res = {}
+    for tgt in (native.SMALLEST, native.LARGEST):
+        out, status = native.phsvds_solve_batched(h, tup, 5, tgt, DELTA, native.PREC_NONE, om, concurrency=4,
+                                                  want_vectors=True)
+        assert status == native.PHSVDS_OK
+        res[tgt] = out
+    for i, A in enumerate(big):
+        nA = res[native.LARGEST][i][0][0]
+        for tgt in (native.SMALLEST, native.LARGEST):
+            sig, U, V = res[tgt][i][0], res[tgt][i][1], res[tgt][i][2]
+            assert np.all(_resid(A, sig, U, V) <= DELTA * nA), (i, tgt)
+            ref = native.phsvds_solve(h, A.m, A.n, A.row_ptr, A.col, A.val, 5, tgt, DELTA, native.PREC_NONE, of,
+                                      want_vectors=False)[0]
+            assert np.all(np.abs(sig - ref) <= 1e-10 * ref), (i, tgt, sig, ref)

@@ -75,3 +75,26 @@ def test_smallest_20_match_the_dense_svd(h, member):
     r = _resid(S, sig, U, V)
     assert np.all(r <= DELTA * sv[-1]), np.max(r) / sv[-1]
     assert st["inner_solves"] > 0
+
+
+def test_fp64_jacobi_davidson_stage1_matches_too(h, member):
+    """The same algorithm in one precision (opts.stage1_inner: FP64 MINRES
+    inner solves on the FP64 products with C): the same 20 values, in fewer
+    outer iterations than the plain FP64 GD+k with the Olsen-Jacobi
+    correction."""
+    A, S, sv = member
+    k = 20
+    runs = {}
+    for inner in (0, 1):
+        o = native.default_opts(block_size=8, precision=native.FP64, stage1_inner=inner, stage2_inner=1,
+                                norm_A=-1.0, time_limit_s=120.0)
+        runs[inner] = native.phsvds_solve(h, A.m, A.n, A.row_ptr, A.col, A.val, k, native.SMALLEST, DELTA,
+                                          native.PREC_JACOBI, o)
+    for inner, (sig, U, V, res, st, _) in runs.items():
+        ref = sv[:k]
+        assert np.all(np.abs(sig - ref) <= 1e-10 * ref), (inner, np.max(np.abs(sig - ref) / ref))
+        assert np.all(_resid(S, sig, U, V) <= DELTA * sv[-1])
+    st0, st1 = runs[0][4], runs[1][4]
+    assert st1["inner_solves"] > 0 and st0["inner_solves"] == 0
+    print("FP64 stage-1 outer iterations: GD+k", st0["iters_stage1"], "JD", st1["iters_stage1"])
+    assert st1["iters_stage1"] < st0["iters_stage1"]
