@@ -1694,6 +1694,21 @@ struct Stage2 {
       // near the tolerance the estimate is checked against a fresh residual
       const double rf = rn < 4.0 * tolB ? fresh_resid(th1) : -1.0;
       if (trace_on()) {
+        if (!have_prev) {
+          // the smallest singular value of R by the one-sided Jacobi SVD, beside
+          // the inverse iteration's (a diagnostic of the trace only)
+          double* Rc = pool.get<double>(LD * LD);
+          double* Sc = pool.get<double>(LD * LD);
+          double* sg = pool.get<double>(LD);
+          CUCHK(cudaMemcpyAsync(Rc, R, sizeof(double) * LD * LD, cudaMemcpyDeviceToDevice, s));
+          set_identity(s, j, Sc, LD);
+          jacobi_svd_ld(s, j, Rc, LD, Sc, LD, sg, 1e-15, 60, nullptr);
+          CUCHK(cudaMemcpyAsync(h.at<double>(4096), sg, sizeof(double) * j, cudaMemcpyDeviceToHost, s));
+          sync(s);
+          double mn = INFINITY;
+          for (int i = 0; i < j; ++i) mn = std::min(mn, *h.at<double>(4096 + 8 * i));
+          fprintf(stderr, "s2 target %d first iteration: sigma_min(R) by SVD %.6e\n", target, mn);
+        }
         CUCHK(cudaMemcpyAsync(h.at<int>(40), sw + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
         sync(s);
         fprintf(stderr, "s2 it=%lld j=%d target=%d shift=%.17g th1=%.17g rn=%.6e rf=%.6e sigmin=%.6e ri=%d\n",
