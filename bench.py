@@ -41,7 +41,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--c3s-steps", type=int, default=2,
-                   help="timed mixed-precision solves of C3's k=20 smallest triplets at full size (0: skip)")
+                   help="timed mixed-precision solves of the full-size smallest-triplet workloads (C3's k=20 "
+                        "smallest, the 512x512 grid's k=10 smallest; 0: skip)")
     p.add_argument("--c3s-mixed-inner", type=int, default=1, help="opts.mixed_inner of that solve")
     p.add_argument("--workload", default="c3", choices=["c3", "grid"],
                    help="c3: random sparse 1e6 x 5e5, k=20 largest (default); grid: weighted grid gradient, "
@@ -888,47 +889,44 @@ def run_learned(a):
             "speedup_learned_over_jacobi": summ["jacobi"]["mean_seconds"] / summ["learned"]["mean_seconds"]}
 
 
-def run_c3_smallest(a):
-    """C3's k = 20 smallest triplets at full size (the same 1e6 x 5e5 matrix
-    as the headline, tol 1e-14 ||A||), mixed precision against FP64 with the
-    same algorithm: the Jacobi preconditioner with the scaled Jacobi-Davidson
-    inner solves in stage 1 (FP32 MINRES in the mixed form, FP64 MINRES with
-    opts.stage1_inner in the FP64 form), JDQMR in stage 2, and ||A||
-    estimated before stage 1 (opts.norm_A = -1).  Per precision one untimed
-    solve (autotuner, graphs), then timed solves with CUDA events on the
-    library's stream (a.c3s_steps for mixed, one for FP64).  The residuals of
-    the returned triplets are recomputed here on the host against the estimate
-    of ||A||, a lower bound, so the check is at least as strict as
-    1e-14 ||A||; the two precisions' values are compared with each other."""
+def smallest_pair(a, A, k, block, steps, workload):
+    """The k smallest triplets of A at tol 1e-14 ||A||, mixed precision
+    against FP64 with the same algorithm: the Jacobi preconditioner with the
+    scaled Jacobi-Davidson inner solves in stage 1 (FP32 MINRES in the mixed
+    form, FP64 MINRES with opts.stage1_inner in the FP64 form), JDQMR in
+    stage 2, and ||A|| estimated before stage 1 (opts.norm_A = -1).  Per
+    precision one untimed solve (autotuner, graphs), then timed solves with
+    CUDA events on the library's stream (`steps` for mixed, one for FP64).
+    The residuals of the returned triplets are recomputed here on the host
+    against the estimate of ||A||, a lower bound, so the check is at least as
+    strict as 1e-14 ||A||; the two precisions' values are compared."""
     import numpy as np
     import scipy.sparse as sp
     import torch
-    from paper_1408_5535_gb300 import native, synth
-    A = synth.random_sparse(1000000, 500000, 12.0, 3)
+    from paper_1408_5535_gb300 import native
     stream = torch.cuda.Stream()
     h = native.Handle(0, stream.cuda_stream)
     rp, ci, va = (torch.from_numpy(x).cuda() for x in (A.row_ptr, A.col, A.val))
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
     S = sp.csr_matrix((A.val, A.col, A.row_ptr), shape=(A.m, A.n))
-    k = 20
-    legs = {"mixed": (native.default_opts(block_size=8, precision=native.MIXED, mixed_inner=a.c3s_mixed_inner,
-                                          stage2_inner=1, norm_A=-1.0, time_limit_s=300.0), max(1, a.c3s_steps)),
-            "fp64": (native.default_opts(block_size=8, precision=native.FP64, stage1_inner=1, stage2_inner=1,
+    legs = {"mixed": (native.default_opts(block_size=block, precision=native.MIXED, mixed_inner=a.c3s_mixed_inner,
+                                          stage2_inner=1, norm_A=-1.0, time_limit_s=300.0), max(1, steps)),
+            "fp64": (native.default_opts(block_size=block, precision=native.FP64, stage1_inner=1, stage2_inner=1,
                                          norm_A=-1.0, time_limit_s=300.0), 1)}
     out = {}
-    for name, (o, steps) in legs.items():
+    for name, (o, nsteps) in legs.items():
         def solve(vectors):
             return native.phsvds_solve(h, A.m, A.n, rp, ci, va, k, native.SMALLEST, TOL, native.PREC_JACOBI, o,
                                        on_device=True, want_vectors=vectors)
         solve(False)
         times, res = [], None
-        for i in range(steps):
+        for i in range(nsteps):
             flush.fill_(1.0)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            res = solve(i == steps - 1)
+            res = solve(i == nsteps - 1)
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
@@ -944,16 +942,39 @@ def run_c3_smallest(a):
                      "iters_stage2": st["iters_stage2"], "inner_steps_stage1": st["inner_steps"],
                      "inner_steps_stage2": st["inner2_steps"], "t_stage1_ms": st["t_stage1_ms"],
                      "t_stage2_ms": st["t_stage2_ms"]}
+    h.close()
     sm, sf = np.array(out["mixed"]["sigma"]), np.array(out["fp64"]["sigma"])
-    return {"workload": "the headline matrix, k=20 smallest, block 8, tol 1e-14*||A||, Jacobi preconditioner with "
-                        "scaled Jacobi-Davidson inner solves in stage 1, JDQMR in stage 2, ||A|| estimated by 30 "
-                        "Lanczos steps on C (opts.norm_A = -1); mixed (FP32 stage and FP32 inner solves) against "
-                        "FP64 (opts.stage1_inner = 1, FP64 inner solves)",
+    return {"workload": workload + "; Jacobi preconditioner with scaled Jacobi-Davidson inner solves in stage 1, "
+                                   "JDQMR in stage 2, ||A|| estimated by 30 Lanczos steps on C (opts.norm_A = -1); "
+                                   "mixed (FP32 stage and FP32 inner solves) against FP64 (opts.stage1_inner = 1)",
             "mixed": out["mixed"], "fp64": out["fp64"],
             "speedup_mixed_over_fp64": out["fp64"]["ms"] / out["mixed"]["ms"],
-            "max_sigma_rel_diff_mixed_vs_fp64": float(np.max(np.abs(sm - sf) / sf)),
-            "plain_fp64": "the plain FP64 method (GD+k with the Olsen-Jacobi correction, no inner solves) reaches "
-                          "its restart limit on this family already at 100000 x 50000"}
+            "max_sigma_rel_diff_mixed_vs_fp64": float(np.max(np.abs(sm - sf) / sf))}
+
+
+def run_c3_smallest(a):
+    """C3's k = 20 smallest triplets at full size (the headline's matrix)."""
+    from paper_1408_5535_gb300 import synth
+    A = synth.random_sparse(1000000, 500000, 12.0, 3)
+    r = smallest_pair(a, A, 20, 8, a.c3s_steps,
+                      "the headline matrix (random sparse 1000000x500000, seed 3), k=20 smallest, block 8, "
+                      "tol 1e-14*||A||")
+    r["plain_fp64"] = ("the plain FP64 method (GD+k with the Olsen-Jacobi correction, no inner solves) reaches its "
+                       "restart limit on this family already at 100000 x 50000")
+    return r
+
+
+def run_c2(a):
+    """The weighted 512 x 512 grid gradient (m = 525,312, n = 262,144,
+    log-normal sigma_log = 1.0, seed 2), k = 10 smallest, block 4."""
+    from paper_1408_5535_gb300 import synth
+    A = synth.grid_gradient(512, 1.0, 2)
+    r = smallest_pair(a, A, 10, 4, a.c3s_steps,
+                      f"weighted Dirichlet grid gradient 512x512 (log-normal sigma_log=1.0, seed 2), m={A.m}, "
+                      f"n={A.n}, nnz={A.nnz}; k=10 smallest, block 4, tol 1e-14*||A||")
+    r["plain_fp64"] = ("the plain FP64 method (unpreconditioned GD+k) needs about 5x more outer iterations per "
+                       "doubling of the grid: 18,511 at 64 x 64, and does not finish at 128 x 128 in minutes")
+    return r
 
 
 def main():
@@ -1058,6 +1079,7 @@ def main():
         line["forms"] = run_forms()
     if rank == 0 and a.workload == "c3" and a.c3s_steps > 0:
         line["c3_smallest"] = run_c3_smallest(a)
+        line["c2_grid512_smallest"] = run_c2(a)
     if rank == 0 and not a.no_cpu:
         line["cpu_baseline"] = cpu_baseline(a, cfg["k"], st["iters_stage1"] + st["iters_stage2"])
     if rank == 0:
