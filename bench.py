@@ -43,7 +43,8 @@ def parse():
     p.add_argument("--c3s-steps", type=int, default=2,
                    help="timed mixed-precision solves of the full-size smallest-triplet workloads (C3's k=20 "
                         "smallest, the 512x512 grid's k=10 smallest; 0: skip)")
-    p.add_argument("--c3s-mixed-inner", type=int, default=1, help="opts.mixed_inner of that solve")
+    p.add_argument("--c3s-mixed-inner", type=int, default=2,
+                   help="opts.mixed_inner of those mixed solves (2: Jacobi-Davidson in the FP32 stage too)")
     p.add_argument("--workload", default="c3", choices=["c3", "grid"],
                    help="c3: random sparse 1e6 x 5e5, k=20 largest (default); grid: weighted grid gradient, "
                         "k=10 smallest")
@@ -946,7 +947,9 @@ def smallest_pair(a, A, k, block, steps, workload):
     sm, sf = np.array(out["mixed"]["sigma"]), np.array(out["fp64"]["sigma"])
     return {"workload": workload + "; Jacobi preconditioner with scaled Jacobi-Davidson inner solves in stage 1, "
                                    "JDQMR in stage 2, ||A|| estimated by 30 Lanczos steps on C (opts.norm_A = -1); "
-                                   "mixed (FP32 stage and FP32 inner solves) against FP64 (opts.stage1_inner = 1)",
+                                   f"mixed (FP32 inner solves, opts.mixed_inner = {a.c3s_mixed_inner}) against FP64 "
+                                   "(opts.stage1_inner = 1, FP64 inner solves), both with at most 60 inner steps "
+                                   "and a 1e-3 residual reduction per solve",
             "mixed": out["mixed"], "fp64": out["fp64"],
             "speedup_mixed_over_fp64": out["fp64"]["ms"] / out["mixed"]["ms"],
             "max_sigma_rel_diff_mixed_vs_fp64": float(np.max(np.abs(sm - sf) / sf))}

@@ -1707,7 +1707,43 @@ struct Stage2 {
           sync(s);
           double mn = INFINITY;
           for (int i = 0; i < j; ++i) mn = std::min(mn, *h.at<double>(4096 + 8 * i));
-          fprintf(stderr, "s2 target %d first iteration: sigma_min(R) by SVD %.6e\n", target, mn);
+          // the invariants the refined search relies on: W = B V, V orthonormal, V orthogonal to D
+          double* bv = pool.get<double>((size_t)N);
+          double* gv = pool.get<double>((size_t)LD * LD);
+          double* gd = pool.get<double>((size_t)LD * (2 * k + 1));
+          double* ww = pool.get<double>(1);
+          double werr = 0.0;
+          for (int c = 0; c < j; ++c) {
+            f.B(V + (size_t)c * N, bv);
+            axpby(s, N, -1.0, W + (size_t)c * N, 1.0, bv);
+            zero(s, ww, 1);
+            col_norms2_dense<double>(s, N, bv, N, 1, ww);
+            CUCHK(cudaMemcpyAsync(h.at<double>(8192), ww, sizeof(double), cudaMemcpyDeviceToHost, s));
+            sync(s);
+            werr = std::max(werr, std::sqrt(std::max(*h.at<double>(8192), 0.0)));
+          }
+          zero(s, gv, (size_t)j * j);
+          Basis<double> PV{V, N, j, nullptr, 0, 0};
+          cgs_pass<double>(s, N, PV, V, N, std::min(j, 8), nullptr, gv, nullptr);
+          double verr = 0.0, derr = 0.0;
+          CUCHK(cudaMemcpyAsync(h.at<double>(8192), gv, sizeof(double) * j * std::min(j, 8), cudaMemcpyDeviceToHost, s));
+          sync(s);
+          for (int c = 0; c < std::min(j, 8); ++c)
+            for (int r = 0; r < j; ++r)
+              verr = std::max(verr, std::fabs(*h.at<double>(8192 + 8 * (r + c * j)) - (r == c ? 1.0 : 0.0)));
+          if (nd > 0) {
+            zero(s, gd, (size_t)nd * 8);
+            Basis<double> PD{D, N, nd, nullptr, 0, 0};
+            cgs_pass<double>(s, N, PD, V, N, std::min(j, 8), nullptr, gd, nullptr);
+            CUCHK(cudaMemcpyAsync(h.at<double>(8192), gd, sizeof(double) * nd * std::min(j, 8), cudaMemcpyDeviceToHost,
+                                  s));
+            sync(s);
+            for (int e = 0; e < nd * std::min(j, 8); ++e) derr = std::max(derr, std::fabs(*h.at<double>(8192 + 8 * e)));
+          }
+          fprintf(stderr,
+                  "s2 target %d first iteration: sigma_min(R) by SVD %.6e, max ||W - B V|| %.3e, "
+                  "|V^T V - I| (first 8 cols) %.3e, |D^T V| (first 8 cols) %.3e, j %d, nd %d\n",
+                  target, mn, werr, verr, derr, j, nd);
         }
         CUCHK(cudaMemcpyAsync(h.at<int>(40), sw + 1, sizeof(int), cudaMemcpyDeviceToHost, s));
         sync(s);

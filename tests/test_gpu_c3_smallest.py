@@ -64,10 +64,12 @@ def test_given_norm_is_used(h, member):
     assert st["norm_A_est"] == pytest.approx(2.0 * sv[-1], rel=1e-15)
 
 
-def test_smallest_20_match_the_dense_svd(h, member):
+@pytest.mark.parametrize("mixed_inner", [1, 2], ids=["mixed", "mixed-fp32-stage-jd"])
+def test_smallest_20_match_the_dense_svd(h, member, mixed_inner):
     A, S, sv = member
     k = 20
-    o = native.default_opts(block_size=8, precision=native.MIXED, stage2_inner=1, norm_A=-1.0)
+    o = native.default_opts(block_size=8, precision=native.MIXED, mixed_inner=mixed_inner, stage2_inner=1,
+                            norm_A=-1.0)
     sig, U, V, res, st, _ = native.phsvds_solve(h, A.m, A.n, A.row_ptr, A.col, A.val, k, native.SMALLEST, DELTA,
                                                 native.PREC_JACOBI, o)
     ref = sv[:k]
