@@ -1499,6 +1499,10 @@ struct Stage2 {
   int nd = 0;
   InnerJD2* jd2 = nullptr;
   double* Bxr = nullptr;
+  // the residual of the current target's own initial guess at its shift (set
+  // at each target switch; negative: not measured)
+  double guess_res = -1.0;
+  int64_t guess_restarts = 0;
 
   Stage2(phsvds_ctx* c, Pool& p, F64Ctx& ff, DevA& A, int k_, const phsvds_opts& o, double delta_, double normA_)
       : ctx(c), s(c->stream), pool(p), f(ff), m(A.m), n(A.n), N(A.m + A.n), k(k_), maxb(o.max_basis),
@@ -1553,16 +1557,27 @@ struct Stage2 {
   // (into tv, free here): the estimate W s1 - th V s1 carries the rounding of
   // every transform that W went through, which near eps ||A|| can sit on
   // either side of the tolerance.
-  double fresh_resid(double th) {
+  double fresh_resid(double th) { return resid_of(xr, th); }
+  double resid_of(const double* x, double th) {
     Host h(ctx);
-    f.B(xr, tv);
+    f.B(x, tv);
     ++mv;
-    axpby(s, N, -th, xr, 1.0, tv);
+    axpby(s, N, -th, x, 1.0, tv);
     zero(s, nrm + 1, 1);
     col_norms2_dense<double>(s, N, tv, N, 1, nrm + 1);
     CUCHK(cudaMemcpyAsync(h.at<double>(24), nrm + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
     sync(s);
     return std::sqrt(std::max(*h.at<double>(24), 0.0));
+  }
+
+  // The basis restarted from one vector (orthonormalised against D): V = [t],
+  // W = [B t], H and the QR afresh at the next iteration.
+  void restart_from(const double* t0) {
+    CUCHK(cudaMemcpyAsync(tv, t0, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+    j = 0;
+    set_identity(s, LD, S, LD);
+    s_ident = true;
+    append(tv);
   }
 
   // Append t (orthonormalised against [Xl | V]) as column j; W(:, j) = B v_j;
@@ -1689,7 +1704,21 @@ struct Stage2 {
       const double th1 = *h.at<double>(0);
       const double rn = std::sqrt(std::max(*h.at<double>(16), 0.0));
       if (!std::isfinite(th1) || !std::isfinite(rn)) throw PhError{PHSVDS_ERR_NAN, "stage 2: non-finite residual"};
-      if (r0 < 0) r0 = rn;
+      if (r0 < 0) {
+        r0 = rn;
+        // the first iteration of a target: if the kept basis gives a refined
+        // residual far above the target's own guess, start from the guess
+        if (guess_res > 0 && rn > 10.0 * guess_res && j > 1) {
+          restart_from(x0 + (size_t)target * N);
+          ++guess_restarts;
+          qr_full = true;
+          have_prev = false;
+          r0 = -1.0;
+          guess_res = -1.0;
+          continue;
+        }
+        guess_res = -1.0;
+      }
       const double tolB = delta * normA / std::sqrt(2.0);
       // near the tolerance the estimate is checked against a fresh residual
       const double rf = rn < 4.0 * tolB ? fresh_resid(th1) : -1.0;
@@ -1740,6 +1769,25 @@ struct Stage2 {
             sync(s);
             for (int e = 0; e < nd * std::min(j, 8); ++e) derr = std::max(derr, std::fabs(*h.at<double>(8192 + 8 * e)));
           }
+          // the guess's coordinates in the basis, s = V^T x0, and ||(W - mu V) s|| / ||s||
+          double* sg2 = pool.get<double>(LD);
+          double* yv = pool.get<double>((size_t)N);
+          double* wy = pool.get<double>((size_t)N);
+          zero(s, sg2, LD);
+          cgs_pass<double>(s, N, PV, const_cast<double*>(x0 + (size_t)target * N), N, 1, nullptr, sg2, nullptr);
+          tall_times_small<double>(s, N, V, N, j, sg2, LD, 1, yv, N, nullptr, 0, nullptr, nullptr);
+          tall_times_small<double>(s, N, W, N, j, sg2, LD, 1, wy, N, nullptr, 0, nullptr, nullptr);
+          axpby(s, N, -shift, yv, 1.0, wy);
+          double* nn2 = pool.get<double>(2);
+          zero(s, nn2, 2);
+          col_norms2_dense<double>(s, N, wy, N, 1, nn2);
+          col_norms2_dense<double>(s, N, yv, N, 1, nn2 + 1);
+          CUCHK(cudaMemcpyAsync(h.at<double>(8192), nn2, sizeof(double) * 2, cudaMemcpyDeviceToHost, s));
+          sync(s);
+          const double rs_ = std::sqrt(std::max(*h.at<double>(8192), 0.0)),
+                       ys_ = std::sqrt(std::max(*h.at<double>(8200), 0.0));
+          fprintf(stderr, "s2 target %d: guess in the basis: ||V V^T x0|| %.6e, its ||(W - mu V) s|| / ||s|| %.3e\n",
+                  target, ys_, ys_ > 0 ? rs_ / ys_ : -1.0);
           fprintf(stderr,
                   "s2 target %d first iteration: sigma_min(R) by SVD %.6e, max ||W - B V|| %.3e, "
                   "|V^T V - I| (first 8 cols) %.3e, |D^T V| (first 8 cols) %.3e, j %d, nd %d\n",
@@ -1786,6 +1834,8 @@ struct Stage2 {
         }
         CUCHK(cudaMemcpyAsync(tv, x0 + (size_t)target * N, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
         append(tv);
+        guess_res = resid_of(x0 + (size_t)target * N, sig_s[target]);
+        ++mv;
         if (trace_on()) {
           // the guess's own residual ||B x0 - s x0|| at its shift
           const double* xg = x0 + (size_t)target * N;
