@@ -54,6 +54,9 @@ def parse():
     p.add_argument("--block", type=int, default=0, help="block size (0: the workload's own, 8 for c3, 4 for grid)")
     p.add_argument("--precision", default="both", choices=["mixed", "fp64", "both"])
     p.add_argument("--precond", default="none", choices=["none", "jacobi"])
+    p.add_argument("--jd", action="store_true",
+                   help="solve the workload by the Jacobi-Davidson path (Jacobi preconditioner, scaled inner solves "
+                        "in stage 1, JDQMR in stage 2, ||A|| estimated)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-forms", action="store_true", help="skip the small runs of the preconditioned forms")
     p.add_argument("--no-cpu", action="store_true")
@@ -578,6 +581,10 @@ def run_ours(a, rank, world):
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     A, cfg = workload(a)
+    if a.jd:
+        cfg["path"] = ("Jacobi-Davidson: Jacobi preconditioner, scaled inner solves in stage 1 (FP32 MINRES, "
+                       f"opts.mixed_inner = {a.c3s_mixed_inner}, in the mixed form; FP64 MINRES, "
+                       "opts.stage1_inner = 1, in the FP64 form), JDQMR in stage 2, ||A|| estimated")
     target = native.LARGEST if cfg["target"] == "largest" else native.SMALLEST
     stream = torch.cuda.Stream(device=dev)
     h = native.Handle(dev, stream.cuda_stream)
@@ -586,14 +593,21 @@ def run_ours(a, rank, world):
     va = torch.from_numpy(A.val).cuda()
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
     precs = {"mixed": [native.MIXED], "fp64": [native.FP64], "both": [native.MIXED, native.FP64]}[a.precision]
-    prec_id = native.PREC_JACOBI if a.precond == "jacobi" else native.PREC_NONE
+    prec_id = native.PREC_JACOBI if (a.precond == "jacobi" or a.jd) else native.PREC_NONE
     g = golden(a)
     results = {}
     for pi, prec in enumerate(precs):
         head = pi == 0                 # the headline precision; the second is the comparison leg
         steps = a.steps if head else max(2, min(a.steps, 5))
-        o = native.default_opts(block_size=a.block, precision=prec, profile=0)
-        op = native.default_opts(block_size=a.block, precision=prec, profile=1)
+        # --jd: the Jacobi-Davidson path of the smallest-triplet blocks (Jacobi
+        # preconditioner, scaled inner solves in stage 1, JDQMR in stage 2,
+        # ||A|| estimated)
+        jdo = {}
+        if a.jd:
+            jdo = dict(stage2_inner=1, norm_A=-1.0)
+            jdo.update(dict(mixed_inner=a.c3s_mixed_inner) if prec == native.MIXED else dict(stage1_inner=1))
+        o = native.default_opts(block_size=a.block, precision=prec, profile=0, **jdo)
+        op = native.default_opts(block_size=a.block, precision=prec, profile=1, **jdo)
 
         def solve(opts, vectors=False):
             return native.phsvds_solve(h, A.m, A.n, rp, ci, va, cfg["k"], target, TOL, prec_id, opts,
