@@ -101,6 +101,55 @@ __global__ void __launch_bounds__(JD_T) k_col_dots(int n, int q, DotPairs<T, NP>
   ordered_commit(part, NP * 8, acc, 0, nullptr, rw);
 }
 
+// The three column dots of a MINRES step, acc[c] += v_c^T Cv_c, acc[8 + c] +=
+// v_c^T v_c, acc[16 + c] += x_c^T Cv_c: each array read once per column, and
+// the columns guarded by a predicate rather than a loop exit, so that the
+// loads of every column can be in flight together (one pass over a chunk of
+// rows per thread leaves no later iteration to overlap them with).  Per
+// column and per thread the sums run in the same order as k_col_dots<T, 3>.
+template <typename T, int V>
+__global__ void __launch_bounds__(JD_T) k_jd_dots3(int n, int q, const T* __restrict__ v, const T* __restrict__ X,
+                                                   const T* __restrict__ Cv, double* __restrict__ acc, RedWs rw) {
+  __shared__ double red[24][JD_T / 32];
+  __shared__ double part[24];
+  T s0[8], s1[8], s2[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) s0[c] = s1[c] = s2[c] = T(0);
+  for (int i = (blockIdx.x * JD_T + threadIdx.x) * V; i < n; i += gridDim.x * JD_T * V) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      if (c < q) {
+        const size_t k = (size_t)c * n + i;
+        T a[V], b[V], x[V];
+        ldv<T, V>(v + k, a);
+        ldv<T, V>(Cv + k, b);
+        ldv<T, V>(X + k, x);
+#pragma unroll
+        for (int u = 0; u < V; ++u) {
+          s0[c] = fma(a[u], b[u], s0[c]);
+          s1[c] = fma(a[u], a[u], s1[c]);
+          s2[c] = fma(x[u], b[u], s2[c]);
+        }
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const double w0 = warp_sum((double)s0[c]), w1 = warp_sum((double)s1[c]), w2 = warp_sum((double)s2[c]);
+    if (lane == 0) red[c][warp] = w0, red[8 + c][warp] = w1, red[16 + c][warp] = w2;
+  }
+  __syncthreads();
+  if (threadIdx.x < 24) {
+    double t = 0.0;
+    if (threadIdx.x % 8 < q)
+      for (int w = 0; w < JD_T / 32; ++w) t += red[threadIdx.x][w];
+    part[threadIdx.x] = t;
+  }
+  __syncthreads();
+  ordered_commit(part, 24, acc, 0, nullptr, rw);
+}
+
 // ---- MINRES state of the b systems: sc[field * 8 + c]
 enum JdField {
   JF_BETA1 = 0, JF_BETA, JF_OLDB, JF_DBAR, JF_EPSLN, JF_PHIBAR, JF_CS, JF_SN, JF_PHI, JF_GAMMA, JF_DELTA,
@@ -231,6 +280,9 @@ __global__ void __launch_bounds__(JD_T) k_jd_lanczos(int n, int q, int nl, const
         for (int u = 0; u < V; ++u) y[c][u] = fma(-cf[c][1], d[u], fma(-cf[c][0], b[u], a[u]));
       }
     }
+    // four locked vectors' loads in flight at a time (the sums per element
+    // keep their order over l)
+#pragma unroll 4
     for (int l = 0; l < nl; ++l) {
       T xl[V];
       ldv<T, V>(Xl + (size_t)l * n + i, xl);
@@ -416,13 +468,12 @@ void jd_init(cudaStream_t s, int n, int q, const T* R, T* r1, T* r2, T* v, T* so
 template <typename T>
 void jd_dots(cudaStream_t s, int n, int q, const T* v, const T* X, const T* Cv, double* acc) {
   ProfScope ps(s, jd_cls<T>());
-  DotPairs<T, 3> pr{{v, v, X}, {Cv, v, Cv}};
   const int V = jd_vec<T>(n), g = jd_grid(n, V);
   const RedWs rw = red_ws((size_t)g * 24);
   if (V > 1)
-    k_col_dots<T, 3, jd_wide<T>()><<<g, JD_T, 0, s>>>(n, q, pr, acc, rw);
+    k_jd_dots3<T, jd_wide<T>()><<<g, JD_T, 0, s>>>(n, q, v, X, Cv, acc, rw);
   else
-    k_col_dots<T, 3, 1><<<g, JD_T, 0, s>>>(n, q, pr, acc, rw);
+    k_jd_dots3<T, 1><<<g, JD_T, 0, s>>>(n, q, v, X, Cv, acc, rw);
   count_launch();
   reduce_partials(s, rw, g, 24, acc, 0, nullptr);
   count_work(jd_cls<T>(), 6.0 * n * q, (double)sizeof(T) * 3 * n * q);
@@ -539,6 +590,8 @@ __global__ void __launch_bounds__(JD_T) k_s2_lanczos(int64_t N, int nq, const do
   double nrm = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)JD_T + threadIdx.x; i < N; i += (int64_t)gridDim.x * JD_T) {
     double y = fma(-m, v[i], Bv[i]);
+    // four loads in flight at a time; the sum keeps its order over l
+#pragma unroll 4
     for (int l = 0; l < nq; ++l) y = fma(-g[l], Q[(size_t)l * N + i], y);
     const double a2 = r2[i];
     y = fma(-c2, a2, fma(-c1, r1[i], y));
