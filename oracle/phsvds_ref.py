@@ -20,6 +20,10 @@ Steps, in the paper's order:
   the basis grows by the residual (GD) or, in the JDQMR form of Sec. 4, by
   an inexact solution of the Jacobi-Davidson correction equation (symmetric
   QMR with a dynamic stop: a READING);
+* stage 1 may also grow its basis by the Jacobi-Davidson correction of Sec.
+  4 (jd1_correction: symmetric QMR on the projected, shifted C, Jacobi-scaled
+  when preconditioned; READINGs), and ||A|| of the user requirement may come
+  from a Lanczos estimate (lanczos_norm_c, a READING);
 * preconditioning (Sec. 4): Jacobi on C with the Olsen correction; from a
   given M ~ A, M^-1 M^-T for C and [0 M^-1; M^-T 0] for B; from C's Jacobi
   M ~ C^-1, [0 A M; M A^T 0] for B in stage 2;
@@ -50,6 +54,7 @@ EPS32 = 2.0 ** -23
 RS_INIT = 0x1000    # columns 2..b of the initial block
 RS_BREAK = 0x2000   # replacement of a numerically dependent new basis vector
 RS_U = 0x3000       # random left vector for an (extremely) small sigma
+RS_NORM = 0x4000    # start vector of the Lanczos estimate of ||C|| (Opts.norm_A < 0)
 
 
 # ---------------------------------------------------------------------------
@@ -206,6 +211,11 @@ class Opts:
     stage2_inner: str = "none"  # "none": GD, t = r; "qmr": JDQMR, t from the correction equation (Sec. 4)
     inner_maxit: int = 300      # READING: inner QMR steps per outer iteration, at most
     stage2_precond: bool = False  # smallest targets: GD stage 2 preconditioned by [0 M A^T; A M 0], M = diag(C)^-1 (Sec. 4)
+    stage1_inner: str = "none"  # "minres": stage 1 expands by the Jacobi-Davidson correction (Sec. 4), jd1_correction
+    inner1_maxit: int = 60      # READING: inner steps per stage-1 correction, at most
+    inner1_tol: float = 1e-3    # READING: ... or until the inner residual has fallen by this factor
+    norm_A: float = 0.0         # ||A|| of the user requirement: 0 the largest Ritz value of stage 1, > 0 given,
+                                # < 0 also the Lanczos estimate lanczos_norm_c (READING, Sec. 3.1)
 
 
 @dataclass
@@ -363,6 +373,18 @@ def gdk(apply_op, n: int, k: int, largest: bool, tol_fn, o: Opts, diagC=None, X0
             Xu = X[:, unconv]
             if apply_prec is not None:
                 T = np.column_stack([apply_prec(Ru[:, c], Xu[:, c]) for c in range(len(unconv))])
+            elif o.stage1_inner == "minres" and o.precond in ("none", "jacobi"):
+                # the Jacobi-Davidson correction of each target (Sec. 4), with
+                # the Jacobi scaling when preconditioned (jd1_correction)
+                sc = None
+                if o.precond == "jacobi" and diagC is not None:
+                    guard = EPS64 * max(theta_max, 1e-300)
+                    sc = 1.0 / np.sqrt(np.maximum(diagC, guard))
+                T = np.empty_like(Ru)
+                for c, i in enumerate(unconv):
+                    Q = np.column_stack([Xl, Xu]) if sc is not None else np.column_stack([Xl, Xu[:, c]])
+                    T[:, c] = jd1_correction(apply_op, Q, float(theta[i]), Ru[:, c], sc, o.inner1_maxit,
+                                             o.inner1_tol, stats)
             elif o.precond == "given" and o.precond_M is not None:
                 # M^-1 M^-T for C (Sec. 4), shift-free, Olsen form
                 m2 = np.asarray(o.precond_M, dtype=np.float64) ** 2
@@ -466,6 +488,82 @@ def symmetric_qmr(apply_M, b: np.ndarray, Qd: np.ndarray, steps: int):
         if not T[k + 1, k] > 1e-300:
             return
         Qs.append(w / T[k + 1, k])
+
+
+def jd1_correction(apply_C, Q: np.ndarray, theta: float, r: np.ndarray, sc, maxit: int, tol: float,
+                   stats: dict) -> np.ndarray:
+    """Correction of stage 1 in its Jacobi-Davidson form (Sec. 4's JDQMR idea
+    applied to C): an approximate solution t of the correction equation
+        (I - QQ^T)(C - theta I)(I - QQ^T) t = r,
+    r the residual of the Ritz pair (theta, x), Q orthonormal and containing
+    x and the locked vectors, by symmetric QMR (MINRES's iterates here).
+    READING (the paper names the inner solver and its inexact stopping but not
+    the rule; these are the GPU library's): at most maxit steps, stopping once
+    the inner residual has fallen to tol times its start.
+    READING (the Jacobi preconditioner D = diag(C), sc = D^{-1/2}): the system
+    is solved symmetrically in y = D^{1/2} t,
+        D^{-1/2} P (C - theta I) P D^{-1/2} y = D^{-1/2} r,   P = I - QQ^T,
+    and t = D^{-1/2} y; the scaled Lanczos vectors leave the complement of Q,
+    so P acts on the operator's input as well as on its output, and Q holds
+    the locked vectors and every Ritz vector of the block.  Returns t."""
+    def proj(z):
+        if Q.shape[1]:
+            for _ in range(2):
+                z = z - Q @ (Q.T @ z)
+        return z
+
+    def op(u):
+        return apply_C(u[:, None])[:, 0] - theta * u
+
+    if sc is None:
+        def apply_M(q):
+            return proj(op(proj(q))), None
+        b = proj(r)
+        Qd = Q
+    else:
+        def apply_M(q):
+            return sc * proj(op(proj(sc * q))), None
+        b = sc * r
+        Qd = np.zeros((r.size, 0))
+    beta0 = float(np.linalg.norm(b))
+    t, k = None, 0
+    for t_k, g, _, _ in symmetric_qmr(apply_M, b, Qd, maxit):
+        k += 1
+        t = t_k
+        if g <= tol * beta0:
+            break
+    stats["inner1"] = stats.get("inner1", 0) + k
+    if t is None:
+        return r.copy()
+    return t if sc is None else sc * t
+
+
+def lanczos_norm_c(apply_C, n: int, seed: int, steps: int = 30) -> float:
+    """An estimate of ||C|| = ||A||^2: the largest eigenvalue of the
+    tridiagonal matrix of `steps` Lanczos steps on C from the seeded start
+    rand_vec(seed, RS_NORM, n) (no reorthogonalisation, which the extreme
+    Ritz value does not need).  A lower bound of ||C||.
+    READING: the paper's stopping criterion ||r|| < delta ||A|| (Sec. 3.1,
+    Sec. 5) needs ||A||; Algorithm 1 estimates it by its current largest Ritz
+    value, which for the smallest triplets can sit far below ||A||; this
+    estimate is the Opts.norm_A < 0 alternative."""
+    v = rand_vec(seed, RS_NORM, n)
+    v = v / np.linalg.norm(v)
+    v0 = np.zeros(n)
+    al, be = [], []
+    beta = 0.0
+    for i in range(max(1, min(steps, n))):
+        w = apply_C(v[:, None])[:, 0]
+        a = float(v @ w)
+        w = w - a * v - beta * v0
+        al.append(a)
+        beta = float(np.linalg.norm(w))
+        if i + 1 == steps or not beta > 1e-14 * abs(a):
+            break
+        be.append(beta)
+        v0, v = v, w / beta
+    T = np.diag(al) + np.diag(be, 1) + np.diag(be, -1)
+    return float(np.max(np.linalg.eigvalsh(T)))
 
 
 def jd_correction(ops: "Ops", Xl: np.ndarray, x: np.ndarray, Bx: np.ndarray, mu: float, r: np.ndarray,
@@ -889,6 +987,8 @@ def phsvds(csr, k: int, largest: bool = False, delta: float = 1e-14, o: Opts | N
         raise ValueError("PHSVDS needs m >= n")
     ops = Ops(A)
     stats: dict = {}
+    if o.norm_A < 0:
+        stats["norm_c_est"] = lanczos_norm_c(ops.C, n, o.seed)
     diagC = np.asarray(A.multiply(A).sum(axis=0)).ravel() if o.precond == "jacobi" else None
     lam, Xv, state = gdk(ops.C, n, k, largest, stage1_tol(delta, o), o, diagC=diagC, stats=stats)
     return _after_stage1(A, ops, k, largest, delta, o, lam, Xv, state, stats)
@@ -900,6 +1000,11 @@ def _after_stage1(A, ops: Ops, k: int, largest: bool, delta: float, o: Opts, lam
     m, n = A.shape
     theta_max = stats["theta_max"]
     normA = math.sqrt(theta_max)
+    # ||A|| of the user requirement (Opts.norm_A): the switch test and stage 2
+    if o.norm_A > 0:
+        normA = max(normA, float(o.norm_A))
+    elif o.norm_A < 0:
+        normA = max(normA, math.sqrt(max(stats.get("norm_c_est", 0.0), 0.0)))
     # stage-1 triplets: s = ||A v||, u = A v / s (r_v = 0)
     AV = ops.Av(Xv)
     sig1 = np.linalg.norm(AV, axis=0)

@@ -80,3 +80,38 @@ def test_grid512_full_size_matches_shift_invert_lanczos(h, mixed_inner):
     assert np.all(np.abs(sig - ref) <= 1e-10 * ref), np.max(np.abs(sig - ref) / ref)
     assert np.all(_resid(S, sig, U, V) <= DELTA * nA), np.max(_resid(S, sig, U, V)) / nA
     assert abs(st["norm_A_est"] - nA) <= 1e-6 * nA
+
+
+def _scaled_columns_300():
+    import scipy.sparse as sp
+    A0 = synth.random_sparse(300, 150, 6.0, 21, values="gaussian", shift=0.05)
+    S = R.as_scipy(A0)
+    S = (S @ sp.diags(10.0 ** (-2.0 * synth.uniform(31, 1, 150)))).tocsr()
+    S.sort_indices()
+    return synth.Csr(S.shape[0], S.shape[1], S.indptr.astype(np.int64), S.indices.astype(np.int32), S.data)
+
+
+@pytest.mark.parametrize("case", ["grid16-unscaled", "scaled-columns-jacobi"])
+def test_fp64_jacobi_davidson_stage1_against_the_oracles_form(h, case):
+    """The FP64 Jacobi-Davidson stage 1 (opts.stage1_inner) against the
+    oracle's form of it (Opts.stage1_inner = "minres", jd1_correction): the
+    same values to 1e-10 relative, residuals recomputed here <= 1e-14 ||A||,
+    and outer iteration counts of the same order (the oracle's inner solver
+    reorthogonalises its Lanczos vectors, the GPU's runs the three-term
+    recurrence, so the counts are not equal)."""
+    if case == "grid16-unscaled":
+        A, k, b, prec, oprec = synth.grid_gradient(16, 1.0, 2), 10, 4, native.PREC_NONE, "none"
+    else:
+        A, k, b, prec, oprec = _scaled_columns_300(), 4, 2, native.PREC_JACOBI, "jacobi"
+    S = R.as_scipy(A)
+    nA = float(np.linalg.norm(S.toarray(), 2))
+    o = native.default_opts(block_size=b, precision=native.FP64, stage1_inner=1, stage2=0, time_limit_s=60.0)
+    sig, U, V, res, st, _ = native.phsvds_solve(h, A.m, A.n, A.row_ptr, A.col, A.val, k, native.SMALLEST, DELTA,
+                                                prec, o)
+    ref = R.phsvds(A, k, largest=False, delta=DELTA, o=R.Opts(block=b, precond=oprec, stage1_inner="minres",
+                                                               stage2=False))
+    assert np.all(np.abs(sig - ref.sigma) <= 1e-10 * ref.sigma), (sig, ref.sigma)
+    assert np.all(_resid(S, sig, U, V) <= 1e-12 * nA)
+    assert st["inner_solves"] > 0 and ref.stats["inner1"] > 0
+    it_gpu, it_ref = st["iters_stage1"], ref.stats["iters"]
+    assert it_gpu <= 3 * it_ref + 20 and it_ref <= 3 * it_gpu + 20, (it_gpu, it_ref)
