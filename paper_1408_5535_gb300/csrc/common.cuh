@@ -29,6 +29,15 @@ __device__ inline T warp_sum(T v) {
   return v;
 }
 
+// A warp's sum of per-thread partials in the element precision (FP32
+// butterflies for the FP32 inner solves: GB300's FP64 pipe is narrow, and
+// FP64 butterflies bound those kernels), widened to FP64 for the block and
+// grid levels of the sum.
+template <typename T>
+__device__ inline double warp_sum_wide(T v) {
+  return (double)warp_sum(v);
+}
+
 // Vectorised row access for b values per row (b in {1,2,4,8}).
 template <typename T, int B> struct Row { T v[B]; };
 

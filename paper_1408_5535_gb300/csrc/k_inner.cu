@@ -13,8 +13,8 @@
 // in FP64.
 //
 // Vectors are FP32, column-major n x b (leading dimension n); every
-// reduction accumulates per thread in FP32 and across threads and blocks in
-// FP64.  The scalars of the b recurrences live on the device, so a step needs
+// reduction accumulates per thread and per warp in FP32 and across warps and
+// blocks in FP64.  The scalars of the b recurrences live on the device, so a step needs
 // no host synchronisation and a run of steps replays as one CUDA graph.
 #include "common.cuh"
 #include "kernels.h"
@@ -49,6 +49,7 @@ __device__ inline void stv(T* __restrict__ p, const T (&r)[V]) {
 }
 // the wide form for element type T
 template <typename T> constexpr int jd_wide() { return sizeof(T) == 4 ? 4 : 2; }
+
 
 // ---- column reductions: acc[8 p + c] += sum_i a_p[c n + i] * b_p[c n + i] for
 // the q columns of each of the NP pairs (a_p, b_p)
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(JD_T) k_col_dots(int n, int q, DotPairs<T, NP>
   for (int p = 0; p < NP; ++p)
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-      const double v = warp_sum((double)s[p][c]);
+      const double v = warp_sum_wide<T>(s[p][c]);
       if (lane == 0) red[p * 8 + c][warp] = v;
     }
   __syncthreads();
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(JD_T) k_jd_dots3(int n, int q, const T* __rest
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
-    const double w0 = warp_sum((double)s0[c]), w1 = warp_sum((double)s1[c]), w2 = warp_sum((double)s2[c]);
+    const double w0 = warp_sum_wide<T>(s0[c]), w1 = warp_sum_wide<T>(s1[c]), w2 = warp_sum_wide<T>(s2[c]);
     if (lane == 0) red[c][warp] = w0, red[8 + c][warp] = w1, red[16 + c][warp] = w2;
   }
   __syncthreads();
@@ -325,7 +326,7 @@ __global__ void __launch_bounds__(JD_T) k_jd_lanczos(int n, int q, int nl, const
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int c = 0; c < 8; ++c) {
-    const double t = warp_sum((double)nrm[c]);
+    const double t = warp_sum_wide<T>(nrm[c]);
     if (lane == 0) red[c][warp] = t;
   }
   __syncthreads();
