@@ -257,8 +257,10 @@ typedef struct {
      * once, each result written once); filled with or without opts.profile */
     double class_flops[12];
     double class_bytes[12];
-    int64_t inner_solves;      /* Jacobi-Davidson corrections (opts.mixed_inner = 1): block inner solves */
-    int64_t inner_steps;       /* ... and their MINRES steps (each one FP32 product with C of the block) */
+    int64_t inner_solves;      /* Jacobi-Davidson corrections of stage 1 (opts.mixed_inner, opts.stage1_inner):
+                                  block inner solves, in every precision the solve used */
+    int64_t inner_steps;       /* ... and their MINRES steps (each one product with C of the block, in the
+                                  inner solve's precision) */
     int64_t inner2_solves;     /* JDQMR corrections of stage 2 (opts.stage2_inner = 1) */
     int64_t inner2_steps;      /* ... and their MINRES steps (each one product with B) */
     int spmm_schedule_f32;     /* schedule of the FP32 products with C (mixed precision; 0 otherwise) */
